@@ -1,0 +1,298 @@
+"""FP64 oracle of hybrid AB-/BA-GMRES (arXiv 2602.17892, Sec. 3, Algorithms 1 and 2).
+
+TEST INFRASTRUCTURE ONLY: the plain, slow, obviously-correct reference the GPU library is
+checked against.  It shares no code with the CUDA path.  Operators are plain callables on
+flat FP64 vectors, so the same routines run with the C oracle projectors, with explicit
+matrices, or with the matched pair B = A^T.
+
+Step by step it follows the paper:
+
+* Sec. 2.1, Eq. (AB_optimality)/(BA_optimality): the Krylov spaces of AB and BA;
+* Eq. (Hessenberg): Arnoldi with modified Gram-Schmidt (Alg. 1/2, lines 5-10), followed by
+  one full second MGS pass whose coefficients are added to H (reorthogonalisation);
+* Eq. (hybrid_proj): Tikhonov on the projected problem, solved through the SVD of the
+  (k+1) x k Hessenberg matrix H_k = U diag(sigma) V^T, c = ||r0|| U^T e1,
+  y = sum_i v_i sigma_i c_i / (sigma_i^2 + lambda^2);
+* Sec. 3.1: GCV(lambda) = ||H y - beta e1||^2 / trace(I - H H_lambda)^2 with
+  H_lambda = (H^T H + lambda^2 I)^{-1} H^T (lambda^2 throughout, as in Eq. (tikhonov));
+* Sec. 3.2: the discrepancy principle, used here to pick lambda: ||H y - beta e1|| = tau eta;
+* Alg. 1 line 13 / Alg. 2 line 13: x_k = x0 + B W_k y_k (AB) or x0 + W_k y_k (BA).
+
+Readings where the paper is silent (the GPU library implements the same readings):
+* GCV minimiser: 256 log-spaced lambda in [sigma_1 1e-8, sigma_1], first grid minimum, then
+  40 golden-section steps in log lambda on the neighbouring bracket (ties to the left); the
+  refined value is kept only if it is not worse than the grid point.
+* DP as a lambda rule: solve rho(lambda) = tau * noise_norm by 60 bisection steps in log
+  lambda over the same range; clamp to the range ends when there is no root.
+* x0 = 0 (u0 = 0); breakdown when h_{k+1,k} <= 1e-14 ||M w_k||.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+GCV_GRID = 256
+GCV_GOLDEN_STEPS = 40
+DP_BISECT_STEPS = 60
+LAMBDA_RANGE = 1e-8
+BREAKDOWN_TOL = 1e-14
+
+
+# ----------------------------------------------------------------------------- small problem
+
+def projected_svd(Hk: np.ndarray, beta: float):
+    """SVD of the (k+1) x k Hessenberg matrix and c = beta U^T e1 (length k+1)."""
+    U, s, Vt = np.linalg.svd(Hk, full_matrices=True)
+    c = beta * U[0, :]
+    return s, c, Vt
+
+
+def residual_sq(lam: float, s: np.ndarray, c: np.ndarray) -> float:
+    """||H y_lambda - beta e1||^2 = sum_i (lam^2 c_i / (s_i^2 + lam^2))^2 + c_{k+1}^2."""
+    k = len(s)
+    f = lam * lam / (s * s + lam * lam)
+    return float(np.sum((f * c[:k]) ** 2) + np.sum(c[k:] ** 2))
+
+
+def gcv_value(lam: float, s: np.ndarray, c: np.ndarray) -> float:
+    """GCV(lambda); trace(I_{k+1} - H H_lambda) = (k+1) - sum_i s_i^2/(s_i^2+lam^2)."""
+    k = len(s)
+    tr = (k + 1) - float(np.sum(s * s / (s * s + lam * lam)))
+    return residual_sq(lam, s, c) / (tr * tr)
+
+
+def gcv_lambda(s: np.ndarray, c: np.ndarray) -> float:
+    s1 = float(s[0])
+    grid = s1 * np.power(10.0, np.linspace(math.log10(LAMBDA_RANGE), 0.0, GCV_GRID))
+    G = np.array([gcv_value(l, s, c) for l in grid])
+    i = int(np.argmin(G))                     # first minimum: ties go to the smaller lambda
+    a = math.log(grid[max(i - 1, 0)])
+    b = math.log(grid[min(i + 1, GCV_GRID - 1)])
+    invphi = (math.sqrt(5.0) - 1.0) / 2.0
+    for _ in range(GCV_GOLDEN_STEPS):
+        x1 = b - invphi * (b - a)
+        x2 = a + invphi * (b - a)
+        if gcv_value(math.exp(x1), s, c) <= gcv_value(math.exp(x2), s, c):
+            b = x2
+        else:
+            a = x1
+    lam = math.exp(0.5 * (a + b))
+    if gcv_value(lam, s, c) > G[i]:
+        lam = float(grid[i])
+    return lam
+
+
+def dp_lambda(s: np.ndarray, c: np.ndarray, target: float) -> float:
+    """lambda with rho(lambda) = target; rho is increasing in lambda."""
+    s1 = float(s[0])
+    lo, hi = math.log(s1 * LAMBDA_RANGE), math.log(s1)
+    rho = lambda L: math.sqrt(residual_sq(math.exp(L), s, c))
+    if rho(lo) >= target:
+        return math.exp(lo)
+    if rho(hi) <= target:
+        return math.exp(hi)
+    for _ in range(DP_BISECT_STEPS):
+        mid = 0.5 * (lo + hi)
+        if rho(mid) < target:
+            lo = mid
+        else:
+            hi = mid
+    return math.exp(0.5 * (lo + hi))
+
+
+def tikhonov_y(lam: float, s: np.ndarray, c: np.ndarray, Vt: np.ndarray) -> np.ndarray:
+    """Solution of Eq. (hybrid_proj) from the SVD; lam = 0 gives the pseudo-inverse (GMRES)."""
+    k = len(s)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        coef = np.where(s > 0, s * c[:k] / (s * s + lam * lam), 0.0)
+    return Vt.T @ coef
+
+
+def choose_lambda(rule: str, s, c, lam_fixed=None, dp_target=None) -> float:
+    if rule == "none":
+        return 0.0
+    if rule == "fixed":
+        return float(lam_fixed)
+    if rule == "gcv":
+        return gcv_lambda(s, c)
+    if rule == "dp":
+        return dp_lambda(s, c, dp_target)
+    raise ValueError(rule)
+
+
+def givens_gmres_y(Hk: np.ndarray, beta: float):
+    """lambda = 0 path of Eq. (proj_pbm) by Givens rotations (Sec. 2.1: 'Givens rotations or
+    a QR factorisation of H_k').  Returns (y, |residual|)."""
+    k1, k = Hk.shape
+    R = Hk.astype(np.float64).copy()
+    g = np.zeros(k1)
+    g[0] = beta
+    for j in range(k):
+        a, b = R[j, j], R[j + 1, j]
+        r = math.hypot(a, b)
+        cs, sn = (1.0, 0.0) if r == 0 else (a / r, b / r)
+        rows = R[[j, j + 1], j:].copy()
+        R[j, j:] = cs * rows[0] + sn * rows[1]
+        R[j + 1, j:] = -sn * rows[0] + cs * rows[1]
+        gj, gj1 = g[j], g[j + 1]
+        g[j], g[j + 1] = cs * gj + sn * gj1, -sn * gj + cs * gj1
+    y = np.zeros(k)
+    for i in range(k - 1, -1, -1):
+        y[i] = (g[i] - R[i, i + 1:k] @ y[i + 1:]) / R[i, i]
+    return y, abs(g[k])
+
+
+# ----------------------------------------------------------------------------- Algorithms 1 / 2
+
+def hybrid_gmres(method: str, A, B, b, iters: int, rule: str = "gcv", lam_fixed=None,
+                 dp_target=None, reorth: bool = True, keep_iterates=(), x0=None,
+                 true_residual: bool = False):
+    """Hybrid AB-GMRES (method='ab', Algorithm 1) or hybrid BA-GMRES ('ba', Algorithm 2).
+
+    A, B: callables on flat FP64 vectors.  rule in {'none', 'fixed', 'gcv', 'dp'}; dp_target
+    is tau * ||e|| for AB and tau * ||B e|| for BA (the noise in the space where Alg. 2
+    measures its residual).  Returns a dict with the final iterate, the per-iteration
+    lambda and projected residual, H, W, y and iterates at the steps in keep_iterates.
+    """
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    if method == "ab":
+        # Alg. 1, lines 1-3: x0 = B u0 (u0 = 0 unless x0 is given), r0 = b - A x0
+        x0v = np.zeros_like(B(b)) if x0 is None else np.asarray(x0, np.float64).reshape(-1)
+        r0 = b - A(x0v)
+        M = lambda w: A(B(w))
+    elif method == "ba":
+        # Alg. 2, lines 1-3: r0 = B (b - A x0)
+        x0v = np.zeros_like(B(b)) if x0 is None else np.asarray(x0, np.float64).reshape(-1)
+        r0 = B(b - A(x0v))
+        M = lambda w: B(A(w))
+    else:
+        raise ValueError(method)
+
+    L = r0.size
+    beta = float(np.linalg.norm(r0))
+    out = dict(lambdas=[], resid=[], status="ok", iterates={}, beta=beta, true_resid=[])
+    if beta == 0.0:
+        out.update(x=x0v.copy(), H=np.zeros((1, 0)), W=np.zeros((0, L)), y=np.zeros(0), k=0,
+                   status="breakdown")
+        return out
+    W = np.zeros((iters + 1, L))
+    H = np.zeros((iters + 1, iters))
+    W[0] = r0 / beta
+    y = np.zeros(0)
+    k_done = 0
+    for k in range(1, iters + 1):
+        q = M(W[k - 1])                                  # line 5: q_k = AB w_k (or BA w_k)
+        qnorm0 = float(np.linalg.norm(q))
+        for _pass in range(2 if reorth else 1):          # lines 6-9 (+ one more pass)
+            for i in range(k):
+                d = float(q @ W[i])
+                H[i, k - 1] += d
+                q = q - d * W[i]
+        hk = float(np.linalg.norm(q))                    # line 10
+        H[k, k - 1] = hk
+        broke = hk <= BREAKDOWN_TOL * qnorm0
+        if not broke:
+            W[k] = q / hk                                # line 11
+        Hk = H[: k + 1, :k]
+        s, c, Vt = projected_svd(Hk, beta)               # line 12: find lambda
+        lam = choose_lambda(rule, s, c, lam_fixed, dp_target)
+        y = tikhonov_y(lam, s, c, Vt)                    # line 13: projected Tikhonov
+        out["lambdas"].append(lam)
+        out["resid"].append(math.sqrt(residual_sq(lam, s, c)))
+        k_done = k
+        if k in keep_iterates or true_residual:
+            xk = _form_x(method, B, x0v, W[:k], y)       # line 14
+            if k in keep_iterates:
+                out["iterates"][k] = xk
+            if true_residual:
+                r = b - A(xk)
+                out["true_resid"].append(float(np.linalg.norm(r if method == "ab" else B(r))))
+        if broke:
+            out["status"] = "breakdown"
+            break
+    out.update(x=_form_x(method, B, x0v, W[:k_done], y), H=H[: k_done + 1, :k_done],
+               W=W[: k_done + 1], y=y, k=k_done)
+    return out
+
+
+def _form_x(method, B, x0v, Wk, y):
+    z = Wk.T @ y
+    return x0v + (B(z) if method == "ab" else z)
+
+
+def restarted_hybrid_gmres(method, A, B, b, cycle: int, n_cycles: int, **kw):
+    """Sec. 3.3: after p = cycle iterations restart from the current iterate."""
+    x = None
+    hist = []
+    for _ in range(n_cycles):
+        res = hybrid_gmres(method, A, B, b, cycle, x0=x, **kw)
+        x = res["x"]
+        hist.append(res)
+    return x, hist
+
+
+# ----------------------------------------------------------------------------- comparators
+
+def golub_kahan(A, At, b, k: int):
+    """Golub-Kahan bidiagonalisation with full reorthogonalisation:
+    A V_k = U_{k+1} Bk,  A^T U_{k+1} = V_k Bk^T + alpha_{k+1} v_{k+1} e_{k+1}^T."""
+    b = np.asarray(b, np.float64).reshape(-1)
+    beta1 = np.linalg.norm(b)
+    U = [b / beta1]
+    v = At(U[0])
+    alpha = np.linalg.norm(v)
+    V = [v / alpha]
+    alphas, betas = [alpha], []
+    for j in range(k):
+        u = A(V[j]) - alphas[j] * U[j]
+        for _ in range(2):
+            for ui in U:
+                u = u - (u @ ui) * ui
+        bet = np.linalg.norm(u)
+        U.append(u / bet)
+        betas.append(bet)
+        v = At(U[j + 1]) - bet * V[j]
+        for _ in range(2):
+            for vi in V:
+                v = v - (v @ vi) * vi
+        al = np.linalg.norm(v)
+        V.append(v / al)
+        alphas.append(al)
+    Bk = np.zeros((k + 1, k))
+    for j in range(k):
+        Bk[j, j] = alphas[j]
+        Bk[j + 1, j] = betas[j]
+    return beta1, np.array(U), np.array(V), Bk, np.array(alphas), np.array(betas)
+
+
+def lsqr_iterate(A, At, b, k: int, lam: float = 0.0):
+    """(Hybrid) LSQR iterate: x = V_k argmin ||Bk y - beta1 e1||^2 + lam^2 ||y||^2."""
+    beta1, U, V, Bk, al, be = golub_kahan(A, At, b, k)
+    rhs = np.zeros(k + 1)
+    rhs[0] = beta1
+    M = np.vstack([Bk, lam * np.eye(k)])
+    y = np.linalg.lstsq(M, np.concatenate([rhs, np.zeros(k)]), rcond=None)[0]
+    return V[:k].T @ y
+
+
+def lsmr_iterate(A, At, b, k: int, lam: float = 0.0):
+    """(Hybrid) LSMR iterate: x = V_k y minimising ||A^T(b - A V_k y)||^2 + lam^2 ||y||^2.
+    With the Golub-Kahan relations ||A^T r||^2 = ||alpha1 beta1 e1 - Bk^T Bk y||^2
+    + (alpha_{k+1} beta_{k+1} y_k)^2."""
+    beta1, U, V, Bk, al, be = golub_kahan(A, At, b, k)
+    T = Bk.T @ Bk
+    last = np.zeros((1, k))
+    last[0, k - 1] = al[k] * be[k - 1]
+    M = np.vstack([T, last, lam * np.eye(k)])
+    rhs = np.zeros(2 * k + 1)
+    rhs[0] = al[0] * beta1
+    y = np.linalg.lstsq(M, rhs, rcond=None)[0]
+    return V[:k].T @ y
+
+
+def rre(x, x_true) -> float:
+    """Relative reconstruction error ||x - x_true|| / ||x_true|| (Sec. 4)."""
+    x = np.asarray(x, np.float64).reshape(-1)
+    x_true = np.asarray(x_true, np.float64).reshape(-1)
+    return float(np.linalg.norm(x - x_true) / np.linalg.norm(x_true))

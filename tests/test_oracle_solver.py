@@ -1,0 +1,209 @@
+"""Pins of the FP64 oracle solver (Algorithms 1/2, Eq. (hybrid_proj), GCV, DP).
+
+The oracle is tied to: the Arnoldi relation and orthonormality (Eq. (Hessenberg)); the
+identity between the projected residual and the true residual (Sec. 2.1); the matched-case
+equivalences with LSQR and LSMR written from the Golub-Kahan process (Sec. 3, 'Relation to
+existing methods'); brute-force minimisation over an explicit Krylov basis; the
+full-dimension closed forms (Sec. 3, 'Optimality conditions', read with lambda^2); a dense
+evaluation of the GCV definition (Sec. 3.1) and of the Tikhonov least-squares problem.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import proj as P
+from oracle import solver as S
+
+
+def _problem(kind="parallel", N=16, views=20, seed=0, eta=0.01):
+    if kind == "parallel":
+        g = synth.parallel2d(N, views)
+    else:
+        g = synth.fanflat2d(N, views, int(1.5 * N), 4.0 * N, 6.0 * N)
+    x = synth.ellipse_phantom(N, seed=seed)
+    bt = P.forward(g, x).reshape(-1)
+    b, e = synth.add_noise(bt, eta, seed + 100)
+    return g, x.reshape(-1), b, e
+
+
+@pytest.mark.parametrize("method", ["ab", "ba"])
+def test_arnoldi_relation_and_orthogonality(method):
+    g, x, b, e = _problem("fan", N=16, views=24)
+    A, B = P.operators(g)
+    res = S.hybrid_gmres(method, A, B, b, 15, rule="gcv")
+    W, H, k = res["W"], res["H"], res["k"]
+    M = (lambda w: A(B(w))) if method == "ab" else (lambda w: B(A(w)))
+    MW = np.stack([M(W[i]) for i in range(k)], axis=1)
+    rel = np.linalg.norm(MW - W[: k + 1].T @ H) / np.linalg.norm(MW)
+    assert rel <= 1e-10
+    assert np.abs(W[: k + 1] @ W[: k + 1].T - np.eye(k + 1)).max() <= 1e-10
+
+
+@pytest.mark.parametrize("method", ["ab", "ba"])
+@pytest.mark.parametrize("rule", ["gcv", "fixed", "none"])
+def test_projected_residual_is_true_residual(method, rule):
+    """AB: ||b - A x_k|| equals ||H y - beta e1||; BA: ||B(b - A x_k)|| does."""
+    g, x, b, e = _problem("parallel", N=16, views=20)
+    A, B = P.operators(g)
+    res = S.hybrid_gmres(method, A, B, b, 12, rule=rule, lam_fixed=0.3, true_residual=True)
+    np.testing.assert_allclose(res["resid"], res["true_resid"], rtol=1e-9)
+
+
+def _krylov_basis(M, r0, k):
+    K = [r0]
+    for _ in range(k - 1):
+        K.append(M(K[-1]))
+    Q, _ = np.linalg.qr(np.stack(K, axis=1))
+    return Q
+
+
+@pytest.mark.parametrize("method", ["ab", "ba"])
+def test_hybrid_iterate_matches_bruteforce_krylov_minimiser(method):
+    """Hybrid AB: u_k = argmin_{u in K_k(AB, b)} ||ABu - b||^2 + lam^2 ||u||^2, x_k = B u_k;
+    hybrid BA: x_k = argmin_{x in K_k(BA, Bb)} ||BAx - Bb||^2 + lam^2 ||x||^2."""
+    g, x, b, e = _problem("fan", N=12, views=16)
+    A, B = P.operators(g)
+    k, lam = 5, 0.7
+    res = S.hybrid_gmres(method, A, B, b, k, rule="fixed", lam_fixed=lam)
+    if method == "ab":
+        M, rhs = (lambda w: A(B(w))), b
+    else:
+        M, rhs = (lambda w: B(A(w))), B(b)
+    Q = _krylov_basis(M, rhs, k)
+    MQ = np.stack([M(Q[:, i]) for i in range(k)], axis=1)
+    stacked = np.vstack([MQ, lam * np.eye(k)])
+    yb = np.linalg.lstsq(stacked, np.concatenate([rhs, np.zeros(k)]), rcond=None)[0]
+    xb = B(Q @ yb) if method == "ab" else Q @ yb
+    np.testing.assert_allclose(res["x"], xb, rtol=1e-7, atol=1e-9 * np.abs(xb).max())
+
+
+def test_matched_ab_is_lsqr_and_ba_is_lsmr():
+    """B = A^T: AB-GMRES iterates equal LSQR's, BA-GMRES iterates equal LSMR's (lambda = 0);
+    hybrid BA-GMRES equals hybrid LSMR at fixed lambda; hybrid AB-GMRES does not equal hybrid
+    LSQR."""
+    g, x, b, e = _problem("parallel", N=12, views=16)
+    A, At = P.operators(g, matched=True)
+    for k in (3, 8, 12):
+        ab = S.hybrid_gmres("ab", A, At, b, k, rule="none")["x"]
+        ba = S.hybrid_gmres("ba", A, At, b, k, rule="none")["x"]
+        lq = S.lsqr_iterate(A, At, b, k)
+        lm = S.lsmr_iterate(A, At, b, k)
+        assert np.linalg.norm(ab - lq) <= 1e-8 * np.linalg.norm(lq)
+        assert np.linalg.norm(ba - lm) <= 1e-8 * np.linalg.norm(lm)
+    lam, k = 2.0, 8
+    hba = S.hybrid_gmres("ba", A, At, b, k, rule="fixed", lam_fixed=lam)["x"]
+    assert np.linalg.norm(hba - S.lsmr_iterate(A, At, b, k, lam)) <= 1e-8 * np.linalg.norm(hba)
+    hab = S.hybrid_gmres("ab", A, At, b, k, rule="fixed", lam_fixed=lam)["x"]
+    hlq = S.lsqr_iterate(A, At, b, k, lam)
+    assert np.linalg.norm(hab - hlq) > 1e-3 * np.linalg.norm(hlq)
+
+
+def test_full_dimension_limits():
+    """BA at k = n gives ((BA)^T BA + lam^2 I)^{-1} (BA)^T B b; AB at k = m gives
+    B ((AB)^T AB + lam^2 I)^{-1} (AB)^T b (generic dense operators, no breakdown)."""
+    rng = np.random.Generator(np.random.PCG64(3))
+    lam = 0.4
+    m, n = 14, 9                                   # m >= n for BA
+    A = rng.standard_normal((m, n))
+    B = A.T + 0.3 * rng.standard_normal((n, m))
+    b = rng.standard_normal(m)
+    res = S.hybrid_gmres("ba", lambda v: A @ v, lambda v: B @ v, b, n, rule="fixed",
+                         lam_fixed=lam)
+    BA = B @ A
+    xf = np.linalg.solve(BA.T @ BA + lam ** 2 * np.eye(n), BA.T @ (B @ b))
+    np.testing.assert_allclose(res["x"], xf, rtol=1e-9, atol=1e-11)
+    m, n = 8, 13                                   # n >= m for AB
+    A = rng.standard_normal((m, n))
+    B = A.T + 0.3 * rng.standard_normal((n, m))
+    b = rng.standard_normal(m)
+    res = S.hybrid_gmres("ab", lambda v: A @ v, lambda v: B @ v, b, m, rule="fixed",
+                         lam_fixed=lam)
+    AB = A @ B
+    xf = B @ np.linalg.solve(AB.T @ AB + lam ** 2 * np.eye(m), AB.T @ b)
+    np.testing.assert_allclose(res["x"], xf, rtol=1e-9, atol=1e-11)
+
+
+@pytest.mark.parametrize("k", [1, 4, 17, 30])
+def test_tikhonov_and_gcv_against_dense_definitions(k):
+    rng = np.random.Generator(np.random.PCG64(k))
+    H = np.triu(rng.standard_normal((k + 1, k)), -1) * np.logspace(0, -5, k)[None, :]
+    beta = 2.5
+    s, c, Vt = S.projected_svd(H, beta)
+    e1 = np.zeros(k + 1)
+    e1[0] = beta
+    for lam in (1e-6, 1e-3, 0.05, 0.8, 3.0):
+        y = S.tikhonov_y(lam, s, c, Vt)
+        yd = np.linalg.lstsq(np.vstack([H, lam * np.eye(k)]),
+                             np.concatenate([e1, np.zeros(k)]), rcond=None)[0]
+        np.testing.assert_allclose(y, yd, rtol=1e-8, atol=1e-10 * np.abs(yd).max())
+        num = np.linalg.norm(H @ yd - e1) ** 2
+        Hl = np.linalg.solve(H.T @ H + lam ** 2 * np.eye(k), H.T)
+        tr = np.trace(np.eye(k + 1) - H @ Hl)
+        np.testing.assert_allclose(S.gcv_value(lam, s, c), num / tr ** 2, rtol=1e-8)
+        np.testing.assert_allclose(S.residual_sq(lam, s, c), num, rtol=1e-8)
+
+
+@pytest.mark.parametrize("k", [3, 12, 40])
+def test_gcv_minimiser_is_global_minimum_on_dense_grid(k):
+    rng = np.random.Generator(np.random.PCG64(100 + k))
+    H = np.triu(rng.standard_normal((k + 1, k)), -1) * np.logspace(0, -4, k)[None, :]
+    s, c, Vt = S.projected_svd(H, 1.0)
+    lam = S.gcv_lambda(s, c)
+    assert s[0] * 1e-8 * (1 - 1e-12) <= lam <= s[0] * (1 + 1e-12)
+    dense = s[0] * np.logspace(-8, 0, 20001)
+    gmin = min(S.gcv_value(l, s, c) for l in dense)
+    assert S.gcv_value(lam, s, c) <= gmin * (1 + 1e-7)
+
+
+@pytest.mark.parametrize("k", [5, 25])
+def test_dp_lambda_hits_target(k):
+    rng = np.random.Generator(np.random.PCG64(200 + k))
+    H = np.triu(rng.standard_normal((k + 1, k)), -1) * np.logspace(0, -4, k)[None, :]
+    beta = 3.0
+    s, c, Vt = S.projected_svd(H, beta)
+    lo = math.sqrt(S.residual_sq(s[0] * 1e-8, s, c))
+    hi = math.sqrt(S.residual_sq(s[0], s, c))
+    target = 0.5 * (lo + hi)
+    lam = S.dp_lambda(s, c, target)
+    y = S.tikhonov_y(lam, s, c, Vt)
+    e1 = np.zeros(k + 1)
+    e1[0] = beta
+    np.testing.assert_allclose(np.linalg.norm(H @ y - e1), target, rtol=1e-10)
+
+
+def test_lambda_zero_svd_path_equals_givens_path():
+    rng = np.random.Generator(np.random.PCG64(9))
+    for k in (1, 5, 20):
+        H = np.triu(rng.standard_normal((k + 1, k)), -1)
+        s, c, Vt = S.projected_svd(H, 1.7)
+        y_svd = S.tikhonov_y(0.0, s, c, Vt)
+        y_giv, res = S.givens_gmres_y(H, 1.7)
+        e1 = np.zeros(k + 1)
+        e1[0] = 1.7
+        y_ls = np.linalg.lstsq(H, e1, rcond=None)[0]
+        np.testing.assert_allclose(y_svd, y_ls, rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(y_giv, y_ls, rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(res, np.linalg.norm(H @ y_ls - e1), rtol=1e-9, atol=1e-14)
+
+
+def test_zero_rhs_breaks_down_at_start():
+    g, x, b, e = _problem("parallel", N=8, views=6)
+    A, B = P.operators(g)
+    res = S.hybrid_gmres("ab", A, B, np.zeros_like(b), 5)
+    assert res["status"] == "breakdown" and res["k"] == 0
+    assert np.all(res["x"] == 0)
+
+
+def test_hybrid_stabilises_semi_convergence():
+    """Sec. 4: plain AB-GMRES semi-converges, the hybrid (GCV) variant keeps the error low."""
+    g, x, b, e = _problem("parallel", N=32, views=30, eta=0.05)
+    A, B = P.operators(g)
+    ks = (5, 10, 20, 40)
+    plain = S.hybrid_gmres("ab", A, B, b, 40, rule="none", keep_iterates=ks)
+    hyb = S.hybrid_gmres("ab", A, B, b, 40, rule="gcv", keep_iterates=ks)
+    e_plain = [S.rre(plain["iterates"][k], x) for k in ks]
+    e_hyb = [S.rre(hyb["iterates"][k], x) for k in ks]
+    assert e_plain[-1] > min(e_plain) * 1.05          # semi-convergence
+    assert e_hyb[-1] < e_plain[-1]
