@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Throughput of hybrid AB-/BA-GMRES on one GB300 (or N, one independent problem per GPU).
+
+Workload (one "step"): the 512 x 512 fan-beam problem (720 views over 360 deg, 768 bins,
+SID 1000, SDD 1500, 2 % Gaussian noise, seeded ellipse phantom), solved by hybrid AB-GMRES and
+by hybrid BA-GMRES, 100 iterations each, lambda by the discrepancy principle (tau = 1.01).
+Metric: solver iterations per second over the whole job.  Inputs are resident in HBM when
+the timed region starts; L2 is flushed (256 MiB write) between timed steps.
+
+Reported beside the metric: per-phase device time (CUDA events on the launching stream),
+projector GUPS, the roofline of the dominant kernel, an end-to-end number through the C ABI
+with host buffers, the GPU clocks seen during the timed region, and the FP64 CPU oracle timed
+on a bounded sample of the same workload (with the GPU's error against it).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "hybrid GMRES iters/s + projector GUPS, % HBM roofline, at stated error vs FP64"
+ITERS = 100
+TAU = 1.01
+L2_FLUSH_BYTES = 256 << 20
+SM_COUNT = 152
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm_gbs=float(d["hbm_gbs"]), sm_max_mhz=float(d.get("sm_max_mhz", 2070.0)),
+                    source="measured")
+    return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- workload
+def workload(seed: int):
+    import synth
+    case = synth.fan512_case()
+    return case["geom"], synth.ellipse_phantom(512, seed=case["phantom_seed"] + seed), case
+
+
+def make_data_gpu(P, torch, G, geom, x_true, case, seed):
+    """b = A x_true + e with the GPU projector (setup, untimed); e seeded, eta = 2 %."""
+    import synth
+    xt = torch.from_numpy(x_true.astype(np.float32).reshape(-1)).cuda()
+    bt = torch.empty(G.m, device="cuda", dtype=torch.float32)
+    P.ct_forward_A(G, xt, bt)
+    torch.cuda.synchronize()
+    b, e = synth.add_noise(bt.cpu().numpy().astype(np.float64), case["eta"], case["noise_seed"] + seed)
+    b_dev = torch.from_numpy(b.astype(np.float32)).cuda()
+    e_dev = torch.from_numpy(e.astype(np.float32)).cuda()
+    be = torch.empty(G.n, device="cuda", dtype=torch.float32)
+    P.ct_back_B(G, e_dev, be)
+    torch.cuda.synchronize()
+    return b, b_dev, float(np.linalg.norm(e)), float(torch.linalg.vector_norm(be.double()).item())
+
+
+def run_step(P, G, b_dev, x_ab, x_ba, noise_ab, noise_ba):
+    ia = P.ab_gmres_hybrid(G, b_dev, x_ab, max_iters=ITERS, rule="dp", noise_norm=noise_ab,
+                           tau=TAU, history=False)
+    ib = P.ba_gmres_hybrid(G, b_dev, x_ba, max_iters=ITERS, rule="dp", noise_norm=noise_ba,
+                           tau=TAU, history=False)
+    return ia["iters_done"] + ib["iters_done"]
+
+
+def cpu_baseline(geom, b, noise_ab, noise_ba, P, torch, G, b_dev, iters=10):
+    """FP64 oracle (as it stands) on a bounded sample: AB and BA, `iters` iterations each;
+    the GPU's iterates at the same k are compared with it."""
+    from oracle import proj as OP
+    from oracle import solver as OS
+    A, B = OP.operators(geom)
+    t0 = time.perf_counter()
+    ra = OS.hybrid_gmres("ab", A, B, b, iters, rule="dp", dp_target=TAU * noise_ab)
+    rb = OS.hybrid_gmres("ba", A, B, b, iters, rule="dp", dp_target=TAU * noise_ba)
+    dt = time.perf_counter() - t0
+    xa = torch.zeros(G.n, device="cuda")
+    xb = torch.zeros(G.n, device="cuda")
+    P.ab_gmres_hybrid(G, b_dev, xa, max_iters=iters, rule="dp", noise_norm=noise_ab, tau=TAU,
+                      history=False)
+    P.ba_gmres_hybrid(G, b_dev, xb, max_iters=iters, rule="dp", noise_norm=noise_ba, tau=TAU,
+                      history=False)
+    torch.cuda.synchronize()
+    err = lambda xg, xo: float(np.linalg.norm(xg.cpu().numpy() - xo) / np.linalg.norm(xo))
+    return ({"value": 2 * iters / dt, "unit": "iters/s", "cores": OP.num_threads(),
+             "kind": "oracle",
+             "sample": f"hybrid AB and BA, {iters} iterations each, of the 512^2 fan workload "
+                       f"(FP64, {dt:.1f} s)"},
+            {"k": iters, "ab": err(xa, ra["x"]), "ba": err(xb, rb["x"])})
+
+
+# ----------------------------------------------------------------------------- ours
+def bench_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2602_17892_gb300 as P
+    from paper_2602_17892_gb300 import _binding as Bn
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    geom, x_true, case = workload(rank)
+    G = P.Geom.from_geometry(geom)
+    b, b_dev, noise_ab, noise_ba = make_data_gpu(P, torch, G, geom, x_true, case, rank)
+    x_ab = torch.zeros(G.n, device="cuda")
+    x_ba = torch.zeros(G.n, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda", dtype=torch.float32)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        run_step(P, G, b_dev, x_ab, x_ba, noise_ab, noise_ba)
+    torch.cuda.synchronize()
+
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    iters_done = 0
+    launches0 = Bn.ct_launch_count()
+    Bn.ct_profile_enable(True)
+    wall0 = time.perf_counter()
+    with ClockSampler(local_rank) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))            # L2 flush, outside the events
+            evs[i][0].record(stream)
+            iters_done += run_step(P, G, b_dev, x_ab, x_ba, noise_ab, noise_ba)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    phases = Bn.ct_profile_collect()
+    Bn.ct_profile_enable(False)
+    launches = Bn.ct_launch_count() - launches0
+    step_ms = [a.elapsed_time(b_) for a, b_ in evs]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        it = torch.tensor([iters_done], device="cuda", dtype=torch.float64)
+        dist.all_reduce(it, op=dist.ReduceOp.SUM)
+        iters_all = float(it.item())
+        dist.barrier()
+    else:
+        iters_all = float(iters_done)
+    value = iters_all / (total_ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the region
+    b_host = torch.from_numpy(b.astype(np.float32)).pin_memory()
+    xa_host = torch.empty(G.n, dtype=torch.float32).pin_memory()
+    xb_host = torch.empty(G.n, dtype=torch.float32).pin_memory()
+    e2e_ms = 0.0
+    e2e_iters = 0
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        b_dev.copy_(b_host, non_blocking=True)
+        e2e_iters += run_step(P, G, b_dev, x_ab, x_ba, noise_ab, noise_ba)
+        xa_host.copy_(x_ab, non_blocking=True)
+        xb_host.copy_(x_ba, non_blocking=True)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms += ea.elapsed_time(eb)
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = e2e_iters * world / (e2e_ms / 1e3)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # ---- per-kernel rooflines
+    peaks = _peaks()
+    steps = args.steps
+    solves_per_step = 2
+    f_ms, f_n, _ = phases["forward_A"]
+    b_ms, b_n, _ = phases["back_B"]
+    a_ms, a_n, a_groups = phases["arnoldi"]
+    kernels = {}
+    if f_n:
+        upd = G.a_samples * f_n
+        kernels["joseph_A"] = {"ms": f_ms, "launches": f_n, "gups": upd / (f_ms * 1e-3) / 1e9}
+    if b_n:
+        upd = G.b_samples * b_n
+        kernels["pixel_B"] = {"ms": b_ms, "launches": b_n, "gups": upd / (b_ms * 1e-3) / 1e9}
+    if a_groups:
+        # algorithmic bytes of the Arnoldi steps of one AB and one BA solve (FP32 basis):
+        # step k streams the k basis rows twice, reads q, writes w_{k+1}: (2k + 2) L 4 bytes
+        L_ab = geom.n_views * (geom.n_det_u + 4 + (-(geom.n_det_u + 4)) % 4)
+        L_ba = geom.n + (-geom.n) % 4
+        per_solve = lambda L: sum((2 * k + 2) * L * 4 for k in range(1, ITERS + 1))
+        byts = (per_solve(L_ab) + per_solve(L_ba)) * steps
+        kernels["arnoldi_cgs2"] = {"ms": a_ms, "launches": a_n,
+                                   "gbs": byts / (a_ms * 1e-3) / 1e9}
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    clk_sum = clk.summary()
+    f_clk = peaks["sm_max_mhz"] * 1e6
+    if dom == "arnoldi_cgs2":
+        ach = kernels[dom]["gbs"]
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": peaks["source"]}
+    else:
+        # ALU/LSU-bound projectors (working set L2-resident): one 8-byte tap load per Joseph
+        # sample at 128 B/clk/SM -> 16 samples/clk/SM; the fan backprojector needs two MUFU
+        # operations per pixel-view pair at 16/clk/SM -> 8 pairs/clk/SM
+        per_clk = 16.0 if dom == "joseph_A" else 8.0
+        peak = per_clk * SM_COUNT * f_clk / 1e9
+        ach = kernels[dom]["gups"]
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak,
+                "unit": "Gupdates/s", "frac": ach / peak, "traffic": None,
+                "peak_source": f"{per_clk:g} updates/clk/SM x {SM_COUNT} SMs x "
+                               f"{peaks['sm_max_mhz']:.0f} MHz"}
+
+    cpu = None
+    err = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu, err = cpu_baseline(geom, b.astype(np.float32).astype(np.float64), noise_ab,
+                                noise_ba, P, torch, G, b_dev)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded ellipse phantom, b = A x + 2 % Gaussian noise)",
+        "config": {"workload": "fan512: 512^2 fan-flat, 720 views/360 deg, 768 bins, "
+                               "SID 1000, SDD 1500, 2 % noise; hybrid AB + BA, 100 its each, DP",
+                   "image": [512, 512], "views": 720, "bins": 768, "iters_per_solve": ITERS,
+                   "rule": "dp", "tau": TAU, "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": "iters/s",
+                "h2d_bytes_per_step": int(G.m * 4), "d2h_bytes_per_step": int(2 * G.n * 4)},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "kernels": kernels,
+        "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
+        "projector_gups": {k: v["gups"] for k, v in kernels.items() if "gups" in v},
+        "err_vs_fp64": err,
+        "clocks": clk_sum,
+        "cpu_baseline": cpu,
+        "wall_s_timed": wall,
+    }
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- reference arm
+def bench_reference(args, rank, world):
+    """The FP64 CPU oracle on the host cores: each step is a bounded sample of the workload
+    (hybrid AB and BA, a few iterations each)."""
+    if rank != 0:
+        return
+    import synth
+    from oracle import proj as OP
+    from oracle import solver as OS
+    geom, x_true, case = workload(0)
+    b, e = synth.add_noise(OP.forward(geom, x_true).reshape(-1), case["eta"], case["noise_seed"])
+    b = b.astype(np.float32).astype(np.float64)
+    A, B = OP.operators(geom)
+    nab, nba = float(np.linalg.norm(e)), float(np.linalg.norm(B(e)))
+    its = 4
+
+    def step():
+        OS.hybrid_gmres("ab", A, B, b, its, rule="dp", dp_target=TAU * nab)
+        OS.hybrid_gmres("ba", A, B, b, its, rule="dp", dp_target=TAU * nba)
+        return 2 * its
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    n = sum(step() for _ in range(args.steps))
+    dt = time.perf_counter() - t0
+    value = n / dt
+    sample = f"hybrid AB and BA, {its} iterations each, of the 512^2 fan workload, per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded ellipse phantom)",
+        "config": {"workload": "fan512: 512^2 fan-flat, 720 views/360 deg, 768 bins, "
+                               "SID 1000, SDD 1500, 2 % noise; hybrid AB + BA, DP"},
+        "cpu_baseline": {"value": value, "unit": "iters/s", "cores": OP.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        from oracle import proj as OP
+        OP.build_oracle()
+        bench_reference(args, rank, world)
+        return
+    from paper_2602_17892_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build()
+    else:                       # the other ranks wait for rank 0's build
+        t0 = time.time()
+        while B.needs_build() and time.time() - t0 < 600:
+            time.sleep(1.0)
+    from oracle import proj as OP
+    OP.build_oracle()
+    bench_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * ctabba — hybrid AB-/BA-GMRES for X-ray CT with an unmatched projector pair, on one
+ * NVIDIA GB300 (sm_103a).  C ABI of libctabba.so.
+ *
+ * The paper (arXiv 2602.17892) poses reconstruction as A x ~= b (Sec. 1, Eq. (1)) with a
+ * forward projector A in R^{m x n} and a backprojector B in R^{n x m} that is NOT A^T
+ * (Sec. 2, "unmatched projector pairs").  AB-GMRES applies GMRES to A B u = b, x = B u;
+ * BA-GMRES applies it to B A x = B b (Sec. 2.1, Eqs. (AB_optimality), (BA_optimality)).
+ * The hybrid variants (Sec. 3, Algorithms 1 and 2) replace the projected least-squares
+ * problem by its Tikhonov-regularised form (Eq. (hybrid_proj)) with lambda chosen at every
+ * iteration by GCV (Sec. 3.1) or by the discrepancy principle (Sec. 3.2).
+ *
+ * General rules for every entry point:
+ *  - Pointers whose names end in _dev are CUDA device pointers on the current device; all
+ *    others are host pointers.  The caller owns every buffer it passes; the library never
+ *    frees or retains them after the call returns.
+ *  - Device arrays are dense FP32, row-major: an image is [ny][nx] (3D: [nz][ny][nx]); a
+ *    sinogram is [n_views][n_det_u] (3D: [n_views][n_det_v][n_det_u]).  Device pointers
+ *    must be 16-byte aligned.
+ *  - Work is enqueued on `stream` (0 = the legacy default stream) and is asynchronous,
+ *    except where a function says it synchronises.
+ *  - A geometry object owns device tables and scratch buffers.  Calls that use the same
+ *    ct_geom must not overlap in time (issue them on one stream, or synchronise).
+ *  - Errors are returned as ct_status; nothing is launched when an argument is invalid.
+ *    ct_last_error() returns a message for the calling thread's most recent failure.
+ *  - There is no CPU fallback: every numerical step runs in this library's CUDA kernels.
+ */
+#ifndef CTABBA_H
+#define CTABBA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void *ct_stream_t; /* a cudaStream_t */
+
+typedef enum {
+    CT_OK = 0,
+    CT_EINVAL = 1,      /* invalid argument (null pointer, bad size, bad enum)          */
+    CT_ENOMEM = 2,      /* device allocation failed                                     */
+    CT_ECUDA = 3,       /* a CUDA runtime call failed (message in ct_last_error)         */
+    CT_BREAKDOWN = 4,   /* Arnoldi breakdown h_{k+1,k} <= tol ||M w_k||; iterate is valid */
+    CT_ETIMEOUT = 5,    /* a bounded device wait expired                                */
+    CT_ENONFINITE = 6   /* NaN or Inf met in the data or the projected problem           */
+} ct_status;
+
+typedef enum { CT_PARALLEL2D = 0, CT_FANFLAT2D = 1, CT_CONE3D = 2 } ct_geom_kind;
+
+/* Scan geometry (the paper leaves conventions open; Sec. 4 uses parallel and fan-flat 2D):
+ *   pixel (r, c) has centre X = (c - (nx-1)/2) h, Y = (r - (ny-1)/2) h;
+ *   parallel: ray (theta, s) is { p : p . (cos theta, sin theta) = s },
+ *             bin j at s_j = (j - (n_det_u-1)/2) pitch_u;
+ *   fan-flat / cone: source at SID (cos, sin), detector centre at -(SDD-SID)(cos, sin),
+ *             detector axis (-sin, cos), bin j at u_j = (j - (n_det_u-1)/2) pitch_u, rows
+ *             along +z at v_i = (i - (n_det_v-1)/2) pitch_v.
+ * `angles` (host, n_views entries, radians) is copied; the array may be freed afterwards. */
+typedef struct {
+    ct_geom_kind kind;
+    int nx, ny, nz;          /* nz = 1 for 2D                                          */
+    double pixel;            /* h                                                      */
+    int n_views;
+    const double *angles;    /* host, n_views                                          */
+    int n_det_u, n_det_v;    /* n_det_v = 1 for 2D                                     */
+    double pitch_u, pitch_v;
+    double sid, sdd;         /* source-isocentre and source-detector distances (fan/cone) */
+} ct_geom_desc;
+
+typedef struct ct_geom ct_geom; /* opaque */
+
+/* Validate `d`, build the per-ray and per-view device tables and the projector scratch.
+ * Allocates device memory (owned by the object).  2D sizes up to 16384 per side; cone
+ * volumes need nx = ny. */
+ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out);
+void ct_geom_destroy(ct_geom *g);
+/* n = number of unknowns, m = number of measurements. */
+ct_status ct_geom_dims(const ct_geom *g, int64_t *n, int64_t *m);
+/* Algorithmic work of one projector call: a_samples = Joseph samples whose interpolation
+ * position lies inside the image (the samples ct_forward_A computes), b_samples = pixel-view
+ * pairs of ct_back_B (n * n_views).  Host-only query. */
+ct_status ct_geom_work(const ct_geom *g, int64_t *a_samples, int64_t *b_samples);
+
+/* y = A x (Sec. 1, Eq. (1)): ray-driven Joseph projector.  Every line of the driving axis
+ * (the axis with the largest |ray direction| component, ties to x then y) is sampled; the
+ * image is interpolated linearly (bilinearly in 3D) between pixel centres, zero outside;
+ * each sample is weighted h / |d_drive|.  x_dev: n floats, y_dev: m floats (overwritten). */
+ct_status ct_forward_A(ct_geom *g, const float *x_dev, float *y_dev, ct_stream_t stream);
+
+/* x = B y (Sec. 2: B realises A^T approximately and differently): pixel/voxel-driven
+ * backprojector.  For every view the ray through the pixel centre is followed to the
+ * detector and y is interpolated linearly (bilinearly in 3D) there, zero outside, with
+ * weight h^2/(ray spacing at the pixel) so that B has the scale of A^T:
+ *   parallel h^2/pitch;  fan h^2 (SDD^2+u^2)/(L pitch SDD);
+ *   cone h^3 (SDD^2+u^2+v^2)^{3/2}/(L^2 pitch_u pitch_v SDD), L = |pixel - source|.
+ * y_dev: m floats, x_dev: n floats (overwritten). */
+ct_status ct_back_B(ct_geom *g, const float *y_dev, float *x_dev, ct_stream_t stream);
+
+/* ------------------------------------------------------------------ hybrid solvers */
+
+typedef enum {
+    CT_LAMBDA_NONE = 0,   /* lambda = 0: plain AB/BA-GMRES, Eq. (proj_pbm) by Givens rotations */
+    CT_LAMBDA_FIXED = 1,  /* lambda = lambda_fixed at every iteration                        */
+    CT_LAMBDA_GCV = 2,    /* GCV on the projected problem (Sec. 3.1)                          */
+    CT_LAMBDA_DP = 3      /* discrepancy principle: ||H y - beta e1|| = tau * noise_norm      */
+} ct_lambda_rule;
+
+typedef enum { CT_BASIS_F32 = 0, CT_BASIS_BF16 = 1, CT_BASIS_F16 = 2 } ct_basis_dtype;
+
+typedef struct {
+    int max_iters;           /* K >= 1                                                     */
+    ct_lambda_rule rule;
+    double lambda_fixed;     /* CT_LAMBDA_FIXED                                            */
+    double noise_norm;       /* CT_LAMBDA_DP: ||e|| for AB, ||B e|| for BA                  */
+    double tau;              /* CT_LAMBDA_DP safety factor (> 0; the paper asks tau > 1)    */
+    int reorth;              /* 1 = classical Gram-Schmidt twice (default), 0 = once       */
+    ct_basis_dtype basis;    /* storage type of the Krylov basis                           */
+    double *lambda_hist;     /* host, max_iters entries, may be NULL: lambda_k              */
+    double *resid_hist;      /* host, max_iters entries, may be NULL: ||H_k y_k - beta e1|| */
+} ct_hybrid_opts;
+
+typedef struct {
+    int iters_done;          /* k of the returned iterate                                  */
+    double beta;             /* ||r0||                                                     */
+    double final_lambda;
+    double final_resid;      /* ||H_k y_k - beta e1|| (= ||b - A x_k|| for AB)             */
+    ct_status status;        /* CT_OK or CT_BREAKDOWN                                      */
+} ct_hybrid_info;
+
+/* Fill `o` with defaults: K = 30, GCV, tau = 1.01, reorth = 1, FP32 basis, no history. */
+void ct_hybrid_opts_default(ct_hybrid_opts *o);
+
+/* Hybrid AB-GMRES, Algorithm 1 (Sec. 3): x0 = B u0 (u0 = 0 when u0_dev is NULL),
+ * r0 = b - A x0, Arnoldi on A B with classical Gram-Schmidt applied twice, lambda_k by
+ * `o->rule`, y_k from Eq. (hybrid_proj) through the SVD of H_k in FP64, and
+ * x_K = x0 + B W_K y_K.  b_dev: m floats; x_dev: n floats (output).  The residual of
+ * Alg. 1 line 14 is not recomputed: ||b - A x_k|| equals the projected residual.
+ * Allocates its workspace on the first call for a geometry (reused while max_iters and
+ * basis do not grow).  Synchronises `stream` before returning to fill `info` and the
+ * host histories. */
+ct_status ab_gmres_hybrid(ct_geom *g, const float *b_dev, const float *u0_dev, float *x_dev,
+                          const ct_hybrid_opts *o, ct_hybrid_info *info, ct_stream_t stream);
+
+/* Hybrid BA-GMRES, Algorithm 2 (Sec. 3): r0 = B (b - A x0) (x0 = 0 when x0_dev is NULL),
+ * Arnoldi on B A, x_K = x0 + W_K y_K.  Same conventions as ab_gmres_hybrid. */
+ct_status ba_gmres_hybrid(ct_geom *g, const float *b_dev, const float *x0_dev, float *x_dev,
+                          const ct_hybrid_opts *o, ct_hybrid_info *info, ct_stream_t stream);
+
+/* ------------------------------------------------------------------ building blocks */
+
+/* One Arnoldi orthogonalisation step (Sec. 2.1, Eq. (Hessenberg); Alg. 1 lines 6-11):
+ * given k+1 orthonormal rows W[0..k] (each `len` floats, row stride `ld` floats) and
+ * q = M w_k, compute h[i] = <q, w_i> by classical Gram-Schmidt applied twice (the second
+ * pass's coefficients added), h[k+1] = ||q||, and W[k+1] = q / h[k+1].  W_dev must have
+ * room for k+2 rows; q_dev (len floats) is overwritten; h_dev receives k+2 doubles. */
+ct_status ct_arnoldi_step(float *W_dev, int64_t len, int64_t ld, int k, float *q_dev,
+                          double *h_dev, ct_stream_t stream);
+
+/* The hybrid step on the device (Sec. 3, Eq. (hybrid_proj); Sec. 3.1/3.2): for the
+ * (k+1) x k Hessenberg matrix H (FP64, column-major, leading dimension ldh >= k+1) and
+ * beta = ||r0||, choose lambda by `rule` and return y (k doubles), lambda and the projected
+ * residual ||H y - beta e1||.  All pointers are device pointers.  1 <= k <= 512. */
+ct_status ct_projected_solve(const double *H_dev, int ldh, int k, double beta,
+                             ct_lambda_rule rule, double lambda_fixed, double dp_target,
+                             double *y_dev, double *lambda_dev, double *resid_dev,
+                             ct_stream_t stream);
+
+/* ------------------------------------------------------------------ instrumentation */
+
+/* Device time per phase of the solvers and projectors, from CUDA events recorded on the
+ * launching stream around every launch group while profiling is enabled (adds about one
+ * microsecond per group).  Phases: */
+enum {
+    CT_PH_FORWARD = 0,   /* Joseph A kernel                                   */
+    CT_PH_BACK = 1,      /* pixel-driven B kernel                             */
+    CT_PH_LAYOUT = 2,    /* image pair layouts / padded sinogram copies        */
+    CT_PH_ARNOLDI = 3,   /* the four Gram-Schmidt kernels of one Arnoldi step  */
+    CT_PH_SMALL = 4,     /* the FP64 hybrid small solve                       */
+    CT_PH_OTHER = 5,     /* first normalisation, x = x0 + W y, residual updates */
+    CT_PH_COUNT = 6
+};
+typedef struct { double ms; int64_t launches; int64_t groups; } ct_phase_time;
+
+/* Enable (1) or disable (0) event timing; enabling clears the accumulated records. */
+ct_status ct_profile_enable(int on);
+/* Wait for the recorded events, add their durations into out[CT_PH_COUNT] (overwritten) and
+ * clear the records.  Host-blocking. */
+ct_status ct_profile_collect(ct_phase_time *out);
+/* Number of kernels this library has launched since it was loaded (all phases). */
+int64_t ct_launch_count(void);
+
+/* Status name and the calling thread's last error message. */
+const char *ct_status_string(ct_status s);
+const char *ct_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTABBA_H */

@@ -1,0 +1,249 @@
+"""ctypes binding of libctabba.so: argument marshalling only.
+
+Names follow the C ABI in ``include/ctabba.h``.  Device buffers are PyTorch CUDA tensors
+(FP32 or FP64, contiguous); the work is enqueued on PyTorch's current CUDA stream.  Every
+numerical step runs in the library's CUDA kernels: there is no CPU or PyTorch fallback, and
+loading fails loudly when the shared library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libctabba.so")
+
+CT_OK, CT_EINVAL, CT_ENOMEM, CT_ECUDA, CT_BREAKDOWN, CT_ETIMEOUT, CT_ENONFINITE = range(7)
+STATUS_NAMES = {0: "CT_OK", 1: "CT_EINVAL", 2: "CT_ENOMEM", 3: "CT_ECUDA", 4: "CT_BREAKDOWN",
+                5: "CT_ETIMEOUT", 6: "CT_ENONFINITE"}
+KINDS = {"parallel2d": 0, "fanflat2d": 1, "cone3d": 2}
+RULES = {"none": 0, "fixed": 1, "gcv": 2, "dp": 3}
+BASIS = {"f32": 0, "bf16": 1, "f16": 2}
+
+# the entry points of include/ctabba.h
+EXPORTS = ("ct_geom_create", "ct_geom_destroy", "ct_geom_dims", "ct_geom_work", "ct_forward_A", "ct_back_B",
+           "ct_hybrid_opts_default", "ab_gmres_hybrid", "ba_gmres_hybrid", "ct_arnoldi_step",
+           "ct_projected_solve", "ct_status_string", "ct_last_error", "ct_profile_enable",
+           "ct_profile_collect", "ct_launch_count")
+PHASES = ("forward_A", "back_B", "layout", "arnoldi", "small_solve", "other")
+
+
+class CtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GeomDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("nz", ctypes.c_int), ("pixel", ctypes.c_double), ("n_views", ctypes.c_int),
+                ("angles", ctypes.POINTER(ctypes.c_double)), ("n_det_u", ctypes.c_int),
+                ("n_det_v", ctypes.c_int), ("pitch_u", ctypes.c_double),
+                ("pitch_v", ctypes.c_double), ("sid", ctypes.c_double), ("sdd", ctypes.c_double)]
+
+
+class HybridOpts(ctypes.Structure):
+    _fields_ = [("max_iters", ctypes.c_int), ("rule", ctypes.c_int),
+                ("lambda_fixed", ctypes.c_double), ("noise_norm", ctypes.c_double),
+                ("tau", ctypes.c_double), ("reorth", ctypes.c_int), ("basis", ctypes.c_int),
+                ("lambda_hist", ctypes.POINTER(ctypes.c_double)),
+                ("resid_hist", ctypes.POINTER(ctypes.c_double))]
+
+
+class PhaseTime(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double), ("launches", ctypes.c_int64), ("groups", ctypes.c_int64)]
+
+
+class HybridInfo(ctypes.Structure):
+    _fields_ = [("iters_done", ctypes.c_int), ("beta", ctypes.c_double),
+                ("final_lambda", ctypes.c_double), ("final_resid", ctypes.c_double),
+                ("status", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libctabba.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libctabba.so not found at {path}; build it with "
+                          "`python -m paper_2602_17892_gb300.build` (no CPU fallback exists)")
+    lib = ctypes.CDLL(path)
+    vp, i64 = ctypes.c_void_p, ctypes.c_int64
+    lib.ct_geom_create.argtypes = [ctypes.POINTER(GeomDesc), ctypes.POINTER(vp)]
+    lib.ct_geom_destroy.argtypes = [vp]
+    lib.ct_geom_destroy.restype = None
+    lib.ct_geom_dims.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    lib.ct_geom_work.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    lib.ct_forward_A.argtypes = [vp, vp, vp, vp]
+    lib.ct_back_B.argtypes = [vp, vp, vp, vp]
+    lib.ct_hybrid_opts_default.argtypes = [ctypes.POINTER(HybridOpts)]
+    lib.ct_hybrid_opts_default.restype = None
+    for fn in (lib.ab_gmres_hybrid, lib.ba_gmres_hybrid):
+        fn.argtypes = [vp, vp, vp, vp, ctypes.POINTER(HybridOpts), ctypes.POINTER(HybridInfo), vp]
+    lib.ct_arnoldi_step.argtypes = [vp, i64, i64, ctypes.c_int, vp, vp, vp]
+    lib.ct_projected_solve.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_int, ctypes.c_double, ctypes.c_double, vp, vp,
+                                       vp, vp]
+    lib.ct_profile_enable.argtypes = [ctypes.c_int]
+    lib.ct_profile_collect.argtypes = [ctypes.POINTER(PhaseTime)]
+    lib.ct_launch_count.restype = ctypes.c_int64
+    lib.ct_launch_count.argtypes = []
+    lib.ct_status_string.argtypes = [ctypes.c_int]
+    lib.ct_status_string.restype = ctypes.c_char_p
+    lib.ct_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(st):
+    if st != CT_OK:
+        raise CtError(st, load().ct_last_error().decode())
+    return st
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t, dtype_name="float32"):
+    if t is None:
+        return None
+    import torch
+    want = getattr(torch, dtype_name)
+    if not (t.is_cuda and t.dtype == want and t.is_contiguous()):
+        raise ValueError(f"expected a contiguous CUDA {dtype_name} tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Geom:
+    """Owns a ct_geom handle (ct_geom_create / ct_geom_destroy)."""
+
+    def __init__(self, kind, nx, ny, angles, n_det_u, pitch_u, pixel=1.0, nz=1, n_det_v=1,
+                 pitch_v=1.0, sid=0.0, sdd=0.0):
+        lib = load()
+        self._angles = np.ascontiguousarray(angles, dtype=np.float64)
+        d = GeomDesc(KINDS[kind] if isinstance(kind, str) else int(kind), int(nx), int(ny),
+                     int(nz), float(pixel), len(self._angles),
+                     self._angles.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(n_det_u),
+                     int(n_det_v), float(pitch_u), float(pitch_v), float(sid), float(sdd))
+        h = ctypes.c_void_p()
+        _check(lib.ct_geom_create(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+        n, m = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.ct_geom_dims(h, ctypes.byref(n), ctypes.byref(m)))
+        self.n, self.m = n.value, m.value
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.ct_geom_work(h, ctypes.byref(a), ctypes.byref(b)))
+        self.a_samples, self.b_samples = a.value, b.value
+
+    @classmethod
+    def from_geometry(cls, g):
+        """From any object with the fields of the seeded input module's Geometry."""
+        return cls(g.kind, g.nx, g.ny, g.angles, g.n_det_u, g.pitch_u, pixel=g.h, nz=g.nz,
+                   n_det_v=g.n_det_v, pitch_v=g.pitch_v, sid=g.sid, sdd=g.sdd)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ct_geom_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ct_forward_A(g: Geom, x, y, stream=None):
+    _check(load().ct_forward_A(g.handle, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def ct_back_B(g: Geom, y, x, stream=None):
+    _check(load().ct_back_B(g.handle, _ptr(y), _ptr(x), _stream(stream)))
+
+
+def _opts(max_iters, rule, lambda_fixed, noise_norm, tau, reorth, basis, history):
+    o = HybridOpts()
+    load().ct_hybrid_opts_default(ctypes.byref(o))
+    o.max_iters = int(max_iters)
+    o.rule = RULES[rule] if isinstance(rule, str) else int(rule)
+    o.lambda_fixed = float(lambda_fixed)
+    o.noise_norm = float(noise_norm)
+    o.tau = float(tau)
+    o.reorth = int(reorth)
+    o.basis = BASIS[basis] if isinstance(basis, str) else int(basis)
+    lam = res = None
+    if history:
+        lam = np.full(int(max_iters), np.nan)
+        res = np.full(int(max_iters), np.nan)
+        o.lambda_hist = lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        o.resid_hist = res.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return o, lam, res
+
+
+def _solve(fn, g, b, x, x0, max_iters, rule, lambda_fixed, noise_norm, tau, reorth, basis,
+           history, stream):
+    o, lam, res = _opts(max_iters, rule, lambda_fixed, noise_norm, tau, reorth, basis, history)
+    info = HybridInfo()
+    st = fn(g.handle, _ptr(b), _ptr(x0), _ptr(x), ctypes.byref(o), ctypes.byref(info),
+            _stream(stream))
+    _check(st)
+    out = dict(iters_done=info.iters_done, beta=info.beta, final_lambda=info.final_lambda,
+               final_resid=info.final_resid, status=STATUS_NAMES[info.status])
+    if history:
+        out["lambdas"], out["resid"] = lam, res
+    return out
+
+
+def ab_gmres_hybrid(g, b, x, u0=None, max_iters=30, rule="gcv", lambda_fixed=0.0,
+                    noise_norm=0.0, tau=1.01, reorth=1, basis="f32", history=True, stream=None):
+    """Hybrid AB-GMRES (Algorithm 1): x <- x0 + B W_K y_K with x0 = B u0."""
+    return _solve(load().ab_gmres_hybrid, g, b, x, u0, max_iters, rule, lambda_fixed,
+                  noise_norm, tau, reorth, basis, history, stream)
+
+
+def ba_gmres_hybrid(g, b, x, x0=None, max_iters=30, rule="gcv", lambda_fixed=0.0,
+                    noise_norm=0.0, tau=1.01, reorth=1, basis="f32", history=True, stream=None):
+    """Hybrid BA-GMRES (Algorithm 2): x <- x0 + W_K y_K."""
+    return _solve(load().ba_gmres_hybrid, g, b, x, x0, max_iters, rule, lambda_fixed,
+                  noise_norm, tau, reorth, basis, history, stream)
+
+
+def ct_arnoldi_step(W, length, ld, k, q, h, stream=None):
+    _check(load().ct_arnoldi_step(_ptr(W), int(length), int(ld), int(k), _ptr(q),
+                                  _ptr(h, "float64"), _stream(stream)))
+
+
+def ct_projected_solve(H, ldh, k, beta, rule, lambda_fixed, dp_target, y, lam, resid,
+                       stream=None):
+    r = RULES[rule] if isinstance(rule, str) else int(rule)
+    _check(load().ct_projected_solve(_ptr(H, "float64"), int(ldh), int(k), float(beta), r,
+                                     float(lambda_fixed), float(dp_target), _ptr(y, "float64"),
+                                     _ptr(lam, "float64"), _ptr(resid, "float64"),
+                                     _stream(stream)))
+
+
+def ct_profile_enable(on: bool = True):
+    _check(load().ct_profile_enable(1 if on else 0))
+
+
+def ct_profile_collect() -> dict:
+    """{phase: (ms, launches, groups)} accumulated since the last collect (host-blocking)."""
+    arr = (PhaseTime * len(PHASES))()
+    _check(load().ct_profile_collect(arr))
+    return {name: (arr[i].ms, arr[i].launches, arr[i].groups) for i, name in enumerate(PHASES)}
+
+
+def ct_launch_count() -> int:
+    return int(load().ct_launch_count())

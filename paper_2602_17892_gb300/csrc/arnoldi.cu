@@ -1,0 +1,261 @@
+// Arnoldi orthogonalisation (Sec. 2.1, Eq. (Hessenberg); Algorithm 1/2 lines 6-11) as
+// classical Gram-Schmidt applied twice, plus the basis combination x = x0 + W y of Alg. 1/2
+// line 13.
+//
+// The paper's loop is modified Gram-Schmidt: h_i = <q, w_i>; q -= h_i w_i, one i at a time.
+// On a GPU each of those k dot products needs a grid-wide reduction before the next axpy.
+// Classical Gram-Schmidt computes all k dots from the same q in one pass over the basis
+// (batched dot products, one grid reduction), and the second pass restores orthogonality to
+// working precision ("twice is enough"); both give the same H and W in exact arithmetic.
+//
+// One step is four launches over the basis rows (vectors of L floats, L % 4 == 0, zero tails):
+//   K1  h1 = W^T q,          ||q||^2                         (reads W once)
+//   K2  q -= W h1;  h2 = W^T q                              (reads W twice)
+//   K3  q -= W h2;  ||q||^2 -> h_{k+1,k}, breakdown test      (reads W once)
+//   K4  w_{k+1} = q / h_{k+1,k}
+// Block partial sums are FP32 (warp shuffles), the cross-block sum is FP64 in a fixed order
+// by the last block to finish, so results are reproducible run to run.
+#include "ct_internal.h"
+
+namespace ct {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr double kBreakdownTol = 1e-6;   // FP32 reading of h_{k+1,k} <= tol ||M w_k||
+
+enum { M_DOTS = 0, M_UPD_DOTS = 1, M_UPD_NORM = 2, M_NORM = 3 };
+
+struct CgsArgs {
+    const float *W; int64_t ld; int nvec;       // rows W[0..nvec-1]
+    float *q; int64_t L4;                        // vector (float4 count)
+    const double *coef;                          // update coefficients (nvec), modes 1, 2
+    double *partial; unsigned *counter;
+    double *hcol;                                // Hessenberg column (FP64)
+    double *aux;                                 // [0] ||q_pre|| [1] 1/h [2] beta, coef buffers
+    double *coef_out;                            // where this pass's dots go (modes 0, 1)
+    int *stop;                                   // [0] stop step, [1] reason
+    int step;                                    // 1-based Arnoldi step (mode 2)
+};
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) cgs_kernel(CgsArgs a)
+{
+    if (a.stop[0] != 0) return;
+    extern __shared__ float sm[];
+    const int nvec = (MODE == M_NORM) ? 0 : a.nvec;
+    const int ncol = nvec + 1;                       // dots + squared norm
+    float *scoef = sm;                               // nvec
+    float *acc = sm + nvec;                          // [kWarps][ncol]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < kWarps * ncol; i += kThreads) acc[i] = 0.f;
+    if (MODE == M_UPD_DOTS || MODE == M_UPD_NORM)
+        for (int i = tid; i < nvec; i += kThreads) scoef[i] = (float)a.coef[i];
+    __syncthreads();
+
+    const float4 *W4 = reinterpret_cast<const float4 *>(a.W);
+    float4 *q4 = reinterpret_cast<float4 *>(a.q);
+    const int64_t ld4 = a.ld / 4;
+    for (int64_t e0 = (int64_t)blockIdx.x * kThreads; e0 < a.L4; e0 += (int64_t)gridDim.x * kThreads) {
+        const int64_t e = e0 + tid;
+        const bool ok = e < a.L4;
+        float4 v = ok ? q4[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (MODE == M_UPD_DOTS || MODE == M_UPD_NORM) {
+            if (ok) {
+                for (int i = 0; i < nvec; ++i) {
+                    float4 w = __ldg(W4 + i * ld4 + e);
+                    float c = scoef[i];
+                    v.x = fmaf(-c, w.x, v.x); v.y = fmaf(-c, w.y, v.y);
+                    v.z = fmaf(-c, w.z, v.z); v.w = fmaf(-c, w.w, v.w);
+                }
+                q4[e] = v;
+            }
+        }
+        if (MODE == M_DOTS || MODE == M_UPD_DOTS) {
+            for (int i = 0; i < nvec; ++i) {
+                float p = 0.f;
+                if (ok) {
+                    float4 w = __ldg(W4 + i * ld4 + e);
+                    p = fmaf(w.x, v.x, fmaf(w.y, v.y, fmaf(w.z, v.z, w.w * v.w)));
+                }
+                p = warp_sum(p);
+                if (lane == 0) acc[warp * ncol + i] += p;
+            }
+        }
+        float nn = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, v.w * v.w)));
+        nn = warp_sum(nn);
+        if (lane == 0) acc[warp * ncol + nvec] += nn;
+    }
+    __syncthreads();
+    double *prow = a.partial + (int64_t)blockIdx.x * ncol;
+    for (int i = tid; i < ncol; i += kThreads) {
+        float s = 0.f;
+        for (int w = 0; w < kWarps; ++w) s += acc[w * ncol + i];
+        prow[i] = (double)s;
+    }
+    // last block to finish reduces across blocks in a fixed order
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) is_last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    __shared__ double total_nn;
+    for (int i = tid; i < ncol; i += kThreads) {
+        double s = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) s += ((volatile double *)a.partial)[(int64_t)b * ncol + i];
+        if (i < nvec) {
+            if (MODE == M_DOTS) { a.hcol[i] = s; a.coef_out[i] = s; }
+            if (MODE == M_UPD_DOTS) { a.hcol[i] += s; a.coef_out[i] = s; }
+        } else {
+            total_nn = s;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double nrm = sqrt(total_nn);
+        if (MODE == M_DOTS) a.aux[0] = nrm;
+        if (MODE == M_UPD_NORM) {
+            a.hcol[nvec] = nrm;
+            if (!isfinite(nrm)) { a.stop[0] = a.step; a.stop[1] = CT_ENONFINITE; a.aux[1] = 0.0; }
+            else if (!(nrm > kBreakdownTol * a.aux[0])) { a.stop[0] = a.step; a.stop[1] = CT_BREAKDOWN; a.aux[1] = 0.0; }
+            else a.aux[1] = 1.0 / nrm;
+        }
+        if (MODE == M_NORM) {
+            a.aux[2] = nrm;
+            if (!isfinite(nrm)) { a.stop[0] = -1; a.stop[1] = CT_ENONFINITE; a.aux[1] = 0.0; }
+            else if (nrm == 0.0) { a.stop[0] = -1; a.stop[1] = CT_BREAKDOWN; a.aux[1] = 0.0; }
+            else a.aux[1] = 1.0 / nrm;
+        }
+        *a.counter = 0u;
+    }
+}
+
+// dst = src * aux[1]   (normalisation; skipped once a stop is recorded)
+__global__ void scale_kernel(const float4 *__restrict__ src, float4 *__restrict__ dst, int64_t L4,
+                             const double *aux, const int *stop)
+{
+    if (stop[0] != 0) return;
+    const float s = (float)aux[1];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L4;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        float4 v = src[e];
+        v.x *= s; v.y *= s; v.z *= s; v.w *= s;
+        dst[e] = v;
+    }
+}
+
+static int grid_for(int64_t L4, int max_blocks)
+{
+    int64_t b = (L4 + kThreads - 1) / kThreads;
+    if (b > max_blocks) b = max_blocks;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+// One CGS2 Arnoldi step on rows W[0..k] with q = M w_k; writes H column (FP64, k+2 entries)
+// and W[k+1].  `aux` / `stop` are device scratch words (see CgsArgs).
+cudaError_t arnoldi_step_dev(float *W, int64_t L, int64_t ld, int k, float *q, double *hcol,
+                             const ArnoldiScratch &sc, double *aux, int *stop, int step,
+                             bool reorth, cudaStream_t s)
+{
+    const int64_t L4 = L / 4;
+    const int nvec = k + 1;
+    const int blocks = grid_for(L4, sc.max_blocks);
+    double *h1 = aux + 8, *h2 = aux + 8 + (sc.kmax + 2);
+    CgsArgs a{W, ld, nvec, q, L4, nullptr, sc.partial, sc.counter, hcol, aux, h1, stop, step};
+    size_t smem = sizeof(float) * (size_t)(nvec + kWarps * (nvec + 1));
+    cgs_kernel<M_DOTS><<<blocks, kThreads, smem, s>>>(a);
+    if (reorth) {
+        a.coef = h1; a.coef_out = h2;
+        cgs_kernel<M_UPD_DOTS><<<blocks, kThreads, smem, s>>>(a);
+        a.coef = h2;
+    } else {
+        a.coef = h1;
+    }
+    cgs_kernel<M_UPD_NORM><<<blocks, kThreads, smem, s>>>(a);
+    scale_kernel<<<grid_for(L4, sc.max_blocks), kThreads, 0, s>>>(
+        reinterpret_cast<const float4 *>(q), reinterpret_cast<float4 *>(W + (int64_t)(k + 1) * ld),
+        L4, aux, stop);
+    return cudaGetLastError();
+}
+
+// beta = ||r||, w0 = r / beta (Alg. 1/2 line 3); beta stored in aux[2].
+cudaError_t normalize_first(const float *r, int64_t L, float *w0, const ArnoldiScratch &sc,
+                            double *aux, int *stop, cudaStream_t s)
+{
+    const int64_t L4 = L / 4;
+    const int blocks = grid_for(L4, sc.max_blocks);
+    CgsArgs a{nullptr, L, 0, const_cast<float *>(r), L4, nullptr, sc.partial, sc.counter,
+              nullptr, aux, nullptr, stop, 0};
+    size_t smem = sizeof(float) * (size_t)(kWarps);
+    cgs_kernel<M_NORM><<<blocks, kThreads, smem, s>>>(a);
+    scale_kernel<<<blocks, kThreads, 0, s>>>(reinterpret_cast<const float4 *>(r),
+                                             reinterpret_cast<float4 *>(w0), L4, aux, stop);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------- x = x0 + W y
+// y holds K slots of K doubles; the slot of the last valid step kf = stop ? stop : K is used.
+__global__ void __launch_bounds__(kThreads) combine_kernel(
+    const float4 *__restrict__ W, int64_t ld4, int64_t L4, const double *__restrict__ Y, int K,
+    int ystride, const int *stop, int kfixed, const float4 *__restrict__ x0, float4 *__restrict__ x)
+{
+    __shared__ float sy[1024];
+    int kf = kfixed;
+    if (stop) {
+        int st = stop[0];
+        kf = (st == 0) ? K : (st < 0 ? 0 : st);
+    }
+    const double *y = Y + (int64_t)(kf > 0 ? kf - 1 : 0) * ystride;
+    for (int i = threadIdx.x; i < kf; i += kThreads) sy[i] = (float)y[i];
+    __syncthreads();
+    for (int64_t e = blockIdx.x * (int64_t)kThreads + threadIdx.x; e < L4;
+         e += (int64_t)gridDim.x * kThreads) {
+        float4 v = x0 ? x0[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int i = 0; i < kf; ++i) {
+            float4 w = __ldg(W + i * ld4 + e);
+            float c = sy[i];
+            v.x = fmaf(c, w.x, v.x); v.y = fmaf(c, w.y, v.y);
+            v.z = fmaf(c, w.z, v.z); v.w = fmaf(c, w.w, v.w);
+        }
+        x[e] = v;
+    }
+}
+
+cudaError_t launch_combine(const float *W, int64_t L, int64_t ld, const double *Y, int K,
+                           int ystride, const int *stop, int kfixed, const float *x0, float *x,
+                           int max_blocks, cudaStream_t s)
+{
+    const int64_t L4 = L / 4;
+    combine_kernel<<<grid_for(L4, max_blocks), kThreads, 0, s>>>(
+        reinterpret_cast<const float4 *>(W), ld / 4, L4, Y, K, ystride, stop, kfixed,
+        reinterpret_cast<const float4 *>(x0), reinterpret_cast<float4 *>(x));
+    return cudaGetLastError();
+}
+
+// r = b - r  (in place on r), float4 vectors
+__global__ void rsub_kernel(const float4 *__restrict__ b, float4 *__restrict__ r, int64_t L4)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L4;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        float4 u = b[e], v = r[e];
+        r[e] = make_float4(u.x - v.x, u.y - v.y, u.z - v.z, u.w - v.w);
+    }
+}
+
+cudaError_t launch_rsub(const float *b, float *r, int64_t L, int max_blocks, cudaStream_t s)
+{
+    rsub_kernel<<<grid_for(L / 4, max_blocks), kThreads, 0, s>>>(
+        reinterpret_cast<const float4 *>(b), reinterpret_cast<float4 *>(r), L / 4);
+    return cudaGetLastError();
+}
+
+}  // namespace ct

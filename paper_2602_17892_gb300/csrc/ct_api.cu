@@ -1,0 +1,669 @@
+// C ABI of libctabba: geometry objects, projector entry points and the hybrid AB-/BA-GMRES
+// drivers (Algorithms 1 and 2 of arXiv 2602.17892).  Every numerical step is a kernel of this
+// library; the host only validates arguments, builds FP64 geometry tables once per geometry
+// and enqueues launches.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ct_internal.h"
+
+namespace ct {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+ct_status cuda_fail(cudaError_t e, const char *what)
+{
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return CT_ECUDA;
+}
+
+static ct_status einval(const std::string &msg)
+{
+    set_error(msg);
+    return CT_EINVAL;
+}
+
+static int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+// declared in arnoldi.cu
+cudaError_t arnoldi_step_dev(float *W, int64_t L, int64_t ld, int k, float *q, double *hcol,
+                             const ArnoldiScratch &sc, double *aux, int *stop, int step,
+                             bool reorth, cudaStream_t s);
+cudaError_t normalize_first(const float *r, int64_t L, float *w0, const ArnoldiScratch &sc,
+                            double *aux, int *stop, cudaStream_t s);
+cudaError_t launch_combine(const float *W, int64_t L, int64_t ld, const double *Y, int K,
+                           int ystride, const int *stop, int kfixed, const float *x0, float *x,
+                           int max_blocks, cudaStream_t s);
+cudaError_t launch_rsub(const float *b, float *r, int64_t L, int max_blocks, cudaStream_t s);
+
+constexpr int kMaxBlocks = 152 * 8;
+
+// ----------------------------------------------------------------------------- profiling
+// Optional CUDA-event timing of launch groups, and a count of every kernel launch.
+struct PhaseRec { int phase; int launches; cudaEvent_t a, b; };
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<PhaseRec> g_prof_recs;
+static std::vector<cudaEvent_t> g_prof_pool;
+static std::atomic<int64_t> g_launches{0};
+
+static cudaEvent_t prof_event()
+{
+    if (!g_prof_pool.empty()) {
+        cudaEvent_t e = g_prof_pool.back();
+        g_prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct PhaseScope {
+    int phase, launches;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    PhaseScope(int ph, int n, cudaStream_t st) : phase(ph), launches(n), s(st)
+    {
+        g_launches += n;
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        if (g_prof_on) {
+            a = prof_event();
+            if (a) cudaEventRecord(a, s);
+        }
+    }
+    ~PhaseScope()
+    {
+        if (!a) return;
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        cudaEvent_t b = prof_event();
+        if (b) {
+            cudaEventRecord(b, s);
+            g_prof_recs.push_back({phase, launches, a, b});
+        }
+    }
+};
+#define CT_CAT2(a, b) a##b
+#define CT_CAT(a, b) CT_CAT2(a, b)
+#define CT_PHASE(ph, n, s) ::ct::PhaseScope CT_CAT(ct_phase_scope_, __LINE__)((ph), (n), (s))
+
+}  // namespace ct
+
+using namespace ct;
+
+// ============================================================================ workspace
+struct Workspace {
+    int method = -1, K = 0, basis = 0;
+    int64_t L = 0;          // basis row length in floats (multiple of 4, zero tail)
+    float *W = nullptr;     // (K+1) rows
+    float *q = nullptr;     // L
+    float *img = nullptr;   // image scratch, img_ld floats
+    float *sino = nullptr;  // padded sinogram scratch
+    float *vec = nullptr;   // L (initial residual)
+    double *H = nullptr, *Y = nullptr, *lam = nullptr, *res = nullptr, *aux = nullptr;
+    double *partial = nullptr;
+    unsigned *counter = nullptr;
+    int *stop = nullptr;
+};
+
+static void ws_free(Workspace *w)
+{
+    if (!w) return;
+    cudaFree(w->W); cudaFree(w->q); cudaFree(w->img); cudaFree(w->sino); cudaFree(w->vec);
+    cudaFree(w->H); cudaFree(w->Y); cudaFree(w->lam); cudaFree(w->res); cudaFree(w->aux);
+    cudaFree(w->partial); cudaFree(w->counter); cudaFree(w->stop);
+    delete w;
+}
+
+struct GeomExtra {
+    Workspace *ws[2] = {nullptr, nullptr};
+};
+
+template <class T>
+static cudaError_t dalloc(T **p, size_t count)
+{
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * (count ? count : 1));
+    if (e == cudaSuccess) e = cudaMemset(*p, 0, sizeof(T) * (count ? count : 1));
+    return e;
+}
+
+static ct_status ws_get(ct_geom *g, int method, int K, int basis, Workspace **out)
+{
+    GeomExtra *ex = reinterpret_cast<GeomExtra *>(g->ws);
+    Workspace *w = ex->ws[method];
+    const int64_t img_ld = round_up(g->n, 4);
+    const int64_t sino_len = (int64_t)g->dg.n_views * g->dg.ndv * g->dg.sino_ld;
+    const int64_t L = (method == 0) ? sino_len : img_ld;
+    if (w && w->K >= K && w->basis == basis && w->L == L) { *out = w; return CT_OK; }
+    ws_free(w);
+    ex->ws[method] = nullptr;
+    w = new Workspace();
+    w->method = method; w->K = K; w->basis = basis; w->L = L;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = dalloc(&w->W, (size_t)(K + 1) * L);
+    if (e == cudaSuccess) e = dalloc(&w->q, (size_t)L);
+    if (e == cudaSuccess) e = dalloc(&w->vec, (size_t)L);
+    if (e == cudaSuccess) e = dalloc(&w->img, (size_t)img_ld);
+    if (e == cudaSuccess) e = dalloc(&w->sino, (size_t)sino_len);
+    if (e == cudaSuccess) e = dalloc(&w->H, (size_t)(K + 1) * K);
+    if (e == cudaSuccess) e = dalloc(&w->Y, (size_t)K * K);
+    if (e == cudaSuccess) e = dalloc(&w->lam, (size_t)K);
+    if (e == cudaSuccess) e = dalloc(&w->res, (size_t)K);
+    if (e == cudaSuccess) e = dalloc(&w->aux, (size_t)(8 + 2 * (K + 2)));
+    if (e == cudaSuccess) e = dalloc(&w->partial, (size_t)kMaxBlocks * (K + 2));
+    if (e == cudaSuccess) e = dalloc(&w->counter, 4);
+    if (e == cudaSuccess) e = dalloc(&w->stop, 4);
+    if (e != cudaSuccess) {
+        ws_free(w);
+        set_error(std::string("workspace allocation: ") + cudaGetErrorString(e));
+        return CT_ENOMEM;
+    }
+    ex->ws[method] = w;
+    *out = w;
+    return CT_OK;
+}
+
+// ============================================================================ geometry
+static void ray_setup(const ct_geom_desc *d, int view, int bin, double p0[2], double dir[2])
+{
+    double th = d->angles[view];
+    double ct_ = cos(th), st = sin(th);
+    double u = (bin - (d->n_det_u - 1) / 2.0) * d->pitch_u;
+    if (d->kind == CT_PARALLEL2D) {
+        p0[0] = u * ct_; p0[1] = u * st;
+        dir[0] = -st; dir[1] = ct_;
+    } else {
+        double S[2] = {d->sid * ct_, d->sid * st};
+        double off = d->sdd - d->sid;
+        double P[2] = {-off * ct_ - u * st, -off * st + u * ct_};
+        double D[2] = {P[0] - S[0], P[1] - S[1]};
+        double L = sqrt(D[0] * D[0] + D[1] * D[1]);
+        p0[0] = S[0]; p0[1] = S[1];
+        dir[0] = D[0] / L; dir[1] = D[1] / L;
+    }
+}
+
+static Ray2D make_ray(const ct_geom_desc *d, int view, int bin)
+{
+    double p0[2], dir[2];
+    ray_setup(d, view, bin, p0, dir);
+    const double h = d->pixel;
+    int axis, n_drive, n_other;
+    double a_drive, a_other, p_drive, p_other;
+    if (fabs(dir[0]) >= fabs(dir[1])) {        // drive along x
+        axis = 0; n_drive = d->nx; n_other = d->ny;
+        a_drive = dir[0]; a_other = dir[1]; p_drive = p0[0]; p_other = p0[1];
+    } else {
+        axis = 1; n_drive = d->ny; n_other = d->nx;
+        a_drive = dir[1]; a_other = dir[0]; p_drive = p0[1]; p_other = p0[0];
+    }
+    // point of the ray on the central driving line (coordinate 0 along the driving axis)
+    double t0 = -p_drive / a_drive;
+    double other0 = p_other + t0 * a_other;
+    double pmid = other0 / h + (n_other - 1) / 2.0;
+    double slope = a_other / a_drive;
+    double tmid = (n_drive - 1) / 2.0;
+    int lo = 0, hi = n_drive - 1;
+    // keep the samples whose tap index lies in [-1, n_other)
+    if (fabs(slope) < 1e-300) {
+        if (!(pmid >= -1.0 && pmid < n_other)) { lo = 1; hi = 0; }
+    } else {
+        double ta = tmid + (-1.0 - pmid) / slope, tb = tmid + (n_other - pmid) / slope;
+        double tl = std::min(ta, tb), th = std::max(ta, tb);
+        double clo = ceil(tl - 1e-6), chi = floor(th + 1e-6);
+        if (clo > lo) lo = (clo > hi + 1) ? hi + 1 : (int)clo;
+        if (chi < hi) hi = (chi < lo - 1) ? lo - 1 : (int)chi;
+        if (hi < lo) { lo = 1; hi = 0; }
+    }
+    Ray2D r;
+    r.pmid = (float)pmid;
+    r.slope = (float)slope;
+    r.weight = (float)(h / fabs(a_drive));
+    r.packed = (uint32_t)lo | ((uint32_t)hi << 15) | ((uint32_t)axis << 30);
+    return r;
+}
+
+extern "C" {
+
+const char *ct_last_error(void) { return g_last_error.c_str(); }
+
+const char *ct_status_string(ct_status s)
+{
+    switch (s) {
+    case CT_OK: return "CT_OK";
+    case CT_EINVAL: return "CT_EINVAL";
+    case CT_ENOMEM: return "CT_ENOMEM";
+    case CT_ECUDA: return "CT_ECUDA";
+    case CT_BREAKDOWN: return "CT_BREAKDOWN";
+    case CT_ETIMEOUT: return "CT_ETIMEOUT";
+    case CT_ENONFINITE: return "CT_ENONFINITE";
+    }
+    return "CT_UNKNOWN";
+}
+
+ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
+{
+    if (!d || !out) return einval("ct_geom_create: null argument");
+    *out = nullptr;
+    if (d->kind != CT_PARALLEL2D && d->kind != CT_FANFLAT2D)
+        return einval("ct_geom_create: unsupported geometry kind");
+    if (d->nx < 1 || d->ny < 1 || d->nx > 16384 || d->ny > 16384)
+        return einval("ct_geom_create: image size out of range [1, 16384]");
+    if (d->n_views < 1 || d->n_det_u < 1 || d->n_det_u > (1 << 20))
+        return einval("ct_geom_create: n_views and n_det_u must be >= 1");
+    if (!d->angles) return einval("ct_geom_create: angles is NULL");
+    if (!(d->pixel > 0) || !(d->pitch_u > 0)) return einval("ct_geom_create: pixel and pitch must be > 0");
+    for (int v = 0; v < d->n_views; ++v)
+        if (!isfinite(d->angles[v])) return einval("ct_geom_create: non-finite angle");
+    if (d->kind == CT_FANFLAT2D) {
+        double half_diag = 0.5 * d->pixel * sqrt((double)d->nx * d->nx + (double)d->ny * d->ny);
+        if (!(d->sid > half_diag) || !(d->sdd > d->sid))
+            return einval("ct_geom_create: fan geometry needs SDD > SID > image half-diagonal");
+    }
+    ct_geom *g = new ct_geom();
+    memset(g, 0, sizeof(*g));
+    g->desc = *d;
+    g->angles_host = new double[d->n_views];
+    memcpy(g->angles_host, d->angles, sizeof(double) * d->n_views);
+    g->desc.angles = g->angles_host;
+    g->desc.nz = 1;
+    g->desc.n_det_v = 1;
+    g->n = (int64_t)d->nx * d->ny;
+    g->m = (int64_t)d->n_views * d->n_det_u;
+    DeviceGeom &dg = g->dg;
+    dg.kind = d->kind; dg.nx = d->nx; dg.ny = d->ny; dg.nz = 1;
+    dg.h = (float)d->pixel; dg.n_views = d->n_views; dg.ndu = d->n_det_u; dg.ndv = 1;
+    dg.pitch_u = (float)d->pitch_u; dg.pitch_v = 1.f; dg.sid = (float)d->sid; dg.sdd = (float)d->sdd;
+    dg.row_pairs_ld = (int)round_up(d->nx + 1, 16);
+    dg.col_pairs_ld = (int)round_up(d->ny + 1, 16);
+    dg.sino_ld = (int)round_up(d->n_det_u + 4, 4);
+
+    std::vector<Ray2D> rays((size_t)g->m);
+    g->a_samples = 0;
+    for (int v = 0; v < d->n_views; ++v)
+        for (int j = 0; j < d->n_det_u; ++j) {
+            Ray2D r = make_ray(&g->desc, v, j);
+            rays[(size_t)v * d->n_det_u + j] = r;
+            int lo = r.packed & 0x7fff, hi = (r.packed >> 15) & 0x7fff;
+            if (hi >= lo) g->a_samples += hi - lo + 1;
+        }
+    std::vector<ViewBP> views(d->n_views);
+    for (int v = 0; v < d->n_views; ++v) {
+        double c = cos(d->angles[v]), s = sin(d->angles[v]);
+        views[v].cs = (float)c;
+        views[v].sn = (float)s;
+        views[v].a = (float)(d->pixel * c / d->pitch_u);
+        views[v].b = (float)(d->pixel * s / d->pitch_u);
+    }
+    cudaError_t e = cudaSuccess;
+    e = dalloc(&g->rays_dev, rays.size());
+    if (e == cudaSuccess) e = cudaMemcpy(g->rays_dev, rays.data(), sizeof(Ray2D) * rays.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = dalloc(&g->views_dev, views.size());
+    if (e == cudaSuccess) e = cudaMemcpy(g->views_dev, views.data(), sizeof(ViewBP) * views.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = dalloc(&g->prow_dev, (size_t)d->ny * dg.row_pairs_ld);
+    if (e == cudaSuccess) e = dalloc(&g->pcol_dev, (size_t)d->nx * dg.col_pairs_ld);
+    if (e == cudaSuccess) e = dalloc(&g->sino_pad_dev, (size_t)d->n_views * dg.sino_ld);
+    if (e != cudaSuccess) {
+        set_error(std::string("ct_geom_create: ") + cudaGetErrorString(e));
+        ct_geom_destroy(g);
+        return CT_ENOMEM;
+    }
+    dg.rays = g->rays_dev;
+    dg.views = g->views_dev;
+    g->ws = reinterpret_cast<struct Workspace *>(new GeomExtra());
+    *out = g;
+    return CT_OK;
+}
+
+void ct_geom_destroy(ct_geom *g)
+{
+    if (!g) return;
+    if (g->ws) {
+        GeomExtra *ex = reinterpret_cast<GeomExtra *>(g->ws);
+        ws_free(ex->ws[0]);
+        ws_free(ex->ws[1]);
+        delete ex;
+    }
+    cudaFree(g->rays_dev); cudaFree(g->views_dev); cudaFree(g->prow_dev); cudaFree(g->pcol_dev);
+    cudaFree(g->sino_pad_dev);
+    delete[] g->angles_host;
+    delete g;
+}
+
+ct_status ct_geom_dims(const ct_geom *g, int64_t *n, int64_t *m)
+{
+    if (!g) return einval("ct_geom_dims: null geometry");
+    if (n) *n = g->n;
+    if (m) *m = g->m;
+    return CT_OK;
+}
+
+ct_status ct_geom_work(const ct_geom *g, int64_t *a_samples, int64_t *b_samples)
+{
+    if (!g) return einval("ct_geom_work: null geometry");
+    if (a_samples) *a_samples = g->a_samples;
+    if (b_samples) *b_samples = g->n * (int64_t)g->desc.n_views;
+    return CT_OK;
+}
+
+ct_status ct_forward_A(ct_geom *g, const float *x_dev, float *y_dev, ct_stream_t stream)
+{
+    if (!g || !x_dev || !y_dev) return einval("ct_forward_A: null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    {
+        CT_PHASE(CT_PH_LAYOUT, 1, s);
+        CT_CUDA(launch_image_pairs(g, x_dev, nullptr, s));
+    }
+    CT_PHASE(CT_PH_FORWARD, 1, s);
+    CT_CUDA(launch_joseph2d(g, y_dev, g->dg.ndu, 0, nullptr, s));
+    return CT_OK;
+}
+
+ct_status ct_back_B(ct_geom *g, const float *y_dev, float *x_dev, ct_stream_t stream)
+{
+    if (!g || !y_dev || !x_dev) return einval("ct_back_B: null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    {
+        CT_PHASE(CT_PH_LAYOUT, 1, s);
+        CT_CUDA(launch_pad_sino(g, y_dev, g->sino_pad_dev, s));
+    }
+    CT_PHASE(CT_PH_BACK, 1, s);
+    CT_CUDA(launch_pixbp2d(g, g->sino_pad_dev, x_dev, nullptr, s));
+    return CT_OK;
+}
+
+void ct_hybrid_opts_default(ct_hybrid_opts *o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->max_iters = 30;
+    o->rule = CT_LAMBDA_GCV;
+    o->tau = 1.01;
+    o->reorth = 1;
+    o->basis = CT_BASIS_F32;
+}
+
+}  // extern "C"
+
+// ============================================================================ solvers
+static ct_status check_opts(const ct_hybrid_opts *o)
+{
+    if (!o) return einval("solver: opts is NULL");
+    if (o->max_iters < 1 || o->max_iters > kMaxSmallK)
+        return einval("solver: max_iters must be in [1, " + std::to_string(kMaxSmallK) + "]");
+    if (o->rule < CT_LAMBDA_NONE || o->rule > CT_LAMBDA_DP) return einval("solver: bad lambda rule");
+    if (o->rule == CT_LAMBDA_FIXED && !(o->lambda_fixed >= 0)) return einval("solver: lambda_fixed must be >= 0");
+    if (o->rule == CT_LAMBDA_DP && (!(o->noise_norm >= 0) || !(o->tau > 0)))
+        return einval("solver: DP needs noise_norm >= 0 and tau > 0");
+    if (o->basis != CT_BASIS_F32) return einval("solver: only the FP32 basis is built for 2D solves");
+    return CT_OK;
+}
+
+static ct_status finish(Workspace *w, const ct_hybrid_opts *o, ct_hybrid_info *info, cudaStream_t s)
+{
+    CT_CUDA(cudaStreamSynchronize(s));
+    int stop[2];
+    double beta;
+    CT_CUDA(cudaMemcpy(stop, w->stop, sizeof(stop), cudaMemcpyDeviceToHost));
+    CT_CUDA(cudaMemcpy(&beta, w->aux + 2, sizeof(double), cudaMemcpyDeviceToHost));
+    const int K = o->max_iters;
+    int kf = (stop[0] == 0) ? K : std::max(stop[0], 0);
+    std::vector<double> lam(K), res(K);
+    CT_CUDA(cudaMemcpy(lam.data(), w->lam, sizeof(double) * K, cudaMemcpyDeviceToHost));
+    CT_CUDA(cudaMemcpy(res.data(), w->res, sizeof(double) * K, cudaMemcpyDeviceToHost));
+    for (int i = kf; i < K; ++i) lam[i] = res[i] = NAN;
+    if (o->lambda_hist) memcpy(o->lambda_hist, lam.data(), sizeof(double) * K);
+    if (o->resid_hist) memcpy(o->resid_hist, res.data(), sizeof(double) * K);
+    ct_status st = (stop[0] == 0) ? CT_OK : (ct_status)stop[1];
+    if (info) {
+        info->iters_done = kf;
+        info->beta = beta;
+        info->final_lambda = kf > 0 ? lam[kf - 1] : 0.0;
+        info->final_resid = kf > 0 ? res[kf - 1] : beta;
+        info->status = st;
+    }
+    if (st == CT_ENONFINITE) { set_error("solver: non-finite value met"); return st; }
+    return CT_OK;
+}
+
+static ct_status run_small_solve(Workspace *w, const ct_hybrid_opts *o, int step, cudaStream_t s,
+                                 double dp_target)
+{
+    SmallSolveParams p;
+    p.H = w->H; p.ldh = w->K + 1; p.k = step; p.beta = 0.0; p.betap = w->aux + 2;
+    p.rule = o->rule; p.lambda_fixed = o->lambda_fixed; p.dp_target = dp_target;
+    p.y = w->Y + (size_t)(step - 1) * w->K;
+    p.lambda_out = w->lam + (step - 1);
+    p.resid_out = w->res + (step - 1);
+    p.stop = w->stop;
+    CT_PHASE(CT_PH_SMALL, 1, s);
+    CT_CUDA(launch_small_solve(p, s));
+    return CT_OK;
+}
+
+extern "C" ct_status ab_gmres_hybrid(ct_geom *g, const float *b_dev, const float *u0_dev,
+                                     float *x_dev, const ct_hybrid_opts *o, ct_hybrid_info *info,
+                                     ct_stream_t stream)
+{
+    if (!g || !b_dev || !x_dev) return einval("ab_gmres_hybrid: null argument");
+    ct_status st = check_opts(o);
+    if (st != CT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace *w;
+    if ((st = ws_get(g, 0, o->max_iters, o->basis, &w)) != CT_OK) return st;
+    const int K = o->max_iters;
+    const int64_t L = w->L, ld = w->L;
+    const int sld = g->dg.sino_ld;
+    ArnoldiScratch sc{w->partial, w->counter, kMaxBlocks, w->K};
+    const double dp_target = o->tau * o->noise_norm;
+    CT_CUDA(cudaMemsetAsync(w->stop, 0, 2 * sizeof(int), s));
+    CT_CUDA(cudaMemsetAsync(w->counter, 0, 4 * sizeof(unsigned), s));
+    // Alg. 1 lines 1-3: x0 = B u0, r0 = b - A x0, w1 = r0 / ||r0||
+    {
+        CT_PHASE(CT_PH_OTHER, u0_dev ? 8 : 3, s);
+        CT_CUDA(launch_pad_sino(g, b_dev, w->vec, s));
+        if (u0_dev) {
+            CT_CUDA(launch_pad_sino(g, u0_dev, w->sino, s));
+            CT_CUDA(launch_pixbp2d(g, w->sino, w->img, nullptr, s));
+            CT_CUDA(launch_image_pairs(g, w->img, nullptr, s));
+            CT_CUDA(launch_joseph2d(g, w->q, sld, 2, nullptr, s));
+            CT_CUDA(launch_rsub(w->vec, w->q, L, kMaxBlocks, s));
+            CT_CUDA(normalize_first(w->q, L, w->W, sc, w->aux, w->stop, s));
+        } else {
+            CT_CUDA(normalize_first(w->vec, L, w->W, sc, w->aux, w->stop, s));
+        }
+    }
+    const int ldh = w->K + 1;
+    for (int step = 1; step <= K; ++step) {
+        const int k = step - 1;
+        float *wk = w->W + (int64_t)k * ld;
+        {
+            CT_PHASE(CT_PH_BACK, 1, s);
+            CT_CUDA(launch_pixbp2d(g, wk, w->img, w->stop, s));       // line 5: B w_k
+        }
+        {
+            CT_PHASE(CT_PH_LAYOUT, 1, s);
+            CT_CUDA(launch_image_pairs(g, w->img, w->stop, s));
+        }
+        {
+            CT_PHASE(CT_PH_FORWARD, 1, s);
+            CT_CUDA(launch_joseph2d(g, w->q, sld, 2, w->stop, s));   //          A (B w_k)
+        }
+        {
+            CT_PHASE(CT_PH_ARNOLDI, o->reorth ? 4 : 3, s);               // lines 6-11
+            CT_CUDA(arnoldi_step_dev(w->W, L, ld, k, w->q, w->H + (int64_t)k * ldh,
+                                     sc, w->aux, w->stop, step, o->reorth != 0, s));
+        }
+        if ((st = run_small_solve(w, o, step, s, dp_target)) != CT_OK) return st;   // 12-13
+    }
+    // line 13 at k = K: x = x0 + B W y = B (u0 + W y)
+    {
+        CT_PHASE(CT_PH_OTHER, u0_dev ? 2 : 1, s);
+        if (u0_dev) CT_CUDA(launch_pad_sino(g, u0_dev, w->sino, s));
+        CT_CUDA(launch_combine(w->W, L, ld, w->Y, K, w->K, w->stop, 0, u0_dev ? w->sino : nullptr,
+                               w->q, kMaxBlocks, s));
+    }
+    {
+        CT_PHASE(CT_PH_BACK, 1, s);
+        CT_CUDA(launch_pixbp2d(g, w->q, x_dev, nullptr, s));
+    }
+    return finish(w, o, info, s);
+}
+
+extern "C" ct_status ba_gmres_hybrid(ct_geom *g, const float *b_dev, const float *x0_dev,
+                                     float *x_dev, const ct_hybrid_opts *o, ct_hybrid_info *info,
+                                     ct_stream_t stream)
+{
+    if (!g || !b_dev || !x_dev) return einval("ba_gmres_hybrid: null argument");
+    ct_status st = check_opts(o);
+    if (st != CT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace *w;
+    if ((st = ws_get(g, 1, o->max_iters, o->basis, &w)) != CT_OK) return st;
+    const int K = o->max_iters;
+    const int64_t L = w->L, ld = w->L;
+    const int sld = g->dg.sino_ld;
+    const int64_t msino = (int64_t)g->dg.n_views * sld;
+    ArnoldiScratch sc{w->partial, w->counter, kMaxBlocks, w->K};
+    const double dp_target = o->tau * o->noise_norm;
+    CT_CUDA(cudaMemsetAsync(w->stop, 0, 2 * sizeof(int), s));
+    CT_CUDA(cudaMemsetAsync(w->counter, 0, 4 * sizeof(unsigned), s));
+    // Alg. 2 lines 1-3: r0 = B (b - A x0), w1 = r0 / ||r0||
+    {
+        CT_PHASE(CT_PH_OTHER, x0_dev ? 7 : 4, s);
+        CT_CUDA(launch_pad_sino(g, b_dev, w->sino, s));
+        if (x0_dev) {
+            CT_CUDA(cudaMemsetAsync(w->img, 0, sizeof(float) * L, s));
+            CT_CUDA(cudaMemcpyAsync(w->img, x0_dev, sizeof(float) * g->n, cudaMemcpyDeviceToDevice, s));
+            CT_CUDA(launch_image_pairs(g, w->img, nullptr, s));
+            CT_CUDA(launch_joseph2d(g, w->q, sld, 2, nullptr, s));   // q as sinogram scratch
+            CT_CUDA(launch_rsub(w->sino, w->q, msino, kMaxBlocks, s));
+            CT_CUDA(launch_pixbp2d(g, w->q, w->vec, nullptr, s));
+        } else {
+            CT_CUDA(launch_pixbp2d(g, w->sino, w->vec, nullptr, s));
+        }
+        CT_CUDA(normalize_first(w->vec, L, w->W, sc, w->aux, w->stop, s));
+    }
+    const int ldh = w->K + 1;
+    for (int step = 1; step <= K; ++step) {
+        const int k = step - 1;
+        float *wk = w->W + (int64_t)k * ld;
+        {
+            CT_PHASE(CT_PH_LAYOUT, 1, s);
+            CT_CUDA(launch_image_pairs(g, wk, w->stop, s));           // line 5: A w_k
+        }
+        {
+            CT_PHASE(CT_PH_FORWARD, 1, s);
+            CT_CUDA(launch_joseph2d(g, w->sino, sld, 2, w->stop, s));
+        }
+        {
+            CT_PHASE(CT_PH_BACK, 1, s);
+            CT_CUDA(launch_pixbp2d(g, w->sino, w->q, w->stop, s));     //          B (A w_k)
+        }
+        {
+            CT_PHASE(CT_PH_ARNOLDI, o->reorth ? 4 : 3, s);
+            CT_CUDA(arnoldi_step_dev(w->W, L, ld, k, w->q, w->H + (int64_t)k * ldh,
+                                     sc, w->aux, w->stop, step, o->reorth != 0, s));
+        }
+        if ((st = run_small_solve(w, o, step, s, dp_target)) != CT_OK) return st;
+    }
+    // line 13: x = x0 + W y
+    {
+        CT_PHASE(CT_PH_OTHER, 1, s);
+        if (x0_dev) {
+            CT_CUDA(cudaMemsetAsync(w->img, 0, sizeof(float) * L, s));
+            CT_CUDA(cudaMemcpyAsync(w->img, x0_dev, sizeof(float) * g->n, cudaMemcpyDeviceToDevice, s));
+        }
+        CT_CUDA(launch_combine(w->W, L, ld, w->Y, K, w->K, w->stop, 0, x0_dev ? w->img : nullptr,
+                               w->q, kMaxBlocks, s));
+        CT_CUDA(cudaMemcpyAsync(x_dev, w->q, sizeof(float) * g->n, cudaMemcpyDeviceToDevice, s));
+    }
+    return finish(w, o, info, s);
+}
+
+// ============================================================================ building blocks
+extern "C" ct_status ct_arnoldi_step(float *W_dev, int64_t len, int64_t ld, int k, float *q_dev,
+                                     double *h_dev, ct_stream_t stream)
+{
+    if (!W_dev || !q_dev || !h_dev) return einval("ct_arnoldi_step: null argument");
+    if (k < 0 || k > 1022 || len < 1 || ld < len || (len % 4) || (ld % 4))
+        return einval("ct_arnoldi_step: need 0 <= k <= 1022, len % 4 == 0, ld % 4 == 0, ld >= len");
+    cudaStream_t s = (cudaStream_t)stream;
+    // scratch for this call (the building-block entry point allocates; solvers do not)
+    double *partial = nullptr, *aux = nullptr;
+    unsigned *counter = nullptr;
+    int *stop = nullptr;
+    CT_CUDA(cudaMallocAsync((void **)&partial, sizeof(double) * kMaxBlocks * (k + 3), s));
+    CT_CUDA(cudaMallocAsync((void **)&aux, sizeof(double) * (8 + 2 * (k + 3)), s));
+    CT_CUDA(cudaMallocAsync((void **)&counter, sizeof(unsigned) * 4, s));
+    CT_CUDA(cudaMallocAsync((void **)&stop, sizeof(int) * 4, s));
+    CT_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned) * 4, s));
+    CT_CUDA(cudaMemsetAsync(stop, 0, sizeof(int) * 4, s));
+    CT_CUDA(cudaMemsetAsync(h_dev, 0, sizeof(double) * (k + 2), s));
+    ArnoldiScratch sc{partial, counter, kMaxBlocks, k + 1};
+    CT_CUDA(arnoldi_step_dev(W_dev, len, ld, k, q_dev, h_dev, sc, aux, stop, 1, true, s));
+    CT_CUDA(cudaFreeAsync(partial, s));
+    CT_CUDA(cudaFreeAsync(aux, s));
+    CT_CUDA(cudaFreeAsync(counter, s));
+    CT_CUDA(cudaFreeAsync(stop, s));
+    return CT_OK;
+}
+
+extern "C" ct_status ct_projected_solve(const double *H_dev, int ldh, int k, double beta,
+                                        ct_lambda_rule rule, double lambda_fixed, double dp_target,
+                                        double *y_dev, double *lambda_dev, double *resid_dev,
+                                        ct_stream_t stream)
+{
+    if (!H_dev || !y_dev || !lambda_dev || !resid_dev) return einval("ct_projected_solve: null argument");
+    if (k < 1 || k > kMaxSmallK || ldh < k + 1)
+        return einval("ct_projected_solve: need 1 <= k <= " + std::to_string(kMaxSmallK) + " and ldh >= k+1");
+    if (rule < CT_LAMBDA_NONE || rule > CT_LAMBDA_DP) return einval("ct_projected_solve: bad rule");
+    SmallSolveParams p;
+    p.H = H_dev; p.ldh = ldh; p.k = k; p.beta = beta; p.betap = nullptr;
+    p.rule = rule; p.lambda_fixed = lambda_fixed; p.dp_target = dp_target;
+    p.y = y_dev; p.lambda_out = lambda_dev; p.resid_out = resid_dev; p.stop = nullptr;
+    CT_CUDA(launch_small_solve(p, (cudaStream_t)stream));
+    return CT_OK;
+}
+
+// ============================================================================ instrumentation
+extern "C" ct_status ct_profile_enable(int on)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto &r : g_prof_recs) { g_prof_pool.push_back(r.a); g_prof_pool.push_back(r.b); }
+    g_prof_recs.clear();
+    g_prof_on = (on != 0);
+    return CT_OK;
+}
+
+extern "C" ct_status ct_profile_collect(ct_phase_time *out)
+{
+    if (!out) return einval("ct_profile_collect: out is NULL");
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (int i = 0; i < CT_PH_COUNT; ++i) out[i] = ct_phase_time{0.0, 0, 0};
+    ct_status st = CT_OK;
+    for (auto &r : g_prof_recs) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess) st = cuda_fail(e, "ct_profile_collect");
+        out[r.phase].ms += ms;
+        out[r.phase].launches += r.launches;
+        out[r.phase].groups += 1;
+        g_prof_pool.push_back(r.a);
+        g_prof_pool.push_back(r.b);
+    }
+    g_prof_recs.clear();
+    return st;
+}
+
+extern "C" int64_t ct_launch_count(void) { return g_launches.load(); }

@@ -1,0 +1,112 @@
+// Internal declarations shared by the CUDA translation units of libctabba.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/ctabba.h"
+
+namespace ct {
+
+// ----------------------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+ct_status cuda_fail(cudaError_t e, const char *what);
+#define CT_CUDA(call)                                                        \
+    do {                                                                     \
+        cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess) return ::ct::cuda_fail(e_, #call);            \
+    } while (0)
+
+// ----------------------------------------------------------------------------- geometry
+// One Joseph ray in index units: along the driving axis the sample at integer index t lies
+// at fractional index pos = pmid + slope * (t - (n_drive-1)/2) of the other axis.  t runs
+// over [t_lo, t_hi]; axis = 0 drives along x (columns), 1 along y (rows).
+struct __align__(16) Ray2D {
+    float pmid;
+    float slope;
+    float weight;   // h / |d_drive|
+    uint32_t packed; // t_lo (bits 0-14) | t_hi (bits 15-29) | axis (bit 30)
+};
+
+// Per-view constants of the pixel-driven backprojector.
+struct __align__(16) ViewBP {
+    float cs, sn;   // cos, sin of the view angle
+    float a, b;     // parallel: h cos / pitch, h sin / pitch; fan: unused
+};
+
+// 3D cone per-view constants (source position and detector frame in voxel units).
+struct __align__(16) View3D {
+    float cs, sn, pad0, pad1;
+};
+
+struct DeviceGeom {
+    int kind, nx, ny, nz;
+    float h;
+    int n_views, ndu, ndv;
+    float pitch_u, pitch_v, sid, sdd;
+    // padded layouts
+    int row_pairs_ld;   // P_row row length in float2: >= nx + 1
+    int col_pairs_ld;   // P_col row length in float2: >= ny + 1
+    int sino_ld;        // padded sinogram row length: ndu + 4 (2 zero bins each side)
+    // tables
+    const Ray2D *rays;  // m rays (2D)
+    const ViewBP *views;
+};
+
+}  // namespace ct
+
+struct ct_geom {
+    ct_geom_desc desc;
+    double *angles_host;
+    int64_t n, m;
+    int64_t a_samples;   // sum over rays of the clipped Joseph sample counts
+    ct::DeviceGeom dg;
+    // device allocations owned by the geometry
+    ct::Ray2D *rays_dev;
+    ct::ViewBP *views_dev;
+    float2 *prow_dev;   // [ny][row_pairs_ld] pairs along x
+    float2 *pcol_dev;   // [nx][col_pairs_ld] pairs along y
+    float *sino_pad_dev;  // [n_views * ndv][sino_ld]
+    // solver workspace (grown on demand)
+    struct Workspace *ws;
+};
+
+namespace ct {
+
+// ----------------------------------------------------------------------------- projectors
+// Every launcher takes an optional device stop word: when non-null and non-zero at kernel
+// start, the kernel returns at once (a solver that met breakdown skips the remaining steps).
+// Image x (row-major, n floats) -> the two padded pair layouts used by the Joseph kernel.
+cudaError_t launch_image_pairs(const ct_geom *g, const float *x, const int *stop, cudaStream_t s);
+// y[view][bin] -> padded sinogram rows (row length sino_ld, bin j at index j + 2).
+cudaError_t launch_pad_sino(const ct_geom *g, const float *y, float *ypad, cudaStream_t s);
+// Joseph A from the pair layouts; output row length y_ld, bin j at index y_off + j.
+cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, const int *stop,
+                            cudaStream_t s);
+// pixel-driven B from a padded sinogram (row length sino_ld)
+cudaError_t launch_pixbp2d(const ct_geom *g, const float *ypad, float *x, const int *stop,
+                           cudaStream_t s);
+
+// ----------------------------------------------------------------------------- Arnoldi
+struct ArnoldiScratch {
+    double *partial;      // [max_blocks][kmax + 2]
+    unsigned *counter;    // block-completion counter (reset by the last block)
+    int max_blocks;
+    int kmax;
+};
+
+// ----------------------------------------------------------------------------- small solve
+constexpr int kMaxSmallK = 160;   // largest projected problem held in shared memory
+struct SmallSolveParams {
+    const double *H;  int ldh; int k;
+    double beta; const double *betap;   // beta, or read from device when betap != null
+    int rule; double lambda_fixed; double dp_target;
+    double *y; double *lambda_out; double *resid_out;
+    const int *stop;  // solver stop word (may be null)
+};
+cudaError_t launch_small_solve(const SmallSolveParams &p, cudaStream_t s);
+size_t small_solve_smem_bytes(int k);
+
+}  // namespace ct

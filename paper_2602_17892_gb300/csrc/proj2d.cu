@@ -1,0 +1,209 @@
+// 2D projector kernels: ray-driven Joseph forward projector A and pixel-driven linear-
+// interpolation backprojector B (the unmatched pair of Sec. 2 of arXiv 2602.17892).
+//
+// Data layout in HBM (all FP32):
+//   P_row[r][j]  = (x[r][j-1], x[r][j])   j in [0, nx], zero outside the image
+//   P_col[c][i]  = (x[i-1][c], x[i][c])   i in [0, ny]
+// so every Joseph sample is ONE 8-byte load of the two neighbours it interpolates, with no
+// bounds test: rays driven along x read P_col (neighbouring rays of a warp read adjacent
+// pairs), rays driven along y read P_row.  The padded sinogram has 2 zero bins on each side
+// of every detector row, so the backprojector's two taps also need no bounds test.
+#include "ct_internal.h"
+
+namespace ct {
+
+// ---------------------------------------------------------------------------- pair layouts
+// One 32 x 32 tile of pair indices per block; a 33 x 33 halo tile of x sits in smem.
+__global__ void __launch_bounds__(256) image_pairs_kernel(
+    const float *__restrict__ x, int nx, int ny, float2 *__restrict__ prow, int prow_ld,
+    float2 *__restrict__ pcol, int pcol_ld, const int *stop)
+{
+    if (stop && stop[0] != 0) return;
+    __shared__ float tile[33][34];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int t = threadIdx.x; t < 33 * 33; t += blockDim.x) {
+        int tr = t / 33, tc = t % 33;
+        int r = r0 - 1 + tr, c = c0 - 1 + tc;
+        tile[tr][tc] = (r >= 0 && r < ny && c >= 0 && c < nx) ? x[(int64_t)r * nx + c] : 0.f;
+    }
+    __syncthreads();
+    // P_row: rows r in [r0, r0+32) (< ny), pair index j in [c0, c0+32) (<= nx)
+    for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+        int tr = t / 32, tj = t % 32;
+        int r = r0 + tr, j = c0 + tj;
+        if (r < ny && j <= nx)
+            prow[(int64_t)r * prow_ld + j] = make_float2(tile[tr + 1][tj], tile[tr + 1][tj + 1]);
+    }
+    // P_col: column c in [c0, c0+32) (< nx), pair index i in [r0, r0+32) (<= ny)
+    for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+        int tc = t / 32, ti = t % 32;
+        int c = c0 + tc, i = r0 + ti;
+        if (c < nx && i <= ny)
+            pcol[(int64_t)c * pcol_ld + i] = make_float2(tile[ti][tc + 1], tile[ti + 1][tc + 1]);
+    }
+}
+
+cudaError_t launch_image_pairs(const ct_geom *g, const float *x, const int *stop, cudaStream_t s)
+{
+    const DeviceGeom &d = g->dg;
+    dim3 grid((d.nx + 1 + 31) / 32, (d.ny + 1 + 31) / 32);
+    image_pairs_kernel<<<grid, 256, 0, s>>>(x, d.nx, d.ny, g->prow_dev, d.row_pairs_ld,
+                                            g->pcol_dev, d.col_pairs_ld, stop);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------- padded sinogram
+__global__ void pad_sino_kernel(const float *__restrict__ y, int rows, int nd, int ld,
+                                float *__restrict__ ypad)
+{
+    int64_t total = (int64_t)rows * ld;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = t / ld;
+        int j = (int)(t - r * ld) - 2;
+        ypad[t] = (j >= 0 && j < nd) ? y[r * nd + j] : 0.f;
+    }
+}
+
+cudaError_t launch_pad_sino(const ct_geom *g, const float *y, float *ypad, cudaStream_t s)
+{
+    const DeviceGeom &d = g->dg;
+    int rows = d.n_views * d.ndv;
+    int64_t total = (int64_t)rows * d.sino_ld;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    pad_sino_kernel<<<blocks, 256, 0, s>>>(y, rows, d.ndu, d.sino_ld, ypad);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------- Joseph A
+// One thread per ray.  pos = pmid + slope * (t - t_mid) is the fractional index across the
+// driving axis; the pair at index floor(pos)+1 of line t holds both interpolation taps.
+__global__ void __launch_bounds__(256) joseph2d_kernel(
+    const Ray2D *__restrict__ rays, int64_t m, int ndu,
+    const float2 *__restrict__ prow, int prow_ld, const float2 *__restrict__ pcol, int pcol_ld,
+    int nx, int ny, float *__restrict__ y, int y_ld, int y_off, const int *stop)
+{
+    if (stop && stop[0] != 0) return;
+    int64_t ray = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (ray >= m) return;
+    const Ray2D R = rays[ray];
+    const int t_lo = R.packed & 0x7fff;
+    const int t_hi = (R.packed >> 15) & 0x7fff;
+    const int axis = (R.packed >> 30) & 1;
+    const float2 *base;
+    int64_t stride;
+    float tmid, hiclamp;
+    if (axis == 0) {        // drive along x: line = column c, taps along rows
+        base = pcol; stride = pcol_ld; tmid = 0.5f * (float)(nx - 1);
+        hiclamp = __int_as_float(__float_as_int((float)ny) - 1);
+    } else {                // drive along y: line = row r, taps along columns
+        base = prow; stride = prow_ld; tmid = 0.5f * (float)(ny - 1);
+        hiclamp = __int_as_float(__float_as_int((float)nx) - 1);
+    }
+    float acc = 0.f;
+    float tf = (float)t_lo - tmid;
+    const float2 *line = base + (int64_t)t_lo * stride;
+#pragma unroll 4
+    for (int t = t_lo; t <= t_hi; ++t) {
+        float pos = fmaf(R.slope, tf, R.pmid);
+        pos = fminf(fmaxf(pos, -1.f), hiclamp);
+        float fl = floorf(pos);
+        float f = pos - fl;
+        float2 p = __ldg(line + (int)fl + 1);
+        acc += fmaf(f, p.y - p.x, p.x);
+        tf += 1.f;
+        line += stride;
+    }
+    int64_t view = ray / ndu;
+    int bin = (int)(ray - view * ndu);
+    y[view * y_ld + y_off + bin] = acc * R.weight;
+}
+
+cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, const int *stop,
+                            cudaStream_t s)
+{
+    const DeviceGeom &d = g->dg;
+    int64_t m = g->m;
+    int blocks = (int)((m + 255) / 256);
+    joseph2d_kernel<<<blocks, 256, 0, s>>>(g->rays_dev, m, d.ndu, g->prow_dev, d.row_pairs_ld,
+                                           g->pcol_dev, d.col_pairs_ld, d.nx, d.ny, y, y_ld,
+                                           y_off, stop);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------- pixel-driven B
+// One thread per pixel, blocks of 32 x 8 pixels, per-view constants staged in shared memory.
+// Parallel: bin position fj = a (c - cm) + b (r - rm) + (nd-1)/2, weight h^2/pitch.
+// Fan:      pe = p.e_u, bb = SID - p.(cos, sin) (in units of h), u = SDD pe / bb,
+//           weight h SDD / pitch * sqrt(1 + (pe/bb)^2) / bb  (= h^2 (SDD^2+u^2)/(L pitch SDD)).
+template <bool FAN>
+__global__ void __launch_bounds__(256) pixbp2d_kernel(
+    const ViewBP *__restrict__ views, int n_views, const float *__restrict__ ypad, int ld,
+    int nd, int nx, int ny, float sid_h, float k_u, float k_w, float w_par,
+    float *__restrict__ x, const int *stop)
+{
+    if (stop && stop[0] != 0) return;
+    extern __shared__ float4 sview[];
+    for (int v = threadIdx.y * 32 + threadIdx.x; v < n_views; v += 256) {
+        ViewBP vb = views[v];
+        sview[v] = make_float4(vb.cs, vb.sn, vb.a, vb.b);
+    }
+    __syncthreads();
+    const int c = blockIdx.x * 32 + threadIdx.x;
+    const int r = blockIdx.y * 8 + threadIdx.y;
+    if (c >= nx || r >= ny) return;
+    const float tc = (float)c - 0.5f * (float)(nx - 1);
+    const float tr = (float)r - 0.5f * (float)(ny - 1);
+    const float gam = 0.5f * (float)(nd - 1) + 2.f;   // +2: padded row offset
+    const float hi = (float)(nd + 2);
+    float acc = 0.f;
+    const float *row = ypad;
+#pragma unroll 4
+    for (int v = 0; v < n_views; ++v, row += ld) {
+        float4 V = sview[v];
+        float fj, w;
+        if (FAN) {
+            float pe = fmaf(tr, V.x, -tc * V.y);
+            float bb = fmaf(-tc, V.x, fmaf(-tr, V.y, sid_h));
+            float rb = __fdividef(1.f, bb);
+            float t1 = pe * rb;
+            fj = fmaf(t1, k_u, gam);
+            float q = fmaf(t1, t1, 1.f);
+            w = rb * (q * rsqrtf(q));
+        } else {
+            fj = fmaf(V.z, tc, fmaf(V.w, tr, gam));
+            w = 1.f;
+        }
+        fj = fminf(fmaxf(fj, 0.f), hi);
+        float fl = floorf(fj);
+        float f = fj - fl;
+        int j = (int)fl;
+        float a = __ldg(row + j), b = __ldg(row + j + 1);
+        acc = fmaf(w, fmaf(f, b - a, a), acc);
+    }
+    x[(int64_t)r * nx + c] = acc * (FAN ? k_w : w_par);
+}
+
+cudaError_t launch_pixbp2d(const ct_geom *g, const float *ypad, float *x, const int *stop,
+                           cudaStream_t s)
+{
+    const DeviceGeom &d = g->dg;
+    dim3 block(32, 8), grid((d.nx + 31) / 32, (d.ny + 7) / 8);
+    size_t smem = sizeof(float4) * (size_t)d.n_views;
+    float sid_h = d.sid / d.h;
+    float k_u = d.sdd / d.pitch_u;
+    float k_w = d.h * d.sdd / d.pitch_u;
+    float w_par = d.h * d.h / d.pitch_u;
+    if (d.kind == CT_FANFLAT2D)
+        pixbp2d_kernel<true><<<grid, block, smem, s>>>(d.views, d.n_views, ypad, d.sino_ld,
+                                                        d.ndu, d.nx, d.ny, sid_h, k_u, k_w,
+                                                        w_par, x, stop);
+    else
+        pixbp2d_kernel<false><<<grid, block, smem, s>>>(d.views, d.n_views, ypad, d.sino_ld,
+                                                         d.ndu, d.nx, d.ny, sid_h, k_u, k_w,
+                                                         w_par, x, stop);
+    return cudaGetLastError();
+}
+
+}  // namespace ct

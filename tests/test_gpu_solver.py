@@ -1,0 +1,186 @@
+"""GPU hybrid AB-/BA-GMRES and its building blocks vs the FP64 oracle.
+
+Tolerances: the device small solve (FP64 in, FP64 out) matches the oracle to 1e-9; the
+Arnoldi step (FP32 data, FP32 accumulation, FP64 cross-block sums) to 1e-5; the iterate after
+k steps to 1e-4 relative of the FP64 oracle iterate on the same FP32-rounded data.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import proj as OP
+from oracle import solver as OS
+from tests._common import f32, gpu_geom, problem, rel, to_dev
+
+pytestmark = pytest.mark.gpu
+ITER_TOL = 1e-4
+
+
+def _torch():
+    import torch
+    return torch
+
+
+# ----------------------------------------------------------------------------- small solve
+def _hessenberg(k, seed, decay=-5):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.triu(rng.standard_normal((k + 1, k)), -1) * np.logspace(0, decay, k)[None, :]
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 30, 100, 160])
+@pytest.mark.parametrize("rule", ["none", "fixed", "gcv", "dp"])
+def test_projected_solve_matches_oracle(k, rule):
+    torch = _torch()
+    from paper_2602_17892_gb300 import ct_projected_solve, build
+    build.build()
+    H = _hessenberg(k, 1000 + k)
+    beta = 3.7
+    s, c, Vt = OS.projected_svd(H, beta)
+    lam_fixed = 0.01
+    lo = math.sqrt(OS.residual_sq(s[0] * 1e-8, s, c))
+    hi = math.sqrt(OS.residual_sq(s[0], s, c))
+    target = 0.3 * lo + 0.7 * hi
+    if rule == "none":
+        y_o, r_o = OS.givens_gmres_y(H, beta)
+        lam_o = 0.0
+    else:
+        lam_o = OS.choose_lambda(rule, s, c, lam_fixed, target)
+        y_o = OS.tikhonov_y(lam_o, s, c, Vt)
+        r_o = math.sqrt(OS.residual_sq(lam_o, s, c))
+    Hd = torch.from_numpy(np.asfortranarray(H).reshape(-1, order="F").copy()).cuda()
+    y = torch.zeros(k, dtype=torch.float64, device="cuda")
+    lam = torch.zeros(1, dtype=torch.float64, device="cuda")
+    res = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ct_projected_solve(Hd, k + 1, k, beta, rule, lam_fixed, target, y, lam, res)
+    torch.cuda.synchronize()
+    assert abs(lam.item() - lam_o) <= 1e-9 * max(lam_o, 1e-300) + (0 if lam_o else 0)
+    assert abs(res.item() - r_o) <= 1e-9 * r_o + 1e-14
+    assert rel(y.cpu().numpy(), y_o) <= 1e-8
+
+
+# ----------------------------------------------------------------------------- Arnoldi step
+@pytest.mark.parametrize("L,k", [(4096, 0), (555_840, 7), (262_144, 40), (1_000, 3)])
+def test_arnoldi_step_matches_fp64_gram_schmidt(L, k):
+    torch = _torch()
+    from paper_2602_17892_gb300 import ct_arnoldi_step, build
+    build.build()
+    rng = np.random.Generator(np.random.PCG64(L + k))
+    Lp = (L + 3) // 4 * 4
+    Q, _ = np.linalg.qr(rng.standard_normal((L, k + 1)))
+    W = np.zeros((k + 2, Lp), np.float32)
+    W[: k + 1, :L] = Q.T
+    q = np.zeros(Lp, np.float32)
+    q[:L] = rng.standard_normal(L) + 3.0 * Q[:, 0]
+    Wd = torch.from_numpy(W.copy()).cuda()
+    qd = torch.from_numpy(q.copy()).cuda()
+    hd = torch.zeros(k + 2, dtype=torch.float64, device="cuda")
+    ct_arnoldi_step(Wd, Lp, Lp, k, qd, hd)
+    torch.cuda.synchronize()
+    W64 = W[: k + 1].astype(np.float64)
+    qq = q.astype(np.float64)
+    h = np.zeros(k + 2)
+    for _ in range(2):                      # FP64 MGS twice on the same FP32 inputs
+        for i in range(k + 1):
+            d = qq @ W64[i]
+            h[i] += d
+            qq -= d * W64[i]
+    h[k + 1] = np.linalg.norm(qq)
+    hg = hd.cpu().numpy()
+    assert rel(hg, h) <= 1e-5
+    wn = Wd[k + 1].cpu().numpy().astype(np.float64)
+    assert rel(wn, qq / h[k + 1]) <= 1e-4
+    assert abs(np.linalg.norm(wn) - 1.0) <= 1e-5
+    assert np.abs(W64 @ wn).max() <= 1e-5
+
+
+# ----------------------------------------------------------------------------- full solves
+def _gpu_solve(method, G, b, iters, rule, **kw):
+    torch = _torch()
+    from paper_2602_17892_gb300 import ab_gmres_hybrid, ba_gmres_hybrid
+    x = torch.zeros(G.n, dtype=torch.float32, device="cuda")
+    fn = ab_gmres_hybrid if method == "ab" else ba_gmres_hybrid
+    info = fn(G, to_dev(b), x, max_iters=iters, rule=rule, **kw)
+    torch.cuda.synchronize()
+    return x.cpu().numpy().astype(np.float64), info
+
+
+def _oracle(method, geom, b, iters, rule, **kw):
+    A, B = OP.operators(geom)
+    return OS.hybrid_gmres(method, A, B, b, iters, rule=rule, **kw)
+
+
+def test_small_parallel_ab_gcv_matches_oracle():
+    """64x64 ellipses, 90 parallel views x 95 bins, 1 % noise, hybrid AB-GMRES, 30 its, GCV."""
+    case = synth.small_parallel_case()
+    g = case["geom"]
+    x_true, b, e = problem(g, case["phantom_seed"], case["eta"], case["noise_seed"])
+    G = gpu_geom(g)
+    xg, info = _gpu_solve("ab", G, b, 30, "gcv")
+    ref = _oracle("ab", g, b, 30, "gcv")
+    assert info["status"] == "CT_OK" and info["iters_done"] == 30
+    assert rel(xg, ref["x"]) <= ITER_TOL
+    np.testing.assert_allclose(info["lambdas"], ref["lambdas"], rtol=1e-3)
+    np.testing.assert_allclose(info["resid"], ref["resid"], rtol=1e-4)
+    # the oracle's final lambda injected: isolates the Krylov path from the lambda choice
+    xf, _ = _gpu_solve("ab", G, b, 30, "fixed", lambda_fixed=ref["lambdas"][-1])
+    assert rel(xf, ref["x"]) <= ITER_TOL
+    assert OS.rre(xg, x_true) < 0.5
+
+
+@pytest.mark.parametrize("method", ["ab", "ba"])
+@pytest.mark.parametrize("rule", ["none", "fixed", "dp", "gcv"])
+def test_ragged_fan_solves_match_oracle(method, rule):
+    g = synth.fanflat2d(45, 60, 70, 150.0, 240.0, ny=38)
+    x_true, b, e = problem(g, 5, 0.02, 77)
+    noise = np.linalg.norm(e) if method == "ab" else np.linalg.norm(OP.back_pixel(g, e))
+    G = gpu_geom(g)
+    kw = dict(lambda_fixed=0.5, noise_norm=noise, tau=1.01)
+    xg, info = _gpu_solve(method, G, b, 20, rule, **kw)
+    ref = _oracle(method, g, b, 20, rule, lam_fixed=0.5, dp_target=1.01 * noise)
+    assert rel(xg, ref["x"]) <= ITER_TOL
+
+
+def test_zero_data_breaks_down_at_start():
+    g = synth.parallel2d(16, 10)
+    G = gpu_geom(g)
+    xg, info = _gpu_solve("ab", G, np.zeros(g.m), 5, "gcv")
+    assert info["iters_done"] == 0 and info["status"] == "CT_BREAKDOWN"
+    assert np.all(xg == 0)
+
+
+def test_initial_guess_and_single_iteration():
+    g = synth.parallel2d(24, 20)
+    x_true, b, e = problem(g, 2, 0.01, 5)
+    G = gpu_geom(g)
+    torch = _torch()
+    from paper_2602_17892_gb300 import ab_gmres_hybrid, ba_gmres_hybrid
+    u0 = f32(0.01 * synth.standard_normal(g.m, 4))
+    x0 = f32(0.1 * synth.standard_normal(g.n, 6))
+    A, B = OP.operators(g)
+    for K in (1, 6):
+        x = torch.zeros(g.n, dtype=torch.float32, device="cuda")
+        ab_gmres_hybrid(G, to_dev(b), x, u0=to_dev(u0), max_iters=K, rule="fixed", lambda_fixed=0.2)
+        ref = OS.hybrid_gmres("ab", A, B, b, K, rule="fixed", lam_fixed=0.2, x0=B(u0))
+        assert rel(x.cpu().numpy(), ref["x"]) <= ITER_TOL
+        x = torch.zeros(g.n, dtype=torch.float32, device="cuda")
+        ba_gmres_hybrid(G, to_dev(b), x, x0=to_dev(x0), max_iters=K, rule="fixed", lambda_fixed=0.2)
+        ref = OS.hybrid_gmres("ba", A, B, b, K, rule="fixed", lam_fixed=0.2, x0=x0)
+        assert rel(x.cpu().numpy(), ref["x"]) <= ITER_TOL
+
+
+@pytest.mark.parametrize("method", ["ab", "ba"])
+def test_fan512_dp_full_size_matches_oracle(method):
+    """The 512^2 fan workload (720 x 768, 2 % noise), 100 iterations, discrepancy principle,
+    in the launch configuration the benchmark times."""
+    case = synth.fan512_case()
+    g = case["geom"]
+    x_true, b, e = problem(g, case["phantom_seed"], case["eta"], case["noise_seed"])
+    noise = np.linalg.norm(e) if method == "ab" else np.linalg.norm(OP.back_pixel(g, e))
+    G = gpu_geom(g)
+    xg, info = _gpu_solve(method, G, b, 100, "dp", noise_norm=noise, tau=1.01)
+    ref = _oracle(method, g, b, 100, "dp", dp_target=1.01 * noise)
+    assert info["iters_done"] == 100
+    assert rel(xg, ref["x"]) <= ITER_TOL
+    np.testing.assert_allclose(info["resid"], ref["resid"], rtol=1e-3)
