@@ -101,8 +101,12 @@ struct PhaseScope {
 using namespace ct;
 
 // ============================================================================ workspace
+constexpr int kSideStreams = 8;   // concurrent small solves (independent of the main chain)
+
 struct Workspace {
     int method = -1, K = 0, basis = 0;
+    cudaStream_t side[kSideStreams] = {};
+    cudaEvent_t fork[kSideStreams] = {}, join[kSideStreams] = {};
     int64_t L = 0;          // basis row length in floats (multiple of 4, zero tail)
     float *W = nullptr;     // (K+1) rows
     float *q = nullptr;     // L
@@ -121,6 +125,11 @@ static void ws_free(Workspace *w)
     cudaFree(w->W); cudaFree(w->q); cudaFree(w->img); cudaFree(w->sino); cudaFree(w->vec);
     cudaFree(w->H); cudaFree(w->Y); cudaFree(w->lam); cudaFree(w->res); cudaFree(w->aux);
     cudaFree(w->partial); cudaFree(w->counter); cudaFree(w->stop);
+    for (int i = 0; i < kSideStreams; ++i) {
+        if (w->side[i]) cudaStreamDestroy(w->side[i]);
+        if (w->fork[i]) cudaEventDestroy(w->fork[i]);
+        if (w->join[i]) cudaEventDestroy(w->join[i]);
+    }
     delete w;
 }
 
@@ -162,6 +171,13 @@ static ct_status ws_get(ct_geom *g, int method, int K, int basis, Workspace **ou
     if (e == cudaSuccess) e = dalloc(&w->partial, (size_t)kMaxBlocks * (K + 2));
     if (e == cudaSuccess) e = dalloc(&w->counter, 4);
     if (e == cudaSuccess) e = dalloc(&w->stop, 4);
+    int prio_lo = 0, prio_hi = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    for (int i = 0; i < kSideStreams && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithPriority(&w->side[i], cudaStreamNonBlocking, prio_hi);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->fork[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->join[i], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         ws_free(w);
         set_error(std::string("workspace allocation: ") + cudaGetErrorString(e));
@@ -435,6 +451,9 @@ static ct_status finish(Workspace *w, const ct_hybrid_opts *o, ct_hybrid_info *i
     return CT_OK;
 }
 
+// The hybrid step of step `step` depends only on H's first `step` columns, and nothing in the
+// Arnoldi chain depends on it, so it runs on one of the side streams, overlapped with the
+// projectors of the following steps (Alg. 1/2 line 12-13).
 static ct_status run_small_solve(Workspace *w, const ct_hybrid_opts *o, int step, cudaStream_t s,
                                  double dp_target)
 {
@@ -445,8 +464,23 @@ static ct_status run_small_solve(Workspace *w, const ct_hybrid_opts *o, int step
     p.lambda_out = w->lam + (step - 1);
     p.resid_out = w->res + (step - 1);
     p.stop = w->stop;
-    CT_PHASE(CT_PH_SMALL, 1, s);
-    CT_CUDA(launch_small_solve(p, s));
+    p.kmax = o->max_iters;
+    p.always_y = 0;
+    const int j = (step - 1) % kSideStreams;
+    CT_CUDA(cudaEventRecord(w->fork[j], s));
+    CT_CUDA(cudaStreamWaitEvent(w->side[j], w->fork[j], 0));
+    CT_PHASE(CT_PH_SMALL, 1, w->side[j]);
+    CT_CUDA(launch_small_solve(p, w->side[j]));
+    return CT_OK;
+}
+
+// the main stream waits for every side stream before it uses the small-solve results
+static ct_status join_side(Workspace *w, cudaStream_t s)
+{
+    for (int j = 0; j < kSideStreams; ++j) {
+        CT_CUDA(cudaEventRecord(w->join[j], w->side[j]));
+        CT_CUDA(cudaStreamWaitEvent(s, w->join[j], 0));
+    }
     return CT_OK;
 }
 
@@ -505,6 +539,7 @@ extern "C" ct_status ab_gmres_hybrid(ct_geom *g, const float *b_dev, const float
         }
         if ((st = run_small_solve(w, o, step, s, dp_target)) != CT_OK) return st;   // 12-13
     }
+    if ((st = join_side(w, s)) != CT_OK) return st;
     // line 13 at k = K: x = x0 + B W y = B (u0 + W y)
     {
         CT_PHASE(CT_PH_OTHER, u0_dev ? 2 : 1, s);
@@ -576,6 +611,7 @@ extern "C" ct_status ba_gmres_hybrid(ct_geom *g, const float *b_dev, const float
         }
         if ((st = run_small_solve(w, o, step, s, dp_target)) != CT_OK) return st;
     }
+    if ((st = join_side(w, s)) != CT_OK) return st;
     // line 13: x = x0 + W y
     {
         CT_PHASE(CT_PH_OTHER, 1, s);
@@ -631,6 +667,7 @@ extern "C" ct_status ct_projected_solve(const double *H_dev, int ldh, int k, dou
     p.H = H_dev; p.ldh = ldh; p.k = k; p.beta = beta; p.betap = nullptr;
     p.rule = rule; p.lambda_fixed = lambda_fixed; p.dp_target = dp_target;
     p.y = y_dev; p.lambda_out = lambda_dev; p.resid_out = resid_dev; p.stop = nullptr;
+    p.kmax = k; p.always_y = 1;
     CT_CUDA(launch_small_solve(p, (cudaStream_t)stream));
     return CT_OK;
 }

@@ -105,6 +105,8 @@ struct SmallSolveParams {
     int rule; double lambda_fixed; double dp_target;
     double *y; double *lambda_out; double *resid_out;
     const int *stop;  // solver stop word (may be null)
+    int kmax;         // last step of the solve: y is formed there (or at a breakdown step)
+    int always_y;     // form y at every k
 };
 cudaError_t launch_small_solve(const SmallSolveParams &p, cudaStream_t s);
 size_t small_solve_smem_bytes(int k);

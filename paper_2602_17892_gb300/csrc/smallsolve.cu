@@ -3,14 +3,29 @@
 //     y = argmin || [H_k; lambda I] y - beta [e1; 0] ||.
 //
 // lambda = 0 (plain AB/BA-GMRES, Eq. (proj_pbm)): Givens QR of H_k and back substitution.
-// lambda > 0: Householder bidiagonalisation P^T H_k Q = [Bd; 0] (Bd upper bidiagonal),
-// g = P^T beta e1; implicit-shift Golub-Kahan QR on Bd gives the singular values sigma_i and,
-// through the left rotations applied to g, the coordinates c = U^T beta e1 that GCV (Sec. 3.1)
-// and the discrepancy principle (Sec. 3.2) need:
+//
+// lambda > 0.  GCV (Sec. 3.1) and the discrepancy principle (Sec. 3.2) need the singular values
+// sigma_i of H_k and c_i^2, c = U^T beta e1:
 //     rho^2(lambda) = sum_i (lambda^2 c_i / (sigma_i^2 + lambda^2))^2 + c_{k+1}^2,
 //     trace(I - H H_lambda) = (k+1) - sum_i sigma_i^2 / (sigma_i^2 + lambda^2).
-// y follows from the bidiagonal Tikhonov problem min ||Bd z - g||^2 + lambda^2 ||z||^2,
-// eliminated with 2k Givens rotations (O(k)), and y = Q z (stored right reflectors).
+// GB300 executes FP64 at 1/64 of the FP32 rate, so a sequential FP64 bidiagonal QR (one thread,
+// O(k^2) dependent rotations) costs milliseconds.  The fast path keeps every step parallel:
+//  1. Givens QR of H_k (FP64): H_k = G [R; 0], g = G^T beta e1; c_{k+1} = g_{k+1}.
+//  2. Householder reduction of R to LOWER bidiagonal L = P^T R Q with P^T g = beta0 e1 (the
+//     first left reflector maps g to a multiple of e1, later left reflectors never touch row 1).
+//     Then c_i = beta0 u_i(1): only first components of the left singular vectors are needed.
+//  3. sigma_i: eigenvalues of the Golub-Kahan tridiagonal T of L (zero diagonal, off-diagonals
+//     alpha_1, beta_2, alpha_2, ...): FP32 bisection (one thread per sigma_i, Sturm counts of
+//     the LDL^T recurrence) gives a bracket, FP64 safeguarded Newton on det(theta I - T)
+//     refines it.
+//  4. c_i^2 = 2 beta0^2 z_i(1)^2 with z_i(1)^2 = det(sigma_i I - T_{2:n}) / p'(sigma_i), the
+//     first-component formula of a symmetric tridiagonal's eigenvectors.
+//  5. Self-check: sum_i c_i^2 must equal beta0^2 (U orthogonal).  If it does not (clustered or
+//     zero singular values), the kernel recomputes sigma and c with the exact sequential path:
+//     Householder upper bidiagonalisation of H_k and implicit-shift Golub-Kahan QR.
+// y is formed only where it is needed (the last step, or a breakdown step): the bidiagonal
+// Tikhonov problem min ||Bd z - g||^2 + lambda^2 ||z||^2 is eliminated with O(k) Givens
+// rotations and y = Q z applies the stored right reflectors.
 //
 // Parameter readings shared with the FP64 CPU oracle: GCV is evaluated on 256 log-spaced
 // lambda in [sigma_1 1e-8, sigma_1], the first grid minimum is refined by 40 golden-section
@@ -59,8 +74,8 @@ __device__ __forceinline__ void givens(double a, double b, double &c, double &s,
     s = b / r;
 }
 
-// Householder vector (LAPACK dlarfg convention): returns beta, tau; x scaled in place so that
-// H = I - tau [1; x][1; x]^T maps [alpha; x] to [beta; 0].
+// Householder vector (LAPACK dlarfg convention): H = I - tau [1; v][1; v]^T maps [alpha; x]
+// to [beta; 0] with v = x * scale.
 __device__ void make_reflector(double alpha, double xnorm2, double &beta, double &tau, double &scale)
 {
     if (xnorm2 == 0.0) { beta = alpha; tau = 0.0; scale = 0.0; return; }
@@ -87,7 +102,6 @@ __device__ int bidiag_svd_serial(double *d, double *e, double *g, int n)
         if (q == 0) break;
         int p = q - 1;
         while (p > 0 && e[p - 1] != 0.0) --p;
-        // a zero on the diagonal of the block: split with rotations
         int zi = -1;
         for (int i = p; i <= q; ++i)
             if (fabs(d[i]) <= eps * bnorm) { zi = i; break; }
@@ -118,7 +132,6 @@ __device__ int bidiag_svd_serial(double *d, double *e, double *g, int n)
             ++iter;
             continue;
         }
-        // Wilkinson shift from the trailing 2x2 of Bd^T Bd
         double t11 = d[q - 1] * d[q - 1] + (q - 1 > p ? e[q - 2] * e[q - 2] : 0.0);
         double t12 = d[q - 1] * e[q - 1];
         double t22 = d[q] * d[q] + e[q - 1] * e[q - 1];
@@ -149,19 +162,45 @@ __device__ int bidiag_svd_serial(double *d, double *e, double *g, int n)
     return iter >= max_iter ? -1 : 0;
 }
 
+// Characteristic polynomial det(theta I - T) of the zero-diagonal tridiagonal with squared
+// off-diagonals t2[0..n-2] (rows first..n-1), its derivative, with power-of-two rescaling.
+// Returns p and dp scaled by the same 2^(-e) (e accumulated in *ex).
+__device__ void charpoly(const double *t2, int first, int n, double th, double &p, double &dp, int &ex)
+{
+    double pm2 = 1.0, pm1 = th, qm2 = 0.0, qm1 = 1.0;   // size-1 block: det = theta, d/dth = 1
+    int e = 0;
+    for (int j = first + 1; j < n; ++j) {
+        const double a = t2[j - 1];
+        double pj = th * pm1 - a * pm2;
+        double qj = pm1 + th * qm1 - a * qm2;
+        pm2 = pm1; pm1 = pj; qm2 = qm1; qm1 = qj;
+        double mag = fabs(pj) + fabs(qj);
+        if (mag > 0x1p+400 || (mag < 0x1p-400 && mag != 0.0)) {
+            int sh = (mag > 0x1p+400) ? -400 : 400;
+            pm1 = ldexp(pm1, sh); pm2 = ldexp(pm2, sh);
+            qm1 = ldexp(qm1, sh); qm2 = ldexp(qm2, sh);
+            e -= sh;
+        }
+    }
+    p = pm1; dp = qm1; ex = e;
+}
+
 size_t small_solve_smem_bytes(int k)
 {
-    size_t nd = (size_t)(k + 1) * k + 12 * (size_t)(k + 1) + kGcvGrid + 64;
+    size_t nd = (size_t)(k + 1) * k + 16 * (size_t)(k + 1) + kGcvGrid + 64;
     return nd * sizeof(double);
 }
 
 __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParams P)
 {
     const int k = P.k;
+    int stop_now = 0;
     if (P.stop) {
         int st = P.stop[0];
         if (st < 0 || (st > 0 && k > st)) return;
+        stop_now = (st == k);
     }
+    const bool need_y = P.always_y || k == P.kmax || stop_now;
     extern __shared__ double sd[];
     const int lda = k + 1;
     double *A = sd;                       // (k+1) x k, column-major
@@ -175,23 +214,27 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
     double *sig = gsv + (k + 1);
     double *cv = sig + (k + 1);           // k+1
     double *z = cv + (k + 1);
-    double *rot = z + (k + 1);            // 2(k+1): Givens c, s
-    double *red = rot + 2 * (k + 1);      // kGcvGrid
-    double *misc = red + kGcvGrid;        // 64
+    double *rot = z + (k + 1);            // 2(k+1)
+    double *t2 = rot + 2 * (k + 1);       // 2(k+1): squared tridiagonal off-diagonals
+    float *lo32 = (float *)(t2 + 2 * (k + 1));   // k floats
+    float *hi32 = lo32 + (k + 1);                // k floats
+    float *t2f = hi32 + (k + 1);                 // 2(k+1) floats
+    double *red = (double *)(t2f + 2 * (k + 1)); // kGcvGrid
+    double *misc = red + kGcvGrid;               // 64
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = kSSThreads / 32;
     const double beta = P.betap ? *P.betap : P.beta;
 
-    for (int t = tid; t < lda * k; t += kSSThreads) {
-        int c = t / lda, r = t - c * lda;
-        A[t] = P.H[(size_t)c * P.ldh + r];
-    }
-    for (int t = tid; t <= k; t += kSSThreads) g[t] = (t == 0) ? beta : 0.0;
-    __syncthreads();
-
-    double lam = 0.0, rho2 = 0.0;
-    if (P.rule == CT_LAMBDA_NONE) {
-        // ---------------- Givens QR of H_k, back substitution (Eq. (proj_pbm))
+    auto load_H = [&]() {
+        for (int t = tid; t < lda * k; t += kSSThreads) {
+            int c = t / lda, r = t - c * lda;
+            A[t] = P.H[(size_t)c * P.ldh + r];
+        }
+        for (int t = tid; t <= k; t += kSSThreads) g[t] = (t == 0) ? beta : 0.0;
+        __syncthreads();
+    };
+    // Givens QR of the Hessenberg matrix in A, rotations applied to g (columns in parallel)
+    auto givens_qr = [&]() {
         for (int j = 0; j < k; ++j) {
             if (tid == 0) {
                 double c, s, r;
@@ -210,7 +253,14 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
             }
             __syncthreads();
         }
-        for (int i = k - 1; i >= 0; --i) {   // column-oriented back substitution
+    };
+
+    load_H();
+    double lam = 0.0;
+    if (P.rule == CT_LAMBDA_NONE) {
+        // ---------------- Eq. (proj_pbm): Givens QR and back substitution
+        givens_qr();
+        for (int i = k - 1; i >= 0; --i) {
             if (tid == 0) {
                 double rii = A[i * lda + i];
                 z[i] = (rii != 0.0) ? g[i] / rii : 0.0;
@@ -222,19 +272,51 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
         }
         for (int i = tid; i < k; i += kSSThreads) P.y[i] = z[i];
         if (tid == 0) {
-            rho2 = g[k] * g[k];
             *P.lambda_out = 0.0;
             *P.resid_out = fabs(g[k]);
         }
         return;
     }
 
-    // ---------------- Householder bidiagonalisation of H_k ((k+1) x k)
+    // ================================================================ fast path
+    givens_qr();                                   // R in rows 0..k-1 of A, g (k+1)
+    // first left reflector: g[0..k-1] -> beta0 e1, applied to R
+    if (warp == 0) {
+        double s2 = 0.0;
+        for (int i = 1 + lane; i < k; i += 32) s2 += g[i] * g[i];
+        s2 = warp_sum_d(s2);
+        if (lane == 0) {
+            double bt, tau, sc;
+            make_reflector(g[0], s2, bt, tau, sc);
+            misc[0] = bt; misc[1] = tau; misc[2] = sc;
+            misc[3] = g[k];                      // c_{k+1}
+        }
+    }
+    __syncthreads();
+    {
+        const double tau = misc[1], sc = misc[2];
+        if (tau != 0.0) {
+            for (int i = 1 + tid; i < k; i += kSSThreads) g[i] *= sc;   // reflector vector
+            __syncthreads();
+            for (int l = warp; l < k; l += nwarps) {
+                double *col = A + (size_t)l * lda;
+                const double c0 = col[0];
+                double w = 0.0;
+                for (int i = 1 + lane; i < k; i += 32) w += g[i] * col[i];
+                w = (warp_sum_d(w) + c0) * tau;
+                __syncwarp();
+                if (lane == 0) col[0] -= w;
+                for (int i = 1 + lane; i < k; i += 32) col[i] -= w * g[i];
+            }
+        }
+    }
+    __syncthreads();
+    const double beta0 = misc[0], ck1 = misc[3];
+    // lower bidiagonalisation: right reflector on row j (cols j..k-1), left on col j (rows j+1..)
     for (int j = 0; j < k; ++j) {
-        // left reflector on column j, rows j..k
         if (warp == 0) {
             double s2 = 0.0;
-            for (int i = j + 1 + lane; i <= k; i += 32) s2 += A[j * lda + i] * A[j * lda + i];
+            for (int l = j + 1 + lane; l < k; l += 32) s2 += A[l * lda + j] * A[l * lda + j];
             s2 = warp_sum_d(s2);
             if (lane == 0) {
                 double bt, tau, sc;
@@ -245,73 +327,230 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
         __syncthreads();
         {
             const double bt = misc[0], tau = misc[1], sc = misc[2];
-            for (int i = j + 1 + tid; i <= k; i += kSSThreads) A[j * lda + i] *= sc;
+            for (int l = j + 1 + tid; l < k; l += kSSThreads) A[l * lda + j] *= sc;
             __syncthreads();
-            if (tid == 0) { A[j * lda + j] = bt; d[j] = bt; }
-            // apply to columns j+1..k-1 and to g (index k as an extra column)
+            if (tid == 0) { A[j * lda + j] = bt; d[j] = bt; tauR[j] = tau; }
             if (tau != 0.0) {
-                for (int l = j + 1 + warp; l <= k; l += nwarps) {
-                    double *col = (l < k) ? A + (size_t)l * lda : g;
-                    const double cj = col[j];
+                for (int i = j + 1 + warp; i < k; i += nwarps) {
+                    const double aij = A[j * lda + i];
                     double w = 0.0;
-                    for (int i = j + 1 + lane; i <= k; i += 32) w += A[j * lda + i] * col[i];
-                    w = warp_sum_d(w) + cj;
-                    w *= tau;
-                    if (lane == 0) col[j] -= w;
-                    for (int i = j + 1 + lane; i <= k; i += 32) col[i] -= w * A[j * lda + i];
+                    for (int l = j + 1 + lane; l < k; l += 32) w += A[l * lda + j] * A[l * lda + i];
+                    w = (warp_sum_d(w) + aij) * tau;
+                    __syncwarp();
+                    if (lane == 0) A[j * lda + i] -= w;
+                    for (int l = j + 1 + lane; l < k; l += 32) A[l * lda + i] -= w * A[l * lda + j];
                 }
             }
         }
         __syncthreads();
-        // right reflector on row j, columns j+1..k-1
-        if (j < k - 1) {
+        if (j + 1 < k) {
             if (warp == 0) {
                 double s2 = 0.0;
-                for (int l = j + 2 + lane; l < k; l += 32) s2 += A[l * lda + j] * A[l * lda + j];
+                for (int i = j + 2 + lane; i < k; i += 32) s2 += A[j * lda + i] * A[j * lda + i];
                 s2 = warp_sum_d(s2);
                 if (lane == 0) {
                     double bt, tau, sc;
-                    make_reflector(A[(j + 1) * lda + j], s2, bt, tau, sc);
+                    make_reflector(A[j * lda + j + 1], s2, bt, tau, sc);
                     misc[0] = bt; misc[1] = tau; misc[2] = sc;
                 }
             }
             __syncthreads();
             const double bt = misc[0], tau = misc[1], sc = misc[2];
-            for (int l = j + 2 + tid; l < k; l += kSSThreads) A[l * lda + j] *= sc;
+            for (int i = j + 2 + tid; i < k; i += kSSThreads) A[j * lda + i] *= sc;
             __syncthreads();
-            if (tid == 0) { A[(j + 1) * lda + j] = bt; e[j] = bt; tauR[j] = tau; }
+            if (tid == 0) { A[j * lda + j + 1] = bt; e[j] = bt; }
             if (tau != 0.0) {
-                for (int i = j + 1 + warp; i <= k; i += nwarps) {
-                    const double ai = A[(j + 1) * lda + i];
+                for (int l = j + 1 + warp; l < k; l += nwarps) {
+                    double *col = A + (size_t)l * lda;
+                    const double c0 = col[j + 1];
                     double w = 0.0;
-                    for (int l = j + 2 + lane; l < k; l += 32) w += A[l * lda + j] * A[l * lda + i];
-                    w = warp_sum_d(w) + ai;
-                    w *= tau;
-                    if (lane == 0) A[(j + 1) * lda + i] -= w;
-                    for (int l = j + 2 + lane; l < k; l += 32) A[l * lda + i] -= w * A[l * lda + j];
+                    for (int i = j + 2 + lane; i < k; i += 32) w += A[j * lda + i] * col[i];
+                    w = (warp_sum_d(w) + c0) * tau;
+                    __syncwarp();
+                    if (lane == 0) col[j + 1] -= w;
+                    for (int i = j + 2 + lane; i < k; i += 32) col[i] -= w * A[j * lda + i];
                 }
             }
             __syncthreads();
         }
     }
-    for (int i = tid; i <= k; i += kSSThreads) {
-        if (i < k) { dsv[i] = d[i]; esv[i] = (i < k - 1) ? e[i] : 0.0; }
-        gsv[i] = g[i];
+    // L: diag d[0..k-1] (alpha), subdiag e[0..k-2] (beta_{j+1} = L[j+1][j])
+    // Golub-Kahan tridiagonal T (n = 2k) off-diagonals alpha_0, beta_1, alpha_1, ..., scaled
+    const int n = 2 * k;
+    if (warp == 0) {
+        double mx = 0.0;
+        for (int i = lane; i < k; i += 32) {
+            mx = fmax(mx, fabs(d[i]));
+            if (i < k - 1) mx = fmax(mx, fabs(e[i]));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) misc[4] = mx;
     }
     __syncthreads();
-
-    // ---------------- singular values and c = U^T g (one thread)
-    if (tid == 0) {
-        int st = bidiag_svd_serial(d, e, g, k);
-        double s1 = 0.0;
-        for (int i = 0; i < k; ++i) {
-            sig[i] = fabs(d[i]);
-            cv[i] = g[i];
-            s1 = fmax(s1, sig[i]);
+    const double tscale = misc[4];
+    const double inv_ts = (tscale > 0.0) ? 1.0 / tscale : 0.0;
+    for (int j = tid; j < n - 1; j += kSSThreads) {
+        double t = ((j & 1) == 0 ? d[j >> 1] : e[j >> 1]) * inv_ts;
+        t2[j] = t * t;
+        t2f[j] = (float)(t * t);
+    }
+    if (tid == 0) misc[5] = 0.0;
+    __syncthreads();
+    // sigma_i (i-th largest), one thread each: FP32 bisection, then FP64 safeguarded Newton
+    for (int i = tid; i < k; i += kSSThreads) {
+        float lo = 0.f, hi = 2.f;
+        const int target = k - i;               // #{sigma < x} >= target  <=>  sigma_i < x
+        for (int it = 0; it < 140 && (hi - lo) > 2e-6f * hi; ++it) {
+            float x = 0.5f * (lo + hi);
+            int cnt = 0;
+            float dd = -x;
+            cnt += (dd < 0.f);
+            for (int j = 1; j < n; ++j) {
+                float dprev = (fabsf(dd) < 1e-30f) ? -1e-30f : dd;
+                dd = -x - __fdividef(t2f[j - 1], dprev);
+                cnt += (dd < 0.f);
+            }
+            if (cnt - k >= target) hi = x; else lo = x;
         }
-        cv[k] = g[k];
-        misc[8] = s1;
-        misc[9] = (double)st;
+        lo32[i] = lo;
+        hi32[i] = hi;
+        double blo = (double)lo * (1.0 - 1e-4), bhi = (double)hi * (1.0 + 1e-4);
+        double th = 0.5 * ((double)lo + (double)hi), th_eval = th;
+        double p = 0.0, dp = 0.0;
+        int ex = 0;
+        // just below sigma_i, i+1 eigenvalues of T lie above theta: det(theta I - T) has sign (-1)^(i+1)
+        const bool neg_lo = (i % 2 == 0);
+        for (int it = 0; it < 12; ++it) {
+            charpoly(t2, 0, n, th, p, dp, ex);
+            th_eval = th;
+            if (p == 0.0) break;
+            if ((p < 0.0) == neg_lo) blo = th; else bhi = th;
+            const double delta = p / dp;
+            if (fabs(delta) <= 2e-16 * fabs(th)) break;          // converged at th_eval
+            double nt = th - delta;
+            if (!(nt > blo && nt < bhi)) nt = 0.5 * (blo + bhi);   // safeguard: bisect
+            th = nt;
+            if (bhi - blo <= 4e-16 * bhi) break;
+        }
+        // first component of the eigenvector: z1^2 = det(th I - T_{2:n}) / p'(th), both at the
+        // last evaluation point (within a rounding error of the root)
+        int ex2;
+        double p2, dp2;
+        charpoly(t2, 1, n, th_eval, p2, dp2, ex2);
+        double z1sq = (dp != 0.0) ? ldexp(p2 / dp, ex2 - ex) : -1.0;
+        sig[i] = th * tscale;
+        double c2 = 2.0 * beta0 * beta0 * z1sq;
+        cv[i] = (c2 >= 0.0 && isfinite(c2)) ? sqrt(c2) : -1.0;
+    }
+    if (tid == 0) cv[k] = fabs(ck1);
+    __syncthreads();
+    // self-check: sum c_i^2 = beta0^2 and the sigma are distinct and ordered
+    if (warp == 0) {
+        double s = 0.0;
+        int bad = 0;
+        for (int i = lane; i < k; i += 32) {
+            if (cv[i] < 0.0 || !isfinite(sig[i])) bad = 1;
+            else s += cv[i] * cv[i];
+            if (i + 1 < k && !(sig[i] > sig[i + 1] * (1.0 + 1e-12))) bad = 1;
+        }
+        s = warp_sum_d(s);
+        bad = __any_sync(0xffffffffu, bad);
+        if (lane == 0) {
+            double ref = beta0 * beta0;
+            misc[6] = (bad || !(fabs(s - ref) <= 1e-10 * ref)) ? 1.0 : 0.0;
+            misc[8] = sig[0];
+        }
+    }
+    __syncthreads();
+    const bool fast = misc[6] == 0.0;
+    // fast-path y needs (d, e, beta0 e1) of the lower bidiagonal and reflectors on coords j..
+    if (fast && need_y && tid == 0) {
+        for (int i = 0; i < k; ++i) { dsv[i] = d[i]; esv[i] = (i < k - 1) ? e[i] : 0.0; gsv[i] = 0.0; }
+        gsv[0] = beta0;
+    }
+
+    if (!fast) {
+        // ================================================================ exact sequential path
+        __syncthreads();
+        load_H();
+        for (int j = 0; j < k; ++j) {
+            if (warp == 0) {
+                double s2 = 0.0;
+                for (int i = j + 1 + lane; i <= k; i += 32) s2 += A[j * lda + i] * A[j * lda + i];
+                s2 = warp_sum_d(s2);
+                if (lane == 0) {
+                    double bt, tau, sc;
+                    make_reflector(A[j * lda + j], s2, bt, tau, sc);
+                    misc[0] = bt; misc[1] = tau; misc[2] = sc;
+                }
+            }
+            __syncthreads();
+            {
+                const double bt = misc[0], tau = misc[1], sc = misc[2];
+                for (int i = j + 1 + tid; i <= k; i += kSSThreads) A[j * lda + i] *= sc;
+                __syncthreads();
+                if (tid == 0) { A[j * lda + j] = bt; d[j] = bt; }
+                if (tau != 0.0) {
+                    for (int l = j + 1 + warp; l <= k; l += nwarps) {
+                        double *col = (l < k) ? A + (size_t)l * lda : g;
+                        const double cj = col[j];
+                        double w = 0.0;
+                        for (int i = j + 1 + lane; i <= k; i += 32) w += A[j * lda + i] * col[i];
+                        w = (warp_sum_d(w) + cj) * tau;
+                        __syncwarp();
+                        if (lane == 0) col[j] -= w;
+                        for (int i = j + 1 + lane; i <= k; i += 32) col[i] -= w * A[j * lda + i];
+                    }
+                }
+            }
+            __syncthreads();
+            if (j < k - 1) {
+                if (warp == 0) {
+                    double s2 = 0.0;
+                    for (int l = j + 2 + lane; l < k; l += 32) s2 += A[l * lda + j] * A[l * lda + j];
+                    s2 = warp_sum_d(s2);
+                    if (lane == 0) {
+                        double bt, tau, sc;
+                        make_reflector(A[(j + 1) * lda + j], s2, bt, tau, sc);
+                        misc[0] = bt; misc[1] = tau; misc[2] = sc;
+                    }
+                }
+                __syncthreads();
+                const double bt = misc[0], tau = misc[1], sc = misc[2];
+                for (int l = j + 2 + tid; l < k; l += kSSThreads) A[l * lda + j] *= sc;
+                __syncthreads();
+                if (tid == 0) { A[(j + 1) * lda + j] = bt; e[j] = bt; tauR[j] = tau; }
+                if (tau != 0.0) {
+                    for (int i = j + 1 + warp; i <= k; i += nwarps) {
+                        const double ai = A[(j + 1) * lda + i];
+                        double w = 0.0;
+                        for (int l = j + 2 + lane; l < k; l += 32) w += A[l * lda + j] * A[l * lda + i];
+                        w = (warp_sum_d(w) + ai) * tau;
+                        __syncwarp();
+                        if (lane == 0) A[(j + 1) * lda + i] -= w;
+                        for (int l = j + 2 + lane; l < k; l += 32) A[l * lda + i] -= w * A[l * lda + j];
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int i = tid; i <= k; i += kSSThreads) {
+            if (i < k) { dsv[i] = d[i]; esv[i] = (i < k - 1) ? e[i] : 0.0; }
+            gsv[i] = g[i];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            bidiag_svd_serial(d, e, g, k);
+            double s1 = 0.0;
+            for (int i = 0; i < k; ++i) {
+                sig[i] = fabs(d[i]);
+                cv[i] = g[i];
+                s1 = fmax(s1, sig[i]);
+            }
+            cv[k] = g[k];
+            misc[8] = s1;
+        }
     }
     __syncthreads();
     const double s1 = misc[8];
@@ -319,20 +558,19 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
     // ---------------- lambda
     if (P.rule == CT_LAMBDA_FIXED) {
         lam = P.lambda_fixed;
-    } else if (s1 == 0.0) {
+    } else if (!(s1 > 0.0)) {
         lam = 0.0;
     } else if (P.rule == CT_LAMBDA_GCV) {
-        // grid: lambda_t = s1 10^(-8 + 8 t / 255)
         for (int t = tid; t < kGcvGrid; t += kSSThreads) {
-            double expo = -8.0 + t * (8.0 / (kGcvGrid - 1));
-            if (t == kGcvGrid - 1) expo = 0.0;
+            double expo = (t == kGcvGrid - 1) ? 0.0 : -8.0 + t * (8.0 / (kGcvGrid - 1));
             double lt = s1 * pow(10.0, expo);
             double l2 = lt * lt, r = 0.0, tr = 0.0;
             for (int i = 0; i < k; ++i) {
                 double s2 = sig[i] * sig[i];
-                double f = l2 / (s2 + l2);
+                double inv = 1.0 / (s2 + l2);
+                double f = l2 * inv;
                 r += (f * cv[i]) * (f * cv[i]);
-                tr += s2 / (s2 + l2);
+                tr += s2 * inv;
             }
             r += cv[k] * cv[k];
             tr = (double)(k + 1) - tr;
@@ -357,10 +595,10 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
             const double invphi = 0.6180339887498949;
             for (int it = 0; it < 40; ++it) {
                 double x1 = b - invphi * (b - a), x2 = a + invphi * (b - a);
-                double r1, t1, r2, t2;
+                double r1, t1, r2, t2_;
                 eval_lambda_warp(exp(x1), sig, cv, k, r1, t1);
-                eval_lambda_warp(exp(x2), sig, cv, k, r2, t2);
-                if (r1 / (t1 * t1) <= r2 / (t2 * t2)) b = x2; else a = x1;
+                eval_lambda_warp(exp(x2), sig, cv, k, r2, t2_);
+                if (r1 / (t1 * t1) <= r2 / (t2_ * t2_)) b = x2; else a = x1;
             }
             double lr = exp(0.5 * (a + b)), rr, tt;
             eval_lambda_warp(lr, sig, cv, k, rr, tt);
@@ -399,55 +637,77 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
         lam = misc[10];
     }
 
-    // ---------------- projected residual and y
+    // ---------------- projected residual
     if (warp == 0) {
         double r, t;
         eval_lambda_warp(lam, sig, cv, k, r, t);
         if (lane == 0) misc[11] = r;
     }
-    if (tid == 0) {
-        // Elden: eliminate the lambda I block of [Bd; lambda I] with 2k Givens rotations
-        double mu = lam, rr = 0.0;   // current lambda-row entry and its right-hand side
-        for (int i = 0; i < k; ++i) {
-            double a = dsv[i], b = (i < k - 1) ? esv[i] : 0.0, gi = gsv[i];
-            double c, s, r;
-            givens(a, mu, c, s, r);
-            dsv[i] = r;                 // new diagonal
-            esv[i] = c * b;             // new superdiagonal
-            z[i] = c * gi + s * rr;     // new right-hand side
-            double f = -s * b;          // fill in the lambda row at column i+1
-            double t = -s * gi + c * rr;
-            if (i < k - 1) {
-                double c2, s2, r2;
-                givens(lam, f, c2, s2, r2);
-                mu = r2;
-                rr = s2 * t;
+    if (need_y) {
+        if (tid == 0) {
+            if (fast) {
+                // lower -> upper bidiagonal by left rotations of rows (j, j+1), rhs beta0 e1
+                double dj = dsv[0];
+                for (int j = 0; j < k - 1; ++j) {
+                    double c, s, r;
+                    givens(dj, esv[j], c, s, r);          // zero beta_{j+1} at (j+1, j)
+                    double ajp = dsv[j + 1];
+                    dsv[j] = r;
+                    double ej = s * ajp;
+                    dj = c * ajp;
+                    double g0 = gsv[j], g1 = gsv[j + 1];
+                    gsv[j] = c * g0 + s * g1;
+                    gsv[j + 1] = -s * g0 + c * g1;
+                    esv[j] = ej;
+                }
+                dsv[k - 1] = dj;
+                esv[k - 1] = 0.0;
+            }
+            // Elden: eliminate lambda I of [Bd; lambda I] with 2k Givens rotations
+            double mu = lam, rr = 0.0;
+            for (int i = 0; i < k; ++i) {
+                double a = dsv[i], b = (i < k - 1) ? esv[i] : 0.0, gi = gsv[i];
+                double c, s, r;
+                givens(a, mu, c, s, r);
+                dsv[i] = r;
+                esv[i] = c * b;
+                z[i] = c * gi + s * rr;
+                double f = -s * b;
+                double t = -s * gi + c * rr;
+                if (i < k - 1) {
+                    double c2, s2, r2;
+                    givens(lam, f, c2, s2, r2);
+                    mu = r2;
+                    rr = s2 * t;
+                }
+            }
+            for (int i = k - 1; i >= 0; --i) {
+                double num = z[i] - ((i < k - 1) ? esv[i] * z[i + 1] : 0.0);
+                z[i] = (dsv[i] != 0.0) ? num / dsv[i] : 0.0;
             }
         }
-        for (int i = k - 1; i >= 0; --i) {
-            double num = z[i] - ((i < k - 1) ? esv[i] * z[i + 1] : 0.0);
-            z[i] = (dsv[i] != 0.0) ? num / dsv[i] : 0.0;
+        __syncthreads();
+        // y = Q z with the stored right reflectors: fast path reflector j acts on coordinates
+        // j..k-1 (vector in row j of A), exact path on j+1..k-1 (vector in row j, cols j+2..)
+        if (warp == 0) {
+            const int first = fast ? k - 1 : k - 3;
+            for (int j = first; j >= 0; --j) {
+                const double tau = tauR[j];
+                if (tau == 0.0) continue;
+                const int c0 = fast ? j : j + 1;
+                const double zj = z[c0];
+                double w = 0.0;
+                for (int l = c0 + 1 + lane; l < k; l += 32) w += A[l * lda + j] * z[l];
+                w = (warp_sum_d(w) + zj) * tau;
+                __syncwarp();
+                if (lane == 0) z[c0] -= w;
+                for (int l = c0 + 1 + lane; l < k; l += 32) z[l] -= w * A[l * lda + j];
+                __syncwarp();
+            }
         }
+        __syncthreads();
+        for (int i = tid; i < k; i += kSSThreads) P.y[i] = z[i];
     }
-    __syncthreads();
-    // y = Q z: right reflectors j = k-3 .. 0 act on coordinates j+1..k-1
-    if (warp == 0) {
-        for (int j = k - 3; j >= 0; --j) {
-            const double tau = tauR[j];
-            if (tau == 0.0) continue;
-            const double zj = z[j + 1];
-            double w = 0.0;
-            for (int l = j + 2 + lane; l < k; l += 32) w += A[l * lda + j] * z[l];
-            w = warp_sum_d(w) + zj;
-            w *= tau;
-            __syncwarp();
-            if (lane == 0) z[j + 1] -= w;
-            for (int l = j + 2 + lane; l < k; l += 32) z[l] -= w * A[l * lda + j];
-            __syncwarp();
-        }
-    }
-    __syncthreads();
-    for (int i = tid; i < k; i += kSSThreads) P.y[i] = z[i];
     if (tid == 0) {
         *P.lambda_out = lam;
         *P.resid_out = sqrt(misc[11]);

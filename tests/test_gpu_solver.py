@@ -55,7 +55,16 @@ def test_projected_solve_matches_oracle(k, rule):
     res = torch.zeros(1, dtype=torch.float64, device="cuda")
     ct_projected_solve(Hd, k + 1, k, beta, rule, lam_fixed, target, y, lam, res)
     torch.cuda.synchronize()
-    assert abs(lam.item() - lam_o) <= 1e-9 * max(lam_o, 1e-300) + (0 if lam_o else 0)
+    lg = lam.item()
+    if rule == "gcv":
+        # a minimiser is fixed only to ~sqrt(eps) where GCV is flat: compare the minimum value
+        # (unique) tightly and the argument loosely
+        assert abs(lg - lam_o) <= 1e-6 * lam_o
+        assert OS.gcv_value(lg, s, c) <= OS.gcv_value(lam_o, s, c) * (1 + 1e-12)
+        y_o = OS.tikhonov_y(lg, s, c, Vt)
+        r_o = math.sqrt(OS.residual_sq(lg, s, c))
+    else:
+        assert abs(lg - lam_o) <= 1e-9 * lam_o
     assert abs(res.item() - r_o) <= 1e-9 * r_o + 1e-14
     assert rel(y.cpu().numpy(), y_o) <= 1e-8
 
