@@ -20,9 +20,12 @@
 //     refines it.
 //  4. c_i^2 = 2 beta0^2 z_i(1)^2 with z_i(1)^2 = det(sigma_i I - T_{2:n}) / p'(sigma_i), the
 //     first-component formula of a symmetric tridiagonal's eigenvectors.
-//  5. Self-check: sum_i c_i^2 must equal beta0^2 (U orthogonal).  If it does not (clustered or
-//     zero singular values), the kernel recomputes sigma and c with the exact sequential path:
-//     Householder upper bidiagonalisation of H_k and implicit-shift Golub-Kahan QR.
+//     For clusters (relative gap < 1e-6) the formula is ill-conditioned; their total weight is a
+//     contour integral of e1^T (zI - T)^{-1} e1 around the cluster, shared by its members
+//     (GCV and DP depend on a cluster only through that total, to O(gap)).
+//  5. Self-check: sum_i c_i^2 must equal beta0^2 (U orthogonal).  If it does not, the kernel
+//     recomputes sigma and c with the exact sequential path: Householder upper
+//     bidiagonalisation of H_k and implicit-shift Golub-Kahan QR.
 // y is formed only where it is needed (the last step, or a breakdown step): the bidiagonal
 // Tikhonov problem min ||Bd z - g||^2 + lambda^2 ||z||^2 is eliminated with O(k) Givens
 // rotations and y = Q z applies the stored right reflectors.
@@ -183,6 +186,44 @@ __device__ void charpoly(const double *t2, int first, int n, double th, double &
         }
     }
     p = pm1; dp = qm1; ex = e;
+}
+
+// Sturm count: number of eigenvalues of the zero-diagonal tridiagonal (squared off-diagonals
+// t2[0..n-2]) below x, from the pivots of T - x I = L D L^T; a pivot smaller than pivmin is
+// replaced by -pivmin before it is counted (so counting and recurrence agree).
+__device__ int count64(const double *t2, int n, double x)
+{
+    const double pivmin = 1e-290;
+    double dd = -x;
+    if (fabs(dd) < pivmin) dd = -pivmin;
+    int cnt = dd < 0.0;
+    for (int j = 1; j < n; ++j) {
+        dd = -x - t2[j - 1] / dd;
+        if (fabs(dd) < pivmin) dd = -pivmin;
+        cnt += dd < 0.0;
+    }
+    return cnt;
+}
+
+// det(z I - T) for complex z (rows first..n-1), power-of-two rescaled: value * 2^ex.
+__device__ void charpoly_c(const double *t2, int first, int n, double zr, double zi,
+                           double &pr, double &pi, int &ex)
+{
+    double ar = 1.0, ai = 0.0, br = zr, bi = zi;   // p_{j-2}, p_{j-1}
+    int e = 0;
+    for (int j = first + 1; j < n; ++j) {
+        const double a = t2[j - 1];
+        double cr = zr * br - zi * bi - a * ar;
+        double ci = zr * bi + zi * br - a * ai;
+        ar = br; ai = bi; br = cr; bi = ci;
+        double mag = fabs(cr) + fabs(ci);
+        if (mag > 0x1p+400 || (mag < 0x1p-400 && mag != 0.0)) {
+            int sh = (mag > 0x1p+400) ? -400 : 400;
+            ar = ldexp(ar, sh); ai = ldexp(ai, sh); br = ldexp(br, sh); bi = ldexp(bi, sh);
+            e -= sh;
+        }
+    }
+    pr = br; pi = bi; ex = e;
 }
 
 size_t small_solve_smem_bytes(int k)
@@ -397,26 +438,43 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
     }
     if (tid == 0) misc[5] = 0.0;
     __syncthreads();
-    // sigma_i (i-th largest), one thread each: FP32 bisection, then FP64 safeguarded Newton
+    // sigma_i (i-th largest), one thread each.  FP32 bisection with Sturm counts gives a bracket
     for (int i = tid; i < k; i += kSSThreads) {
         float lo = 0.f, hi = 2.f;
         const int target = k - i;               // #{sigma < x} >= target  <=>  sigma_i < x
         for (int it = 0; it < 140 && (hi - lo) > 2e-6f * hi; ++it) {
             float x = 0.5f * (lo + hi);
-            int cnt = 0;
             float dd = -x;
-            cnt += (dd < 0.f);
+            if (fabsf(dd) < 1e-30f) dd = -1e-30f;
+            int cnt = dd < 0.f;
             for (int j = 1; j < n; ++j) {
-                float dprev = (fabsf(dd) < 1e-30f) ? -1e-30f : dd;
-                dd = -x - __fdividef(t2f[j - 1], dprev);
-                cnt += (dd < 0.f);
+                dd = -x - __fdividef(t2f[j - 1], dd);
+                if (fabsf(dd) < 1e-30f) dd = -1e-30f;
+                cnt += dd < 0.f;
             }
             if (cnt - k >= target) hi = x; else lo = x;
         }
         lo32[i] = lo;
         hi32[i] = hi;
-        double blo = (double)lo * (1.0 - 1e-4), bhi = (double)hi * (1.0 + 1e-4);
-        double th = 0.5 * ((double)lo + (double)hi), th_eval = th;
+    }
+    __syncthreads();
+    // FP64: brackets that overlap a neighbour's are isolated by FP64 Sturm-count bisection, then
+    // safeguarded Newton on det(theta I - T); c_i^2 by the first-component formula
+    for (int i = tid; i < k; i += kSSThreads) {
+        double blo = (double)lo32[i] * (1.0 - 2e-4), bhi = (double)hi32[i] * (1.0 + 2e-4);
+        const bool iso = (i == 0 || (double)lo32[i - 1] * (1.0 - 2e-4) > bhi) &&
+                         (i == k - 1 || (double)hi32[i + 1] * (1.0 + 2e-4) < blo);
+        if (!iso) {
+            const int tgt = k - i;
+            int clo = count64(t2, n, blo) - k, chi = count64(t2, n, bhi) - k;
+            if (!(clo <= tgt - 1 && chi >= tgt)) { blo = 0.0; bhi = 2.0; clo = 0; chi = k; }
+            for (int it = 0; it < 200 && chi - clo > 1 && bhi - blo > 1e-15 * bhi; ++it) {
+                double mid = 0.5 * (blo + bhi);
+                int cm = count64(t2, n, mid) - k;
+                if (cm >= tgt) { bhi = mid; chi = cm; } else { blo = mid; clo = cm; }
+            }
+        }
+        double th = 0.5 * (blo + bhi), th_eval = th;
         double p = 0.0, dp = 0.0;
         int ex = 0;
         // just below sigma_i, i+1 eigenvalues of T lie above theta: det(theta I - T) has sign (-1)^(i+1)
@@ -439,9 +497,59 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
         double p2, dp2;
         charpoly(t2, 1, n, th_eval, p2, dp2, ex2);
         double z1sq = (dp != 0.0) ? ldexp(p2 / dp, ex2 - ex) : -1.0;
-        sig[i] = th * tscale;
+        sig[i] = th;                               // scaled units until the end of this block
         double c2 = 2.0 * beta0 * beta0 * z1sq;
-        cv[i] = (c2 >= 0.0 && isfinite(c2)) ? sqrt(c2) : -1.0;
+        cv[i] = (c2 >= 0.0 && isfinite(c2)) ? c2 : -1.0;   // c_i^2 for now
+    }
+    __syncthreads();
+    // clusters (relative gap < 1e-6): the first-component formula is ill-conditioned there, but
+    // lambda rules only see a cluster's total weight sum c_i^2, a contour integral of the
+    // resolvent entry r(z) = e1^T (z I - T)^{-1} e1 = det(zI - T_{2:n}) / det(zI - T) around it
+    // (32-point trapezoidal rule on a circle of a third of the distance to the next eigenvalue)
+    int *clist = reinterpret_cast<int *>(rot);
+    if (tid == 0) {
+        int nc = 0;
+        for (int i = 0; i < k;) {
+            int b = i;
+            while (b + 1 < k && sig[b] - sig[b + 1] < 1e-6 * sig[b]) ++b;
+            if (b > i) { clist[2 * nc] = i; clist[2 * nc + 1] = b; ++nc; }
+            i = b + 1;
+        }
+        misc[7] = (double)nc;
+    }
+    __syncthreads();
+    {
+        const int nc = (int)misc[7];
+        for (int q = warp; q < nc; q += nwarps) {
+            const int a = clist[2 * q], b = clist[2 * q + 1];
+            const double c = 0.5 * (sig[a] + sig[b]), half = 0.5 * (sig[a] - sig[b]);
+            double R = c + sig[b];                                  // the mirrored cluster at -sigma
+            if (a > 0) R = fmin(R, sig[a - 1] - c);
+            if (b + 1 < k) R = fmin(R, c - sig[b + 1]);
+            const double rho = fmax(R / 3.0, 10.0 * half);
+            const double ph = 2.0 * 3.141592653589793 * (lane + 0.5) / 32.0;
+            double sn, cs;
+            sincos(ph, &sn, &cs);
+            const double zr = c + rho * cs, zi = rho * sn;
+            double pr, pi, p2r, p2i;
+            int ex, ex2;
+            charpoly_c(t2, 0, n, zr, zi, pr, pi, ex);
+            charpoly_c(t2, 1, n, zr, zi, p2r, p2i, ex2);
+            const double den = pr * pr + pi * pi;
+            double rr = (p2r * pr + p2i * pi) / den, ri = (p2i * pr - p2r * pi) / den;
+            rr = ldexp(rr, ex2 - ex); ri = ldexp(ri, ex2 - ex);
+            double w = rho * (cs * rr - sn * ri);                   // Re(rho e^{i ph} r(z))
+            w = warp_sum_d(w) / 32.0;
+            if (lane == 0) {
+                const double each = 2.0 * beta0 * beta0 * w / (double)(b - a + 1);
+                for (int j = a; j <= b; ++j) cv[j] = (each >= 0.0 && isfinite(each)) ? each : -1.0;
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < k; i += kSSThreads) {
+        sig[i] *= tscale;
+        cv[i] = (cv[i] >= 0.0) ? sqrt(cv[i]) : -1.0;
     }
     if (tid == 0) cv[k] = fabs(ck1);
     __syncthreads();
@@ -452,7 +560,7 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
         for (int i = lane; i < k; i += 32) {
             if (cv[i] < 0.0 || !isfinite(sig[i])) bad = 1;
             else s += cv[i] * cv[i];
-            if (i + 1 < k && !(sig[i] > sig[i + 1] * (1.0 + 1e-12))) bad = 1;
+            if (i + 1 < k && !(sig[i] >= sig[i + 1])) bad = 1;
         }
         s = warp_sum_d(s);
         bad = __any_sync(0xffffffffu, bad);
