@@ -149,13 +149,34 @@ ct_status ba_gmres_hybrid(ct_geom *g, const float *b_dev, const float *x0_dev, f
 
 /* ------------------------------------------------------------------ building blocks */
 
-/* One Arnoldi orthogonalisation step (Sec. 2.1, Eq. (Hessenberg); Alg. 1 lines 6-11):
+/* One Arnoldi orthogonalisation step (Sec. 2.1, Eq. (Hessenberg); Alg. 1 lines 6-11).
+ * Allocates its scratch with stream-ordered cudaMallocAsync/cudaFreeAsync on every call.
  * given k+1 orthonormal rows W[0..k] (each `len` floats, row stride `ld` floats) and
  * q = M w_k, compute h[i] = <q, w_i> by classical Gram-Schmidt applied twice (the second
  * pass's coefficients added), h[k+1] = ||q||, and W[k+1] = q / h[k+1].  W_dev must have
  * room for k+2 rows; q_dev (len floats) is overwritten; h_dev receives k+2 doubles. */
 ct_status ct_arnoldi_step(float *W_dev, int64_t len, int64_t ld, int k, float *q_dev,
                           double *h_dev, ct_stream_t stream);
+
+/* ct_arnoldi_step without any device allocation.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate GPU memory while they run.  cudaFree
+ * synchronises the whole device, which would stall acquisition or other work that the caller
+ * keeps running on other streams, and an application that reserves the GPU's memory through its
+ * own pool cannot let a library take more.  ct_arnoldi_step allocates and frees its scratch
+ * (per-block partial sums, counters) on every call; this variant keeps that scratch in one
+ * static device array of about 1.3 MB in the library, which every GPU that loads the library
+ * holds until the process exits.
+ *   - Same arguments, results and layout rules as ct_arnoldi_step.
+ *   - Limit: k <= 126 (h has at most 128 entries); larger k returns CT_EINVAL with a message,
+ *     and nothing is launched.
+ *   - The first call on a device, with that device current, looks up the array's device
+ *     address (cudaGetSymbolAddress) once; make that first call before any stream capture.
+ *   - Every call uses the same array and the array keeps the previous call's contents (the
+ *     call clears what must start at zero), so calls that overlap on the GPU (different
+ *     streams, or concurrent host threads) race: serialise them.
+ *   - Calls no cudaMalloc, cudaFree or allocating library routine. */
+ct_status ct_arnoldi_step_noalloc(float *W_dev, int64_t len, int64_t ld, int k, float *q_dev,
+                                  double *h_dev, ct_stream_t stream);
 
 /* The hybrid step on the device (Sec. 3, Eq. (hybrid_proj); Sec. 3.1/3.2): for the
  * (k+1) x k Hessenberg matrix H (FP64, column-major, leading dimension ldh >= k+1) and

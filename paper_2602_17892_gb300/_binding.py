@@ -24,7 +24,7 @@ BASIS = {"f32": 0, "bf16": 1, "f16": 2}
 
 # the entry points of include/ctabba.h
 EXPORTS = ("ct_geom_create", "ct_geom_destroy", "ct_geom_dims", "ct_geom_work", "ct_forward_A", "ct_back_B",
-           "ct_hybrid_opts_default", "ab_gmres_hybrid", "ba_gmres_hybrid", "ct_arnoldi_step",
+           "ct_hybrid_opts_default", "ab_gmres_hybrid", "ba_gmres_hybrid", "ct_arnoldi_step", "ct_arnoldi_step_noalloc",
            "ct_projected_solve", "ct_status_string", "ct_last_error", "ct_profile_enable",
            "ct_profile_collect", "ct_launch_count")
 PHASES = ("forward_A", "back_B", "layout", "arnoldi", "small_solve", "other")
@@ -87,6 +87,8 @@ def load(path: str = LIB_PATH):
     for fn in (lib.ab_gmres_hybrid, lib.ba_gmres_hybrid):
         fn.argtypes = [vp, vp, vp, vp, ctypes.POINTER(HybridOpts), ctypes.POINTER(HybridInfo), vp]
     lib.ct_arnoldi_step.argtypes = [vp, i64, i64, ctypes.c_int, vp, vp, vp]
+    lib.ct_arnoldi_step_noalloc.argtypes = [vp, i64, i64, ctypes.c_int, vp, vp, vp]
+    lib.ct_arnoldi_step_noalloc.restype = ctypes.c_int
     lib.ct_projected_solve.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_int, ctypes.c_double, ctypes.c_double, vp, vp,
                                        vp, vp]
@@ -223,6 +225,12 @@ def ba_gmres_hybrid(g, b, x, x0=None, max_iters=30, rule="gcv", lambda_fixed=0.0
 def ct_arnoldi_step(W, length, ld, k, q, h, stream=None):
     _check(load().ct_arnoldi_step(_ptr(W), int(length), int(ld), int(k), _ptr(q),
                                   _ptr(h, "float64"), _stream(stream)))
+
+
+def ct_arnoldi_step_noalloc(W, length, ld, k, q, h, stream=None):
+    """As ct_arnoldi_step, with its scratch in a static device array (no allocation)."""
+    _check(load().ct_arnoldi_step_noalloc(_ptr(W), int(length), int(ld), int(k), _ptr(q),
+                                          _ptr(h, "float64"), _stream(stream)))
 
 
 def ct_projected_solve(H, ldh, k, beta, rule, lambda_fixed, dp_target, y, lam, resid,

@@ -15,6 +15,8 @@
 //   K4  w_{k+1} = q / h_{k+1,k}
 // Block partial sums are FP32 (warp shuffles), the cross-block sum is FP64 in a fixed order
 // by the last block to finish, so results are reproducible run to run.
+#include <mutex>
+
 #include "ct_internal.h"
 
 namespace ct {
@@ -259,3 +261,74 @@ cudaError_t launch_rsub(const float *b, float *r, int64_t L, int max_blocks, cud
 }
 
 }  // namespace ct
+
+namespace ct {
+
+// ----------------------------------------------------------------------------- no-allocation variant
+// Scratch of ct_arnoldi_step_noalloc: a file-scope device array, so the entry point never
+// allocates.  Every GPU that loads the library holds it (about 1.3 MB) until the process exits.
+constexpr int kNoAllocMaxK = 126;                    // h has at most k + 2 = 128 entries
+constexpr int kNoAllocBlocks = 152 * 8;
+constexpr size_t kNoAllocPartial = (size_t)kNoAllocBlocks * (kNoAllocMaxK + 3);   // doubles
+constexpr size_t kNoAllocAux = 8 + 2 * (kNoAllocMaxK + 3);                          // doubles
+constexpr size_t kNoAllocBytes = (kNoAllocPartial + kNoAllocAux) * sizeof(double) + 64;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[64] = {nullptr};
+
+}  // namespace ct
+
+extern "C" ct_status ct_arnoldi_step_noalloc(float *W_dev, int64_t len, int64_t ld, int k,
+                                             float *q_dev, double *h_dev, ct_stream_t stream)
+{
+    using namespace ct;
+    if (!W_dev || !q_dev || !h_dev) {
+        set_error("ct_arnoldi_step_noalloc: null argument");
+        return CT_EINVAL;
+    }
+    if (k < 0 || k > kNoAllocMaxK) {
+        set_error("ct_arnoldi_step_noalloc: k = " + std::to_string(k) +
+                  " exceeds the static scratch (0 <= k <= " + std::to_string(kNoAllocMaxK) + ")");
+        return CT_EINVAL;
+    }
+    if (len < 1 || ld < len || (len % 4) || (ld % 4)) {
+        set_error("ct_arnoldi_step_noalloc: need len % 4 == 0, ld % 4 == 0, ld >= len >= 1");
+        return CT_EINVAL;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "ct_arnoldi_step_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= 64) {
+        set_error("ct_arnoldi_step_noalloc: device ordinal out of range");
+        return CT_EINVAL;
+    }
+    void *base = nullptr;
+    {
+        // one-time set-up per device, with that device current: the device address of the
+        // static array (its name in host code is only a host-side stand-in)
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            e = cudaGetSymbolAddress(&g_noalloc_ptr[dev], g_noalloc_scratch);
+            if (e != cudaSuccess) {
+                g_noalloc_ptr[dev] = nullptr;
+                return cuda_fail(e, "ct_arnoldi_step_noalloc: cudaGetSymbolAddress");
+            }
+        }
+        base = g_noalloc_ptr[dev];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    double *partial = reinterpret_cast<double *>(base);
+    double *aux = partial + kNoAllocPartial;
+    unsigned *counter = reinterpret_cast<unsigned *>(aux + kNoAllocAux);
+    int *stop = reinterpret_cast<int *>(counter + 4);
+    // the array keeps the previous call's contents: clear what must start at zero
+    e = cudaMemsetAsync(counter, 0, 4 * sizeof(unsigned) + 4 * sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(aux, 0, kNoAllocAux * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h_dev, 0, sizeof(double) * (k + 2), s);
+    if (e != cudaSuccess) return cuda_fail(e, "ct_arnoldi_step_noalloc: clearing scratch");
+    ArnoldiScratch sc{partial, counter, kNoAllocBlocks, kNoAllocMaxK + 1};
+    e = arnoldi_step_dev(W_dev, len, ld, k, q_dev, h_dev, sc, aux, stop, 1, true, s);
+    if (e != cudaSuccess) return cuda_fail(e, "ct_arnoldi_step_noalloc: launch");
+    return CT_OK;
+}
