@@ -126,6 +126,8 @@ typedef struct {
     double final_lambda;
     double final_resid;      /* ||H_k y_k - beta e1|| (= ||b - A x_k|| for AB)             */
     ct_status status;        /* CT_OK or CT_BREAKDOWN                                      */
+    int fast_path_steps;     /* steps whose hybrid step took the parallel path (the others ran
+                                the exact sequential SVD path; diagnostics only)            */
 } ct_hybrid_info;
 
 /* Fill `o` with defaults: K = 30, GCV, tau = 1.01, reorth = 1, FP32 basis, no history. */

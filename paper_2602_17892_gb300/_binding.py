@@ -59,7 +59,7 @@ class PhaseTime(ctypes.Structure):
 class HybridInfo(ctypes.Structure):
     _fields_ = [("iters_done", ctypes.c_int), ("beta", ctypes.c_double),
                 ("final_lambda", ctypes.c_double), ("final_resid", ctypes.c_double),
-                ("status", ctypes.c_int)]
+                ("status", ctypes.c_int), ("fast_path_steps", ctypes.c_int)]
 
 
 _lib = None
@@ -202,7 +202,8 @@ def _solve(fn, g, b, x, x0, max_iters, rule, lambda_fixed, noise_norm, tau, reor
             _stream(stream))
     _check(st)
     out = dict(iters_done=info.iters_done, beta=info.beta, final_lambda=info.final_lambda,
-               final_resid=info.final_resid, status=STATUS_NAMES[info.status])
+               final_resid=info.final_resid, status=STATUS_NAMES[info.status],
+               fast_path_steps=info.fast_path_steps)
     if history:
         out["lambdas"], out["resid"] = lam, res
     return out

@@ -101,12 +101,9 @@ struct PhaseScope {
 using namespace ct;
 
 // ============================================================================ workspace
-constexpr int kSideStreams = 8;   // concurrent small solves (independent of the main chain)
-
 struct Workspace {
     int method = -1, K = 0, basis = 0;
-    cudaStream_t side[kSideStreams] = {};
-    cudaEvent_t fork[kSideStreams] = {}, join[kSideStreams] = {};
+    int *path = nullptr;    // per step: 1 = parallel small-solve path accepted
     int64_t L = 0;          // basis row length in floats (multiple of 4, zero tail)
     float *W = nullptr;     // (K+1) rows
     float *q = nullptr;     // L
@@ -124,12 +121,7 @@ static void ws_free(Workspace *w)
     if (!w) return;
     cudaFree(w->W); cudaFree(w->q); cudaFree(w->img); cudaFree(w->sino); cudaFree(w->vec);
     cudaFree(w->H); cudaFree(w->Y); cudaFree(w->lam); cudaFree(w->res); cudaFree(w->aux);
-    cudaFree(w->partial); cudaFree(w->counter); cudaFree(w->stop);
-    for (int i = 0; i < kSideStreams; ++i) {
-        if (w->side[i]) cudaStreamDestroy(w->side[i]);
-        if (w->fork[i]) cudaEventDestroy(w->fork[i]);
-        if (w->join[i]) cudaEventDestroy(w->join[i]);
-    }
+    cudaFree(w->partial); cudaFree(w->counter); cudaFree(w->stop); cudaFree(w->path);
     delete w;
 }
 
@@ -171,13 +163,7 @@ static ct_status ws_get(ct_geom *g, int method, int K, int basis, Workspace **ou
     if (e == cudaSuccess) e = dalloc(&w->partial, (size_t)kMaxBlocks * (K + 2));
     if (e == cudaSuccess) e = dalloc(&w->counter, 4);
     if (e == cudaSuccess) e = dalloc(&w->stop, 4);
-    int prio_lo = 0, prio_hi = 0;
-    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
-    for (int i = 0; i < kSideStreams && e == cudaSuccess; ++i) {
-        e = cudaStreamCreateWithPriority(&w->side[i], cudaStreamNonBlocking, prio_hi);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->fork[i], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->join[i], cudaEventDisableTiming);
-    }
+    if (e == cudaSuccess) e = dalloc(&w->path, (size_t)K);
     if (e != cudaSuccess) {
         ws_free(w);
         set_error(std::string("workspace allocation: ") + cudaGetErrorString(e));
@@ -434,6 +420,8 @@ static ct_status finish(Workspace *w, const ct_hybrid_opts *o, ct_hybrid_info *i
     const int K = o->max_iters;
     int kf = (stop[0] == 0) ? K : std::max(stop[0], 0);
     std::vector<double> lam(K), res(K);
+    std::vector<int> path(K);
+    CT_CUDA(cudaMemcpy(path.data(), w->path, sizeof(int) * K, cudaMemcpyDeviceToHost));
     CT_CUDA(cudaMemcpy(lam.data(), w->lam, sizeof(double) * K, cudaMemcpyDeviceToHost));
     CT_CUDA(cudaMemcpy(res.data(), w->res, sizeof(double) * K, cudaMemcpyDeviceToHost));
     for (int i = kf; i < K; ++i) lam[i] = res[i] = NAN;
@@ -446,41 +434,33 @@ static ct_status finish(Workspace *w, const ct_hybrid_opts *o, ct_hybrid_info *i
         info->final_lambda = kf > 0 ? lam[kf - 1] : 0.0;
         info->final_resid = kf > 0 ? res[kf - 1] : beta;
         info->status = st;
+        info->fast_path_steps = 0;
+        if (o->rule != CT_LAMBDA_NONE)
+            for (int i = 0; i < kf; ++i) info->fast_path_steps += path[i];
     }
     if (st == CT_ENONFINITE) { set_error("solver: non-finite value met"); return st; }
     return CT_OK;
 }
 
-// The hybrid step of step `step` depends only on H's first `step` columns, and nothing in the
-// Arnoldi chain depends on it, so it runs on one of the side streams, overlapped with the
-// projectors of the following steps (Alg. 1/2 line 12-13).
-static ct_status run_small_solve(Workspace *w, const ct_hybrid_opts *o, int step, cudaStream_t s,
-                                 double dp_target)
+// The hybrid step (Alg. 1/2 lines 12-13) of step k depends only on H's first k columns, and with
+// a fixed iteration count nothing in the Arnoldi chain depends on it.  All K projected problems
+// are therefore solved after the loop in one launch, one CTA per k (the lambda_k history is
+// the same as if each had been solved inside its iteration); y is formed for the final k.
+static ct_status run_small_solves(Workspace *w, const ct_hybrid_opts *o, cudaStream_t s,
+                                  double dp_target)
 {
     SmallSolveParams p;
-    p.H = w->H; p.ldh = w->K + 1; p.k = step; p.beta = 0.0; p.betap = w->aux + 2;
+    p.H = w->H; p.ldh = w->K + 1; p.k = o->max_iters; p.beta = 0.0; p.betap = w->aux + 2;
     p.rule = o->rule; p.lambda_fixed = o->lambda_fixed; p.dp_target = dp_target;
-    p.y = w->Y + (size_t)(step - 1) * w->K;
-    p.lambda_out = w->lam + (step - 1);
-    p.resid_out = w->res + (step - 1);
+    p.y = w->Y; p.ystride = w->K;
+    p.lambda_out = w->lam;
+    p.resid_out = w->res;
     p.stop = w->stop;
     p.kmax = o->max_iters;
     p.always_y = 0;
-    const int j = (step - 1) % kSideStreams;
-    CT_CUDA(cudaEventRecord(w->fork[j], s));
-    CT_CUDA(cudaStreamWaitEvent(w->side[j], w->fork[j], 0));
-    CT_PHASE(CT_PH_SMALL, 1, w->side[j]);
-    CT_CUDA(launch_small_solve(p, w->side[j]));
-    return CT_OK;
-}
-
-// the main stream waits for every side stream before it uses the small-solve results
-static ct_status join_side(Workspace *w, cudaStream_t s)
-{
-    for (int j = 0; j < kSideStreams; ++j) {
-        CT_CUDA(cudaEventRecord(w->join[j], w->side[j]));
-        CT_CUDA(cudaStreamWaitEvent(s, w->join[j], 0));
-    }
+    p.path = w->path;
+    CT_PHASE(CT_PH_SMALL, 1, s);
+    CT_CUDA(launch_small_solve_batched(p, s));
     return CT_OK;
 }
 
@@ -501,6 +481,7 @@ extern "C" ct_status ab_gmres_hybrid(ct_geom *g, const float *b_dev, const float
     const double dp_target = o->tau * o->noise_norm;
     CT_CUDA(cudaMemsetAsync(w->stop, 0, 2 * sizeof(int), s));
     CT_CUDA(cudaMemsetAsync(w->counter, 0, 4 * sizeof(unsigned), s));
+    CT_CUDA(cudaMemsetAsync(w->path, 0, sizeof(int) * K, s));
     // Alg. 1 lines 1-3: x0 = B u0, r0 = b - A x0, w1 = r0 / ||r0||
     {
         CT_PHASE(CT_PH_OTHER, u0_dev ? 8 : 3, s);
@@ -537,9 +518,8 @@ extern "C" ct_status ab_gmres_hybrid(ct_geom *g, const float *b_dev, const float
             CT_CUDA(arnoldi_step_dev(w->W, L, ld, k, w->q, w->H + (int64_t)k * ldh,
                                      sc, w->aux, w->stop, step, o->reorth != 0, s));
         }
-        if ((st = run_small_solve(w, o, step, s, dp_target)) != CT_OK) return st;   // 12-13
     }
-    if ((st = join_side(w, s)) != CT_OK) return st;
+    if ((st = run_small_solves(w, o, s, dp_target)) != CT_OK) return st;        // lines 12-13
     // line 13 at k = K: x = x0 + B W y = B (u0 + W y)
     {
         CT_PHASE(CT_PH_OTHER, u0_dev ? 2 : 1, s);
@@ -572,6 +552,7 @@ extern "C" ct_status ba_gmres_hybrid(ct_geom *g, const float *b_dev, const float
     const double dp_target = o->tau * o->noise_norm;
     CT_CUDA(cudaMemsetAsync(w->stop, 0, 2 * sizeof(int), s));
     CT_CUDA(cudaMemsetAsync(w->counter, 0, 4 * sizeof(unsigned), s));
+    CT_CUDA(cudaMemsetAsync(w->path, 0, sizeof(int) * K, s));
     // Alg. 2 lines 1-3: r0 = B (b - A x0), w1 = r0 / ||r0||
     {
         CT_PHASE(CT_PH_OTHER, x0_dev ? 7 : 4, s);
@@ -609,9 +590,8 @@ extern "C" ct_status ba_gmres_hybrid(ct_geom *g, const float *b_dev, const float
             CT_CUDA(arnoldi_step_dev(w->W, L, ld, k, w->q, w->H + (int64_t)k * ldh,
                                      sc, w->aux, w->stop, step, o->reorth != 0, s));
         }
-        if ((st = run_small_solve(w, o, step, s, dp_target)) != CT_OK) return st;
     }
-    if ((st = join_side(w, s)) != CT_OK) return st;
+    if ((st = run_small_solves(w, o, s, dp_target)) != CT_OK) return st;        // lines 12-13
     // line 13: x = x0 + W y
     {
         CT_PHASE(CT_PH_OTHER, 1, s);
@@ -667,7 +647,7 @@ extern "C" ct_status ct_projected_solve(const double *H_dev, int ldh, int k, dou
     p.H = H_dev; p.ldh = ldh; p.k = k; p.beta = beta; p.betap = nullptr;
     p.rule = rule; p.lambda_fixed = lambda_fixed; p.dp_target = dp_target;
     p.y = y_dev; p.lambda_out = lambda_dev; p.resid_out = resid_dev; p.stop = nullptr;
-    p.kmax = k; p.always_y = 1;
+    p.kmax = k; p.always_y = 1; p.path = nullptr; p.ystride = 0;
     CT_CUDA(launch_small_solve(p, (cudaStream_t)stream));
     return CT_OK;
 }

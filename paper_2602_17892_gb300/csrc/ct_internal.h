@@ -107,8 +107,14 @@ struct SmallSolveParams {
     const int *stop;  // solver stop word (may be null)
     int kmax;         // last step of the solve: y is formed there (or at a breakdown step)
     int always_y;     // form y at every k
+    int *path;        // optional: 1 where the parallel path was accepted, 0 where the exact
+                      // sequential path ran (indexed by k - 1)
+    int ystride;      // batched launch: block b solves k = b + 1, y at y + b * ystride,
+                      // lambda_out[b], resid_out[b], path[b]
 };
 cudaError_t launch_small_solve(const SmallSolveParams &p, cudaStream_t s);
+// all steps k = 1..p.k of one solve in one launch (one CTA per k)
+cudaError_t launch_small_solve_batched(const SmallSolveParams &p, cudaStream_t s);
 size_t small_solve_smem_bytes(int k);
 
 }  // namespace ct

@@ -232,8 +232,16 @@ size_t small_solve_smem_bytes(int k)
     return nd * sizeof(double);
 }
 
-__global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParams P)
+__global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParams P, int batched)
 {
+    if (batched) {      // block b solves the projected problem of step k = b + 1
+        const int b = blockIdx.x;
+        P.k = b + 1;
+        P.y += (size_t)b * P.ystride;
+        P.lambda_out += b;
+        P.resid_out += b;
+        if (P.path) P.path += b;
+    }
     const int k = P.k;
     int stop_now = 0;
     if (P.stop) {
@@ -572,6 +580,7 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
     }
     __syncthreads();
     const bool fast = misc[6] == 0.0;
+    if (tid == 0 && P.path) *P.path = fast ? 1 : 0;
     // fast-path y needs (d, e, beta0 e1) of the lower bidiagonal and reflectors on coords j..
     if (fast && need_y && tid == 0) {
         for (int i = 0; i < k; ++i) { dsv[i] = d[i]; esv[i] = (i < k - 1) ? e[i] : 0.0; gsv[i] = 0.0; }
@@ -822,9 +831,19 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
     }
 }
 
+static cudaError_t set_smem_attr();
+
 cudaError_t launch_small_solve(const SmallSolveParams &p, cudaStream_t s)
 {
     size_t smem = small_solve_smem_bytes(p.k);
+    cudaError_t e = set_smem_attr();
+    if (e != cudaSuccess) return e;
+    small_solve_kernel<<<1, kSSThreads, smem, s>>>(p, 0);
+    return cudaGetLastError();
+}
+
+static cudaError_t set_smem_attr()
+{
     static bool attr_set[64] = {false};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -836,7 +855,14 @@ cudaError_t launch_small_solve(const SmallSolveParams &p, cudaStream_t s)
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
     }
-    small_solve_kernel<<<1, kSSThreads, smem, s>>>(p);
+    return cudaSuccess;
+}
+
+cudaError_t launch_small_solve_batched(const SmallSolveParams &p, cudaStream_t s)
+{
+    cudaError_t e = set_smem_attr();
+    if (e != cudaSuccess) return e;
+    small_solve_kernel<<<p.k, kSSThreads, small_solve_smem_bytes(p.k), s>>>(p, 1);
     return cudaGetLastError();
 }
 
