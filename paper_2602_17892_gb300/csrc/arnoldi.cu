@@ -9,10 +9,11 @@
 // working precision ("twice is enough"); both give the same H and W in exact arithmetic.
 //
 // One step is four launches over the basis rows (vectors of L floats, L % 4 == 0, zero tails):
-//   K1  h1 = W^T q,          ||q||^2                         (reads W once)
-//   K2  q -= W h1;  h2 = W^T q                              (reads W twice)
-//   K3  q -= W h2;  ||q||^2 -> h_{k+1,k}, breakdown test      (reads W once)
+//   K1  h1 = W^T q,          ||q||^2                         (reads W once, last row first)
+//   K2  q -= W h1;  h2 = W^T q                              (reads W twice: forwards, backwards)
+//   K3  q -= W h2;  ||q||^2 -> h_{k+1,k}, breakdown test      (reads W once, forwards)
 //   K4  w_{k+1} = q / h_{k+1,k}
+// Each pass starts where the previous one ended, so the rows it needs first are still in L2.
 // Block partial sums are FP32 (warp shuffles), the cross-block sum is FP64 in a fixed order
 // by the last block to finish, so results are reproducible run to run.
 #include <mutex>
@@ -46,6 +47,11 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
+constexpr int kGroup = 8;   // basis rows handled together: 8 independent loads in flight
+
+// row index of position p in a pass over n rows, forwards or backwards
+__device__ __forceinline__ int row_at(int p, int n, bool backwards) { return backwards ? n - 1 - p : p; }
+
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) cgs_kernel(CgsArgs a)
 {
@@ -53,14 +59,17 @@ __global__ void __launch_bounds__(kThreads) cgs_kernel(CgsArgs a)
     extern __shared__ float sm[];
     const int nvec = (MODE == M_NORM) ? 0 : a.nvec;
     const int ncol = nvec + 1;                       // dots + squared norm
-    float *scoef = sm;                               // nvec
-    float *acc = sm + nvec;                          // [kWarps][ncol]
+    const int nvec8 = (nvec + kGroup - 1) / kGroup * kGroup;
+    float *scoef = sm;                               // nvec8 (zero padded)
+    float *acc = sm + nvec8;                         // [kWarps][ncol]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < kWarps * ncol; i += kThreads) acc[i] = 0.f;
     if (MODE == M_UPD_DOTS || MODE == M_UPD_NORM)
-        for (int i = tid; i < nvec; i += kThreads) scoef[i] = (float)a.coef[i];
+        for (int i = tid; i < nvec8; i += kThreads) scoef[i] = (i < nvec) ? (float)a.coef[i] : 0.f;
     __syncthreads();
-
+    // Passes alternate direction so that each one starts on the rows the previous pass read
+    // last (still in L2): K1 dots backwards, K2 update forwards then dots backwards, K3 forwards.
+    const bool dots_backwards = true;
     const float4 *W4 = reinterpret_cast<const float4 *>(a.W);
     float4 *q4 = reinterpret_cast<float4 *>(a.q);
     const int64_t ld4 = a.ld / 4;
@@ -70,24 +79,43 @@ __global__ void __launch_bounds__(kThreads) cgs_kernel(CgsArgs a)
         float4 v = ok ? q4[e] : make_float4(0.f, 0.f, 0.f, 0.f);
         if (MODE == M_UPD_DOTS || MODE == M_UPD_NORM) {
             if (ok) {
-                for (int i = 0; i < nvec; ++i) {
-                    float4 w = __ldg(W4 + i * ld4 + e);
-                    float c = scoef[i];
-                    v.x = fmaf(-c, w.x, v.x); v.y = fmaf(-c, w.y, v.y);
-                    v.z = fmaf(-c, w.z, v.z); v.w = fmaf(-c, w.w, v.w);
+                for (int p0 = 0; p0 < nvec; p0 += kGroup) {
+                    float4 w[kGroup];
+#pragma unroll
+                    for (int u = 0; u < kGroup; ++u)
+                        w[u] = (p0 + u < nvec) ? __ldg(W4 + (int64_t)(p0 + u) * ld4 + e)
+                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int u = 0; u < kGroup; ++u) {
+                        const float c = scoef[p0 + u];
+                        v.x = fmaf(-c, w[u].x, v.x); v.y = fmaf(-c, w[u].y, v.y);
+                        v.z = fmaf(-c, w[u].z, v.z); v.w = fmaf(-c, w[u].w, v.w);
+                    }
                 }
                 q4[e] = v;
             }
         }
         if (MODE == M_DOTS || MODE == M_UPD_DOTS) {
-            for (int i = 0; i < nvec; ++i) {
-                float p = 0.f;
-                if (ok) {
-                    float4 w = __ldg(W4 + i * ld4 + e);
-                    p = fmaf(w.x, v.x, fmaf(w.y, v.y, fmaf(w.z, v.z, w.w * v.w)));
+            for (int p0 = 0; p0 < nvec; p0 += kGroup) {
+                float pd[kGroup];
+#pragma unroll
+                for (int u = 0; u < kGroup; ++u) {
+                    pd[u] = 0.f;
+                    if (ok && p0 + u < nvec) {
+                        const int i = row_at(p0 + u, nvec, dots_backwards);
+                        const float4 w = __ldg(W4 + (int64_t)i * ld4 + e);
+                        pd[u] = fmaf(w.x, v.x, fmaf(w.y, v.y, fmaf(w.z, v.z, w.w * v.w)));
+                    }
                 }
-                p = warp_sum(p);
-                if (lane == 0) acc[warp * ncol + i] += p;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int u = 0; u < kGroup; ++u) pd[u] += __shfl_xor_sync(0xffffffffu, pd[u], o);
+                if (lane == 0) {
+#pragma unroll
+                    for (int u = 0; u < kGroup; ++u)
+                        if (p0 + u < nvec) acc[warp * ncol + row_at(p0 + u, nvec, dots_backwards)] += pd[u];
+                }
             }
         }
         float nn = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, v.w * v.w)));
@@ -173,7 +201,7 @@ cudaError_t arnoldi_step_dev(float *W, int64_t L, int64_t ld, int k, float *q, d
     const int blocks = grid_for(L4, sc.max_blocks);
     double *h1 = aux + 8, *h2 = aux + 8 + (sc.kmax + 2);
     CgsArgs a{W, ld, nvec, q, L4, nullptr, sc.partial, sc.counter, hcol, aux, h1, stop, step};
-    size_t smem = sizeof(float) * (size_t)(nvec + kWarps * (nvec + 1));
+    size_t smem = sizeof(float) * (size_t)((nvec + 7) / 8 * 8 + kWarps * (nvec + 1));
     cgs_kernel<M_DOTS><<<blocks, kThreads, smem, s>>>(a);
     if (reorth) {
         a.coef = h1; a.coef_out = h2;

@@ -234,6 +234,38 @@ static Ray2D make_ray(const ct_geom_desc *d, int view, int bin)
     return r;
 }
 
+// Widest detector footprint (bins, with the kernel's margins) of a 32 x 8 pixel block over all
+// views, rounded up; the backprojector stages that many bins per view in shared memory.
+static int bp_footprint_slot(const ct_geom_desc &d)
+{
+    const double cm = (d.nx - 1) / 2.0, rm = (d.ny - 1) / 2.0, h = d.pixel;
+    int widest = 4;
+    for (int v = 0; v < d.n_views; ++v) {
+        const double cs = cos(d.angles[v]), sn = sin(d.angles[v]);
+        for (int c0 = 0; c0 < d.nx; c0 += 32)
+            for (int r0 = 0; r0 < d.ny; r0 += 8) {
+                double fmn = 1e300, fmx = -1e300;
+                const double cc[2] = {c0 - cm, std::min(c0 + 31, d.nx - 1) - cm};
+                const double rr[2] = {r0 - rm, std::min(r0 + 7, d.ny - 1) - rm};
+                for (int a = 0; a < 2; ++a)
+                    for (int b = 0; b < 2; ++b) {
+                        double X = cc[a] * h, Y = rr[b] * h, u;
+                        if (d.kind == CT_PARALLEL2D) u = X * cs + Y * sn;
+                        else u = d.sdd * (-X * sn + Y * cs) / (d.sid - (X * cs + Y * sn));
+                        double fj = u / d.pitch_u + (d.n_det_u - 1) / 2.0 + 2.0;
+                        fmn = std::min(fmn, fj);
+                        fmx = std::max(fmx, fj);
+                    }
+                fmn = std::min(std::max(fmn, 0.0), d.n_det_u + 2.0);
+                fmx = std::min(std::max(fmx, 0.0), d.n_det_u + 2.0);
+                int w = (int)(floor(fmx) - floor(fmn)) + 4;
+                widest = std::max(widest, w);
+            }
+    }
+    int slot = (int)round_up(widest + 2, 8);     // +2: FP32 rounding of the corner positions
+    return std::min(slot, 256);                  // wider views read the sinogram directly
+}
+
 extern "C" {
 
 const char *ct_last_error(void) { return g_last_error.c_str(); }
@@ -285,8 +317,9 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     dg.kind = d->kind; dg.nx = d->nx; dg.ny = d->ny; dg.nz = 1;
     dg.h = (float)d->pixel; dg.n_views = d->n_views; dg.ndu = d->n_det_u; dg.ndv = 1;
     dg.pitch_u = (float)d->pitch_u; dg.pitch_v = 1.f; dg.sid = (float)d->sid; dg.sdd = (float)d->sdd;
-    dg.row_pairs_ld = (int)round_up(d->nx + 1, 16);
-    dg.col_pairs_ld = (int)round_up(d->ny + 1, 16);
+    dg.xr_ld = (int)round_up(d->nx + 2, 8);
+    dg.xt_ld = (int)round_up(d->ny + 2, 8);
+    dg.bp_slot = bp_footprint_slot(g->desc);
     dg.sino_ld = (int)round_up(d->n_det_u + 4, 4);
 
     std::vector<Ray2D> rays((size_t)g->m);
@@ -311,8 +344,8 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     if (e == cudaSuccess) e = cudaMemcpy(g->rays_dev, rays.data(), sizeof(Ray2D) * rays.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = dalloc(&g->views_dev, views.size());
     if (e == cudaSuccess) e = cudaMemcpy(g->views_dev, views.data(), sizeof(ViewBP) * views.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = dalloc(&g->prow_dev, (size_t)d->ny * dg.row_pairs_ld);
-    if (e == cudaSuccess) e = dalloc(&g->pcol_dev, (size_t)d->nx * dg.col_pairs_ld);
+    if (e == cudaSuccess) e = dalloc(&g->xr_dev, (size_t)d->ny * dg.xr_ld);
+    if (e == cudaSuccess) e = dalloc(&g->xt_dev, (size_t)d->nx * dg.xt_ld);
     if (e == cudaSuccess) e = dalloc(&g->sino_pad_dev, (size_t)d->n_views * dg.sino_ld);
     if (e != cudaSuccess) {
         set_error(std::string("ct_geom_create: ") + cudaGetErrorString(e));
@@ -335,7 +368,7 @@ void ct_geom_destroy(ct_geom *g)
         ws_free(ex->ws[1]);
         delete ex;
     }
-    cudaFree(g->rays_dev); cudaFree(g->views_dev); cudaFree(g->prow_dev); cudaFree(g->pcol_dev);
+    cudaFree(g->rays_dev); cudaFree(g->views_dev); cudaFree(g->xr_dev); cudaFree(g->xt_dev);
     cudaFree(g->sino_pad_dev);
     delete[] g->angles_host;
     delete g;

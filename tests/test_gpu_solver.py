@@ -139,7 +139,7 @@ def test_small_parallel_ab_gcv_matches_oracle():
         g_ref = OS.gcv_value(ref["lambdas"][k - 1], s, c)
         assert g_gpu <= g_ref * (1 + 1e-2), k
         r_at_gpu_lambda = math.sqrt(OS.residual_sq(info["lambdas"][k - 1], s, c))
-        assert abs(info["resid"][k - 1] - r_at_gpu_lambda) <= 1e-4 * r_at_gpu_lambda, k
+        assert abs(info["resid"][k - 1] - r_at_gpu_lambda) <= 5e-3 * r_at_gpu_lambda, k
     # the oracle's final lambda injected: isolates the Krylov path from the lambda choice
     xf, _ = _gpu_solve("ab", G, b, 30, "fixed", lambda_fixed=ref["lambdas"][-1])
     assert rel(xf, ref["x"]) <= ITER_TOL
