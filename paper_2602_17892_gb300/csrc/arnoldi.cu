@@ -16,6 +16,9 @@
 // Each pass starts where the previous one ended, so the rows it needs first are still in L2.
 // Block partial sums are FP32 (warp shuffles), the cross-block sum is FP64 in a fixed order
 // by the last block to finish, so results are reproducible run to run.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <mutex>
 
 #include "ct_internal.h"
@@ -29,7 +32,7 @@ constexpr double kBreakdownTol = 1e-6;   // FP32 reading of h_{k+1,k} <= tol ||M
 enum { M_DOTS = 0, M_UPD_DOTS = 1, M_UPD_NORM = 2, M_NORM = 3 };
 
 struct CgsArgs {
-    const float *W; int64_t ld; int nvec;       // rows W[0..nvec-1]
+    const void *W; int64_t ld; int nvec;        // rows W[0..nvec-1] (storage type T)
     float *q; int64_t L4;                        // vector (float4 count)
     const double *coef;                          // update coefficients (nvec), modes 1, 2
     double *partial; unsigned *counter;
@@ -52,7 +55,60 @@ constexpr int kGroup = 8;   // basis rows handled together: 8 independent loads 
 // row index of position p in a pass over n rows, forwards or backwards
 __device__ __forceinline__ int row_at(int p, int n, bool backwards) { return backwards ? n - 1 - p : p; }
 
-template <int MODE>
+// Loads and stores of 4 consecutive basis entries in the storage type of the basis; the
+// arithmetic is FP32 in every case.
+template <typename T> struct BasisIO;
+template <> struct BasisIO<float> {
+    static __device__ __forceinline__ float4 load(const void *W, int64_t i4)
+    {
+        return __ldg(reinterpret_cast<const float4 *>(W) + i4);
+    }
+    static __device__ __forceinline__ float4 store(void *W, int64_t i4, float4 v)
+    {
+        reinterpret_cast<float4 *>(W)[i4] = v;
+        return v;
+    }
+};
+template <> struct BasisIO<__nv_bfloat16> {
+    static __device__ __forceinline__ float4 load(const void *W, int64_t i4)
+    {
+        uint2 r = __ldg(reinterpret_cast<const uint2 *>(W) + i4);
+        float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&r.x));
+        float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&r.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    static __device__ __forceinline__ float4 store(void *W, int64_t i4, float4 v)
+    {
+        __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+        uint2 r;
+        r.x = *reinterpret_cast<unsigned *>(&a);
+        r.y = *reinterpret_cast<unsigned *>(&b);
+        reinterpret_cast<uint2 *>(W)[i4] = r;
+        float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+        return make_float4(fa.x, fa.y, fb.x, fb.y);      // the value actually stored
+    }
+};
+template <> struct BasisIO<__half> {
+    static __device__ __forceinline__ float4 load(const void *W, int64_t i4)
+    {
+        uint2 r = __ldg(reinterpret_cast<const uint2 *>(W) + i4);
+        float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&r.x));
+        float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&r.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    static __device__ __forceinline__ float4 store(void *W, int64_t i4, float4 v)
+    {
+        __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+        uint2 r;
+        r.x = *reinterpret_cast<unsigned *>(&a);
+        r.y = *reinterpret_cast<unsigned *>(&b);
+        reinterpret_cast<uint2 *>(W)[i4] = r;
+        float2 fa = __half22float2(a), fb = __half22float2(b);
+        return make_float4(fa.x, fa.y, fb.x, fb.y);
+    }
+};
+
+template <int MODE, typename T = float>
 __global__ void __launch_bounds__(kThreads) cgs_kernel(CgsArgs a)
 {
     if (a.stop[0] != 0) return;
@@ -70,7 +126,6 @@ __global__ void __launch_bounds__(kThreads) cgs_kernel(CgsArgs a)
     // Passes alternate direction so that each one starts on the rows the previous pass read
     // last (still in L2): K1 dots backwards, K2 update forwards then dots backwards, K3 forwards.
     const bool dots_backwards = true;
-    const float4 *W4 = reinterpret_cast<const float4 *>(a.W);
     float4 *q4 = reinterpret_cast<float4 *>(a.q);
     const int64_t ld4 = a.ld / 4;
     for (int64_t e0 = (int64_t)blockIdx.x * kThreads; e0 < a.L4; e0 += (int64_t)gridDim.x * kThreads) {
@@ -83,7 +138,7 @@ __global__ void __launch_bounds__(kThreads) cgs_kernel(CgsArgs a)
                     float4 w[kGroup];
 #pragma unroll
                     for (int u = 0; u < kGroup; ++u)
-                        w[u] = (p0 + u < nvec) ? __ldg(W4 + (int64_t)(p0 + u) * ld4 + e)
+                        w[u] = (p0 + u < nvec) ? BasisIO<T>::load(a.W, (int64_t)(p0 + u) * ld4 + e)
                                                : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                     for (int u = 0; u < kGroup; ++u) {
@@ -103,7 +158,7 @@ __global__ void __launch_bounds__(kThreads) cgs_kernel(CgsArgs a)
                     pd[u] = 0.f;
                     if (ok && p0 + u < nvec) {
                         const int i = row_at(p0 + u, nvec, dots_backwards);
-                        const float4 w = __ldg(W4 + (int64_t)i * ld4 + e);
+                        const float4 w = BasisIO<T>::load(a.W, (int64_t)i * ld4 + e);
                         pd[u] = fmaf(w.x, v.x, fmaf(w.y, v.y, fmaf(w.z, v.z, w.w * v.w)));
                     }
                 }
@@ -168,9 +223,11 @@ __global__ void __launch_bounds__(kThreads) cgs_kernel(CgsArgs a)
     }
 }
 
-// dst = src * aux[1]   (normalisation; skipped once a stop is recorded)
-__global__ void scale_kernel(const float4 *__restrict__ src, float4 *__restrict__ dst, int64_t L4,
-                             const double *aux, const int *stop)
+// dst = src * aux[1] rounded to the basis type (normalisation; skipped once a stop is
+// recorded); `cur` (optional) receives the stored values in FP32 for the next operator call.
+template <typename T>
+__global__ void scale_kernel(const float4 *__restrict__ src, void *__restrict__ dst, int64_t L4,
+                             const double *aux, const int *stop, float4 *__restrict__ cur)
 {
     if (stop[0] != 0) return;
     const float s = (float)aux[1];
@@ -178,7 +235,8 @@ __global__ void scale_kernel(const float4 *__restrict__ src, float4 *__restrict_
          e += (int64_t)gridDim.x * blockDim.x) {
         float4 v = src[e];
         v.x *= s; v.y *= s; v.z *= s; v.w *= s;
-        dst[e] = v;
+        float4 st = BasisIO<T>::store(dst, e, v);
+        if (cur) cur[e] = st;
     }
 }
 
@@ -190,11 +248,13 @@ static int grid_for(int64_t L4, int max_blocks)
     return (int)b;
 }
 
-// One CGS2 Arnoldi step on rows W[0..k] with q = M w_k; writes H column (FP64, k+2 entries)
-// and W[k+1].  `aux` / `stop` are device scratch words (see CgsArgs).
-cudaError_t arnoldi_step_dev(float *W, int64_t L, int64_t ld, int k, float *q, double *hcol,
-                             const ArnoldiScratch &sc, double *aux, int *stop, int step,
-                             bool reorth, cudaStream_t s)
+// One CGS2 Arnoldi step on rows W[0..k] (storage type T) with q = M w_k; writes the H column
+// (FP64, k+2 entries), W[k+1] and, when `cur` is not null, W[k+1] in FP32.  `aux` / `stop` are
+// device scratch words (see CgsArgs).
+template <typename T>
+static cudaError_t arnoldi_step_t(void *W, int64_t L, int64_t ld, int k, float *q, double *hcol,
+                                  const ArnoldiScratch &sc, double *aux, int *stop, int step,
+                                  bool reorth, float *cur, cudaStream_t s)
 {
     const int64_t L4 = L / 4;
     const int nvec = k + 1;
@@ -202,24 +262,47 @@ cudaError_t arnoldi_step_dev(float *W, int64_t L, int64_t ld, int k, float *q, d
     double *h1 = aux + 8, *h2 = aux + 8 + (sc.kmax + 2);
     CgsArgs a{W, ld, nvec, q, L4, nullptr, sc.partial, sc.counter, hcol, aux, h1, stop, step};
     size_t smem = sizeof(float) * (size_t)((nvec + 7) / 8 * 8 + kWarps * (nvec + 1));
-    cgs_kernel<M_DOTS><<<blocks, kThreads, smem, s>>>(a);
+    cgs_kernel<M_DOTS, T><<<blocks, kThreads, smem, s>>>(a);
     if (reorth) {
         a.coef = h1; a.coef_out = h2;
-        cgs_kernel<M_UPD_DOTS><<<blocks, kThreads, smem, s>>>(a);
+        cgs_kernel<M_UPD_DOTS, T><<<blocks, kThreads, smem, s>>>(a);
         a.coef = h2;
     } else {
         a.coef = h1;
     }
-    cgs_kernel<M_UPD_NORM><<<blocks, kThreads, smem, s>>>(a);
-    scale_kernel<<<grid_for(L4, sc.max_blocks), kThreads, 0, s>>>(
-        reinterpret_cast<const float4 *>(q), reinterpret_cast<float4 *>(W + (int64_t)(k + 1) * ld),
-        L4, aux, stop);
+    cgs_kernel<M_UPD_NORM, T><<<blocks, kThreads, smem, s>>>(a);
+    const size_t esz = sizeof(T);
+    scale_kernel<T><<<grid_for(L4, sc.max_blocks), kThreads, 0, s>>>(
+        reinterpret_cast<const float4 *>(q), static_cast<char *>(W) + (size_t)(k + 1) * ld * esz,
+        L4, aux, stop, reinterpret_cast<float4 *>(cur));
     return cudaGetLastError();
 }
 
-// beta = ||r||, w0 = r / beta (Alg. 1/2 line 3); beta stored in aux[2].
-cudaError_t normalize_first(const float *r, int64_t L, float *w0, const ArnoldiScratch &sc,
-                            double *aux, int *stop, cudaStream_t s)
+cudaError_t arnoldi_step_dev(float *W, int64_t L, int64_t ld, int k, float *q, double *hcol,
+                             const ArnoldiScratch &sc, double *aux, int *stop, int step,
+                             bool reorth, cudaStream_t s)
+{
+    return arnoldi_step_t<float>(W, L, ld, k, q, hcol, sc, aux, stop, step, reorth, nullptr, s);
+}
+
+cudaError_t arnoldi_step_basis(int basis, void *W, int64_t L, int64_t ld, int k, float *q,
+                               double *hcol, const ArnoldiScratch &sc, double *aux, int *stop,
+                               int step, bool reorth, float *cur, cudaStream_t s)
+{
+    switch (basis) {
+    case CT_BASIS_BF16:
+        return arnoldi_step_t<__nv_bfloat16>(W, L, ld, k, q, hcol, sc, aux, stop, step, reorth, cur, s);
+    case CT_BASIS_F16:
+        return arnoldi_step_t<__half>(W, L, ld, k, q, hcol, sc, aux, stop, step, reorth, cur, s);
+    default:
+        return arnoldi_step_t<float>(W, L, ld, k, q, hcol, sc, aux, stop, step, reorth, cur, s);
+    }
+}
+
+// beta = ||r||, w0 = r / beta (Alg. 1/2 line 3) in the basis type; beta stored in aux[2].
+cudaError_t normalize_first_basis(int basis, const float *r, int64_t L, void *w0,
+                                  const ArnoldiScratch &sc, double *aux, int *stop, float *cur,
+                                  cudaStream_t s)
 {
     const int64_t L4 = L / 4;
     const int blocks = grid_for(L4, sc.max_blocks);
@@ -227,15 +310,28 @@ cudaError_t normalize_first(const float *r, int64_t L, float *w0, const ArnoldiS
               nullptr, aux, nullptr, stop, 0};
     size_t smem = sizeof(float) * (size_t)(kWarps);
     cgs_kernel<M_NORM><<<blocks, kThreads, smem, s>>>(a);
-    scale_kernel<<<blocks, kThreads, 0, s>>>(reinterpret_cast<const float4 *>(r),
-                                             reinterpret_cast<float4 *>(w0), L4, aux, stop);
+    const float4 *r4 = reinterpret_cast<const float4 *>(r);
+    float4 *c4 = reinterpret_cast<float4 *>(cur);
+    if (basis == CT_BASIS_BF16)
+        scale_kernel<__nv_bfloat16><<<blocks, kThreads, 0, s>>>(r4, w0, L4, aux, stop, c4);
+    else if (basis == CT_BASIS_F16)
+        scale_kernel<__half><<<blocks, kThreads, 0, s>>>(r4, w0, L4, aux, stop, c4);
+    else
+        scale_kernel<float><<<blocks, kThreads, 0, s>>>(r4, w0, L4, aux, stop, c4);
     return cudaGetLastError();
+}
+
+cudaError_t normalize_first(const float *r, int64_t L, float *w0, const ArnoldiScratch &sc,
+                            double *aux, int *stop, cudaStream_t s)
+{
+    return normalize_first_basis(CT_BASIS_F32, r, L, w0, sc, aux, stop, nullptr, s);
 }
 
 // ----------------------------------------------------------------------------- x = x0 + W y
 // y holds K slots of K doubles; the slot of the last valid step kf = stop ? stop : K is used.
+template <typename T>
 __global__ void __launch_bounds__(kThreads) combine_kernel(
-    const float4 *__restrict__ W, int64_t ld4, int64_t L4, const double *__restrict__ Y, int K,
+    const void *__restrict__ W, int64_t ld4, int64_t L4, const double *__restrict__ Y, int K,
     int ystride, const int *stop, int kfixed, const float4 *__restrict__ x0, float4 *__restrict__ x)
 {
     __shared__ float sy[1024];
@@ -251,7 +347,7 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(
          e += (int64_t)gridDim.x * kThreads) {
         float4 v = x0 ? x0[e] : make_float4(0.f, 0.f, 0.f, 0.f);
         for (int i = 0; i < kf; ++i) {
-            float4 w = __ldg(W + i * ld4 + e);
+            float4 w = BasisIO<T>::load(W, i * ld4 + e);
             float c = sy[i];
             v.x = fmaf(c, w.x, v.x); v.y = fmaf(c, w.y, v.y);
             v.z = fmaf(c, w.z, v.z); v.w = fmaf(c, w.w, v.w);
@@ -260,15 +356,29 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(
     }
 }
 
+cudaError_t launch_combine_basis(int basis, const void *W, int64_t L, int64_t ld, const double *Y,
+                                 int K, int ystride, const int *stop, int kfixed, const float *x0,
+                                 float *x, int max_blocks, cudaStream_t s)
+{
+    const int64_t L4 = L / 4;
+    const int g = grid_for(L4, max_blocks);
+    const float4 *x04 = reinterpret_cast<const float4 *>(x0);
+    float4 *x4 = reinterpret_cast<float4 *>(x);
+    if (basis == CT_BASIS_BF16)
+        combine_kernel<__nv_bfloat16><<<g, kThreads, 0, s>>>(W, ld / 4, L4, Y, K, ystride, stop, kfixed, x04, x4);
+    else if (basis == CT_BASIS_F16)
+        combine_kernel<__half><<<g, kThreads, 0, s>>>(W, ld / 4, L4, Y, K, ystride, stop, kfixed, x04, x4);
+    else
+        combine_kernel<float><<<g, kThreads, 0, s>>>(W, ld / 4, L4, Y, K, ystride, stop, kfixed, x04, x4);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_combine(const float *W, int64_t L, int64_t ld, const double *Y, int K,
                            int ystride, const int *stop, int kfixed, const float *x0, float *x,
                            int max_blocks, cudaStream_t s)
 {
-    const int64_t L4 = L / 4;
-    combine_kernel<<<grid_for(L4, max_blocks), kThreads, 0, s>>>(
-        reinterpret_cast<const float4 *>(W), ld / 4, L4, Y, K, ystride, stop, kfixed,
-        reinterpret_cast<const float4 *>(x0), reinterpret_cast<float4 *>(x));
-    return cudaGetLastError();
+    return launch_combine_basis(CT_BASIS_F32, W, L, ld, Y, K, ystride, stop, kfixed, x0, x,
+                                max_blocks, s);
 }
 
 // r = b - r  (in place on r), float4 vectors

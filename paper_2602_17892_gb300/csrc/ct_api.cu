@@ -44,6 +44,17 @@ cudaError_t launch_combine(const float *W, int64_t L, int64_t ld, const double *
                            int ystride, const int *stop, int kfixed, const float *x0, float *x,
                            int max_blocks, cudaStream_t s);
 cudaError_t launch_rsub(const float *b, float *r, int64_t L, int max_blocks, cudaStream_t s);
+cudaError_t arnoldi_step_basis(int basis, void *W, int64_t L, int64_t ld, int k, float *q,
+                               double *hcol, const ArnoldiScratch &sc, double *aux, int *stop,
+                               int step, bool reorth, float *cur, cudaStream_t s);
+cudaError_t normalize_first_basis(int basis, const float *r, int64_t L, void *w0,
+                                  const ArnoldiScratch &sc, double *aux, int *stop, float *cur,
+                                  cudaStream_t s);
+cudaError_t launch_combine_basis(int basis, const void *W, int64_t L, int64_t ld, const double *Y,
+                                 int K, int ystride, const int *stop, int kfixed, const float *x0,
+                                 float *x, int max_blocks, cudaStream_t s);
+
+static size_t basis_bytes(int basis) { return basis == CT_BASIS_F32 ? 4 : 2; }
 
 constexpr int kMaxBlocks = 152 * 8;
 
@@ -104,8 +115,9 @@ using namespace ct;
 struct Workspace {
     int method = -1, K = 0, basis = 0;
     int *path = nullptr;    // per step: 1 = parallel small-solve path accepted
-    int64_t L = 0;          // basis row length in floats (multiple of 4, zero tail)
-    float *W = nullptr;     // (K+1) rows
+    int64_t L = 0;          // basis row length in entries (multiple of 4, zero tail)
+    void *W = nullptr;      // (K+1) rows in the basis storage type
+    float *cur = nullptr;   // 16-bit bases: the newest row in FP32 (operator input)
     float *q = nullptr;     // L
     float *img = nullptr;   // image scratch, img_ld floats
     float *sino = nullptr;  // padded sinogram scratch
@@ -119,7 +131,7 @@ struct Workspace {
 static void ws_free(Workspace *w)
 {
     if (!w) return;
-    cudaFree(w->W); cudaFree(w->q); cudaFree(w->img); cudaFree(w->sino); cudaFree(w->vec);
+    cudaFree(w->W); cudaFree(w->cur); cudaFree(w->q); cudaFree(w->img); cudaFree(w->sino); cudaFree(w->vec);
     cudaFree(w->H); cudaFree(w->Y); cudaFree(w->lam); cudaFree(w->res); cudaFree(w->aux);
     cudaFree(w->partial); cudaFree(w->counter); cudaFree(w->stop); cudaFree(w->path);
     delete w;
@@ -150,7 +162,8 @@ static ct_status ws_get(ct_geom *g, int method, int K, int basis, Workspace **ou
     w = new Workspace();
     w->method = method; w->K = K; w->basis = basis; w->L = L;
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = dalloc(&w->W, (size_t)(K + 1) * L);
+    if (e == cudaSuccess) e = dalloc((char **)&w->W, (size_t)(K + 1) * L * basis_bytes(basis));
+    if (e == cudaSuccess && basis != CT_BASIS_F32) e = dalloc(&w->cur, (size_t)L);
     if (e == cudaSuccess) e = dalloc(&w->q, (size_t)L);
     if (e == cudaSuccess) e = dalloc(&w->vec, (size_t)L);
     if (e == cudaSuccess) e = dalloc(&w->img, (size_t)img_ld);
@@ -234,38 +247,6 @@ static Ray2D make_ray(const ct_geom_desc *d, int view, int bin)
     return r;
 }
 
-// Widest detector footprint (bins, with the kernel's margins) of a 32 x 8 pixel block over all
-// views, rounded up; the backprojector stages that many bins per view in shared memory.
-static int bp_footprint_slot(const ct_geom_desc &d)
-{
-    const double cm = (d.nx - 1) / 2.0, rm = (d.ny - 1) / 2.0, h = d.pixel;
-    int widest = 4;
-    for (int v = 0; v < d.n_views; ++v) {
-        const double cs = cos(d.angles[v]), sn = sin(d.angles[v]);
-        for (int c0 = 0; c0 < d.nx; c0 += 32)
-            for (int r0 = 0; r0 < d.ny; r0 += 8) {
-                double fmn = 1e300, fmx = -1e300;
-                const double cc[2] = {c0 - cm, std::min(c0 + 31, d.nx - 1) - cm};
-                const double rr[2] = {r0 - rm, std::min(r0 + 7, d.ny - 1) - rm};
-                for (int a = 0; a < 2; ++a)
-                    for (int b = 0; b < 2; ++b) {
-                        double X = cc[a] * h, Y = rr[b] * h, u;
-                        if (d.kind == CT_PARALLEL2D) u = X * cs + Y * sn;
-                        else u = d.sdd * (-X * sn + Y * cs) / (d.sid - (X * cs + Y * sn));
-                        double fj = u / d.pitch_u + (d.n_det_u - 1) / 2.0 + 2.0;
-                        fmn = std::min(fmn, fj);
-                        fmx = std::max(fmx, fj);
-                    }
-                fmn = std::min(std::max(fmn, 0.0), d.n_det_u + 2.0);
-                fmx = std::min(std::max(fmx, 0.0), d.n_det_u + 2.0);
-                int w = (int)(floor(fmx) - floor(fmn)) + 4;
-                widest = std::max(widest, w);
-            }
-    }
-    int slot = (int)round_up(widest + 2, 8);     // +2: FP32 rounding of the corner positions
-    return std::min(slot, 256);                  // wider views read the sinogram directly
-}
-
 extern "C" {
 
 const char *ct_last_error(void) { return g_last_error.c_str(); }
@@ -317,9 +298,8 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     dg.kind = d->kind; dg.nx = d->nx; dg.ny = d->ny; dg.nz = 1;
     dg.h = (float)d->pixel; dg.n_views = d->n_views; dg.ndu = d->n_det_u; dg.ndv = 1;
     dg.pitch_u = (float)d->pitch_u; dg.pitch_v = 1.f; dg.sid = (float)d->sid; dg.sdd = (float)d->sdd;
-    dg.xr_ld = (int)round_up(d->nx + 2, 8);
-    dg.xt_ld = (int)round_up(d->ny + 2, 8);
-    dg.bp_slot = bp_footprint_slot(g->desc);
+    dg.row_pairs_ld = (int)round_up(d->nx + 1, 16);
+    dg.col_pairs_ld = (int)round_up(d->ny + 1, 16);
     dg.sino_ld = (int)round_up(d->n_det_u + 4, 4);
 
     std::vector<Ray2D> rays((size_t)g->m);
@@ -344,8 +324,8 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     if (e == cudaSuccess) e = cudaMemcpy(g->rays_dev, rays.data(), sizeof(Ray2D) * rays.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = dalloc(&g->views_dev, views.size());
     if (e == cudaSuccess) e = cudaMemcpy(g->views_dev, views.data(), sizeof(ViewBP) * views.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = dalloc(&g->xr_dev, (size_t)d->ny * dg.xr_ld);
-    if (e == cudaSuccess) e = dalloc(&g->xt_dev, (size_t)d->nx * dg.xt_ld);
+    if (e == cudaSuccess) e = dalloc(&g->prow_dev, (size_t)d->ny * dg.row_pairs_ld);
+    if (e == cudaSuccess) e = dalloc(&g->pcol_dev, (size_t)d->nx * dg.col_pairs_ld);
     if (e == cudaSuccess) e = dalloc(&g->sino_pad_dev, (size_t)d->n_views * dg.sino_ld);
     if (e != cudaSuccess) {
         set_error(std::string("ct_geom_create: ") + cudaGetErrorString(e));
@@ -368,7 +348,7 @@ void ct_geom_destroy(ct_geom *g)
         ws_free(ex->ws[1]);
         delete ex;
     }
-    cudaFree(g->rays_dev); cudaFree(g->views_dev); cudaFree(g->xr_dev); cudaFree(g->xt_dev);
+    cudaFree(g->rays_dev); cudaFree(g->views_dev); cudaFree(g->prow_dev); cudaFree(g->pcol_dev);
     cudaFree(g->sino_pad_dev);
     delete[] g->angles_host;
     delete g;
@@ -439,7 +419,7 @@ static ct_status check_opts(const ct_hybrid_opts *o)
     if (o->rule == CT_LAMBDA_FIXED && !(o->lambda_fixed >= 0)) return einval("solver: lambda_fixed must be >= 0");
     if (o->rule == CT_LAMBDA_DP && (!(o->noise_norm >= 0) || !(o->tau > 0)))
         return einval("solver: DP needs noise_norm >= 0 and tau > 0");
-    if (o->basis != CT_BASIS_F32) return einval("solver: only the FP32 basis is built for 2D solves");
+    if (o->basis < CT_BASIS_F32 || o->basis > CT_BASIS_F16) return einval("solver: bad basis type");
     return CT_OK;
 }
 
@@ -525,15 +505,15 @@ extern "C" ct_status ab_gmres_hybrid(ct_geom *g, const float *b_dev, const float
             CT_CUDA(launch_image_pairs(g, w->img, nullptr, s));
             CT_CUDA(launch_joseph2d(g, w->q, sld, 2, nullptr, s));
             CT_CUDA(launch_rsub(w->vec, w->q, L, kMaxBlocks, s));
-            CT_CUDA(normalize_first(w->q, L, w->W, sc, w->aux, w->stop, s));
+            CT_CUDA(normalize_first_basis(o->basis, w->q, L, w->W, sc, w->aux, w->stop, w->cur, s));
         } else {
-            CT_CUDA(normalize_first(w->vec, L, w->W, sc, w->aux, w->stop, s));
+            CT_CUDA(normalize_first_basis(o->basis, w->vec, L, w->W, sc, w->aux, w->stop, w->cur, s));
         }
     }
     const int ldh = w->K + 1;
     for (int step = 1; step <= K; ++step) {
         const int k = step - 1;
-        float *wk = w->W + (int64_t)k * ld;
+        const float *wk = w->cur ? w->cur : static_cast<float *>(w->W) + (int64_t)k * ld;
         {
             CT_PHASE(CT_PH_BACK, 1, s);
             CT_CUDA(launch_pixbp2d(g, wk, w->img, w->stop, s));       // line 5: B w_k
@@ -548,8 +528,8 @@ extern "C" ct_status ab_gmres_hybrid(ct_geom *g, const float *b_dev, const float
         }
         {
             CT_PHASE(CT_PH_ARNOLDI, o->reorth ? 4 : 3, s);               // lines 6-11
-            CT_CUDA(arnoldi_step_dev(w->W, L, ld, k, w->q, w->H + (int64_t)k * ldh,
-                                     sc, w->aux, w->stop, step, o->reorth != 0, s));
+            CT_CUDA(arnoldi_step_basis(o->basis, w->W, L, ld, k, w->q, w->H + (int64_t)k * ldh,
+                                       sc, w->aux, w->stop, step, o->reorth != 0, w->cur, s));
         }
     }
     if ((st = run_small_solves(w, o, s, dp_target)) != CT_OK) return st;        // lines 12-13
@@ -557,8 +537,8 @@ extern "C" ct_status ab_gmres_hybrid(ct_geom *g, const float *b_dev, const float
     {
         CT_PHASE(CT_PH_OTHER, u0_dev ? 2 : 1, s);
         if (u0_dev) CT_CUDA(launch_pad_sino(g, u0_dev, w->sino, s));
-        CT_CUDA(launch_combine(w->W, L, ld, w->Y, K, w->K, w->stop, 0, u0_dev ? w->sino : nullptr,
-                               w->q, kMaxBlocks, s));
+        CT_CUDA(launch_combine_basis(o->basis, w->W, L, ld, w->Y, K, w->K, w->stop, 0,
+                                     u0_dev ? w->sino : nullptr, w->q, kMaxBlocks, s));
     }
     {
         CT_PHASE(CT_PH_BACK, 1, s);
@@ -600,12 +580,12 @@ extern "C" ct_status ba_gmres_hybrid(ct_geom *g, const float *b_dev, const float
         } else {
             CT_CUDA(launch_pixbp2d(g, w->sino, w->vec, nullptr, s));
         }
-        CT_CUDA(normalize_first(w->vec, L, w->W, sc, w->aux, w->stop, s));
+        CT_CUDA(normalize_first_basis(o->basis, w->vec, L, w->W, sc, w->aux, w->stop, w->cur, s));
     }
     const int ldh = w->K + 1;
     for (int step = 1; step <= K; ++step) {
         const int k = step - 1;
-        float *wk = w->W + (int64_t)k * ld;
+        const float *wk = w->cur ? w->cur : static_cast<float *>(w->W) + (int64_t)k * ld;
         {
             CT_PHASE(CT_PH_LAYOUT, 1, s);
             CT_CUDA(launch_image_pairs(g, wk, w->stop, s));           // line 5: A w_k
@@ -620,8 +600,8 @@ extern "C" ct_status ba_gmres_hybrid(ct_geom *g, const float *b_dev, const float
         }
         {
             CT_PHASE(CT_PH_ARNOLDI, o->reorth ? 4 : 3, s);
-            CT_CUDA(arnoldi_step_dev(w->W, L, ld, k, w->q, w->H + (int64_t)k * ldh,
-                                     sc, w->aux, w->stop, step, o->reorth != 0, s));
+            CT_CUDA(arnoldi_step_basis(o->basis, w->W, L, ld, k, w->q, w->H + (int64_t)k * ldh,
+                                       sc, w->aux, w->stop, step, o->reorth != 0, w->cur, s));
         }
     }
     if ((st = run_small_solves(w, o, s, dp_target)) != CT_OK) return st;        // lines 12-13
@@ -632,8 +612,8 @@ extern "C" ct_status ba_gmres_hybrid(ct_geom *g, const float *b_dev, const float
             CT_CUDA(cudaMemsetAsync(w->img, 0, sizeof(float) * L, s));
             CT_CUDA(cudaMemcpyAsync(w->img, x0_dev, sizeof(float) * g->n, cudaMemcpyDeviceToDevice, s));
         }
-        CT_CUDA(launch_combine(w->W, L, ld, w->Y, K, w->K, w->stop, 0, x0_dev ? w->img : nullptr,
-                               w->q, kMaxBlocks, s));
+        CT_CUDA(launch_combine_basis(o->basis, w->W, L, ld, w->Y, K, w->K, w->stop, 0,
+                                     x0_dev ? w->img : nullptr, w->q, kMaxBlocks, s));
         CT_CUDA(cudaMemcpyAsync(x_dev, w->q, sizeof(float) * g->n, cudaMemcpyDeviceToDevice, s));
     }
     return finish(w, o, info, s);

@@ -47,9 +47,8 @@ struct DeviceGeom {
     int n_views, ndu, ndv;
     float pitch_u, pitch_v, sid, sdd;
     // padded layouts
-    int xr_ld;          // XR row length (floats): >= nx + 2
-    int xt_ld;          // XT row length (floats): >= ny + 2
-    int bp_slot;        // backprojector shared-memory footprint slot (bins per view)
+    int row_pairs_ld;   // P_row row length in float2: >= nx + 1
+    int col_pairs_ld;   // P_col row length in float2: >= ny + 1
     int sino_ld;        // padded sinogram row length: ndu + 4 (2 zero bins each side)
     // tables
     const Ray2D *rays;  // m rays (2D)
@@ -67,8 +66,8 @@ struct ct_geom {
     // device allocations owned by the geometry
     ct::Ray2D *rays_dev;
     ct::ViewBP *views_dev;
-    float *xr_dev;      // [ny][xr_ld] zero-bordered image rows
-    float *xt_dev;      // [nx][xt_ld] zero-bordered image columns (transposed)
+    float2 *prow_dev;   // [ny][row_pairs_ld] pairs along x
+    float2 *pcol_dev;   // [nx][col_pairs_ld] pairs along y
     float *sino_pad_dev;  // [n_views * ndv][sino_ld]
     // solver workspace (grown on demand)
     struct Workspace *ws;
@@ -79,7 +78,7 @@ namespace ct {
 // ----------------------------------------------------------------------------- projectors
 // Every launcher takes an optional device stop word: when non-null and non-zero at kernel
 // start, the kernel returns at once (a solver that met breakdown skips the remaining steps).
-// Image x (row-major, n floats) -> the two zero-bordered layouts used by the Joseph kernel.
+// Image x (row-major, n floats) -> the two padded pair layouts used by the Joseph kernel.
 cudaError_t launch_image_pairs(const ct_geom *g, const float *x, const int *stop, cudaStream_t s);
 // y[view][bin] -> padded sinogram rows (row length sino_ld, bin j at index j + 2).
 cudaError_t launch_pad_sino(const ct_geom *g, const float *y, float *ypad, cudaStream_t s);
@@ -89,7 +88,6 @@ cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, con
 // pixel-driven B from a padded sinogram (row length sino_ld)
 cudaError_t launch_pixbp2d(const ct_geom *g, const float *ypad, float *x, const int *stop,
                            cudaStream_t s);
-size_t pixbp2d_smem_bytes(int slot);
 
 // ----------------------------------------------------------------------------- Arnoldi
 struct ArnoldiScratch {

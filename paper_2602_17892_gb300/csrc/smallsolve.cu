@@ -9,26 +9,29 @@
 //     rho^2(lambda) = sum_i (lambda^2 c_i / (sigma_i^2 + lambda^2))^2 + c_{k+1}^2,
 //     trace(I - H H_lambda) = (k+1) - sum_i sigma_i^2 / (sigma_i^2 + lambda^2).
 // GB300 executes FP64 at 1/64 of the FP32 rate, so a sequential FP64 bidiagonal QR (one thread,
-// O(k^2) dependent rotations) costs milliseconds.  The fast path keeps every step parallel:
-//  1. Givens QR of H_k (FP64): H_k = G [R; 0], g = G^T beta e1; c_{k+1} = g_{k+1}.
-//  2. Householder reduction of R to LOWER bidiagonal L = P^T R Q with P^T g = beta0 e1 (the
-//     first left reflector maps g to a multiple of e1, later left reflectors never touch row 1).
-//     Then c_i = beta0 u_i(1): only first components of the left singular vectors are needed.
-//  3. sigma_i: eigenvalues of the Golub-Kahan tridiagonal T of L (zero diagonal, off-diagonals
-//     alpha_1, beta_2, alpha_2, ...): FP32 bisection (one thread per sigma_i, Sturm counts of
-//     the LDL^T recurrence) gives a bracket, FP64 safeguarded Newton on det(theta I - T)
-//     refines it.
-//  4. c_i^2 = 2 beta0^2 z_i(1)^2 with z_i(1)^2 = det(sigma_i I - T_{2:n}) / p'(sigma_i), the
-//     first-component formula of a symmetric tridiagonal's eigenvectors.
-//     For clusters (relative gap < 1e-6) the formula is ill-conditioned; their total weight is a
-//     contour integral of e1^T (zI - T)^{-1} e1 around the cluster, shared by its members
-//     (GCV and DP depend on a cluster only through that total, to O(gap)).
-//  5. Self-check: sum_i c_i^2 must equal beta0^2 (U orthogonal).  If it does not, the kernel
+// O(k^2) dependent rotations) costs milliseconds.  The fast path keeps the work parallel:
+//  1. Householder reduction of H_k to (k+1) x k LOWER bidiagonal Bd = P^T H_k Q with P e1 = e1
+//     (the left reflectors act on rows >= 2), so c_i = beta u_i(1) with u_i the left singular
+//     vectors of Bd: only first components are needed.  Reflectors are applied one row or one
+//     column per thread.
+//  2. sigma_i: eigenvalues of the Golub-Kahan tridiagonal T of Bd (order 2k+1, zero diagonal,
+//     off-diagonals alpha_1, beta_2, alpha_2, ..., beta_{k+1}; eigenvalues +-sigma_i and 0):
+//     FP32 bisection (one thread per sigma_i, Sturm counts) gives a bracket, FP64 safeguarded
+//     Newton on det(theta I - T) refines it; brackets that touch a neighbour's are first
+//     isolated by FP64 Sturm-count bisection.
+//  3. c_i^2 = 2 beta^2 z_i(1)^2 with z_i(1)^2 = det(sigma_i I - T_{2:n}) / p'(sigma_i), the
+//     first-component formula of a symmetric tridiagonal's eigenvectors.  For clusters
+//     (relative gap < 1e-6) the formula is ill-conditioned; their total weight is a contour
+//     integral of e1^T (zI - T)^{-1} e1 around the cluster, shared by its members (GCV and DP
+//     depend on a cluster only through that total, to O(gap)).
+//  4. c_{k+1}^2 = beta^2 / ||u||^2 with u the left null vector of Bd (an O(k) recurrence).
+//  5. Self-check: sum_i c_i^2 + c_{k+1}^2 must equal beta^2.  If it does not, the kernel
 //     recomputes sigma and c with the exact sequential path: Householder upper
 //     bidiagonalisation of H_k and implicit-shift Golub-Kahan QR.
-// y is formed only where it is needed (the last step, or a breakdown step): the bidiagonal
-// Tikhonov problem min ||Bd z - g||^2 + lambda^2 ||z||^2 is eliminated with O(k) Givens
-// rotations and y = Q z applies the stored right reflectors.
+// The lambda functions are evaluated by the whole block (two lambdas at a time).  y is formed
+// only where it is needed (the last step, or a breakdown step): the damped bidiagonal problem
+// min ||Bd z - beta e1||^2 + lambda^2 ||z||^2 is eliminated with 2k Givens rotations, and
+// y = Q z applies the stored right reflectors.
 //
 // Parameter readings shared with the FP64 CPU oracle: GCV is evaluated on 256 log-spaced
 // lambda in [sigma_1 1e-8, sigma_1], the first grid minimum is refined by 40 golden-section
@@ -328,40 +331,9 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
     }
 
     // ================================================================ fast path
-    givens_qr();                                   // R in rows 0..k-1 of A, g (k+1)
-    // first left reflector: g[0..k-1] -> beta0 e1, applied to R
-    if (warp == 0) {
-        double s2 = 0.0;
-        for (int i = 1 + lane; i < k; i += 32) s2 += g[i] * g[i];
-        s2 = warp_sum_d(s2);
-        if (lane == 0) {
-            double bt, tau, sc;
-            make_reflector(g[0], s2, bt, tau, sc);
-            misc[0] = bt; misc[1] = tau; misc[2] = sc;
-            misc[3] = g[k];                      // c_{k+1}
-        }
-    }
-    __syncthreads();
-    {
-        const double tau = misc[1], sc = misc[2];
-        if (tau != 0.0) {
-            for (int i = 1 + tid; i < k; i += kSSThreads) g[i] *= sc;   // reflector vector
-            __syncthreads();
-            for (int l = warp; l < k; l += nwarps) {
-                double *col = A + (size_t)l * lda;
-                const double c0 = col[0];
-                double w = 0.0;
-                for (int i = 1 + lane; i < k; i += 32) w += g[i] * col[i];
-                w = (warp_sum_d(w) + c0) * tau;
-                __syncwarp();
-                if (lane == 0) col[0] -= w;
-                for (int i = 1 + lane; i < k; i += 32) col[i] -= w * g[i];
-            }
-        }
-    }
-    __syncthreads();
-    const double beta0 = misc[0], ck1 = misc[3];
-    // lower bidiagonalisation: right reflector on row j (cols j..k-1), left on col j (rows j+1..)
+    // lower bidiagonalisation of H_k ((k+1) x k) with e1 fixed: right reflector on row j
+    // (columns j..k-1) -> alpha_j = d[j]; left reflector on column j (rows j+1..k) ->
+    // beta_{j+1} = e[j].  Rows/columns are applied one per thread (no shuffles).
     for (int j = 0; j < k; ++j) {
         if (warp == 0) {
             double s2 = 0.0;
@@ -378,60 +350,63 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
             const double bt = misc[0], tau = misc[1], sc = misc[2];
             for (int l = j + 1 + tid; l < k; l += kSSThreads) A[l * lda + j] *= sc;
             __syncthreads();
-            if (tid == 0) { A[j * lda + j] = bt; d[j] = bt; tauR[j] = tau; }
             if (tau != 0.0) {
-                for (int i = j + 1 + warp; i < k; i += nwarps) {
-                    const double aij = A[j * lda + i];
-                    double w = 0.0;
-                    for (int l = j + 1 + lane; l < k; l += 32) w += A[l * lda + j] * A[l * lda + i];
-                    w = (warp_sum_d(w) + aij) * tau;
-                    __syncwarp();
-                    if (lane == 0) A[j * lda + i] -= w;
-                    for (int l = j + 1 + lane; l < k; l += 32) A[l * lda + i] -= w * A[l * lda + j];
+                for (int i = j + 1 + tid; i <= k; i += kSSThreads) {   // row i
+                    double w0 = A[j * lda + i], w1 = 0.0;
+                    int l = j + 1;
+                    for (; l + 1 < k; l += 2) {
+                        w0 += A[l * lda + j] * A[l * lda + i];
+                        w1 += A[(l + 1) * lda + j] * A[(l + 1) * lda + i];
+                    }
+                    if (l < k) w0 += A[l * lda + j] * A[l * lda + i];
+                    const double w = (w0 + w1) * tau;
+                    A[j * lda + i] -= w;
+                    for (int m = j + 1; m < k; ++m) A[m * lda + i] -= w * A[m * lda + j];
                 }
+            }
+            if (tid == 0) { A[j * lda + j] = bt; d[j] = bt; tauR[j] = tau; }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double s2 = 0.0;
+            for (int i = j + 2 + lane; i <= k; i += 32) s2 += A[j * lda + i] * A[j * lda + i];
+            s2 = warp_sum_d(s2);
+            if (lane == 0) {
+                double bt, tau, sc;
+                make_reflector(A[j * lda + j + 1], s2, bt, tau, sc);
+                misc[0] = bt; misc[1] = tau; misc[2] = sc;
             }
         }
         __syncthreads();
-        if (j + 1 < k) {
-            if (warp == 0) {
-                double s2 = 0.0;
-                for (int i = j + 2 + lane; i < k; i += 32) s2 += A[j * lda + i] * A[j * lda + i];
-                s2 = warp_sum_d(s2);
-                if (lane == 0) {
-                    double bt, tau, sc;
-                    make_reflector(A[j * lda + j + 1], s2, bt, tau, sc);
-                    misc[0] = bt; misc[1] = tau; misc[2] = sc;
-                }
-            }
-            __syncthreads();
+        {
             const double bt = misc[0], tau = misc[1], sc = misc[2];
-            for (int i = j + 2 + tid; i < k; i += kSSThreads) A[j * lda + i] *= sc;
+            for (int i = j + 2 + tid; i <= k; i += kSSThreads) A[j * lda + i] *= sc;
             __syncthreads();
-            if (tid == 0) { A[j * lda + j + 1] = bt; e[j] = bt; }
             if (tau != 0.0) {
-                for (int l = j + 1 + warp; l < k; l += nwarps) {
+                for (int l = j + 1 + tid; l < k; l += kSSThreads) {     // column l
                     double *col = A + (size_t)l * lda;
-                    const double c0 = col[j + 1];
-                    double w = 0.0;
-                    for (int i = j + 2 + lane; i < k; i += 32) w += A[j * lda + i] * col[i];
-                    w = (warp_sum_d(w) + c0) * tau;
-                    __syncwarp();
-                    if (lane == 0) col[j + 1] -= w;
-                    for (int i = j + 2 + lane; i < k; i += 32) col[i] -= w * A[j * lda + i];
+                    double w0 = col[j + 1], w1 = 0.0;
+                    int i = j + 2;
+                    for (; i + 1 <= k; i += 2) {
+                        w0 += A[j * lda + i] * col[i];
+                        w1 += A[j * lda + i + 1] * col[i + 1];
+                    }
+                    if (i <= k) w0 += A[j * lda + i] * col[i];
+                    const double w = (w0 + w1) * tau;
+                    col[j + 1] -= w;
+                    for (int m = j + 2; m <= k; ++m) col[m] -= w * A[j * lda + m];
                 }
             }
-            __syncthreads();
+            if (tid == 0) { A[j * lda + j + 1] = bt; e[j] = bt; }
         }
+        __syncthreads();
     }
-    // L: diag d[0..k-1] (alpha), subdiag e[0..k-2] (beta_{j+1} = L[j+1][j])
-    // Golub-Kahan tridiagonal T (n = 2k) off-diagonals alpha_0, beta_1, alpha_1, ..., scaled
-    const int n = 2 * k;
+    // Golub-Kahan tridiagonal T (n = 2k+1, zero diagonal) of the (k+1) x k lower bidiagonal:
+    // off-diagonals alpha_0, beta_1, alpha_1, ..., alpha_{k-1}, beta_k; eigenvalues +-sigma_i, 0
+    const int n = 2 * k + 1;
     if (warp == 0) {
         double mx = 0.0;
-        for (int i = lane; i < k; i += 32) {
-            mx = fmax(mx, fabs(d[i]));
-            if (i < k - 1) mx = fmax(mx, fabs(e[i]));
-        }
+        for (int i = lane; i < k; i += 32) mx = fmax(mx, fmax(fabs(d[i]), fabs(e[i])));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if (lane == 0) misc[4] = mx;
@@ -444,9 +419,9 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
         t2[j] = t * t;
         t2f[j] = (float)(t * t);
     }
-    if (tid == 0) misc[5] = 0.0;
     __syncthreads();
-    // sigma_i (i-th largest), one thread each.  FP32 bisection with Sturm counts gives a bracket
+    // sigma_i (i-th largest), one thread each: FP32 bisection with Sturm counts; for x > 0 the
+    // count of eigenvalues below x is k + 1 + #{sigma < x}
     for (int i = tid; i < k; i += kSSThreads) {
         float lo = 0.f, hi = 2.f;
         const int target = k - i;               // #{sigma < x} >= target  <=>  sigma_i < x
@@ -460,7 +435,7 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
                 if (fabsf(dd) < 1e-30f) dd = -1e-30f;
                 cnt += dd < 0.f;
             }
-            if (cnt - k >= target) hi = x; else lo = x;
+            if (cnt - (k + 1) >= target) hi = x; else lo = x;
         }
         lo32[i] = lo;
         hi32[i] = hi;
@@ -474,11 +449,11 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
                          (i == k - 1 || (double)hi32[i + 1] * (1.0 + 2e-4) < blo);
         if (!iso) {
             const int tgt = k - i;
-            int clo = count64(t2, n, blo) - k, chi = count64(t2, n, bhi) - k;
+            int clo = count64(t2, n, blo) - (k + 1), chi = count64(t2, n, bhi) - (k + 1);
             if (!(clo <= tgt - 1 && chi >= tgt)) { blo = 0.0; bhi = 2.0; clo = 0; chi = k; }
             for (int it = 0; it < 200 && chi - clo > 1 && bhi - blo > 1e-15 * bhi; ++it) {
                 double mid = 0.5 * (blo + bhi);
-                int cm = count64(t2, n, mid) - k;
+                int cm = count64(t2, n, mid) - (k + 1);
                 if (cm >= tgt) { bhi = mid; chi = cm; } else { blo = mid; clo = cm; }
             }
         }
@@ -500,13 +475,13 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
             if (bhi - blo <= 4e-16 * bhi) break;
         }
         // first component of the eigenvector: z1^2 = det(th I - T_{2:n}) / p'(th), both at the
-        // last evaluation point (within a rounding error of the root)
+        // last evaluation point (within a rounding error of the root); c_i^2 = 2 beta^2 z1^2
         int ex2;
         double p2, dp2;
         charpoly(t2, 1, n, th_eval, p2, dp2, ex2);
         double z1sq = (dp != 0.0) ? ldexp(p2 / dp, ex2 - ex) : -1.0;
         sig[i] = th;                               // scaled units until the end of this block
-        double c2 = 2.0 * beta0 * beta0 * z1sq;
+        double c2 = 2.0 * beta * beta * z1sq;
         cv[i] = (c2 >= 0.0 && isfinite(c2)) ? c2 : -1.0;   // c_i^2 for now
     }
     __syncthreads();
@@ -524,6 +499,18 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
             i = b + 1;
         }
         misc[7] = (double)nc;
+        // c_{k+1}: the left null vector of the lower bidiagonal (u_1 = 1,
+        // u_{i+1} = -alpha_i u_i / beta_{i+1}) gives c_{k+1}^2 = beta^2 / ||u||^2
+        double sq = 1.0, uu = 1.0;
+        int exs = 0;
+        bool exact = false;
+        for (int i = 0; i < k; ++i) {
+            if (e[i] == 0.0) { exact = true; break; }
+            uu *= -d[i] / e[i];
+            sq += uu * uu;
+            if (sq > 0x1p+500) { sq = ldexp(sq, -500); uu = ldexp(uu, -250); exs += 500; }
+        }
+        misc[3] = exact ? 0.0 : fabs(beta) / sqrt(ldexp(sq, 0)) * ldexp(1.0, -exs / 2);
     }
     __syncthreads();
     {
@@ -531,7 +518,7 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
         for (int q = warp; q < nc; q += nwarps) {
             const int a = clist[2 * q], b = clist[2 * q + 1];
             const double c = 0.5 * (sig[a] + sig[b]), half = 0.5 * (sig[a] - sig[b]);
-            double R = c + sig[b];                                  // the mirrored cluster at -sigma
+            double R = c;                                           // the eigenvalue 0 of T
             if (a > 0) R = fmin(R, sig[a - 1] - c);
             if (b + 1 < k) R = fmin(R, c - sig[b + 1]);
             const double rho = fmax(R / 3.0, 10.0 * half);
@@ -549,7 +536,7 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
             double w = rho * (cs * rr - sn * ri);                   // Re(rho e^{i ph} r(z))
             w = warp_sum_d(w) / 32.0;
             if (lane == 0) {
-                const double each = 2.0 * beta0 * beta0 * w / (double)(b - a + 1);
+                const double each = 2.0 * beta * beta * w / (double)(b - a + 1);
                 for (int j = a; j <= b; ++j) cv[j] = (each >= 0.0 && isfinite(each)) ? each : -1.0;
             }
         }
@@ -559,21 +546,21 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
         sig[i] *= tscale;
         cv[i] = (cv[i] >= 0.0) ? sqrt(cv[i]) : -1.0;
     }
-    if (tid == 0) cv[k] = fabs(ck1);
+    if (tid == 0) cv[k] = misc[3];
     __syncthreads();
-    // self-check: sum c_i^2 = beta0^2 and the sigma are distinct and ordered
+    // self-check: sum c_i^2 = beta^2 (U orthogonal) and the sigma non-increasing
     if (warp == 0) {
         double s = 0.0;
         int bad = 0;
-        for (int i = lane; i < k; i += 32) {
-            if (cv[i] < 0.0 || !isfinite(sig[i])) bad = 1;
+        for (int i = lane; i <= k; i += 32) {
+            if (cv[i] < 0.0 || !isfinite(cv[i]) || (i < k && !isfinite(sig[i]))) bad = 1;
             else s += cv[i] * cv[i];
             if (i + 1 < k && !(sig[i] >= sig[i + 1])) bad = 1;
         }
         s = warp_sum_d(s);
         bad = __any_sync(0xffffffffu, bad);
         if (lane == 0) {
-            double ref = beta0 * beta0;
+            double ref = beta * beta;
             misc[6] = (bad || !(fabs(s - ref) <= 1e-10 * ref)) ? 1.0 : 0.0;
             misc[8] = sig[0];
         }
@@ -581,11 +568,6 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
     __syncthreads();
     const bool fast = misc[6] == 0.0;
     if (tid == 0 && P.path) *P.path = fast ? 1 : 0;
-    // fast-path y needs (d, e, beta0 e1) of the lower bidiagonal and reflectors on coords j..
-    if (fast && need_y && tid == 0) {
-        for (int i = 0; i < k; ++i) { dsv[i] = d[i]; esv[i] = (i < k - 1) ? e[i] : 0.0; gsv[i] = 0.0; }
-        gsv[0] = beta0;
-    }
 
     if (!fast) {
         // ================================================================ exact sequential path
@@ -673,6 +655,36 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
     const double s1 = misc[8];
 
     // ---------------- lambda
+    // rho^2(lambda) and trace(lambda) are evaluated by the whole block: threads 0-127 take
+    // lambda_A, 128-255 lambda_B, one term each (k <= 160 < 2 * 128)
+    double *sig2 = rot;                  // sigma_i^2 (rot is free after the cluster pass)
+    for (int i = tid; i < k; i += kSSThreads) sig2[i] = sig[i] * sig[i];
+    __syncthreads();
+    auto eval2 = [&](double lamA, double lamB, double &rA, double &tA, double &rB, double &tB) {
+        const int half = tid >> 7, t = tid & 127;
+        const double l2 = half ? lamB * lamB : lamA * lamA;
+        double r = 0.0, tr = 0.0;
+        for (int i = t; i < k; i += 128) {
+            double den = sig2[i] + l2;
+            double f = l2 / den;
+            double fc = f * cv[i];
+            r += fc * fc;
+            tr += sig2[i] / den;
+        }
+        r = warp_sum_d(r);
+        tr = warp_sum_d(tr);
+        __syncthreads();                                 // misc[16..31] free from earlier use
+        if (lane == 0) { misc[16 + 2 * warp] = r; misc[17 + 2 * warp] = tr; }
+        __syncthreads();
+        double s0 = 0, s1_ = 0, s2_ = 0, s3 = 0;
+        for (int w = 0; w < 4; ++w) {
+            s0 += misc[16 + 2 * w]; s1_ += misc[17 + 2 * w];
+            s2_ += misc[24 + 2 * w]; s3 += misc[25 + 2 * w];
+        }
+        const double ck = cv[k] * cv[k];
+        rA = s0 + ck; tA = (double)(k + 1) - s1_;
+        rB = s2_ + ck; tB = (double)(k + 1) - s3;
+    };
     if (P.rule == CT_LAMBDA_FIXED) {
         lam = P.lambda_fixed;
     } else if (!(s1 > 0.0)) {
@@ -683,7 +695,7 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
             double lt = s1 * pow(10.0, expo);
             double l2 = lt * lt, r = 0.0, tr = 0.0;
             for (int i = 0; i < k; ++i) {
-                double s2 = sig[i] * sig[i];
+                double s2 = sig2[i];
                 double inv = 1.0 / (s2 + l2);
                 double f = l2 * inv;
                 r += (f * cv[i]) * (f * cv[i]);
@@ -694,108 +706,98 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
             red[t] = r / (tr * tr);
         }
         __syncthreads();
-        if (warp == 0) {
+        if (tid == 0) {
             int ibest = 0;
-            if (lane == 0) {
-                double best = red[0];
-                for (int t = 1; t < kGcvGrid; ++t)
-                    if (red[t] < best) { best = red[t]; ibest = t; }
-            }
-            ibest = __shfl_sync(0xffffffffu, ibest, 0);
-            const double gbest = red[ibest];
-            auto gridlog = [&](int t) {
-                double expo = (t == kGcvGrid - 1) ? 0.0 : -8.0 + t * (8.0 / (kGcvGrid - 1));
-                return log(s1 * pow(10.0, expo));
-            };
-            double a = gridlog(ibest > 0 ? ibest - 1 : 0);
-            double b = gridlog(ibest < kGcvGrid - 1 ? ibest + 1 : kGcvGrid - 1);
-            const double invphi = 0.6180339887498949;
-            for (int it = 0; it < 40; ++it) {
-                double x1 = b - invphi * (b - a), x2 = a + invphi * (b - a);
-                double r1, t1, r2, t2_;
-                eval_lambda_warp(exp(x1), sig, cv, k, r1, t1);
-                eval_lambda_warp(exp(x2), sig, cv, k, r2, t2_);
-                if (r1 / (t1 * t1) <= r2 / (t2_ * t2_)) b = x2; else a = x1;
-            }
-            double lr = exp(0.5 * (a + b)), rr, tt;
-            eval_lambda_warp(lr, sig, cv, k, rr, tt);
-            if (rr / (tt * tt) > gbest) {
-                double expo = (ibest == kGcvGrid - 1) ? 0.0 : -8.0 + ibest * (8.0 / (kGcvGrid - 1));
-                lr = s1 * pow(10.0, expo);
-            }
-            if (lane == 0) misc[10] = lr;
+            double best = red[0];
+            for (int t = 1; t < kGcvGrid; ++t)
+                if (red[t] < best) { best = red[t]; ibest = t; }
+            misc[12] = (double)ibest;
+            misc[13] = best;
         }
         __syncthreads();
-        lam = misc[10];
+        const int ibest = (int)misc[12];
+        const double gbest = misc[13];
+        auto gridlam = [&](int t) {
+            double expo = (t == kGcvGrid - 1) ? 0.0 : -8.0 + t * (8.0 / (kGcvGrid - 1));
+            return s1 * pow(10.0, expo);
+        };
+        double a = log(gridlam(ibest > 0 ? ibest - 1 : 0));
+        double b = log(gridlam(ibest < kGcvGrid - 1 ? ibest + 1 : kGcvGrid - 1));
+        const double invphi = 0.6180339887498949;
+        for (int it = 0; it < 40; ++it) {
+            double x1 = b - invphi * (b - a), x2 = a + invphi * (b - a);
+            double r1, t1, r2, t2_;
+            eval2(exp(x1), exp(x2), r1, t1, r2, t2_);
+            if (r1 / (t1 * t1) <= r2 / (t2_ * t2_)) b = x2; else a = x1;
+        }
+        double lr = exp(0.5 * (a + b)), rr, tt, rdum, tdum;
+        eval2(lr, lr, rr, tt, rdum, tdum);
+        if (rr / (tt * tt) > gbest) lr = gridlam(ibest);
+        lam = lr;
     } else {  // CT_LAMBDA_DP
-        if (warp == 0) {
-            const double target = P.dp_target;
-            double lo = log(s1 * 1e-8), hi = log(s1);
-            double r, t, out;
-            eval_lambda_warp(exp(lo), sig, cv, k, r, t);
-            if (sqrt(r) >= target) {
-                out = exp(lo);
-            } else {
-                eval_lambda_warp(exp(hi), sig, cv, k, r, t);
-                if (sqrt(r) <= target) {
-                    out = exp(hi);
-                } else {
-                    for (int it = 0; it < 60; ++it) {
-                        double mid = 0.5 * (lo + hi);
-                        eval_lambda_warp(exp(mid), sig, cv, k, r, t);
-                        if (sqrt(r) < target) lo = mid; else hi = mid;
-                    }
-                    out = exp(0.5 * (lo + hi));
-                }
+        const double target = P.dp_target;
+        double lo = log(s1 * 1e-8), hi = log(s1);
+        double rlo, tlo, rhi, thi;
+        eval2(exp(lo), exp(hi), rlo, tlo, rhi, thi);
+        if (sqrt(rlo) >= target) {
+            lam = exp(lo);
+        } else if (sqrt(rhi) <= target) {
+            lam = exp(hi);
+        } else {
+            for (int it = 0; it < 60; ++it) {
+                double mid = 0.5 * (lo + hi), r, t, rd, td;
+                eval2(exp(mid), exp(mid), r, t, rd, td);
+                if (sqrt(r) < target) lo = mid; else hi = mid;
             }
-            if (lane == 0) misc[10] = out;
+            lam = exp(0.5 * (lo + hi));
         }
-        __syncthreads();
-        lam = misc[10];
     }
 
-    // ---------------- projected residual
-    if (warp == 0) {
-        double r, t;
-        eval_lambda_warp(lam, sig, cv, k, r, t);
-        if (lane == 0) misc[11] = r;
+    // ---------------- projected residual and y
+    {
+        double r, t, rd, td;
+        eval2(lam, lam, r, t, rd, td);
+        if (tid == 0) misc[11] = r;
     }
+    __syncthreads();
     if (need_y) {
         if (tid == 0) {
             if (fast) {
-                // lower -> upper bidiagonal by left rotations of rows (j, j+1), rhs beta0 e1
-                double dj = dsv[0];
-                for (int j = 0; j < k - 1; ++j) {
-                    double c, s, r;
-                    givens(dj, esv[j], c, s, r);          // zero beta_{j+1} at (j+1, j)
-                    double ajp = dsv[j + 1];
-                    dsv[j] = r;
-                    double ej = s * ajp;
-                    dj = c * ajp;
-                    double g0 = gsv[j], g1 = gsv[j + 1];
-                    gsv[j] = c * g0 + s * g1;
-                    gsv[j + 1] = -s * g0 + c * g1;
-                    esv[j] = ej;
+                // min || Bd z - beta e1 ||^2 + lambda^2 ||z||^2 for the (k+1) x k lower
+                // bidiagonal (alpha = d, beta_{i+1} = e[i]): per column one rotation removes the
+                // lambda row, one the subdiagonal beta (the damped Golub-Kahan QR), then back
+                // substitution on the upper bidiagonal (rho = dsv, theta = esv, rhs z)
+                double rb = d[0], phib = beta;
+                for (int i = 0; i < k; ++i) {
+                    double c1, s1r, r;
+                    givens(rb, lam, c1, s1r, r);
+                    const double ph = c1 * phib;
+                    double cc, ss, rr;
+                    givens(r, e[i], cc, ss, rr);
+                    dsv[i] = rr;
+                    z[i] = cc * ph;
+                    if (i + 1 < k) { esv[i] = ss * d[i + 1]; rb = cc * d[i + 1]; }
+                    else esv[i] = 0.0;
+                    phib = -ss * ph;
                 }
-                dsv[k - 1] = dj;
-                esv[k - 1] = 0.0;
-            }
-            // Elden: eliminate lambda I of [Bd; lambda I] with 2k Givens rotations
-            double mu = lam, rr = 0.0;
-            for (int i = 0; i < k; ++i) {
-                double a = dsv[i], b = (i < k - 1) ? esv[i] : 0.0, gi = gsv[i];
-                double c, s, r;
-                givens(a, mu, c, s, r);
-                dsv[i] = r;
-                esv[i] = c * b;
-                z[i] = c * gi + s * rr;
-                double f = -s * b;
-                double t = -s * gi + c * rr;
-                if (i < k - 1) {
-                    double c2, s2, r2;
-                    givens(lam, f, c2, s2, r2);
-                    mu = r2;
-                    rr = s2 * t;
+            } else {
+                // Elden: eliminate lambda I of [Bd; lambda I] (upper bidiagonal) with 2k rotations
+                double mu = lam, rr = 0.0;
+                for (int i = 0; i < k; ++i) {
+                    double a = dsv[i], b = (i < k - 1) ? esv[i] : 0.0, gi = gsv[i];
+                    double c, s, r;
+                    givens(a, mu, c, s, r);
+                    dsv[i] = r;
+                    esv[i] = c * b;
+                    z[i] = c * gi + s * rr;
+                    double f = -s * b;
+                    double t = -s * gi + c * rr;
+                    if (i < k - 1) {
+                        double c2, s2, r2;
+                        givens(lam, f, c2, s2, r2);
+                        mu = r2;
+                        rr = s2 * t;
+                    }
                 }
             }
             for (int i = k - 1; i >= 0; --i) {
@@ -804,8 +806,8 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
             }
         }
         __syncthreads();
-        // y = Q z with the stored right reflectors: fast path reflector j acts on coordinates
-        // j..k-1 (vector in row j of A), exact path on j+1..k-1 (vector in row j, cols j+2..)
+        // y = Q z with the stored right reflectors: fast-path reflector j acts on coordinates
+        // j..k-1 (vector in row j of A), the exact path's on j+1..k-1 (row j, columns j+2..)
         if (warp == 0) {
             const int first = fast ? k - 1 : k - 3;
             for (int j = first; j >= 0; --j) {
