@@ -132,45 +132,66 @@ __global__ void __launch_bounds__(kThreads) cgs_kernel(CgsArgs a)
         const int64_t e = e0 + tid;
         const bool ok = e < a.L4;
         float4 v = ok ? q4[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+        // rows of a group in flight while the previous group is consumed (software pipeline)
+        auto load_group = [&](float4 *buf, int p0, bool backwards) {
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u)
+                buf[u] = (ok && p0 + u < nvec)
+                             ? BasisIO<T>::load(a.W, (int64_t)row_at(p0 + u, nvec, backwards) * ld4 + e)
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+        };
         if (MODE == M_UPD_DOTS || MODE == M_UPD_NORM) {
-            if (ok) {
-                for (int p0 = 0; p0 < nvec; p0 += kGroup) {
-                    float4 w[kGroup];
-#pragma unroll
-                    for (int u = 0; u < kGroup; ++u)
-                        w[u] = (p0 + u < nvec) ? BasisIO<T>::load(a.W, (int64_t)(p0 + u) * ld4 + e)
-                                               : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                    for (int u = 0; u < kGroup; ++u) {
-                        const float c = scoef[p0 + u];
-                        v.x = fmaf(-c, w[u].x, v.x); v.y = fmaf(-c, w[u].y, v.y);
-                        v.z = fmaf(-c, w[u].z, v.z); v.w = fmaf(-c, w[u].w, v.w);
-                    }
-                }
-                q4[e] = v;
-            }
-        }
-        if (MODE == M_DOTS || MODE == M_UPD_DOTS) {
+            float4 wb[kGroup], wn[kGroup];
+            load_group(wb, 0, false);
             for (int p0 = 0; p0 < nvec; p0 += kGroup) {
-                float pd[kGroup];
+                if (p0 + kGroup < nvec) load_group(wn, p0 + kGroup, false);
 #pragma unroll
                 for (int u = 0; u < kGroup; ++u) {
-                    pd[u] = 0.f;
-                    if (ok && p0 + u < nvec) {
-                        const int i = row_at(p0 + u, nvec, dots_backwards);
-                        const float4 w = BasisIO<T>::load(a.W, (int64_t)i * ld4 + e);
-                        pd[u] = fmaf(w.x, v.x, fmaf(w.y, v.y, fmaf(w.z, v.z, w.w * v.w)));
-                    }
+                    const float c = scoef[p0 + u];          // zero beyond nvec
+                    v.x = fmaf(-c, wb[u].x, v.x); v.y = fmaf(-c, wb[u].y, v.y);
+                    v.z = fmaf(-c, wb[u].z, v.z); v.w = fmaf(-c, wb[u].w, v.w);
                 }
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1)
+                for (int u = 0; u < kGroup; ++u) wb[u] = wn[u];
+            }
+            if (ok) q4[e] = v;
+        }
+        if (MODE == M_DOTS || MODE == M_UPD_DOTS) {
+            float4 wb[kGroup], wn[kGroup];
+            load_group(wb, 0, dots_backwards);
+            for (int p0 = 0; p0 < nvec; p0 += kGroup) {
+                if (p0 + kGroup < nvec) load_group(wn, p0 + kGroup, dots_backwards);
+                float pd[kGroup];
 #pragma unroll
-                    for (int u = 0; u < kGroup; ++u) pd[u] += __shfl_xor_sync(0xffffffffu, pd[u], o);
-                if (lane == 0) {
+                for (int u = 0; u < kGroup; ++u)
+                    pd[u] = fmaf(wb[u].x, v.x, fmaf(wb[u].y, v.y, fmaf(wb[u].z, v.z, wb[u].w * v.w)));
+                // transpose reduction: after the xor-16/8/4 exchange stages lane l holds a partial
+                // sum of group row (l >> 2) over 8 lanes; xor-2/1 complete it (9 shuffles for 8 rows)
+                const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+                float q4v[4], q2v[2], q1;
 #pragma unroll
-                    for (int u = 0; u < kGroup; ++u)
-                        if (p0 + u < nvec) acc[warp * ncol + row_at(p0 + u, nvec, dots_backwards)] += pd[u];
+                for (int j = 0; j < 4; ++j) {
+                    float send = b4 ? pd[j] : pd[j + 4];
+                    float keep = b4 ? pd[j + 4] : pd[j];
+                    q4v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
                 }
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    float send = b3 ? q4v[j] : q4v[j + 2];
+                    float keep = b3 ? q4v[j + 2] : q4v[j];
+                    q2v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+                }
+                {
+                    float send = b2 ? q2v[0] : q2v[1];
+                    float keep = b2 ? q2v[1] : q2v[0];
+                    q1 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+                }
+                q1 += __shfl_xor_sync(0xffffffffu, q1, 2);
+                q1 += __shfl_xor_sync(0xffffffffu, q1, 1);
+                const int pr = p0 + (lane >> 2);
+                if ((lane & 3) == 0 && pr < nvec) acc[warp * ncol + row_at(pr, nvec, dots_backwards)] += q1;
+#pragma unroll
+                for (int u = 0; u < kGroup; ++u) wb[u] = wn[u];
             }
         }
         float nn = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, v.w * v.w)));

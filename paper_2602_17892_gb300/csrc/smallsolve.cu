@@ -37,6 +37,8 @@
 // lambda in [sigma_1 1e-8, sigma_1], the first grid minimum is refined by 40 golden-section
 // steps in log lambda on the neighbouring bracket (kept only if not worse); DP solves
 // rho(lambda) = tau ||e|| by 60 bisection steps in log lambda over the same range.
+#include <algorithm>
+
 #include "ct_internal.h"
 
 namespace ct {
@@ -75,9 +77,28 @@ __device__ void eval_lambda_warp(double lam, const double *sig, const double *cv
 __device__ __forceinline__ void givens(double a, double b, double &c, double &s, double &r)
 {
     if (b == 0.0) { c = 1.0; s = 0.0; r = a; return; }
+    const double r2 = fma(a, a, b * b);
+    if (r2 > 1e-280 && r2 < 1e280) {         // one rsqrt instead of hypot and two divisions
+        const double ri = rsqrt(r2);
+        c = a * ri;
+        s = b * ri;
+        r = r2 * ri;
+        return;
+    }
     r = hypot(a, b);
     c = a / r;
     s = b / r;
+}
+
+// 1/x in FP64 from the FP32 reciprocal and two Newton steps (relative error ~1e-16)
+__device__ __forceinline__ double rcp64(double x)
+{
+    const double ax = fabs(x);
+    if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
+    double r = (double)__frcp_rn((float)x);
+    r = r * fma(-x, r, 2.0);
+    r = r * fma(-x, r, 2.0);
+    return r;
 }
 
 // Householder vector (LAPACK dlarfg convention): H = I - tau [1; v][1; v]^T maps [alpha; x]
@@ -423,19 +444,33 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
     // sigma_i (i-th largest), one thread each: FP32 bisection with Sturm counts; for x > 0 the
     // count of eigenvalues below x is k + 1 + #{sigma < x}
     for (int i = tid; i < k; i += kSSThreads) {
+        // three Sturm counts per step (independent recurrences, interleaved): the bracket
+        // shrinks fourfold per step
         float lo = 0.f, hi = 2.f;
         const int target = k - i;               // #{sigma < x} >= target  <=>  sigma_i < x
-        for (int it = 0; it < 140 && (hi - lo) > 2e-6f * hi; ++it) {
-            float x = 0.5f * (lo + hi);
-            float dd = -x;
-            if (fabsf(dd) < 1e-30f) dd = -1e-30f;
-            int cnt = dd < 0.f;
+        for (int it = 0; it < 80 && (hi - lo) > 2e-6f * hi; ++it) {
+            const float w = hi - lo;
+            const float x1 = lo + 0.25f * w, x2 = lo + 0.5f * w, x3 = lo + 0.75f * w;
+            float d1 = -x1, d2 = -x2, d3 = -x3;
+            if (fabsf(d1) < 1e-30f) d1 = -1e-30f;
+            if (fabsf(d2) < 1e-30f) d2 = -1e-30f;
+            if (fabsf(d3) < 1e-30f) d3 = -1e-30f;
+            int c1 = d1 < 0.f, c2 = d2 < 0.f, c3 = d3 < 0.f;
             for (int j = 1; j < n; ++j) {
-                dd = -x - __fdividef(t2f[j - 1], dd);
-                if (fabsf(dd) < 1e-30f) dd = -1e-30f;
-                cnt += dd < 0.f;
+                const float t = t2f[j - 1];
+                d1 = -x1 - __fdividef(t, d1);
+                d2 = -x2 - __fdividef(t, d2);
+                d3 = -x3 - __fdividef(t, d3);
+                if (fabsf(d1) < 1e-30f) d1 = -1e-30f;
+                if (fabsf(d2) < 1e-30f) d2 = -1e-30f;
+                if (fabsf(d3) < 1e-30f) d3 = -1e-30f;
+                c1 += d1 < 0.f; c2 += d2 < 0.f; c3 += d3 < 0.f;
             }
-            if (cnt - (k + 1) >= target) hi = x; else lo = x;
+            const int off = k + 1;
+            if (c1 - off >= target) hi = x1;
+            else if (c2 - off >= target) { lo = x1; hi = x2; }
+            else if (c3 - off >= target) { lo = x2; hi = x3; }
+            else lo = x3;
         }
         lo32[i] = lo;
         hi32[i] = hi;
@@ -665,11 +700,10 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
         const double l2 = half ? lamB * lamB : lamA * lamA;
         double r = 0.0, tr = 0.0;
         for (int i = t; i < k; i += 128) {
-            double den = sig2[i] + l2;
-            double f = l2 / den;
-            double fc = f * cv[i];
+            const double inv = rcp64(sig2[i] + l2);
+            double fc = l2 * inv * cv[i];
             r += fc * fc;
-            tr += sig2[i] / den;
+            tr += sig2[i] * inv;
         }
         r = warp_sum_d(r);
         tr = warp_sum_d(tr);
@@ -696,7 +730,7 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
             double l2 = lt * lt, r = 0.0, tr = 0.0;
             for (int i = 0; i < k; ++i) {
                 double s2 = sig2[i];
-                double inv = 1.0 / (s2 + l2);
+                double inv = rcp64(s2 + l2);
                 double f = l2 * inv;
                 r += (f * cv[i]) * (f * cv[i]);
                 tr += s2 * inv;
@@ -864,7 +898,10 @@ cudaError_t launch_small_solve_batched(const SmallSolveParams &p, cudaStream_t s
 {
     cudaError_t e = set_smem_attr();
     if (e != cudaSuccess) return e;
-    small_solve_kernel<<<p.k, kSSThreads, small_solve_smem_bytes(p.k), s>>>(p, 1);
+    // at most one CTA per SM: the FP64 pipe (two lanes per clock per SM on GB300) is the bound,
+    // so two projected problems sharing an SM would each run at half speed
+    const size_t smem = std::max(small_solve_smem_bytes(p.k), (size_t)(116 * 1024));
+    small_solve_kernel<<<p.k, kSSThreads, smem, s>>>(p, 1);
     return cudaGetLastError();
 }
 
