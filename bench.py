@@ -36,6 +36,9 @@ ITERS = 100
 TAU = 1.01
 L2_FLUSH_BYTES = 256 << 20
 SM_COUNT = 152
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the kernels
+# as they are now (profiles/*_fan512.md); None once a kernel changes until it is re-captured
+KERNEL_TRAFFIC = {"pixel_B": 2.08e6, "joseph_A": 13.18e6, "arnoldi_cgs2": None}
 
 
 def _peaks():
@@ -274,7 +277,7 @@ def bench_ours(args, rank, world, local_rank):
     if dom == "arnoldi_cgs2":
         ach = kernels[dom]["gbs"]
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": KERNEL_TRAFFIC.get(dom),
                 "peak_source": peaks["source"]}
     else:
         # ALU/LSU-bound projectors (working set L2-resident): one 8-byte tap load per Joseph
@@ -284,7 +287,7 @@ def bench_ours(args, rank, world, local_rank):
         peak = per_clk * SM_COUNT * f_clk / 1e9
         ach = kernels[dom]["gups"]
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak,
-                "unit": "Gupdates/s", "frac": ach / peak, "traffic": None,
+                "unit": "Gupdates/s", "frac": ach / peak, "traffic": KERNEL_TRAFFIC.get(dom),
                 "peak_source": f"{per_clk:g} updates/clk/SM x {SM_COUNT} SMs x "
                                f"{peaks['sm_max_mhz']:.0f} MHz"}
 
