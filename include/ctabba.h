@@ -149,6 +149,45 @@ ct_status ab_gmres_hybrid(ct_geom *g, const float *b_dev, const float *u0_dev, f
 ct_status ba_gmres_hybrid(ct_geom *g, const float *b_dev, const float *x0_dev, float *x_dev,
                           const ct_hybrid_opts *o, ct_hybrid_info *info, ct_stream_t stream);
 
+/* ------------------------------------------------------------------ tile autotuning */
+
+/* Time the candidate launch shapes of the projectors on this geometry (Joseph A: 128, 256 or
+ * 512 rays per block; pixel-driven B: blocks of 32 x 4, 32 x 8 or 32 x 16 pixels) and keep the
+ * fastest for later calls on `g`.  Geometries of the same kind and sizes reuse an earlier
+ * result.  Runs a few dozen projector launches on `stream`, synchronises it, and allocates two
+ * temporary device buffers.  The chosen shapes are returned in *a_threads and *b_rows (either
+ * may be NULL). */
+ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, int *a_threads, int *b_rows);
+
+/* ------------------------------------------------------------------ batched solves */
+
+/* Many independent problems (for instance CT slices of uneven size and geometry) solved
+ * together.  The first ct_batch_solve captures every problem's whole solve (Algorithm 1 or 2:
+ * all iterations, the hybrid steps and the final iterate) into one CUDA graph whose branches are
+ * independent, so the GPU runs the problems concurrently; later calls with the same buffers and
+ * noise norms replay that graph with a single launch.  Each problem needs its own ct_geom (the
+ * geometry owns the problem's workspace; ct_batch_create allocates it).
+ * methods[i]: 0 = hybrid AB-GMRES, 1 = hybrid BA-GMRES, 2 = AB when m < n, else BA (Sec. 2.1:
+ * AB-GMRES for underdetermined, BA-GMRES for overdetermined systems).  All problems share `o`
+ * (its history pointers must be NULL) except the discrepancy-principle noise norms, which
+ * ct_batch_solve takes per problem.  autotune != 0 runs ct_geom_autotune on every geometry. */
+typedef struct ct_batch ct_batch;
+ct_status ct_batch_create(int n_prob, ct_geom *const *geoms, const int *methods,
+                          const ct_hybrid_opts *o, int autotune, ct_batch **out);
+/* b_dev[i]: m_i floats, x_dev[i]: n_i floats (device pointers in host arrays of n_prob
+ * entries); noise_norms: host array (used by CT_LAMBDA_DP, may be NULL otherwise); info: host
+ * array of n_prob entries (may be NULL).  Initial guesses are zero.  Synchronises `stream`.
+ * Calls on one batch must not overlap. */
+ct_status ct_batch_solve(ct_batch *bt, const float *const *b_dev, float *const *x_dev,
+                         const double *noise_norms, ct_hybrid_info *info, ct_stream_t stream);
+/* Kernel launches one replay of the batch's graph performs (0 before the first solve). */
+int64_t ct_batch_launches(const ct_batch *bt);
+void ct_batch_destroy(ct_batch *bt);
+/* One call: create a batch (with autotuning), solve it once, destroy it. */
+ct_status abba_solve(int n_prob, ct_geom *const *geoms, const float *const *b_dev,
+                     float *const *x_dev, const int *methods, const ct_hybrid_opts *o,
+                     const double *noise_norms, ct_hybrid_info *info, ct_stream_t stream);
+
 /* ------------------------------------------------------------------ building blocks */
 
 /* One Arnoldi orthogonalisation step (Sec. 2.1, Eq. (Hessenberg); Alg. 1 lines 6-11).

@@ -26,7 +26,8 @@ BASIS = {"f32": 0, "bf16": 1, "f16": 2}
 EXPORTS = ("ct_geom_create", "ct_geom_destroy", "ct_geom_dims", "ct_geom_work", "ct_forward_A", "ct_back_B",
            "ct_hybrid_opts_default", "ab_gmres_hybrid", "ba_gmres_hybrid", "ct_arnoldi_step", "ct_arnoldi_step_noalloc",
            "ct_projected_solve", "ct_status_string", "ct_last_error", "ct_profile_enable",
-           "ct_profile_collect", "ct_launch_count")
+           "ct_profile_collect", "ct_launch_count", "ct_geom_autotune", "ct_batch_create",
+           "ct_batch_solve", "ct_batch_launches", "ct_batch_destroy", "abba_solve")
 PHASES = ("forward_A", "back_B", "layout", "arnoldi", "small_solve", "other")
 
 
@@ -96,6 +97,18 @@ def load(path: str = LIB_PATH):
     lib.ct_profile_collect.argtypes = [ctypes.POINTER(PhaseTime)]
     lib.ct_launch_count.restype = ctypes.c_int64
     lib.ct_launch_count.argtypes = []
+    lib.ct_geom_autotune.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.ct_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(HybridOpts), ctypes.c_int, ctypes.POINTER(vp)]
+    lib.ct_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(HybridInfo), vp]
+    lib.ct_batch_launches.argtypes = [vp]
+    lib.ct_batch_launches.restype = ctypes.c_int64
+    lib.ct_batch_destroy.argtypes = [vp]
+    lib.ct_batch_destroy.restype = None
+    lib.abba_solve.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(HybridOpts),
+                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(HybridInfo), vp]
     lib.ct_status_string.argtypes = [ctypes.c_int]
     lib.ct_status_string.restype = ctypes.c_char_p
     lib.ct_last_error.restype = ctypes.c_char_p
@@ -256,3 +269,79 @@ def ct_profile_collect() -> dict:
 
 def ct_launch_count() -> int:
     return int(load().ct_launch_count())
+
+
+def ct_geom_autotune(g: Geom, stream=None):
+    """Time the projector launch shapes on this geometry; returns (a_threads, b_rows)."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(load().ct_geom_autotune(g.handle, _stream(stream), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def _info_dict(inf):
+    return dict(iters_done=inf.iters_done, beta=inf.beta, final_lambda=inf.final_lambda,
+                final_resid=inf.final_resid, status=STATUS_NAMES[inf.status],
+                fast_path_steps=inf.fast_path_steps)
+
+
+class Batch:
+    """ct_batch: many independent problems solved through one captured CUDA graph."""
+
+    def __init__(self, geoms, methods=None, max_iters=30, rule="gcv", lambda_fixed=0.0, tau=1.01,
+                 reorth=1, basis="f32", autotune=True):
+        lib = load()
+        self.geoms = list(geoms)
+        n = len(self.geoms)
+        o, _, _ = _opts(max_iters, rule, lambda_fixed, 0.0, tau, reorth, basis, False)
+        self._o = o
+        gh = (ctypes.c_void_p * n)(*[g.handle.value for g in self.geoms])
+        mth = None
+        if methods is not None:
+            m = [{"ab": 0, "ba": 1, "auto": 2}.get(x, x) for x in methods]
+            mth = (ctypes.c_int * n)(*m)
+        h = ctypes.c_void_p()
+        _check(lib.ct_batch_create(n, gh, mth, ctypes.byref(o), 1 if autotune else 0, ctypes.byref(h)))
+        self.handle = h
+        self.n = n
+
+    def solve(self, b_list, x_list, noise_norms=None, stream=None):
+        lib = load()
+        n = self.n
+        bp = (ctypes.c_void_p * n)(*[_ptr(b).value for b in b_list])
+        xp = (ctypes.c_void_p * n)(*[_ptr(x).value for x in x_list])
+        nz = (ctypes.c_double * n)(*noise_norms) if noise_norms is not None else None
+        infos = (HybridInfo * n)()
+        _check(lib.ct_batch_solve(self.handle, bp, xp, nz, infos, _stream(stream)))
+        return [_info_dict(infos[i]) for i in range(n)]
+
+    def launches(self) -> int:
+        return int(load().ct_batch_launches(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ct_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def abba_solve(geoms, b_list, x_list, methods=None, max_iters=30, rule="gcv", lambda_fixed=0.0,
+               noise_norms=None, tau=1.01, basis="f32", stream=None):
+    """One-shot batched solve (creates, solves and destroys a ct_batch)."""
+    lib = load()
+    n = len(geoms)
+    o, _, _ = _opts(max_iters, rule, lambda_fixed, 0.0, tau, 1, basis, False)
+    gh = (ctypes.c_void_p * n)(*[g.handle.value for g in geoms])
+    mth = None
+    if methods is not None:
+        mth = (ctypes.c_int * n)(*[{"ab": 0, "ba": 1, "auto": 2}.get(x, x) for x in methods])
+    bp = (ctypes.c_void_p * n)(*[_ptr(b).value for b in b_list])
+    xp = (ctypes.c_void_p * n)(*[_ptr(x).value for x in x_list])
+    nz = (ctypes.c_double * n)(*noise_norms) if noise_norms is not None else None
+    infos = (HybridInfo * n)()
+    _check(lib.abba_solve(n, gh, bp, xp, mth, ctypes.byref(o), nz, infos, _stream(stream)))
+    return [_info_dict(infos[i]) for i in range(n)]

@@ -8,7 +8,9 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -301,6 +303,8 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     dg.row_pairs_ld = (int)round_up(d->nx + 1, 16);
     dg.col_pairs_ld = (int)round_up(d->ny + 1, 16);
     dg.sino_ld = (int)round_up(d->n_det_u + 4, 4);
+    dg.tune_a_threads = 256;
+    dg.tune_b_rows = 8;
 
     std::vector<Ray2D> rays((size_t)g->m);
     g->a_samples = 0;
@@ -423,9 +427,17 @@ static ct_status check_opts(const ct_hybrid_opts *o)
     return CT_OK;
 }
 
+static ct_status read_info(Workspace *w, const ct_hybrid_opts *o, ct_hybrid_info *info);
+
 static ct_status finish(Workspace *w, const ct_hybrid_opts *o, ct_hybrid_info *info, cudaStream_t s)
 {
     CT_CUDA(cudaStreamSynchronize(s));
+    return read_info(w, o, info);
+}
+
+// host copies of the solve's status, lambda and residual histories (after a synchronisation)
+static ct_status read_info(Workspace *w, const ct_hybrid_opts *o, ct_hybrid_info *info)
+{
     int stop[2];
     double beta;
     CT_CUDA(cudaMemcpy(stop, w->stop, sizeof(stop), cudaMemcpyDeviceToHost));
@@ -477,16 +489,15 @@ static ct_status run_small_solves(Workspace *w, const ct_hybrid_opts *o, cudaStr
     return CT_OK;
 }
 
-extern "C" ct_status ab_gmres_hybrid(ct_geom *g, const float *b_dev, const float *u0_dev,
-                                     float *x_dev, const ct_hybrid_opts *o, ct_hybrid_info *info,
-                                     ct_stream_t stream)
+// Algorithm 1, enqueued on s without any host synchronisation (graph-capturable once the
+// workspace exists); the caller reads the results with read_info after synchronising.
+static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev, float *x_dev,
+                            const ct_hybrid_opts *o, cudaStream_t s, Workspace **wout)
 {
-    if (!g || !b_dev || !x_dev) return einval("ab_gmres_hybrid: null argument");
-    ct_status st = check_opts(o);
-    if (st != CT_OK) return st;
-    cudaStream_t s = (cudaStream_t)stream;
+    ct_status st;
     Workspace *w;
     if ((st = ws_get(g, 0, o->max_iters, o->basis, &w)) != CT_OK) return st;
+    *wout = w;
     const int K = o->max_iters;
     const int64_t L = w->L, ld = w->L;
     const int sld = g->dg.sino_ld;
@@ -544,19 +555,30 @@ extern "C" ct_status ab_gmres_hybrid(ct_geom *g, const float *b_dev, const float
         CT_PHASE(CT_PH_BACK, 1, s);
         CT_CUDA(launch_pixbp2d(g, w->q, x_dev, nullptr, s));
     }
-    return finish(w, o, info, s);
+    return CT_OK;
 }
 
-extern "C" ct_status ba_gmres_hybrid(ct_geom *g, const float *b_dev, const float *x0_dev,
+extern "C" ct_status ab_gmres_hybrid(ct_geom *g, const float *b_dev, const float *u0_dev,
                                      float *x_dev, const ct_hybrid_opts *o, ct_hybrid_info *info,
                                      ct_stream_t stream)
 {
-    if (!g || !b_dev || !x_dev) return einval("ba_gmres_hybrid: null argument");
+    if (!g || !b_dev || !x_dev) return einval("ab_gmres_hybrid: null argument");
     ct_status st = check_opts(o);
     if (st != CT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    Workspace *w = nullptr;
+    if ((st = enqueue_ab(g, b_dev, u0_dev, x_dev, o, s, &w)) != CT_OK) return st;
+    return finish(w, o, info, s);
+}
+
+// Algorithm 2, enqueued on s without host synchronisation (see enqueue_ab).
+static ct_status enqueue_ba(ct_geom *g, const float *b_dev, const float *x0_dev, float *x_dev,
+                            const ct_hybrid_opts *o, cudaStream_t s, Workspace **wout)
+{
+    ct_status st;
     Workspace *w;
     if ((st = ws_get(g, 1, o->max_iters, o->basis, &w)) != CT_OK) return st;
+    *wout = w;
     const int K = o->max_iters;
     const int64_t L = w->L, ld = w->L;
     const int sld = g->dg.sino_ld;
@@ -616,6 +638,19 @@ extern "C" ct_status ba_gmres_hybrid(ct_geom *g, const float *b_dev, const float
                                      x0_dev ? w->img : nullptr, w->q, kMaxBlocks, s));
         CT_CUDA(cudaMemcpyAsync(x_dev, w->q, sizeof(float) * g->n, cudaMemcpyDeviceToDevice, s));
     }
+    return CT_OK;
+}
+
+extern "C" ct_status ba_gmres_hybrid(ct_geom *g, const float *b_dev, const float *x0_dev,
+                                     float *x_dev, const ct_hybrid_opts *o, ct_hybrid_info *info,
+                                     ct_stream_t stream)
+{
+    if (!g || !b_dev || !x_dev) return einval("ba_gmres_hybrid: null argument");
+    ct_status st = check_opts(o);
+    if (st != CT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace *w = nullptr;
+    if ((st = enqueue_ba(g, b_dev, x0_dev, x_dev, o, s, &w)) != CT_OK) return st;
     return finish(w, o, info, s);
 }
 
@@ -697,3 +732,256 @@ extern "C" ct_status ct_profile_collect(ct_phase_time *out)
 }
 
 extern "C" int64_t ct_launch_count(void) { return g_launches.load(); }
+
+// ============================================================================ autotuning
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
+
+extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, int *a_threads, int *b_rows)
+{
+    if (!g) return einval("ct_geom_autotune: null geometry");
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0;
+    CT_CUDA(cudaGetDevice(&dev));
+    const auto key = std::make_tuple(dev, (int)g->desc.kind, g->desc.nx, g->desc.ny,
+                                     g->desc.n_views, g->desc.n_det_u);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            g->dg.tune_a_threads = it->second.first;
+            g->dg.tune_b_rows = it->second.second;
+            if (a_threads) *a_threads = g->dg.tune_a_threads;
+            if (b_rows) *b_rows = g->dg.tune_b_rows;
+            return CT_OK;
+        }
+    }
+    float *x = nullptr, *y = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CT_CUDA(cudaMalloc(&x, sizeof(float) * (size_t)g->n));
+    CT_CUDA(cudaMalloc(&y, sizeof(float) * (size_t)g->dg.n_views * g->dg.sino_ld));
+    CT_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * (size_t)g->n, s));
+    CT_CUDA(cudaMemsetAsync(y, 0, sizeof(float) * (size_t)g->dg.n_views * g->dg.sino_ld, s));
+    CT_CUDA(cudaEventCreate(&e0));
+    CT_CUDA(cudaEventCreate(&e1));
+    CT_CUDA(launch_image_pairs(g, x, nullptr, s));
+    auto time_best = [&](auto launch, const int *cand, int ncand, int *field) -> ct_status {
+        float best = 1e30f;
+        int best_c = cand[0];
+        for (int c = 0; c < ncand; ++c) {
+            *field = cand[c];
+            CT_CUDA(launch());                       // warm-up
+            float t = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                CT_CUDA(cudaEventRecord(e0, s));
+                CT_CUDA(launch());
+                CT_CUDA(cudaEventRecord(e1, s));
+                CT_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                t = std::min(t, ms);
+            }
+            if (t < best) { best = t; best_c = cand[c]; }
+        }
+        *field = best_c;
+        return CT_OK;
+    };
+    static const int a_cand[3] = {128, 256, 512};
+    static const int b_cand[3] = {4, 8, 16};
+    ct_status st = time_best([&]() { return launch_joseph2d(g, y, g->dg.sino_ld, 2, nullptr, s); },
+                             a_cand, 3, &g->dg.tune_a_threads);
+    if (st == CT_OK)
+        st = time_best([&]() { return launch_pixbp2d(g, y, x, nullptr, s); }, b_cand, 3,
+                       &g->dg.tune_b_rows);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(x);
+    cudaFree(y);
+    if (st != CT_OK) return st;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = {g->dg.tune_a_threads, g->dg.tune_b_rows};
+    }
+    if (a_threads) *a_threads = g->dg.tune_a_threads;
+    if (b_rows) *b_rows = g->dg.tune_b_rows;
+    return CT_OK;
+}
+
+// ============================================================================ batched solves
+struct ct_batch {
+    int n = 0;
+    std::vector<ct_geom *> g;
+    std::vector<int> method;
+    ct_hybrid_opts o{};
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    cudaStream_t cap = nullptr;         // capture stream (the legacy default stream cannot capture)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const float *> b_ptrs;
+    std::vector<float *> x_ptrs;
+    std::vector<double> noise;
+    std::vector<Workspace *> ws;
+    int64_t launches = 0;
+};
+
+extern "C" void ct_batch_destroy(ct_batch *bt)
+{
+    if (!bt) return;
+    if (bt->exec) cudaGraphExecDestroy(bt->exec);
+    if (bt->graph) cudaGraphDestroy(bt->graph);
+    for (auto s : bt->streams) if (s) cudaStreamDestroy(s);
+    for (auto e : bt->join) if (e) cudaEventDestroy(e);
+    if (bt->fork) cudaEventDestroy(bt->fork);
+    if (bt->cap) cudaStreamDestroy(bt->cap);
+    delete bt;
+}
+
+extern "C" int64_t ct_batch_launches(const ct_batch *bt) { return bt ? bt->launches : 0; }
+
+extern "C" ct_status ct_batch_create(int n_prob, ct_geom *const *geoms, const int *methods,
+                                     const ct_hybrid_opts *o, int autotune, ct_batch **out)
+{
+    if (!out || !geoms || n_prob < 1) return einval("ct_batch_create: need n_prob >= 1, geoms, out");
+    *out = nullptr;
+    ct_status st = check_opts(o);
+    if (st != CT_OK) return st;
+    if (o->lambda_hist || o->resid_hist) return einval("ct_batch_create: history pointers must be NULL");
+    for (int i = 0; i < n_prob; ++i) {
+        if (!geoms[i]) return einval("ct_batch_create: null geometry");
+        for (int j = 0; j < i; ++j)
+            if (geoms[j] == geoms[i]) return einval("ct_batch_create: each problem needs its own ct_geom");
+        int mth = methods ? methods[i] : 2;
+        if (mth < 0 || mth > 2) return einval("ct_batch_create: method must be 0, 1 or 2");
+    }
+    ct_batch *bt = new ct_batch();
+    bt->n = n_prob;
+    bt->o = *o;
+    bt->g.assign(geoms, geoms + n_prob);
+    bt->method.resize(n_prob);
+    bt->ws.assign(n_prob, nullptr);
+    cudaError_t e = small_solve_prepare();
+    if (e != cudaSuccess) { ct_batch_destroy(bt); return cuda_fail(e, "ct_batch_create"); }
+    for (int i = 0; i < n_prob; ++i) {
+        int mth = methods ? methods[i] : 2;
+        if (mth == 2) mth = (geoms[i]->m < geoms[i]->n) ? 0 : 1;
+        bt->method[i] = mth;
+        if (autotune && (st = ct_geom_autotune(geoms[i], nullptr, nullptr, nullptr)) != CT_OK) {
+            ct_batch_destroy(bt);
+            return st;
+        }
+        if ((st = ws_get(geoms[i], mth, o->max_iters, o->basis, &bt->ws[i])) != CT_OK) {
+            ct_batch_destroy(bt);
+            return st;
+        }
+    }
+    bt->streams.assign(n_prob, nullptr);
+    bt->join.assign(n_prob, nullptr);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bt->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking);
+    for (int i = 0; i < n_prob && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&bt->streams[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bt->join[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) { ct_batch_destroy(bt); return cuda_fail(e, "ct_batch_create"); }
+    *out = bt;
+    return CT_OK;
+}
+
+// Capture every problem's solve as one independent branch of a CUDA graph.
+static ct_status batch_capture(ct_batch *bt)
+{
+    cudaStream_t s = bt->cap;
+    if (bt->exec) { cudaGraphExecDestroy(bt->exec); bt->exec = nullptr; }
+    if (bt->graph) { cudaGraphDestroy(bt->graph); bt->graph = nullptr; }
+    bool prof;
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        prof = g_prof_on;
+        g_prof_on = false;                  // no per-phase events inside the graph
+    }
+    const int64_t l0 = g_launches.load();
+    ct_status st = CT_OK;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaEventRecord(bt->fork, s);
+    for (int i = 0; i < bt->n && e == cudaSuccess && st == CT_OK; ++i) {
+        cudaStream_t si = bt->streams[i];
+        e = cudaStreamWaitEvent(si, bt->fork, 0);
+        if (e != cudaSuccess) break;
+        ct_hybrid_opts oi = bt->o;
+        oi.noise_norm = bt->noise[i];
+        Workspace *w = nullptr;
+        st = (bt->method[i] == 0)
+                 ? enqueue_ab(bt->g[i], bt->b_ptrs[i], nullptr, bt->x_ptrs[i], &oi, si, &w)
+                 : enqueue_ba(bt->g[i], bt->b_ptrs[i], nullptr, bt->x_ptrs[i], &oi, si, &w);
+        if (st != CT_OK) break;
+        bt->ws[i] = w;
+        e = cudaEventRecord(bt->join[i], si);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, bt->join[i], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+    bt->launches = g_launches.load() - l0;
+    g_launches -= bt->launches;             // counted again at every replay
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        g_prof_on = prof;
+    }
+    if (st != CT_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+    if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(e, "batch capture"); }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+    bt->graph = graph;
+    CT_CUDA(cudaGraphInstantiate(&bt->exec, graph, 0));
+    return CT_OK;
+}
+
+extern "C" ct_status ct_batch_solve(ct_batch *bt, const float *const *b_dev, float *const *x_dev,
+                                    const double *noise_norms, ct_hybrid_info *info,
+                                    ct_stream_t stream)
+{
+    if (!bt || !b_dev || !x_dev) return einval("ct_batch_solve: null argument");
+    for (int i = 0; i < bt->n; ++i)
+        if (!b_dev[i] || !x_dev[i]) return einval("ct_batch_solve: null buffer");
+    if (bt->o.rule == CT_LAMBDA_DP && !noise_norms) return einval("ct_batch_solve: DP needs noise_norms");
+    cudaStream_t s = (cudaStream_t)stream;
+    bool same = bt->exec && bt->b_ptrs.size() == (size_t)bt->n;
+    for (int i = 0; same && i < bt->n; ++i) {
+        double nz = noise_norms ? noise_norms[i] : 0.0;
+        same = bt->b_ptrs[i] == b_dev[i] && bt->x_ptrs[i] == x_dev[i] && bt->noise[i] == nz;
+    }
+    if (!same) {
+        bt->b_ptrs.assign(b_dev, b_dev + bt->n);
+        bt->x_ptrs.assign(x_dev, x_dev + bt->n);
+        bt->noise.resize(bt->n);
+        for (int i = 0; i < bt->n; ++i) {
+            bt->noise[i] = noise_norms ? noise_norms[i] : 0.0;
+            if (!(bt->noise[i] >= 0)) return einval("ct_batch_solve: noise norms must be >= 0");
+        }
+        ct_status st = batch_capture(bt);
+        if (st != CT_OK) return st;
+    }
+    CT_CUDA(cudaGraphLaunch(bt->exec, s));
+    g_launches += bt->launches;
+    CT_CUDA(cudaStreamSynchronize(s));
+    ct_status first_err = CT_OK;
+    for (int i = 0; i < bt->n; ++i) {
+        ct_hybrid_opts oi = bt->o;
+        oi.noise_norm = bt->noise[i];
+        ct_status st = read_info(bt->ws[i], &oi, info ? &info[i] : nullptr);
+        if (st != CT_OK && first_err == CT_OK) first_err = st;
+    }
+    return first_err;
+}
+
+extern "C" ct_status abba_solve(int n_prob, ct_geom *const *geoms, const float *const *b_dev,
+                                float *const *x_dev, const int *methods, const ct_hybrid_opts *o,
+                                const double *noise_norms, ct_hybrid_info *info, ct_stream_t stream)
+{
+    ct_batch *bt = nullptr;
+    ct_status st = ct_batch_create(n_prob, geoms, methods, o, 1, &bt);
+    if (st != CT_OK) return st;
+    st = ct_batch_solve(bt, b_dev, x_dev, noise_norms, info, stream);
+    ct_batch_destroy(bt);
+    return st;
+}

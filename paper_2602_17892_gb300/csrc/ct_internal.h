@@ -50,6 +50,8 @@ struct DeviceGeom {
     int row_pairs_ld;   // P_row row length in float2: >= nx + 1
     int col_pairs_ld;   // P_col row length in float2: >= ny + 1
     int sino_ld;        // padded sinogram row length: ndu + 4 (2 zero bins each side)
+    int tune_a_threads; // Joseph A: rays (threads) per block, chosen by ct_geom_autotune
+    int tune_b_rows;    // pixel-driven B: block of 32 x tune_b_rows pixels
     // tables
     const Ray2D *rays;  // m rays (2D)
     const ViewBP *views;
@@ -113,6 +115,8 @@ struct SmallSolveParams {
                       // lambda_out[b], resid_out[b], path[b]
 };
 cudaError_t launch_small_solve(const SmallSolveParams &p, cudaStream_t s);
+// sets the kernel's shared-memory limit on the current device (call before a stream capture)
+cudaError_t small_solve_prepare();
 // all steps k = 1..p.k of one solve in one launch (one CTA per k)
 cudaError_t launch_small_solve_batched(const SmallSolveParams &p, cudaStream_t s);
 size_t small_solve_smem_bytes(int k);

@@ -79,7 +79,7 @@ cudaError_t launch_pad_sino(const ct_geom *g, const float *y, float *ypad, cudaS
 // ---------------------------------------------------------------------------- Joseph A
 // One thread per ray.  pos = pmid + slope * (t - t_mid) is the fractional index across the
 // driving axis; the pair at index floor(pos)+1 of line t holds both interpolation taps.
-__global__ void __launch_bounds__(256) joseph2d_kernel(
+__global__ void __launch_bounds__(512) joseph2d_kernel(
     const Ray2D *__restrict__ rays, int64_t m, int ndu,
     const float2 *__restrict__ prow, int prow_ld, const float2 *__restrict__ pcol, int pcol_ld,
     int nx, int ny, float *__restrict__ y, int y_ld, int y_off, const int *stop)
@@ -125,33 +125,36 @@ cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, con
 {
     const DeviceGeom &d = g->dg;
     int64_t m = g->m;
-    int blocks = (int)((m + 255) / 256);
-    joseph2d_kernel<<<blocks, 256, 0, s>>>(g->rays_dev, m, d.ndu, g->prow_dev, d.row_pairs_ld,
+    const int threads = d.tune_a_threads > 0 ? d.tune_a_threads : 256;
+    int blocks = (int)((m + threads - 1) / threads);
+    joseph2d_kernel<<<blocks, threads, 0, s>>>(g->rays_dev, m, d.ndu, g->prow_dev, d.row_pairs_ld,
                                            g->pcol_dev, d.col_pairs_ld, d.nx, d.ny, y, y_ld,
                                            y_off, stop);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------- pixel-driven B
-// One thread per pixel, blocks of 32 x 8 pixels, per-view constants staged in shared memory.
+// One thread per pixel, blocks of 32 x tune_b_rows pixels, per-view constants staged in shared
+// memory.
 // Parallel: bin position fj = a (c - cm) + b (r - rm) + (nd-1)/2, weight h^2/pitch.
 // Fan:      pe = p.e_u, bb = SID - p.(cos, sin) (in units of h), u = SDD pe / bb,
 //           weight h SDD / pitch * sqrt(1 + (pe/bb)^2) / bb  (= h^2 (SDD^2+u^2)/(L pitch SDD)).
 template <bool FAN>
-__global__ void __launch_bounds__(256) pixbp2d_kernel(
+__global__ void __launch_bounds__(512) pixbp2d_kernel(
     const ViewBP *__restrict__ views, int n_views, const float *__restrict__ ypad, int ld,
     int nd, int nx, int ny, float sid_h, float k_u, float k_w, float w_par,
     float *__restrict__ x, const int *stop)
 {
     if (stop && stop[0] != 0) return;
     extern __shared__ float4 sview[];
-    for (int v = threadIdx.y * 32 + threadIdx.x; v < n_views; v += 256) {
+    const int nthr = blockDim.x * blockDim.y;
+    for (int v = threadIdx.y * 32 + threadIdx.x; v < n_views; v += nthr) {
         ViewBP vb = views[v];
         sview[v] = make_float4(vb.cs, vb.sn, vb.a, vb.b);
     }
     __syncthreads();
     const int c = blockIdx.x * 32 + threadIdx.x;
-    const int r = blockIdx.y * 8 + threadIdx.y;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
     if (c >= nx || r >= ny) return;
     const float tc = (float)c - 0.5f * (float)(nx - 1);
     const float tr = (float)r - 0.5f * (float)(ny - 1);
@@ -189,7 +192,8 @@ cudaError_t launch_pixbp2d(const ct_geom *g, const float *ypad, float *x, const 
                            cudaStream_t s)
 {
     const DeviceGeom &d = g->dg;
-    dim3 block(32, 8), grid((d.nx + 31) / 32, (d.ny + 7) / 8);
+    const int rows = d.tune_b_rows > 0 ? d.tune_b_rows : 8;
+    dim3 block(32, rows), grid((d.nx + 31) / 32, (d.ny + rows - 1) / rows);
     size_t smem = sizeof(float4) * (size_t)d.n_views;
     float sid_h = d.sid / d.h;
     float k_u = d.sdd / d.pitch_u;

@@ -894,6 +894,8 @@ static cudaError_t set_smem_attr()
     return cudaSuccess;
 }
 
+cudaError_t small_solve_prepare() { return set_smem_attr(); }
+
 cudaError_t launch_small_solve_batched(const SmallSolveParams &p, cudaStream_t s)
 {
     cudaError_t e = set_smem_attr();
