@@ -103,7 +103,10 @@ typedef enum {
     CT_LAMBDA_NONE = 0,   /* lambda = 0: plain AB/BA-GMRES, Eq. (proj_pbm) by Givens rotations */
     CT_LAMBDA_FIXED = 1,  /* lambda = lambda_fixed at every iteration                        */
     CT_LAMBDA_GCV = 2,    /* GCV on the projected problem (Sec. 3.1)                          */
-    CT_LAMBDA_DP = 3      /* discrepancy principle: ||H y - beta e1|| = tau * noise_norm      */
+    CT_LAMBDA_DP = 3,     /* discrepancy principle: ||H y - beta e1|| = tau * noise_norm      */
+    CT_LAMBDA_LEARNED = 4 /* not in the paper: lambda_k = sigma_1 10^net(features of H_k) from a
+                             trained network (see "learned lambda" below); GCV where the
+                             network's output is not finite                                  */
 } ct_lambda_rule;
 
 typedef enum { CT_BASIS_F32 = 0, CT_BASIS_BF16 = 1, CT_BASIS_F16 = 2 } ct_basis_dtype;
@@ -118,6 +121,10 @@ typedef struct {
     ct_basis_dtype basis;    /* storage type of the Krylov basis                           */
     double *lambda_hist;     /* host, max_iters entries, may be NULL: lambda_k              */
     double *resid_hist;      /* host, max_iters entries, may be NULL: ||H_k y_k - beta e1|| */
+    const float *lambda_net_dev; /* CT_LAMBDA_LEARNED: the network's CT_MLP_NPARAMS FP32
+                                    parameters (device; read during the solve)              */
+    float *features_dev;     /* device, max_iters x CT_MLP_NIN floats, may be NULL: row k-1
+                                receives the features of H_k (any rule but CT_LAMBDA_NONE)  */
 } ct_hybrid_opts;
 
 typedef struct {
@@ -128,6 +135,7 @@ typedef struct {
     ct_status status;        /* CT_OK or CT_BREAKDOWN                                      */
     int fast_path_steps;     /* steps whose hybrid step took the parallel path (the others ran
                                 the exact sequential SVD path; diagnostics only)            */
+    int lambda_fallback_steps; /* CT_LAMBDA_LEARNED: steps where GCV replaced the network   */
 } ct_hybrid_info;
 
 /* Fill `o` with defaults: K = 30, GCV, tau = 1.01, reorth = 1, FP32 basis, no history. */
@@ -222,11 +230,67 @@ ct_status ct_arnoldi_step_noalloc(float *W_dev, int64_t len, int64_t ld, int k, 
 /* The hybrid step on the device (Sec. 3, Eq. (hybrid_proj); Sec. 3.1/3.2): for the
  * (k+1) x k Hessenberg matrix H (FP64, column-major, leading dimension ldh >= k+1) and
  * beta = ||r0||, choose lambda by `rule` and return y (k doubles), lambda and the projected
- * residual ||H y - beta e1||.  All pointers are device pointers.  1 <= k <= 512. */
+ * residual ||H y - beta e1||.  All pointers are device pointers.  1 <= k <= 160;
+ * rule CT_LAMBDA_NONE .. CT_LAMBDA_DP. */
 ct_status ct_projected_solve(const double *H_dev, int ldh, int k, double beta,
                              ct_lambda_rule rule, double lambda_fixed, double dp_target,
                              double *y_dev, double *lambda_dev, double *resid_dev,
                              ct_stream_t stream);
+
+/* ------------------------------------------------------------------ learned lambda */
+
+/* Not in the paper.  A 3-layer perceptron predicts log10(lambda_k / sigma_1(H_k)) from
+ * features of the projected problem; CT_LAMBDA_LEARNED uses it in place of GCV or the
+ * discrepancy principle, which stay the fallback and the measure of its reconstruction error.
+ *
+ * Features of H_k (CT_MLP_NIN = 80 floats, computed by the hybrid step from the SVD of H_k,
+ * H_k = U diag(sigma) V^T, c = beta U^T e1 with c_{k+1} the component outside range(H_k)):
+ *   [0] k / max_iters; [1..32] log10(sigma_i / sigma_1) for the 32 largest sigma_i (pad -16);
+ *   [33..64] |c_i| / beta for the same i (pad 0); [65] |c_{k+1}| / beta; [66] log10 sigma_1;
+ *   [67] log10 beta; [68..79] 0.
+ * Network: 80 -> 64 -> 64 -> 1, GELU (tanh form) after both hidden layers.  Parameters, one
+ * FP32 vector of CT_MLP_NPARAMS entries in this order: W1[64][80], b1[64], W2[64][64], b2[64],
+ * w3[64], b3.  bf16 != 0: weights, inputs and both hidden activations are rounded to BF16 and
+ * the products accumulate in FP32 on the tensor cores (the solver's inference always works
+ * this way); bf16 == 0: the same arithmetic in FP32 on the CUDA cores. */
+#define CT_MLP_NIN 80
+#define CT_MLP_NPARAMS 9409
+
+/* out_dev[i] = net(X_dev[i][0..79]) for i < n.  X: n x 80 floats, row-major. */
+ct_status ct_mlp_forward(const float *params_dev, const float *X_dev, int n, float *out_dev,
+                         int bf16, ct_stream_t stream);
+/* Gradient of the mean squared error (1/n) sum_i (net(X_i) - Y_i)^2 with respect to every
+ * parameter into grad_dev (CT_MLP_NPARAMS floats), and that error into *loss_dev (device, may
+ * be NULL).  Deterministic (fixed summation order).  Allocates its scratch with
+ * cudaMallocAsync/cudaFreeAsync on `stream`. */
+ct_status ct_mlp_grad(const float *params_dev, const float *X_dev, const float *Y_dev, int n,
+                      float *grad_dev, float *loss_dev, int bf16, ct_stream_t stream);
+/* One Adam step (Kingma and Ba; beta1 = 0.9, beta2 = 0.999, eps = 1e-8, bias-corrected with
+ * step number t >= 1) on the FP32 parameters, moments m_dev and v_dev updated in place. */
+ct_status ct_mlp_adam(float *params_dev, const float *grad_dev, float *m_dev, float *v_dev,
+                      float lr, int t, ct_stream_t stream);
+/* Mini-batch training: `epochs` passes over the n samples in batches of `batch` rows (the last
+ * partial batch of a pass included), one ct_mlp_grad and one ct_mlp_adam per batch, Adam's
+ * step counter starting at *t + 1 (updated).  The caller shuffles X/Y between calls if it
+ * wants a new order.  loss_hist_dev (device, may be NULL) receives each batch's loss in order
+ * (ceil(n / batch) * epochs floats). */
+ct_status ct_mlp_train(float *params_dev, float *m_dev, float *v_dev, const float *X_dev,
+                       const float *Y_dev, int n, int batch, int epochs, float lr, int *t,
+                       float *loss_hist_dev, int bf16, ct_stream_t stream);
+
+/* Training samples from one hybrid AB-GMRES solve (Algorithm 1 with u0 = 0, o->max_iters = K
+ * <= 64, FP32 basis, any rule but CT_LAMBDA_NONE) of b_dev, whose exact image x_true_dev
+ * (n floats) is known.  For k = 1..K: feats_dev row k-1 (80 floats) gets the features of H_k
+ * and labels_dev[k-1] = log10(lambda*_k / sigma_1(H_k)), where lambda*_k minimises the
+ * reconstruction error ||x_k(lambda) - x_true|| with x_k(lambda) = B W_k y_k(lambda):
+ * lambda is searched like GCV (256 log-spaced points on [1e-8 sigma_1, sigma_1], the best one
+ * refined by 40 golden-section steps).  The error is a quadratic in y through
+ * G = Z^T Z, g = Z^T x_true with Z = B W_K (K extra applications of B).  Labels are NaN
+ * where H_k is zero.  x_dev (n floats) receives the solve's own iterate.  Allocates scratch
+ * with cudaMallocAsync; synchronises `stream`. */
+ct_status ct_lambda_samples(ct_geom *g, const float *b_dev, const float *x_true_dev,
+                            const ct_hybrid_opts *o, float *x_dev, float *feats_dev,
+                            float *labels_dev, ct_hybrid_info *info, ct_stream_t stream);
 
 /* ------------------------------------------------------------------ instrumentation */
 

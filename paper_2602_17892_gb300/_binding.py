@@ -19,7 +19,8 @@ CT_OK, CT_EINVAL, CT_ENOMEM, CT_ECUDA, CT_BREAKDOWN, CT_ETIMEOUT, CT_ENONFINITE 
 STATUS_NAMES = {0: "CT_OK", 1: "CT_EINVAL", 2: "CT_ENOMEM", 3: "CT_ECUDA", 4: "CT_BREAKDOWN",
                 5: "CT_ETIMEOUT", 6: "CT_ENONFINITE"}
 KINDS = {"parallel2d": 0, "fanflat2d": 1, "cone3d": 2}
-RULES = {"none": 0, "fixed": 1, "gcv": 2, "dp": 3}
+RULES = {"none": 0, "fixed": 1, "gcv": 2, "dp": 3, "learned": 4}
+CT_MLP_NIN, CT_MLP_NPARAMS = 80, 9409
 BASIS = {"f32": 0, "bf16": 1, "f16": 2}
 
 # the entry points of include/ctabba.h
@@ -27,7 +28,8 @@ EXPORTS = ("ct_geom_create", "ct_geom_destroy", "ct_geom_dims", "ct_geom_work", 
            "ct_hybrid_opts_default", "ab_gmres_hybrid", "ba_gmres_hybrid", "ct_arnoldi_step", "ct_arnoldi_step_noalloc",
            "ct_projected_solve", "ct_status_string", "ct_last_error", "ct_profile_enable",
            "ct_profile_collect", "ct_launch_count", "ct_geom_autotune", "ct_batch_create",
-           "ct_batch_solve", "ct_batch_launches", "ct_batch_destroy", "abba_solve")
+           "ct_batch_solve", "ct_batch_launches", "ct_batch_destroy", "abba_solve", "ct_mlp_forward",
+           "ct_mlp_grad", "ct_mlp_adam", "ct_mlp_train", "ct_lambda_samples")
 PHASES = ("forward_A", "back_B", "layout", "arnoldi", "small_solve", "other")
 
 
@@ -50,7 +52,8 @@ class HybridOpts(ctypes.Structure):
                 ("lambda_fixed", ctypes.c_double), ("noise_norm", ctypes.c_double),
                 ("tau", ctypes.c_double), ("reorth", ctypes.c_int), ("basis", ctypes.c_int),
                 ("lambda_hist", ctypes.POINTER(ctypes.c_double)),
-                ("resid_hist", ctypes.POINTER(ctypes.c_double))]
+                ("resid_hist", ctypes.POINTER(ctypes.c_double)),
+                ("lambda_net_dev", ctypes.c_void_p), ("features_dev", ctypes.c_void_p)]
 
 
 class PhaseTime(ctypes.Structure):
@@ -60,7 +63,8 @@ class PhaseTime(ctypes.Structure):
 class HybridInfo(ctypes.Structure):
     _fields_ = [("iters_done", ctypes.c_int), ("beta", ctypes.c_double),
                 ("final_lambda", ctypes.c_double), ("final_resid", ctypes.c_double),
-                ("status", ctypes.c_int), ("fast_path_steps", ctypes.c_int)]
+                ("status", ctypes.c_int), ("fast_path_steps", ctypes.c_int),
+                ("lambda_fallback_steps", ctypes.c_int)]
 
 
 _lib = None
@@ -109,6 +113,13 @@ def load(path: str = LIB_PATH):
     lib.abba_solve.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(HybridOpts),
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(HybridInfo), vp]
+    lib.ct_mlp_forward.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_int, vp]
+    lib.ct_mlp_grad.argtypes = [vp, vp, vp, ctypes.c_int, vp, vp, ctypes.c_int, vp]
+    lib.ct_mlp_adam.argtypes = [vp, vp, vp, vp, ctypes.c_float, ctypes.c_int, vp]
+    lib.ct_mlp_train.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_float, ctypes.POINTER(ctypes.c_int), vp, ctypes.c_int, vp]
+    lib.ct_lambda_samples.argtypes = [vp, vp, vp, ctypes.POINTER(HybridOpts), vp, vp, vp,
+                                      ctypes.POINTER(HybridInfo), vp]
     lib.ct_status_string.argtypes = [ctypes.c_int]
     lib.ct_status_string.restype = ctypes.c_char_p
     lib.ct_last_error.restype = ctypes.c_char_p
@@ -188,7 +199,8 @@ def ct_back_B(g: Geom, y, x, stream=None):
     _check(load().ct_back_B(g.handle, _ptr(y), _ptr(x), _stream(stream)))
 
 
-def _opts(max_iters, rule, lambda_fixed, noise_norm, tau, reorth, basis, history):
+def _opts(max_iters, rule, lambda_fixed, noise_norm, tau, reorth, basis, history,
+          lambda_net=None, features=None):
     o = HybridOpts()
     load().ct_hybrid_opts_default(ctypes.byref(o))
     o.max_iters = int(max_iters)
@@ -198,6 +210,8 @@ def _opts(max_iters, rule, lambda_fixed, noise_norm, tau, reorth, basis, history
     o.tau = float(tau)
     o.reorth = int(reorth)
     o.basis = BASIS[basis] if isinstance(basis, str) else int(basis)
+    o.lambda_net_dev = _ptr(lambda_net).value if lambda_net is not None else None
+    o.features_dev = _ptr(features).value if features is not None else None
     lam = res = None
     if history:
         lam = np.full(int(max_iters), np.nan)
@@ -208,32 +222,33 @@ def _opts(max_iters, rule, lambda_fixed, noise_norm, tau, reorth, basis, history
 
 
 def _solve(fn, g, b, x, x0, max_iters, rule, lambda_fixed, noise_norm, tau, reorth, basis,
-           history, stream):
-    o, lam, res = _opts(max_iters, rule, lambda_fixed, noise_norm, tau, reorth, basis, history)
+           history, stream, lambda_net=None, features=None):
+    o, lam, res = _opts(max_iters, rule, lambda_fixed, noise_norm, tau, reorth, basis, history,
+                        lambda_net, features)
     info = HybridInfo()
     st = fn(g.handle, _ptr(b), _ptr(x0), _ptr(x), ctypes.byref(o), ctypes.byref(info),
             _stream(stream))
     _check(st)
-    out = dict(iters_done=info.iters_done, beta=info.beta, final_lambda=info.final_lambda,
-               final_resid=info.final_resid, status=STATUS_NAMES[info.status],
-               fast_path_steps=info.fast_path_steps)
+    out = _info_dict(info)
     if history:
         out["lambdas"], out["resid"] = lam, res
     return out
 
 
 def ab_gmres_hybrid(g, b, x, u0=None, max_iters=30, rule="gcv", lambda_fixed=0.0,
-                    noise_norm=0.0, tau=1.01, reorth=1, basis="f32", history=True, stream=None):
+                    noise_norm=0.0, tau=1.01, reorth=1, basis="f32", history=True, stream=None,
+                    lambda_net=None, features=None):
     """Hybrid AB-GMRES (Algorithm 1): x <- x0 + B W_K y_K with x0 = B u0."""
     return _solve(load().ab_gmres_hybrid, g, b, x, u0, max_iters, rule, lambda_fixed,
-                  noise_norm, tau, reorth, basis, history, stream)
+                  noise_norm, tau, reorth, basis, history, stream, lambda_net, features)
 
 
 def ba_gmres_hybrid(g, b, x, x0=None, max_iters=30, rule="gcv", lambda_fixed=0.0,
-                    noise_norm=0.0, tau=1.01, reorth=1, basis="f32", history=True, stream=None):
+                    noise_norm=0.0, tau=1.01, reorth=1, basis="f32", history=True, stream=None,
+                    lambda_net=None, features=None):
     """Hybrid BA-GMRES (Algorithm 2): x <- x0 + W_K y_K."""
     return _solve(load().ba_gmres_hybrid, g, b, x, x0, max_iters, rule, lambda_fixed,
-                  noise_norm, tau, reorth, basis, history, stream)
+                  noise_norm, tau, reorth, basis, history, stream, lambda_net, features)
 
 
 def ct_arnoldi_step(W, length, ld, k, q, h, stream=None):
@@ -281,19 +296,21 @@ def ct_geom_autotune(g: Geom, stream=None):
 def _info_dict(inf):
     return dict(iters_done=inf.iters_done, beta=inf.beta, final_lambda=inf.final_lambda,
                 final_resid=inf.final_resid, status=STATUS_NAMES[inf.status],
-                fast_path_steps=inf.fast_path_steps)
+                fast_path_steps=inf.fast_path_steps,
+                lambda_fallback_steps=inf.lambda_fallback_steps)
 
 
 class Batch:
     """ct_batch: many independent problems solved through one captured CUDA graph."""
 
     def __init__(self, geoms, methods=None, max_iters=30, rule="gcv", lambda_fixed=0.0, tau=1.01,
-                 reorth=1, basis="f32", autotune=True):
+                 reorth=1, basis="f32", autotune=True, lambda_net=None):
         lib = load()
         self.geoms = list(geoms)
         n = len(self.geoms)
-        o, _, _ = _opts(max_iters, rule, lambda_fixed, 0.0, tau, reorth, basis, False)
+        o, _, _ = _opts(max_iters, rule, lambda_fixed, 0.0, tau, reorth, basis, False, lambda_net)
         self._o = o
+        self._net = lambda_net
         gh = (ctypes.c_void_p * n)(*[g.handle.value for g in self.geoms])
         mth = None
         if methods is not None:
@@ -330,11 +347,11 @@ class Batch:
 
 
 def abba_solve(geoms, b_list, x_list, methods=None, max_iters=30, rule="gcv", lambda_fixed=0.0,
-               noise_norms=None, tau=1.01, basis="f32", stream=None):
+               noise_norms=None, tau=1.01, basis="f32", stream=None, lambda_net=None):
     """One-shot batched solve (creates, solves and destroys a ct_batch)."""
     lib = load()
     n = len(geoms)
-    o, _, _ = _opts(max_iters, rule, lambda_fixed, 0.0, tau, 1, basis, False)
+    o, _, _ = _opts(max_iters, rule, lambda_fixed, 0.0, tau, 1, basis, False, lambda_net)
     gh = (ctypes.c_void_p * n)(*[g.handle.value for g in geoms])
     mth = None
     if methods is not None:
@@ -345,3 +362,43 @@ def abba_solve(geoms, b_list, x_list, methods=None, max_iters=30, rule="gcv", la
     infos = (HybridInfo * n)()
     _check(lib.abba_solve(n, gh, bp, xp, mth, ctypes.byref(o), nz, infos, _stream(stream)))
     return [_info_dict(infos[i]) for i in range(n)]
+
+
+# ------------------------------------------------------------------ learned lambda
+
+def ct_mlp_forward(params, X, out, bf16=True, stream=None):
+    """out[i] = net(X[i]) for the n x 80 feature rows X (FP32 CUDA tensors)."""
+    _check(load().ct_mlp_forward(_ptr(params), _ptr(X), int(X.shape[0]), _ptr(out),
+                                 1 if bf16 else 0, _stream(stream)))
+
+
+def ct_mlp_grad(params, X, Y, grad, loss=None, bf16=True, stream=None):
+    """grad <- d/dparams of mean((net(X) - Y)^2); loss (1-element tensor) <- that mean."""
+    _check(load().ct_mlp_grad(_ptr(params), _ptr(X), _ptr(Y), int(X.shape[0]), _ptr(grad),
+                              _ptr(loss), 1 if bf16 else 0, _stream(stream)))
+
+
+def ct_mlp_adam(params, grad, m, v, lr, t, stream=None):
+    _check(load().ct_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), float(lr), int(t),
+                              _stream(stream)))
+
+
+def ct_mlp_train(params, m, v, X, Y, batch, epochs, lr, t=0, loss_hist=None, bf16=True,
+                 stream=None):
+    """Mini-batch Adam training; returns the updated Adam step counter."""
+    tc = ctypes.c_int(int(t))
+    _check(load().ct_mlp_train(_ptr(params), _ptr(m), _ptr(v), _ptr(X), _ptr(Y),
+                               int(X.shape[0]), int(batch), int(epochs), float(lr),
+                               ctypes.byref(tc), _ptr(loss_hist), 1 if bf16 else 0,
+                               _stream(stream)))
+    return tc.value
+
+
+def ct_lambda_samples(g, b, x_true, x, feats, labels, max_iters=30, rule="gcv", stream=None):
+    """Features (K x 80) and labels (K) of the learned lambda rule from one AB solve."""
+    o, _, _ = _opts(max_iters, rule, 0.0, 0.0, 1.01, 1, "f32", False)
+    info = HybridInfo()
+    _check(load().ct_lambda_samples(g.handle, _ptr(b), _ptr(x_true), ctypes.byref(o), _ptr(x),
+                                    _ptr(feats), _ptr(labels), ctypes.byref(info),
+                                    _stream(stream)))
+    return _info_dict(info)

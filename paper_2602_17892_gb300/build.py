@@ -34,6 +34,7 @@ def _sources():
 
 def _deps():
     return _sources() + sorted(glob.glob(os.path.join(CSRC, "*.h"))) + sorted(
+        glob.glob(os.path.join(CSRC, "*.cuh"))) + sorted(
         glob.glob(os.path.join(INCLUDE, "*.h")))
 
 

@@ -419,7 +419,9 @@ static ct_status check_opts(const ct_hybrid_opts *o)
     if (!o) return einval("solver: opts is NULL");
     if (o->max_iters < 1 || o->max_iters > kMaxSmallK)
         return einval("solver: max_iters must be in [1, " + std::to_string(kMaxSmallK) + "]");
-    if (o->rule < CT_LAMBDA_NONE || o->rule > CT_LAMBDA_DP) return einval("solver: bad lambda rule");
+    if (o->rule < CT_LAMBDA_NONE || o->rule > CT_LAMBDA_LEARNED) return einval("solver: bad lambda rule");
+    if (o->rule == CT_LAMBDA_LEARNED && !o->lambda_net_dev)
+        return einval("solver: CT_LAMBDA_LEARNED needs lambda_net_dev");
     if (o->rule == CT_LAMBDA_FIXED && !(o->lambda_fixed >= 0)) return einval("solver: lambda_fixed must be >= 0");
     if (o->rule == CT_LAMBDA_DP && (!(o->noise_norm >= 0) || !(o->tau > 0)))
         return einval("solver: DP needs noise_norm >= 0 and tau > 0");
@@ -460,8 +462,12 @@ static ct_status read_info(Workspace *w, const ct_hybrid_opts *o, ct_hybrid_info
         info->final_resid = kf > 0 ? res[kf - 1] : beta;
         info->status = st;
         info->fast_path_steps = 0;
+        info->lambda_fallback_steps = 0;
         if (o->rule != CT_LAMBDA_NONE)
-            for (int i = 0; i < kf; ++i) info->fast_path_steps += path[i];
+            for (int i = 0; i < kf; ++i) {
+                info->fast_path_steps += path[i] & 1;
+                info->lambda_fallback_steps += (path[i] >> 1) & 1;
+            }
     }
     if (st == CT_ENONFINITE) { set_error("solver: non-finite value met"); return st; }
     return CT_OK;
@@ -484,6 +490,8 @@ static ct_status run_small_solves(Workspace *w, const ct_hybrid_opts *o, cudaStr
     p.kmax = o->max_iters;
     p.always_y = 0;
     p.path = w->path;
+    p.net = (o->rule == CT_LAMBDA_LEARNED) ? o->lambda_net_dev : nullptr;
+    p.features = o->features_dev;
     CT_PHASE(CT_PH_SMALL, 1, s);
     CT_CUDA(launch_small_solve_batched(p, s));
     return CT_OK;
@@ -700,6 +708,123 @@ extern "C" ct_status ct_projected_solve(const double *H_dev, int ldh, int k, dou
     return CT_OK;
 }
 
+// ============================================================================ learned lambda
+extern "C" ct_status ct_mlp_forward(const float *params_dev, const float *X_dev, int n,
+                                    float *out_dev, int bf16, ct_stream_t stream)
+{
+    if (!params_dev || !X_dev || !out_dev) return einval("ct_mlp_forward: null argument");
+    if (n < 0) return einval("ct_mlp_forward: n < 0");
+    if (n == 0) return CT_OK;
+    CT_CUDA(launch_mlp_forward(params_dev, X_dev, n, out_dev, bf16 != 0, (cudaStream_t)stream));
+    g_launches += 1;
+    return CT_OK;
+}
+
+static ct_status mlp_grad_into(const float *P, const float *X, const float *Y, int n, float *grad,
+                               float *loss, bool bf16, float *part, float *lpart, cudaStream_t s)
+{
+    CT_CUDA(launch_mlp_grad(P, X, Y, n, part, lpart, grad, loss, bf16, s));
+    g_launches += 2;
+    return CT_OK;
+}
+
+extern "C" ct_status ct_mlp_grad(const float *params_dev, const float *X_dev, const float *Y_dev,
+                                 int n, float *grad_dev, float *loss_dev, int bf16,
+                                 ct_stream_t stream)
+{
+    if (!params_dev || !X_dev || !Y_dev || !grad_dev) return einval("ct_mlp_grad: null argument");
+    if (n < 1) return einval("ct_mlp_grad: n must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nblk = (n + mlp_rows_per_block() - 1) / mlp_rows_per_block();
+    float *part = nullptr, *lpart = nullptr;
+    CT_CUDA(cudaMallocAsync((void **)&part, sizeof(float) * (size_t)nblk * mlp_num_params(), s));
+    CT_CUDA(cudaMallocAsync((void **)&lpart, sizeof(float) * (size_t)nblk, s));
+    ct_status st = mlp_grad_into(params_dev, X_dev, Y_dev, n, grad_dev, loss_dev, bf16 != 0, part,
+                                 lpart, s);
+    CT_CUDA(cudaFreeAsync(part, s));
+    CT_CUDA(cudaFreeAsync(lpart, s));
+    return st;
+}
+
+extern "C" ct_status ct_mlp_adam(float *params_dev, const float *grad_dev, float *m_dev,
+                                 float *v_dev, float lr, int t, ct_stream_t stream)
+{
+    if (!params_dev || !grad_dev || !m_dev || !v_dev) return einval("ct_mlp_adam: null argument");
+    if (t < 1 || !(lr > 0.f)) return einval("ct_mlp_adam: need t >= 1 and lr > 0");
+    CT_CUDA(launch_mlp_adam(params_dev, grad_dev, m_dev, v_dev, lr, t, (cudaStream_t)stream));
+    g_launches += 1;
+    return CT_OK;
+}
+
+extern "C" ct_status ct_mlp_train(float *params_dev, float *m_dev, float *v_dev, const float *X_dev,
+                                  const float *Y_dev, int n, int batch, int epochs, float lr,
+                                  int *t, float *loss_hist_dev, int bf16, ct_stream_t stream)
+{
+    if (!params_dev || !m_dev || !v_dev || !X_dev || !Y_dev || !t)
+        return einval("ct_mlp_train: null argument");
+    if (n < 1 || batch < 1 || epochs < 0 || *t < 0 || !(lr > 0.f))
+        return einval("ct_mlp_train: need n >= 1, batch >= 1, epochs >= 0, *t >= 0, lr > 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int bmax = std::min(batch, n);
+    const int nblk = (bmax + mlp_rows_per_block() - 1) / mlp_rows_per_block();
+    float *part = nullptr, *lpart = nullptr, *grad = nullptr;
+    CT_CUDA(cudaMallocAsync((void **)&part, sizeof(float) * (size_t)nblk * mlp_num_params(), s));
+    CT_CUDA(cudaMallocAsync((void **)&lpart, sizeof(float) * (size_t)nblk, s));
+    CT_CUDA(cudaMallocAsync((void **)&grad, sizeof(float) * (size_t)mlp_num_params(), s));
+    ct_status st = CT_OK;
+    int64_t step = 0;
+    for (int ep = 0; ep < epochs && st == CT_OK; ++ep) {
+        for (int off = 0; off < n && st == CT_OK; off += batch, ++step) {
+            const int nb = std::min(batch, n - off);
+            st = mlp_grad_into(params_dev, X_dev + (int64_t)off * CT_MLP_NIN, Y_dev + off, nb, grad,
+                               loss_hist_dev ? loss_hist_dev + step : nullptr, bf16 != 0, part,
+                               lpart, s);
+            if (st != CT_OK) break;
+            cudaError_t e = launch_mlp_adam(params_dev, grad, m_dev, v_dev, lr, *t + 1, s);
+            if (e != cudaSuccess) { st = cuda_fail(e, "ct_mlp_train"); break; }
+            g_launches += 1;
+            *t += 1;
+        }
+    }
+    cudaFreeAsync(part, s);
+    cudaFreeAsync(lpart, s);
+    cudaFreeAsync(grad, s);
+    return st;
+}
+
+extern "C" ct_status ct_lambda_samples(ct_geom *g, const float *b_dev, const float *x_true_dev,
+                                       const ct_hybrid_opts *o, float *x_dev, float *feats_dev,
+                                       float *labels_dev, ct_hybrid_info *info, ct_stream_t stream)
+{
+    if (!g || !b_dev || !x_true_dev || !x_dev || !feats_dev || !labels_dev)
+        return einval("ct_lambda_samples: null argument");
+    ct_status st = check_opts(o);
+    if (st != CT_OK) return st;
+    if (o->max_iters > 64) return einval("ct_lambda_samples: max_iters must be <= 64");
+    if (o->basis != CT_BASIS_F32) return einval("ct_lambda_samples: needs the FP32 basis");
+    if (o->rule == CT_LAMBDA_NONE) return einval("ct_lambda_samples: rule must not be CT_LAMBDA_NONE");
+    cudaStream_t s = (cudaStream_t)stream;
+    ct_hybrid_opts oo = *o;
+    oo.features_dev = feats_dev;
+    Workspace *w = nullptr;
+    if ((st = enqueue_ab(g, b_dev, nullptr, x_dev, &oo, s, &w)) != CT_OK) return st;
+    const int K = o->max_iters;
+    const int64_t img_ld = round_up(g->n, 4);
+    float *Z = nullptr;
+    double *G = nullptr;
+    CT_CUDA(cudaMallocAsync((void **)&Z, sizeof(float) * (size_t)K * img_ld, s));
+    CT_CUDA(cudaMallocAsync((void **)&G, sizeof(double) * (size_t)K * (K + 1), s));
+    for (int j = 0; j < K; ++j)         // Z = B W_K (the AB basis is in padded-sinogram layout)
+        CT_CUDA(launch_pixbp2d(g, static_cast<const float *>(w->W) + (int64_t)j * w->L,
+                               Z + (int64_t)j * img_ld, nullptr, s));
+    CT_CUDA(launch_gram(Z, img_ld, g->n, K, x_true_dev, G, G + (size_t)K * K, s));
+    CT_CUDA(launch_lambda_labels(w->H, w->K + 1, w->aux + 2, G, K, G + (size_t)K * K, labels_dev, s));
+    g_launches += K + 2;
+    CT_CUDA(cudaFreeAsync(Z, s));
+    CT_CUDA(cudaFreeAsync(G, s));
+    return finish(w, &oo, info, s);
+}
+
 // ============================================================================ instrumentation
 extern "C" ct_status ct_profile_enable(int on)
 {
@@ -847,7 +972,8 @@ extern "C" ct_status ct_batch_create(int n_prob, ct_geom *const *geoms, const in
     *out = nullptr;
     ct_status st = check_opts(o);
     if (st != CT_OK) return st;
-    if (o->lambda_hist || o->resid_hist) return einval("ct_batch_create: history pointers must be NULL");
+    if (o->lambda_hist || o->resid_hist || o->features_dev)
+        return einval("ct_batch_create: history and feature pointers must be NULL");
     for (int i = 0; i < n_prob; ++i) {
         if (!geoms[i]) return einval("ct_batch_create: null geometry");
         for (int j = 0; j < i; ++j)

@@ -102,17 +102,20 @@ struct ArnoldiScratch {
 // ----------------------------------------------------------------------------- small solve
 constexpr int kMaxSmallK = 160;   // largest projected problem held in shared memory
 struct SmallSolveParams {
-    const double *H;  int ldh; int k;
-    double beta; const double *betap;   // beta, or read from device when betap != null
-    int rule; double lambda_fixed; double dp_target;
-    double *y; double *lambda_out; double *resid_out;
-    const int *stop;  // solver stop word (may be null)
-    int kmax;         // last step of the solve: y is formed there (or at a breakdown step)
-    int always_y;     // form y at every k
-    int *path;        // optional: 1 where the parallel path was accepted, 0 where the exact
-                      // sequential path ran (indexed by k - 1)
-    int ystride;      // batched launch: block b solves k = b + 1, y at y + b * ystride,
+    const double *H = nullptr;  int ldh = 0; int k = 0;
+    double beta = 0.0; const double *betap = nullptr;   // beta, or read from device when betap != null
+    int rule = 0; double lambda_fixed = 0.0; double dp_target = 0.0;
+    double *y = nullptr; double *lambda_out = nullptr; double *resid_out = nullptr;
+    const int *stop = nullptr;  // solver stop word (may be null)
+    int kmax = 0;     // last step of the solve: y is formed there (or at a breakdown step)
+    int always_y = 0; // form y at every k
+    int *path = nullptr; // optional: 1 where the parallel path was accepted, 0 where the exact
+                      // sequential path ran (indexed by k - 1); + 2 where CT_LAMBDA_LEARNED
+                      // fell back to GCV
+    int ystride = 0;  // batched launch: block b solves k = b + 1, y at y + b * ystride,
                       // lambda_out[b], resid_out[b], path[b]
+    const float *net = nullptr;   // CT_LAMBDA_LEARNED: FP32 network parameters (device)
+    float *features = nullptr;    // optional: row k - 1 (80 floats) gets the features of H_k
 };
 cudaError_t launch_small_solve(const SmallSolveParams &p, cudaStream_t s);
 // sets the kernel's shared-memory limit on the current device (call before a stream capture)
@@ -120,5 +123,24 @@ cudaError_t small_solve_prepare();
 // all steps k = 1..p.k of one solve in one launch (one CTA per k)
 cudaError_t launch_small_solve_batched(const SmallSolveParams &p, cudaStream_t s);
 size_t small_solve_smem_bytes(int k);
+
+// ----------------------------------------------------------------------------- learned lambda
+// network kernels (mlp.cu): P = FP32 parameter vector, X = n x 80 row-major features
+cudaError_t mlp_prepare();
+int mlp_num_params();
+int mlp_rows_per_block();
+cudaError_t launch_mlp_forward(const float *P, const float *X, int n, float *out, bool bf16,
+                               cudaStream_t s);
+// part: ceil(n / rows_per_block) * num_params floats; lpart: ceil(n / rows_per_block) floats
+cudaError_t launch_mlp_grad(const float *P, const float *X, const float *Y, int n, float *part,
+                            float *lpart, float *grad, float *loss, bool bf16, cudaStream_t s);
+cudaError_t launch_mlp_adam(float *P, const float *G, float *M, float *V, float lr, int t,
+                            cudaStream_t s);
+// training labels (lambda_data.cu): G = Z^T Z (K x K, FP64) and gv = Z^T x_true for Z = n x K
+// (column i at Z + i * ldz); labels[k-1] = log10(lambda*_k / sigma_1(H_k)), K <= 64
+cudaError_t launch_gram(const float *Z, int64_t ldz, int64_t n, int K, const float *xt,
+                        double *G, double *gv, cudaStream_t s);
+cudaError_t launch_lambda_labels(const double *H, int ldh, const double *betap, const double *G,
+                                 int K, const double *gv, float *labels, cudaStream_t s);
 
 }  // namespace ct

@@ -40,6 +40,7 @@
 #include <algorithm>
 
 #include "ct_internal.h"
+#include "mlp_dev.cuh"
 
 namespace ct {
 
@@ -689,6 +690,41 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
     __syncthreads();
     const double s1 = misc[8];
 
+    // ---------------- features of the projected problem (learned lambda rule; training data):
+    // k / K, then for the 32 largest sigma_i log10(sigma_i / sigma_1) (pad -16) and |c_i| / beta
+    // (pad 0), |c_{k+1}| / beta, log10 sigma_1, log10 beta, zeros to 80 entries
+    float *feat = reinterpret_cast<float *>(red);    // red is free until the lambda search
+    float *hbuf = feat + mlp::kIn;                   // 128 floats of network scratch
+    const bool learned = P.rule == CT_LAMBDA_LEARNED && P.net != nullptr;
+    if (P.features || learned) {
+        if (!fast && tid == 0) {
+            // the exact path leaves sigma unsorted: order (sigma_i, c_i) by decreasing sigma
+            for (int i = 1; i < k; ++i) {
+                const double sv = sig[i], cw = cv[i];
+                int j = i - 1;
+                while (j >= 0 && sig[j] < sv) { sig[j + 1] = sig[j]; cv[j + 1] = cv[j]; --j; }
+                sig[j + 1] = sv;
+                cv[j + 1] = cw;
+            }
+        }
+        __syncthreads();
+        const bool ok = s1 > 0.0 && beta > 0.0;
+        for (int i = tid; i < mlp::kIn; i += kSSThreads) {
+            float v = 0.f;
+            if (ok) {
+                if (i == 0) v = (float)((double)k / (double)P.kmax);
+                else if (i <= 32) v = (i - 1 < k) ? (float)fmax(log10(sig[i - 1] / s1), -16.0) : -16.f;
+                else if (i <= 64) v = (i - 33 < k) ? (float)(fabs(cv[i - 33]) / beta) : 0.f;
+                else if (i == 65) v = (float)(fabs(cv[k]) / beta);
+                else if (i == 66) v = (float)log10(s1);
+                else if (i == 67) v = (float)log10(beta);
+            }
+            feat[i] = v;
+            if (P.features) P.features[(size_t)(k - 1) * mlp::kIn + i] = v;
+        }
+        __syncthreads();
+    }
+
     // ---------------- lambda
     // rho^2(lambda) and trace(lambda) are evaluated by the whole block: threads 0-127 take
     // lambda_A, 128-255 lambda_B, one term each (k <= 160 < 2 * 128)
@@ -719,11 +755,31 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
         rA = s0 + ck; tA = (double)(k + 1) - s1_;
         rB = s2_ + ck; tB = (double)(k + 1) - s3;
     };
+    bool have_lam = true;
     if (P.rule == CT_LAMBDA_FIXED) {
         lam = P.lambda_fixed;
     } else if (!(s1 > 0.0)) {
         lam = 0.0;
-    } else if (P.rule == CT_LAMBDA_GCV) {
+    } else if (learned) {
+        // the network's output is log10(lambda / sigma_1), kept inside the GCV search range;
+        // a non-finite output falls back to GCV
+        if (warp == 0) {
+            const float o = mlp::infer_row_bf16(P.net, feat, hbuf);
+            if (lane == 0) misc[14] = (double)o;
+        }
+        __syncthreads();
+        const double o = misc[14];
+        if (isfinite(o)) {
+            lam = s1 * pow(10.0, fmin(fmax(o, -8.0), 0.0));
+        } else {
+            have_lam = false;
+            if (tid == 0 && P.path) *P.path |= 2;
+        }
+    } else {
+        have_lam = false;
+    }
+    if (have_lam) {
+    } else if (P.rule != CT_LAMBDA_DP) {   // GCV, and the learned rule's fallback
         for (int t = tid; t < kGcvGrid; t += kSSThreads) {
             double expo = (t == kGcvGrid - 1) ? 0.0 : -8.0 + t * (8.0 / (kGcvGrid - 1));
             double lt = s1 * pow(10.0, expo);

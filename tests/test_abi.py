@@ -70,3 +70,24 @@ def test_solver_rejects_bad_options(lib):
     assert st == Bn.CT_EINVAL
     st = lib.ct_projected_solve(None, 2, 1, 1.0, 0, 0.0, 0.0, None, None, None, None)
     assert st == Bn.CT_EINVAL
+
+
+def test_learned_lambda_entry_points_reject_bad_arguments(lib):
+    from paper_2602_17892_gb300 import _binding as Bn
+    o = Bn.HybridOpts()
+    lib.ct_hybrid_opts_default(ctypes.byref(o))
+    assert o.lambda_net_dev is None and o.features_dev is None
+    assert lib.ct_mlp_forward(None, None, 4, None, 1, None) == Bn.CT_EINVAL
+    assert lib.ct_mlp_grad(None, None, None, 4, None, None, 1, None) == Bn.CT_EINVAL
+    assert lib.ct_mlp_adam(None, None, None, None, 1e-3, 1, None) == Bn.CT_EINVAL
+    t = ctypes.c_int(0)
+    assert lib.ct_mlp_train(None, None, None, None, None, 4, 4, 1, 1e-3, ctypes.byref(t), None,
+                            1, None) == Bn.CT_EINVAL
+    assert lib.ct_lambda_samples(None, None, None, ctypes.byref(o), None, None, None, None,
+                                 None) == Bn.CT_EINVAL
+    # the learned rule without a network is refused before anything is launched
+    o.rule = Bn.RULES["learned"]
+    st = lib.ab_gmres_hybrid(ctypes.c_void_p(1), ctypes.c_void_p(16), None, ctypes.c_void_p(16),
+                             ctypes.byref(o), None, None)
+    assert st == Bn.CT_EINVAL and b"lambda_net_dev" in lib.ct_last_error()
+    assert Bn.CT_MLP_NPARAMS == 64 * 80 + 64 + 64 * 64 + 64 + 64 + 1
