@@ -156,7 +156,7 @@ static ct_status ws_get(ct_geom *g, int method, int K, int basis, Workspace **ou
     GeomExtra *ex = reinterpret_cast<GeomExtra *>(g->ws);
     Workspace *w = ex->ws[method];
     const int64_t img_ld = round_up(g->n, 4);
-    const int64_t sino_len = (int64_t)g->dg.n_views * g->dg.ndv * g->dg.sino_ld;
+    const int64_t sino_len = (int64_t)g->dg.n_views * g->dg.sino_view_ld;
     const int64_t L = (method == 0) ? sino_len : img_ld;
     if (w && w->K >= K && w->basis == basis && w->L == L) { *out = w; return CT_OK; }
     ws_free(w);
@@ -249,6 +249,51 @@ static Ray2D make_ray(const ct_geom_desc *d, int view, int bin)
     return r;
 }
 
+// In-plane (fan) part of the rays of column iu of a cone view: every ray of the column has the
+// x-y projection of the fan ray through detector column iu, D = P - S unnormalised.
+static RayXY make_ray_xy(const ct_geom_desc *d, int view, int iu)
+{
+    const double th = d->angles[view];
+    const double c = cos(th), sn = sin(th);
+    const double u = (iu - (d->n_det_u - 1) / 2.0) * d->pitch_u;
+    const double Sx = d->sid * c, Sy = d->sid * sn;
+    const double off = d->sdd - d->sid;
+    const double Dx = (-off * c - u * sn) - Sx, Dy = (-off * sn + u * c) - Sy;
+    const double h = d->pixel;
+    const int axis = fabs(Dx) >= fabs(Dy) ? 0 : 1;
+    const double Da = axis == 0 ? Dx : Dy, Do = axis == 0 ? Dy : Dx;
+    const double Sa = axis == 0 ? Sx : Sy, So = axis == 0 ? Sy : Sx;
+    const int n_drive = axis == 0 ? d->nx : d->ny, n_other = axis == 0 ? d->ny : d->nx;
+    const double slope = Do / Da;
+    const double bmid = (So - Sa * slope) / h + (n_other - 1) / 2.0;
+    const double tmid = (n_drive - 1) / 2.0;
+    int lo = 0, hi = n_drive - 1;
+    if (fabs(slope) < 1e-300) {
+        if (!(bmid >= -1.0 && bmid < n_other)) { lo = 1; hi = 0; }
+    } else {
+        double ta = tmid + (-1.0 - bmid) / slope, tb = tmid + (n_other - bmid) / slope;
+        double tl = std::min(ta, tb), tu = std::max(ta, tb);
+        double clo = ceil(tl - 1e-6), chi = floor(tu + 1e-6);
+        if (clo > lo) lo = (clo > hi + 1) ? hi + 1 : (int)clo;
+        if (chi < hi) hi = (chi < lo - 1) ? lo - 1 : (int)chi;
+        if (hi < lo) { lo = 1; hi = 0; }
+    }
+    RayXY r;
+    r.bmid = (float)bmid;
+    r.bslope = (float)slope;
+    r.dxy2 = (float)((Dx * Dx + Dy * Dy) / (Da * Da));
+    r.packed = (uint32_t)lo | ((uint32_t)hi << 15) | ((uint32_t)axis << 30);
+    r.rda = 1.0 / Da;
+    r.sa_h = Sa / h;
+    r.sx_h = Sx / h;
+    r.sy_h = Sy / h;
+    r.dx = Dx;
+    r.dy = Dy;
+    return r;
+}
+
+cudaError_t count_joseph3d_samples(const ct_geom *g, int64_t *out);
+
 extern "C" {
 
 const char *ct_last_error(void) { return g_last_error.c_str(); }
@@ -271,8 +316,9 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
 {
     if (!d || !out) return einval("ct_geom_create: null argument");
     *out = nullptr;
-    if (d->kind != CT_PARALLEL2D && d->kind != CT_FANFLAT2D)
+    if (d->kind != CT_PARALLEL2D && d->kind != CT_FANFLAT2D && d->kind != CT_CONE3D)
         return einval("ct_geom_create: unsupported geometry kind");
+    const bool cone = d->kind == CT_CONE3D;
     if (d->nx < 1 || d->ny < 1 || d->nx > 16384 || d->ny > 16384)
         return einval("ct_geom_create: image size out of range [1, 16384]");
     if (d->n_views < 1 || d->n_det_u < 1 || d->n_det_u > (1 << 20))
@@ -281,10 +327,16 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     if (!(d->pixel > 0) || !(d->pitch_u > 0)) return einval("ct_geom_create: pixel and pitch must be > 0");
     for (int v = 0; v < d->n_views; ++v)
         if (!isfinite(d->angles[v])) return einval("ct_geom_create: non-finite angle");
-    if (d->kind == CT_FANFLAT2D) {
+    if (d->kind != CT_PARALLEL2D) {
         double half_diag = 0.5 * d->pixel * sqrt((double)d->nx * d->nx + (double)d->ny * d->ny);
         if (!(d->sid > half_diag) || !(d->sdd > d->sid))
-            return einval("ct_geom_create: fan geometry needs SDD > SID > image half-diagonal");
+            return einval("ct_geom_create: fan/cone geometry needs SDD > SID > image half-diagonal");
+    }
+    if (cone) {
+        if (d->nz < 1 || d->nz > 16384) return einval("ct_geom_create: nz out of range [1, 16384]");
+        if (d->n_det_v < 1 || d->n_det_v > 65535 || d->n_views > 65535)
+            return einval("ct_geom_create: cone needs 1 <= n_det_v, n_views <= 65535");
+        if (!(d->pitch_v > 0)) return einval("ct_geom_create: pitch_v must be > 0");
     }
     ct_geom *g = new ct_geom();
     memset(g, 0, sizeof(*g));
@@ -292,29 +344,47 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     g->angles_host = new double[d->n_views];
     memcpy(g->angles_host, d->angles, sizeof(double) * d->n_views);
     g->desc.angles = g->angles_host;
-    g->desc.nz = 1;
-    g->desc.n_det_v = 1;
-    g->n = (int64_t)d->nx * d->ny;
-    g->m = (int64_t)d->n_views * d->n_det_u;
+    if (!cone) {
+        g->desc.nz = 1;
+        g->desc.n_det_v = 1;
+        g->desc.pitch_v = 1.0;
+    }
+    const int nz = g->desc.nz, ndv = g->desc.n_det_v;
+    g->n = (int64_t)d->nx * d->ny * nz;
+    g->m = (int64_t)d->n_views * ndv * d->n_det_u;
     DeviceGeom &dg = g->dg;
-    dg.kind = d->kind; dg.nx = d->nx; dg.ny = d->ny; dg.nz = 1;
-    dg.h = (float)d->pixel; dg.n_views = d->n_views; dg.ndu = d->n_det_u; dg.ndv = 1;
-    dg.pitch_u = (float)d->pitch_u; dg.pitch_v = 1.f; dg.sid = (float)d->sid; dg.sdd = (float)d->sdd;
+    dg.kind = d->kind; dg.nx = d->nx; dg.ny = d->ny; dg.nz = nz;
+    dg.h = (float)d->pixel; dg.n_views = d->n_views; dg.ndu = d->n_det_u; dg.ndv = ndv;
+    dg.pitch_u = (float)d->pitch_u; dg.pitch_v = (float)g->desc.pitch_v;
+    dg.sid = (float)d->sid; dg.sdd = (float)d->sdd;
     dg.row_pairs_ld = (int)round_up(d->nx + 1, 16);
     dg.col_pairs_ld = (int)round_up(d->ny + 1, 16);
     dg.sino_ld = (int)round_up(d->n_det_u + 4, 4);
+    dg.sino_view_ld = cone ? (int64_t)(ndv + 3) * dg.sino_ld : dg.sino_ld;
+    dg.sino_row0 = cone ? dg.sino_ld : 0;
+    dg.plane_x = cone ? (int64_t)(nz + 2) * dg.col_pairs_ld : 0;
+    dg.plane_y = cone ? (int64_t)(nz + 2) * dg.row_pairs_ld : 0;
     dg.tune_a_threads = 256;
-    dg.tune_b_rows = 8;
+    dg.tune_b_rows = cone ? 4 : 8;
 
-    std::vector<Ray2D> rays((size_t)g->m);
+    std::vector<Ray2D> rays;
+    std::vector<RayXY> rays_xy;
     g->a_samples = 0;
-    for (int v = 0; v < d->n_views; ++v)
-        for (int j = 0; j < d->n_det_u; ++j) {
-            Ray2D r = make_ray(&g->desc, v, j);
-            rays[(size_t)v * d->n_det_u + j] = r;
-            int lo = r.packed & 0x7fff, hi = (r.packed >> 15) & 0x7fff;
-            if (hi >= lo) g->a_samples += hi - lo + 1;
-        }
+    if (cone) {
+        rays_xy.resize((size_t)d->n_views * d->n_det_u);
+        for (int v = 0; v < d->n_views; ++v)
+            for (int j = 0; j < d->n_det_u; ++j)
+                rays_xy[(size_t)v * d->n_det_u + j] = make_ray_xy(&g->desc, v, j);
+    } else {
+        rays.resize((size_t)g->m);
+        for (int v = 0; v < d->n_views; ++v)
+            for (int j = 0; j < d->n_det_u; ++j) {
+                Ray2D r = make_ray(&g->desc, v, j);
+                rays[(size_t)v * d->n_det_u + j] = r;
+                int lo = r.packed & 0x7fff, hi = (r.packed >> 15) & 0x7fff;
+                if (hi >= lo) g->a_samples += hi - lo + 1;
+            }
+    }
     std::vector<ViewBP> views(d->n_views);
     for (int v = 0; v < d->n_views; ++v) {
         double c = cos(d->angles[v]), s = sin(d->angles[v]);
@@ -323,21 +393,39 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
         views[v].a = (float)(d->pixel * c / d->pitch_u);
         views[v].b = (float)(d->pixel * s / d->pitch_u);
     }
+    const size_t prow_n = cone ? (size_t)(d->ny + 2) * dg.plane_y : (size_t)d->ny * dg.row_pairs_ld;
+    const size_t pcol_n = cone ? (size_t)(d->nx + 2) * dg.plane_x : (size_t)d->nx * dg.col_pairs_ld;
     cudaError_t e = cudaSuccess;
-    e = dalloc(&g->rays_dev, rays.size());
-    if (e == cudaSuccess) e = cudaMemcpy(g->rays_dev, rays.data(), sizeof(Ray2D) * rays.size(), cudaMemcpyHostToDevice);
+    if (cone) {
+        e = dalloc(&g->rays_xy_dev, rays_xy.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g->rays_xy_dev, rays_xy.data(), sizeof(RayXY) * rays_xy.size(), cudaMemcpyHostToDevice);
+    } else {
+        e = dalloc(&g->rays_dev, rays.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g->rays_dev, rays.data(), sizeof(Ray2D) * rays.size(), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = dalloc(&g->views_dev, views.size());
     if (e == cudaSuccess) e = cudaMemcpy(g->views_dev, views.data(), sizeof(ViewBP) * views.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = dalloc(&g->prow_dev, (size_t)d->ny * dg.row_pairs_ld);
-    if (e == cudaSuccess) e = dalloc(&g->pcol_dev, (size_t)d->nx * dg.col_pairs_ld);
-    if (e == cudaSuccess) e = dalloc(&g->sino_pad_dev, (size_t)d->n_views * dg.sino_ld);
+    if (e == cudaSuccess) e = dalloc(&g->prow_dev, prow_n);
+    if (e == cudaSuccess) e = dalloc(&g->pcol_dev, pcol_n);
+    if (e == cudaSuccess) e = dalloc(&g->sino_pad_dev, (size_t)d->n_views * dg.sino_view_ld);
     if (e != cudaSuccess) {
         set_error(std::string("ct_geom_create: ") + cudaGetErrorString(e));
         ct_geom_destroy(g);
         return CT_ENOMEM;
     }
     dg.rays = g->rays_dev;
+    dg.rays_xy = g->rays_xy_dev;
     dg.views = g->views_dev;
+    if (cone) {
+        e = count_joseph3d_samples(g, &g->a_samples);
+        if (e != cudaSuccess) {
+            set_error(std::string("ct_geom_create: ") + cudaGetErrorString(e));
+            ct_geom_destroy(g);
+            return CT_ECUDA;
+        }
+    }
     g->ws = reinterpret_cast<struct Workspace *>(new GeomExtra());
     *out = g;
     return CT_OK;
@@ -352,7 +440,8 @@ void ct_geom_destroy(ct_geom *g)
         ws_free(ex->ws[1]);
         delete ex;
     }
-    cudaFree(g->rays_dev); cudaFree(g->views_dev); cudaFree(g->prow_dev); cudaFree(g->pcol_dev);
+    cudaFree(g->rays_dev); cudaFree(g->rays_xy_dev); cudaFree(g->views_dev);
+    cudaFree(g->prow_dev); cudaFree(g->pcol_dev);
     cudaFree(g->sino_pad_dev);
     delete[] g->angles_host;
     delete g;
@@ -383,7 +472,7 @@ ct_status ct_forward_A(ct_geom *g, const float *x_dev, float *y_dev, ct_stream_t
         CT_CUDA(launch_image_pairs(g, x_dev, nullptr, s));
     }
     CT_PHASE(CT_PH_FORWARD, 1, s);
-    CT_CUDA(launch_joseph2d(g, y_dev, g->dg.ndu, 0, nullptr, s));
+    CT_CUDA(launch_forward_proj(g, y_dev, false, nullptr, s));
     return CT_OK;
 }
 
@@ -396,7 +485,7 @@ ct_status ct_back_B(ct_geom *g, const float *y_dev, float *x_dev, ct_stream_t st
         CT_CUDA(launch_pad_sino(g, y_dev, g->sino_pad_dev, s));
     }
     CT_PHASE(CT_PH_BACK, 1, s);
-    CT_CUDA(launch_pixbp2d(g, g->sino_pad_dev, x_dev, nullptr, s));
+    CT_CUDA(launch_back_proj(g, g->sino_pad_dev, x_dev, nullptr, s));
     return CT_OK;
 }
 
@@ -508,7 +597,6 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
     *wout = w;
     const int K = o->max_iters;
     const int64_t L = w->L, ld = w->L;
-    const int sld = g->dg.sino_ld;
     ArnoldiScratch sc{w->partial, w->counter, kMaxBlocks, w->K};
     const double dp_target = o->tau * o->noise_norm;
     CT_CUDA(cudaMemsetAsync(w->stop, 0, 2 * sizeof(int), s));
@@ -520,9 +608,9 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
         CT_CUDA(launch_pad_sino(g, b_dev, w->vec, s));
         if (u0_dev) {
             CT_CUDA(launch_pad_sino(g, u0_dev, w->sino, s));
-            CT_CUDA(launch_pixbp2d(g, w->sino, w->img, nullptr, s));
+            CT_CUDA(launch_back_proj(g, w->sino, w->img, nullptr, s));
             CT_CUDA(launch_image_pairs(g, w->img, nullptr, s));
-            CT_CUDA(launch_joseph2d(g, w->q, sld, 2, nullptr, s));
+            CT_CUDA(launch_forward_proj(g, w->q, true, nullptr, s));
             CT_CUDA(launch_rsub(w->vec, w->q, L, kMaxBlocks, s));
             CT_CUDA(normalize_first_basis(o->basis, w->q, L, w->W, sc, w->aux, w->stop, w->cur, s));
         } else {
@@ -535,7 +623,7 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
         const float *wk = w->cur ? w->cur : static_cast<float *>(w->W) + (int64_t)k * ld;
         {
             CT_PHASE(CT_PH_BACK, 1, s);
-            CT_CUDA(launch_pixbp2d(g, wk, w->img, w->stop, s));       // line 5: B w_k
+            CT_CUDA(launch_back_proj(g, wk, w->img, w->stop, s));       // line 5: B w_k
         }
         {
             CT_PHASE(CT_PH_LAYOUT, 1, s);
@@ -543,7 +631,7 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
         }
         {
             CT_PHASE(CT_PH_FORWARD, 1, s);
-            CT_CUDA(launch_joseph2d(g, w->q, sld, 2, w->stop, s));   //          A (B w_k)
+            CT_CUDA(launch_forward_proj(g, w->q, true, w->stop, s));   //          A (B w_k)
         }
         {
             CT_PHASE(CT_PH_ARNOLDI, o->reorth ? 4 : 3, s);               // lines 6-11
@@ -561,7 +649,7 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
     }
     {
         CT_PHASE(CT_PH_BACK, 1, s);
-        CT_CUDA(launch_pixbp2d(g, w->q, x_dev, nullptr, s));
+        CT_CUDA(launch_back_proj(g, w->q, x_dev, nullptr, s));
     }
     return CT_OK;
 }
@@ -589,8 +677,7 @@ static ct_status enqueue_ba(ct_geom *g, const float *b_dev, const float *x0_dev,
     *wout = w;
     const int K = o->max_iters;
     const int64_t L = w->L, ld = w->L;
-    const int sld = g->dg.sino_ld;
-    const int64_t msino = (int64_t)g->dg.n_views * sld;
+    const int64_t msino = (int64_t)g->dg.n_views * g->dg.sino_view_ld;
     ArnoldiScratch sc{w->partial, w->counter, kMaxBlocks, w->K};
     const double dp_target = o->tau * o->noise_norm;
     CT_CUDA(cudaMemsetAsync(w->stop, 0, 2 * sizeof(int), s));
@@ -604,11 +691,11 @@ static ct_status enqueue_ba(ct_geom *g, const float *b_dev, const float *x0_dev,
             CT_CUDA(cudaMemsetAsync(w->img, 0, sizeof(float) * L, s));
             CT_CUDA(cudaMemcpyAsync(w->img, x0_dev, sizeof(float) * g->n, cudaMemcpyDeviceToDevice, s));
             CT_CUDA(launch_image_pairs(g, w->img, nullptr, s));
-            CT_CUDA(launch_joseph2d(g, w->q, sld, 2, nullptr, s));   // q as sinogram scratch
+            CT_CUDA(launch_forward_proj(g, w->q, true, nullptr, s));   // q as sinogram scratch
             CT_CUDA(launch_rsub(w->sino, w->q, msino, kMaxBlocks, s));
-            CT_CUDA(launch_pixbp2d(g, w->q, w->vec, nullptr, s));
+            CT_CUDA(launch_back_proj(g, w->q, w->vec, nullptr, s));
         } else {
-            CT_CUDA(launch_pixbp2d(g, w->sino, w->vec, nullptr, s));
+            CT_CUDA(launch_back_proj(g, w->sino, w->vec, nullptr, s));
         }
         CT_CUDA(normalize_first_basis(o->basis, w->vec, L, w->W, sc, w->aux, w->stop, w->cur, s));
     }
@@ -622,11 +709,11 @@ static ct_status enqueue_ba(ct_geom *g, const float *b_dev, const float *x0_dev,
         }
         {
             CT_PHASE(CT_PH_FORWARD, 1, s);
-            CT_CUDA(launch_joseph2d(g, w->sino, sld, 2, w->stop, s));
+            CT_CUDA(launch_forward_proj(g, w->sino, true, w->stop, s));
         }
         {
             CT_PHASE(CT_PH_BACK, 1, s);
-            CT_CUDA(launch_pixbp2d(g, w->sino, w->q, w->stop, s));     //          B (A w_k)
+            CT_CUDA(launch_back_proj(g, w->sino, w->q, w->stop, s));     //          B (A w_k)
         }
         {
             CT_PHASE(CT_PH_ARNOLDI, o->reorth ? 4 : 3, s);
@@ -815,7 +902,7 @@ extern "C" ct_status ct_lambda_samples(ct_geom *g, const float *b_dev, const flo
     CT_CUDA(cudaMallocAsync((void **)&Z, sizeof(float) * (size_t)K * img_ld, s));
     CT_CUDA(cudaMallocAsync((void **)&G, sizeof(double) * (size_t)K * (K + 1), s));
     for (int j = 0; j < K; ++j)         // Z = B W_K (the AB basis is in padded-sinogram layout)
-        CT_CUDA(launch_pixbp2d(g, static_cast<const float *>(w->W) + (int64_t)j * w->L,
+        CT_CUDA(launch_back_proj(g, static_cast<const float *>(w->W) + (int64_t)j * w->L,
                                Z + (int64_t)j * img_ld, nullptr, s));
     CT_CUDA(launch_gram(Z, img_ld, g->n, K, x_true_dev, G, G + (size_t)K * K, s));
     CT_CUDA(launch_lambda_labels(w->H, w->K + 1, w->aux + 2, G, K, G + (size_t)K * K, labels_dev, s));
@@ -865,6 +952,11 @@ static std::map<std::tuple<int, int, int, int, int, int>, std::pair<int, int>> g
 extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, int *a_threads, int *b_rows)
 {
     if (!g) return einval("ct_geom_autotune: null geometry");
+    if (g->desc.kind == CT_CONE3D) {      // the 3D kernels have one launch shape
+        if (a_threads) *a_threads = 256;
+        if (b_rows) *b_rows = 4;
+        return CT_OK;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     int dev = 0;
     CT_CUDA(cudaGetDevice(&dev));
@@ -916,7 +1008,7 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, int *a_thr
     ct_status st = time_best([&]() { return launch_joseph2d(g, y, g->dg.sino_ld, 2, nullptr, s); },
                              a_cand, 3, &g->dg.tune_a_threads);
     if (st == CT_OK)
-        st = time_best([&]() { return launch_pixbp2d(g, y, x, nullptr, s); }, b_cand, 3,
+        st = time_best([&]() { return launch_back_proj(g, y, x, nullptr, s); }, b_cand, 3,
                        &g->dg.tune_b_rows);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -36,9 +36,19 @@ struct __align__(16) ViewBP {
     float a, b;     // parallel: h cos / pitch, h sin / pitch; fan: unused
 };
 
-// 3D cone per-view constants (source position and detector frame in voxel units).
-struct __align__(16) View3D {
-    float cs, sn, pad0, pad1;
+// One (view, detector column u) of a cone geometry.  All rays of the column share their x-y
+// projection (the fan ray of that column), so its in-plane Joseph parameters are computed once
+// on the host in FP64; the z part depends on the detector row v and is formed per ray.
+// D = (detector point - source) in physical units, Da its component on the driving axis.
+struct __align__(16) RayXY {
+    float bmid, bslope;   // in-plane tap position across the driving axis at its central plane
+                          // (index units) and its change per plane
+    float dxy2;           // (Dx^2 + Dy^2) / Da^2
+    uint32_t packed;      // t_lo (bits 0-14) | t_hi (bits 15-29) | axis (bits 30-31: 0 x, 1 y)
+    double rda;           // 1 / Da
+    double sa_h;          // source coordinate on the driving axis / h
+    double sx_h, sy_h;    // source / h      (rays driven along z)
+    double dx, dy;        // Dx, Dy          (rays driven along z)
 };
 
 struct DeviceGeom {
@@ -52,8 +62,14 @@ struct DeviceGeom {
     int sino_ld;        // padded sinogram row length: ndu + 4 (2 zero bins each side)
     int tune_a_threads; // Joseph A: rays (threads) per block, chosen by ct_geom_autotune
     int tune_b_rows;    // pixel-driven B: block of 32 x tune_b_rows pixels
+    int64_t sino_view_ld; // floats per view in the padded sinogram (2D: sino_ld; 3D: (ndv + 2)
+                          // rows of sino_ld, detector row 0 at row 1)
+    int sino_row0;      // offset of detector row 0 inside a padded view (0 in 2D, sino_ld in 3D)
+    int64_t plane_x;    // 3D: pairs per plane of P_x ((nz + 2) * col_pairs_ld)
+    int64_t plane_y;    // 3D: pairs per plane of P_y ((nz + 2) * row_pairs_ld)
     // tables
     const Ray2D *rays;  // m rays (2D)
+    const RayXY *rays_xy; // n_views x ndu (3D)
     const ViewBP *views;
 };
 
@@ -67,10 +83,11 @@ struct ct_geom {
     ct::DeviceGeom dg;
     // device allocations owned by the geometry
     ct::Ray2D *rays_dev;
+    ct::RayXY *rays_xy_dev;
     ct::ViewBP *views_dev;
-    float2 *prow_dev;   // [ny][row_pairs_ld] pairs along x
-    float2 *pcol_dev;   // [nx][col_pairs_ld] pairs along y
-    float *sino_pad_dev;  // [n_views * ndv][sino_ld]
+    float2 *prow_dev;   // 2D: [ny][row_pairs_ld] pairs along x; 3D: P_y, [ny + 2][nz + 2][row_pairs_ld]
+    float2 *pcol_dev;   // 2D: [nx][col_pairs_ld] pairs along y; 3D: P_x, [nx + 2][nz + 2][col_pairs_ld]
+    float *sino_pad_dev;  // [n_views][sino_view_ld]
     // solver workspace (grown on demand)
     struct Workspace *ws;
 };
@@ -80,15 +97,27 @@ namespace ct {
 // ----------------------------------------------------------------------------- projectors
 // Every launcher takes an optional device stop word: when non-null and non-zero at kernel
 // start, the kernel returns at once (a solver that met breakdown skips the remaining steps).
-// Image x (row-major, n floats) -> the two padded pair layouts used by the Joseph kernel.
+// Image x (row-major, n floats) -> the two padded pair layouts used by the Joseph kernels.
 cudaError_t launch_image_pairs(const ct_geom *g, const float *x, const int *stop, cudaStream_t s);
-// y[view][bin] -> padded sinogram rows (row length sino_ld, bin j at index j + 2).
+// y[view][v][u] -> padded sinogram (sino_view_ld floats per view, row length sino_ld, bin u of
+// row v at index sino_row0 + v * sino_ld + u + 2).
 cudaError_t launch_pad_sino(const ct_geom *g, const float *y, float *ypad, cudaStream_t s);
-// Joseph A from the pair layouts; output row length y_ld, bin j at index y_off + j.
+// y = A x from the pair layouts: padded != 0 writes the padded sinogram layout, else the dense
+// [view][v][u] layout.
+cudaError_t launch_forward_proj(const ct_geom *g, float *y, bool padded, const int *stop,
+                                cudaStream_t s);
+// x = B y from a padded sinogram
+cudaError_t launch_back_proj(const ct_geom *g, const float *ypad, float *x, const int *stop,
+                             cudaStream_t s);
+// kind-specific launchers (2D: proj2d.cu, 3D: proj3d.cu); element (view, v, u) of y at
+// view * y_view_ld + v * y_ld + y_off + u
 cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, const int *stop,
                             cudaStream_t s);
-// pixel-driven B from a padded sinogram (row length sino_ld)
 cudaError_t launch_pixbp2d(const ct_geom *g, const float *ypad, float *x, const int *stop,
+                           cudaStream_t s);
+cudaError_t launch_joseph3d(const ct_geom *g, float *y, int64_t y_view_ld, int y_ld, int y_off,
+                            const int *stop, cudaStream_t s);
+cudaError_t launch_voxbp3d(const ct_geom *g, const float *ypad, float *x, const int *stop,
                            cudaStream_t s);
 
 // ----------------------------------------------------------------------------- Arnoldi

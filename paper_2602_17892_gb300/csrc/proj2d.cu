@@ -8,72 +8,107 @@
 // bounds test: rays driven along x read P_col (neighbouring rays of a warp read adjacent
 // pairs), rays driven along y read P_row.  The padded sinogram has 2 zero bins on each side
 // of every detector row, so the backprojector's two taps also need no bounds test.
+#include <algorithm>
+
 #include "ct_internal.h"
 
 namespace ct {
 
 // ---------------------------------------------------------------------------- pair layouts
-// One 32 x 32 tile of pair indices per block; a 33 x 33 halo tile of x sits in smem.
+// One 32 x 32 tile of pair indices of one z slice (blockIdx.z) per block; a 33 x 33 halo tile
+// of the slice sits in smem.  Pair (r, j) of P_row goes to prow[(r + roff) * rs + z_off(z) + j]
+// and pair (c, i) of P_col to pcol[(c + roff) * cs + z_off(z) + i], z_off(z) = (z + zoff) * zs
+// (2D: roff = zoff = 0; 3D: one zero plane and one zero row of padding, roff = zoff = 1).
 __global__ void __launch_bounds__(256) image_pairs_kernel(
-    const float *__restrict__ x, int nx, int ny, float2 *__restrict__ prow, int prow_ld,
-    float2 *__restrict__ pcol, int pcol_ld, const int *stop)
+    const float *__restrict__ x, int nx, int ny, float2 *__restrict__ prow, int64_t rs,
+    int64_t rzs, float2 *__restrict__ pcol, int64_t cs, int64_t czs, int off, const int *stop)
 {
     if (stop && stop[0] != 0) return;
     __shared__ float tile[33][34];
-    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32, z = blockIdx.z;
+    const float *xs = x + (int64_t)z * nx * ny;
     for (int t = threadIdx.x; t < 33 * 33; t += blockDim.x) {
         int tr = t / 33, tc = t % 33;
         int r = r0 - 1 + tr, c = c0 - 1 + tc;
-        tile[tr][tc] = (r >= 0 && r < ny && c >= 0 && c < nx) ? x[(int64_t)r * nx + c] : 0.f;
+        tile[tr][tc] = (r >= 0 && r < ny && c >= 0 && c < nx) ? xs[(int64_t)r * nx + c] : 0.f;
     }
     __syncthreads();
     // P_row: rows r in [r0, r0+32) (< ny), pair index j in [c0, c0+32) (<= nx)
+    float2 *pr = prow + (int64_t)off * rs + (int64_t)(z + off) * rzs;
     for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
         int tr = t / 32, tj = t % 32;
         int r = r0 + tr, j = c0 + tj;
         if (r < ny && j <= nx)
-            prow[(int64_t)r * prow_ld + j] = make_float2(tile[tr + 1][tj], tile[tr + 1][tj + 1]);
+            pr[(int64_t)r * rs + j] = make_float2(tile[tr + 1][tj], tile[tr + 1][tj + 1]);
     }
     // P_col: column c in [c0, c0+32) (< nx), pair index i in [r0, r0+32) (<= ny)
+    float2 *pc = pcol + (int64_t)off * cs + (int64_t)(z + off) * czs;
     for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
         int tc = t / 32, ti = t % 32;
         int c = c0 + tc, i = r0 + ti;
         if (c < nx && i <= ny)
-            pcol[(int64_t)c * pcol_ld + i] = make_float2(tile[ti][tc + 1], tile[ti + 1][tc + 1]);
+            pc[(int64_t)c * cs + i] = make_float2(tile[ti][tc + 1], tile[ti + 1][tc + 1]);
     }
 }
 
 cudaError_t launch_image_pairs(const ct_geom *g, const float *x, const int *stop, cudaStream_t s)
 {
     const DeviceGeom &d = g->dg;
-    dim3 grid((d.nx + 1 + 31) / 32, (d.ny + 1 + 31) / 32);
-    image_pairs_kernel<<<grid, 256, 0, s>>>(x, d.nx, d.ny, g->prow_dev, d.row_pairs_ld,
-                                            g->pcol_dev, d.col_pairs_ld, stop);
+    dim3 grid((d.nx + 1 + 31) / 32, (d.ny + 1 + 31) / 32, d.nz);
+    if (d.kind == CT_CONE3D)
+        image_pairs_kernel<<<grid, 256, 0, s>>>(x, d.nx, d.ny, g->prow_dev, d.plane_y,
+                                                d.row_pairs_ld, g->pcol_dev, d.plane_x,
+                                                d.col_pairs_ld, 1, stop);
+    else
+        image_pairs_kernel<<<grid, 256, 0, s>>>(x, d.nx, d.ny, g->prow_dev, d.row_pairs_ld, 0,
+                                                g->pcol_dev, d.col_pairs_ld, 0, 0, stop);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------- padded sinogram
-__global__ void pad_sino_kernel(const float *__restrict__ y, int rows, int nd, int ld,
-                                float *__restrict__ ypad)
+// y[view][v][u] -> ypad[view * view_ld + row0 + v * ld + 2 + u]; the margins are zero
+__global__ void pad_sino_kernel(const float *__restrict__ y, int n_views, int nv, int nu, int ld,
+                                int64_t view_ld, int row0, float *__restrict__ ypad)
 {
-    int64_t total = (int64_t)rows * ld;
+    const int64_t total = (int64_t)n_views * nv * ld;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = t / ld;
-        int j = (int)(t - r * ld) - 2;
-        ypad[t] = (j >= 0 && j < nd) ? y[r * nd + j] : 0.f;
+        const int64_t r = t / ld;                   // view * nv + v
+        const int j = (int)(t - r * ld) - 2;
+        const int64_t view = r / nv;
+        const int v = (int)(r - view * nv);
+        ypad[view * view_ld + row0 + (int64_t)v * ld + j + 2] =
+            (j >= 0 && j < nu) ? y[r * nu + j] : 0.f;
     }
 }
 
 cudaError_t launch_pad_sino(const ct_geom *g, const float *y, float *ypad, cudaStream_t s)
 {
     const DeviceGeom &d = g->dg;
-    int rows = d.n_views * d.ndv;
-    int64_t total = (int64_t)rows * d.sino_ld;
-    int blocks = (int)((total + 255) / 256);
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    pad_sino_kernel<<<blocks, 256, 0, s>>>(y, rows, d.ndu, d.sino_ld, ypad);
+    const int64_t total = (int64_t)d.n_views * d.ndv * d.sino_ld;
+    int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    pad_sino_kernel<<<blocks, 256, 0, s>>>(y, d.n_views, d.ndv, d.ndu, d.sino_ld, d.sino_view_ld,
+                                           d.sino_row0, ypad);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------- dispatch
+cudaError_t launch_forward_proj(const ct_geom *g, float *y, bool padded, const int *stop,
+                                cudaStream_t s)
+{
+    const DeviceGeom &d = g->dg;
+    if (d.kind == CT_CONE3D)
+        return padded ? launch_joseph3d(g, y, d.sino_view_ld, d.sino_ld, d.sino_row0 + 2, stop, s)
+                      : launch_joseph3d(g, y, (int64_t)d.ndv * d.ndu, d.ndu, 0, stop, s);
+    return padded ? launch_joseph2d(g, y, d.sino_ld, 2, stop, s)
+                  : launch_joseph2d(g, y, d.ndu, 0, stop, s);
+}
+
+cudaError_t launch_back_proj(const ct_geom *g, const float *ypad, float *x, const int *stop,
+                             cudaStream_t s)
+{
+    if (g->dg.kind == CT_CONE3D) return launch_voxbp3d(g, ypad, x, stop, s);
+    return launch_pixbp2d(g, ypad, x, stop, s);
 }
 
 // ---------------------------------------------------------------------------- Joseph A

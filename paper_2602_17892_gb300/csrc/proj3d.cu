@@ -1,0 +1,271 @@
+// 3D cone-beam projector kernels: ray-driven Joseph forward projector A (bilinear taps in the
+// planes of the driving axis) and voxel-driven backprojector B (bilinear interpolation on the
+// flat detector), the 3D form of the unmatched pair of Sec. 2.
+//
+// Data layout in HBM (all FP32; the volume is x[z][y][x]):
+//   P_x[x+1][z+1][y+1] = (x[z][y][x], x[z][y+1][x]) for x in [-1, nx], z in [-1, nz], y in [-1, ny)
+//   P_y[y+1][z+1][x+1] = (x[z][y][x], x[z][y][x+1]) for y in [-1, ny], z in [-1, nz], x in [-1, nx)
+// (zero outside the volume; each plane has (nz + 2) rows of ld pairs).  A Joseph sample is two
+// 8-byte loads (the two rows of its 2 x 2 taps) with no bounds test: rays driven along x read
+// P_x, along y P_y, and the rare rays driven along z read P_y across its planes.
+// The padded sinogram of a cone geometry has, per view, one zero detector row above the
+// detector rows and two below, and 2 zero bins on each side of every row, so B's four taps need
+// no bounds test either (positions are clamped into the zero margins).
+#include "ct_internal.h"
+
+namespace ct {
+
+// ---------------------------------------------------------------------------- Joseph A (3D)
+// One thread per ray (view, row v, column u); a block covers consecutive u of one (view, v),
+// and the grid runs v slowest, so the blocks in flight share a band of z planes in L2.
+// In-plane geometry of the ray comes from the (view, u) table (FP64 on the host); the z part
+// and the clipped plane range are computed per ray in FP64, the samples in FP32.
+// Plane range and sampling parameters of ray (view, iv, column R): mode 0/1 = driven along
+// x/y (tap positions b = bmid + bslope t', z = zmid + zslope t', t' = t - (n_drive-1)/2),
+// mode 2 = driven along z (x and y positions per sample from the FP64 fields).
+struct Ray3D {
+    int lo, hi, mode;
+    float weight;
+    double zmid, zslope;            // modes 0/1
+    double xmid, xs, ymid, ys;      // mode 2
+};
+
+__device__ __forceinline__ void clip_range(double mid, double sl, double tmid, int n, int &lo,
+                                           int &hi)
+{
+    if (sl == 0.0) {
+        if (!(mid >= -1.0 && mid < n)) hi = lo - 1;
+        return;
+    }
+    const double r = 1.0 / sl;
+    const double ta = tmid + (-1.0 - mid) * r, tb = tmid + ((double)n - mid) * r;
+    const double tl = fmin(ta, tb), th = fmax(ta, tb);
+    const double clo = ceil(tl - 1e-6), chi = floor(th + 1e-6);
+    if (clo > lo) lo = (clo > hi + 1) ? hi + 1 : (int)clo;
+    if (chi < hi) hi = (chi < lo - 1) ? lo - 1 : (int)chi;
+}
+
+__device__ __forceinline__ Ray3D setup_ray3d(const RayXY &R, int iv, int ndv, double pitch_v,
+                                             double h, int nx, int ny, int nz)
+{
+    Ray3D q;
+    const double v = (iv - 0.5 * (ndv - 1)) * pitch_v;
+    if (fabs(v) * fabs(R.rda) <= 1.0) {
+        // driven along x or y (ties with z go to x / y): the in-plane part comes from the
+        // column table, the second tap axis is z
+        q.mode = (R.packed >> 30) & 3;
+        q.lo = R.packed & 0x7fff;
+        q.hi = (R.packed >> 15) & 0x7fff;
+        const int n_drive = q.mode == 0 ? nx : ny;
+        q.zslope = v * R.rda;                              // dz per plane (index units)
+        q.zmid = 0.5 * (nz - 1) - R.sa_h * q.zslope;       // z at the central driving plane
+        clip_range(q.zmid, q.zslope, 0.5 * (n_drive - 1), nz, q.lo, q.hi);
+        q.weight = (float)(h * sqrt(R.dxy2 + q.zslope * q.zslope));     // h |D| / |Da|
+    } else {
+        // driven along z: the ray meets plane z_k = (k - (nz-1)/2) h at
+        // x = S_x + z_k D_x / v (S_z = 0), i.e. x(k) = S_x/h + (nx-1)/2 + (k - (nz-1)/2) D_x/v
+        q.mode = 2;
+        q.lo = 0;
+        q.hi = nz - 1;
+        q.xs = R.dx / v;
+        q.ys = R.dy / v;
+        q.xmid = R.sx_h + 0.5 * (nx - 1);
+        q.ymid = R.sy_h + 0.5 * (ny - 1);
+        clip_range(q.xmid, q.xs, 0.5 * (nz - 1), nx, q.lo, q.hi);
+        clip_range(q.ymid, q.ys, 0.5 * (nz - 1), ny, q.lo, q.hi);
+        q.weight = (float)(h * sqrt(1.0 + q.xs * q.xs + q.ys * q.ys));
+    }
+    return q;
+}
+
+__global__ void __launch_bounds__(256) joseph3d_kernel(
+    const RayXY *__restrict__ rxy, int ndu, int ndv, double pitch_v, double h,
+    const float2 *__restrict__ px, int64_t psx, int ldx, const float2 *__restrict__ py,
+    int64_t psy, int ldy, int nx, int ny, int nz, float *__restrict__ y, int64_t y_view_ld,
+    int y_ld, int y_off, const int *stop)
+{
+    if (stop && stop[0] != 0) return;
+    const int iu = blockIdx.x * blockDim.x + threadIdx.x;
+    if (iu >= ndu) return;
+    const int view = blockIdx.y, iv = blockIdx.z;
+    const RayXY R = rxy[(int64_t)view * ndu + iu];
+    const Ray3D q = setup_ray3d(R, iv, ndv, pitch_v, h, nx, ny, nz);
+    float acc = 0.f;
+    if (q.mode != 2) {
+        const bool ax = q.mode == 0;
+        const float2 *L = ax ? px : py;
+        const int64_t ps = ax ? psx : psy;
+        const int ld = ax ? ldx : ldy;
+        const int nb = ax ? ny : nx;
+        const float bhi = __int_as_float(__float_as_int((float)nb) - 1);
+        const float zhi = __int_as_float(__float_as_int((float)nz) - 1);
+        const float bmid = R.bmid, bsl = R.bslope;
+        const float zm = (float)q.zmid, zs = (float)q.zslope;
+        float tf = (float)q.lo - 0.5f * (float)((ax ? nx : ny) - 1);
+        const float2 *plane = L + (int64_t)(q.lo + 1) * ps;
+        for (int t = q.lo; t <= q.hi; ++t) {
+            const float pb = fminf(fmaxf(fmaf(bsl, tf, bmid), -1.f), bhi);
+            const float pz = fminf(fmaxf(fmaf(zs, tf, zm), -1.f), zhi);
+            const float fb = floorf(pb), fz = floorf(pz);
+            const float wb = pb - fb, wz = pz - fz;
+            const float2 *row = plane + (int64_t)((int)fz + 1) * ld + (int)fb + 1;
+            const float2 p0 = __ldg(row), p1 = __ldg(row + ld);
+            const float a0 = fmaf(wb, p0.y - p0.x, p0.x);
+            const float a1 = fmaf(wb, p1.y - p1.x, p1.x);
+            acc += fmaf(wz, a1 - a0, a0);
+            tf += 1.f;
+            plane += ps;
+        }
+    } else {
+        // taps from P_y: pairs along x, plane y + 1, row z + 1
+        const double zt = 0.5 * (nz - 1);
+        const float xhi = __int_as_float(__float_as_int((float)nx) - 1);
+        const float yhi = __int_as_float(__float_as_int((float)ny) - 1);
+        for (int t = q.lo; t <= q.hi; ++t) {
+            const double tf = t - zt;
+            const float pxf = fminf(fmaxf((float)(q.xmid + q.xs * tf), -1.f), xhi);
+            const float pyf = fminf(fmaxf((float)(q.ymid + q.ys * tf), -1.f), yhi);
+            const float fx = floorf(pxf), fy = floorf(pyf);
+            const float wx = pxf - fx, wy = pyf - fy;
+            const float2 *row = py + (int64_t)((int)fy + 1) * psy + (int64_t)(t + 1) * ldy + (int)fx + 1;
+            const float2 p0 = __ldg(row), p1 = __ldg(row + psy);
+            const float a0 = fmaf(wx, p0.y - p0.x, p0.x);
+            const float a1 = fmaf(wx, p1.y - p1.x, p1.x);
+            acc += fmaf(wy, a1 - a0, a0);
+        }
+    }
+    y[(int64_t)view * y_view_ld + (int64_t)iv * y_ld + y_off + iu] = acc * q.weight;
+}
+
+// Total number of Joseph samples of the geometry (sum of the clipped plane ranges), for the
+// projector's work count.
+__global__ void joseph3d_count_kernel(const RayXY *__restrict__ rxy, int ndu, int ndv,
+                                      int n_views, double pitch_v, double h, int nx, int ny,
+                                      int nz, unsigned long long *count)
+{
+    const int64_t total = (int64_t)n_views * ndu * ndv;
+    unsigned long long local = 0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t col = t / ndv;
+        const int iv = (int)(t - col * ndv);
+        const Ray3D q = setup_ray3d(rxy[col], iv, ndv, pitch_v, h, nx, ny, nz);
+        if (q.hi >= q.lo) local += (unsigned long long)(q.hi - q.lo + 1);
+    }
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(count, local);
+}
+
+cudaError_t count_joseph3d_samples(const ct_geom *g, int64_t *out)
+{
+    const DeviceGeom &d = g->dg;
+    unsigned long long *cnt = nullptr, h = 0;
+    cudaError_t e = cudaMalloc(&cnt, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(cnt, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) {
+        joseph3d_count_kernel<<<152 * 8, 256>>>(d.rays_xy, d.ndu, d.ndv, d.n_views,
+                                                (double)g->desc.pitch_v, g->desc.pixel, d.nx,
+                                                d.ny, d.nz, cnt);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(cnt);
+    *out = (int64_t)h;
+    return e;
+}
+
+cudaError_t launch_joseph3d(const ct_geom *g, float *y, int64_t y_view_ld, int y_ld, int y_off,
+                            const int *stop, cudaStream_t s)
+{
+    const DeviceGeom &d = g->dg;
+    dim3 block(256), grid((d.ndu + 255) / 256, d.n_views, d.ndv);
+    joseph3d_kernel<<<grid, block, 0, s>>>(d.rays_xy, d.ndu, d.ndv, (double)g->desc.pitch_v,
+                                           g->desc.pixel, g->pcol_dev, d.plane_x, d.col_pairs_ld,
+                                           g->prow_dev, d.plane_y, d.row_pairs_ld, d.nx, d.ny,
+                                           d.nz, y, y_view_ld, y_ld, y_off, stop);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------- voxel-driven B
+// One thread per (x, y) column and kZChunk consecutive z; blocks of 32 x 4 columns; all views
+// per thread (per-view cos and sin staged in shared memory).  With p the voxel centre in units
+// of h, pe = p . e_u, bb = SID/h - p . (cos, sin), rho = 1 / bb:
+//   u = SDD pe rho, v = SDD z rho, and the weight h^3 (SDD^2+u^2+v^2)^{3/2} / (L^2 pu pv SDD),
+//   L = |p - S| = h bb sqrt(1 + (pe rho)^2 + (z rho)^2), equals
+//   (SDD^2 h / (pu pv)) rho^2 sqrt(1 + (pe rho)^2 + (z rho)^2).
+constexpr int kZChunk = 8;
+
+__global__ void __launch_bounds__(128) voxbp3d_kernel(
+    const ViewBP *__restrict__ views, int n_views, const float *__restrict__ ypad,
+    int64_t view_ld, int ld, int ndu, int ndv, int nx, int ny, int nz, float sid_h, float ku,
+    float kv, float kw, float *__restrict__ x, const int *stop)
+{
+    if (stop && stop[0] != 0) return;
+    extern __shared__ float2 sv3[];
+    const int nthr = blockDim.x * blockDim.y;
+    for (int v = threadIdx.y * blockDim.x + threadIdx.x; v < n_views; v += nthr)
+        sv3[v] = make_float2(views[v].cs, views[v].sn);
+    __syncthreads();
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z0 = blockIdx.z * kZChunk;
+    if (c >= nx || r >= ny) return;
+    const float tc = (float)c - 0.5f * (float)(nx - 1);
+    const float tr = (float)r - 0.5f * (float)(ny - 1);
+    const float tz0 = (float)z0 - 0.5f * (float)(nz - 1);
+    const float gu = 0.5f * (float)(ndu - 1) + 2.f;      // +2: padded row offset
+    const float gv = 0.5f * (float)(ndv - 1) + 1.f;      // +1: zero row above row 0
+    const float uhi = (float)(ndu + 2), vhi = (float)(ndv + 1);
+    float acc[kZChunk];
+#pragma unroll
+    for (int j = 0; j < kZChunk; ++j) acc[j] = 0.f;
+    const float *vw = ypad;
+    for (int v = 0; v < n_views; ++v, vw += view_ld) {
+        const float2 V = sv3[v];
+        const float pe = fmaf(tr, V.x, -tc * V.y);
+        const float bb = fmaf(-tc, V.x, fmaf(-tr, V.y, sid_h));
+        const float rho = __fdividef(1.f, bb);
+        const float a = pe * rho;
+        float fu = fminf(fmaxf(fmaf(a, ku, gu), 0.f), uhi);
+        const float ful = floorf(fu);
+        const float wu = fu - ful;
+        const float *col = vw + (int)ful;
+        const float s2 = fmaf(a, a, 1.f);
+        const float rho2 = rho * rho;
+#pragma unroll
+        for (int j = 0; j < kZChunk; ++j) {
+            const float b = (tz0 + (float)j) * rho;
+            float fv = fminf(fmaxf(fmaf(b, kv, gv), 0.f), vhi);
+            const float fvl = floorf(fv);
+            const float wv = fv - fvl;
+            const float *p = col + (int64_t)(int)fvl * ld;
+            const float t00 = __ldg(p), t01 = __ldg(p + 1);
+            const float t10 = __ldg(p + ld), t11 = __ldg(p + ld + 1);
+            const float r0 = fmaf(wu, t01 - t00, t00);
+            const float r1 = fmaf(wu, t11 - t10, t10);
+            const float q = fmaf(b, b, s2);
+            acc[j] = fmaf(rho2 * (q * rsqrtf(q)), fmaf(wv, r1 - r0, r0), acc[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kZChunk; ++j)
+        if (z0 + j < nz) x[((int64_t)(z0 + j) * ny + r) * nx + c] = acc[j] * kw;
+}
+
+cudaError_t launch_voxbp3d(const ct_geom *g, const float *ypad, float *x, const int *stop,
+                           cudaStream_t s)
+{
+    const DeviceGeom &d = g->dg;
+    dim3 block(32, 4), grid((d.nx + 31) / 32, (d.ny + 3) / 4, (d.nz + kZChunk - 1) / kZChunk);
+    const double h = g->desc.pixel;
+    const float sid_h = (float)(g->desc.sid / h);
+    const float ku = (float)(g->desc.sdd / g->desc.pitch_u);
+    const float kv = (float)(g->desc.sdd / g->desc.pitch_v);
+    const float kw = (float)(g->desc.sdd * g->desc.sdd * h / (g->desc.pitch_u * g->desc.pitch_v));
+    voxbp3d_kernel<<<grid, block, sizeof(float2) * (size_t)d.n_views, s>>>(
+        d.views, d.n_views, ypad, d.sino_view_ld, d.sino_ld, d.ndu, d.ndv, d.nx, d.ny, d.nz,
+        sid_h, ku, kv, kw, x, stop);
+    return cudaGetLastError();
+}
+
+}  // namespace ct

@@ -170,11 +170,13 @@ def ellipse_phantom(N: int, n_ellipses: int = 10, seed: int = 0, ny: int | None 
 
 def ellipsoid_phantom(N: int, n_ellipsoids: int = 10, seed: int = 0, h: float = 1.0) -> np.ndarray:
     """FP64 (N, N, N) volume [z][y][x]: sum of ellipsoid indicators at voxel centres; centres
-    uniform in the ball of radius 0.7 N/2, semi-axes U[0.05, 0.35] N/2, Euler angles U[0, pi)."""
+    uniform in the ball of radius 0.7 N/2, semi-axes U[0.05, 0.35] N/2, Euler angles U[0, pi).
+
+    Each ellipsoid is evaluated only on the voxels of its bounding box, with the same
+    elementwise arithmetic for every voxel (the result does not depend on the box)."""
     g = _rng(seed)
     half = N * h / 2.0
     c = (np.arange(N, dtype=np.float64) - (N - 1) / 2.0) * h
-    ZZ, YY, XX = np.meshgrid(c, c, c, indexing="ij")
     vol = np.zeros((N, N, N), dtype=np.float64)
     for _ in range(n_ellipsoids):
         d = g.standard_normal(3)
@@ -189,10 +191,20 @@ def ellipsoid_phantom(N: int, n_ellipsoids: int = 10, seed: int = 0, h: float = 
         Rx = np.array([[1.0, 0, 0], [0, cb, -sb], [0, sb, cb]])
         Rz2 = np.array([[cg, -sg, 0], [sg, cg, 0], [0, 0, 1.0]])
         R = Rz1 @ Rx @ Rz2
-        P = np.stack([XX - centre[0], YY - centre[1], ZZ - centre[2]], axis=-1)
-        L = P @ R  # coordinates in the ellipsoid frame
-        q = (L[..., 0] / axes[0]) ** 2 + (L[..., 1] / axes[1]) ** 2 + (L[..., 2] / axes[2]) ** 2
-        vol[q <= 1.0] += val
+        # half-extent of the ellipsoid along each axis: |R_i| . axes (row norms of R diag(axes))
+        ext = np.sqrt(((R * axes[None, :]) ** 2).sum(axis=1)) + 2.0 * h
+        lo = np.clip(np.floor((centre - ext) / h + (N - 1) / 2.0).astype(int), 0, N)
+        hi = np.clip(np.ceil((centre + ext) / h + (N - 1) / 2.0).astype(int) + 1, 0, N)
+        if np.any(hi <= lo):
+            continue
+        X = (c[lo[0]:hi[0]] - centre[0])[None, None, :]
+        Y = (c[lo[1]:hi[1]] - centre[1])[None, :, None]
+        Z = (c[lo[2]:hi[2]] - centre[2])[:, None, None]
+        q = np.zeros((hi[2] - lo[2], hi[1] - lo[1], hi[0] - lo[0]))
+        for k in range(3):          # coordinates in the ellipsoid frame: (P R)_k / axes_k
+            Lk = X * R[0, k] + Y * R[1, k] + Z * R[2, k]
+            q += (Lk / axes[k]) ** 2
+        vol[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]][q <= 1.0] += val
     return vol
 
 
