@@ -292,8 +292,6 @@ static RayXY make_ray_xy(const ct_geom_desc *d, int view, int iu)
     return r;
 }
 
-cudaError_t count_joseph3d_samples(const ct_geom *g, int64_t *out);
-
 extern "C" {
 
 const char *ct_last_error(void) { return g_last_error.c_str(); }

@@ -119,6 +119,8 @@ cudaError_t launch_joseph3d(const ct_geom *g, float *y, int64_t y_view_ld, int y
                             const int *stop, cudaStream_t s);
 cudaError_t launch_voxbp3d(const ct_geom *g, const float *ypad, float *x, const int *stop,
                            cudaStream_t s);
+// total Joseph sample count of a cone geometry (one counting launch, synchronous)
+cudaError_t count_joseph3d_samples(const ct_geom *g, int64_t *out);
 
 // ----------------------------------------------------------------------------- Arnoldi
 struct ArnoldiScratch {
