@@ -248,13 +248,15 @@ ct_status ct_projected_solve(const double *H_dev, int ldh, int k, double beta,
  *   [0] k / max_iters; [1..32] log10(sigma_i / sigma_1) for the 32 largest sigma_i (pad -16);
  *   [33..64] |c_i| / beta for the same i (pad 0); [65] |c_{k+1}| / beta; [66] log10 sigma_1;
  *   [67] log10 beta; [68..79] 0.
- * Network: 80 -> 64 -> 64 -> 1, GELU (tanh form) after both hidden layers.  Parameters, one
- * FP32 vector of CT_MLP_NPARAMS entries in this order: W1[64][80], b1[64], W2[64][64], b2[64],
- * w3[64], b3.  bf16 != 0: weights, inputs and both hidden activations are rounded to BF16 and
- * the products accumulate in FP32 on the tensor cores (the solver's inference always works
- * this way); bf16 == 0: the same arithmetic in FP32 on the CUDA cores. */
+ * Network: the features standardised in FP32, f' = (f - mu) * isd, then 80 -> 64 -> 64 -> 1
+ * with GELU (tanh form) after both hidden layers.  Parameters, one FP32 vector of
+ * CT_MLP_NPARAMS entries in this order: W1[64][80], b1[64], W2[64][64], b2[64], w3[64], b3,
+ * mu[80], isd[80] (mu and isd are set before training and get zero gradient).  bf16 != 0:
+ * weights, standardised inputs and both hidden activations are rounded to BF16 and the
+ * products accumulate in FP32 on the tensor cores (the solver's inference always works this
+ * way); bf16 == 0: the same arithmetic in FP32 on the CUDA cores. */
 #define CT_MLP_NIN 80
-#define CT_MLP_NPARAMS 9409
+#define CT_MLP_NPARAMS 9569
 
 /* out_dev[i] = net(X_dev[i][0..79]) for i < n.  X: n x 80 floats, row-major. */
 ct_status ct_mlp_forward(const float *params_dev, const float *X_dev, int n, float *out_dev,

@@ -1,7 +1,9 @@
 """FP64 oracle of the learned lambda rule's network (not in the paper).
 
 TEST INFRASTRUCTURE ONLY.  A 3-layer perceptron, 80 (padded) inputs -> 64 -> 64 -> 1 with GELU
-(tanh form) after the two hidden layers, trained by mean-squared error and Adam.  The GPU
+(tanh form) after the two hidden layers, trained by mean-squared error and Adam.  The inputs are
+first standardised, x' = (x - mu) * isd, with mu and isd fixed before training (zero
+gradient).  The GPU
 training kernels are checked against forward(), backward() and adam_step() here on the same
 BF16-rounded weights and inputs.
 
@@ -102,11 +104,14 @@ def init_params(seed: int = 0):
         "b2": np.zeros(N_HID),
         "w3": rng.standard_normal(N_HID) * math.sqrt(1.0 / N_HID),
         "b3": np.zeros(1),
+        "mu": np.zeros(N_IN),
+        "isd": np.ones(N_IN),
     }
 
 
 def forward(p, X):
     """X: (B, 80).  Returns prediction (B,) and the cache for backward."""
+    X = (X - p["mu"]) * p["isd"]
     z1 = X @ p["W1"].T + p["b1"]
     a1 = gelu(z1)
     z2 = a1 @ p["W2"].T + p["b2"]
@@ -134,6 +139,8 @@ def backward(p, X, y):
     d_z1 = d_a1 * gelu_grad(z1)
     g["W1"] = d_z1.T @ X
     g["b1"] = d_z1.sum(0)
+    g["mu"] = np.zeros_like(p["mu"])       # the standardisation is not trained
+    g["isd"] = np.zeros_like(p["isd"])
     return g
 
 

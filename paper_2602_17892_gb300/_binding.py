@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "CT_OK", 1: "CT_EINVAL", 2: "CT_ENOMEM", 3: "CT_ECUDA", 4: "C
                 5: "CT_ETIMEOUT", 6: "CT_ENONFINITE"}
 KINDS = {"parallel2d": 0, "fanflat2d": 1, "cone3d": 2}
 RULES = {"none": 0, "fixed": 1, "gcv": 2, "dp": 3, "learned": 4}
-CT_MLP_NIN, CT_MLP_NPARAMS = 80, 9409
+CT_MLP_NIN, CT_MLP_NPARAMS = 80, 9569
 BASIS = {"f32": 0, "bf16": 1, "f16": 2}
 
 # the entry points of include/ctabba.h

@@ -48,7 +48,7 @@ __device__ void mlp_load(MlpShared<BF16> &S, const float *__restrict__ P,
     if (tid == 0) S.b3 = P[kOffB3];
     for (int i = tid; i < kRows * kIn; i += kMlpThreads) {
         const int r = i / kIn, c = i % kIn, row = row0 + r;
-        S.X[r][c] = E::from(row < n ? X[(int64_t)row * kIn + c] : 0.f);
+        S.X[r][c] = E::from(row < n ? standardise(P, X[(int64_t)row * kIn + c], c) : 0.f);
     }
     __syncthreads();
 }
@@ -209,6 +209,8 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_grad_kernel(
         for (int r = 0; r < kRows; ++r) s += E::to(S.D1[r][j]);
         G[kOffB1 + j] = s;
     }
+    // the standardisation is fixed: zero gradient (Adam then leaves it unchanged)
+    for (int j = tid; j < 2 * kIn; j += kMlpThreads) G[kOffMu + j] = 0.f;
 }
 
 // grad[i] = sum over CTAs of part[b][i] in CTA order; loss = (sum of lpart) / n

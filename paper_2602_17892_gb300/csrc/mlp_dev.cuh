@@ -2,10 +2,12 @@
 // inference: parameter layout, GELU and the 16 x 8 output tile of a matrix product.
 //
 // Network (not in the paper): 80 features -> 64 -> 64 -> 1, GELU (tanh form) after both hidden
-// layers, output log10(lambda / sigma_1).  Parameters are one FP32 vector in this order:
-// W1[64][80], b1[64], W2[64][64], b2[64], w3[64], b3.  In BF16 mode the weights, the inputs and
-// both hidden activations are rounded to BF16 before each product (biases stay FP32) and the
-// products accumulate in FP32 on the tensor cores.
+// layers, output log10(lambda / sigma_1).  The features are first standardised in FP32,
+// f' = (f - mu) * isd, with mu and isd fixed by training (not trained themselves).  Parameters
+// are one FP32 vector in this order: W1[64][80], b1[64], W2[64][64], b2[64], w3[64], b3,
+// mu[80], isd[80].  In BF16 mode the weights, the standardised inputs and both hidden
+// activations are rounded to BF16 before each product (biases stay FP32) and the products
+// accumulate in FP32 on the tensor cores.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -15,7 +17,13 @@ namespace mlp {
 constexpr int kIn = 80, kHid = 64;
 constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kHid * kIn, kOffW2 = kOffB1 + kHid,
               kOffB2 = kOffW2 + kHid * kHid, kOffW3 = kOffB2 + kHid, kOffB3 = kOffW3 + kHid,
-              kNParams = kOffB3 + 1;
+              kOffMu = kOffB3 + 1, kOffIsd = kOffMu + kIn, kNParams = kOffIsd + kIn;
+
+// standardised feature k (FP32)
+__device__ __forceinline__ float standardise(const float *__restrict__ P, float f, int k)
+{
+    return (f - P[kOffMu + k]) * P[kOffIsd + k];
+}
 
 // tanh(u) = 1 - 2 / (exp(2u) + 1): absolute error a few FP32 ulps for every u (exp(2u) = inf
 // gives 1, exp(2u) = 0 gives -1), unlike a hardware tanh approximation
@@ -101,7 +109,8 @@ __device__ __forceinline__ float infer_row_bf16(const float *__restrict__ P, con
     const __nv_bfloat16 zero = __float2bfloat16(0.f);
     for (int n0 = 0; n0 < kHid; n0 += 8) {
         float c[4] = {0.f, 0.f, 0.f, 0.f};
-        tile16x8<true>([&](int m, int k) { return m == 0 ? __float2bfloat16(f[k]) : zero; },
+        tile16x8<true>([&](int m, int k) {
+                           return m == 0 ? __float2bfloat16(standardise(P, f[k], k)) : zero; },
                        [&](int k, int n) { return __float2bfloat16(P[kOffW1 + (n0 + n) * kIn + k]); },
                        kIn, c);
         if (g == 0) {

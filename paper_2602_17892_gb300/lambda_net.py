@@ -14,9 +14,8 @@ Training problems: 256 x 256 parallel-beam scans with the angular sampling of th
 ellipse workload (90 views over [0, pi), ceil(sqrt(2) N) + 4 bins), random 10-ellipse phantoms
 (seed = problem index), Gaussian noise of level eta ~ U[0.5 %, 5 %], K = 30 steps, GCV.
 
-Inputs are standardised for training (mean and spread of each feature over the training set);
-the affine map is folded into the first layer before the parameters are saved, so the saved
-network reads the raw features the solver computes.
+The network standardises its inputs in FP32 with the mean and spread of each feature over the
+training set (stored with the parameters), so that BF16 rounding acts on O(1) values.
 
 ``python -m paper_2602_17892_gb300.lambda_net --solves 20000`` generates the data, trains, and
 writes ``data/lambda_net_parallel256.npz`` next to this file.
@@ -117,39 +116,31 @@ def generate(seeds, geom=None, K: int = K_TRAIN, workers: int = 8, log=None):
     return feats, labels, mask
 
 
-def init_params(seed: int = 0) -> np.ndarray:
-    """He-normal weights, zero biases, in the library's parameter order."""
+def init_params(seed: int = 0, mu=None, sd=None) -> np.ndarray:
+    """He-normal weights, zero biases, and the input standardisation (mu, 1 / sd; identity by
+    default), in the library's parameter order."""
     g = np.random.Generator(np.random.PCG64(seed))
     W1 = g.standard_normal((N_HID, CT_MLP_NIN)) * math.sqrt(2.0 / CT_MLP_NIN)
     W2 = g.standard_normal((N_HID, N_HID)) * math.sqrt(2.0 / N_HID)
     w3 = g.standard_normal(N_HID) * math.sqrt(1.0 / N_HID)
-    p = np.concatenate([W1.ravel(), np.zeros(N_HID), W2.ravel(), np.zeros(N_HID), w3, [0.0]])
+    mu = np.zeros(CT_MLP_NIN) if mu is None else np.asarray(mu, np.float64)
+    isd = np.ones(CT_MLP_NIN) if sd is None else 1.0 / np.asarray(sd, np.float64)
+    p = np.concatenate([W1.ravel(), np.zeros(N_HID), W2.ravel(), np.zeros(N_HID), w3, [0.0],
+                        mu, isd])
     assert p.size == CT_MLP_NPARAMS
-    return p.astype(np.float32)
-
-
-def fold_standardisation(params: np.ndarray, mu: np.ndarray, sd: np.ndarray) -> np.ndarray:
-    """Parameters for raw inputs x from those trained on (x - mu) / sd."""
-    p = params.astype(np.float64).copy()
-    W1 = p[: N_HID * CT_MLP_NIN].reshape(N_HID, CT_MLP_NIN)
-    b1 = p[N_HID * CT_MLP_NIN: N_HID * CT_MLP_NIN + N_HID]
-    W1n = W1 / sd[None, :]
-    b1n = b1 - W1n @ mu
-    p[: N_HID * CT_MLP_NIN] = W1n.ravel()
-    p[N_HID * CT_MLP_NIN: N_HID * CT_MLP_NIN + N_HID] = b1n
     return p.astype(np.float32)
 
 
 def train(X, Y, Xv=None, Yv=None, epochs: int = 40, batch: int = 4096, lr: float = 1e-3,
           seed: int = 0, log=None):
-    """Adam on standardised inputs with the library's training kernels; returns the folded
-    FP32 parameters (numpy) and a history of (epoch, train loss, validation loss)."""
+    """Adam with the library's training kernels; the standardisation (mean and spread of each
+    feature over X) is part of the parameters.  Returns the FP32 parameters (numpy) and a
+    history of (epoch, train loss, validation loss)."""
     import torch
-    mu = X.mean(0)
-    sd = X.std(0)
+    mu = X.double().mean(0)
+    sd = X.double().std(0)
     sd = torch.where(sd > 1e-6, sd, torch.ones_like(sd))
-    Xs = ((X - mu) / sd).contiguous()
-    P = torch.from_numpy(init_params(seed)).cuda()
+    P = torch.from_numpy(init_params(seed, mu.cpu().numpy(), sd.cpu().numpy())).cuda()
     m = torch.zeros_like(P)
     v = torch.zeros_like(P)
     gen = torch.Generator(device="cuda")
@@ -160,20 +151,15 @@ def train(X, Y, Xv=None, Yv=None, epochs: int = 40, batch: int = 4096, lr: float
     for ep in range(epochs):
         step_lr = lr * (0.1 ** (ep / max(1, epochs - 1)))       # decays to lr / 10
         perm = torch.randperm(X.shape[0], device="cuda", generator=gen)
-        Xp, Yp = Xs[perm].contiguous(), Y[perm].contiguous()
+        Xp, Yp = X[perm].contiguous(), Y[perm].contiguous()
         lh = torch.empty(nb, dtype=torch.float32, device="cuda")
         t = ct_mlp_train(P, m, v, Xp, Yp, batch, 1, step_lr, t=t, loss_hist=lh)
         tr = float(lh.mean())
-        va = float("nan")
-        if Xv is not None:
-            va = mse(fold_standardisation(P.cpu().numpy(), mu.cpu().numpy().astype(np.float64),
-                                          sd.cpu().numpy().astype(np.float64)), Xv, Yv)
+        va = mse(P.cpu().numpy(), Xv, Yv) if Xv is not None else float("nan")
         hist.append((ep, tr, va))
         if log:
             log(f"  epoch {ep:3d}  lr {step_lr:.2e}  train {tr:.4f}  val {va:.4f}")
-    folded = fold_standardisation(P.cpu().numpy(), mu.cpu().numpy().astype(np.float64),
-                                  sd.cpu().numpy().astype(np.float64))
-    return folded, hist
+    return P.cpu().numpy(), hist
 
 
 def mse(params: np.ndarray, X, Y) -> float:

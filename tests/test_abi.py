@@ -90,4 +90,4 @@ def test_learned_lambda_entry_points_reject_bad_arguments(lib):
     st = lib.ab_gmres_hybrid(ctypes.c_void_p(1), ctypes.c_void_p(16), None, ctypes.c_void_p(16),
                              ctypes.byref(o), None, None)
     assert st == Bn.CT_EINVAL and b"lambda_net_dev" in lib.ct_last_error()
-    assert Bn.CT_MLP_NPARAMS == 64 * 80 + 64 + 64 * 64 + 64 + 64 + 1
+    assert Bn.CT_MLP_NPARAMS == 64 * 80 + 64 + 64 * 64 + 64 + 64 + 1 + 2 * 80

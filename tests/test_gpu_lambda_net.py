@@ -19,19 +19,23 @@ from tests._common import gpu_geom, problem, rel, to_dev
 
 pytestmark = pytest.mark.gpu
 
-NP = 9409
+NP = 9569
+B3 = 9408                   # offset of b3 in the parameter vector
+
+
+KEYS = (("W1", (64, 80)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)), ("w3", (64,)),
+        ("b3", (1,)), ("mu", (80,)), ("isd", (80,)))
 
 
 def _flat(p):
-    return np.concatenate([p["W1"].ravel(), p["b1"], p["W2"].ravel(), p["b2"], p["w3"], p["b3"]])
+    return np.concatenate([p[k].ravel() for k, _ in KEYS])
 
 
 def _unflat(v):
     v = np.asarray(v, np.float64)
     o = 0
     out = {}
-    for key, shape in (("W1", (64, 80)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)),
-                       ("w3", (64,)), ("b3", (1,))):
+    for key, shape in KEYS:
         size = int(np.prod(shape))
         out[key] = v[o:o + size].reshape(shape)
         o += size
@@ -40,19 +44,27 @@ def _unflat(v):
 
 
 def _params(seed, bias_scale=0.1):
+    """Oracle-initialised weights, random biases and a non-trivial input standardisation."""
     p = OM.init_params(seed)
     rng = np.random.Generator(np.random.PCG64(seed + 100))
     for key in ("b1", "b2", "b3"):
         p[key] = bias_scale * rng.standard_normal(p[key].shape)
+    p["mu"] = 0.3 * rng.standard_normal(80)
+    p["isd"] = 0.5 + rng.random(80)
     v = np.asarray(_flat(p), np.float32)
     return v, _unflat(v.astype(np.float64))
 
 
-def _bf16_params(p):
+def _bf16_case(p, X):
+    """The BF16 network as the oracle sees it: weights rounded to BF16, biases FP32, and the
+    input standardised in FP32 (as the kernel does) then rounded to BF16."""
     q = {k: OM.bf16_round(v) for k, v in p.items()}
-    for key in ("b1", "b2", "b3"):        # biases stay FP32
+    for key in ("b1", "b2", "b3"):
         q[key] = p[key]
-    return q
+    q["mu"] = np.zeros(80)
+    q["isd"] = np.ones(80)
+    Xs = (X.astype(np.float32) - p["mu"].astype(np.float32)) * p["isd"].astype(np.float32)
+    return q, OM.bf16_round(Xs.astype(np.float64))
 
 
 def _data(n, seed):
@@ -74,7 +86,7 @@ def test_forward_matches_oracle(bf16, n):
     torch.cuda.synchronize()
     Xo = X.astype(np.float64)
     if bf16:
-        ref, _ = OM.forward(_bf16_params(p), OM.bf16_round(Xo))
+        ref, _ = OM.forward(*_bf16_case(p, X))
         assert rel(out.cpu().numpy(), ref) <= 1e-2
     else:
         ref, _ = OM.forward(p, Xo)
@@ -95,12 +107,13 @@ def test_gradient_matches_oracle(bf16):
     ct_mlp_grad(to_dev(v), to_dev(X).reshape(n, 80), to_dev(Y), grad, loss, bf16=bf16)
     torch.cuda.synchronize()
     Xo, Yo = X.astype(np.float64), Y.astype(np.float64)
-    pp, Xr = (_bf16_params(p), OM.bf16_round(Xo)) if bf16 else (p, Xo)
+    pp, Xr = _bf16_case(p, X) if bf16 else (p, Xo)
     ref = OM.backward(pp, Xr, Yo)
     got = _unflat(grad.cpu().numpy())
     tol = 1e-2 if bf16 else 1e-5
-    for key in ref:
+    for key in ("W1", "b1", "W2", "b2", "w3", "b3"):
         assert rel(got[key], ref[key]) <= tol, (key, rel(got[key], ref[key]))
+    assert not got["mu"].any() and not got["isd"].any()
     assert abs(float(loss.cpu()[0]) - OM.loss(pp, Xr, Yo)) <= tol * OM.loss(pp, Xr, Yo)
 
 
@@ -230,7 +243,7 @@ def test_learned_rule_evaluates_the_network_and_falls_back_to_gcv():
     G = gpu_geom(geom)
     rng = np.random.Generator(np.random.PCG64(43))
     v = (0.05 * rng.standard_normal(NP)).astype(np.float32)
-    v[-1] = -2.0                                   # b3: outputs near log10(lambda/sigma_1) = -2
+    v[B3] = -2.0                                   # b3: outputs near log10(lambda/sigma_1) = -2
     P = to_dev(v)
     feats = torch.zeros((K, 80), dtype=torch.float32, device="cuda")
     x = torch.empty(G.n, dtype=torch.float32, device="cuda")
@@ -246,7 +259,7 @@ def test_learned_rule_evaluates_the_network_and_falls_back_to_gcv():
     assert np.all(np.abs(got - pred) < 1e-5), (got, pred)
     # NaN network -> GCV at every step
     Pn = P.clone()
-    Pn[-1] = float("nan")
+    Pn[B3] = float("nan")
     outn = ab_gmres_hybrid(G, to_dev(b), x, max_iters=K, rule="learned", lambda_net=Pn)
     xg = torch.empty_like(x)
     outg = ab_gmres_hybrid(G, to_dev(b), xg, max_iters=K, rule="gcv")

@@ -24,9 +24,12 @@ def test_backward_matches_central_differences():
     p = M.init_params(1)
     X = rng.standard_normal((7, M.N_IN))
     y = rng.standard_normal(7)
+    p["mu"] = rng.standard_normal(M.N_IN) * 0.3          # a non-trivial standardisation
+    p["isd"] = 0.5 + rng.random(M.N_IN)
     g = M.backward(p, X, y)
+    assert not g["mu"].any() and not g["isd"].any()      # fixed, not trained
     h = 1e-6
-    for key in p:
+    for key in ("W1", "b1", "W2", "b2", "w3", "b3"):
         flat = p[key].reshape(-1)
         for idx in rng.choice(flat.size, size=min(6, flat.size), replace=False):
             old = flat[idx]
