@@ -9,8 +9,10 @@ the timed region starts; L2 is flushed (256 MiB write) between timed steps.
 
 Reported beside the metric: per-phase device time (CUDA events on the launching stream),
 projector GUPS, the roofline of the dominant kernel, an end-to-end number through the C ABI
-with host buffers, the GPU clocks seen during the timed region, and the FP64 CPU oracle timed
-on a bounded sample of the same workload (with the GPU's error against it).
+with host buffers, the GPU clocks seen during the timed region, the FP64 CPU oracle timed
+on a bounded sample of the same workload (with the GPU's error against it), and "variants":
+the 16-bit Krylov bases, the learned lambda rule, a sample of the uneven batched-slice
+workload under one CUDA graph, and the 512^3 cone workload (FP32 and BF16 basis).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -291,6 +293,10 @@ def bench_ours(args, rank, world, local_rank):
                 "peak_source": f"{per_clk:g} updates/clk/SM x {SM_COUNT} SMs x "
                                f"{peaks['sm_max_mhz']:.0f} MHz"}
 
+    variants = None
+    if world == 1 and args.variants != "none":
+        variants = run_variants(P, torch, G, b_dev, x_true, noise_ab, args.variants)
+
     cpu = None
     err = None
     if world == 1 and not args.no_cpu_baseline:
@@ -317,11 +323,211 @@ def bench_ours(args, rank, world, local_rank):
         "err_vs_fp64": err,
         "clocks": clk_sum,
         "cpu_baseline": cpu,
+        "variants": variants,
         "wall_s_timed": wall,
     }
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- variants
+# The forms the scope adds beside the plain FP32 method, each at its own workload, reported
+# beside the main metric (rank 0, one GPU, after the timed region; not part of `value`).
+
+def _timed(torch, fn, reps=1):
+    """Device time (ms) of fn() on the current stream, CUDA events, after one warm-up call."""
+    fn()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(reps):
+        out = fn()
+    b.record(st)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps, out
+
+
+def variant_basis_precision(P, torch, G, b_dev, x_true, noise_ab):
+    """Hybrid AB-GMRES on the 512^2 fan workload (100 its, DP) with the Krylov basis stored
+    in FP32, FP16 and BF16: iterations/s, relative error to the phantom and to the FP32-basis
+    iterate, basis bytes."""
+    xt = torch.from_numpy(x_true.astype(np.float32).reshape(-1)).cuda()
+    out, ref = {}, None
+    for basis in ("f32", "f16", "bf16"):
+        x = torch.zeros(G.n, device="cuda")
+        ms, _ = _timed(torch, lambda: P.ab_gmres_hybrid(G, b_dev, x, max_iters=ITERS, rule="dp",
+                                                        noise_norm=noise_ab, tau=TAU,
+                                                        basis=basis, history=False), reps=2)
+        if ref is None:
+            ref = x.clone()
+        L = G.m + (-G.m) % 4
+        out[basis] = {"iters_s": ITERS / (ms * 1e-3), "ms_per_solve": ms,
+                      "rre": float(torch.linalg.vector_norm(x - xt) / torch.linalg.vector_norm(xt)),
+                      "rel_to_f32_basis": float(torch.linalg.vector_norm(x - ref) /
+                                                torch.linalg.vector_norm(ref)),
+                      "basis_gb": (ITERS + 1) * L * (4 if basis == "f32" else 2) / 1e9}
+    return out
+
+
+def variant_batched(P, torch, n_slices=32, iters=60):
+    """A sample of the uneven batch (first `n_slices` of the 256-slice recipe: N in
+    {256..1024}, parallel/fan, 180-1440 views, 1 % noise, AB/BA by shape, 60 its, GCV): one
+    graph replay of the whole batch vs the same solves issued one after another, with
+    autotuned and with default launch shapes."""
+    import synth
+    cases = synth.batched_slices(256, seed=7)[:n_slices]
+    geoms, bs, xs, work = [], [], [], 0
+    for c in cases:
+        g = c["geom"]
+        G = P.Geom.from_geometry(g)
+        x_true = synth.ellipse_phantom(g.nx, seed=c["phantom_seed"], ny=g.ny, h=g.h)
+        xt = torch.from_numpy(x_true.astype(np.float32).reshape(-1)).cuda()
+        bt = torch.empty(G.m, device="cuda")
+        P.ct_forward_A(G, xt, bt)
+        b, _ = synth.add_noise(bt.cpu().numpy().astype(np.float64), c["eta"], c["noise_seed"])
+        geoms.append(G)
+        bs.append(torch.from_numpy(b.astype(np.float32)).cuda())
+        xs.append(torch.zeros(G.n, device="cuda"))
+        work += (G.a_samples + G.b_samples) * iters
+    total_iters = iters * len(cases)
+    res = {"slices": len(cases), "iters_per_slice": iters,
+           "pixels": int(sum(G.n for G in geoms)), "views": [int(c["geom"].n_views) for c in cases]}
+    for tuned in (True, False):
+        bt = P.Batch(geoms, ["auto"] * len(geoms), max_iters=iters, rule="gcv", autotune=tuned)
+        t0 = time.perf_counter()
+        bt.solve(bs, xs)                          # first call captures the graph
+        torch.cuda.synchronize()
+        capture_s = time.perf_counter() - t0
+        ms, _ = _timed(torch, lambda: bt.solve(bs, xs))
+        key = "graph_tuned" if tuned else "graph_default_shapes"
+        res[key] = {"iters_s": total_iters / (ms * 1e-3), "ms": ms,
+                    "gups": work / (ms * 1e-3) / 1e9, "first_call_s": capture_s,
+                    "launches_per_replay": bt.launches()}
+        bt.close()
+    methods = ["ab" if G.m < G.n else "ba" for G in geoms]
+
+    def sequential():
+        for G, m, b, x in zip(geoms, methods, bs, xs):
+            fn = P.ab_gmres_hybrid if m == "ab" else P.ba_gmres_hybrid
+            fn(G, b, x, max_iters=iters, rule="gcv", history=False)
+    ms, _ = _timed(torch, sequential)
+    res["sequential_solves"] = {"iters_s": total_iters / (ms * 1e-3), "ms": ms,
+                                "gups": work / (ms * 1e-3) / 1e9}
+    res["graph_speedup_vs_sequential"] = res["sequential_solves"]["ms"] / res["graph_tuned"]["ms"]
+    for G in geoms:
+        G.close()
+    return res
+
+
+def variant_cone(P, torch, iters=ITERS):
+    """The 512^3 cone workload (400 views, 768 x 768 detector, 1 % noise), hybrid AB-GMRES,
+    GCV, with the Krylov basis in FP32 and in BF16: iterations/s, projector GUPS, basis bytes,
+    relative error to the phantom and between the two."""
+    import synth
+    from paper_2602_17892_gb300 import _binding as Bn
+    case = synth.cone512_case()
+    g = case["geom"]
+    x_true = synth.ellipsoid_phantom(g.nx, seed=case["phantom_seed"], h=g.h)
+    G = P.Geom.from_geometry(g)
+    xt = torch.from_numpy(x_true.astype(np.float32).reshape(-1)).cuda()
+    del x_true
+    bt = torch.empty(G.m, device="cuda")
+    P.ct_forward_A(G, xt, bt)
+    b, _ = synth.add_noise(bt.cpu().numpy().astype(np.float64), case["eta"], case["noise_seed"])
+    b_dev = torch.from_numpy(b.astype(np.float32)).cuda()
+    del b, bt
+    out = {"image": [g.nx, g.ny, g.nz], "views": g.n_views, "detector": [g.n_det_v, g.n_det_u],
+           "iters": iters, "rule": "gcv"}
+    ref = None
+    for basis in ("bf16", "f32"):
+        x = torch.zeros(G.n, device="cuda")
+        P.ab_gmres_hybrid(G, b_dev, x, max_iters=2, rule="gcv", basis=basis, history=False)
+        torch.cuda.synchronize()
+        Bn.ct_profile_enable(True)
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        P.ab_gmres_hybrid(G, b_dev, x, max_iters=iters, rule="gcv", basis=basis, history=False)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ph = Bn.ct_profile_collect()
+        Bn.ct_profile_enable(False)
+        ms = e0.elapsed_time(e1)
+        L = G.m  # padded sinogram entries are reported by the library's own basis size below
+        out[basis] = {"iters_s": iters / (ms * 1e-3), "s_per_solve": ms / 1e3,
+                      "rre": float(torch.linalg.vector_norm(x - xt) / torch.linalg.vector_norm(xt)),
+                      "phase_ms": {k: v[0] for k, v in ph.items()},
+                      "gups_A": G.a_samples * ph["forward_A"][1] / (ph["forward_A"][0] * 1e-3) / 1e9,
+                      "gups_B": G.b_samples * ph["back_B"][1] / (ph["back_B"][0] * 1e-3) / 1e9,
+                      "basis_gb_approx": (iters + 1) * L * (2 if basis == "bf16" else 4) / 1e9,
+                      "max_mem_gb": torch.cuda.max_memory_allocated() / 1e9}
+        if ref is None:
+            ref = x.clone()
+        else:
+            out["rel_bf16_vs_f32"] = float(torch.linalg.vector_norm(ref - x) /
+                                           torch.linalg.vector_norm(x))
+        del x
+    G.close()
+    return out
+
+
+def variant_learned(P, torch, n_test=16, K=30):
+    """The learned lambda rule (network trained by the library on 20 000 solves of the
+    256^2 parallel recipe) against GCV and DP on held-out problems: mean relative error,
+    device time per solve, and the iteration count at which the learned rule first matches
+    GCV's error at K."""
+    from paper_2602_17892_gb300 import lambda_net as LN
+    net, meta = LN.load_params()
+    geom = LN.training_geometry()
+    G = P.Geom.from_geometry(geom)
+    res = {"rre": {"learned": [], "gcv": [], "dp": []}, "ms_per_solve": {}, "iters_to_gcv_error": []}
+    times = {"learned": 0.0, "gcv": 0.0, "dp": 0.0}
+    x = torch.zeros(G.n, device="cuda")
+    for sd in range(30_000_000, 30_000_000 + n_test):
+        xt, b, nn = LN.make_problem(geom, G, sd)
+        nx = float(torch.linalg.vector_norm(xt))
+        for rule in ("learned", "gcv", "dp"):
+            ms, _ = _timed(torch, lambda: P.ab_gmres_hybrid(
+                G, b, x, max_iters=K, rule=rule, noise_norm=nn, tau=TAU, history=False,
+                lambda_net=net if rule == "learned" else None))
+            times[rule] += ms
+            res["rre"][rule].append(float(torch.linalg.vector_norm(x - xt)) / nx)
+        target = res["rre"]["gcv"][-1]
+        k_hit = None
+        for k in range(5, K + 1, 5):
+            P.ab_gmres_hybrid(G, b, x, max_iters=k, rule="learned", history=False, lambda_net=net)
+            if float(torch.linalg.vector_norm(x - xt)) / nx <= target:
+                k_hit = k
+                break
+        res["iters_to_gcv_error"].append(k_hit)
+    G.close()
+    res["mean_rre"] = {k: float(np.mean(v)) for k, v in res["rre"].items()}
+    res["ms_per_solve"] = {k: v / n_test for k, v in times.items()}
+    res["K"] = K
+    res["train_solves"] = meta.get("train_solves")
+    del res["rre"]
+    return res
+
+
+def run_variants(P, torch, G, b_dev, x_true, noise_ab, which):
+    out = {}
+    jobs = {"basis_precision_fan512_ab": lambda: variant_basis_precision(P, torch, G, b_dev, x_true, noise_ab),
+            "learned_lambda_parallel256": lambda: variant_learned(P, torch),
+            "batched_slices_sample": lambda: variant_batched(P, torch),
+            "cone512": lambda: variant_cone(P, torch)}
+    for name, fn in jobs.items():
+        if which != "all" and name not in which.split(","):
+            continue
+        try:
+            t0 = time.perf_counter()
+            out[name] = fn()
+            out[name]["wall_s"] = time.perf_counter() - t0
+        except Exception as exc:                 # reported, never hides the main metric
+            out[name] = {"error": f"{type(exc).__name__}: {exc}"}
+        torch.cuda.empty_cache()
+    return out
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -373,6 +579,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variants", default="all",
+                    help="'all', 'none' or a comma list of: basis_precision_fan512_ab, "
+                         "learned_lambda_parallel256, batched_slices_sample, cone512")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
