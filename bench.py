@@ -178,6 +178,7 @@ def bench_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     geom, x_true, case = workload(rank)
     G = P.Geom.from_geometry(geom)
+    shapes = P.ct_geom_autotune(G)              # setup: projector launch shapes for this geometry
     b, b_dev, noise_ab, noise_ba = make_data_gpu(P, torch, G, geom, x_true, case, rank)
     x_ab = torch.zeros(G.n, device="cuda")
     x_ba = torch.zeros(G.n, device="cuda")
@@ -254,8 +255,8 @@ def bench_ours(args, rank, world, local_rank):
     peaks = _peaks()
     steps = args.steps
     solves_per_step = 2
-    f_ms, f_n, _ = phases["forward_A"]
-    b_ms, b_n, _ = phases["back_B"]
+    f_ms, _, f_n = phases["forward_A"]          # groups = projector applications
+    b_ms, _, b_n = phases["back_B"]
     a_ms, a_n, a_groups = phases["arnoldi"]
     kernels = {}
     if f_n:
@@ -312,6 +313,7 @@ def bench_ours(args, rank, world, local_rank):
                                "SID 1000, SDD 1500, 2 % noise; hybrid AB + BA, 100 its each, DP",
                    "image": [512, 512], "views": 720, "bins": 768, "iters_per_solve": ITERS,
                    "rule": "dp", "tau": TAU, "l2": "flushed between steps (256 MiB write)",
+                   "launch_shapes": shapes,
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": "iters/s",
                 "h2d_bytes_per_step": int(G.m * 4), "d2h_bytes_per_step": int(2 * G.n * 4)},
@@ -431,6 +433,7 @@ def variant_cone(P, torch, iters=ITERS):
     g = case["geom"]
     x_true = synth.ellipsoid_phantom(g.nx, seed=case["phantom_seed"], h=g.h)
     G = P.Geom.from_geometry(g)
+    shapes = P.ct_geom_autotune(G)
     xt = torch.from_numpy(x_true.astype(np.float32).reshape(-1)).cuda()
     del x_true
     bt = torch.empty(G.m, device="cuda")
@@ -439,7 +442,7 @@ def variant_cone(P, torch, iters=ITERS):
     b_dev = torch.from_numpy(b.astype(np.float32)).cuda()
     del b, bt
     out = {"image": [g.nx, g.ny, g.nz], "views": g.n_views, "detector": [g.n_det_v, g.n_det_u],
-           "iters": iters, "rule": "gcv"}
+           "iters": iters, "rule": "gcv", "launch_shapes": shapes}
     ref = None
     for basis in ("bf16", "f32"):
         x = torch.zeros(G.n, device="cuda")
@@ -459,8 +462,8 @@ def variant_cone(P, torch, iters=ITERS):
         out[basis] = {"iters_s": iters / (ms * 1e-3), "s_per_solve": ms / 1e3,
                       "rre": float(torch.linalg.vector_norm(x - xt) / torch.linalg.vector_norm(xt)),
                       "phase_ms": {k: v[0] for k, v in ph.items()},
-                      "gups_A": G.a_samples * ph["forward_A"][1] / (ph["forward_A"][0] * 1e-3) / 1e9,
-                      "gups_B": G.b_samples * ph["back_B"][1] / (ph["back_B"][0] * 1e-3) / 1e9,
+                      "gups_A": G.a_samples * ph["forward_A"][2] / (ph["forward_A"][0] * 1e-3) / 1e9,
+                      "gups_B": G.b_samples * ph["back_B"][2] / (ph["back_B"][0] * 1e-3) / 1e9,
                       "basis_gb_approx": (iters + 1) * L * (2 if basis == "bf16" else 4) / 1e9,
                       "max_mem_gb": torch.cuda.max_memory_allocated() / 1e9}
         if ref is None:

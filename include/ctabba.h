@@ -159,13 +159,24 @@ ct_status ba_gmres_hybrid(ct_geom *g, const float *b_dev, const float *x0_dev, f
 
 /* ------------------------------------------------------------------ tile autotuning */
 
-/* Time the candidate launch shapes of the projectors on this geometry (Joseph A: 128, 256 or
- * 512 rays per block; pixel-driven B: blocks of 32 x 4, 32 x 8 or 32 x 16 pixels) and keep the
- * fastest for later calls on `g`.  Geometries of the same kind and sizes reuse an earlier
- * result.  Runs a few dozen projector launches on `stream`, synchronises it, and allocates two
- * temporary device buffers.  The chosen shapes are returned in *a_threads and *b_rows (either
- * may be NULL). */
-ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, int *a_threads, int *b_rows);
+/* Launch shapes of the projector kernels of a geometry. */
+typedef struct {
+    int a_threads;   /* 2D Joseph A: rays (threads) per block                             */
+    int a_views;     /* 2D Joseph A: consecutive views per block (each warp one view)     */
+    int a_slab;      /* 3D Joseph A: z-slab thickness (tap rows) of one pass; each pass
+                        reads one slab of the volume's pair layouts, so it stays in L2    */
+    int b_rows;      /* 2D pixel-driven B: pixel rows per 32-pixel-wide block             */
+} ct_launch_shapes;
+
+/* Time the candidate launch shapes of the projectors on this geometry and keep the fastest for
+ * later calls on `g`.  2D: Joseph A with (rays, views) per block in (128, 1), (256, 1),
+ * (512, 1), (128, 2), (256, 2), (256, 4), (512, 4), (512, 8); pixel-driven B with blocks of
+ * 32 x 4, 32 x 8 or 32 x 16 pixels.  3D: Joseph slab thickness 8, 16, 32 or 64 (the voxel-driven
+ * B has one shape, 32 x 4 columns of 8 voxels).  The shapes change only the order of work, not
+ * the arithmetic of a sample.  Geometries of the same kind and sizes reuse an earlier result.
+ * Runs a few dozen projector launches on `stream`, synchronises it, and allocates two temporary
+ * device buffers.  The chosen shapes are written to *out (may be NULL). */
+ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_shapes *out);
 
 /* ------------------------------------------------------------------ batched solves */
 

@@ -60,6 +60,11 @@ class PhaseTime(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double), ("launches", ctypes.c_int64), ("groups", ctypes.c_int64)]
 
 
+class LaunchShapes(ctypes.Structure):
+    _fields_ = [("a_threads", ctypes.c_int), ("a_views", ctypes.c_int), ("a_slab", ctypes.c_int),
+                ("b_rows", ctypes.c_int)]
+
+
 class HybridInfo(ctypes.Structure):
     _fields_ = [("iters_done", ctypes.c_int), ("beta", ctypes.c_double),
                 ("final_lambda", ctypes.c_double), ("final_resid", ctypes.c_double),
@@ -101,7 +106,7 @@ def load(path: str = LIB_PATH):
     lib.ct_profile_collect.argtypes = [ctypes.POINTER(PhaseTime)]
     lib.ct_launch_count.restype = ctypes.c_int64
     lib.ct_launch_count.argtypes = []
-    lib.ct_geom_autotune.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.ct_geom_autotune.argtypes = [vp, vp, ctypes.POINTER(LaunchShapes)]
     lib.ct_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(HybridOpts), ctypes.c_int, ctypes.POINTER(vp)]
     lib.ct_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
@@ -286,11 +291,12 @@ def ct_launch_count() -> int:
     return int(load().ct_launch_count())
 
 
-def ct_geom_autotune(g: Geom, stream=None):
-    """Time the projector launch shapes on this geometry; returns (a_threads, b_rows)."""
-    a, b = ctypes.c_int(), ctypes.c_int()
-    _check(load().ct_geom_autotune(g.handle, _stream(stream), ctypes.byref(a), ctypes.byref(b)))
-    return a.value, b.value
+def ct_geom_autotune(g: Geom, stream=None) -> dict:
+    """Time the projector launch shapes on this geometry; returns the chosen shapes."""
+    sh = LaunchShapes()
+    _check(load().ct_geom_autotune(g.handle, _stream(stream), ctypes.byref(sh)))
+    return {"a_threads": sh.a_threads, "a_views": sh.a_views, "a_slab": sh.a_slab,
+            "b_rows": sh.b_rows}
 
 
 def _info_dict(inf):

@@ -151,6 +151,12 @@ static cudaError_t dalloc(T **p, size_t count)
     return e;
 }
 
+// kernel launches of one forward projection (3D: one per z slab)
+static int fwd_launches(const ct_geom *g)
+{
+    return g->dg.kind == CT_CONE3D ? joseph3d_launches(g) : 1;
+}
+
 static ct_status ws_get(ct_geom *g, int method, int K, int basis, Workspace **out)
 {
     GeomExtra *ex = reinterpret_cast<GeomExtra *>(g->ws);
@@ -319,8 +325,8 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     const bool cone = d->kind == CT_CONE3D;
     if (d->nx < 1 || d->ny < 1 || d->nx > 16384 || d->ny > 16384)
         return einval("ct_geom_create: image size out of range [1, 16384]");
-    if (d->n_views < 1 || d->n_det_u < 1 || d->n_det_u > (1 << 20))
-        return einval("ct_geom_create: n_views and n_det_u must be >= 1");
+    if (d->n_views < 1 || d->n_views > 65535 || d->n_det_u < 1 || d->n_det_u > (1 << 20))
+        return einval("ct_geom_create: need 1 <= n_views <= 65535 and 1 <= n_det_u <= 2^20");
     if (!d->angles) return einval("ct_geom_create: angles is NULL");
     if (!(d->pixel > 0) || !(d->pitch_u > 0)) return einval("ct_geom_create: pixel and pitch must be > 0");
     for (int v = 0; v < d->n_views; ++v)
@@ -332,8 +338,8 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     }
     if (cone) {
         if (d->nz < 1 || d->nz > 16384) return einval("ct_geom_create: nz out of range [1, 16384]");
-        if (d->n_det_v < 1 || d->n_det_v > 65535 || d->n_views > 65535)
-            return einval("ct_geom_create: cone needs 1 <= n_det_v, n_views <= 65535");
+        if (d->n_det_v < 1 || d->n_det_v > 65535)
+            return einval("ct_geom_create: cone needs 1 <= n_det_v <= 65535");
         if (!(d->pitch_v > 0)) return einval("ct_geom_create: pitch_v must be > 0");
     }
     ct_geom *g = new ct_geom();
@@ -363,7 +369,9 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     dg.plane_x = cone ? (int64_t)(nz + 2) * dg.col_pairs_ld : 0;
     dg.plane_y = cone ? (int64_t)(nz + 2) * dg.row_pairs_ld : 0;
     dg.tune_a_threads = 256;
+    dg.tune_a_views = 1;
     dg.tune_b_rows = cone ? 4 : 8;
+    dg.tune_a_slab = 16;
 
     std::vector<Ray2D> rays;
     std::vector<RayXY> rays_xy;
@@ -469,7 +477,7 @@ ct_status ct_forward_A(ct_geom *g, const float *x_dev, float *y_dev, ct_stream_t
         CT_PHASE(CT_PH_LAYOUT, 1, s);
         CT_CUDA(launch_image_pairs(g, x_dev, nullptr, s));
     }
-    CT_PHASE(CT_PH_FORWARD, 1, s);
+    CT_PHASE(CT_PH_FORWARD, fwd_launches(g), s);
     CT_CUDA(launch_forward_proj(g, y_dev, false, nullptr, s));
     return CT_OK;
 }
@@ -628,7 +636,7 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
             CT_CUDA(launch_image_pairs(g, w->img, w->stop, s));
         }
         {
-            CT_PHASE(CT_PH_FORWARD, 1, s);
+            CT_PHASE(CT_PH_FORWARD, fwd_launches(g), s);
             CT_CUDA(launch_forward_proj(g, w->q, true, w->stop, s));   //          A (B w_k)
         }
         {
@@ -706,7 +714,7 @@ static ct_status enqueue_ba(ct_geom *g, const float *b_dev, const float *x0_dev,
             CT_CUDA(launch_image_pairs(g, wk, w->stop, s));           // line 5: A w_k
         }
         {
-            CT_PHASE(CT_PH_FORWARD, 1, s);
+            CT_PHASE(CT_PH_FORWARD, fwd_launches(g), s);
             CT_CUDA(launch_forward_proj(g, w->sino, true, w->stop, s));
         }
         {
@@ -945,47 +953,57 @@ extern "C" int64_t ct_launch_count(void) { return g_launches.load(); }
 
 // ============================================================================ autotuning
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
+static std::map<std::tuple<int, int, int, int, int, int, int, int>, ct_launch_shapes> g_tune_cache;
 
-extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, int *a_threads, int *b_rows)
+static ct_launch_shapes shapes_of(const DeviceGeom &d)
+{
+    ct_launch_shapes r;
+    r.a_threads = d.tune_a_threads;
+    r.a_views = d.tune_a_views;
+    r.a_slab = d.tune_a_slab;
+    r.b_rows = d.tune_b_rows;
+    return r;
+}
+
+extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_shapes *out)
 {
     if (!g) return einval("ct_geom_autotune: null geometry");
-    if (g->desc.kind == CT_CONE3D) {      // the 3D kernels have one launch shape
-        if (a_threads) *a_threads = 256;
-        if (b_rows) *b_rows = 4;
-        return CT_OK;
-    }
+    const bool cone = g->desc.kind == CT_CONE3D;
+    DeviceGeom &dg = g->dg;
     cudaStream_t s = (cudaStream_t)stream;
     int dev = 0;
     CT_CUDA(cudaGetDevice(&dev));
-    const auto key = std::make_tuple(dev, (int)g->desc.kind, g->desc.nx, g->desc.ny,
-                                     g->desc.n_views, g->desc.n_det_u);
+    const auto key = std::make_tuple(dev, (int)g->desc.kind, g->desc.nx, g->desc.ny, g->desc.nz,
+                                     g->desc.n_views, g->desc.n_det_u, g->desc.n_det_v);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            g->dg.tune_a_threads = it->second.first;
-            g->dg.tune_b_rows = it->second.second;
-            if (a_threads) *a_threads = g->dg.tune_a_threads;
-            if (b_rows) *b_rows = g->dg.tune_b_rows;
+            dg.tune_a_threads = it->second.a_threads;
+            dg.tune_a_views = it->second.a_views;
+            dg.tune_a_slab = it->second.a_slab;
+            dg.tune_b_rows = it->second.b_rows;
+            if (out) *out = it->second;
             return CT_OK;
         }
     }
     float *x = nullptr, *y = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const size_t ylen = (size_t)dg.n_views * (size_t)dg.sino_view_ld;
     CT_CUDA(cudaMalloc(&x, sizeof(float) * (size_t)g->n));
-    CT_CUDA(cudaMalloc(&y, sizeof(float) * (size_t)g->dg.n_views * g->dg.sino_ld));
+    CT_CUDA(cudaMalloc(&y, sizeof(float) * ylen));
     CT_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * (size_t)g->n, s));
-    CT_CUDA(cudaMemsetAsync(y, 0, sizeof(float) * (size_t)g->dg.n_views * g->dg.sino_ld, s));
+    CT_CUDA(cudaMemsetAsync(y, 0, sizeof(float) * ylen, s));
     CT_CUDA(cudaEventCreate(&e0));
     CT_CUDA(cudaEventCreate(&e1));
     CT_CUDA(launch_image_pairs(g, x, nullptr, s));
-    auto time_best = [&](auto launch, const int *cand, int ncand, int *field) -> ct_status {
+    // time each candidate (one warm-up, best of three) and keep the fastest
+    auto time_best = [&](auto launch, int ncand, auto set) -> ct_status {
         float best = 1e30f;
-        int best_c = cand[0];
+        int best_c = 0;
         for (int c = 0; c < ncand; ++c) {
-            *field = cand[c];
-            CT_CUDA(launch());                       // warm-up
+            set(c);
+            CT_CUDA(launch());
             float t = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {
                 CT_CUDA(cudaEventRecord(e0, s));
@@ -996,18 +1014,26 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, int *a_thr
                 CT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
                 t = std::min(t, ms);
             }
-            if (t < best) { best = t; best_c = cand[c]; }
+            if (t < best) { best = t; best_c = c; }
         }
-        *field = best_c;
+        set(best_c);
         return CT_OK;
     };
-    static const int a_cand[3] = {128, 256, 512};
-    static const int b_cand[3] = {4, 8, 16};
-    ct_status st = time_best([&]() { return launch_joseph2d(g, y, g->dg.sino_ld, 2, nullptr, s); },
-                             a_cand, 3, &g->dg.tune_a_threads);
-    if (st == CT_OK)
-        st = time_best([&]() { return launch_back_proj(g, y, x, nullptr, s); }, b_cand, 3,
-                       &g->dg.tune_b_rows);
+    // 2D Joseph A: (rays per block, views per block); 3D: z-slab thickness of the Joseph passes;
+    // 2D B: pixel rows per 32-wide block (the 3D backprojector has one shape)
+    static const int a2[8][2] = {{128, 1}, {256, 1}, {512, 1}, {128, 2},
+                                 {256, 2}, {256, 4}, {512, 4}, {512, 8}};
+    static const int a3[4] = {8, 16, 32, 64};
+    static const int b2[3] = {4, 8, 16};
+    auto fwd = [&]() { return launch_forward_proj(g, y, true, nullptr, s); };
+    ct_status st;
+    if (cone)
+        st = time_best(fwd, 4, [&](int c) { dg.tune_a_slab = a3[c]; });
+    else
+        st = time_best(fwd, 8, [&](int c) { dg.tune_a_threads = a2[c][0]; dg.tune_a_views = a2[c][1]; });
+    if (st == CT_OK && !cone)
+        st = time_best([&]() { return launch_back_proj(g, y, x, nullptr, s); }, 3,
+                       [&](int c) { dg.tune_b_rows = b2[c]; });
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(x);
@@ -1015,10 +1041,9 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, int *a_thr
     if (st != CT_OK) return st;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key] = {g->dg.tune_a_threads, g->dg.tune_b_rows};
+        g_tune_cache[key] = shapes_of(dg);
     }
-    if (a_threads) *a_threads = g->dg.tune_a_threads;
-    if (b_rows) *b_rows = g->dg.tune_b_rows;
+    if (out) *out = shapes_of(dg);
     return CT_OK;
 }
 
@@ -1083,7 +1108,7 @@ extern "C" ct_status ct_batch_create(int n_prob, ct_geom *const *geoms, const in
         int mth = methods ? methods[i] : 2;
         if (mth == 2) mth = (geoms[i]->m < geoms[i]->n) ? 0 : 1;
         bt->method[i] = mth;
-        if (autotune && (st = ct_geom_autotune(geoms[i], nullptr, nullptr, nullptr)) != CT_OK) {
+        if (autotune && (st = ct_geom_autotune(geoms[i], nullptr, nullptr)) != CT_OK) {
             ct_batch_destroy(bt);
             return st;
         }

@@ -61,7 +61,9 @@ struct DeviceGeom {
     int col_pairs_ld;   // P_col row length in float2: >= ny + 1
     int sino_ld;        // padded sinogram row length: ndu + 4 (2 zero bins each side)
     int tune_a_threads; // Joseph A: rays (threads) per block, chosen by ct_geom_autotune
+    int tune_a_views;   // 2D Joseph A: views per block (each warp one view)
     int tune_b_rows;    // pixel-driven B: block of 32 x tune_b_rows pixels
+    int tune_a_slab;    // 3D Joseph A: z slab thickness (tap rows) per launch
     int64_t sino_view_ld; // floats per view in the padded sinogram (2D: sino_ld; 3D: (ndv + 2)
                           // rows of sino_ld, detector row 0 at row 1)
     int sino_row0;      // offset of detector row 0 inside a padded view (0 in 2D, sino_ld in 3D)
@@ -119,6 +121,8 @@ cudaError_t launch_joseph3d(const ct_geom *g, float *y, int64_t y_view_ld, int y
                             const int *stop, cudaStream_t s);
 cudaError_t launch_voxbp3d(const ct_geom *g, const float *ypad, float *x, const int *stop,
                            cudaStream_t s);
+// kernel launches made by one launch_joseph3d (one per z slab)
+int joseph3d_launches(const ct_geom *g);
 // total Joseph sample count of a cone geometry (one counting launch, synchronous)
 cudaError_t count_joseph3d_samples(const ct_geom *g, int64_t *out);
 

@@ -114,14 +114,19 @@ cudaError_t launch_back_proj(const ct_geom *g, const float *ypad, float *x, cons
 // ---------------------------------------------------------------------------- Joseph A
 // One thread per ray.  pos = pmid + slope * (t - t_mid) is the fractional index across the
 // driving axis; the pair at index floor(pos)+1 of line t holds both interpolation taps.
+// A block covers blockDim.x / vpb consecutive bins of vpb consecutive views (each warp one
+// view): the views of a block cross nearly the same pixels, so their warps share L1 lines.
 __global__ void __launch_bounds__(512) joseph2d_kernel(
-    const Ray2D *__restrict__ rays, int64_t m, int ndu,
+    const Ray2D *__restrict__ rays, int n_views, int ndu, int vpb,
     const float2 *__restrict__ prow, int prow_ld, const float2 *__restrict__ pcol, int pcol_ld,
     int nx, int ny, float *__restrict__ y, int y_ld, int y_off, const int *stop)
 {
     if (stop && stop[0] != 0) return;
-    int64_t ray = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (ray >= m) return;
+    const int bins_pb = blockDim.x / vpb;
+    const int bin = blockIdx.x * bins_pb + (int)threadIdx.x % bins_pb;
+    const int view0 = blockIdx.y * vpb + (int)threadIdx.x / bins_pb;
+    if (bin >= ndu || view0 >= n_views) return;
+    const int64_t ray = (int64_t)view0 * ndu + bin;
     const Ray2D R = rays[ray];
     const int t_lo = R.packed & 0x7fff;
     const int t_hi = (R.packed >> 15) & 0x7fff;
@@ -150,21 +155,20 @@ __global__ void __launch_bounds__(512) joseph2d_kernel(
         tf += 1.f;
         line += stride;
     }
-    int64_t view = ray / ndu;
-    int bin = (int)(ray - view * ndu);
-    y[view * y_ld + y_off + bin] = acc * R.weight;
+    y[(int64_t)view0 * y_ld + y_off + bin] = acc * R.weight;
 }
 
 cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, const int *stop,
                             cudaStream_t s)
 {
     const DeviceGeom &d = g->dg;
-    int64_t m = g->m;
     const int threads = d.tune_a_threads > 0 ? d.tune_a_threads : 256;
-    int blocks = (int)((m + threads - 1) / threads);
-    joseph2d_kernel<<<blocks, threads, 0, s>>>(g->rays_dev, m, d.ndu, g->prow_dev, d.row_pairs_ld,
-                                           g->pcol_dev, d.col_pairs_ld, d.nx, d.ny, y, y_ld,
-                                           y_off, stop);
+    const int vpb = (d.tune_a_views > 0 && threads / d.tune_a_views >= 32) ? d.tune_a_views : 1;
+    const int bins_pb = threads / vpb;
+    dim3 grid((d.ndu + bins_pb - 1) / bins_pb, (d.n_views + vpb - 1) / vpb);
+    joseph2d_kernel<<<grid, threads, 0, s>>>(g->rays_dev, d.n_views, d.ndu, vpb, g->prow_dev,
+                                             d.row_pairs_ld, g->pcol_dev, d.col_pairs_ld, d.nx,
+                                             d.ny, y, y_ld, y_off, stop);
     return cudaGetLastError();
 }
 

@@ -11,6 +11,9 @@
 // The padded sinogram of a cone geometry has, per view, one zero detector row above the
 // detector rows and two below, and 2 zero bins on each side of every row, so B's four taps need
 // no bounds test either (positions are clamped into the zero margins).
+#include <algorithm>
+#include <cmath>
+
 #include "ct_internal.h"
 
 namespace ct {
@@ -78,21 +81,36 @@ __device__ __forceinline__ Ray3D setup_ray3d(const RayXY &R, int iv, int ndv, do
     return q;
 }
 
+// The volume is processed in z slabs so that the pair rows a launch reads stay in L2: slab s
+// owns the samples whose lower tap row r = floor(z) + 1 (padded row index) lies in
+// [r_lo, r_hi); membership is decided on the same FP32 position the sample uses, so every
+// sample belongs to exactly one slab.  Launches after the first of a call add to y.
 __global__ void __launch_bounds__(256) joseph3d_kernel(
     const RayXY *__restrict__ rxy, int ndu, int ndv, double pitch_v, double h,
     const float2 *__restrict__ px, int64_t psx, int ldx, const float2 *__restrict__ py,
     int64_t psy, int ldy, int nx, int ny, int nz, float *__restrict__ y, int64_t y_view_ld,
-    int y_ld, int y_off, const int *stop)
+    int y_ld, int y_off, int iv0, int r_lo, int r_hi, int accumulate, const int *stop)
 {
     if (stop && stop[0] != 0) return;
     const int iu = blockIdx.x * blockDim.x + threadIdx.x;
     if (iu >= ndu) return;
-    const int view = blockIdx.y, iv = blockIdx.z;
+    const int view = blockIdx.y, iv = iv0 + blockIdx.z;
     const RayXY R = rxy[(int64_t)view * ndu + iu];
     const Ray3D q = setup_ray3d(R, iv, ndv, pitch_v, h, nx, ny, nz);
     float acc = 0.f;
+    bool any = false;
     if (q.mode != 2) {
         const bool ax = q.mode == 0;
+        const float tmid = 0.5f * (float)((ax ? nx : ny) - 1);
+        // planes whose z position can fall in the slab (FP64, one plane of margin each side)
+        int lo = q.lo, hi = q.hi;
+        if (q.zslope != 0.0) {
+            const double r = 1.0 / q.zslope;
+            const double ta = (double)tmid + ((r_lo - 1) - 1.0 - q.zmid) * r;
+            const double tb = (double)tmid + ((r_hi - 1) + 1.0 - q.zmid) * r;
+            lo = max(lo, (int)floor(fmin(ta, tb)) - 1);
+            hi = min(hi, (int)ceil(fmax(ta, tb)) + 1);
+        }
         const float2 *L = ax ? px : py;
         const int64_t ps = ax ? psx : psy;
         const int ld = ax ? ldx : ldy;
@@ -101,27 +119,34 @@ __global__ void __launch_bounds__(256) joseph3d_kernel(
         const float zhi = __int_as_float(__float_as_int((float)nz) - 1);
         const float bmid = R.bmid, bsl = R.bslope;
         const float zm = (float)q.zmid, zs = (float)q.zslope;
-        float tf = (float)q.lo - 0.5f * (float)((ax ? nx : ny) - 1);
-        const float2 *plane = L + (int64_t)(q.lo + 1) * ps;
-        for (int t = q.lo; t <= q.hi; ++t) {
-            const float pb = fminf(fmaxf(fmaf(bsl, tf, bmid), -1.f), bhi);
+        float tf = (float)lo - tmid;
+        const float2 *plane = L + (int64_t)(lo + 1) * ps;
+        for (int t = lo; t <= hi; ++t) {
             const float pz = fminf(fmaxf(fmaf(zs, tf, zm), -1.f), zhi);
-            const float fb = floorf(pb), fz = floorf(pz);
-            const float wb = pb - fb, wz = pz - fz;
-            const float2 *row = plane + (int64_t)((int)fz + 1) * ld + (int)fb + 1;
-            const float2 p0 = __ldg(row), p1 = __ldg(row + ld);
-            const float a0 = fmaf(wb, p0.y - p0.x, p0.x);
-            const float a1 = fmaf(wb, p1.y - p1.x, p1.x);
-            acc += fmaf(wz, a1 - a0, a0);
+            const float fz = floorf(pz);
+            const int rz = (int)fz + 1;
+            if (rz >= r_lo && rz < r_hi) {
+                const float pb = fminf(fmaxf(fmaf(bsl, tf, bmid), -1.f), bhi);
+                const float fb = floorf(pb);
+                const float wb = pb - fb, wz = pz - fz;
+                const float2 *row = plane + (int64_t)rz * ld + (int)fb + 1;
+                const float2 p0 = __ldg(row), p1 = __ldg(row + ld);
+                const float a0 = fmaf(wb, p0.y - p0.x, p0.x);
+                const float a1 = fmaf(wb, p1.y - p1.x, p1.x);
+                acc += fmaf(wz, a1 - a0, a0);
+                any = true;
+            }
             tf += 1.f;
             plane += ps;
         }
     } else {
-        // taps from P_y: pairs along x, plane y + 1, row z + 1
+        // driven along z: plane t is in the slab when its padded row t + 1 is; taps from P_y
+        // (pairs along x, plane y + 1, row z + 1)
         const double zt = 0.5 * (nz - 1);
         const float xhi = __int_as_float(__float_as_int((float)nx) - 1);
         const float yhi = __int_as_float(__float_as_int((float)ny) - 1);
-        for (int t = q.lo; t <= q.hi; ++t) {
+        const int lo = max(q.lo, r_lo - 1), hi = min(q.hi, r_hi - 2);
+        for (int t = lo; t <= hi; ++t) {
             const double tf = t - zt;
             const float pxf = fminf(fmaxf((float)(q.xmid + q.xs * tf), -1.f), xhi);
             const float pyf = fminf(fmaxf((float)(q.ymid + q.ys * tf), -1.f), yhi);
@@ -132,9 +157,12 @@ __global__ void __launch_bounds__(256) joseph3d_kernel(
             const float a0 = fmaf(wx, p0.y - p0.x, p0.x);
             const float a1 = fmaf(wx, p1.y - p1.x, p1.x);
             acc += fmaf(wy, a1 - a0, a0);
+            any = true;
         }
     }
-    y[(int64_t)view * y_view_ld + (int64_t)iv * y_ld + y_off + iu] = acc * q.weight;
+    float *out = y + (int64_t)view * y_view_ld + (int64_t)iv * y_ld + y_off + iu;
+    if (!accumulate) *out = acc * q.weight;
+    else if (any) *out += acc * q.weight;
 }
 
 // Total number of Joseph samples of the geometry (sum of the clipped plane ranges), for the
@@ -174,16 +202,65 @@ cudaError_t count_joseph3d_samples(const ct_geom *g, int64_t *out)
     return e;
 }
 
+// Detector rows that can see physical heights [z_a, z_b] of a volume whose x-y cross-section
+// lies within radius rxy of the axis: v = SDD z / (SID - p . d) with |p . d| <= rxy.
+static void rows_for_heights(const ct_geom *g, double z_a, double z_b, int &iv_lo, int &iv_hi)
+{
+    const ct_geom_desc &d = g->desc;
+    // taps may sit one voxel outside the volume: widen the radius by two voxels
+    const double rxy = 0.5 * d.pixel * sqrt((double)d.nx * d.nx + (double)d.ny * d.ny) + 2.0 * d.pixel;
+    double vmin = 1e300, vmax = -1e300;
+    for (double z : {z_a, z_b})
+        for (double sd : {-rxy, rxy}) {
+            const double v = d.sdd * z / (d.sid - sd);
+            vmin = std::min(vmin, v);
+            vmax = std::max(vmax, v);
+        }
+    const double c = 0.5 * (d.n_det_v - 1);
+    iv_lo = std::max(0, (int)floor(vmin / d.pitch_v + c) - 2);
+    iv_hi = std::min(d.n_det_v - 1, (int)ceil(vmax / d.pitch_v + c) + 2);
+}
+
 cudaError_t launch_joseph3d(const ct_geom *g, float *y, int64_t y_view_ld, int y_ld, int y_off,
                             const int *stop, cudaStream_t s)
 {
     const DeviceGeom &d = g->dg;
-    dim3 block(256), grid((d.ndu + 255) / 256, d.n_views, d.ndv);
-    joseph3d_kernel<<<grid, block, 0, s>>>(d.rays_xy, d.ndu, d.ndv, (double)g->desc.pitch_v,
-                                           g->desc.pixel, g->pcol_dev, d.plane_x, d.col_pairs_ld,
-                                           g->prow_dev, d.plane_y, d.row_pairs_ld, d.nx, d.ny,
-                                           d.nz, y, y_view_ld, y_ld, y_off, stop);
-    return cudaGetLastError();
+    const int slab = d.tune_a_slab > 0 ? d.tune_a_slab : 16;
+    const int n_rows = d.nz + 1;                 // padded tap rows r = floor(z) + 1 in [0, nz]
+    const int n_slabs = (n_rows + slab - 1) / slab;
+    if (n_slabs > 1) {
+        // every launch adds to y: start from zero (margins of a padded layout stay zero)
+        const size_t total = (size_t)d.n_views * (size_t)y_view_ld;
+        cudaError_t e = cudaMemsetAsync(y, 0, sizeof(float) * total, s);
+        if (e != cudaSuccess) return e;
+    }
+    const double h = g->desc.pixel, zc = 0.5 * (d.nz - 1);
+    for (int k = 0; k < n_slabs; ++k) {
+        const int r_lo = k * slab, r_hi = std::min(n_rows, (k + 1) * slab);
+        int iv_lo = 0, iv_hi = d.ndv - 1;
+        if (n_slabs > 1) {
+            // heights the slab's samples touch: z index in [r_lo - 2, r_hi], one of margin
+            rows_for_heights(g, (r_lo - 2 - zc) * h, (r_hi - zc) * h, iv_lo, iv_hi);
+            if (iv_hi < iv_lo) continue;
+        }
+        dim3 block(256), grid((d.ndu + 255) / 256, d.n_views, iv_hi - iv_lo + 1);
+        joseph3d_kernel<<<grid, block, 0, s>>>(d.rays_xy, d.ndu, d.ndv, (double)g->desc.pitch_v,
+                                               h, g->pcol_dev, d.plane_x, d.col_pairs_ld,
+                                               g->prow_dev, d.plane_y, d.row_pairs_ld, d.nx,
+                                               d.ny, d.nz, y, y_view_ld, y_ld, y_off, iv_lo, r_lo,
+                                               r_hi, n_slabs > 1 ? 1 : 0, stop);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// number of kernel launches one launch_joseph3d makes (for the library's launch count)
+int joseph3d_launches(const ct_geom *g)
+{
+    const DeviceGeom &d = g->dg;
+    const int slab = d.tune_a_slab > 0 ? d.tune_a_slab : 16;
+    return (d.nz + 1 + slab - 1) / slab;
 }
 
 // ---------------------------------------------------------------------------- voxel-driven B

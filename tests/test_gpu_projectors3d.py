@@ -115,3 +115,17 @@ def test_hybrid_ab_on_a_cone_problem(basis, tol):
     ref = OS.hybrid_gmres("ab", A, B, b, 10, rule="gcv")
     assert out["iters_done"] == 10
     assert rel(x.cpu().numpy(), ref["x"]) <= tol
+
+
+def test_autotuned_slab_thickness_keeps_the_result():
+    """The 3D autotuner picks a z-slab thickness; A is the same up to summation order."""
+    from paper_2602_17892_gb300 import ct_geom_autotune
+    g = GEOMS["cone_32"]
+    x = _volume(g, 4)
+    G = gpu_geom(g)
+    y_default = gpu_A(G, x)
+    sh = ct_geom_autotune(G)
+    assert sh["a_slab"] in (8, 16, 32, 64)
+    y_tuned = gpu_A(G, x)
+    assert rel(y_tuned, y_default) <= 1e-6
+    assert rel(y_tuned, OP.forward(g, x).reshape(-1)) <= TOL
