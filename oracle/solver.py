@@ -109,6 +109,51 @@ def tikhonov_y(lam: float, s: np.ndarray, c: np.ndarray, Vt: np.ndarray) -> np.n
     return Vt.T @ coef
 
 
+def lcurve_curvature(lam: float, s: np.ndarray, c: np.ndarray) -> float:
+    """Curvature of the projected L-curve (log ||H y_lam - beta e1||, log ||y_lam||) at lam
+    (Sec. 3.1, L-curve criterion), in closed form from eta = ||y||^2, rho = ||H y - beta e1||^2
+    and eta' = d eta / d lam (filter factors f_i = s_i^2 / (s_i^2 + lam^2)).  With
+    X = log sqrt(rho), Y = log sqrt(eta) and rho' = -lam^2 eta', the curvature
+    (X' Y'' - X'' Y') / (X'^2 + Y'^2)^(3/2) reduces to
+        kappa = 2 eta rho (lam^2 eta' rho + 2 lam eta rho + lam^4 eta eta')
+                / (|eta'| (lam^4 eta^2 + rho^2)^(3/2))."""
+    k = len(s)
+    pos = s > 0
+    f = s * s / (s * s + lam * lam)
+    ci = c[:k]
+    eta = float(np.sum((f[pos] * ci[pos] / s[pos]) ** 2))
+    rho = float(np.sum(((1.0 - f) * ci) ** 2) + np.sum(c[k:] ** 2))
+    deta = float(-4.0 / lam * np.sum((1.0 - f[pos]) * f[pos] ** 2 * (ci[pos] / s[pos]) ** 2))
+    if eta == 0.0 or rho == 0.0 or deta == 0.0:
+        return 0.0
+    num = lam * lam * deta * rho + 2.0 * lam * eta * rho + lam ** 4 * eta * deta
+    return 2.0 * eta * rho * num / (abs(deta) * (lam ** 4 * eta * eta + rho * rho) ** 1.5)
+
+
+def lcurve_lambda(s: np.ndarray, c: np.ndarray) -> float:
+    """The L-curve corner: the first maximum of the curvature on the 256-point grid of GCV,
+    refined by 40 golden-section steps in log lambda on the neighbouring bracket (kept only if
+    not worse)."""
+    s1 = float(s[0])
+    grid = s1 * np.power(10.0, np.linspace(math.log10(LAMBDA_RANGE), 0.0, GCV_GRID))
+    K = np.array([lcurve_curvature(l, s, c) for l in grid])
+    i = int(np.argmax(K))
+    a = math.log(grid[max(i - 1, 0)])
+    b = math.log(grid[min(i + 1, GCV_GRID - 1)])
+    invphi = (math.sqrt(5.0) - 1.0) / 2.0
+    for _ in range(GCV_GOLDEN_STEPS):
+        x1 = b - invphi * (b - a)
+        x2 = a + invphi * (b - a)
+        if lcurve_curvature(math.exp(x1), s, c) >= lcurve_curvature(math.exp(x2), s, c):
+            b = x2
+        else:
+            a = x1
+    lam = math.exp(0.5 * (a + b))
+    if lcurve_curvature(lam, s, c) < K[i]:
+        lam = float(grid[i])
+    return lam
+
+
 def choose_lambda(rule: str, s, c, lam_fixed=None, dp_target=None) -> float:
     if rule == "none":
         return 0.0
@@ -118,6 +163,8 @@ def choose_lambda(rule: str, s, c, lam_fixed=None, dp_target=None) -> float:
         return gcv_lambda(s, c)
     if rule == "dp":
         return dp_lambda(s, c, dp_target)
+    if rule == "lcurve":
+        return lcurve_lambda(s, c)
     raise ValueError(rule)
 
 

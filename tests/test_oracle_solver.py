@@ -207,3 +207,45 @@ def test_hybrid_stabilises_semi_convergence():
     e_hyb = [S.rre(hyb["iterates"][k], x) for k in ks]
     assert e_plain[-1] > min(e_plain) * 1.05          # semi-convergence
     assert e_hyb[-1] < e_plain[-1]
+
+
+@pytest.mark.parametrize("k", [4, 17])
+def test_lcurve_curvature_matches_finite_differences(k):
+    """The closed-form curvature against central differences of the parametric curve
+    (log ||H y - beta e1||, log ||y||) in t = ln lambda, with y from the stacked least-squares
+    problem (no SVD); curvature does not depend on the parametrisation."""
+    rng = np.random.Generator(np.random.PCG64(300 + k))
+    H = np.triu(rng.standard_normal((k + 1, k)), -1) * np.logspace(0, -4, k)[None, :]
+    beta = 1.3
+    s, c, Vt = S.projected_svd(H, beta)
+    e1 = np.zeros(k + 1)
+    e1[0] = beta
+
+    def point(t):
+        lam = math.exp(t)
+        y = np.linalg.lstsq(np.vstack([H, lam * np.eye(k)]), np.concatenate([e1, np.zeros(k)]),
+                            rcond=None)[0]
+        return math.log(np.linalg.norm(H @ y - e1)), math.log(np.linalg.norm(y))
+
+    for lam in s[0] * np.array([1e-4, 1e-3, 1e-2, 0.1, 0.5]):
+        t, h = math.log(lam), 1e-3
+        (xm2, ym2), (xm, ym), (x0, y0), (xp, yp), (xp2, yp2) = [point(t + j * h) for j in (-2, -1, 0, 1, 2)]
+        x1 = (-xp2 + 8 * xp - 8 * xm + xm2) / (12 * h)
+        y1 = (-yp2 + 8 * yp - 8 * ym + ym2) / (12 * h)
+        x2 = (-xp2 + 16 * xp - 30 * x0 + 16 * xm - xm2) / (12 * h * h)
+        y2 = (-yp2 + 16 * yp - 30 * y0 + 16 * ym - ym2) / (12 * h * h)
+        kfd = (x1 * y2 - x2 * y1) / (x1 * x1 + y1 * y1) ** 1.5
+        kcf = S.lcurve_curvature(lam, s, c)
+        assert abs(kcf - kfd) <= 1e-4 * max(1.0, abs(kfd)), (lam, kcf, kfd)
+
+
+@pytest.mark.parametrize("k", [6, 20])
+def test_lcurve_corner_is_the_curvature_maximum(k):
+    rng = np.random.Generator(np.random.PCG64(400 + k))
+    H = np.triu(rng.standard_normal((k + 1, k)), -1) * np.logspace(0, -4, k)[None, :]
+    s, c, Vt = S.projected_svd(H, 2.0)
+    lam = S.lcurve_lambda(s, c)
+    assert s[0] * 1e-8 * (1 - 1e-12) <= lam <= s[0] * (1 + 1e-12)
+    dense = s[0] * np.logspace(-8, 0, 20001)
+    kmax = max(S.lcurve_curvature(l, s, c) for l in dense)
+    assert S.lcurve_curvature(lam, s, c) >= kmax * (1 - 1e-6)
