@@ -104,9 +104,11 @@ typedef enum {
     CT_LAMBDA_FIXED = 1,  /* lambda = lambda_fixed at every iteration                        */
     CT_LAMBDA_GCV = 2,    /* GCV on the projected problem (Sec. 3.1)                          */
     CT_LAMBDA_DP = 3,     /* discrepancy principle: ||H y - beta e1|| = tau * noise_norm      */
-    CT_LAMBDA_LEARNED = 4 /* not in the paper: lambda_k = sigma_1 10^net(features of H_k) from a
+    CT_LAMBDA_LEARNED = 4,/* not in the paper: lambda_k = sigma_1 10^net(features of H_k) from a
                              trained network (see "learned lambda" below); GCV where the
                              network's output is not finite                                  */
+    CT_LAMBDA_LCURVE = 5  /* L-curve criterion (Sec. 3.1): the corner (maximum curvature) of
+                             (log ||H y - beta e1||, log ||y||), searched on the GCV grid     */
 } ct_lambda_rule;
 
 typedef enum { CT_BASIS_F32 = 0, CT_BASIS_BF16 = 1, CT_BASIS_F16 = 2 } ct_basis_dtype;
@@ -156,6 +158,23 @@ ct_status ab_gmres_hybrid(ct_geom *g, const float *b_dev, const float *u0_dev, f
  * Arnoldi on B A, x_K = x0 + W_K y_K.  Same conventions as ab_gmres_hybrid. */
 ct_status ba_gmres_hybrid(ct_geom *g, const float *b_dev, const float *x0_dev, float *x_dev,
                           const ct_hybrid_opts *o, ct_hybrid_info *info, ct_stream_t stream);
+
+/* Restarted hybrid AB-/BA-GMRES (Sec. 3.3, Restarting): `cycles` cycles of o->max_iters = p
+ * steps each, every cycle restarting Algorithm 1 / 2 from the iterate of the previous one
+ * (AB keeps its iterate as u with x = B u, so its restart r0 = b - A B u equals the restart from
+ * x; BA restarts from x).  The Krylov basis holds p + 1 vectors whatever the number of cycles.
+ * lambda is chosen per step by o->rule as in the plain solvers.  x_dev (n floats) receives the
+ * final iterate (its input content is ignored).  o->lambda_hist / o->resid_hist, when given,
+ * need cycles * p entries (cycle-major); o->features_dev is ignored.  info: iters_done sums the
+ * cycles, beta is the first cycle's ||r0||, the rest describes the last cycle.  Synchronises
+ * `stream` after every cycle.  A cycle that starts from an exact iterate (r0 = 0) ends the
+ * solve. */
+ct_status ab_gmres_hybrid_restarted(ct_geom *g, const float *b_dev, float *x_dev, int cycles,
+                                    const ct_hybrid_opts *o, ct_hybrid_info *info,
+                                    ct_stream_t stream);
+ct_status ba_gmres_hybrid_restarted(ct_geom *g, const float *b_dev, float *x_dev, int cycles,
+                                    const ct_hybrid_opts *o, ct_hybrid_info *info,
+                                    ct_stream_t stream);
 
 /* ------------------------------------------------------------------ tile autotuning */
 
@@ -242,7 +261,7 @@ ct_status ct_arnoldi_step_noalloc(float *W_dev, int64_t len, int64_t ld, int k, 
  * (k+1) x k Hessenberg matrix H (FP64, column-major, leading dimension ldh >= k+1) and
  * beta = ||r0||, choose lambda by `rule` and return y (k doubles), lambda and the projected
  * residual ||H y - beta e1||.  All pointers are device pointers.  1 <= k <= 160;
- * rule CT_LAMBDA_NONE .. CT_LAMBDA_DP. */
+ * any rule but CT_LAMBDA_LEARNED. */
 ct_status ct_projected_solve(const double *H_dev, int ldh, int k, double beta,
                              ct_lambda_rule rule, double lambda_fixed, double dp_target,
                              double *y_dev, double *lambda_dev, double *resid_dev,

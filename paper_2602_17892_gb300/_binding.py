@@ -19,7 +19,7 @@ CT_OK, CT_EINVAL, CT_ENOMEM, CT_ECUDA, CT_BREAKDOWN, CT_ETIMEOUT, CT_ENONFINITE 
 STATUS_NAMES = {0: "CT_OK", 1: "CT_EINVAL", 2: "CT_ENOMEM", 3: "CT_ECUDA", 4: "CT_BREAKDOWN",
                 5: "CT_ETIMEOUT", 6: "CT_ENONFINITE"}
 KINDS = {"parallel2d": 0, "fanflat2d": 1, "cone3d": 2}
-RULES = {"none": 0, "fixed": 1, "gcv": 2, "dp": 3, "learned": 4}
+RULES = {"none": 0, "fixed": 1, "gcv": 2, "dp": 3, "learned": 4, "lcurve": 5}
 CT_MLP_NIN, CT_MLP_NPARAMS = 80, 9569
 BASIS = {"f32": 0, "bf16": 1, "f16": 2}
 
@@ -29,7 +29,8 @@ EXPORTS = ("ct_geom_create", "ct_geom_destroy", "ct_geom_dims", "ct_geom_work", 
            "ct_projected_solve", "ct_status_string", "ct_last_error", "ct_profile_enable",
            "ct_profile_collect", "ct_launch_count", "ct_geom_autotune", "ct_batch_create",
            "ct_batch_solve", "ct_batch_launches", "ct_batch_destroy", "abba_solve", "ct_mlp_forward",
-           "ct_mlp_grad", "ct_mlp_adam", "ct_mlp_train", "ct_lambda_samples")
+           "ct_mlp_grad", "ct_mlp_adam", "ct_mlp_train", "ct_lambda_samples",
+           "ab_gmres_hybrid_restarted", "ba_gmres_hybrid_restarted")
 PHASES = ("forward_A", "back_B", "layout", "arnoldi", "small_solve", "other")
 
 
@@ -96,6 +97,9 @@ def load(path: str = LIB_PATH):
     lib.ct_hybrid_opts_default.restype = None
     for fn in (lib.ab_gmres_hybrid, lib.ba_gmres_hybrid):
         fn.argtypes = [vp, vp, vp, vp, ctypes.POINTER(HybridOpts), ctypes.POINTER(HybridInfo), vp]
+    for fn in (lib.ab_gmres_hybrid_restarted, lib.ba_gmres_hybrid_restarted):
+        fn.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.POINTER(HybridOpts),
+                       ctypes.POINTER(HybridInfo), vp]
     lib.ct_arnoldi_step.argtypes = [vp, i64, i64, ctypes.c_int, vp, vp, vp]
     lib.ct_arnoldi_step_noalloc.argtypes = [vp, i64, i64, ctypes.c_int, vp, vp, vp]
     lib.ct_arnoldi_step_noalloc.restype = ctypes.c_int
@@ -254,6 +258,43 @@ def ba_gmres_hybrid(g, b, x, x0=None, max_iters=30, rule="gcv", lambda_fixed=0.0
     """Hybrid BA-GMRES (Algorithm 2): x <- x0 + W_K y_K."""
     return _solve(load().ba_gmres_hybrid, g, b, x, x0, max_iters, rule, lambda_fixed,
                   noise_norm, tau, reorth, basis, history, stream, lambda_net, features)
+
+
+def _solve_restarted(fn, g, b, x, cycles, max_iters, rule, lambda_fixed, noise_norm, tau,
+                     reorth, basis, history, stream, lambda_net):
+    o, _, _ = _opts(max_iters, rule, lambda_fixed, noise_norm, tau, reorth, basis, False,
+                    lambda_net)
+    lam = res = None
+    if history:
+        lam = np.full(int(cycles) * int(max_iters), np.nan)
+        res = np.full(int(cycles) * int(max_iters), np.nan)
+        o.lambda_hist = lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        o.resid_hist = res.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    info = HybridInfo()
+    _check(fn(g.handle, _ptr(b), _ptr(x), int(cycles), ctypes.byref(o), ctypes.byref(info),
+              _stream(stream)))
+    out = _info_dict(info)
+    if history:
+        out["lambdas"], out["resid"] = lam, res
+    return out
+
+
+def ab_gmres_hybrid_restarted(g, b, x, cycles, max_iters=10, rule="gcv", lambda_fixed=0.0,
+                              noise_norm=0.0, tau=1.01, reorth=1, basis="f32", history=True,
+                              stream=None, lambda_net=None):
+    """Restarted hybrid AB-GMRES (Sec. 3.3): `cycles` cycles of `max_iters` steps."""
+    return _solve_restarted(load().ab_gmres_hybrid_restarted, g, b, x, cycles, max_iters, rule,
+                            lambda_fixed, noise_norm, tau, reorth, basis, history, stream,
+                            lambda_net)
+
+
+def ba_gmres_hybrid_restarted(g, b, x, cycles, max_iters=10, rule="gcv", lambda_fixed=0.0,
+                              noise_norm=0.0, tau=1.01, reorth=1, basis="f32", history=True,
+                              stream=None, lambda_net=None):
+    """Restarted hybrid BA-GMRES (Sec. 3.3): `cycles` cycles of `max_iters` steps."""
+    return _solve_restarted(load().ba_gmres_hybrid_restarted, g, b, x, cycles, max_iters, rule,
+                            lambda_fixed, noise_norm, tau, reorth, basis, history, stream,
+                            lambda_net)
 
 
 def ct_arnoldi_step(W, length, ld, k, q, h, stream=None):

@@ -514,7 +514,7 @@ static ct_status check_opts(const ct_hybrid_opts *o)
     if (!o) return einval("solver: opts is NULL");
     if (o->max_iters < 1 || o->max_iters > kMaxSmallK)
         return einval("solver: max_iters must be in [1, " + std::to_string(kMaxSmallK) + "]");
-    if (o->rule < CT_LAMBDA_NONE || o->rule > CT_LAMBDA_LEARNED) return einval("solver: bad lambda rule");
+    if (o->rule < CT_LAMBDA_NONE || o->rule > CT_LAMBDA_LCURVE) return einval("solver: bad lambda rule");
     if (o->rule == CT_LAMBDA_LEARNED && !o->lambda_net_dev)
         return einval("solver: CT_LAMBDA_LEARNED needs lambda_net_dev");
     if (o->rule == CT_LAMBDA_FIXED && !(o->lambda_fixed >= 0)) return einval("solver: lambda_fixed must be >= 0");
@@ -595,7 +595,8 @@ static ct_status run_small_solves(Workspace *w, const ct_hybrid_opts *o, cudaStr
 // Algorithm 1, enqueued on s without any host synchronisation (graph-capturable once the
 // workspace exists); the caller reads the results with read_info after synchronising.
 static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev, float *x_dev,
-                            const ct_hybrid_opts *o, cudaStream_t s, Workspace **wout)
+                            const ct_hybrid_opts *o, cudaStream_t s, Workspace **wout,
+                            bool u0_padded = false)
 {
     ct_status st;
     Workspace *w;
@@ -613,8 +614,8 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
         CT_PHASE(CT_PH_OTHER, u0_dev ? 8 : 3, s);
         CT_CUDA(launch_pad_sino(g, b_dev, w->vec, s));
         if (u0_dev) {
-            CT_CUDA(launch_pad_sino(g, u0_dev, w->sino, s));
-            CT_CUDA(launch_back_proj(g, w->sino, w->img, nullptr, s));
+            if (!u0_padded) CT_CUDA(launch_pad_sino(g, u0_dev, w->sino, s));
+            CT_CUDA(launch_back_proj(g, u0_padded ? u0_dev : w->sino, w->img, nullptr, s));
             CT_CUDA(launch_image_pairs(g, w->img, nullptr, s));
             CT_CUDA(launch_forward_proj(g, w->q, true, nullptr, s));
             CT_CUDA(launch_rsub(w->vec, w->q, L, kMaxBlocks, s));
@@ -649,9 +650,10 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
     // line 13 at k = K: x = x0 + B W y = B (u0 + W y)
     {
         CT_PHASE(CT_PH_OTHER, u0_dev ? 2 : 1, s);
-        if (u0_dev) CT_CUDA(launch_pad_sino(g, u0_dev, w->sino, s));
+        if (u0_dev && !u0_padded) CT_CUDA(launch_pad_sino(g, u0_dev, w->sino, s));
         CT_CUDA(launch_combine_basis(o->basis, w->W, L, ld, w->Y, K, w->K, w->stop, 0,
-                                     u0_dev ? w->sino : nullptr, w->q, kMaxBlocks, s));
+                                     u0_dev ? (u0_padded ? u0_dev : w->sino) : nullptr, w->q,
+                                     kMaxBlocks, s));
     }
     {
         CT_PHASE(CT_PH_BACK, 1, s);
@@ -755,6 +757,74 @@ extern "C" ct_status ba_gmres_hybrid(ct_geom *g, const float *b_dev, const float
     return finish(w, o, info, s);
 }
 
+// ============================================================================ restarts
+// Sec. 3.3 (Restarting): cycles of o->max_iters steps, each restarted from the previous
+// iterate.  AB keeps the iterate in its own variable u (x = B u), in the padded sinogram layout,
+// so a restart is r0 = b - A B u, exactly the restart from x = B u; BA restarts from x.
+static ct_status restarted(ct_geom *g, const float *b_dev, float *x_dev, int cycles,
+                           const ct_hybrid_opts *o, ct_hybrid_info *info, cudaStream_t s,
+                           bool ab)
+{
+    ct_status st = check_opts(o);
+    if (st != CT_OK) return st;
+    if (cycles < 1) return einval("restarted solver: cycles must be >= 1");
+    const int K = o->max_iters;
+    ct_hybrid_opts oc = *o;
+    std::vector<double> lam((size_t)K), res((size_t)K);
+    oc.lambda_hist = o->lambda_hist ? lam.data() : nullptr;
+    oc.resid_hist = o->resid_hist ? res.data() : nullptr;
+    oc.features_dev = nullptr;
+    float *u = nullptr;
+    ct_hybrid_info total{};
+    for (int c = 0; c < cycles; ++c) {
+        Workspace *w = nullptr;
+        if (ab) st = enqueue_ab(g, b_dev, c == 0 ? nullptr : u, x_dev, &oc, s, &w, true);
+        else st = enqueue_ba(g, b_dev, c == 0 ? nullptr : x_dev, x_dev, &oc, s, &w);
+        if (st != CT_OK) break;
+        if (ab) {
+            if (!u) {
+                cudaError_t e = cudaMallocAsync((void **)&u, sizeof(float) * (size_t)w->L, s);
+                if (e != cudaSuccess) { st = cuda_fail(e, "restarted solver"); break; }
+            }
+            cudaError_t e = cudaMemcpyAsync(u, w->q, sizeof(float) * (size_t)w->L,
+                                            cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) { st = cuda_fail(e, "restarted solver"); break; }
+        }
+        ct_hybrid_info ic{};
+        st = finish(w, &oc, &ic, s);
+        if (st != CT_OK) break;
+        if (o->lambda_hist) memcpy(o->lambda_hist + (size_t)c * K, lam.data(), sizeof(double) * K);
+        if (o->resid_hist) memcpy(o->resid_hist + (size_t)c * K, res.data(), sizeof(double) * K);
+        if (c == 0) total.beta = ic.beta;
+        total.iters_done += ic.iters_done;
+        total.final_lambda = ic.final_lambda;
+        total.final_resid = ic.final_resid;
+        total.fast_path_steps += ic.fast_path_steps;
+        total.lambda_fallback_steps += ic.lambda_fallback_steps;
+        total.status = ic.status;
+        if (ic.iters_done == 0) break;           // r0 = 0: the iterate is exact
+    }
+    if (u) cudaFreeAsync(u, s);
+    if (info) *info = total;
+    return st;
+}
+
+extern "C" ct_status ab_gmres_hybrid_restarted(ct_geom *g, const float *b_dev, float *x_dev,
+                                               int cycles, const ct_hybrid_opts *o,
+                                               ct_hybrid_info *info, ct_stream_t stream)
+{
+    if (!g || !b_dev || !x_dev) return einval("ab_gmres_hybrid_restarted: null argument");
+    return restarted(g, b_dev, x_dev, cycles, o, info, (cudaStream_t)stream, true);
+}
+
+extern "C" ct_status ba_gmres_hybrid_restarted(ct_geom *g, const float *b_dev, float *x_dev,
+                                               int cycles, const ct_hybrid_opts *o,
+                                               ct_hybrid_info *info, ct_stream_t stream)
+{
+    if (!g || !b_dev || !x_dev) return einval("ba_gmres_hybrid_restarted: null argument");
+    return restarted(g, b_dev, x_dev, cycles, o, info, (cudaStream_t)stream, false);
+}
+
 // ============================================================================ building blocks
 extern "C" ct_status ct_arnoldi_step(float *W_dev, int64_t len, int64_t ld, int k, float *q_dev,
                                      double *h_dev, ct_stream_t stream)
@@ -791,7 +861,8 @@ extern "C" ct_status ct_projected_solve(const double *H_dev, int ldh, int k, dou
     if (!H_dev || !y_dev || !lambda_dev || !resid_dev) return einval("ct_projected_solve: null argument");
     if (k < 1 || k > kMaxSmallK || ldh < k + 1)
         return einval("ct_projected_solve: need 1 <= k <= " + std::to_string(kMaxSmallK) + " and ldh >= k+1");
-    if (rule < CT_LAMBDA_NONE || rule > CT_LAMBDA_DP) return einval("ct_projected_solve: bad rule");
+    if (rule < CT_LAMBDA_NONE || rule > CT_LAMBDA_LCURVE || rule == CT_LAMBDA_LEARNED)
+        return einval("ct_projected_solve: bad rule");
     SmallSolveParams p;
     p.H = H_dev; p.ldh = ldh; p.k = k; p.beta = beta; p.betap = nullptr;
     p.rule = rule; p.lambda_fixed = lambda_fixed; p.dp_target = dp_target;

@@ -779,6 +779,93 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
         have_lam = false;
     }
     if (have_lam) {
+    } else if (P.rule == CT_LAMBDA_LCURVE) {
+        // L-curve corner (Sec. 3.1): maximum curvature of (log ||H y - beta e1||, log ||y||).
+        // With inv_i = 1/(sigma_i^2 + lambda^2): eta = ||y||^2 = sum (sigma_i c_i inv_i)^2,
+        // rho = sum (lambda^2 c_i inv_i)^2 + c_{k+1}^2, eta' = -4 lambda D with
+        // D = sum sigma_i^2 c_i^2 inv_i^3, and the curvature of the log-log curve is
+        //   kappa = eta rho (eta rho - 2 lambda^2 D (rho + lambda^2 eta))
+        //           / (D (lambda^4 eta^2 + rho^2)^(3/2)).
+        auto kappa = [&](double l, double eta, double rho, double D) {
+            if (!(eta > 0.0) || !(rho > 0.0) || !(D > 0.0)) return 0.0;
+            const double l2 = l * l;
+            const double q = l2 * l2 * eta * eta + rho * rho;
+            return eta * rho * (eta * rho - 2.0 * l2 * D * (rho + l2 * eta)) / (D * q * sqrt(q));
+        };
+        auto gridlam = [&](int t) {
+            double expo = (t == kGcvGrid - 1) ? 0.0 : -8.0 + t * (8.0 / (kGcvGrid - 1));
+            return s1 * pow(10.0, expo);
+        };
+        const double ck2 = cv[k] * cv[k];
+        for (int t = tid; t < kGcvGrid; t += kSSThreads) {
+            const double lt = gridlam(t), l2 = lt * lt;
+            double eta = 0.0, rho = 0.0, D = 0.0;
+            for (int i = 0; i < k; ++i) {
+                const double inv = rcp64(sig2[i] + l2);
+                const double a = sig[i] * cv[i] * inv;
+                const double r = l2 * cv[i] * inv;
+                eta += a * a;
+                rho += r * r;
+                D += a * a * inv;
+            }
+            red[t] = kappa(lt, eta, rho + ck2, D);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int ibest = 0;
+            double best = red[0];
+            for (int t = 1; t < kGcvGrid; ++t)
+                if (red[t] > best) { best = red[t]; ibest = t; }
+            misc[12] = (double)ibest;
+            misc[13] = best;
+        }
+        __syncthreads();
+        const int ibest = (int)misc[12];
+        const double kbest = misc[13];
+        // two lambdas per block pass: threads 0-127 take lamA, 128-255 lamB
+        auto evalk2 = [&](double lamA, double lamB, double &kA, double &kB) {
+            const int half = tid >> 7, t = tid & 127;
+            const double l = half ? lamB : lamA, l2 = l * l;
+            double eta = 0.0, rho = 0.0, D = 0.0;
+            for (int i = t; i < k; i += 128) {
+                const double inv = rcp64(sig2[i] + l2);
+                const double a = sig[i] * cv[i] * inv;
+                const double r = l2 * cv[i] * inv;
+                eta += a * a;
+                rho += r * r;
+                D += a * a * inv;
+            }
+            eta = warp_sum_d(eta);
+            rho = warp_sum_d(rho);
+            D = warp_sum_d(D);
+            __syncthreads();
+            if (lane == 0) {
+                misc[16 + 3 * warp] = eta;
+                misc[17 + 3 * warp] = rho;
+                misc[18 + 3 * warp] = D;
+            }
+            __syncthreads();
+            double e0 = 0, r0 = 0, d0 = 0, e1 = 0, r1 = 0, d1 = 0;
+            for (int w = 0; w < 4; ++w) {
+                e0 += misc[16 + 3 * w]; r0 += misc[17 + 3 * w]; d0 += misc[18 + 3 * w];
+                e1 += misc[28 + 3 * w]; r1 += misc[29 + 3 * w]; d1 += misc[30 + 3 * w];
+            }
+            kA = kappa(lamA, e0, r0 + ck2, d0);
+            kB = kappa(lamB, e1, r1 + ck2, d1);
+        };
+        double a = log(gridlam(ibest > 0 ? ibest - 1 : 0));
+        double b = log(gridlam(ibest < kGcvGrid - 1 ? ibest + 1 : kGcvGrid - 1));
+        const double invphi = 0.6180339887498949;
+        for (int it = 0; it < 40; ++it) {
+            const double x1 = b - invphi * (b - a), x2 = a + invphi * (b - a);
+            double k1, k2;
+            evalk2(exp(x1), exp(x2), k1, k2);
+            if (k1 >= k2) b = x2; else a = x1;
+        }
+        double lr = exp(0.5 * (a + b)), kr, kdum;
+        evalk2(lr, lr, kr, kdum);
+        if (kr < kbest) lr = gridlam(ibest);
+        lam = lr;
     } else if (P.rule != CT_LAMBDA_DP) {   // GCV, and the learned rule's fallback
         for (int t = tid; t < kGcvGrid; t += kSSThreads) {
             double expo = (t == kGcvGrid - 1) ? 0.0 : -8.0 + t * (8.0 / (kGcvGrid - 1));

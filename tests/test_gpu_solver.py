@@ -30,7 +30,7 @@ def _hessenberg(k, seed, decay=-5):
 
 
 @pytest.mark.parametrize("k", [1, 2, 5, 30, 100, 160])
-@pytest.mark.parametrize("rule", ["none", "fixed", "gcv", "dp"])
+@pytest.mark.parametrize("rule", ["none", "fixed", "gcv", "dp", "lcurve"])
 def test_projected_solve_matches_oracle(k, rule):
     torch = _torch()
     from paper_2602_17892_gb300 import ct_projected_solve, build
@@ -61,6 +61,14 @@ def test_projected_solve_matches_oracle(k, rule):
         # (unique) tightly and the argument loosely
         assert abs(lg - lam_o) <= 1e-6 * lam_o
         assert OS.gcv_value(lg, s, c) <= OS.gcv_value(lam_o, s, c) * (1 + 1e-12)
+        y_o = OS.tikhonov_y(lg, s, c, Vt)
+        r_o = math.sqrt(OS.residual_sq(lg, s, c))
+    elif rule == "lcurve":
+        # the corner is a maximum of the curvature: compare the maximum value tightly and the
+        # argument loosely (flat top)
+        assert abs(lg - lam_o) <= 1e-5 * lam_o
+        ko = OS.lcurve_curvature(lam_o, s, c)
+        assert OS.lcurve_curvature(lg, s, c) >= ko - 1e-10 * abs(ko)
         y_o = OS.tikhonov_y(lg, s, c, Vt)
         r_o = math.sqrt(OS.residual_sq(lg, s, c))
     else:
@@ -147,7 +155,7 @@ def test_small_parallel_ab_gcv_matches_oracle():
 
 
 @pytest.mark.parametrize("method", ["ab", "ba"])
-@pytest.mark.parametrize("rule", ["none", "fixed", "dp", "gcv"])
+@pytest.mark.parametrize("rule", ["none", "fixed", "dp", "gcv", "lcurve"])
 def test_ragged_fan_solves_match_oracle(method, rule):
     g = synth.fanflat2d(45, 60, 70, 150.0, 240.0, ny=38)
     x_true, b, e = problem(g, 5, 0.02, 77)
@@ -233,3 +241,26 @@ def test_low_precision_basis_small(method, basis):
     err = rel(xg, ref["x"])
     tol = BASIS_TOL[method][basis]
     assert np.isfinite(err) and (tol is None or err <= tol), err
+
+
+@pytest.mark.parametrize("method", ["ab", "ba"])
+@pytest.mark.parametrize("rule", ["gcv", "dp", "lcurve"])
+def test_restarted_solves_match_oracle(method, rule):
+    """Sec. 3.3: three cycles of six steps, each restarted from the previous iterate."""
+    from paper_2602_17892_gb300 import ab_gmres_hybrid_restarted, ba_gmres_hybrid_restarted
+    torch = _torch()
+    g = synth.fanflat2d(45, 60, 70, 150.0, 240.0, ny=38)
+    x_true, b, e = problem(g, 5, 0.02, 77)
+    noise = np.linalg.norm(e) if method == "ab" else np.linalg.norm(OP.back_pixel(g, e))
+    G = gpu_geom(g)
+    x = torch.full((G.n,), 7.0, dtype=torch.float32, device="cuda")     # ignored on input
+    fn = ab_gmres_hybrid_restarted if method == "ab" else ba_gmres_hybrid_restarted
+    out = fn(G, to_dev(b), x, 3, max_iters=6, rule=rule, noise_norm=noise, tau=1.01)
+    torch.cuda.synchronize()
+    assert out["iters_done"] == 18 and out["lambdas"].shape == (18,)
+    A, B = OP.operators(g)
+    xo, hist = OS.restarted_hybrid_gmres(method, A, B, b, 6, 3, rule=rule, dp_target=1.01 * noise)
+    assert rel(x.cpu().numpy(), xo) <= ITER_TOL
+    if rule == "dp":           # a root of a monotone function: fixed to rounding (GCV and the
+        lam_o = np.concatenate([h["lambdas"] for h in hist])     # L-curve have flat extrema)
+        np.testing.assert_allclose(out["lambdas"], lam_o, rtol=1e-3)
