@@ -192,15 +192,31 @@ def givens_gmres_y(Hk: np.ndarray, beta: float):
 
 # ----------------------------------------------------------------------------- Algorithms 1 / 2
 
+def stop_reached(stop_rule, resid, k: int, stop_target=None, stop_tol=None) -> bool:
+    """Stopping criteria of Sec. 3.2 on the residual norms rho_1..rho_k (resid, 0-based):
+    'dp'  stops at the first k with rho_k <= tau ||e|| (stop_target; the paper prints the
+          inequality reversed), 'rns' at the first k >= 2 with
+          |rho_{k-1} - rho_k| / rho_{k-1} < stop_tol."""
+    if stop_rule is None or stop_rule == "none":
+        return False
+    if stop_rule == "dp":
+        return resid[k - 1] <= stop_target
+    if stop_rule == "rns":
+        return k >= 2 and abs(resid[k - 2] - resid[k - 1]) < stop_tol * resid[k - 2]
+    raise ValueError(stop_rule)
+
+
 def hybrid_gmres(method: str, A, B, b, iters: int, rule: str = "gcv", lam_fixed=None,
                  dp_target=None, reorth: bool = True, keep_iterates=(), x0=None,
-                 true_residual: bool = False):
+                 true_residual: bool = False, stop_rule=None, stop_tol=None, stop_target=None):
     """Hybrid AB-GMRES (method='ab', Algorithm 1) or hybrid BA-GMRES ('ba', Algorithm 2).
 
-    A, B: callables on flat FP64 vectors.  rule in {'none', 'fixed', 'gcv', 'dp'}; dp_target
-    is tau * ||e|| for AB and tau * ||B e|| for BA (the noise in the space where Alg. 2
-    measures its residual).  Returns a dict with the final iterate, the per-iteration
-    lambda and projected residual, H, W, y and iterates at the steps in keep_iterates.
+    A, B: callables on flat FP64 vectors.  rule in {'none', 'fixed', 'gcv', 'dp', 'lcurve'};
+    dp_target is tau * ||e|| for AB and tau * ||B e|| for BA (the noise in the space where
+    Alg. 2 measures its residual).  stop_rule in {None, 'dp', 'rns'} ends the iteration early
+    (Sec. 3.2; stop_target, stop_tol).  Returns a dict with the final iterate, the
+    per-iteration lambda and projected residual, H, W, y and iterates at the steps in
+    keep_iterates.
     """
     b = np.asarray(b, dtype=np.float64).reshape(-1)
     if method == "ab":
@@ -257,6 +273,9 @@ def hybrid_gmres(method: str, A, B, b, iters: int, rule: str = "gcv", lam_fixed=
                 out["true_resid"].append(float(np.linalg.norm(r if method == "ab" else B(r))))
         if broke:
             out["status"] = "breakdown"
+            break
+        if stop_reached(stop_rule, out["resid"], k, stop_target, stop_tol):
+            out["status"] = "stopped"
             break
     out.update(x=_form_x(method, B, x0v, W[:k_done], y), H=H[: k_done + 1, :k_done],
                W=W[: k_done + 1], y=y, k=k_done)

@@ -249,3 +249,37 @@ def test_lcurve_corner_is_the_curvature_maximum(k):
     dense = s[0] * np.logspace(-8, 0, 20001)
     kmax = max(S.lcurve_curvature(l, s, c) for l in dense)
     assert S.lcurve_curvature(lam, s, c) >= kmax * (1 - 1e-6)
+
+
+@pytest.mark.parametrize("method", ["ab", "ba"])
+def test_dp_stopping_rule_stops_at_first_consistent_residual(method):
+    """Sec. 3.2: the DP stop returns the first iterate whose residual, computed from the
+    iterate with the operators (not from the projected problem), is within tau ||e||."""
+    g, x_true, b, e = _problem("fan", N=16, views=24, seed=3, eta=0.02)
+    A, B = P.operators(g)
+    noise = np.linalg.norm(e) if method == "ab" else np.linalg.norm(B(e))
+    # lambda = 0: the residual falls through the noise level within the 25 steps
+    full = S.hybrid_gmres(method, A, B, b, 25, rule="none", keep_iterates=tuple(range(1, 26)))
+    res = S.hybrid_gmres(method, A, B, b, 25, rule="none", stop_rule="dp", stop_target=1.01 * noise)
+    k = res["k"]
+    assert res["status"] == "stopped" and 1 <= k < 25
+
+    def true_res(x):
+        r = b - A(x)
+        return np.linalg.norm(r if method == "ab" else B(r))
+    assert true_res(res["x"]) <= 1.01 * noise * (1 + 1e-9)
+    if k > 1:
+        assert true_res(full["iterates"][k - 1]) > 1.01 * noise
+    np.testing.assert_allclose(res["x"], full["iterates"][k], rtol=1e-10, atol=1e-12)
+
+
+def test_rns_stopping_rule():
+    g, x_true, b, e = _problem("parallel", N=16, views=20, seed=4, eta=0.01)
+    A, B = P.operators(g)
+    full = S.hybrid_gmres("ab", A, B, b, 30, rule="gcv", true_residual=True)
+    res = S.hybrid_gmres("ab", A, B, b, 30, rule="gcv", stop_rule="rns", stop_tol=1e-3)
+    k = res["k"]
+    tr = full["true_resid"]            # ||b - A x_k|| from the iterates themselves
+    rel_change = [abs(tr[j - 1] - tr[j]) / tr[j - 1] for j in range(1, len(tr))]
+    first = next(j + 2 for j, v in enumerate(rel_change) if v < 1e-3 * (1 + 1e-6))
+    assert k == first
