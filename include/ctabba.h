@@ -113,6 +113,14 @@ typedef enum {
 
 typedef enum { CT_BASIS_F32 = 0, CT_BASIS_BF16 = 1, CT_BASIS_F16 = 2 } ct_basis_dtype;
 
+/* Stopping rules (Sec. 3.2) on rho_k = ||H_k y_k - beta e1|| (= ||b - A x_k|| for AB,
+ * ||B (b - A x_k)|| for BA): the solve returns x_k at the first step k that meets the rule (or
+ * x_K).  DP: rho_k <= tau * noise_norm (the paper prints the inequality reversed);
+ * RNS: |rho_{k-1} - rho_k| < stop_tol * rho_{k-1}, k >= 2.  The rule is checked on the device
+ * every stop_every steps, so up to stop_every - 1 steps beyond the stopping step are computed
+ * (and discarded); once it fires, the remaining launches of the solve return at once. */
+typedef enum { CT_STOP_NONE = 0, CT_STOP_DP = 1, CT_STOP_RNS = 2 } ct_stop_rule;
+
 typedef struct {
     int max_iters;           /* K >= 1                                                     */
     ct_lambda_rule rule;
@@ -127,10 +135,13 @@ typedef struct {
                                     parameters (device; read during the solve)              */
     float *features_dev;     /* device, max_iters x CT_MLP_NIN floats, may be NULL: row k-1
                                 receives the features of H_k (any rule but CT_LAMBDA_NONE)  */
+    ct_stop_rule stop_rule;  /* CT_STOP_NONE (default): exactly max_iters steps             */
+    double stop_tol;         /* CT_STOP_RNS tolerance (> 0)                                 */
+    int stop_every;          /* steps between device-side checks of the rule (>= 1)         */
 } ct_hybrid_opts;
 
 typedef struct {
-    int iters_done;          /* k of the returned iterate                                  */
+    int iters_done;          /* k of the returned iterate (the stopping step under a rule)  */
     double beta;             /* ||r0||                                                     */
     double final_lambda;
     double final_resid;      /* ||H_k y_k - beta e1|| (= ||b - A x_k|| for AB)             */
@@ -140,7 +151,8 @@ typedef struct {
     int lambda_fallback_steps; /* CT_LAMBDA_LEARNED: steps where GCV replaced the network   */
 } ct_hybrid_info;
 
-/* Fill `o` with defaults: K = 30, GCV, tau = 1.01, reorth = 1, FP32 basis, no history. */
+/* Fill `o` with defaults: K = 30, GCV, tau = 1.01, reorth = 1, FP32 basis, no history, no
+ * stopping rule (stop_tol = 1e-3, stop_every = 5 for when one is set). */
 void ct_hybrid_opts_default(ct_hybrid_opts *o);
 
 /* Hybrid AB-GMRES, Algorithm 1 (Sec. 3): x0 = B u0 (u0 = 0 when u0_dev is NULL),

@@ -22,6 +22,7 @@ KINDS = {"parallel2d": 0, "fanflat2d": 1, "cone3d": 2}
 RULES = {"none": 0, "fixed": 1, "gcv": 2, "dp": 3, "learned": 4, "lcurve": 5}
 CT_MLP_NIN, CT_MLP_NPARAMS = 80, 9569
 BASIS = {"f32": 0, "bf16": 1, "f16": 2}
+STOPS = {"none": 0, "dp": 1, "rns": 2}
 
 # the entry points of include/ctabba.h
 EXPORTS = ("ct_geom_create", "ct_geom_destroy", "ct_geom_dims", "ct_geom_work", "ct_forward_A", "ct_back_B",
@@ -54,7 +55,9 @@ class HybridOpts(ctypes.Structure):
                 ("tau", ctypes.c_double), ("reorth", ctypes.c_int), ("basis", ctypes.c_int),
                 ("lambda_hist", ctypes.POINTER(ctypes.c_double)),
                 ("resid_hist", ctypes.POINTER(ctypes.c_double)),
-                ("lambda_net_dev", ctypes.c_void_p), ("features_dev", ctypes.c_void_p)]
+                ("lambda_net_dev", ctypes.c_void_p), ("features_dev", ctypes.c_void_p),
+                ("stop_rule", ctypes.c_int), ("stop_tol", ctypes.c_double),
+                ("stop_every", ctypes.c_int)]
 
 
 class PhaseTime(ctypes.Structure):
@@ -209,7 +212,7 @@ def ct_back_B(g: Geom, y, x, stream=None):
 
 
 def _opts(max_iters, rule, lambda_fixed, noise_norm, tau, reorth, basis, history,
-          lambda_net=None, features=None):
+          lambda_net=None, features=None, stop=None, stop_tol=1e-3, stop_every=5):
     o = HybridOpts()
     load().ct_hybrid_opts_default(ctypes.byref(o))
     o.max_iters = int(max_iters)
@@ -219,6 +222,9 @@ def _opts(max_iters, rule, lambda_fixed, noise_norm, tau, reorth, basis, history
     o.tau = float(tau)
     o.reorth = int(reorth)
     o.basis = BASIS[basis] if isinstance(basis, str) else int(basis)
+    o.stop_rule = STOPS[stop] if isinstance(stop, str) else int(stop or 0)
+    o.stop_tol = float(stop_tol)
+    o.stop_every = int(stop_every)
     o.lambda_net_dev = _ptr(lambda_net).value if lambda_net is not None else None
     o.features_dev = _ptr(features).value if features is not None else None
     lam = res = None
@@ -231,9 +237,10 @@ def _opts(max_iters, rule, lambda_fixed, noise_norm, tau, reorth, basis, history
 
 
 def _solve(fn, g, b, x, x0, max_iters, rule, lambda_fixed, noise_norm, tau, reorth, basis,
-           history, stream, lambda_net=None, features=None):
+           history, stream, lambda_net=None, features=None, stop=None, stop_tol=1e-3,
+           stop_every=5):
     o, lam, res = _opts(max_iters, rule, lambda_fixed, noise_norm, tau, reorth, basis, history,
-                        lambda_net, features)
+                        lambda_net, features, stop, stop_tol, stop_every)
     info = HybridInfo()
     st = fn(g.handle, _ptr(b), _ptr(x0), _ptr(x), ctypes.byref(o), ctypes.byref(info),
             _stream(stream))
@@ -246,18 +253,20 @@ def _solve(fn, g, b, x, x0, max_iters, rule, lambda_fixed, noise_norm, tau, reor
 
 def ab_gmres_hybrid(g, b, x, u0=None, max_iters=30, rule="gcv", lambda_fixed=0.0,
                     noise_norm=0.0, tau=1.01, reorth=1, basis="f32", history=True, stream=None,
-                    lambda_net=None, features=None):
+                    lambda_net=None, features=None, stop=None, stop_tol=1e-3, stop_every=5):
     """Hybrid AB-GMRES (Algorithm 1): x <- x0 + B W_K y_K with x0 = B u0."""
     return _solve(load().ab_gmres_hybrid, g, b, x, u0, max_iters, rule, lambda_fixed,
-                  noise_norm, tau, reorth, basis, history, stream, lambda_net, features)
+                  noise_norm, tau, reorth, basis, history, stream, lambda_net, features, stop,
+                  stop_tol, stop_every)
 
 
 def ba_gmres_hybrid(g, b, x, x0=None, max_iters=30, rule="gcv", lambda_fixed=0.0,
                     noise_norm=0.0, tau=1.01, reorth=1, basis="f32", history=True, stream=None,
-                    lambda_net=None, features=None):
+                    lambda_net=None, features=None, stop=None, stop_tol=1e-3, stop_every=5):
     """Hybrid BA-GMRES (Algorithm 2): x <- x0 + W_K y_K."""
     return _solve(load().ba_gmres_hybrid, g, b, x, x0, max_iters, rule, lambda_fixed,
-                  noise_norm, tau, reorth, basis, history, stream, lambda_net, features)
+                  noise_norm, tau, reorth, basis, history, stream, lambda_net, features, stop,
+                  stop_tol, stop_every)
 
 
 def _solve_restarted(fn, g, b, x, cycles, max_iters, rule, lambda_fixed, noise_norm, tau,

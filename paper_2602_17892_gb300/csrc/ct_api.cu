@@ -504,6 +504,9 @@ void ct_hybrid_opts_default(ct_hybrid_opts *o)
     o->tau = 1.01;
     o->reorth = 1;
     o->basis = CT_BASIS_F32;
+    o->stop_rule = CT_STOP_NONE;
+    o->stop_tol = 1e-3;
+    o->stop_every = 5;
 }
 
 }  // extern "C"
@@ -521,6 +524,11 @@ static ct_status check_opts(const ct_hybrid_opts *o)
     if (o->rule == CT_LAMBDA_DP && (!(o->noise_norm >= 0) || !(o->tau > 0)))
         return einval("solver: DP needs noise_norm >= 0 and tau > 0");
     if (o->basis < CT_BASIS_F32 || o->basis > CT_BASIS_F16) return einval("solver: bad basis type");
+    if (o->stop_rule < CT_STOP_NONE || o->stop_rule > CT_STOP_RNS) return einval("solver: bad stop rule");
+    if (o->stop_rule != CT_STOP_NONE && o->stop_every < 1) return einval("solver: stop_every must be >= 1");
+    if (o->stop_rule == CT_STOP_DP && (!(o->noise_norm >= 0) || !(o->tau > 0)))
+        return einval("solver: the DP stop needs noise_norm >= 0 and tau > 0");
+    if (o->stop_rule == CT_STOP_RNS && !(o->stop_tol > 0)) return einval("solver: stop_tol must be > 0");
     return CT_OK;
 }
 
@@ -572,9 +580,52 @@ static ct_status read_info(Workspace *w, const ct_hybrid_opts *o, ct_hybrid_info
 // a fixed iteration count nothing in the Arnoldi chain depends on it.  All K projected problems
 // are therefore solved after the loop in one launch, one CTA per k (the lambda_k history is
 // the same as if each had been solved inside its iteration); y is formed for the final k.
+static SmallSolveParams small_params(Workspace *w, const ct_hybrid_opts *o, double dp_target)
+{
+    SmallSolveParams p;
+    p.H = w->H; p.ldh = w->K + 1; p.k = o->max_iters; p.beta = 0.0; p.betap = w->aux + 2;
+    p.rule = o->rule; p.lambda_fixed = o->lambda_fixed; p.dp_target = dp_target;
+    p.y = w->Y; p.ystride = w->K;
+    p.lambda_out = w->lam;
+    p.resid_out = w->res;
+    p.stop = w->stop;
+    p.kmax = o->max_iters;
+    p.always_y = 0;
+    p.path = w->path;
+    p.net = (o->rule == CT_LAMBDA_LEARNED) ? o->lambda_net_dev : nullptr;
+    p.features = o->features_dev;
+    return p;
+}
+
+// With a stopping rule the hybrid steps run inside the loop, every stop_every steps, for the
+// steps since the last check, followed by the device-side check of the rule; after the loop
+// one launch forms y at the stopping (or last) step.
+static ct_status stop_checkpoint(Workspace *w, const ct_hybrid_opts *o, cudaStream_t s,
+                                 double dp_target, int step, int &checked)
+{
+    if (o->stop_rule == CT_STOP_NONE) return CT_OK;
+    if (step % o->stop_every != 0 && step != o->max_iters) return CT_OK;
+    SmallSolveParams p = small_params(w, o, dp_target);
+    p.kfirst = checked;
+    p.k = step - checked;
+    CT_PHASE(CT_PH_SMALL, 2, s);
+    CT_CUDA(launch_small_solve_batched(p, s));
+    CT_CUDA(launch_stop_check(w->res, checked, step, o->stop_rule, o->tau * o->noise_norm,
+                              o->stop_tol, w->stop, s));
+    checked = step;
+    return CT_OK;
+}
+
 static ct_status run_small_solves(Workspace *w, const ct_hybrid_opts *o, cudaStream_t s,
                                   double dp_target)
 {
+    if (o->stop_rule != CT_STOP_NONE) {            // y of the final step only
+        SmallSolveParams p = small_params(w, o, dp_target);
+        p.only_y = 1;
+        CT_PHASE(CT_PH_SMALL, 1, s);
+        CT_CUDA(launch_small_solve_batched(p, s));
+        return CT_OK;
+    }
     SmallSolveParams p;
     p.H = w->H; p.ldh = w->K + 1; p.k = o->max_iters; p.beta = 0.0; p.betap = w->aux + 2;
     p.rule = o->rule; p.lambda_fixed = o->lambda_fixed; p.dp_target = dp_target;
@@ -625,6 +676,7 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
         }
     }
     const int ldh = w->K + 1;
+    int checked = 0;                 // steps whose hybrid step ran (stopping rules)
     for (int step = 1; step <= K; ++step) {
         const int k = step - 1;
         const float *wk = w->cur ? w->cur : static_cast<float *>(w->W) + (int64_t)k * ld;
@@ -645,6 +697,7 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
             CT_CUDA(arnoldi_step_basis(o->basis, w->W, L, ld, k, w->q, w->H + (int64_t)k * ldh,
                                        sc, w->aux, w->stop, step, o->reorth != 0, w->cur, s));
         }
+        if ((st = stop_checkpoint(w, o, s, dp_target, step, checked)) != CT_OK) return st;
     }
     if ((st = run_small_solves(w, o, s, dp_target)) != CT_OK) return st;        // lines 12-13
     // line 13 at k = K: x = x0 + B W y = B (u0 + W y)
@@ -708,6 +761,7 @@ static ct_status enqueue_ba(ct_geom *g, const float *b_dev, const float *x0_dev,
         CT_CUDA(normalize_first_basis(o->basis, w->vec, L, w->W, sc, w->aux, w->stop, w->cur, s));
     }
     const int ldh = w->K + 1;
+    int checked = 0;                 // steps whose hybrid step ran (stopping rules)
     for (int step = 1; step <= K; ++step) {
         const int k = step - 1;
         const float *wk = w->cur ? w->cur : static_cast<float *>(w->W) + (int64_t)k * ld;
@@ -728,6 +782,7 @@ static ct_status enqueue_ba(ct_geom *g, const float *b_dev, const float *x0_dev,
             CT_CUDA(arnoldi_step_basis(o->basis, w->W, L, ld, k, w->q, w->H + (int64_t)k * ldh,
                                        sc, w->aux, w->stop, step, o->reorth != 0, w->cur, s));
         }
+        if ((st = stop_checkpoint(w, o, s, dp_target, step, checked)) != CT_OK) return st;
     }
     if ((st = run_small_solves(w, o, s, dp_target)) != CT_OK) return st;        // lines 12-13
     // line 13: x = x0 + W y

@@ -151,12 +151,19 @@ struct SmallSolveParams {
                       // lambda_out[b], resid_out[b], path[b]
     const float *net = nullptr;   // CT_LAMBDA_LEARNED: FP32 network parameters (device)
     float *features = nullptr;    // optional: row k - 1 (80 floats) gets the features of H_k
+    int kfirst = 0;   // batched launch: block b solves k = kfirst + b + 1 (outputs indexed k - 1)
+    int only_y = 0;   // batched launch: only the block of the final step (stop[0] when set,
+                      // else kmax) runs, and it forms y
 };
 cudaError_t launch_small_solve(const SmallSolveParams &p, cudaStream_t s);
 // sets the kernel's shared-memory limit on the current device (call before a stream capture)
 cudaError_t small_solve_prepare();
-// all steps k = 1..p.k of one solve in one launch (one CTA per k)
+// steps k = p.kfirst + 1 .. p.kfirst + p.k of one solve in one launch (one CTA per k)
 cudaError_t launch_small_solve_batched(const SmallSolveParams &p, cudaStream_t s);
+// stopping rules (Sec. 3.2) on the residual norms res[k0 .. k1-1] (steps k0+1 .. k1): sets
+// stop[0] = the first step that meets the rule (stop[1] = CT_OK) unless stop[0] is already set
+cudaError_t launch_stop_check(const double *res, int k0, int k1, int rule, double target,
+                              double tol, int *stop, cudaStream_t s);
 size_t small_solve_smem_bytes(int k);
 
 // ----------------------------------------------------------------------------- learned lambda

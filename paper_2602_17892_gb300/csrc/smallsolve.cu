@@ -259,13 +259,13 @@ size_t small_solve_smem_bytes(int k)
 
 __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParams P, int batched)
 {
-    if (batched) {      // block b solves the projected problem of step k = b + 1
-        const int b = blockIdx.x;
-        P.k = b + 1;
-        P.y += (size_t)b * P.ystride;
-        P.lambda_out += b;
-        P.resid_out += b;
-        if (P.path) P.path += b;
+    if (batched) {      // block b solves the projected problem of step k = kfirst + b + 1
+        const int kk = P.kfirst + (int)blockIdx.x + 1;
+        P.k = kk;
+        P.y += (size_t)(kk - 1) * P.ystride;
+        P.lambda_out += kk - 1;
+        P.resid_out += kk - 1;
+        if (P.path) P.path += kk - 1;
     }
     const int k = P.k;
     int stop_now = 0;
@@ -274,7 +274,11 @@ __global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParam
         if (st < 0 || (st > 0 && k > st)) return;
         stop_now = (st == k);
     }
-    const bool need_y = P.always_y || k == P.kmax || stop_now;
+    if (P.only_y) {
+        const int target = (P.stop && P.stop[0] > 0) ? P.stop[0] : P.kmax;
+        if (k != target) return;
+    }
+    const bool need_y = P.always_y || k == P.kmax || stop_now || P.only_y;
     extern __shared__ double sd[];
     const int lda = k + 1;
     double *A = sd;                       // (k+1) x k, column-major
@@ -1043,10 +1047,37 @@ cudaError_t launch_small_solve_batched(const SmallSolveParams &p, cudaStream_t s
 {
     cudaError_t e = set_smem_attr();
     if (e != cudaSuccess) return e;
+    if (p.k < 1) return cudaSuccess;
     // at most one CTA per SM: the FP64 pipe (two lanes per clock per SM on GB300) is the bound,
     // so two projected problems sharing an SM would each run at half speed
-    const size_t smem = std::max(small_solve_smem_bytes(p.k), (size_t)(116 * 1024));
+    const size_t smem = std::max(small_solve_smem_bytes(p.kfirst + p.k), (size_t)(116 * 1024));
     small_solve_kernel<<<p.k, kSSThreads, smem, s>>>(p, 1);
+    return cudaGetLastError();
+}
+
+// rule 1: discrepancy principle, rho_k <= target; rule 2: residual norm stagnation,
+// |rho_{k-1} - rho_k| < tol rho_{k-1} (k >= 2)
+__global__ void stop_check_kernel(const double *__restrict__ res, int k0, int k1, int rule,
+                                  double target, double tol, int *stop)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (stop[0] != 0) return;
+    for (int k = k0 + 1; k <= k1; ++k) {
+        bool hit = false;
+        if (rule == CT_STOP_DP) hit = res[k - 1] <= target;
+        else if (rule == CT_STOP_RNS && k >= 2) hit = fabs(res[k - 2] - res[k - 1]) < tol * res[k - 2];
+        if (hit) {
+            stop[1] = CT_OK;
+            stop[0] = k;
+            return;
+        }
+    }
+}
+
+cudaError_t launch_stop_check(const double *res, int k0, int k1, int rule, double target,
+                              double tol, int *stop, cudaStream_t s)
+{
+    stop_check_kernel<<<1, 32, 0, s>>>(res, k0, k1, rule, target, tol, stop);
     return cudaGetLastError();
 }
 

@@ -264,3 +264,23 @@ def test_restarted_solves_match_oracle(method, rule):
     if rule == "dp":           # a root of a monotone function: fixed to rounding (GCV and the
         lam_o = np.concatenate([h["lambdas"] for h in hist])     # L-curve have flat extrema)
         np.testing.assert_allclose(out["lambdas"], lam_o, rtol=1e-3)
+
+
+@pytest.mark.parametrize("method", ["ab", "ba"])
+@pytest.mark.parametrize("stop,rule", [("dp", "none"), ("dp", "lcurve"), ("rns", "gcv")])
+def test_stopping_rules_match_oracle(method, stop, rule):
+    """Sec. 3.2: the device-side check stops at the same step as the oracle, whatever the
+    check interval, and returns that step's iterate."""
+    g = synth.fanflat2d(45, 60, 70, 150.0, 240.0, ny=38)
+    x_true, b, e = problem(g, 5, 0.02, 77)
+    noise = np.linalg.norm(e) if method == "ab" else np.linalg.norm(OP.back_pixel(g, e))
+    A, B = OP.operators(g)
+    ref = OS.hybrid_gmres(method, A, B, b, 40, rule=rule, dp_target=1.01 * noise,
+                          stop_rule=stop, stop_tol=1e-2, stop_target=1.01 * noise)
+    G = gpu_geom(g)
+    for every in (1, 4):
+        xg, info = _gpu_solve(method, G, b, 40, rule, noise_norm=noise, tau=1.01, stop=stop,
+                              stop_tol=1e-2, stop_every=every)
+        assert info["iters_done"] == ref["k"], (every, info, ref["k"], ref["status"])
+        assert info["status"] == "CT_OK"
+        assert rel(xg, ref["x"]) <= ITER_TOL
