@@ -366,8 +366,8 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     dg.sino_ld = (int)round_up(d->n_det_u + 4, 4);
     dg.sino_view_ld = cone ? (int64_t)(ndv + 3) * dg.sino_ld : dg.sino_ld;
     dg.sino_row0 = cone ? dg.sino_ld : 0;
-    dg.plane_x = cone ? (int64_t)(nz + 2) * dg.col_pairs_ld : 0;
-    dg.plane_y = cone ? (int64_t)(nz + 2) * dg.row_pairs_ld : 0;
+    dg.slice_x = cone ? (int64_t)(d->nx + 2) * dg.col_pairs_ld : 0;
+    dg.slice_y = cone ? (int64_t)(d->ny + 2) * dg.row_pairs_ld : 0;
     dg.tune_a_threads = 256;
     dg.tune_a_views = 1;
     dg.tune_b_rows = cone ? 4 : 8;
@@ -399,8 +399,8 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
         views[v].a = (float)(d->pixel * c / d->pitch_u);
         views[v].b = (float)(d->pixel * s / d->pitch_u);
     }
-    const size_t prow_n = cone ? (size_t)(d->ny + 2) * dg.plane_y : (size_t)d->ny * dg.row_pairs_ld;
-    const size_t pcol_n = cone ? (size_t)(d->nx + 2) * dg.plane_x : (size_t)d->nx * dg.col_pairs_ld;
+    const size_t prow_n = cone ? (size_t)(nz + 2) * dg.slice_y : (size_t)d->ny * dg.row_pairs_ld;
+    const size_t pcol_n = cone ? (size_t)(nz + 2) * dg.slice_x : (size_t)d->nx * dg.col_pairs_ld;
     cudaError_t e = cudaSuccess;
     if (cone) {
         e = dalloc(&g->rays_xy_dev, rays_xy.size());

@@ -16,9 +16,10 @@ namespace ct {
 
 // ---------------------------------------------------------------------------- pair layouts
 // One 32 x 32 tile of pair indices of one z slice (blockIdx.z) per block; a 33 x 33 halo tile
-// of the slice sits in smem.  Pair (r, j) of P_row goes to prow[(r + roff) * rs + z_off(z) + j]
-// and pair (c, i) of P_col to pcol[(c + roff) * cs + z_off(z) + i], z_off(z) = (z + zoff) * zs
-// (2D: roff = zoff = 0; 3D: one zero plane and one zero row of padding, roff = zoff = 1).
+// of the slice sits in smem.  Pair (r, j) of P_row goes to
+// prow[(z + off) * rzs + (r + off) * rs + j] and pair (c, i) of P_col to
+// pcol[(z + off) * czs + (c + off) * cs + i] (2D: off = 0, one slice; 3D: off = 1, a zero
+// slice and a zero row of padding on each side).
 __global__ void __launch_bounds__(256) image_pairs_kernel(
     const float *__restrict__ x, int nx, int ny, float2 *__restrict__ prow, int64_t rs,
     int64_t rzs, float2 *__restrict__ pcol, int64_t cs, int64_t czs, int off, const int *stop)
@@ -56,9 +57,9 @@ cudaError_t launch_image_pairs(const ct_geom *g, const float *x, const int *stop
     const DeviceGeom &d = g->dg;
     dim3 grid((d.nx + 1 + 31) / 32, (d.ny + 1 + 31) / 32, d.nz);
     if (d.kind == CT_CONE3D)
-        image_pairs_kernel<<<grid, 256, 0, s>>>(x, d.nx, d.ny, g->prow_dev, d.plane_y,
-                                                d.row_pairs_ld, g->pcol_dev, d.plane_x,
-                                                d.col_pairs_ld, 1, stop);
+        image_pairs_kernel<<<grid, 256, 0, s>>>(x, d.nx, d.ny, g->prow_dev, d.row_pairs_ld,
+                                                d.slice_y, g->pcol_dev, d.col_pairs_ld,
+                                                d.slice_x, 1, stop);
     else
         image_pairs_kernel<<<grid, 256, 0, s>>>(x, d.nx, d.ny, g->prow_dev, d.row_pairs_ld, 0,
                                                 g->pcol_dev, d.col_pairs_ld, 0, 0, stop);

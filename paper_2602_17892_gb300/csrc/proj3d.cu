@@ -3,11 +3,14 @@
 // flat detector), the 3D form of the unmatched pair of Sec. 2.
 //
 // Data layout in HBM (all FP32; the volume is x[z][y][x]):
-//   P_x[x+1][z+1][y+1] = (x[z][y][x], x[z][y+1][x]) for x in [-1, nx], z in [-1, nz], y in [-1, ny)
-//   P_y[y+1][z+1][x+1] = (x[z][y][x], x[z][y][x+1]) for y in [-1, ny], z in [-1, nz], x in [-1, nx)
-// (zero outside the volume; each plane has (nz + 2) rows of ld pairs).  A Joseph sample is two
-// 8-byte loads (the two rows of its 2 x 2 taps) with no bounds test: rays driven along x read
-// P_x, along y P_y, and the rare rays driven along z read P_y across its planes.
+//   P_x[z+1][x+1][y+1] = (x[z][y][x], x[z][y+1][x]) for z in [-1, nz], x in [-1, nx], y in [-1, ny)
+//   P_y[z+1][y+1][x+1] = (x[z][y][x], x[z][y][x+1]) for z in [-1, nz], y in [-1, ny], x in [-1, nx)
+// (zero outside the volume; rows of ld pairs, one z slice after the other).  A Joseph sample is
+// two 8-byte loads (the two z rows of its 2 x 2 taps) with no bounds test: rays driven along x
+// read P_x, along y P_y, and the rare rays driven along z read P_y (two y rows of one slice).
+// z is the slowest index so that consecutive samples of a ray (one step along x or y) are one
+// row apart in memory: a ray stays within a few pages while it crosses the volume, and a z slab
+// of rows is one contiguous block.
 // The padded sinogram of a cone geometry has, per view, one zero detector row above the
 // detector rows and two below, and 2 zero bins on each side of every row, so B's four taps need
 // no bounds test either (positions are clamped into the zero margins).
@@ -87,8 +90,8 @@ __device__ __forceinline__ Ray3D setup_ray3d(const RayXY &R, int iv, int ndv, do
 // sample belongs to exactly one slab.  Launches after the first of a call add to y.
 __global__ void __launch_bounds__(256) joseph3d_kernel(
     const RayXY *__restrict__ rxy, int ndu, int ndv, double pitch_v, double h,
-    const float2 *__restrict__ px, int64_t psx, int ldx, const float2 *__restrict__ py,
-    int64_t psy, int ldy, int nx, int ny, int nz, float *__restrict__ y, int64_t y_view_ld,
+    const float2 *__restrict__ px, int64_t zsx, int ldx, const float2 *__restrict__ py,
+    int64_t zsy, int ldy, int nx, int ny, int nz, float *__restrict__ y, int64_t y_view_ld,
     int y_ld, int y_off, int iv0, int r_lo, int r_hi, int accumulate, const int *stop)
 {
     if (stop && stop[0] != 0) return;
@@ -112,15 +115,15 @@ __global__ void __launch_bounds__(256) joseph3d_kernel(
             hi = min(hi, (int)ceil(fmax(ta, tb)) + 1);
         }
         const float2 *L = ax ? px : py;
-        const int64_t ps = ax ? psx : psy;
-        const int ld = ax ? ldx : ldy;
+        const int64_t zsl = ax ? zsx : zsy;       // pairs per z slice
+        const int ld = ax ? ldx : ldy;            // pairs per row (one step along the drive)
         const int nb = ax ? ny : nx;
         const float bhi = __int_as_float(__float_as_int((float)nb) - 1);
         const float zhi = __int_as_float(__float_as_int((float)nz) - 1);
         const float bmid = R.bmid, bsl = R.bslope;
         const float zm = (float)q.zmid, zs = (float)q.zslope;
         float tf = (float)lo - tmid;
-        const float2 *plane = L + (int64_t)(lo + 1) * ps;
+        const float2 *line = L + (int64_t)(lo + 1) * ld;
         for (int t = lo; t <= hi; ++t) {
             const float pz = fminf(fmaxf(fmaf(zs, tf, zm), -1.f), zhi);
             const float fz = floorf(pz);
@@ -129,19 +132,19 @@ __global__ void __launch_bounds__(256) joseph3d_kernel(
                 const float pb = fminf(fmaxf(fmaf(bsl, tf, bmid), -1.f), bhi);
                 const float fb = floorf(pb);
                 const float wb = pb - fb, wz = pz - fz;
-                const float2 *row = plane + (int64_t)rz * ld + (int)fb + 1;
-                const float2 p0 = __ldg(row), p1 = __ldg(row + ld);
+                const float2 *row = line + (int64_t)rz * zsl + (int)fb + 1;
+                const float2 p0 = __ldg(row), p1 = __ldg(row + zsl);
                 const float a0 = fmaf(wb, p0.y - p0.x, p0.x);
                 const float a1 = fmaf(wb, p1.y - p1.x, p1.x);
                 acc += fmaf(wz, a1 - a0, a0);
                 any = true;
             }
             tf += 1.f;
-            plane += ps;
+            line += ld;
         }
     } else {
         // driven along z: plane t is in the slab when its padded row t + 1 is; taps from P_y
-        // (pairs along x, plane y + 1, row z + 1)
+        // (pairs along x; slice t + 1, rows y + 1 and y + 2)
         const double zt = 0.5 * (nz - 1);
         const float xhi = __int_as_float(__float_as_int((float)nx) - 1);
         const float yhi = __int_as_float(__float_as_int((float)ny) - 1);
@@ -152,8 +155,8 @@ __global__ void __launch_bounds__(256) joseph3d_kernel(
             const float pyf = fminf(fmaxf((float)(q.ymid + q.ys * tf), -1.f), yhi);
             const float fx = floorf(pxf), fy = floorf(pyf);
             const float wx = pxf - fx, wy = pyf - fy;
-            const float2 *row = py + (int64_t)((int)fy + 1) * psy + (int64_t)(t + 1) * ldy + (int)fx + 1;
-            const float2 p0 = __ldg(row), p1 = __ldg(row + psy);
+            const float2 *row = py + (int64_t)(t + 1) * zsy + (int64_t)((int)fy + 1) * ldy + (int)fx + 1;
+            const float2 p0 = __ldg(row), p1 = __ldg(row + ldy);
             const float a0 = fmaf(wx, p0.y - p0.x, p0.x);
             const float a1 = fmaf(wx, p1.y - p1.x, p1.x);
             acc += fmaf(wy, a1 - a0, a0);
@@ -245,8 +248,8 @@ cudaError_t launch_joseph3d(const ct_geom *g, float *y, int64_t y_view_ld, int y
         }
         dim3 block(256), grid((d.ndu + 255) / 256, d.n_views, iv_hi - iv_lo + 1);
         joseph3d_kernel<<<grid, block, 0, s>>>(d.rays_xy, d.ndu, d.ndv, (double)g->desc.pitch_v,
-                                               h, g->pcol_dev, d.plane_x, d.col_pairs_ld,
-                                               g->prow_dev, d.plane_y, d.row_pairs_ld, d.nx,
+                                               h, g->pcol_dev, d.slice_x, d.col_pairs_ld,
+                                               g->prow_dev, d.slice_y, d.row_pairs_ld, d.nx,
                                                d.ny, d.nz, y, y_view_ld, y_ld, y_off, iv_lo, r_lo,
                                                r_hi, n_slabs > 1 ? 1 : 0, stop);
         cudaError_t e = cudaGetLastError();
