@@ -126,11 +126,12 @@ __global__ void __launch_bounds__(512) joseph2d_kernel(
     const int bins_pb = blockDim.x / vpb;
     const int bin = blockIdx.x * bins_pb + (int)threadIdx.x % bins_pb;
     const int view0 = blockIdx.y * vpb + (int)threadIdx.x / bins_pb;
-    if (bin >= ndu || view0 >= n_views) return;
-    const int64_t ray = (int64_t)view0 * ndu + bin;
+    const bool valid = bin < ndu && view0 < n_views;   // all lanes stay for the warp range
+    const int64_t ray = valid ? (int64_t)view0 * ndu + bin : 0;
     const Ray2D R = rays[ray];
-    const int t_lo = R.packed & 0x7fff;
-    const int t_hi = (R.packed >> 15) & 0x7fff;
+    int t_lo = R.packed & 0x7fff;
+    int t_hi = (R.packed >> 15) & 0x7fff;
+    if (!valid) { t_lo = 1; t_hi = 0; }
     const int axis = (R.packed >> 30) & 1;
     const float2 *base;
     int64_t stride;
@@ -142,21 +143,27 @@ __global__ void __launch_bounds__(512) joseph2d_kernel(
         base = prow; stride = prow_ld; tmid = 0.5f * (float)(ny - 1);
         hiclamp = __int_as_float(__float_as_int((float)nx) - 1);
     }
+    // the warp steps through the union of its lanes' driving ranges together, so that at every
+    // step its lanes read neighbouring pairs of one line (a lane outside its own range idles)
+    const int wlo = __reduce_min_sync(0xffffffffu, t_hi >= t_lo ? t_lo : 0x7fffffff);
+    const int whi = __reduce_max_sync(0xffffffffu, t_hi >= t_lo ? t_hi : -1);
     float acc = 0.f;
-    float tf = (float)t_lo - tmid;
-    const float2 *line = base + (int64_t)t_lo * stride;
+    float tf = (float)wlo - tmid;
+    const float2 *line = base + (int64_t)(wlo <= whi ? wlo : 0) * stride;
 #pragma unroll 4
-    for (int t = t_lo; t <= t_hi; ++t) {
-        float pos = fmaf(R.slope, tf, R.pmid);
-        pos = fminf(fmaxf(pos, -1.f), hiclamp);
-        float fl = floorf(pos);
-        float f = pos - fl;
-        float2 p = __ldg(line + (int)fl + 1);
-        acc += fmaf(f, p.y - p.x, p.x);
+    for (int t = wlo; t <= whi; ++t) {
+        if (t >= t_lo && t <= t_hi) {
+            float pos = fmaf(R.slope, tf, R.pmid);
+            pos = fminf(fmaxf(pos, -1.f), hiclamp);
+            const float fl = floorf(pos);
+            const float f = pos - fl;
+            const float2 p = __ldg(line + (int)fl + 1);
+            acc += fmaf(f, p.y - p.x, p.x);
+        }
         tf += 1.f;
         line += stride;
     }
-    y[(int64_t)view0 * y_ld + y_off + bin] = acc * R.weight;
+    if (valid) y[(int64_t)view0 * y_ld + y_off + bin] = acc * R.weight;
 }
 
 cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, const int *stop,

@@ -96,24 +96,32 @@ __global__ void __launch_bounds__(256) joseph3d_kernel(
 {
     if (stop && stop[0] != 0) return;
     const int iu = blockIdx.x * blockDim.x + threadIdx.x;
-    if (iu >= ndu) return;
+    const bool valid = iu < ndu;          // all lanes stay for the warp-wide plane range
     const int view = blockIdx.y, iv = iv0 + blockIdx.z;
-    const RayXY R = rxy[(int64_t)view * ndu + iu];
+    const RayXY R = rxy[(int64_t)view * ndu + (valid ? iu : 0)];
     const Ray3D q = setup_ray3d(R, iv, ndv, pitch_v, h, nx, ny, nz);
     float acc = 0.f;
     bool any = false;
-    if (q.mode != 2) {
-        const bool ax = q.mode == 0;
-        const float tmid = 0.5f * (float)((ax ? nx : ny) - 1);
-        // planes whose z position can fall in the slab (FP64, one plane of margin each side)
-        int lo = q.lo, hi = q.hi;
-        if (q.zslope != 0.0) {
-            const double r = 1.0 / q.zslope;
-            const double ta = (double)tmid + ((r_lo - 1) - 1.0 - q.zmid) * r;
-            const double tb = (double)tmid + ((r_hi - 1) + 1.0 - q.zmid) * r;
-            lo = max(lo, (int)floor(fmin(ta, tb)) - 1);
-            hi = min(hi, (int)ceil(fmax(ta, tb)) + 1);
-        }
+    // planes of the x/y-driven rays that can fall in the slab (FP64, one plane of margin)
+    int lo = q.lo, hi = q.hi;
+    const bool xy = valid && q.mode != 2;
+    const bool ax = q.mode == 0;
+    const float tmid = 0.5f * (float)((ax ? nx : ny) - 1);
+    if (!xy) {
+        lo = 1;
+        hi = 0;
+    } else if (q.zslope != 0.0) {
+        const double r = 1.0 / q.zslope;
+        const double ta = (double)tmid + ((r_lo - 1) - 1.0 - q.zmid) * r;
+        const double tb = (double)tmid + ((r_hi - 1) + 1.0 - q.zmid) * r;
+        lo = max(lo, (int)floor(fmin(ta, tb)) - 1);
+        hi = min(hi, (int)ceil(fmax(ta, tb)) + 1);
+    }
+    // the warp steps through the union of its lanes' plane ranges together, so that at every
+    // step its lanes read neighbouring pairs of one row (a lane outside its own range idles)
+    const int wlo = __reduce_min_sync(0xffffffffu, hi >= lo ? lo : 0x7fffffff);
+    const int whi = __reduce_max_sync(0xffffffffu, hi >= lo ? hi : -1);
+    if (wlo <= whi) {
         const float2 *L = ax ? px : py;
         const int64_t zsl = ax ? zsx : zsy;       // pairs per z slice
         const int ld = ax ? ldx : ldy;            // pairs per row (one step along the drive)
@@ -122,13 +130,13 @@ __global__ void __launch_bounds__(256) joseph3d_kernel(
         const float zhi = __int_as_float(__float_as_int((float)nz) - 1);
         const float bmid = R.bmid, bsl = R.bslope;
         const float zm = (float)q.zmid, zs = (float)q.zslope;
-        float tf = (float)lo - tmid;
-        const float2 *line = L + (int64_t)(lo + 1) * ld;
-        for (int t = lo; t <= hi; ++t) {
+        float tf = (float)wlo - tmid;
+        const float2 *line = L + (int64_t)(wlo + 1) * ld;
+        for (int t = wlo; t <= whi; ++t) {
             const float pz = fminf(fmaxf(fmaf(zs, tf, zm), -1.f), zhi);
             const float fz = floorf(pz);
             const int rz = (int)fz + 1;
-            if (rz >= r_lo && rz < r_hi) {
+            if (t >= lo && t <= hi && rz >= r_lo && rz < r_hi) {
                 const float pb = fminf(fmaxf(fmaf(bsl, tf, bmid), -1.f), bhi);
                 const float fb = floorf(pb);
                 const float wb = pb - fb, wz = pz - fz;
@@ -142,14 +150,15 @@ __global__ void __launch_bounds__(256) joseph3d_kernel(
             tf += 1.f;
             line += ld;
         }
-    } else {
+    }
+    if (valid && q.mode == 2) {
         // driven along z: plane t is in the slab when its padded row t + 1 is; taps from P_y
         // (pairs along x; slice t + 1, rows y + 1 and y + 2)
         const double zt = 0.5 * (nz - 1);
         const float xhi = __int_as_float(__float_as_int((float)nx) - 1);
         const float yhi = __int_as_float(__float_as_int((float)ny) - 1);
-        const int lo = max(q.lo, r_lo - 1), hi = min(q.hi, r_hi - 2);
-        for (int t = lo; t <= hi; ++t) {
+        const int zlo = max(q.lo, r_lo - 1), zhi2 = min(q.hi, r_hi - 2);
+        for (int t = zlo; t <= zhi2; ++t) {
             const double tf = t - zt;
             const float pxf = fminf(fmaxf((float)(q.xmid + q.xs * tf), -1.f), xhi);
             const float pyf = fminf(fmaxf((float)(q.ymid + q.ys * tf), -1.f), yhi);
@@ -163,6 +172,7 @@ __global__ void __launch_bounds__(256) joseph3d_kernel(
             any = true;
         }
     }
+    if (!valid) return;
     float *out = y + (int64_t)view * y_view_ld + (int64_t)iv * y_ld + y_off + iu;
     if (!accumulate) *out = acc * q.weight;
     else if (any) *out += acc * q.weight;
