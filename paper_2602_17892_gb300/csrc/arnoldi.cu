@@ -214,14 +214,21 @@ __global__ void __launch_bounds__(kThreads) cgs_kernel(CgsArgs a)
     if (!is_last) return;
     __threadfence();
     __shared__ double total_nn;
-    for (int i = tid; i < ncol; i += kThreads) {
+    // column i is summed by warp i % kWarps: lane l adds blocks l, l + 32, ... and the warp's
+    // lanes are then added by a fixed xor tree (a fixed order: reproducible run to run)
+    for (int i = warp; i < ncol; i += kWarps) {
         double s = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) s += ((volatile double *)a.partial)[(int64_t)b * ncol + i];
-        if (i < nvec) {
-            if (MODE == M_DOTS) { a.hcol[i] = s; a.coef_out[i] = s; }
-            if (MODE == M_UPD_DOTS) { a.hcol[i] += s; a.coef_out[i] = s; }
-        } else {
-            total_nn = s;
+        for (int b = lane; b < (int)gridDim.x; b += 32)
+            s += ((volatile double *)a.partial)[(int64_t)b * ncol + i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            if (i < nvec) {
+                if (MODE == M_DOTS) { a.hcol[i] = s; a.coef_out[i] = s; }
+                if (MODE == M_UPD_DOTS) { a.hcol[i] += s; a.coef_out[i] = s; }
+            } else {
+                total_nn = s;
+            }
         }
     }
     __syncthreads();
