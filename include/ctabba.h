@@ -196,13 +196,16 @@ typedef struct {
     int a_views;     /* 2D Joseph A: consecutive views per block (each warp one view)     */
     int a_slab;      /* 3D Joseph A: z-slab thickness (tap rows) of one pass; each pass
                         reads one slab of the volume's pair layouts, so it stays in L2    */
-    int b_rows;      /* 2D pixel-driven B: pixel rows per 32-pixel-wide block             */
+    int b_rows;      /* 2D pixel-driven B: pixel rows per block                           */
+    int b_px;        /* 2D pixel-driven B: pixels per thread (1 or 2, 32 columns apart);
+                        a block is 32 b_px pixels wide                                      */
 } ct_launch_shapes;
 
 /* Time the candidate launch shapes of the projectors on this geometry and keep the fastest for
  * later calls on `g`.  2D: Joseph A with (rays, views) per block in (128, 1), (256, 1),
- * (512, 1), (128, 2), (256, 2), (256, 4), (512, 4), (512, 8); pixel-driven B with blocks of
- * 32 x 4, 32 x 8 or 32 x 16 pixels.  3D: Joseph slab thickness 8, 16, 32 or 64 (the voxel-driven
+ * (512, 1), (128, 2), (256, 2), (256, 4), (512, 4), (512, 8); pixel-driven B with 4, 8 or 16
+ * pixel rows per block and 1 or 2 pixels per thread.  3D: Joseph slab thickness 8, 16, 32 or
+ * 64 (the voxel-driven
  * B has one shape, 32 x 4 columns of 8 voxels).  The shapes change only the order of work, not
  * the arithmetic of a sample.  Geometries of the same kind and sizes reuse an earlier result.
  * Runs a few dozen projector launches on `stream`, synchronises it, and allocates two temporary

@@ -66,7 +66,7 @@ class PhaseTime(ctypes.Structure):
 
 class LaunchShapes(ctypes.Structure):
     _fields_ = [("a_threads", ctypes.c_int), ("a_views", ctypes.c_int), ("a_slab", ctypes.c_int),
-                ("b_rows", ctypes.c_int)]
+                ("b_rows", ctypes.c_int), ("b_px", ctypes.c_int)]
 
 
 class HybridInfo(ctypes.Structure):
@@ -346,7 +346,7 @@ def ct_geom_autotune(g: Geom, stream=None) -> dict:
     sh = LaunchShapes()
     _check(load().ct_geom_autotune(g.handle, _stream(stream), ctypes.byref(sh)))
     return {"a_threads": sh.a_threads, "a_views": sh.a_views, "a_slab": sh.a_slab,
-            "b_rows": sh.b_rows}
+            "b_rows": sh.b_rows, "b_px": sh.b_px}
 
 
 def _info_dict(inf):

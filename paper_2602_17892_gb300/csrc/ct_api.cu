@@ -255,6 +255,31 @@ static Ray2D make_ray(const ct_geom_desc *d, int view, int bin)
     return r;
 }
 
+// Whether every pixel centre projects inside the detector in every view (2D), with half a bin
+// of margin in the padded row: the bin position is an affine (parallel) or projective (fan)
+// function of the pixel position, so its extremes over the image are at the corner pixels.
+static bool pixels_inside_detector(const ct_geom_desc *d)
+{
+    const double cx = 0.5 * (d->nx - 1), cy = 0.5 * (d->ny - 1);
+    const double gam = 0.5 * (d->n_det_u - 1) + 2.0, hi = d->n_det_u + 1.5;
+    for (int v = 0; v < d->n_views; ++v) {
+        const double c = cos(d->angles[v]), sn = sin(d->angles[v]);
+        for (double sx : {-cx, cx})
+            for (double sy : {-cy, cy}) {
+                double fj;
+                if (d->kind == CT_PARALLEL2D) {
+                    fj = d->pixel * (c * sx + sn * sy) / d->pitch_u + gam;
+                } else {
+                    const double pe = sy * c - sx * sn;
+                    const double bb = d->sid / d->pixel - sx * c - sy * sn;
+                    fj = d->sdd / d->pitch_u * pe / bb + gam;
+                }
+                if (!(fj >= 0.5 && fj <= hi)) return false;
+            }
+    }
+    return true;
+}
+
 // In-plane (fan) part of the rays of column iu of a cone view: every ray of the column has the
 // x-y projection of the fan ray through detector column iu, D = P - S unnormalised.
 static RayXY make_ray_xy(const ct_geom_desc *d, int view, int iu)
@@ -371,6 +396,8 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     dg.tune_a_threads = 256;
     dg.tune_a_views = 1;
     dg.tune_b_rows = cone ? 4 : 8;
+    dg.tune_b_px = 1;
+    dg.b_noclamp = cone ? 0 : (pixels_inside_detector(&g->desc) ? 1 : 0);
     dg.tune_a_slab = 16;
 
     std::vector<Ray2D> rays;
@@ -1088,6 +1115,7 @@ static ct_launch_shapes shapes_of(const DeviceGeom &d)
     r.a_views = d.tune_a_views;
     r.a_slab = d.tune_a_slab;
     r.b_rows = d.tune_b_rows;
+    r.b_px = d.tune_b_px;
     return r;
 }
 
@@ -1109,6 +1137,7 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
             dg.tune_a_views = it->second.a_views;
             dg.tune_a_slab = it->second.a_slab;
             dg.tune_b_rows = it->second.b_rows;
+            dg.tune_b_px = it->second.b_px;
             if (out) *out = it->second;
             return CT_OK;
         }
@@ -1150,7 +1179,7 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
     static const int a2[8][2] = {{128, 1}, {256, 1}, {512, 1}, {128, 2},
                                  {256, 2}, {256, 4}, {512, 4}, {512, 8}};
     static const int a3[4] = {8, 16, 32, 64};
-    static const int b2[3] = {4, 8, 16};
+    static const int b2[6][2] = {{4, 1}, {8, 1}, {16, 1}, {4, 2}, {8, 2}, {16, 2}};
     auto fwd = [&]() { return launch_forward_proj(g, y, true, nullptr, s); };
     ct_status st;
     if (cone)
@@ -1158,8 +1187,8 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
     else
         st = time_best(fwd, 8, [&](int c) { dg.tune_a_threads = a2[c][0]; dg.tune_a_views = a2[c][1]; });
     if (st == CT_OK && !cone)
-        st = time_best([&]() { return launch_back_proj(g, y, x, nullptr, s); }, 3,
-                       [&](int c) { dg.tune_b_rows = b2[c]; });
+        st = time_best([&]() { return launch_back_proj(g, y, x, nullptr, s); }, 6,
+                       [&](int c) { dg.tune_b_rows = b2[c][0]; dg.tune_b_px = b2[c][1]; });
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(x);

@@ -181,12 +181,15 @@ cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, con
 }
 
 // ---------------------------------------------------------------------------- pixel-driven B
-// One thread per pixel, blocks of 32 x tune_b_rows pixels, per-view constants staged in shared
-// memory.
+// One thread per PX pixels of a row (columns c, c + 32, ...), blocks of 32 PX x tune_b_rows
+// pixels, per-view constants staged in shared memory.
 // Parallel: bin position fj = a (c - cm) + b (r - rm) + (nd-1)/2, weight h^2/pitch.
 // Fan:      pe = p.e_u, bb = SID - p.(cos, sin) (in units of h), u = SDD pe / bb,
 //           weight h SDD / pitch * sqrt(1 + (pe/bb)^2) / bb  (= h^2 (SDD^2+u^2)/(L pitch SDD)).
-template <bool FAN>
+// The second pixel of a thread is 32 columns on: pe and bb follow by one FMA each.
+// CLAMP = false when every pixel centre of the image projects inside the detector in every
+// view (checked on the host at geometry creation): the bin positions then need no clamp.
+template <bool FAN, bool CLAMP, int PX>
 __global__ void __launch_bounds__(512) pixbp2d_kernel(
     const ViewBP *__restrict__ views, int n_views, const float *__restrict__ ypad, int ld,
     int nd, int nx, int ny, float sid_h, float k_u, float k_w, float w_par,
@@ -200,60 +203,88 @@ __global__ void __launch_bounds__(512) pixbp2d_kernel(
         sview[v] = make_float4(vb.cs, vb.sn, vb.a, vb.b);
     }
     __syncthreads();
-    const int c = blockIdx.x * 32 + threadIdx.x;
+    const int c0 = blockIdx.x * (32 * PX) + threadIdx.x;
     const int r = blockIdx.y * blockDim.y + threadIdx.y;
-    if (c >= nx || r >= ny) return;
-    const float tc = (float)c - 0.5f * (float)(nx - 1);
+    if (c0 >= nx || r >= ny) return;
+    bool valid[PX];
+#pragma unroll
+    for (int p = 0; p < PX; ++p) valid[p] = c0 + 32 * p < nx;
+    const float tc = (float)c0 - 0.5f * (float)(nx - 1);
     const float tr = (float)r - 0.5f * (float)(ny - 1);
     const float gam = 0.5f * (float)(nd - 1) + 2.f;   // +2: padded row offset
     const float hi = (float)(nd + 2);
-    float acc = 0.f;
+    float acc[PX];
+#pragma unroll
+    for (int p = 0; p < PX; ++p) acc[p] = 0.f;
     const float *row = ypad;
 #pragma unroll 4
     for (int v = 0; v < n_views; ++v, row += ld) {
-        float4 V = sview[v];
-        float fj, w;
+        const float4 V = sview[v];
+        float pe = 0.f, bb = 0.f;
         if (FAN) {
-            float pe = fmaf(tr, V.x, -tc * V.y);
-            float bb = fmaf(-tc, V.x, fmaf(-tr, V.y, sid_h));
-            float rb = __fdividef(1.f, bb);
-            float t1 = pe * rb;
-            fj = fmaf(t1, k_u, gam);
-            float q = fmaf(t1, t1, 1.f);
-            w = rb * (q * rsqrtf(q));
-        } else {
-            fj = fmaf(V.z, tc, fmaf(V.w, tr, gam));
-            w = 1.f;
+            pe = fmaf(tr, V.x, -tc * V.y);
+            bb = fmaf(-tc, V.x, fmaf(-tr, V.y, sid_h));
         }
-        fj = fminf(fmaxf(fj, 0.f), hi);
-        float fl = floorf(fj);
-        float f = fj - fl;
-        int j = (int)fl;
-        float a = __ldg(row + j), b = __ldg(row + j + 1);
-        acc = fmaf(w, fmaf(f, b - a, a), acc);
+#pragma unroll
+        for (int p = 0; p < PX; ++p) {
+            float fj, w;
+            if (FAN) {
+                const float pep = p ? fmaf(-32.f * p, V.y, pe) : pe;
+                const float bbp = p ? fmaf(-32.f * p, V.x, bb) : bb;
+                const float rb = __fdividef(1.f, bbp);
+                const float t1 = pep * rb;
+                fj = fmaf(t1, k_u, gam);
+                w = rb * sqrtf(fmaf(t1, t1, 1.f));
+            } else {
+                fj = fmaf(V.z, tc + 32.f * p, fmaf(V.w, tr, gam));
+                w = 1.f;
+            }
+            if (CLAMP) fj = fminf(fmaxf(fj, 0.f), hi);
+            const float fl = floorf(fj);
+            const float f = fj - fl;
+            const int j = (int)fl;
+            if (PX == 1 || valid[p]) {
+                const float a = __ldg(row + j), b = __ldg(row + j + 1);
+                acc[p] = fmaf(w, fmaf(f, b - a, a), acc[p]);
+            }
+        }
     }
-    x[(int64_t)r * nx + c] = acc * (FAN ? k_w : w_par);
+#pragma unroll
+    for (int p = 0; p < PX; ++p)
+        if (valid[p]) x[(int64_t)r * nx + c0 + 32 * p] = acc[p] * (FAN ? k_w : w_par);
+}
+
+template <bool FAN, bool CLAMP, int PX>
+static void launch_pixbp2d_t(const ct_geom *g, const float *ypad, float *x, const int *stop,
+                             cudaStream_t s)
+{
+    const DeviceGeom &d = g->dg;
+    const int rows = d.tune_b_rows > 0 ? d.tune_b_rows : 8;
+    dim3 block(32, rows), grid((d.nx + 32 * PX - 1) / (32 * PX), (d.ny + rows - 1) / rows);
+    const size_t smem = sizeof(float4) * (size_t)d.n_views;
+    const float sid_h = d.sid / d.h, k_u = d.sdd / d.pitch_u, k_w = d.h * d.sdd / d.pitch_u;
+    const float w_par = d.h * d.h / d.pitch_u;
+    pixbp2d_kernel<FAN, CLAMP, PX><<<grid, block, smem, s>>>(d.views, d.n_views, ypad, d.sino_ld,
+                                                             d.ndu, d.nx, d.ny, sid_h, k_u, k_w,
+                                                             w_par, x, stop);
 }
 
 cudaError_t launch_pixbp2d(const ct_geom *g, const float *ypad, float *x, const int *stop,
                            cudaStream_t s)
 {
     const DeviceGeom &d = g->dg;
-    const int rows = d.tune_b_rows > 0 ? d.tune_b_rows : 8;
-    dim3 block(32, rows), grid((d.nx + 31) / 32, (d.ny + rows - 1) / rows);
-    size_t smem = sizeof(float4) * (size_t)d.n_views;
-    float sid_h = d.sid / d.h;
-    float k_u = d.sdd / d.pitch_u;
-    float k_w = d.h * d.sdd / d.pitch_u;
-    float w_par = d.h * d.h / d.pitch_u;
-    if (d.kind == CT_FANFLAT2D)
-        pixbp2d_kernel<true><<<grid, block, smem, s>>>(d.views, d.n_views, ypad, d.sino_ld,
-                                                        d.ndu, d.nx, d.ny, sid_h, k_u, k_w,
-                                                        w_par, x, stop);
-    else
-        pixbp2d_kernel<false><<<grid, block, smem, s>>>(d.views, d.n_views, ypad, d.sino_ld,
-                                                         d.ndu, d.nx, d.ny, sid_h, k_u, k_w,
-                                                         w_par, x, stop);
+    const bool fan = d.kind == CT_FANFLAT2D, clamp = !d.b_noclamp, two = d.tune_b_px == 2;
+    if (fan) {
+        if (clamp) two ? launch_pixbp2d_t<true, true, 2>(g, ypad, x, stop, s)
+                       : launch_pixbp2d_t<true, true, 1>(g, ypad, x, stop, s);
+        else two ? launch_pixbp2d_t<true, false, 2>(g, ypad, x, stop, s)
+                 : launch_pixbp2d_t<true, false, 1>(g, ypad, x, stop, s);
+    } else {
+        if (clamp) two ? launch_pixbp2d_t<false, true, 2>(g, ypad, x, stop, s)
+                       : launch_pixbp2d_t<false, true, 1>(g, ypad, x, stop, s);
+        else two ? launch_pixbp2d_t<false, false, 2>(g, ypad, x, stop, s)
+                 : launch_pixbp2d_t<false, false, 1>(g, ypad, x, stop, s);
+    }
     return cudaGetLastError();
 }
 
