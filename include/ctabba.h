@@ -204,8 +204,8 @@ typedef struct {
 /* Time the candidate launch shapes of the projectors on this geometry and keep the fastest for
  * later calls on `g`.  2D: Joseph A with (rays, views) per block in (128, 1), (256, 1),
  * (512, 1), (128, 2), (256, 2), (256, 4), (512, 4), (512, 8); pixel-driven B with 4, 8 or 16
- * pixel rows per block and 1 or 2 pixels per thread.  3D: Joseph slab thickness 8, 16, 32 or
- * 64 (the voxel-driven
+ * pixel rows per block and 1 or 2 pixels per thread.  3D: Joseph slab thickness 8, 16, 32,
+ * 64 or the whole volume in one pass (the voxel-driven
  * B has one shape, 32 x 4 columns of 8 voxels).  The shapes change only the order of work, not
  * the arithmetic of a sample.  Geometries of the same kind and sizes reuse an earlier result.
  * Runs a few dozen projector launches on `stream`, synchronises it, and allocates two temporary

@@ -1178,12 +1178,12 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
     // 2D B: pixel rows per 32-wide block (the 3D backprojector has one shape)
     static const int a2[8][2] = {{128, 1}, {256, 1}, {512, 1}, {128, 2},
                                  {256, 2}, {256, 4}, {512, 4}, {512, 8}};
-    static const int a3[4] = {8, 16, 32, 64};
+    static const int a3[5] = {8, 16, 32, 64, 1 << 20};   // the last one: a single pass
     static const int b2[6][2] = {{4, 1}, {8, 1}, {16, 1}, {4, 2}, {8, 2}, {16, 2}};
     auto fwd = [&]() { return launch_forward_proj(g, y, true, nullptr, s); };
     ct_status st;
     if (cone)
-        st = time_best(fwd, 4, [&](int c) { dg.tune_a_slab = a3[c]; });
+        st = time_best(fwd, 5, [&](int c) { dg.tune_a_slab = a3[c]; });
     else
         st = time_best(fwd, 8, [&](int c) { dg.tune_a_threads = a2[c][0]; dg.tune_a_views = a2[c][1]; });
     if (st == CT_OK && !cone)

@@ -125,7 +125,7 @@ def test_autotuned_slab_thickness_keeps_the_result():
     G = gpu_geom(g)
     y_default = gpu_A(G, x)
     sh = ct_geom_autotune(G)
-    assert sh["a_slab"] in (8, 16, 32, 64)
+    assert sh["a_slab"] in (8, 16, 32, 64, 1 << 20)
     y_tuned = gpu_A(G, x)
     assert rel(y_tuned, y_default) <= 1e-6
     assert rel(y_tuned, OP.forward(g, x).reshape(-1)) <= TOL
