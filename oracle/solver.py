@@ -119,11 +119,13 @@ def lcurve_curvature(lam: float, s: np.ndarray, c: np.ndarray) -> float:
                 / (|eta'| (lam^4 eta^2 + rho^2)^(3/2))."""
     k = len(s)
     pos = s > 0
-    f = s * s / (s * s + lam * lam)
+    d = s * s + lam * lam
+    f = s * s / d
+    g = lam * lam / d                      # 1 - f without cancellation at small lambda
     ci = c[:k]
     eta = float(np.sum((f[pos] * ci[pos] / s[pos]) ** 2))
-    rho = float(np.sum(((1.0 - f) * ci) ** 2) + np.sum(c[k:] ** 2))
-    deta = float(-4.0 / lam * np.sum((1.0 - f[pos]) * f[pos] ** 2 * (ci[pos] / s[pos]) ** 2))
+    rho = float(np.sum((g * ci) ** 2) + np.sum(c[k:] ** 2))
+    deta = float(-4.0 / lam * np.sum(g[pos] * f[pos] ** 2 * (ci[pos] / s[pos]) ** 2))
     if eta == 0.0 or rho == 0.0 or deta == 0.0:
         return 0.0
     num = lam * lam * deta * rho + 2.0 * lam * eta * rho + lam ** 4 * eta * deta
