@@ -123,6 +123,7 @@ struct Workspace {
     float *q = nullptr;     // L
     float *img = nullptr;   // image scratch, img_ld floats
     float *sino = nullptr;  // padded sinogram scratch
+    float *sino2 = nullptr; // second padded sinogram (BA with an initial guess; on first use)
     float *vec = nullptr;   // L (initial residual)
     double *H = nullptr, *Y = nullptr, *lam = nullptr, *res = nullptr, *aux = nullptr;
     double *partial = nullptr;
@@ -134,6 +135,7 @@ static void ws_free(Workspace *w)
 {
     if (!w) return;
     cudaFree(w->W); cudaFree(w->cur); cudaFree(w->q); cudaFree(w->img); cudaFree(w->sino); cudaFree(w->vec);
+    cudaFree(w->sino2);
     cudaFree(w->H); cudaFree(w->Y); cudaFree(w->lam); cudaFree(w->res); cudaFree(w->aux);
     cudaFree(w->partial); cudaFree(w->counter); cudaFree(w->stop); cudaFree(w->path);
     delete w;
@@ -776,12 +778,19 @@ static ct_status enqueue_ba(ct_geom *g, const float *b_dev, const float *x0_dev,
         CT_PHASE(CT_PH_OTHER, x0_dev ? 7 : 4, s);
         CT_CUDA(launch_pad_sino(g, b_dev, w->sino, s));
         if (x0_dev) {
+            if (!w->sino2) {            // b - A x0 needs a second sinogram (q is image-sized)
+                cudaError_t e = dalloc(&w->sino2, (size_t)msino);
+                if (e != cudaSuccess) {
+                    set_error(std::string("workspace allocation: ") + cudaGetErrorString(e));
+                    return CT_ENOMEM;
+                }
+            }
             CT_CUDA(cudaMemsetAsync(w->img, 0, sizeof(float) * L, s));
             CT_CUDA(cudaMemcpyAsync(w->img, x0_dev, sizeof(float) * g->n, cudaMemcpyDeviceToDevice, s));
             CT_CUDA(launch_image_pairs(g, w->img, nullptr, s));
-            CT_CUDA(launch_forward_proj(g, w->q, true, nullptr, s));   // q as sinogram scratch
-            CT_CUDA(launch_rsub(w->sino, w->q, msino, kMaxBlocks, s));
-            CT_CUDA(launch_back_proj(g, w->q, w->vec, nullptr, s));
+            CT_CUDA(launch_forward_proj(g, w->sino2, true, nullptr, s));      // A x0
+            CT_CUDA(launch_rsub(w->sino, w->sino2, msino, kMaxBlocks, s));    // b - A x0
+            CT_CUDA(launch_back_proj(g, w->sino2, w->vec, nullptr, s));
         } else {
             CT_CUDA(launch_back_proj(g, w->sino, w->vec, nullptr, s));
         }

@@ -257,7 +257,7 @@ size_t small_solve_smem_bytes(int k)
     return nd * sizeof(double);
 }
 
-__global__ void __launch_bounds__(kSSThreads) small_solve_kernel(SmallSolveParams P, int batched)
+__global__ void __launch_bounds__(kSSThreads, 1) small_solve_kernel(SmallSolveParams P, int batched)
 {
     if (batched) {      // block b solves the projected problem of step k = kfirst + b + 1
         const int kk = P.kfirst + (int)blockIdx.x + 1;
