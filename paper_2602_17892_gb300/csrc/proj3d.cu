@@ -3,11 +3,14 @@
 // flat detector), the 3D form of the unmatched pair of Sec. 2.
 //
 // Data layout in HBM (all FP32; the volume is x[z][y][x]):
-//   P_x[z+1][x+1][y+1] = (x[z][y][x], x[z][y+1][x]) for z in [-1, nz], x in [-1, nx], y in [-1, ny)
-//   P_y[z+1][y+1][x+1] = (x[z][y][x], x[z][y][x+1]) for z in [-1, nz], y in [-1, ny], x in [-1, nx)
-// (zero outside the volume; rows of ld pairs, one z slice after the other).  A Joseph sample is
-// two 8-byte loads (the two z rows of its 2 x 2 taps) with no bounds test: rays driven along x
-// read P_x, along y P_y, and the rare rays driven along z read P_y (two y rows of one slice).
+//   P_x[z+1][x+1][y+1] = (x[z][y][x], x[z][y+1][x]) for z in [-1, nz+1], x in [-1, nx+1], y in [-1, ny]
+//   P_y[z+1][y+1][x+1] = (x[z][y][x], x[z][y][x+1]) for z in [-1, nz+1], y in [-1, ny+1], x in [-1, nx]
+// (zero outside the volume; rows of ld >= n + 2 pairs, one z slice after the other).  A
+// Joseph sample is two 8-byte loads (the two z rows of its 2 x 2 taps) with no bounds test:
+// rays driven along x read P_x, along y P_y, and the rare rays driven along z read P_y (two y
+// rows of one slice).  Tap positions are clamped to [-1, n]: a sample outside the volume then
+// reads only zero padding and adds exactly zero, so a ray's plane range only has to contain
+// its samples inside the volume (it is computed in FP32 with a margin).
 // z is the slowest index so that consecutive samples of a ray (one step along x or y) are one
 // row apart in memory: a ray stays within a few pages while it crosses the volume, and a z slab
 // of rows is one contiguous block.
@@ -99,23 +102,29 @@ __global__ void __launch_bounds__(256) joseph3d_kernel(
     const bool valid = iu < ndu;          // all lanes stay for the warp-wide plane range
     const int view = blockIdx.y, iv = iv0 + blockIdx.z;
     const RayXY R = rxy[(int64_t)view * ndu + (valid ? iu : 0)];
-    const Ray3D q = setup_ray3d(R, iv, ndv, pitch_v, h, nx, ny, nz);
+    const double v = (iv - 0.5 * (ndv - 1)) * pitch_v;
+    const bool zdrive = fabs(v) * fabs(R.rda) > 1.0;      // |v| > |Da|: driven along z
+    const int mode = zdrive ? 2 : (int)((R.packed >> 30) & 3);
+    const bool ax = mode == 0;
+    const int n_drive = ax ? nx : ny;
+    const float tmid = 0.5f * (float)(n_drive - 1);
+    // z of the samples: z(t) = zmid + zslope (t - tmid), zslope = v / Da (FP64, two operations)
+    const double zsl_d = v * R.rda;
+    const float zs = (float)zsl_d, zm = (float)(0.5 * (nz - 1) - R.sa_h * zsl_d);
     float acc = 0.f;
     bool any = false;
-    // planes of the x/y-driven rays that can fall in the slab (FP64, one plane of margin)
-    int lo = q.lo, hi = q.hi;
-    const bool xy = valid && q.mode != 2;
-    const bool ax = q.mode == 0;
-    const float tmid = 0.5f * (float)((ax ? nx : ny) - 1);
-    if (!xy) {
+    int lo = R.packed & 0x7fff, hi = (R.packed >> 15) & 0x7fff;
+    if (!valid || zdrive) {
         lo = 1;
         hi = 0;
-    } else if (q.zslope != 0.0) {
-        const double r = 1.0 / q.zslope;
-        const double ta = (double)tmid + ((r_lo - 1) - 1.0 - q.zmid) * r;
-        const double tb = (double)tmid + ((r_hi - 1) + 1.0 - q.zmid) * r;
-        lo = max(lo, (int)floor(fmin(ta, tb)) - 1);
-        hi = min(hi, (int)ceil(fmax(ta, tb)) + 1);
+    } else if (fabsf(zs) > 1e-20f) {
+        // planes whose z can fall in [r_lo - 2, r_hi] (the slab's tap rows, FP32, two planes of
+        // margin); samples outside the volume add zero, so a superset is enough
+        const float r = __frcp_rn(zs);
+        const float ta = tmid + ((float)(r_lo - 2) - zm) * r;
+        const float tb = tmid + ((float)r_hi - zm) * r;
+        lo = max(lo, (int)floorf(fminf(ta, tb)) - 2);
+        hi = min(hi, (int)ceilf(fmaxf(ta, tb)) + 2);
     }
     // the warp steps through the union of its lanes' plane ranges together, so that at every
     // step its lanes read neighbouring pairs of one row (a lane outside its own range idles)
@@ -125,11 +134,8 @@ __global__ void __launch_bounds__(256) joseph3d_kernel(
         const float2 *L = ax ? px : py;
         const int64_t zsl = ax ? zsx : zsy;       // pairs per z slice
         const int ld = ax ? ldx : ldy;            // pairs per row (one step along the drive)
-        const int nb = ax ? ny : nx;
-        const float bhi = __int_as_float(__float_as_int((float)nb) - 1);
-        const float zhi = __int_as_float(__float_as_int((float)nz) - 1);
+        const float bhi = (float)(ax ? ny : nx), zhi = (float)nz;
         const float bmid = R.bmid, bsl = R.bslope;
-        const float zm = (float)q.zmid, zs = (float)q.zslope;
         float tf = (float)wlo - tmid;
         const float2 *line = L + (int64_t)(wlo + 1) * ld;
         for (int t = wlo; t <= whi; ++t) {
@@ -151,12 +157,15 @@ __global__ void __launch_bounds__(256) joseph3d_kernel(
             line += ld;
         }
     }
-    if (valid && q.mode == 2) {
-        // driven along z: plane t is in the slab when its padded row t + 1 is; taps from P_y
-        // (pairs along x; slice t + 1, rows y + 1 and y + 2)
+    float weight = (float)h * sqrtf(R.dxy2 + zs * zs);                  // h |D| / |Da|
+    if (valid && zdrive) {
+        // driven along z (FP64 per sample; rare): plane t meets the ray at
+        // x = S_x/h + (nx-1)/2 + (t - (nz-1)/2) D_x / v, likewise y; taps from P_y (pairs
+        // along x; slice t + 1, rows y + 1 and y + 2); plane t is in the slab when t + 1 is
+        const Ray3D q = setup_ray3d(R, iv, ndv, pitch_v, h, nx, ny, nz);
+        weight = q.weight;
         const double zt = 0.5 * (nz - 1);
-        const float xhi = __int_as_float(__float_as_int((float)nx) - 1);
-        const float yhi = __int_as_float(__float_as_int((float)ny) - 1);
+        const float xhi = (float)nx, yhi = (float)ny;
         const int zlo = max(q.lo, r_lo - 1), zhi2 = min(q.hi, r_hi - 2);
         for (int t = zlo; t <= zhi2; ++t) {
             const double tf = t - zt;
@@ -174,8 +183,8 @@ __global__ void __launch_bounds__(256) joseph3d_kernel(
     }
     if (!valid) return;
     float *out = y + (int64_t)view * y_view_ld + (int64_t)iv * y_ld + y_off + iu;
-    if (!accumulate) *out = acc * q.weight;
-    else if (any) *out += acc * q.weight;
+    if (!accumulate) *out = acc * weight;
+    else if (any) *out += acc * weight;
 }
 
 // Total number of Joseph samples of the geometry (sum of the clipped plane ranges), for the
