@@ -186,7 +186,8 @@ cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, con
 // Parallel: bin position fj = a (c - cm) + b (r - rm) + (nd-1)/2, weight h^2/pitch.
 // Fan:      pe = p.e_u, bb = SID - p.(cos, sin) (in units of h), u = SDD pe / bb,
 //           weight h SDD / pitch * sqrt(1 + (pe/bb)^2) / bb  (= h^2 (SDD^2+u^2)/(L pitch SDD)).
-// The second pixel of a thread is 32 columns on: pe and bb follow by one FMA each.
+// Each pixel's terms are formed exactly as with one pixel per thread, so the launch shape never
+// changes a result.
 // CLAMP = false when every pixel centre of the image projects inside the detector in every
 // view (checked on the host at geometry creation): the bin positions then need no clamp.
 template <bool FAN, bool CLAMP, int PX>
@@ -220,23 +221,19 @@ __global__ void __launch_bounds__(512) pixbp2d_kernel(
 #pragma unroll 4
     for (int v = 0; v < n_views; ++v, row += ld) {
         const float4 V = sview[v];
-        float pe = 0.f, bb = 0.f;
-        if (FAN) {
-            pe = fmaf(tr, V.x, -tc * V.y);
-            bb = fmaf(-tc, V.x, fmaf(-tr, V.y, sid_h));
-        }
 #pragma unroll
         for (int p = 0; p < PX; ++p) {
+            const float tcp = tc + 32.f * p;        // exact: integers and half-integers
             float fj, w;
             if (FAN) {
-                const float pep = p ? fmaf(-32.f * p, V.y, pe) : pe;
-                const float bbp = p ? fmaf(-32.f * p, V.x, bb) : bb;
-                const float rb = __fdividef(1.f, bbp);
-                const float t1 = pep * rb;
+                const float pe = fmaf(tr, V.x, -tcp * V.y);
+                const float bb = fmaf(-tcp, V.x, fmaf(-tr, V.y, sid_h));
+                const float rb = __fdividef(1.f, bb);
+                const float t1 = pe * rb;
                 fj = fmaf(t1, k_u, gam);
                 w = rb * sqrtf(fmaf(t1, t1, 1.f));
             } else {
-                fj = fmaf(V.z, tc + 32.f * p, fmaf(V.w, tr, gam));
+                fj = fmaf(V.z, tcp, fmaf(V.w, tr, gam));
                 w = 1.f;
             }
             if (CLAMP) fj = fminf(fmaxf(fj, 0.f), hi);
