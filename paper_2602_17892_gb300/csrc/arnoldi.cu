@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "ct_internal.h"
@@ -276,6 +277,36 @@ static int grid_for(int64_t L4, int max_blocks)
     return (int)b;
 }
 
+// Blocks of the Gram-Schmidt kernels that are resident at once on the device (one wave): a
+// grid larger than that leaves a partial second wave as a tail, so the grid is capped to it and
+// the kernels' element loop takes the rest.  Queried once per device for the largest kernel.
+static int cgs_wave_blocks()
+{
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152 * 2;
+    if (!cached[dev]) {
+        int per_sm = 0, sms = 0;
+        const size_t smem = sizeof(float) * (size_t)(168 + kWarps * 169);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cgs_kernel<M_UPD_DOTS, float>,
+                                                          kThreads, smem) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            per_sm < 1 || sms < 1) {
+            per_sm = 2;
+            sms = 152;
+        }
+        cached[dev] = per_sm * sms;
+    }
+    return cached[dev];
+}
+
+// Caches the one-wave grid of the Gram-Schmidt kernels for the current device (call before a
+// stream capture).
+cudaError_t arnoldi_prepare()
+{
+    return cgs_wave_blocks() > 0 ? cudaSuccess : cudaErrorUnknown;
+}
+
 // One CGS2 Arnoldi step on rows W[0..k] (storage type T) with q = M w_k; writes the H column
 // (FP64, k+2 entries), W[k+1] and, when `cur` is not null, W[k+1] in FP32.  `aux` / `stop` are
 // device scratch words (see CgsArgs).
@@ -286,7 +317,7 @@ static cudaError_t arnoldi_step_t(void *W, int64_t L, int64_t ld, int k, float *
 {
     const int64_t L4 = L / 4;
     const int nvec = k + 1;
-    const int blocks = grid_for(L4, sc.max_blocks);
+    const int blocks = grid_for(L4, std::min(sc.max_blocks, cgs_wave_blocks()));
     double *h1 = aux + 8, *h2 = aux + 8 + (sc.kmax + 2);
     CgsArgs a{W, ld, nvec, q, L4, nullptr, sc.partial, sc.counter, hcol, aux, h1, stop, step};
     size_t smem = sizeof(float) * (size_t)((nvec + 7) / 8 * 8 + kWarps * (nvec + 1));

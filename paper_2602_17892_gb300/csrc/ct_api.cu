@@ -1268,6 +1268,8 @@ extern "C" ct_status ct_batch_create(int n_prob, ct_geom *const *geoms, const in
     bt->method.resize(n_prob);
     bt->ws.assign(n_prob, nullptr);
     cudaError_t e = small_solve_prepare();
+    if (e == cudaSuccess) e = arnoldi_prepare();
+    if (e == cudaSuccess) e = mlp_prepare();
     if (e != cudaSuccess) { ct_batch_destroy(bt); return cuda_fail(e, "ct_batch_create"); }
     for (int i = 0; i < n_prob; ++i) {
         int mth = methods ? methods[i] : 2;

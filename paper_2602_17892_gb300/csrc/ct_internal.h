@@ -136,6 +136,9 @@ struct ArnoldiScratch {
     int kmax;
 };
 
+// caches the Gram-Schmidt kernels' one-wave grid for the current device (before a capture)
+cudaError_t arnoldi_prepare();
+
 // ----------------------------------------------------------------------------- small solve
 constexpr int kMaxSmallK = 160;   // largest projected problem held in shared memory
 struct SmallSolveParams {
