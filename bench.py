@@ -533,6 +533,48 @@ def run_variants(P, torch, G, b_dev, x_true, noise_ab, which):
     return out
 
 
+# ----------------------------------------------------------------------------- projectors only
+def bench_projectors(args):
+    """A and B alone on one workload (fan512, cone256 or cone512): device time per call with
+    CUDA events, GUPS; the command the projector profiles in profiles/ are taken with."""
+    import torch
+    import synth
+    import paper_2602_17892_gb300 as P
+    if args.projectors == "fan512":
+        g = synth.fan512_case()["geom"]
+        x = synth.ellipse_phantom(512, seed=0)
+    else:
+        N = 256 if args.projectors == "cone256" else 512
+        g = synth.cone512_case(N)["geom"]
+        x = synth.ellipsoid_phantom(N, seed=0)
+    G = P.Geom.from_geometry(g)
+    shapes = P.ct_geom_autotune(G) if not args.no_autotune else None
+    xd = torch.from_numpy(x.astype(np.float32).reshape(-1)).cuda()
+    yd = torch.empty(G.m, device="cuda")
+    xb = torch.empty(G.n, device="cuda")
+    for _ in range(args.warmup):
+        P.ct_forward_A(G, xd, yd)
+        P.ct_back_B(G, yd, xb)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record(st)
+    for _ in range(args.steps):
+        P.ct_forward_A(G, xd, yd)
+    ev[1].record(st)
+    for _ in range(args.steps):
+        P.ct_back_B(G, yd, xb)
+    ev[2].record(st)
+    torch.cuda.synchronize()
+    a_ms = ev[0].elapsed_time(ev[1]) / args.steps
+    b_ms = ev[1].elapsed_time(ev[2]) / args.steps
+    print(json.dumps({"projectors": args.projectors, "image": list(g.image_shape), "views": g.n_views,
+                      "detector": [g.n_det_v, g.n_det_u], "launch_shapes": shapes,
+                      "A_ms": a_ms, "B_ms": b_ms, "A_gups": G.a_samples / (a_ms * 1e-3) / 1e9,
+                      "B_gups": G.b_samples / (b_ms * 1e-3) / 1e9, "steps": args.steps,
+                      "warmup": args.warmup}), flush=True)
+
+
 # ----------------------------------------------------------------------------- reference arm
 def bench_reference(args, rank, world):
     """The FP64 CPU oracle on the host cores: each step is a bounded sample of the workload
@@ -582,6 +624,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--projectors", choices=["fan512", "cone256", "cone512"], default=None,
+                    help="time A and B alone on this workload instead of the solver benchmark")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--variants", default="all",
                     help="'all', 'none' or a comma list of: basis_precision_fan512_ab, "
                          "learned_lambda_parallel256, batched_slices_sample, cone512")
@@ -601,6 +646,9 @@ def main():
         t0 = time.time()
         while B.needs_build() and time.time() - t0 < 600:
             time.sleep(1.0)
+    if args.projectors:
+        bench_projectors(args)
+        return
     from oracle import proj as OP
     OP.build_oracle()
     bench_ours(args, rank, world, local_rank)
