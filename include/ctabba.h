@@ -193,7 +193,8 @@ ct_status ba_gmres_hybrid_restarted(ct_geom *g, const float *b_dev, float *x_dev
 /* Launch shapes of the projector kernels of a geometry. */
 typedef struct {
     int a_threads;   /* 2D Joseph A: rays (threads) per block                             */
-    int a_views;     /* 2D Joseph A: consecutive views per block (each warp one view)     */
+    int a_views;     /* Joseph A: 2D, consecutive views per block (each warp one view);
+                        3D, detector rows per block of 32 columns (each warp one row)       */
     int a_slab;      /* 3D Joseph A: z-slab thickness (tap rows) of one pass; each pass
                         reads one slab of the volume's pair layouts, so it stays in L2    */
     int b_rows;      /* 2D pixel-driven B: pixel rows per block                           */
@@ -204,8 +205,9 @@ typedef struct {
 /* Time the candidate launch shapes of the projectors on this geometry and keep the fastest for
  * later calls on `g`.  2D: Joseph A with (rays, views) per block in (128, 1), (256, 1),
  * (512, 1), (128, 2), (256, 2), (256, 4), (512, 4), (512, 8); pixel-driven B with 4, 8 or 16
- * pixel rows per block and 1 or 2 pixels per thread.  3D: Joseph slab thickness 8, 16, 32,
- * 64 or the whole volume in one pass (the voxel-driven
+ * pixel rows per block and 1 or 2 pixels per thread.  3D: Joseph (slab thickness, detector
+ * rows per block) in (16, 1), (16, 4), (16, 8), (64, 4), (64, 8) and one pass over the whole
+ * volume with 1, 4 or 8 rows (the voxel-driven
  * B has one shape, 32 x 4 columns of 8 voxels).  The shapes change only the order of work, not
  * the arithmetic of a sample.  Geometries of the same kind and sizes reuse an earlier result.
  * Runs a few dozen projector launches on `stream`, synchronises it, and allocates two temporary

@@ -397,7 +397,7 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     dg.slice_x = cone ? (int64_t)(d->nx + 3) * dg.col_pairs_ld : 0;
     dg.slice_y = cone ? (int64_t)(d->ny + 3) * dg.row_pairs_ld : 0;
     dg.tune_a_threads = 256;
-    dg.tune_a_views = 1;
+    dg.tune_a_views = cone ? 8 : 1;
     dg.tune_b_rows = cone ? 4 : 8;
     dg.tune_b_px = 1;
     dg.b_noclamp = cone ? 0 : (pixels_inside_detector(&g->desc) ? 1 : 0);
@@ -1188,12 +1188,14 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
     // 2D B: pixel rows per 32-wide block (the 3D backprojector has one shape)
     static const int a2[8][2] = {{128, 1}, {256, 1}, {512, 1}, {128, 2},
                                  {256, 2}, {256, 4}, {512, 4}, {512, 8}};
-    static const int a3[5] = {8, 16, 32, 64, 1 << 20};   // the last one: a single pass
+    // 3D: (z-slab thickness, detector rows per block); 1 << 20 = one pass over the volume
+    static const int a3[8][2] = {{16, 1}, {16, 4}, {16, 8}, {64, 4}, {64, 8},
+                                 {1 << 20, 1}, {1 << 20, 4}, {1 << 20, 8}};
     static const int b2[6][2] = {{4, 1}, {8, 1}, {16, 1}, {4, 2}, {8, 2}, {16, 2}};
     auto fwd = [&]() { return launch_forward_proj(g, y, true, nullptr, s); };
     ct_status st;
     if (cone)
-        st = time_best(fwd, 5, [&](int c) { dg.tune_a_slab = a3[c]; });
+        st = time_best(fwd, 8, [&](int c) { dg.tune_a_slab = a3[c][0]; dg.tune_a_views = a3[c][1]; });
     else
         st = time_best(fwd, 8, [&](int c) { dg.tune_a_threads = a2[c][0]; dg.tune_a_views = a2[c][1]; });
     if (st == CT_OK && !cone)

@@ -95,12 +95,16 @@ __global__ void __launch_bounds__(256) joseph3d_kernel(
     const RayXY *__restrict__ rxy, int ndu, int ndv, double pitch_v, double h,
     const float2 *__restrict__ px, int64_t zsx, int ldx, const float2 *__restrict__ py,
     int64_t zsy, int ldy, int nx, int ny, int nz, float *__restrict__ y, int64_t y_view_ld,
-    int y_ld, int y_off, int iv0, int r_lo, int r_hi, int accumulate, const int *stop)
+    int y_ld, int y_off, int iv0, int iv1, int r_lo, int r_hi, int accumulate, const int *stop)
 {
     if (stop && stop[0] != 0) return;
-    const int iu = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = iu < ndu;          // all lanes stay for the warp-wide plane range
-    const int view = blockIdx.y, iv = iv0 + blockIdx.z;
+    // a block is 32 detector columns x blockDim.y detector rows of one view (a warp is one row):
+    // neighbouring rows cross neighbouring z rows of the pair layouts, which they share in L1
+    const int iu = blockIdx.x * 32 + threadIdx.x;
+    const int view = blockIdx.y;
+    const int iv_raw = iv0 + blockIdx.z * blockDim.y + threadIdx.y;
+    const bool valid = iu < ndu && iv_raw <= iv1;   // all lanes stay for the warp-wide range
+    const int iv = valid ? iv_raw : iv0;
     const RayXY R = rxy[(int64_t)view * ndu + (valid ? iu : 0)];
     const double v = (iv - 0.5 * (ndv - 1)) * pitch_v;
     const bool zdrive = fabs(v) * fabs(R.rda) > 1.0;      // |v| > |Da|: driven along z
@@ -265,12 +269,13 @@ cudaError_t launch_joseph3d(const ct_geom *g, float *y, int64_t y_view_ld, int y
             rows_for_heights(g, (r_lo - 2 - zc) * h, (r_hi - zc) * h, iv_lo, iv_hi);
             if (iv_hi < iv_lo) continue;
         }
-        dim3 block(256), grid((d.ndu + 255) / 256, d.n_views, iv_hi - iv_lo + 1);
+        const int vb = (d.tune_a_views >= 1 && d.tune_a_views <= 8) ? d.tune_a_views : 8;
+        dim3 block(32, vb), grid((d.ndu + 31) / 32, d.n_views, (iv_hi - iv_lo + vb) / vb);
         joseph3d_kernel<<<grid, block, 0, s>>>(d.rays_xy, d.ndu, d.ndv, (double)g->desc.pitch_v,
                                                h, g->pcol_dev, d.slice_x, d.col_pairs_ld,
                                                g->prow_dev, d.slice_y, d.row_pairs_ld, d.nx,
-                                               d.ny, d.nz, y, y_view_ld, y_ld, y_off, iv_lo, r_lo,
-                                               r_hi, n_slabs > 1 ? 1 : 0, stop);
+                                               d.ny, d.nz, y, y_view_ld, y_ld, y_off, iv_lo,
+                                               iv_hi, r_lo, r_hi, n_slabs > 1 ? 1 : 0, stop);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
