@@ -446,6 +446,7 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     if (e == cudaSuccess) e = dalloc(&g->prow_dev, prow_n);
     if (e == cudaSuccess) e = dalloc(&g->pcol_dev, pcol_n);
     if (e == cudaSuccess) e = dalloc(&g->sino_pad_dev, (size_t)d->n_views * dg.sino_view_ld);
+    if (e == cudaSuccess) e = dalloc(&g->sino_pairs_dev, (size_t)d->n_views * dg.sino_view_ld);
     if (e != cudaSuccess) {
         set_error(std::string("ct_geom_create: ") + cudaGetErrorString(e));
         ct_geom_destroy(g);
@@ -479,6 +480,7 @@ void ct_geom_destroy(ct_geom *g)
     cudaFree(g->rays_dev); cudaFree(g->rays_xy_dev); cudaFree(g->views_dev);
     cudaFree(g->prow_dev); cudaFree(g->pcol_dev);
     cudaFree(g->sino_pad_dev);
+    cudaFree(g->sino_pairs_dev);
     delete[] g->angles_host;
     delete g;
 }
@@ -520,7 +522,7 @@ ct_status ct_back_B(ct_geom *g, const float *y_dev, float *x_dev, ct_stream_t st
         CT_PHASE(CT_PH_LAYOUT, 1, s);
         CT_CUDA(launch_pad_sino(g, y_dev, g->sino_pad_dev, s));
     }
-    CT_PHASE(CT_PH_BACK, 1, s);
+    CT_PHASE(CT_PH_BACK, 2, s);
     CT_CUDA(launch_back_proj(g, g->sino_pad_dev, x_dev, nullptr, s));
     return CT_OK;
 }
@@ -711,7 +713,7 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
         const int k = step - 1;
         const float *wk = w->cur ? w->cur : static_cast<float *>(w->W) + (int64_t)k * ld;
         {
-            CT_PHASE(CT_PH_BACK, 1, s);
+            CT_PHASE(CT_PH_BACK, 2, s);
             CT_CUDA(launch_back_proj(g, wk, w->img, w->stop, s));       // line 5: B w_k
         }
         {
@@ -739,7 +741,7 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
                                      kMaxBlocks, s));
     }
     {
-        CT_PHASE(CT_PH_BACK, 1, s);
+        CT_PHASE(CT_PH_BACK, 2, s);
         CT_CUDA(launch_back_proj(g, w->q, x_dev, nullptr, s));
     }
     return CT_OK;
@@ -811,7 +813,7 @@ static ct_status enqueue_ba(ct_geom *g, const float *b_dev, const float *x0_dev,
             CT_CUDA(launch_forward_proj(g, w->sino, true, w->stop, s));
         }
         {
-            CT_PHASE(CT_PH_BACK, 1, s);
+            CT_PHASE(CT_PH_BACK, 2, s);
             CT_CUDA(launch_back_proj(g, w->sino, w->q, w->stop, s));     //          B (A w_k)
         }
         {
@@ -1075,7 +1077,7 @@ extern "C" ct_status ct_lambda_samples(ct_geom *g, const float *b_dev, const flo
                                Z + (int64_t)j * img_ld, nullptr, s));
     CT_CUDA(launch_gram(Z, img_ld, g->n, K, x_true_dev, G, G + (size_t)K * K, s));
     CT_CUDA(launch_lambda_labels(w->H, w->K + 1, w->aux + 2, G, K, G + (size_t)K * K, labels_dev, s));
-    g_launches += K + 2;
+    g_launches += 2 * K + 2;
     CT_CUDA(cudaFreeAsync(Z, s));
     CT_CUDA(cudaFreeAsync(G, s));
     return finish(w, &oo, info, s);

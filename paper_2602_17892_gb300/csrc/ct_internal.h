@@ -92,6 +92,7 @@ struct ct_geom {
     float2 *prow_dev;   // 2D: [ny][row_pairs_ld] pairs along x; 3D: P_y, [nz + 3][ny + 3][row_pairs_ld]
     float2 *pcol_dev;   // 2D: [nx][col_pairs_ld] pairs along y; 3D: P_x, [nz + 3][nx + 3][col_pairs_ld]
     float *sino_pad_dev;  // [n_views][sino_view_ld]
+    float2 *sino_pairs_dev; // [n_views][sino_view_ld] (bin j, bin j + 1) pairs read by B
     // solver workspace (grown on demand)
     struct Workspace *ws;
 };
@@ -110,18 +111,18 @@ cudaError_t launch_pad_sino(const ct_geom *g, const float *y, float *ypad, cudaS
 // [view][v][u] layout.
 cudaError_t launch_forward_proj(const ct_geom *g, float *y, bool padded, const int *stop,
                                 cudaStream_t s);
-// x = B y from a padded sinogram
+// x = B y from a padded sinogram (two launches: the pair layout of y, then B)
 cudaError_t launch_back_proj(const ct_geom *g, const float *ypad, float *x, const int *stop,
                              cudaStream_t s);
 // kind-specific launchers (2D: proj2d.cu, 3D: proj3d.cu); element (view, v, u) of y at
 // view * y_view_ld + v * y_ld + y_off + u
 cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, const int *stop,
                             cudaStream_t s);
-cudaError_t launch_pixbp2d(const ct_geom *g, const float *ypad, float *x, const int *stop,
+cudaError_t launch_pixbp2d(const ct_geom *g, const float2 *ypair, float *x, const int *stop,
                            cudaStream_t s);
 cudaError_t launch_joseph3d(const ct_geom *g, float *y, int64_t y_view_ld, int y_ld, int y_off,
                             const int *stop, cudaStream_t s);
-cudaError_t launch_voxbp3d(const ct_geom *g, const float *ypad, float *x, const int *stop,
+cudaError_t launch_voxbp3d(const ct_geom *g, const float2 *ypair, float *x, const int *stop,
                            cudaStream_t s);
 // kernel launches made by one launch_joseph3d (one per z slab)
 int joseph3d_launches(const ct_geom *g);

@@ -93,6 +93,36 @@ cudaError_t launch_pad_sino(const ct_geom *g, const float *y, float *ypad, cudaS
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------- sinogram pairs
+// pairs[e] = (ypad[e], ypad[e + 1]) over the whole padded sinogram (the element after a row's
+// last one is the next row's first zero margin, or zero at the end): a backprojector tap pair
+// is then one aligned 8-byte load.
+__global__ void sino_pairs_kernel(const float *__restrict__ ypad, int64_t total,
+                                  float2 *__restrict__ pairs, const int *stop)
+{
+    if (stop && stop[0] != 0) return;
+    const int64_t n4 = total / 4;               // total is a multiple of 4 (rows are)
+    const float4 *y4 = reinterpret_cast<const float4 *>(ypad);
+    float4 *p4 = reinterpret_cast<float4 *>(pairs);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n4;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = __ldg(y4 + e);
+        const float nx = (e + 1 < n4) ? __ldg(ypad + 4 * (e + 1)) : 0.f;
+        p4[2 * e] = make_float4(a.x, a.y, a.y, a.z);
+        p4[2 * e + 1] = make_float4(a.z, a.w, a.w, nx);
+    }
+}
+
+static cudaError_t launch_sino_pairs(const ct_geom *g, const float *ypad, const int *stop,
+                                     cudaStream_t s)
+{
+    const DeviceGeom &d = g->dg;
+    const int64_t total = (int64_t)d.n_views * d.sino_view_ld;
+    const int blocks = (int)std::min<int64_t>((total / 4 + 255) / 256, 152 * 8);
+    sino_pairs_kernel<<<blocks, 256, 0, s>>>(ypad, total, g->sino_pairs_dev, stop);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------- dispatch
 cudaError_t launch_forward_proj(const ct_geom *g, float *y, bool padded, const int *stop,
                                 cudaStream_t s)
@@ -108,8 +138,10 @@ cudaError_t launch_forward_proj(const ct_geom *g, float *y, bool padded, const i
 cudaError_t launch_back_proj(const ct_geom *g, const float *ypad, float *x, const int *stop,
                              cudaStream_t s)
 {
-    if (g->dg.kind == CT_CONE3D) return launch_voxbp3d(g, ypad, x, stop, s);
-    return launch_pixbp2d(g, ypad, x, stop, s);
+    cudaError_t e = launch_sino_pairs(g, ypad, stop, s);
+    if (e != cudaSuccess) return e;
+    if (g->dg.kind == CT_CONE3D) return launch_voxbp3d(g, g->sino_pairs_dev, x, stop, s);
+    return launch_pixbp2d(g, g->sino_pairs_dev, x, stop, s);
 }
 
 // ---------------------------------------------------------------------------- Joseph A
@@ -192,7 +224,7 @@ cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, con
 // view (checked on the host at geometry creation): the bin positions then need no clamp.
 template <bool FAN, bool CLAMP, int PX>
 __global__ void __launch_bounds__(512) pixbp2d_kernel(
-    const ViewBP *__restrict__ views, int n_views, const float *__restrict__ ypad, int ld,
+    const ViewBP *__restrict__ views, int n_views, const float2 *__restrict__ ypair, int ld,
     int nd, int nx, int ny, float sid_h, float k_u, float k_w, float w_par,
     float *__restrict__ x, const int *stop)
 {
@@ -217,7 +249,7 @@ __global__ void __launch_bounds__(512) pixbp2d_kernel(
     float acc[PX];
 #pragma unroll
     for (int p = 0; p < PX; ++p) acc[p] = 0.f;
-    const float *row = ypad;
+    const float2 *row = ypair;
 #pragma unroll 4
     for (int v = 0; v < n_views; ++v, row += ld) {
         const float4 V = sview[v];
@@ -241,8 +273,8 @@ __global__ void __launch_bounds__(512) pixbp2d_kernel(
             const float f = fj - fl;
             const int j = (int)fl;
             if (PX == 1 || valid[p]) {
-                const float a = __ldg(row + j), b = __ldg(row + j + 1);
-                acc[p] = fmaf(w, fmaf(f, b - a, a), acc[p]);
+                const float2 ab = __ldg(row + j);          // taps j and j + 1
+                acc[p] = fmaf(w, fmaf(f, ab.y - ab.x, ab.x), acc[p]);
             }
         }
     }
@@ -252,7 +284,7 @@ __global__ void __launch_bounds__(512) pixbp2d_kernel(
 }
 
 template <bool FAN, bool CLAMP, int PX>
-static void launch_pixbp2d_t(const ct_geom *g, const float *ypad, float *x, const int *stop,
+static void launch_pixbp2d_t(const ct_geom *g, const float2 *ypad, float *x, const int *stop,
                              cudaStream_t s)
 {
     const DeviceGeom &d = g->dg;
@@ -266,7 +298,7 @@ static void launch_pixbp2d_t(const ct_geom *g, const float *ypad, float *x, cons
                                                              w_par, x, stop);
 }
 
-cudaError_t launch_pixbp2d(const ct_geom *g, const float *ypad, float *x, const int *stop,
+cudaError_t launch_pixbp2d(const ct_geom *g, const float2 *ypad, float *x, const int *stop,
                            cudaStream_t s)
 {
     const DeviceGeom &d = g->dg;

@@ -300,7 +300,7 @@ int joseph3d_launches(const ct_geom *g)
 constexpr int kZChunk = 8;
 
 __global__ void __launch_bounds__(128) voxbp3d_kernel(
-    const ViewBP *__restrict__ views, int n_views, const float *__restrict__ ypad,
+    const ViewBP *__restrict__ views, int n_views, const float2 *__restrict__ ypad,
     int64_t view_ld, int ld, int ndu, int ndv, int nx, int ny, int nz, float sid_h, float ku,
     float kv, float kw, float *__restrict__ x, const int *stop)
 {
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(128) voxbp3d_kernel(
     float acc[kZChunk];
 #pragma unroll
     for (int j = 0; j < kZChunk; ++j) acc[j] = 0.f;
-    const float *vw = ypad;
+    const float2 *vw = ypad;
     for (int v = 0; v < n_views; ++v, vw += view_ld) {
         const float2 V = sv3[v];
         const float pe = fmaf(tr, V.x, -tc * V.y);
@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(128) voxbp3d_kernel(
         float fu = fminf(fmaxf(fmaf(a, ku, gu), 0.f), uhi);
         const float ful = floorf(fu);
         const float wu = fu - ful;
-        const float *col = vw + (int)ful;
+        const float2 *col = vw + (int)ful;
         const float s2 = fmaf(a, a, 1.f);
         const float rho2 = rho * rho;
 #pragma unroll
@@ -342,11 +342,10 @@ __global__ void __launch_bounds__(128) voxbp3d_kernel(
             float fv = fminf(fmaxf(fmaf(b, kv, gv), 0.f), vhi);
             const float fvl = floorf(fv);
             const float wv = fv - fvl;
-            const float *p = col + (int64_t)(int)fvl * ld;
-            const float t00 = __ldg(p), t01 = __ldg(p + 1);
-            const float t10 = __ldg(p + ld), t11 = __ldg(p + ld + 1);
-            const float r0 = fmaf(wu, t01 - t00, t00);
-            const float r1 = fmaf(wu, t11 - t10, t10);
+            const float2 *p = col + (int64_t)(int)fvl * ld;
+            const float2 t0 = __ldg(p), t1 = __ldg(p + ld);     // (bin u, bin u + 1) of two rows
+            const float r0 = fmaf(wu, t0.y - t0.x, t0.x);
+            const float r1 = fmaf(wu, t1.y - t1.x, t1.x);
             const float q = fmaf(b, b, s2);
             acc[j] = fmaf(rho2 * (q * rsqrtf(q)), fmaf(wv, r1 - r0, r0), acc[j]);
         }
@@ -356,7 +355,7 @@ __global__ void __launch_bounds__(128) voxbp3d_kernel(
         if (z0 + j < nz) x[((int64_t)(z0 + j) * ny + r) * nx + c] = acc[j] * kw;
 }
 
-cudaError_t launch_voxbp3d(const ct_geom *g, const float *ypad, float *x, const int *stop,
+cudaError_t launch_voxbp3d(const ct_geom *g, const float2 *ypad, float *x, const int *stop,
                            cudaStream_t s)
 {
     const DeviceGeom &d = g->dg;
