@@ -157,7 +157,7 @@ struct SmallSolveParams {
                       // lambda_out[b], resid_out[b], path[b]
     const float *net = nullptr;   // CT_LAMBDA_LEARNED: FP32 network parameters (device)
     float *features = nullptr;    // optional: row k - 1 (80 floats) gets the features of H_k
-    int kfirst = 0;   // batched launch: block b solves k = kfirst + b + 1 (outputs indexed k - 1)
+    int kfirst = 0;   // batched launch over k = kfirst + 1 .. kfirst + k (outputs indexed k - 1)
     int only_y = 0;   // batched launch: only the block of the final step (stop[0] when set,
                       // else kmax) runs, and it forms y
 };

@@ -259,8 +259,10 @@ size_t small_solve_smem_bytes(int k)
 
 __global__ void __launch_bounds__(kSSThreads, 1) small_solve_kernel(SmallSolveParams P, int batched)
 {
-    if (batched) {      // block b solves the projected problem of step k = kfirst + b + 1
-        const int kk = P.kfirst + (int)blockIdx.x + 1;
+    if (batched) {
+        // block b solves step k = kfirst + (count - b): the largest problems (longest blocks)
+        // start first, on separate SMs, and the short ones fill in behind them
+        const int kk = P.kfirst + (int)(gridDim.x - blockIdx.x);
         P.k = kk;
         P.y += (size_t)(kk - 1) * P.ystride;
         P.lambda_out += kk - 1;
