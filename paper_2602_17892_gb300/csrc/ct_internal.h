@@ -153,8 +153,8 @@ struct SmallSolveParams {
     int *path = nullptr; // optional: 1 where the parallel path was accepted, 0 where the exact
                       // sequential path ran (indexed by k - 1); + 2 where CT_LAMBDA_LEARNED
                       // fell back to GCV
-    int ystride = 0;  // batched launch: block b solves k = b + 1, y at y + b * ystride,
-                      // lambda_out[b], resid_out[b], path[b]
+    int ystride = 0;  // batched launch: step k has y at y + (k - 1) * ystride,
+                      // lambda_out[k - 1], resid_out[k - 1], path[k - 1]
     const float *net = nullptr;   // CT_LAMBDA_LEARNED: FP32 network parameters (device)
     float *features = nullptr;    // optional: row k - 1 (80 floats) gets the features of H_k
     int kfirst = 0;   // batched launch over k = kfirst + 1 .. kfirst + k (outputs indexed k - 1)
