@@ -394,8 +394,12 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     dg.sino_ld = (int)round_up(d->n_det_u + 4, 4);
     dg.sino_view_ld = cone ? (int64_t)(ndv + 3) * dg.sino_ld : dg.sino_ld;
     dg.sino_row0 = cone ? dg.sino_ld : 0;
-    dg.slice_x = cone ? (int64_t)(d->nx + 3) * dg.col_pairs_ld : 0;
-    dg.slice_y = cone ? (int64_t)(d->ny + 3) * dg.row_pairs_ld : 0;
+    // 3D: both layouts have max(nx, ny) + 3 rows per slice, so that any driving index of any
+    // lane of a warp addresses a row inside either layout (lanes outside their own range still
+    // load, with zero weight)
+    const int nmax = std::max(d->nx, d->ny);
+    dg.slice_x = cone ? (int64_t)(nmax + 3) * dg.col_pairs_ld : 0;
+    dg.slice_y = cone ? (int64_t)(nmax + 3) * dg.row_pairs_ld : 0;
     dg.tune_a_threads = 256;
     dg.tune_a_views = cone ? 8 : 1;
     dg.tune_b_rows = cone ? 4 : 8;

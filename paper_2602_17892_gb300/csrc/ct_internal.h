@@ -69,8 +69,8 @@ struct DeviceGeom {
     int64_t sino_view_ld; // floats per view in the padded sinogram (2D: sino_ld; 3D: (ndv + 2)
                           // rows of sino_ld, detector row 0 at row 1)
     int sino_row0;      // offset of detector row 0 inside a padded view (0 in 2D, sino_ld in 3D)
-    int64_t slice_x;    // 3D: pairs per z slice of P_x ((nx + 3) * col_pairs_ld)
-    int64_t slice_y;    // 3D: pairs per z slice of P_y ((ny + 3) * row_pairs_ld)
+    int64_t slice_x;    // 3D: pairs per z slice of P_x ((max(nx, ny) + 3) * col_pairs_ld)
+    int64_t slice_y;    // 3D: pairs per z slice of P_y ((max(nx, ny) + 3) * row_pairs_ld)
     // tables
     const Ray2D *rays;  // m rays (2D)
     const RayXY *rays_xy; // n_views x ndu (3D)
@@ -89,8 +89,8 @@ struct ct_geom {
     ct::Ray2D *rays_dev;
     ct::RayXY *rays_xy_dev;
     ct::ViewBP *views_dev;
-    float2 *prow_dev;   // 2D: [ny][row_pairs_ld] pairs along x; 3D: P_y, [nz + 3][ny + 3][row_pairs_ld]
-    float2 *pcol_dev;   // 2D: [nx][col_pairs_ld] pairs along y; 3D: P_x, [nz + 3][nx + 3][col_pairs_ld]
+    float2 *prow_dev;   // 2D: [ny][row_pairs_ld] pairs along x; 3D: P_y, [nz + 3][slice_y]
+    float2 *pcol_dev;   // 2D: [nx][col_pairs_ld] pairs along y; 3D: P_x, [nz + 3][slice_x]
     float *sino_pad_dev;  // [n_views][sino_view_ld]
     float2 *sino_pairs_dev; // [n_views][sino_view_ld] (bin j, bin j + 1) pairs read by B
     // solver workspace (grown on demand)

@@ -3,9 +3,10 @@
 // flat detector), the 3D form of the unmatched pair of Sec. 2.
 //
 // Data layout in HBM (all FP32; the volume is x[z][y][x]):
-//   P_x[z+1][x+1][y+1] = (x[z][y][x], x[z][y+1][x]) for z in [-1, nz+1], x in [-1, nx+1], y in [-1, ny]
-//   P_y[z+1][y+1][x+1] = (x[z][y][x], x[z][y][x+1]) for z in [-1, nz+1], y in [-1, ny+1], x in [-1, nx]
-// (zero outside the volume; rows of ld >= n + 2 pairs, one z slice after the other).  A
+//   P_x[z+1][x+1][y+1] = (x[z][y][x], x[z][y+1][x]) for z in [-1, nz+1], x in [-1, M+1], y in [-1, ny]
+//   P_y[z+1][y+1][x+1] = (x[z][y][x], x[z][y][x+1]) for z in [-1, nz+1], y in [-1, M+1], x in [-1, nx]
+// with M = max(nx, ny) (zero outside the volume; rows of ld >= n + 2 pairs, one z slice after
+// the other).  A
 // Joseph sample is two 8-byte loads (the two z rows of its 2 x 2 taps) with no bounds test:
 // rays driven along x read P_x, along y P_y, and the rare rays driven along z read P_y (two y
 // rows of one slice).  Tap positions are clamped to [-1, n]: a sample outside the volume then
@@ -142,21 +143,23 @@ __global__ void __launch_bounds__(256) joseph3d_kernel(
         const float bmid = R.bmid, bsl = R.bslope;
         float tf = (float)wlo - tmid;
         const float2 *line = L + (int64_t)(wlo + 1) * ld;
+        // branch-free body (positions are clamped, so every load is in bounds; a sample outside
+        // the lane's range or the slab is weighted by zero), unrolled so that the loads of
+        // several planes are in flight together
+#pragma unroll 4
         for (int t = wlo; t <= whi; ++t) {
             const float pz = fminf(fmaxf(fmaf(zs, tf, zm), -1.f), zhi);
-            const float fz = floorf(pz);
+            const float pb = fminf(fmaxf(fmaf(bsl, tf, bmid), -1.f), bhi);
+            const float fz = floorf(pz), fb = floorf(pb);
             const int rz = (int)fz + 1;
-            if (t >= lo && t <= hi && rz >= r_lo && rz < r_hi) {
-                const float pb = fminf(fmaxf(fmaf(bsl, tf, bmid), -1.f), bhi);
-                const float fb = floorf(pb);
-                const float wb = pb - fb, wz = pz - fz;
-                const float2 *row = line + (int64_t)rz * zsl + (int)fb + 1;
-                const float2 p0 = __ldg(row), p1 = __ldg(row + zsl);
-                const float a0 = fmaf(wb, p0.y - p0.x, p0.x);
-                const float a1 = fmaf(wb, p1.y - p1.x, p1.x);
-                acc += fmaf(wz, a1 - a0, a0);
-                any = true;
-            }
+            const float wb = pb - fb, wz = pz - fz;
+            const float2 *row = line + (int64_t)rz * zsl + (int)fb + 1;
+            const float2 p0 = __ldg(row), p1 = __ldg(row + zsl);
+            const float a0 = fmaf(wb, p0.y - p0.x, p0.x);
+            const float a1 = fmaf(wb, p1.y - p1.x, p1.x);
+            const bool in = t >= lo && t <= hi && rz >= r_lo && rz < r_hi;
+            acc += in ? fmaf(wz, a1 - a0, a0) : 0.f;
+            any |= in;
             tf += 1.f;
             line += ld;
         }
