@@ -388,9 +388,10 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     dg.h = (float)d->pixel; dg.n_views = d->n_views; dg.ndu = d->n_det_u; dg.ndv = ndv;
     dg.pitch_u = (float)d->pitch_u; dg.pitch_v = (float)g->desc.pitch_v;
     dg.sid = (float)d->sid; dg.sdd = (float)d->sdd;
-    // 3D: one more zero pair per row so that taps clamped to n still read zeros
-    dg.row_pairs_ld = (int)round_up(d->nx + (cone ? 2 : 1), 16);
-    dg.col_pairs_ld = (int)round_up(d->ny + (cone ? 2 : 1), 16);
+    // at least n + 2 pairs per line: pair indices -1 and n + 1 (taps at or beyond the edge)
+    // read zeros
+    dg.row_pairs_ld = (int)round_up(d->nx + 2, 16);
+    dg.col_pairs_ld = (int)round_up(d->ny + 2, 16);
     dg.sino_ld = (int)round_up(d->n_det_u + 4, 4);
     dg.sino_view_ld = cone ? (int64_t)(ndv + 3) * dg.sino_ld : dg.sino_ld;
     dg.sino_row0 = cone ? dg.sino_ld : 0;
@@ -433,8 +434,8 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
         views[v].a = (float)(d->pixel * c / d->pitch_u);
         views[v].b = (float)(d->pixel * s / d->pitch_u);
     }
-    const size_t prow_n = cone ? (size_t)(nz + 3) * dg.slice_y : (size_t)d->ny * dg.row_pairs_ld;
-    const size_t pcol_n = cone ? (size_t)(nz + 3) * dg.slice_x : (size_t)d->nx * dg.col_pairs_ld;
+    const size_t prow_n = cone ? (size_t)(nz + 3) * dg.slice_y : (size_t)(d->ny + 2) * dg.row_pairs_ld;
+    const size_t pcol_n = cone ? (size_t)(nz + 3) * dg.slice_x : (size_t)(d->nx + 2) * dg.col_pairs_ld;
     cudaError_t e = cudaSuccess;
     if (cone) {
         e = dalloc(&g->rays_xy_dev, rays_xy.size());

@@ -18,8 +18,8 @@ namespace ct {
 // One 32 x 32 tile of pair indices of one z slice (blockIdx.z) per block; a 33 x 33 halo tile
 // of the slice sits in smem.  Pair (r, j) of P_row goes to
 // prow[(z + off) * rzs + (r + off) * rs + j] and pair (c, i) of P_col to
-// pcol[(z + off) * czs + (c + off) * cs + i] (2D: off = 0, one slice; 3D: off = 1, a zero
-// slice and a zero row of padding on each side).
+// pcol[(z + off) * czs + (c + off) * cs + i] (off = 1: a zero row of padding on each side,
+// and in 3D a zero slice on each side; 2D has one slice and rzs = czs = 0).
 __global__ void __launch_bounds__(256) image_pairs_kernel(
     const float *__restrict__ x, int nx, int ny, float2 *__restrict__ prow, int64_t rs,
     int64_t rzs, float2 *__restrict__ pcol, int64_t cs, int64_t czs, int off, const int *stop)
@@ -62,7 +62,7 @@ cudaError_t launch_image_pairs(const ct_geom *g, const float *x, const int *stop
                                                 d.slice_x, 1, stop);
     else
         image_pairs_kernel<<<grid, 256, 0, s>>>(x, d.nx, d.ny, g->prow_dev, d.row_pairs_ld, 0,
-                                                g->pcol_dev, d.col_pairs_ld, 0, 0, stop);
+                                                g->pcol_dev, d.col_pairs_ld, 0, 1, stop);
     return cudaGetLastError();
 }
 
@@ -149,51 +149,73 @@ cudaError_t launch_back_proj(const ct_geom *g, const float *ypad, float *x, cons
 // driving axis; the pair at index floor(pos)+1 of line t holds both interpolation taps.
 // A block covers blockDim.x / vpb consecutive bins of vpb consecutive views (each warp one
 // view): the views of a block cross nearly the same pixels, so their warps share L1 lines.
+//
+// floor(pos) and the pair address come from ONE round-down FP32 addition: for K an integer
+// with 2^23 <= K + pos < 2^24 (unit spacing there), s = K + pos rounded towards -infinity is
+// exactly K + floor(pos), s - K and pos - (s - K) are exact, and the bit pattern of s is the
+// integer 0x4B000000 + (s - 2^23).  K also carries the offset of line t from a chunk base
+// (t - t0) * stride, an integer kept exactly in FP32, so the pair address is one multiply-add
+// of that bit pattern; chunks of lines keep (t - t0) * stride below 2^22.
+//
+// No clamp: within a ray's clipped range [t_lo, t_hi] its position lies in [-1, n_other] up
+// to FP32 rounding, so the pair index stays in [-1, n_other + 1], which the layouts hold as
+// zero pairs (a zero line before line 0 and at least n_other + 2 pairs per line); a lane
+// outside its own range skips the load.
+constexpr float kFloor2p23 = 8388608.f;   // 2^23
+constexpr float kFloorK0 = 8388610.f;     // 2^23 + 2: K + pos >= 2^23 for pos >= -2
+constexpr int kFloorSpan = 1 << 22;       // line (or view) offsets per chunk stay below this
+
+// chunk length in lines (or views) of `stride` elements
+static inline int floor_chunk(int64_t stride)
+{
+    return (int)std::max<int64_t>(1, kFloorSpan / std::max<int64_t>(stride, 1));
+}
+
 __global__ void __launch_bounds__(512) joseph2d_kernel(
     const Ray2D *__restrict__ rays, int n_views, int ndu, int vpb,
-    const float2 *__restrict__ prow, int prow_ld, const float2 *__restrict__ pcol, int pcol_ld,
-    int nx, int ny, float *__restrict__ y, int y_ld, int y_off, const int *stop)
+    const float2 *__restrict__ prow, int prow_ld, int prow_chunk, const float2 *__restrict__ pcol,
+    int pcol_ld, int pcol_chunk, int nx, int ny, float *__restrict__ y, int y_ld, int y_off,
+    const int *stop)
 {
     if (stop && stop[0] != 0) return;
     const int bins_pb = blockDim.x / vpb;
     const int bin = blockIdx.x * bins_pb + (int)threadIdx.x % bins_pb;
     const int view0 = blockIdx.y * vpb + (int)threadIdx.x / bins_pb;
     const bool valid = bin < ndu && view0 < n_views;   // all lanes stay for the warp range
-    const int64_t ray = valid ? (int64_t)view0 * ndu + bin : 0;
-    const Ray2D R = rays[ray];
+    const Ray2D R = rays[valid ? (int64_t)view0 * ndu + bin : 0];
     int t_lo = R.packed & 0x7fff;
     int t_hi = (R.packed >> 15) & 0x7fff;
     if (!valid) { t_lo = 1; t_hi = 0; }
     const int axis = (R.packed >> 30) & 1;
-    const float2 *base;
-    int64_t stride;
-    float tmid, hiclamp;
-    if (axis == 0) {        // drive along x: line = column c, taps along rows
-        base = pcol; stride = pcol_ld; tmid = 0.5f * (float)(nx - 1);
-        hiclamp = __int_as_float(__float_as_int((float)ny) - 1);
-    } else {                // drive along y: line = row r, taps along columns
-        base = prow; stride = prow_ld; tmid = 0.5f * (float)(ny - 1);
-        hiclamp = __int_as_float(__float_as_int((float)nx) - 1);
-    }
+    const float2 *base;          // line 0 of the layout the ray reads
+    int stride, chunk, n_drive;
+    if (axis == 0) { base = pcol; stride = pcol_ld; chunk = pcol_chunk; n_drive = nx; }  // along x
+    else { base = prow; stride = prow_ld; chunk = prow_chunk; n_drive = ny; }            // along y
+    const float tmid = 0.5f * (float)(n_drive - 1);
     // the warp steps through the union of its lanes' driving ranges together, so that at every
     // step its lanes read neighbouring pairs of one line (a lane outside its own range idles)
     const int wlo = __reduce_min_sync(0xffffffffu, t_hi >= t_lo ? t_lo : 0x7fffffff);
     const int whi = __reduce_max_sync(0xffffffffu, t_hi >= t_lo ? t_hi : -1);
+    const uint64_t abase = reinterpret_cast<uint64_t>(base) -
+                           8ull * ((uint64_t)__float_as_uint(kFloor2p23) + 1ull);
     float acc = 0.f;
     float tf = (float)wlo - tmid;
-    const float2 *line = base + (int64_t)(wlo <= whi ? wlo : 0) * stride;
+    for (int t0 = wlo; t0 <= whi; t0 += chunk) {
+        const int t1 = min(whi, t0 + chunk - 1);
+        const uint64_t lb = abase + 8ull * (uint64_t)t0 * (uint64_t)stride;
+        float K = kFloorK0;                       // 2^23 + 2 + (t - t0) * stride
 #pragma unroll 4
-    for (int t = wlo; t <= whi; ++t) {
-        if (t >= t_lo && t <= t_hi) {
-            float pos = fmaf(R.slope, tf, R.pmid);
-            pos = fminf(fmaxf(pos, -1.f), hiclamp);
-            const float fl = floorf(pos);
-            const float f = pos - fl;
-            const float2 p = __ldg(line + (int)fl + 1);
-            acc += fmaf(f, p.y - p.x, p.x);
+        for (int t = t0; t <= t1; ++t) {
+            if (t >= t_lo && t <= t_hi) {
+                const float pos = fmaf(R.slope, tf, R.pmid);
+                const float sk = __fadd_rd(pos, K);
+                const float f = pos - (sk - K);
+                const float2 p = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * __float_as_uint(sk)));
+                acc += fmaf(f, p.y - p.x, p.x);
+            }
+            tf += 1.f;
+            K += (float)stride;
         }
-        tf += 1.f;
-        line += stride;
     }
     if (valid) y[(int64_t)view0 * y_ld + y_off + bin] = acc * R.weight;
 }
@@ -206,8 +228,11 @@ cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, con
     const int vpb = (d.tune_a_views > 0 && threads / d.tune_a_views >= 32) ? d.tune_a_views : 1;
     const int bins_pb = threads / vpb;
     dim3 grid((d.ndu + bins_pb - 1) / bins_pb, (d.n_views + vpb - 1) / vpb);
-    joseph2d_kernel<<<grid, threads, 0, s>>>(g->rays_dev, d.n_views, d.ndu, vpb, g->prow_dev,
-                                             d.row_pairs_ld, g->pcol_dev, d.col_pairs_ld, d.nx,
+    // line 0 of each 2D layout follows one zero line
+    const float2 *prow = g->prow_dev + d.row_pairs_ld, *pcol = g->pcol_dev + d.col_pairs_ld;
+    joseph2d_kernel<<<grid, threads, 0, s>>>(g->rays_dev, d.n_views, d.ndu, vpb, prow,
+                                             d.row_pairs_ld, floor_chunk(d.row_pairs_ld), pcol,
+                                             d.col_pairs_ld, floor_chunk(d.col_pairs_ld), d.nx,
                                              d.ny, y, y_ld, y_off, stop);
     return cudaGetLastError();
 }
@@ -225,7 +250,7 @@ cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, con
 template <bool FAN, bool CLAMP, int PX>
 __global__ void __launch_bounds__(512) pixbp2d_kernel(
     const ViewBP *__restrict__ views, int n_views, const float2 *__restrict__ ypair, int ld,
-    int nd, int nx, int ny, float sid_h, float k_u, float k_w, float w_par,
+    int vchunk, int nd, int nx, int ny, float sid_h, float k_u, float k_w, float w_par,
     float *__restrict__ x, const int *stop)
 {
     if (stop && stop[0] != 0) return;
@@ -249,33 +274,41 @@ __global__ void __launch_bounds__(512) pixbp2d_kernel(
     float acc[PX];
 #pragma unroll
     for (int p = 0; p < PX; ++p) acc[p] = 0.f;
-    const float2 *row = ypair;
+    // floor(fj) and the pair address from one round-down addition (as in the Joseph kernel):
+    // K = 2^23 + (v - v0) ld over chunks of views; fj >= 0 in the padded row
+    const uint64_t ybase = reinterpret_cast<uint64_t>(ypair) - 8ull * __float_as_uint(kFloor2p23);
+    for (int v0 = 0; v0 < n_views; v0 += vchunk) {
+        const int v1 = min(n_views, v0 + vchunk);
+        const uint64_t rb = ybase + 8ull * (uint64_t)v0 * (uint64_t)ld;
+        float K = kFloor2p23;
 #pragma unroll 4
-    for (int v = 0; v < n_views; ++v, row += ld) {
-        const float4 V = sview[v];
+        for (int v = v0; v < v1; ++v) {
+            const float4 V = sview[v];
 #pragma unroll
-        for (int p = 0; p < PX; ++p) {
-            const float tcp = tc + 32.f * p;        // exact: integers and half-integers
-            float fj, w;
-            if (FAN) {
-                const float pe = fmaf(tr, V.x, -tcp * V.y);
-                const float bb = fmaf(-tcp, V.x, fmaf(-tr, V.y, sid_h));
-                const float rb = __fdividef(1.f, bb);
-                const float t1 = pe * rb;
-                fj = fmaf(t1, k_u, gam);
-                w = rb * sqrtf(fmaf(t1, t1, 1.f));
-            } else {
-                fj = fmaf(V.z, tcp, fmaf(V.w, tr, gam));
-                w = 1.f;
+            for (int p = 0; p < PX; ++p) {
+                const float tcp = tc + 32.f * p;        // exact: integers and half-integers
+                float fj, w;
+                if (FAN) {
+                    const float pe = fmaf(tr, V.x, -tcp * V.y);
+                    const float bb = fmaf(-tcp, V.x, fmaf(-tr, V.y, sid_h));
+                    const float rbb = __fdividef(1.f, bb);
+                    const float t1 = pe * rbb;
+                    fj = fmaf(t1, k_u, gam);
+                    w = rbb * sqrtf(fmaf(t1, t1, 1.f));
+                } else {
+                    fj = fmaf(V.z, tcp, fmaf(V.w, tr, gam));
+                    w = 1.f;
+                }
+                if (CLAMP) fj = fminf(fmaxf(fj, 0.f), hi);
+                const float sk = __fadd_rd(fj, K);
+                const float f = fj - (sk - K);
+                if (PX == 1 || valid[p]) {
+                    // taps j and j + 1 of view v
+                    const float2 ab = __ldg(reinterpret_cast<const float2 *>(rb + 8ull * __float_as_uint(sk)));
+                    acc[p] = fmaf(w, fmaf(f, ab.y - ab.x, ab.x), acc[p]);
+                }
             }
-            if (CLAMP) fj = fminf(fmaxf(fj, 0.f), hi);
-            const float fl = floorf(fj);
-            const float f = fj - fl;
-            const int j = (int)fl;
-            if (PX == 1 || valid[p]) {
-                const float2 ab = __ldg(row + j);          // taps j and j + 1
-                acc[p] = fmaf(w, fmaf(f, ab.y - ab.x, ab.x), acc[p]);
-            }
+            K += (float)ld;
         }
     }
 #pragma unroll
@@ -294,8 +327,8 @@ static void launch_pixbp2d_t(const ct_geom *g, const float2 *ypad, float *x, con
     const float sid_h = d.sid / d.h, k_u = d.sdd / d.pitch_u, k_w = d.h * d.sdd / d.pitch_u;
     const float w_par = d.h * d.h / d.pitch_u;
     pixbp2d_kernel<FAN, CLAMP, PX><<<grid, block, smem, s>>>(d.views, d.n_views, ypad, d.sino_ld,
-                                                             d.ndu, d.nx, d.ny, sid_h, k_u, k_w,
-                                                             w_par, x, stop);
+                                                             floor_chunk(d.sino_ld), d.ndu, d.nx,
+                                                             d.ny, sid_h, k_u, k_w, w_par, x, stop);
 }
 
 cudaError_t launch_pixbp2d(const ct_geom *g, const float2 *ypad, float *x, const int *stop,

@@ -190,42 +190,67 @@ __device__ int bidiag_svd_serial(double *d, double *e, double *g, int n)
     return iter >= max_iter ? -1 : 0;
 }
 
-// Characteristic polynomial det(theta I - T) of the zero-diagonal tridiagonal with squared
-// off-diagonals t2[0..n-2] (rows first..n-1), its derivative, with power-of-two rescaling.
-// Returns p and dp scaled by the same 2^(-e) (e accumulated in *ex).
+// |v| ordered as an integer: the bit pattern without the sign
+__device__ __forceinline__ long long abs_bits(double v)
+{
+    return __double_as_longlong(v) & 0x7fffffffffffffffll;
+}
+
+// det(theta I - T_{first..n-1}) and its derivative by the three-term recurrence, value * 2^ex.
+// The scale is checked every fourth step (integer compares of the bit patterns): with the
+// scaled T (squared off-diagonals <= 1) and theta <= 2 four steps grow the magnitudes by at
+// most 4^4, so values rescaled beyond 2^(+-400) stay far from overflow and underflow.
 __device__ void charpoly(const double *t2, int first, int n, double th, double &p, double &dp, int &ex)
 {
     double pm2 = 1.0, pm1 = th, qm2 = 0.0, qm1 = 1.0;   // size-1 block: det = theta, d/dth = 1
     int e = 0;
+    const long long big = __double_as_longlong(0x1p+400), small = __double_as_longlong(0x1p-400);
     for (int j = first + 1; j < n; ++j) {
         const double a = t2[j - 1];
-        double pj = th * pm1 - a * pm2;
-        double qj = pm1 + th * qm1 - a * qm2;
+        const double pj = th * pm1 - a * pm2;
+        const double qj = pm1 + th * qm1 - a * qm2;
         pm2 = pm1; pm1 = pj; qm2 = qm1; qm1 = qj;
-        double mag = fabs(pj) + fabs(qj);
-        if (mag > 0x1p+400 || (mag < 0x1p-400 && mag != 0.0)) {
-            int sh = (mag > 0x1p+400) ? -400 : 400;
-            pm1 = ldexp(pm1, sh); pm2 = ldexp(pm2, sh);
-            qm1 = ldexp(qm1, sh); qm2 = ldexp(qm2, sh);
-            e -= sh;
+        if (((j - first) & 3) == 0) {
+            const long long mag = max(max(abs_bits(pm1), abs_bits(pm2)),
+                                      max(abs_bits(qm1), abs_bits(qm2)));
+            if (mag > big || (mag < small && mag != 0)) {
+                const int sh = (mag > big) ? -400 : 400;
+                pm1 = ldexp(pm1, sh); pm2 = ldexp(pm2, sh);
+                qm1 = ldexp(qm1, sh); qm2 = ldexp(qm2, sh);
+                e -= sh;
+            }
         }
     }
     p = pm1; dp = qm1; ex = e;
 }
 
 // Sturm count: number of eigenvalues of the zero-diagonal tridiagonal (squared off-diagonals
-// t2[0..n-2]) below x, from the pivots of T - x I = L D L^T; a pivot smaller than pivmin is
-// replaced by -pivmin before it is counted (so counting and recurrence agree).
+// t2[0..n-2]) below x, as the number of sign changes along the leading minors
+// p_0 = 1, p_1 = -x, p_j = -x p_{j-1} - t2[j-2] p_{j-2} of T - x I (Sylvester: the pivots of
+// T - x I = L D L^T are p_j / p_{j-1}).  Division-free; a zero minor takes the sign opposite to
+// its predecessor (as a zero pivot replaced by a tiny negative one would).  Rescaled by powers
+// of two every fourth step as in charpoly (x <= 2).
 __device__ int count64(const double *t2, int n, double x)
 {
-    const double pivmin = 1e-290;
-    double dd = -x;
-    if (fabs(dd) < pivmin) dd = -pivmin;
-    int cnt = dd < 0.0;
-    for (int j = 1; j < n; ++j) {
-        dd = -x - t2[j - 1] / dd;
-        if (fabs(dd) < pivmin) dd = -pivmin;
-        cnt += dd < 0.0;
+    double pm2 = 1.0, pm1 = -x;
+    const long long b1 = __double_as_longlong(pm1);
+    bool sprev = b1 < 0 || (b1 << 1) == 0;
+    int cnt = sprev;
+    const long long big = __double_as_longlong(0x1p+400), small = __double_as_longlong(0x1p-400);
+    for (int j = 2; j <= n; ++j) {
+        const double pj = -x * pm1 - t2[j - 2] * pm2;
+        const long long bj = __double_as_longlong(pj);
+        const bool sj = ((bj << 1) == 0) ? !sprev : (bj < 0);
+        cnt += sj != sprev;
+        sprev = sj;
+        pm2 = pm1; pm1 = pj;
+        if ((j & 3) == 0) {
+            const long long mag = max(abs_bits(pm1), abs_bits(pm2));
+            if (mag > big || (mag < small && mag != 0)) {
+                const int sh = (mag > big) ? -400 : 400;
+                pm1 = ldexp(pm1, sh); pm2 = ldexp(pm2, sh);
+            }
+        }
     }
     return cnt;
 }
