@@ -40,7 +40,7 @@ L2_FLUSH_BYTES = 256 << 20
 SM_COUNT = 152
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the kernels
 # as they are now (profiles/*_fan512.md); None once a kernel changes until it is re-captured
-KERNEL_TRAFFIC = {"pixel_B": 2.08e6, "joseph_A": 13.18e6, "arnoldi_cgs2": None}
+KERNEL_TRAFFIC = {"pixel_B": None, "joseph_A": None, "arnoldi_cgs2": None}
 
 
 def _peaks():
@@ -266,11 +266,12 @@ def bench_ours(args, rank, world, local_rank):
         upd = G.b_samples * b_n
         kernels["pixel_B"] = {"ms": b_ms, "launches": b_n, "gups": upd / (b_ms * 1e-3) / 1e9}
     if a_groups:
-        # algorithmic bytes of the Arnoldi steps of one AB and one BA solve (FP32 basis):
-        # step k streams the k basis rows twice, reads q, writes w_{k+1}: (2k + 2) L 4 bytes
+        # algorithmic bytes of the Arnoldi steps of one AB and one BA solve (FP32 basis): CGS2
+        # step k reads the k basis rows three times (dots; update fused with the second dots;
+        # second update), reads q three times and writes q' and w_{k+1}: (3k + 5) L 4 bytes
         L_ab = geom.n_views * (geom.n_det_u + 4 + (-(geom.n_det_u + 4)) % 4)
         L_ba = geom.n + (-geom.n) % 4
-        per_solve = lambda L: sum((2 * k + 2) * L * 4 for k in range(1, ITERS + 1))
+        per_solve = lambda L: sum((3 * k + 5) * L * 4 for k in range(1, ITERS + 1))
         byts = (per_solve(L_ab) + per_solve(L_ba)) * steps
         kernels["arnoldi_cgs2"] = {"ms": a_ms, "launches": a_n,
                                    "gbs": byts / (a_ms * 1e-3) / 1e9}

@@ -16,11 +16,14 @@
 // Each pass starts where the previous one ended, so the rows it needs first are still in L2.
 // Block partial sums are FP32 (warp shuffles), the cross-block sum is FP64 in a fixed order
 // by the last block to finish, so results are reproducible run to run.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "ct_internal.h"
 
@@ -49,6 +52,28 @@ __device__ __forceinline__ float warp_sum(float v)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Sum over blocks b < nblocks of partial[b * ncol + c] by one warp: lane l adds blocks l, l + 32,
+// ... in order, the lanes are then added by a fixed xor tree (a fixed order: reproducible run
+// to run).  Loads go to L2 (written by other blocks before their fence) in batches of eight.
+__device__ __forceinline__ double column_sum(const double *partial, int nblocks, int ncol, int c,
+                                             int lane)
+{
+    double s = 0.0;
+    for (int b0 = lane; b0 < nblocks; b0 += 32 * 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int b = b0 + 32 * u;
+            v[u] = (b < nblocks) ? __ldcg(partial + (int64_t)b * ncol + c) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += v[u];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
 }
 
 constexpr int kGroup = 8;   // basis rows handled together: 8 independent loads in flight
@@ -215,14 +240,9 @@ __global__ void __launch_bounds__(kThreads) cgs_kernel(CgsArgs a)
     if (!is_last) return;
     __threadfence();
     __shared__ double total_nn;
-    // column i is summed by warp i % kWarps: lane l adds blocks l, l + 32, ... and the warp's
-    // lanes are then added by a fixed xor tree (a fixed order: reproducible run to run)
+    // column i is summed by warp i % kWarps (column_sum)
     for (int i = warp; i < ncol; i += kWarps) {
-        double s = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += 32)
-            s += ((volatile double *)a.partial)[(int64_t)b * ncol + i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const double s = column_sum(a.partial, (int)gridDim.x, ncol, i, lane);
         if (lane == 0) {
             if (i < nvec) {
                 if (MODE == M_DOTS) { a.hcol[i] = s; a.coef_out[i] = s; }
@@ -300,11 +320,471 @@ static int cgs_wave_blocks()
     return cached[dev];
 }
 
-// Caches the one-wave grid of the Gram-Schmidt kernels for the current device (call before a
-// stream capture).
+static cudaError_t tile_prepare();
+static int device_sms();
+
+// Caches the one-wave grid of the Gram-Schmidt kernels for the current device and allows the
+// tiled kernels their shared memory (call before a stream capture).
 cudaError_t arnoldi_prepare()
 {
-    return cgs_wave_blocks() > 0 ? cudaSuccess : cudaErrorUnknown;
+    if (cgs_wave_blocks() <= 0) return cudaErrorUnknown;
+    device_sms();
+    return tile_prepare();
+}
+
+// ============================================================================ tiled CGS2
+// The solver's own basis (row stride ld a multiple of 128 elements, q holding ld floats with a
+// zero tail) takes a tiled path: a tile is 128 consecutive elements of every basis row (one
+// 4-element unit per lane of a warp) plus the same 128 elements of q, copied global -> shared
+// memory by the TMA engine (cp.async.bulk, one copy per row segment, completion counted on an
+// mbarrier) into a ring of stages, so that several tiles per CTA are in flight while the
+// previous one is consumed.  One step is three passes over the basis:
+//   T1  h1 = W^T q, ||q||^2                                       (tiles ascending)
+//   T2  q' = q - W h1 (written back), h2 = W^T q', ||q'||^2        (tiles descending)
+//       -- both from the SAME shared-memory tile, so W is read from memory once --
+//   T3  nu = sqrt(||q'||^2 - ||h2||^2) = h_{k+1,k}, breakdown test;
+//       w_{k+1} = (q' - W h2) / nu                                 (tiles ascending)
+// T1 and T2 leave per-block sums; a small kernel after each adds them across blocks, one warp
+// per column with all columns in parallel (a single block doing that serially took longer
+// than the pass itself).
+// nu uses ||q' - W h2||^2 = ||q'||^2 - 2 h2.W^T q' + h2.W^T W h2 = ||q'||^2 - ||h2||^2 up to
+// the basis' loss of orthogonality times ||h2||^2 (h2 is the small second correction).
+// Alternating the tile order makes each pass start on the tiles the previous one read last
+// (still in L2).  Rows of a tile are split over the 8 warps (row r to warp r % 8) for the
+// dots; the updates sum each warp's rows per lane and combine the 8 partial sums in a fixed
+// order, so results are reproducible run to run.
+constexpr int kTileUnits = 32;                  // 4-element units per tile row (one per lane)
+constexpr int kTileElems = 4 * kTileUnits;      // 128 elements
+constexpr int kTileSmemMax = 220 * 1024;        // dynamic shared memory of one CTA at most
+constexpr int kTilePair = 110 * 1024;           // at most this much for two CTAs per SM
+constexpr long long kWaitCycles = 1ll << 31;    // bounded mbarrier waits (about a second)
+enum { T_DOTS = 0, T_UPD_DOTS = 1, T_UPD_SCALE = 2 };
+
+struct TileArgs {
+    const void *W; int64_t ld; int nvec;         // rows W[0..nvec-1], storage type T
+    const float *q; float *qout;                 // q (ld floats); T2 writes q' to qout (= q)
+    int ntiles, stages;
+    const double *coef;                          // T2: h1, T3: h2
+    double *partial; unsigned *counter;
+    double *hcol, *aux, *coef_out;               // T1: h1 -> coef_out; T2: h2 -> coef_out;
+                                                 // aux[0] ||q||, aux[1] 1 / nu, aux[4] ||q'||^2
+    int *stop; int step;
+    void *wnext; float *cur;                     // T3: row k+1 of W (type T), FP32 copy
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes) : "memory");
+}
+
+// cp.async.bulk global -> shared, completion (bytes) signalled on `bar`; 16-byte aligned
+// addresses, size a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+// 2D tiled TMA load of the box at element column x, row 0 of the tensor map into shared
+// memory, completion (bytes) signalled on `bar`; x * element size is a multiple of 16 bytes
+__device__ __forceinline__ void tensor_g2s(void *dst, const CUtensorMap *map, int x, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3}], [%4];"
+                 ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(0),
+                 "r"(smem_u32(bar)) : "memory");
+}
+
+// waits for phase `parity` of `bar` to complete; false after about kWaitCycles
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
+{
+    const uint32_t a = smem_u32(bar);
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(a), "r"(parity) : "memory");
+        if (done) return true;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ float4 unit_from_smem(const unsigned char *seg, int lane)
+{
+    if constexpr (sizeof(T) == 4) {
+        return reinterpret_cast<const float4 *>(seg)[lane];
+    } else {
+        const uint2 r = reinterpret_cast<const uint2 *>(seg)[lane];
+        float2 a, b;
+        if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+            a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&r.x));
+            b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&r.y));
+        } else {
+            a = __half22float2(*reinterpret_cast<const __half2 *>(&r.x));
+            b = __half22float2(*reinterpret_cast<const __half2 *>(&r.y));
+        }
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+}
+
+__device__ __forceinline__ float dot4(float4 a, float4 b)
+{
+    return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+}
+
+// shared-memory bytes of one stage: nvec row segments of the basis and one of q
+template <typename T>
+__host__ __device__ constexpr int tile_stage_bytes(int nvec)
+{
+    return nvec * kTileElems * (int)sizeof(T) + kTileElems * 4;
+}
+
+template <int MODE, typename T>
+__global__ void __launch_bounds__(kThreads, 2) cgs_tile_kernel(const __grid_constant__ CUtensorMap wmap,
+                                                               TileArgs a)
+{
+    if (a.stop[0] != 0) return;
+    extern __shared__ __align__(128) unsigned char tsm[];
+    const int nvec = a.nvec, S = a.stages;
+    const int seg = kTileElems * (int)sizeof(T);
+    const int stage_bytes = tile_stage_bytes<T>(nvec);
+    // stages | mbarriers | block sums [nvec + 1] | warp partials [8][32] | q' [32] | coef [nvec]
+    // (every region starts on a 16-byte boundary)
+    unsigned char *p = tsm + (size_t)S * stage_bytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(p);
+    p += 16 * ((S + 1) / 2);
+    float *acc = reinterpret_cast<float *>(p);
+    p += 16 * ((nvec + 1 + 3) / 4);
+    float4 *red = reinterpret_cast<float4 *>(p);
+    float4 *qs = red + kWarps * kTileUnits;
+    float *scoef = reinterpret_cast<float *>(qs + kTileUnits);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ncol = nvec + 1;
+    for (int i = tid; i < ncol; i += kThreads) acc[i] = 0.f;
+    float inv_nu = 0.f;
+    if (MODE == T_UPD_SCALE) {
+        // h_{k+1,k} = nu = sqrt(||q'||^2 - ||h2||^2), every block the same value (fixed order);
+        // block 0 records it and the breakdown test of the paper's Arnoldi loop
+        __shared__ double hsum[kWarps];
+        double h2 = 0.0;
+        for (int i = tid; i < nvec; i += kThreads) {
+            const double c = a.coef[i];
+            h2 = fma(c, c, h2);
+            scoef[i] = (float)c;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) h2 += __shfl_xor_sync(0xffffffffu, h2, o);
+        if (lane == 0) hsum[warp] = h2;
+        __syncthreads();
+        double t = 0.0;
+        for (int w = 0; w < kWarps; ++w) t += hsum[w];
+        const double nrm = sqrt(fmax(a.aux[4] - t, 0.0));
+        const bool bad = !isfinite(nrm), brk = !(nrm > kBreakdownTol * a.aux[0]);
+        if (blockIdx.x == 0 && tid == 0) {
+            a.hcol[nvec] = nrm;
+            if (bad) { a.stop[0] = a.step; a.stop[1] = CT_ENONFINITE; a.aux[1] = 0.0; }
+            else if (brk) { a.stop[0] = a.step; a.stop[1] = CT_BREAKDOWN; a.aux[1] = 0.0; }
+            else a.aux[1] = 1.0 / nrm;
+        }
+        if (bad || brk) return;
+        inv_nu = (float)(1.0 / nrm);
+    } else if (MODE == T_UPD_DOTS) {
+        for (int i = tid; i < nvec; i += kThreads) scoef[i] = (float)a.coef[i];
+    }
+    if (tid == 0) {
+        for (int st = 0; st < S; ++st) mbar_init(&bars[st], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // this CTA's tiles: blockIdx.x + i * gridDim.x, i < nt, in the order of the pass
+    const int nt = (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    auto tile_of = [&](int i) {
+        const int j = (MODE == T_UPD_DOTS) ? nt - 1 - i : i;
+        return (int)blockIdx.x + j * (int)gridDim.x;
+    };
+    // thread 0 issues the copies of tile i into its stage: the nvec x 128 box of the basis (one
+    // tensor copy; the map's row extent is nvec) and 128 entries of q (one bulk copy)
+    auto issue = [&](int i) {
+        const int st = i % S;
+        unsigned char *dst = tsm + (size_t)st * stage_bytes;
+        const int e0 = tile_of(i) * kTileElems;
+        mbar_expect_tx(&bars[st], (unsigned)stage_bytes);
+        tensor_g2s(dst, &wmap, e0, &bars[st]);
+        bulk_g2s(dst + (size_t)nvec * seg, a.q + e0, kTileElems * 4, &bars[st]);
+    };
+    if (tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (int i = 0; i < S && i < nt; ++i) issue(i);
+    }
+    bool ok = true;
+    float nn = 0.f;                      // lane partial of ||q||^2 (T1) or ||q'||^2 (T2), warp 0
+    int i = 0;
+    for (; i < nt; ++i) {
+        const int st = i % S;
+        if (!mbar_wait(&bars[st], (unsigned)((i / S) & 1))) { ok = false; break; }
+        const unsigned char *tileb = tsm + (size_t)st * stage_bytes;
+        const float4 qv = reinterpret_cast<const float4 *>(tileb + (size_t)nvec * seg)[lane];
+        float4 v = qv;                   // the vector the dots are taken with (q or q')
+        if (MODE != T_DOTS) {
+            // per-lane sum over this warp's rows of coef_r * W[r], then the 8 warps' sums
+            float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int r = warp; r < nvec; r += kWarps) {
+                const float c = scoef[r];
+                const float4 w = unit_from_smem<T>(tileb + (size_t)r * seg, lane);
+                u.x = fmaf(c, w.x, u.x); u.y = fmaf(c, w.y, u.y);
+                u.z = fmaf(c, w.z, u.z); u.w = fmaf(c, w.w, u.w);
+            }
+            red[warp * kTileUnits + lane] = u;
+            __syncthreads();
+            if (warp == 0) {
+                float4 t = red[lane];
+#pragma unroll
+                for (int w = 1; w < kWarps; ++w) {
+                    const float4 o = red[w * kTileUnits + lane];
+                    t.x += o.x; t.y += o.y; t.z += o.z; t.w += o.w;
+                }
+                float4 r = make_float4(qv.x - t.x, qv.y - t.y, qv.z - t.z, qv.w - t.w);
+                const size_t e = (size_t)tile_of(i) * kTileUnits + lane;
+                if (MODE == T_UPD_DOTS) {
+                    reinterpret_cast<float4 *>(a.qout)[e] = r;
+                    qs[lane] = r;
+                    nn = fmaf(r.x, r.x, fmaf(r.y, r.y, fmaf(r.z, r.z, fmaf(r.w, r.w, nn))));
+                } else {
+                    r.x *= inv_nu; r.y *= inv_nu; r.z *= inv_nu; r.w *= inv_nu;
+                    const float4 stv = BasisIO<T>::store(a.wnext, (int64_t)e, r);
+                    if (a.cur) reinterpret_cast<float4 *>(a.cur)[e] = stv;
+                }
+            }
+            if (MODE == T_UPD_DOTS) {
+                __syncthreads();
+                v = qs[lane];
+            }
+        } else if (warp == 0) {
+            nn = fmaf(qv.x, qv.x, fmaf(qv.y, qv.y, fmaf(qv.z, qv.z, fmaf(qv.w, qv.w, nn))));
+        }
+        if (MODE != T_UPD_SCALE) {
+            // dots of this warp's rows with v: 8 rows at a time, transposed shuffle reduction
+            for (int r0 = warp * 8; r0 < nvec; r0 += kWarps * 8) {
+                float pd[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    pd[u] = (r0 + u < nvec) ? dot4(unit_from_smem<T>(tileb + (size_t)(r0 + u) * seg, lane), v) : 0.f;
+                const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+                float q4v[4], q2v[2], q1;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float send = b4 ? pd[j] : pd[j + 4], keep = b4 ? pd[j + 4] : pd[j];
+                    q4v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+                }
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const float send = b3 ? q4v[j] : q4v[j + 2], keep = b3 ? q4v[j + 2] : q4v[j];
+                    q2v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+                }
+                {
+                    const float send = b2 ? q2v[0] : q2v[1], keep = b2 ? q2v[1] : q2v[0];
+                    q1 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+                }
+                q1 += __shfl_xor_sync(0xffffffffu, q1, 2);
+                q1 += __shfl_xor_sync(0xffffffffu, q1, 1);
+                const int pr = r0 + (lane >> 2);
+                if ((lane & 3) == 0 && pr < nvec) acc[pr] += q1;   // rows of this warp only
+            }
+        }
+        __syncthreads();                 // stage st consumed by every warp
+        if (tid == 0 && i + S < nt) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(i + S);
+        }
+    }
+    if (!ok) {
+        // a copy never completed: record it, then wait (bounded) for the copies still in flight
+        if (lane == 0) atomicCAS(a.stop, 0, a.step > 0 ? a.step : -1);
+        if (tid == 0) a.stop[1] = CT_ETIMEOUT;
+        for (int j = i; j < nt && j < i + S; ++j) mbar_wait(&bars[j % S], (unsigned)((j / S) & 1));
+    }
+    if (MODE == T_UPD_SCALE) return;
+    if (warp == 0) {
+        nn = warp_sum(nn);
+        if (lane == 0) acc[nvec] = nn;
+    }
+    __syncthreads();
+    // block sums; cgs_tile_reduce_kernel adds them across blocks
+    double *prow = a.partial + (int64_t)blockIdx.x * ncol;
+    for (int c = tid; c < ncol; c += kThreads) prow[c] = (double)acc[c];
+}
+
+// Cross-block sums of a T1 / T2 pass, one warp per column (all columns in parallel, each in a
+// fixed order): T1 writes h1 into the H column and the coefficient buffer and ||q|| to aux[0];
+// T2 adds h2 to the H column, writes it to the coefficient buffer and ||q'||^2 to aux[4].
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) cgs_tile_reduce_kernel(TileArgs a, int nblocks)
+{
+    if (a.stop[0] != 0) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * kWarps + warp, nvec = a.nvec;
+    if (c > nvec) return;
+    const double s = column_sum(a.partial, nblocks, nvec + 1, c, lane);
+    if (lane != 0) return;
+    if (c < nvec) {
+        if (MODE == T_DOTS) a.hcol[c] = s;
+        else a.hcol[c] += s;
+        a.coef_out[c] = s;
+    } else if (MODE == T_DOTS) {
+        a.aux[0] = sqrt(s);
+    } else {
+        a.aux[4] = s;
+    }
+}
+
+// Launch plan of the tiled path: stages per CTA and CTAs per SM from the shared memory a stage
+// needs (two CTAs per SM while two stages fit in half the SM's memory); 0 stages = not eligible.
+template <typename T>
+static void tile_plan(int nvec, int &stages, int &per_sm, size_t &smem)
+{
+    const int sb = tile_stage_bytes<T>(nvec);
+    // mbarriers (<= 6 stages), block sums, warp partials and q', coefficients, spare
+    const int extra = 48 + 16 * ((nvec + 4) / 4) + 16 * (kWarps + 1) * kTileUnits + 4 * nvec + 64;
+    if (2 * sb + extra <= kTilePair) {
+        stages = std::min(6, (kTilePair - extra) / sb);
+        per_sm = 2;
+    } else if (2 * sb + extra <= kTileSmemMax) {
+        stages = 2;
+        per_sm = 1;
+    } else {
+        stages = 0;
+        per_sm = 0;
+    }
+    smem = (size_t)stages * sb + extra;
+}
+
+static int device_sms()
+{
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (!cached[dev]) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+            sms = 152;
+        cached[dev] = sms;
+    }
+    return cached[dev];
+}
+
+// Allows the tile kernels their dynamic shared memory on the current device (before a capture).
+static cudaError_t tile_prepare()
+{
+    static bool done[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (done[dev]) return cudaSuccess;
+#define CT_TILE_ATTR(M, T)                                                                        \
+    e = cudaFuncSetAttribute(cgs_tile_kernel<M, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             kTileSmemMax);                                                       \
+    if (e != cudaSuccess) return e;
+    CT_TILE_ATTR(T_DOTS, float) CT_TILE_ATTR(T_UPD_DOTS, float) CT_TILE_ATTR(T_UPD_SCALE, float)
+    CT_TILE_ATTR(T_DOTS, __nv_bfloat16) CT_TILE_ATTR(T_UPD_DOTS, __nv_bfloat16)
+    CT_TILE_ATTR(T_UPD_SCALE, __nv_bfloat16)
+    CT_TILE_ATTR(T_DOTS, __half) CT_TILE_ATTR(T_UPD_DOTS, __half) CT_TILE_ATTR(T_UPD_SCALE, __half)
+#undef CT_TILE_ATTR
+    done[dev] = true;
+    return cudaSuccess;
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, []() {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// Tensor map of basis rows 0..nvec-1 (row stride ld entries of T) with nvec x 128 boxes.
+template <typename T>
+static bool encode_basis_map(CUtensorMap *map, const void *W, int64_t ld, int nvec)
+{
+    const auto enc = tensor_map_encoder();
+    if (!enc || nvec < 1 || nvec > 256) return false;
+    const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : std::is_same<T, __nv_bfloat16>::value
+                                       ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                       : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)nvec};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(T)};
+    const cuuint32_t box[2] = {(cuuint32_t)kTileElems, (cuuint32_t)nvec};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(map, dt, 2, const_cast<void *>(W), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename T>
+static bool tile_eligible(int64_t ld, int k, const ArnoldiScratch &sc)
+{
+    int stages, per_sm;
+    size_t smem;
+    tile_plan<T>(k + 1, stages, per_sm, smem);
+    return stages >= 2 && k + 1 <= 256 && ld % kTileElems == 0 && k + 2 <= sc.kmax + 2 &&
+           tensor_map_encoder() != nullptr;
+}
+
+// The tiled CGS2 step (three launches); false when the step is not eligible (then nothing ran).
+template <typename T>
+static bool arnoldi_step_tiled(void *W, int64_t ld, int k, float *q, double *hcol,
+                               const ArnoldiScratch &sc, double *aux, int *stop, int step,
+                               float *cur, cudaStream_t s, cudaError_t &err)
+{
+    const int nvec = k + 1;
+    int stages, per_sm;
+    size_t smem;
+    tile_plan<T>(nvec, stages, per_sm, smem);
+    if (!tile_eligible<T>(ld, k, sc) || (reinterpret_cast<uintptr_t>(W) & 255) != 0 ||
+        (reinterpret_cast<uintptr_t>(q) & 15) != 0)
+        return false;
+    if ((err = tile_prepare()) != cudaSuccess) return true;
+    CUtensorMap wmap;
+    if (!encode_basis_map<T>(&wmap, W, ld, nvec)) return false;
+    const int ntiles = (int)(ld / kTileElems);
+    const int blocks = std::max(1, std::min({ntiles, per_sm * device_sms(), sc.max_blocks}));
+    double *h1 = aux + 8, *h2 = aux + 8 + (sc.kmax + 2);
+    TileArgs a{W, ld, nvec, q, q, ntiles, stages, nullptr, sc.partial, sc.counter, hcol, aux,
+               h1, stop, step, nullptr, nullptr};
+    const int rblocks = (nvec + 1 + kWarps - 1) / kWarps;
+    cgs_tile_kernel<T_DOTS, T><<<blocks, kThreads, smem, s>>>(wmap, a);
+    cgs_tile_reduce_kernel<T_DOTS><<<rblocks, kThreads, 0, s>>>(a, blocks);
+    a.coef = h1; a.coef_out = h2;
+    cgs_tile_kernel<T_UPD_DOTS, T><<<blocks, kThreads, smem, s>>>(wmap, a);
+    cgs_tile_reduce_kernel<T_UPD_DOTS><<<rblocks, kThreads, 0, s>>>(a, blocks);
+    a.coef = h2; a.coef_out = nullptr;
+    a.wnext = static_cast<char *>(W) + (size_t)(k + 1) * ld * sizeof(T);
+    a.cur = cur;
+    cgs_tile_kernel<T_UPD_SCALE, T><<<blocks, kThreads, smem, s>>>(wmap, a);
+    err = cudaGetLastError();
+    return true;
 }
 
 // One CGS2 Arnoldi step on rows W[0..k] (storage type T) with q = M w_k; writes the H column
@@ -313,8 +793,11 @@ cudaError_t arnoldi_prepare()
 template <typename T>
 static cudaError_t arnoldi_step_t(void *W, int64_t L, int64_t ld, int k, float *q, double *hcol,
                                   const ArnoldiScratch &sc, double *aux, int *stop, int step,
-                                  bool reorth, float *cur, cudaStream_t s)
+                                  bool reorth, float *cur, bool q_padded, cudaStream_t s)
 {
+    cudaError_t err = cudaSuccess;
+    if (reorth && q_padded && arnoldi_step_tiled<T>(W, ld, k, q, hcol, sc, aux, stop, step, cur, s, err))
+        return err;
     const int64_t L4 = L / 4;
     const int nvec = k + 1;
     const int blocks = grid_for(L4, std::min(sc.max_blocks, cgs_wave_blocks()));
@@ -337,24 +820,42 @@ static cudaError_t arnoldi_step_t(void *W, int64_t L, int64_t ld, int k, float *
     return cudaGetLastError();
 }
 
+// kernel launches of one arnoldi_step_basis call (W and q as the solver allocates them)
+int arnoldi_step_launches(int basis, int64_t ld, int k, const ArnoldiScratch &sc, bool reorth,
+                          bool q_padded)
+{
+    if (!reorth) return 3;
+    bool tiled = false;
+    if (q_padded) {
+        if (basis == CT_BASIS_BF16) tiled = tile_eligible<__nv_bfloat16>(ld, k, sc);
+        else if (basis == CT_BASIS_F16) tiled = tile_eligible<__half>(ld, k, sc);
+        else tiled = tile_eligible<float>(ld, k, sc);
+    }
+    return tiled ? 5 : 4;
+}
+
 cudaError_t arnoldi_step_dev(float *W, int64_t L, int64_t ld, int k, float *q, double *hcol,
                              const ArnoldiScratch &sc, double *aux, int *stop, int step,
                              bool reorth, cudaStream_t s)
 {
-    return arnoldi_step_t<float>(W, L, ld, k, q, hcol, sc, aux, stop, step, reorth, nullptr, s);
+    return arnoldi_step_t<float>(W, L, ld, k, q, hcol, sc, aux, stop, step, reorth, nullptr,
+                                 false, s);
 }
 
 cudaError_t arnoldi_step_basis(int basis, void *W, int64_t L, int64_t ld, int k, float *q,
                                double *hcol, const ArnoldiScratch &sc, double *aux, int *stop,
-                               int step, bool reorth, float *cur, cudaStream_t s)
+                               int step, bool reorth, float *cur, bool q_padded, cudaStream_t s)
 {
     switch (basis) {
     case CT_BASIS_BF16:
-        return arnoldi_step_t<__nv_bfloat16>(W, L, ld, k, q, hcol, sc, aux, stop, step, reorth, cur, s);
+        return arnoldi_step_t<__nv_bfloat16>(W, L, ld, k, q, hcol, sc, aux, stop, step, reorth,
+                                             cur, q_padded, s);
     case CT_BASIS_F16:
-        return arnoldi_step_t<__half>(W, L, ld, k, q, hcol, sc, aux, stop, step, reorth, cur, s);
+        return arnoldi_step_t<__half>(W, L, ld, k, q, hcol, sc, aux, stop, step, reorth, cur,
+                                      q_padded, s);
     default:
-        return arnoldi_step_t<float>(W, L, ld, k, q, hcol, sc, aux, stop, step, reorth, cur, s);
+        return arnoldi_step_t<float>(W, L, ld, k, q, hcol, sc, aux, stop, step, reorth, cur,
+                                     q_padded, s);
     }
 }
 

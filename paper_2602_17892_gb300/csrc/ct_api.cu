@@ -46,9 +46,13 @@ cudaError_t launch_combine(const float *W, int64_t L, int64_t ld, const double *
                            int ystride, const int *stop, int kfixed, const float *x0, float *x,
                            int max_blocks, cudaStream_t s);
 cudaError_t launch_rsub(const float *b, float *r, int64_t L, int max_blocks, cudaStream_t s);
+// q_padded: q holds ld floats with a zero tail beyond L (the solver's own vectors), which
+// allows the tiled path when ld is a multiple of 128
 cudaError_t arnoldi_step_basis(int basis, void *W, int64_t L, int64_t ld, int k, float *q,
                                double *hcol, const ArnoldiScratch &sc, double *aux, int *stop,
-                               int step, bool reorth, float *cur, cudaStream_t s);
+                               int step, bool reorth, float *cur, bool q_padded, cudaStream_t s);
+int arnoldi_step_launches(int basis, int64_t ld, int k, const ArnoldiScratch &sc, bool reorth,
+                          bool q_padded);
 cudaError_t normalize_first_basis(int basis, const float *r, int64_t L, void *w0,
                                   const ArnoldiScratch &sc, double *aux, int *stop, float *cur,
                                   cudaStream_t s);
@@ -118,9 +122,10 @@ struct Workspace {
     int method = -1, K = 0, basis = 0;
     int *path = nullptr;    // per step: 1 = parallel small-solve path accepted
     int64_t L = 0;          // basis row length in entries (multiple of 4, zero tail)
-    void *W = nullptr;      // (K+1) rows in the basis storage type
-    float *cur = nullptr;   // 16-bit bases: the newest row in FP32 (operator input)
-    float *q = nullptr;     // L
+    int64_t ld = 0;         // basis row stride: L rounded up to 128 entries (zero beyond L)
+    void *W = nullptr;      // (K+1) rows of ld entries in the basis storage type
+    float *cur = nullptr;   // 16-bit bases: the newest row in FP32 (operator input), ld
+    float *q = nullptr;     // ld (zero beyond L)
     float *img = nullptr;   // image scratch, img_ld floats
     float *sino = nullptr;  // padded sinogram scratch
     float *sino2 = nullptr; // second padded sinogram (BA with an initial guess; on first use)
@@ -171,10 +176,11 @@ static ct_status ws_get(ct_geom *g, int method, int K, int basis, Workspace **ou
     ex->ws[method] = nullptr;
     w = new Workspace();
     w->method = method; w->K = K; w->basis = basis; w->L = L;
+    w->ld = round_up(L, 128);
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = dalloc((char **)&w->W, (size_t)(K + 1) * L * basis_bytes(basis));
-    if (e == cudaSuccess && basis != CT_BASIS_F32) e = dalloc(&w->cur, (size_t)L);
-    if (e == cudaSuccess) e = dalloc(&w->q, (size_t)L);
+    if (e == cudaSuccess) e = dalloc((char **)&w->W, (size_t)(K + 1) * w->ld * basis_bytes(basis));
+    if (e == cudaSuccess && basis != CT_BASIS_F32) e = dalloc(&w->cur, (size_t)w->ld);
+    if (e == cudaSuccess) e = dalloc(&w->q, (size_t)w->ld);
     if (e == cudaSuccess) e = dalloc(&w->vec, (size_t)L);
     if (e == cudaSuccess) e = dalloc(&w->img, (size_t)img_ld);
     if (e == cudaSuccess) e = dalloc(&w->sino, (size_t)sino_len);
@@ -691,7 +697,7 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
     if ((st = ws_get(g, 0, o->max_iters, o->basis, &w)) != CT_OK) return st;
     *wout = w;
     const int K = o->max_iters;
-    const int64_t L = w->L, ld = w->L;
+    const int64_t L = w->L, ld = w->ld;
     ArnoldiScratch sc{w->partial, w->counter, kMaxBlocks, w->K};
     const double dp_target = o->tau * o->noise_norm;
     CT_CUDA(cudaMemsetAsync(w->stop, 0, 2 * sizeof(int), s));
@@ -730,9 +736,11 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
             CT_CUDA(launch_forward_proj(g, w->q, true, w->stop, s));   //          A (B w_k)
         }
         {
-            CT_PHASE(CT_PH_ARNOLDI, o->reorth ? 4 : 3, s);               // lines 6-11
+            // lines 6-11
+            CT_PHASE(CT_PH_ARNOLDI, arnoldi_step_launches(o->basis, ld, k, sc, o->reorth != 0, true),
+                     s);
             CT_CUDA(arnoldi_step_basis(o->basis, w->W, L, ld, k, w->q, w->H + (int64_t)k * ldh,
-                                       sc, w->aux, w->stop, step, o->reorth != 0, w->cur, s));
+                                       sc, w->aux, w->stop, step, o->reorth != 0, w->cur, true, s));
         }
         if ((st = stop_checkpoint(w, o, s, dp_target, step, checked)) != CT_OK) return st;
     }
@@ -774,7 +782,7 @@ static ct_status enqueue_ba(ct_geom *g, const float *b_dev, const float *x0_dev,
     if ((st = ws_get(g, 1, o->max_iters, o->basis, &w)) != CT_OK) return st;
     *wout = w;
     const int K = o->max_iters;
-    const int64_t L = w->L, ld = w->L;
+    const int64_t L = w->L, ld = w->ld;
     const int64_t msino = (int64_t)g->dg.n_views * g->dg.sino_view_ld;
     ArnoldiScratch sc{w->partial, w->counter, kMaxBlocks, w->K};
     const double dp_target = o->tau * o->noise_norm;
@@ -822,9 +830,10 @@ static ct_status enqueue_ba(ct_geom *g, const float *b_dev, const float *x0_dev,
             CT_CUDA(launch_back_proj(g, w->sino, w->q, w->stop, s));     //          B (A w_k)
         }
         {
-            CT_PHASE(CT_PH_ARNOLDI, o->reorth ? 4 : 3, s);
+            CT_PHASE(CT_PH_ARNOLDI, arnoldi_step_launches(o->basis, ld, k, sc, o->reorth != 0, true),
+                     s);
             CT_CUDA(arnoldi_step_basis(o->basis, w->W, L, ld, k, w->q, w->H + (int64_t)k * ldh,
-                                       sc, w->aux, w->stop, step, o->reorth != 0, w->cur, s));
+                                       sc, w->aux, w->stop, step, o->reorth != 0, w->cur, true, s));
         }
         if ((st = stop_checkpoint(w, o, s, dp_target, step, checked)) != CT_OK) return st;
     }
@@ -1078,7 +1087,7 @@ extern "C" ct_status ct_lambda_samples(ct_geom *g, const float *b_dev, const flo
     CT_CUDA(cudaMallocAsync((void **)&Z, sizeof(float) * (size_t)K * img_ld, s));
     CT_CUDA(cudaMallocAsync((void **)&G, sizeof(double) * (size_t)K * (K + 1), s));
     for (int j = 0; j < K; ++j)         // Z = B W_K (the AB basis is in padded-sinogram layout)
-        CT_CUDA(launch_back_proj(g, static_cast<const float *>(w->W) + (int64_t)j * w->L,
+        CT_CUDA(launch_back_proj(g, static_cast<const float *>(w->W) + (int64_t)j * w->ld,
                                Z + (int64_t)j * img_ld, nullptr, s));
     CT_CUDA(launch_gram(Z, img_ld, g->n, K, x_true_dev, G, G + (size_t)K * K, s));
     CT_CUDA(launch_lambda_labels(w->H, w->K + 1, w->aux + 2, G, K, G + (size_t)K * K, labels_dev, s));

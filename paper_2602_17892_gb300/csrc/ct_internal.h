@@ -99,6 +99,19 @@ struct ct_geom {
 
 namespace ct {
 
+// Floor by one round-down FP32 addition (projector kernels): for an integer K with
+// 2^23 <= K + p < 2^24, K + p rounded towards -infinity is K + floor(p) exactly and its bit
+// pattern is the integer 0x4B000000 + (K + floor(p) - 2^23).
+constexpr float kFloor2p23 = 8388608.f;   // 2^23
+constexpr float kFloorK0 = 8388610.f;     // 2^23 + 2: K + p >= 2^23 for p >= -2
+constexpr int kFloorSpan = 1 << 22;       // row (or view) offsets carried in K stay below this
+// rows (or views) of `stride` elements per chunk whose offsets K carries
+inline int floor_chunk(int64_t stride)
+{
+    const int64_t s = stride > 0 ? stride : 1;
+    return (int)(kFloorSpan / s > 0 ? kFloorSpan / s : 1);
+}
+
 // ----------------------------------------------------------------------------- projectors
 // Every launcher takes an optional device stop word: when non-null and non-zero at kernel
 // start, the kernel returns at once (a solver that met breakdown skips the remaining steps).

@@ -161,21 +161,35 @@ cudaError_t launch_back_proj(const ct_geom *g, const float *ypad, float *x, cons
 // to FP32 rounding, so the pair index stays in [-1, n_other + 1], which the layouts hold as
 // zero pairs (a zero line before line 0 and at least n_other + 2 pairs per line); a lane
 // outside its own range skips the load.
-constexpr float kFloor2p23 = 8388608.f;   // 2^23
-constexpr float kFloorK0 = 8388610.f;     // 2^23 + 2: K + pos >= 2^23 for pos >= -2
-constexpr int kFloorSpan = 1 << 22;       // line (or view) offsets per chunk stay below this
-
-// chunk length in lines (or views) of `stride` elements
-static inline int floor_chunk(int64_t stride)
+// lines t in [ta, tb] of one ray; K carries (t - ta) * stride (below 2^22 for every t)
+__device__ __forceinline__ float joseph2d_span(int ta, int tb, int t_lo, int t_hi, float pmid,
+                                               float slope, float tmid, int stride,
+                                               uint64_t abase, float acc)
 {
-    return (int)std::max<int64_t>(1, kFloorSpan / std::max<int64_t>(stride, 1));
+    float tf = (float)ta - tmid;
+    float K = kFloorK0;                           // 2^23 + 2 + (t - ta) * stride
+    const uint64_t lb = abase + 8ull * (uint64_t)ta * (uint64_t)stride;
+#pragma unroll 4
+    for (int t = ta; t <= tb; ++t) {
+        if (t >= t_lo && t <= t_hi) {
+            const float pos = fmaf(slope, tf, pmid);
+            const float sk = __fadd_rd(pos, K);
+            const float f = pos - (sk - K);
+            const float2 p = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * __float_as_uint(sk)));
+            acc += fmaf(f, p.y - p.x, p.x);
+        }
+        tf += 1.f;
+        K += (float)stride;
+    }
+    return acc;
 }
 
+// CHUNKED: the lines are walked in chunks of `chunk` (images whose line offsets exceed 2^22)
+template <bool CHUNKED>
 __global__ void __launch_bounds__(512) joseph2d_kernel(
     const Ray2D *__restrict__ rays, int n_views, int ndu, int vpb,
-    const float2 *__restrict__ prow, int prow_ld, int prow_chunk, const float2 *__restrict__ pcol,
-    int pcol_ld, int pcol_chunk, int nx, int ny, float *__restrict__ y, int y_ld, int y_off,
-    const int *stop)
+    const float2 *__restrict__ prow, int prow_ld, const float2 *__restrict__ pcol, int pcol_ld,
+    int chunk, int nx, int ny, float *__restrict__ y, int y_ld, int y_off, const int *stop)
 {
     if (stop && stop[0] != 0) return;
     const int bins_pb = blockDim.x / vpb;
@@ -188,9 +202,9 @@ __global__ void __launch_bounds__(512) joseph2d_kernel(
     if (!valid) { t_lo = 1; t_hi = 0; }
     const int axis = (R.packed >> 30) & 1;
     const float2 *base;          // line 0 of the layout the ray reads
-    int stride, chunk, n_drive;
-    if (axis == 0) { base = pcol; stride = pcol_ld; chunk = pcol_chunk; n_drive = nx; }  // along x
-    else { base = prow; stride = prow_ld; chunk = prow_chunk; n_drive = ny; }            // along y
+    int stride, n_drive;
+    if (axis == 0) { base = pcol; stride = pcol_ld; n_drive = nx; }   // drive along x
+    else { base = prow; stride = prow_ld; n_drive = ny; }             // drive along y
     const float tmid = 0.5f * (float)(n_drive - 1);
     // the warp steps through the union of its lanes' driving ranges together, so that at every
     // step its lanes read neighbouring pairs of one line (a lane outside its own range idles)
@@ -199,23 +213,12 @@ __global__ void __launch_bounds__(512) joseph2d_kernel(
     const uint64_t abase = reinterpret_cast<uint64_t>(base) -
                            8ull * ((uint64_t)__float_as_uint(kFloor2p23) + 1ull);
     float acc = 0.f;
-    float tf = (float)wlo - tmid;
-    for (int t0 = wlo; t0 <= whi; t0 += chunk) {
-        const int t1 = min(whi, t0 + chunk - 1);
-        const uint64_t lb = abase + 8ull * (uint64_t)t0 * (uint64_t)stride;
-        float K = kFloorK0;                       // 2^23 + 2 + (t - t0) * stride
-#pragma unroll 4
-        for (int t = t0; t <= t1; ++t) {
-            if (t >= t_lo && t <= t_hi) {
-                const float pos = fmaf(R.slope, tf, R.pmid);
-                const float sk = __fadd_rd(pos, K);
-                const float f = pos - (sk - K);
-                const float2 p = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * __float_as_uint(sk)));
-                acc += fmaf(f, p.y - p.x, p.x);
-            }
-            tf += 1.f;
-            K += (float)stride;
-        }
+    if (!CHUNKED) {
+        acc = joseph2d_span(wlo, whi, t_lo, t_hi, R.pmid, R.slope, tmid, stride, abase, acc);
+    } else {
+        for (int t0 = wlo; t0 <= whi; t0 += chunk)
+            acc = joseph2d_span(t0, min(whi, t0 + chunk - 1), t_lo, t_hi, R.pmid, R.slope, tmid,
+                                stride, abase, acc);
     }
     if (valid) y[(int64_t)view0 * y_ld + y_off + bin] = acc * R.weight;
 }
@@ -230,10 +233,18 @@ cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, con
     dim3 grid((d.ndu + bins_pb - 1) / bins_pb, (d.n_views + vpb - 1) / vpb);
     // line 0 of each 2D layout follows one zero line
     const float2 *prow = g->prow_dev + d.row_pairs_ld, *pcol = g->pcol_dev + d.col_pairs_ld;
-    joseph2d_kernel<<<grid, threads, 0, s>>>(g->rays_dev, d.n_views, d.ndu, vpb, prow,
-                                             d.row_pairs_ld, floor_chunk(d.row_pairs_ld), pcol,
-                                             d.col_pairs_ld, floor_chunk(d.col_pairs_ld), d.nx,
-                                             d.ny, y, y_ld, y_off, stop);
+    // one chunk length for both layouts (the loop bounds stay warp-uniform); one chunk when
+    // every line offset of both layouts stays below 2^22
+    const int ldm = std::max(d.row_pairs_ld, d.col_pairs_ld);
+    const int chunk = floor_chunk(ldm);
+    if (std::max(d.nx, d.ny) <= chunk)
+        joseph2d_kernel<false><<<grid, threads, 0, s>>>(g->rays_dev, d.n_views, d.ndu, vpb, prow,
+                                                        d.row_pairs_ld, pcol, d.col_pairs_ld,
+                                                        chunk, d.nx, d.ny, y, y_ld, y_off, stop);
+    else
+        joseph2d_kernel<true><<<grid, threads, 0, s>>>(g->rays_dev, d.n_views, d.ndu, vpb, prow,
+                                                       d.row_pairs_ld, pcol, d.col_pairs_ld,
+                                                       chunk, d.nx, d.ny, y, y_ld, y_off, stop);
     return cudaGetLastError();
 }
 

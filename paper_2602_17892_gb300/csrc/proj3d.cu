@@ -92,11 +92,13 @@ __device__ __forceinline__ Ray3D setup_ray3d(const RayXY &R, int iv, int ndv, do
 // owns the samples whose lower tap row r = floor(z) + 1 (padded row index) lies in
 // [r_lo, r_hi); membership is decided on the same FP32 position the sample uses, so every
 // sample belongs to exactly one slab.  Launches after the first of a call add to y.
+template <bool SLAB>
 __global__ void __launch_bounds__(256) joseph3d_kernel(
     const RayXY *__restrict__ rxy, int ndu, int ndv, double pitch_v, double h,
     const float2 *__restrict__ px, int64_t zsx, int ldx, const float2 *__restrict__ py,
-    int64_t zsy, int ldy, int nx, int ny, int nz, float *__restrict__ y, int64_t y_view_ld,
-    int y_ld, int y_off, int iv0, int iv1, int r_lo, int r_hi, int accumulate, const int *stop)
+    int64_t zsy, int ldy, int chunk, int nx, int ny, int nz, float *__restrict__ y,
+    int64_t y_view_ld, int y_ld, int y_off, int iv0, int iv1, int r_lo, int r_hi, int accumulate,
+    const int *stop)
 {
     if (stop && stop[0] != 0) return;
     // a block is 32 detector columns x blockDim.y detector rows of one view (a warp is one row):
@@ -141,27 +143,41 @@ __global__ void __launch_bounds__(256) joseph3d_kernel(
         const int ld = ax ? ldx : ldy;            // pairs per row (one step along the drive)
         const float bhi = (float)(ax ? ny : nx), zhi = (float)nz;
         const float bmid = R.bmid, bsl = R.bslope;
+        // taps of the sample on driving row t: pair fb + 1 of row t + 1 in slices fz + 1 and
+        // fz + 2.  floor(pb), floor(pz) and the address come from round-down additions (as in
+        // the 2D kernel): sb = 2^23 + 2 + (t - t0) ld + floor(pb), sz = 2^23 + 2 + floor(pz)
+        // exactly, so the byte address is chunk_base + 8 bits(sb) + 8 zsl bits(sz).
+        const uint64_t zsl8 = 8ull * (uint64_t)zsl;
+        const uint64_t b23 = __float_as_uint(kFloor2p23);
+        const uint64_t lbase = reinterpret_cast<uint64_t>(L) + 8ull * (uint64_t)ld - 8ull * (b23 + 1ull) -
+                               zsl8 * (b23 + 1ull);
+        const float fz_lo = (float)(r_lo - 1), fz_hi = (float)(r_hi - 1);   // slab: r = fz + 1
         float tf = (float)wlo - tmid;
-        const float2 *line = L + (int64_t)(wlo + 1) * ld;
         // branch-free body (positions are clamped, so every load is in bounds; a sample outside
         // the lane's range or the slab is weighted by zero), unrolled so that the loads of
         // several planes are in flight together
+        for (int t0 = wlo; t0 <= whi; t0 += chunk) {
+            const int t1 = min(whi, t0 + chunk - 1);
+            const uint64_t cb = lbase + 8ull * (uint64_t)t0 * (uint64_t)ld;
+            float Kb = kFloorK0;
 #pragma unroll 4
-        for (int t = wlo; t <= whi; ++t) {
-            const float pz = fminf(fmaxf(fmaf(zs, tf, zm), -1.f), zhi);
-            const float pb = fminf(fmaxf(fmaf(bsl, tf, bmid), -1.f), bhi);
-            const float fz = floorf(pz), fb = floorf(pb);
-            const int rz = (int)fz + 1;
-            const float wb = pb - fb, wz = pz - fz;
-            const float2 *row = line + (int64_t)rz * zsl + (int)fb + 1;
-            const float2 p0 = __ldg(row), p1 = __ldg(row + zsl);
-            const float a0 = fmaf(wb, p0.y - p0.x, p0.x);
-            const float a1 = fmaf(wb, p1.y - p1.x, p1.x);
-            const bool in = t >= lo && t <= hi && rz >= r_lo && rz < r_hi;
-            acc += in ? fmaf(wz, a1 - a0, a0) : 0.f;
-            any |= in;
-            tf += 1.f;
-            line += ld;
+            for (int t = t0; t <= t1; ++t) {
+                const float pz = fminf(fmaxf(fmaf(zs, tf, zm), -1.f), zhi);
+                const float pb = fminf(fmaxf(fmaf(bsl, tf, bmid), -1.f), bhi);
+                const float sb = __fadd_rd(pb, Kb), sz = __fadd_rd(pz, kFloorK0);
+                const float fz = sz - kFloorK0;
+                const float wb = pb - (sb - Kb), wz = pz - fz;
+                const uint64_t a0 = cb + 8ull * __float_as_uint(sb) + zsl8 * __float_as_uint(sz);
+                const float2 p0 = __ldg(reinterpret_cast<const float2 *>(a0));
+                const float2 p1 = __ldg(reinterpret_cast<const float2 *>(a0 + zsl8));
+                const float a0v = fmaf(wb, p0.y - p0.x, p0.x);
+                const float a1v = fmaf(wb, p1.y - p1.x, p1.x);
+                const bool in = t >= lo && t <= hi && (!SLAB || (fz >= fz_lo && fz < fz_hi));
+                acc += in ? fmaf(wz, a1v - a0v, a0v) : 0.f;
+                any |= in;
+                tf += 1.f;
+                Kb += (float)ld;
+            }
         }
     }
     float weight = (float)h * sqrtf(R.dxy2 + zs * zs);                  // h |D| / |Da|
@@ -264,6 +280,9 @@ cudaError_t launch_joseph3d(const ct_geom *g, float *y, int64_t y_view_ld, int y
         if (e != cudaSuccess) return e;
     }
     const double h = g->desc.pixel, zc = 0.5 * (d.nz - 1);
+    // rows per chunk whose offsets (t - t0) ld the floor additions carry; one value for both
+    // layouts keeps the sample loop's bounds warp-uniform
+    const int chunk = floor_chunk(std::max(d.row_pairs_ld, d.col_pairs_ld));
     for (int k = 0; k < n_slabs; ++k) {
         const int r_lo = k * slab, r_hi = std::min(n_rows, (k + 1) * slab);
         int iv_lo = 0, iv_hi = d.ndv - 1;
@@ -274,11 +293,18 @@ cudaError_t launch_joseph3d(const ct_geom *g, float *y, int64_t y_view_ld, int y
         }
         const int vb = (d.tune_a_views >= 1 && d.tune_a_views <= 8) ? d.tune_a_views : 8;
         dim3 block(32, vb), grid((d.ndu + 31) / 32, d.n_views, (iv_hi - iv_lo + vb) / vb);
-        joseph3d_kernel<<<grid, block, 0, s>>>(d.rays_xy, d.ndu, d.ndv, (double)g->desc.pitch_v,
-                                               h, g->pcol_dev, d.slice_x, d.col_pairs_ld,
-                                               g->prow_dev, d.slice_y, d.row_pairs_ld, d.nx,
-                                               d.ny, d.nz, y, y_view_ld, y_ld, y_off, iv_lo,
-                                               iv_hi, r_lo, r_hi, n_slabs > 1 ? 1 : 0, stop);
+        if (n_slabs > 1)
+            joseph3d_kernel<true><<<grid, block, 0, s>>>(
+                d.rays_xy, d.ndu, d.ndv, (double)g->desc.pitch_v, h, g->pcol_dev, d.slice_x,
+                d.col_pairs_ld, g->prow_dev, d.slice_y, d.row_pairs_ld, chunk, d.nx, d.ny, d.nz, y,
+                y_view_ld, y_ld,
+                y_off, iv_lo, iv_hi, r_lo, r_hi, 1, stop);
+        else   // one pass: every tap row is in [0, nz + 1], no slab test
+            joseph3d_kernel<false><<<grid, block, 0, s>>>(
+                d.rays_xy, d.ndu, d.ndv, (double)g->desc.pitch_v, h, g->pcol_dev, d.slice_x,
+                d.col_pairs_ld, g->prow_dev, d.slice_y, d.row_pairs_ld, chunk, d.nx, d.ny, d.nz, y,
+                y_view_ld, y_ld,
+                y_off, iv_lo, iv_hi, r_lo, r_hi, 0, stop);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -136,12 +136,15 @@ def test_small_parallel_ab_gcv_matches_oracle():
     xg, info = _gpu_solve("ab", G, b, 30, "gcv")
     ref = _oracle("ab", g, b, 30, "gcv")
     assert info["status"] == "CT_OK" and info["iters_done"] == 30
-    assert rel(xg, ref["x"]) <= ITER_TOL
     # GCV is flat near its minimum, so the FP32-perturbed projected problem may move the
-    # argument by a few per cent: compare the GCV value the GPU's lambda attains on the oracle's
-    # projected problem with the oracle's minimum (unique).  Projected residuals at a given
-    # lambda are not compared per step: with sigma_min(H_k) ~ 1e-4 sigma_1 they move by ~1e-3
-    # between an FP32 and an FP64 Krylov basis, while the regularised iterate does not.
+    # argument by a few per cent (and the iterate with it by ~1e-4 after 30 steps): the GPU
+    # iterate is compared with the oracle's iterate at the lambda the GPU's GCV chose, and that
+    # choice by the GCV value it attains on the oracle's projected problem against the oracle's
+    # minimum (unique).  Projected residuals at a given lambda are not compared per step: with
+    # sigma_min(H_k) ~ 1e-4 sigma_1 they move by ~1e-3 between an FP32 and an FP64 Krylov
+    # basis, while the regularised iterate does not.
+    ref_g = _oracle("ab", g, b, 30, "fixed", lam_fixed=info["lambdas"][-1])
+    assert rel(xg, ref_g["x"]) <= ITER_TOL
     for k in range(1, 31):
         s, c, _ = OS.projected_svd(ref["H"][: k + 1, :k], ref["beta"])
         g_gpu = OS.gcv_value(info["lambdas"][k - 1], s, c)
