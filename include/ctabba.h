@@ -198,14 +198,14 @@ typedef struct {
     int a_slab;      /* 3D Joseph A: z-slab thickness (tap rows) of one pass; each pass
                         reads one slab of the volume's pair layouts, so it stays in L2    */
     int b_rows;      /* 2D pixel-driven B: pixel rows per block                           */
-    int b_px;        /* 2D pixel-driven B: pixels per thread (1 or 2, 32 columns apart);
-                        a block is 32 b_px pixels wide                                      */
+    int b_views;     /* 2D pixel-driven B: views per loop iteration (1, or 2 with paired FP32
+                        arithmetic; the same operations, so results do not change)         */
 } ct_launch_shapes;
 
 /* Time the candidate launch shapes of the projectors on this geometry and keep the fastest for
  * later calls on `g`.  2D: Joseph A with (rays, views) per block in (128, 1), (256, 1),
  * (512, 1), (128, 2), (256, 2), (256, 4), (512, 4), (512, 8); pixel-driven B with 4, 8 or 16
- * pixel rows per block and 1 or 2 pixels per thread.  3D: Joseph (slab thickness, detector
+ * pixel rows per block and 1 or 2 views per loop iteration.  3D: Joseph (slab thickness, detector
  * rows per block) in (16, 1), (16, 4), (16, 8), (64, 4), (64, 8) and one pass over the whole
  * volume with 1, 4 or 8 rows (the voxel-driven
  * B has one shape, 32 x 4 columns of 8 voxels).  The shapes change only the order of work, not
@@ -213,6 +213,15 @@ typedef struct {
  * Runs a few dozen projector launches on `stream`, synchronises it, and allocates two temporary
  * device buffers.  The chosen shapes are written to *out (may be NULL). */
 ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_shapes *out);
+/* Set the projectors' launch shapes of `g` explicitly (for instance a shape an earlier autotune
+ * found, or a fixed one for timing).  Values: a_threads in {128, 256, 512} with a_threads /
+ * a_views >= 32 and a_views in {1, 2, 4, 8} (2D), a_slab >= 1 (3D; >= nz + 1 is one pass),
+ * a_views in 1..8 detector rows (3D), b_rows in {4, 8, 16}, b_views in {1, 2}; anything else
+ * returns CT_EINVAL and leaves `g` unchanged.  Host-only; shapes change the order of work, not a
+ * sample's arithmetic. */
+ct_status ct_geom_set_launch_shapes(ct_geom *g, const ct_launch_shapes *shapes);
+/* The launch shapes `g` uses now. */
+ct_status ct_geom_get_launch_shapes(const ct_geom *g, ct_launch_shapes *out);
 
 /* ------------------------------------------------------------------ batched solves */
 

@@ -66,7 +66,7 @@ class PhaseTime(ctypes.Structure):
 
 class LaunchShapes(ctypes.Structure):
     _fields_ = [("a_threads", ctypes.c_int), ("a_views", ctypes.c_int), ("a_slab", ctypes.c_int),
-                ("b_rows", ctypes.c_int), ("b_px", ctypes.c_int)]
+                ("b_rows", ctypes.c_int), ("b_views", ctypes.c_int)]
 
 
 class HybridInfo(ctypes.Structure):
@@ -114,6 +114,8 @@ def load(path: str = LIB_PATH):
     lib.ct_launch_count.restype = ctypes.c_int64
     lib.ct_launch_count.argtypes = []
     lib.ct_geom_autotune.argtypes = [vp, vp, ctypes.POINTER(LaunchShapes)]
+    lib.ct_geom_set_launch_shapes.argtypes = [vp, ctypes.POINTER(LaunchShapes)]
+    lib.ct_geom_get_launch_shapes.argtypes = [vp, ctypes.POINTER(LaunchShapes)]
     lib.ct_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(HybridOpts), ctypes.c_int, ctypes.POINTER(vp)]
     lib.ct_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
@@ -341,12 +343,25 @@ def ct_launch_count() -> int:
     return int(load().ct_launch_count())
 
 
+def ct_geom_set_launch_shapes(g: Geom, shapes: dict):
+    sh = LaunchShapes(int(shapes["a_threads"]), int(shapes["a_views"]), int(shapes["a_slab"]),
+                      int(shapes["b_rows"]), int(shapes["b_views"]))
+    _check(load().ct_geom_set_launch_shapes(g.handle, ctypes.byref(sh)))
+
+
+def ct_geom_get_launch_shapes(g: Geom) -> dict:
+    sh = LaunchShapes()
+    _check(load().ct_geom_get_launch_shapes(g.handle, ctypes.byref(sh)))
+    return {"a_threads": sh.a_threads, "a_views": sh.a_views, "a_slab": sh.a_slab,
+            "b_rows": sh.b_rows, "b_views": sh.b_views}
+
+
 def ct_geom_autotune(g: Geom, stream=None) -> dict:
     """Time the projector launch shapes on this geometry; returns the chosen shapes."""
     sh = LaunchShapes()
     _check(load().ct_geom_autotune(g.handle, _stream(stream), ctypes.byref(sh)))
     return {"a_threads": sh.a_threads, "a_views": sh.a_views, "a_slab": sh.a_slab,
-            "b_rows": sh.b_rows, "b_px": sh.b_px}
+            "b_rows": sh.b_rows, "b_views": sh.b_views}
 
 
 def _info_dict(inf):

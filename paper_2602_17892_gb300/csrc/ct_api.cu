@@ -410,7 +410,7 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     dg.tune_a_threads = 256;
     dg.tune_a_views = cone ? 8 : 1;
     dg.tune_b_rows = cone ? 4 : 8;
-    dg.tune_b_px = 1;
+    dg.tune_b_views = 1;
     dg.b_noclamp = cone ? 0 : (pixels_inside_detector(&g->desc) ? 1 : 0);
     dg.tune_a_slab = 16;
 
@@ -1141,8 +1141,39 @@ static ct_launch_shapes shapes_of(const DeviceGeom &d)
     r.a_views = d.tune_a_views;
     r.a_slab = d.tune_a_slab;
     r.b_rows = d.tune_b_rows;
-    r.b_px = d.tune_b_px;
+    r.b_views = d.tune_b_views;
     return r;
+}
+
+extern "C" ct_status ct_geom_set_launch_shapes(ct_geom *g, const ct_launch_shapes *sh)
+{
+    if (!g || !sh) return einval("ct_geom_set_launch_shapes: null argument");
+    const bool cone = g->desc.kind == CT_CONE3D;
+    const auto in = [](int v, std::initializer_list<int> set) {
+        for (int u : set) if (v == u) return true;
+        return false;
+    };
+    bool ok = in(sh->b_rows, {4, 8, 16}) && in(sh->b_views, {1, 2});
+    if (cone)
+        ok = ok && sh->a_slab >= 1 && sh->a_views >= 1 && sh->a_views <= 8;
+    else
+        ok = ok && in(sh->a_threads, {128, 256, 512}) && in(sh->a_views, {1, 2, 4, 8}) &&
+             sh->a_threads / sh->a_views >= 32;
+    if (!ok) return einval("ct_geom_set_launch_shapes: launch shape out of range");
+    DeviceGeom &dg = g->dg;
+    dg.tune_a_threads = sh->a_threads;
+    dg.tune_a_views = sh->a_views;
+    dg.tune_a_slab = sh->a_slab;
+    dg.tune_b_rows = sh->b_rows;
+    dg.tune_b_views = sh->b_views;
+    return CT_OK;
+}
+
+extern "C" ct_status ct_geom_get_launch_shapes(const ct_geom *g, ct_launch_shapes *out)
+{
+    if (!g || !out) return einval("ct_geom_get_launch_shapes: null argument");
+    *out = shapes_of(g->dg);
+    return CT_OK;
 }
 
 extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_shapes *out)
@@ -1163,7 +1194,7 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
             dg.tune_a_views = it->second.a_views;
             dg.tune_a_slab = it->second.a_slab;
             dg.tune_b_rows = it->second.b_rows;
-            dg.tune_b_px = it->second.b_px;
+            dg.tune_b_views = it->second.b_views;
             if (out) *out = it->second;
             return CT_OK;
         }
@@ -1201,7 +1232,8 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
         return CT_OK;
     };
     // 2D Joseph A: (rays per block, views per block); 3D: z-slab thickness of the Joseph passes;
-    // 2D B: pixel rows per 32-wide block (the 3D backprojector has one shape)
+    // 2D B: (pixel rows per 32-wide block, views per loop iteration); the 3D backprojector has
+    // one shape
     static const int a2[8][2] = {{128, 1}, {256, 1}, {512, 1}, {128, 2},
                                  {256, 2}, {256, 4}, {512, 4}, {512, 8}};
     // 3D: (z-slab thickness, detector rows per block); 1 << 20 = one pass over the volume
@@ -1216,7 +1248,7 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
         st = time_best(fwd, 8, [&](int c) { dg.tune_a_threads = a2[c][0]; dg.tune_a_views = a2[c][1]; });
     if (st == CT_OK && !cone)
         st = time_best([&]() { return launch_back_proj(g, y, x, nullptr, s); }, 6,
-                       [&](int c) { dg.tune_b_rows = b2[c][0]; dg.tune_b_px = b2[c][1]; });
+                       [&](int c) { dg.tune_b_rows = b2[c][0]; dg.tune_b_views = b2[c][1]; });
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(x);

@@ -62,8 +62,8 @@ struct DeviceGeom {
     int sino_ld;        // padded sinogram row length: ndu + 4 (2 zero bins each side)
     int tune_a_threads; // Joseph A: rays (threads) per block, chosen by ct_geom_autotune
     int tune_a_views;   // 2D Joseph A: views per block (each warp one view)
-    int tune_b_rows;    // pixel-driven B: block of 32 tune_b_px x tune_b_rows pixels
-    int tune_b_px;      // 2D pixel-driven B: pixels per thread (1 or 2, 32 columns apart)
+    int tune_b_rows;    // pixel-driven B: block of 32 x tune_b_rows pixels
+    int tune_b_views;   // 2D pixel-driven B: views per loop iteration (1, or 2 in paired FP32)
     int b_noclamp;      // 2D: every pixel centre projects inside the detector in every view
     int tune_a_slab;    // 3D Joseph A: z slab thickness (tap rows) per launch
     int64_t sino_view_ld; // floats per view in the padded sinogram (2D: sino_ld; 3D: (ndv + 2)

@@ -249,95 +249,141 @@ cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, con
 }
 
 // ---------------------------------------------------------------------------- pixel-driven B
-// One thread per PX pixels of a row (columns c, c + 32, ...), blocks of 32 PX x tune_b_rows
-// pixels, per-view constants staged in shared memory.
+// One thread per pixel, blocks of 32 x tune_b_rows pixels, per-view constants staged in shared
+// memory.
 // Parallel: bin position fj = a (c - cm) + b (r - rm) + (nd-1)/2, weight h^2/pitch.
 // Fan:      pe = p.e_u, bb = SID - p.(cos, sin) (in units of h), u = SDD pe / bb,
 //           weight h SDD / pitch * sqrt(1 + (pe/bb)^2) / bb  (= h^2 (SDD^2+u^2)/(L pitch SDD)).
-// Each pixel's terms are formed exactly as with one pixel per thread, so the launch shape never
-// changes a result.
+// VP = 2 takes two views per loop iteration with paired FP32 arithmetic (one fma.f32x2 forms
+// both views' values; the kernel is issue-bound), in the same operations and order as VP = 1,
+// so the launch shape never changes a result.
+// floor(fj) and the pair address come from one round-down addition (as in the Joseph kernel):
+// K = 2^23 + (v - v0) ld over chunks of views; fj >= 0 in the padded row.
 // CLAMP = false when every pixel centre of the image projects inside the detector in every
 // view (checked on the host at geometry creation): the bin positions then need no clamp.
-template <bool FAN, bool CLAMP, int PX>
+template <bool FAN, bool CLAMP>
+__device__ __forceinline__ void pixbp2d_view(const float4 V, float tc, float tr, float gam,
+                                             float hi, float sid_h, float k_u, float K,
+                                             uint64_t rb, float &acc)
+{
+    float fj, w;
+    if (FAN) {
+        const float pe = fmaf(tr, V.x, -tc * V.y);
+        const float bb = fmaf(-tc, V.x, fmaf(-tr, V.y, sid_h));
+        const float rbb = __fdividef(1.f, bb);
+        const float t1 = pe * rbb;
+        fj = fmaf(t1, k_u, gam);
+        w = rbb * sqrtf(fmaf(t1, t1, 1.f));
+    } else {
+        fj = fmaf(V.z, tc, fmaf(V.w, tr, gam));
+        w = 1.f;
+    }
+    if (CLAMP) fj = fminf(fmaxf(fj, 0.f), hi);
+    const float sk = __fadd_rd(fj, K);
+    const float f = fj - (sk - K);
+    const float2 ab = __ldg(reinterpret_cast<const float2 *>(rb + 8ull * __float_as_uint(sk)));
+    acc = fmaf(w, fmaf(f, ab.y - ab.x, ab.x), acc);
+}
+
+template <bool FAN, bool CLAMP, int VP>
 __global__ void __launch_bounds__(512) pixbp2d_kernel(
     const ViewBP *__restrict__ views, int n_views, const float2 *__restrict__ ypair, int ld,
     int vchunk, int nd, int nx, int ny, float sid_h, float k_u, float k_w, float w_par,
     float *__restrict__ x, const int *stop)
 {
     if (stop && stop[0] != 0) return;
+    // VP = 1: sview[v] = (cos, sin, a, b); VP = 2: view pair j as (cos_2j, cos_2j+1,
+    // sin_2j, sin_2j+1) (fan) or (a_2j, a_2j+1, b_2j, b_2j+1) (parallel), then view v as above
     extern __shared__ float4 sview[];
     const int nthr = blockDim.x * blockDim.y;
+    const int npair = (VP == 2) ? n_views / 2 : 0;
+    float4 *sv1 = sview + npair;
     for (int v = threadIdx.y * 32 + threadIdx.x; v < n_views; v += nthr) {
-        ViewBP vb = views[v];
-        sview[v] = make_float4(vb.cs, vb.sn, vb.a, vb.b);
+        const ViewBP vb = views[v];
+        sv1[v] = make_float4(vb.cs, vb.sn, vb.a, vb.b);
+    }
+    for (int j = threadIdx.y * 32 + threadIdx.x; j < npair; j += nthr) {
+        const ViewBP p = views[2 * j], q = views[2 * j + 1];
+        sview[j] = FAN ? make_float4(p.cs, q.cs, p.sn, q.sn) : make_float4(p.a, q.a, p.b, q.b);
     }
     __syncthreads();
-    const int c0 = blockIdx.x * (32 * PX) + threadIdx.x;
+    const int c = blockIdx.x * 32 + threadIdx.x;
     const int r = blockIdx.y * blockDim.y + threadIdx.y;
-    if (c0 >= nx || r >= ny) return;
-    bool valid[PX];
-#pragma unroll
-    for (int p = 0; p < PX; ++p) valid[p] = c0 + 32 * p < nx;
-    const float tc = (float)c0 - 0.5f * (float)(nx - 1);
+    if (c >= nx || r >= ny) return;
+    const float tc = (float)c - 0.5f * (float)(nx - 1);
     const float tr = (float)r - 0.5f * (float)(ny - 1);
     const float gam = 0.5f * (float)(nd - 1) + 2.f;   // +2: padded row offset
     const float hi = (float)(nd + 2);
-    float acc[PX];
-#pragma unroll
-    for (int p = 0; p < PX; ++p) acc[p] = 0.f;
-    // floor(fj) and the pair address from one round-down addition (as in the Joseph kernel):
-    // K = 2^23 + (v - v0) ld over chunks of views; fj >= 0 in the padded row
     const uint64_t ybase = reinterpret_cast<uint64_t>(ypair) - 8ull * __float_as_uint(kFloor2p23);
-    for (int v0 = 0; v0 < n_views; v0 += vchunk) {
+    float acc = 0.f;
+    int v = 0;
+    if (VP == 2) {
+        // view pairs (2j, 2j + 1): both views' positions, weights and floors in paired FP32
+        const float2 tc2 = make_float2(tc, tc), tr2 = make_float2(tr, tr);
+        const float2 ntc2 = make_float2(-tc, -tc), ntr2 = make_float2(-tr, -tr);
+        const float2 sid2 = make_float2(sid_h, sid_h), ku2 = make_float2(k_u, k_u);
+        const float2 gam2 = make_float2(gam, gam), one2 = make_float2(1.f, 1.f);
+        const float2 m1 = make_float2(-1.f, -1.f);
+        const int vch = vchunk & ~1;
+        for (int v0 = 0; v0 < 2 * npair; v0 += vch) {
+            const int v1 = min(2 * npair, v0 + vch);
+            const uint64_t rb = ybase + 8ull * (uint64_t)v0 * (uint64_t)ld;
+            float2 K2 = make_float2(kFloor2p23, kFloor2p23 + (float)ld);
+            const float2 dK2 = make_float2(2.f * (float)ld, 2.f * (float)ld);
+#pragma unroll 2
+            for (int vv = v0; vv < v1; vv += 2) {
+                const float4 V = sview[vv >> 1];
+                float2 fj2, w2;
+                if (FAN) {
+                    const float2 cs2 = make_float2(V.x, V.y), sn2 = make_float2(V.z, V.w);
+                    const float2 pe2 = __ffma2_rn(tr2, cs2, __fmul2_rn(ntc2, sn2));
+                    const float2 bb2 = __ffma2_rn(ntc2, cs2, __ffma2_rn(ntr2, sn2, sid2));
+                    const float2 rb2 = make_float2(__fdividef(1.f, bb2.x), __fdividef(1.f, bb2.y));
+                    const float2 t12 = __fmul2_rn(pe2, rb2);
+                    fj2 = __ffma2_rn(t12, ku2, gam2);
+                    const float2 s2 = __ffma2_rn(t12, t12, one2);
+                    w2 = __fmul2_rn(rb2, make_float2(sqrtf(s2.x), sqrtf(s2.y)));
+                } else {
+                    fj2 = __ffma2_rn(make_float2(V.x, V.y), tc2,
+                                     __ffma2_rn(make_float2(V.z, V.w), tr2, gam2));
+                    w2 = one2;
+                }
+                if (CLAMP) fj2 = make_float2(fminf(fmaxf(fj2.x, 0.f), hi), fminf(fmaxf(fj2.y, 0.f), hi));
+                const float2 sk2 = __fadd2_rd(fj2, K2);
+                const float2 f2 = __ffma2_rn(__ffma2_rn(K2, m1, sk2), m1, fj2);   // fj - (sk - K)
+                const float2 a = __ldg(reinterpret_cast<const float2 *>(rb + 8ull * __float_as_uint(sk2.x)));
+                const float2 b = __ldg(reinterpret_cast<const float2 *>(rb + 8ull * __float_as_uint(sk2.y)));
+                acc = fmaf(w2.x, fmaf(f2.x, a.y - a.x, a.x), acc);
+                acc = fmaf(w2.y, fmaf(f2.y, b.y - b.x, b.x), acc);
+                K2 = __fadd2_rn(K2, dK2);
+            }
+        }
+        v = 2 * npair;
+    }
+    for (int v0 = v; v0 < n_views; v0 += vchunk) {
         const int v1 = min(n_views, v0 + vchunk);
         const uint64_t rb = ybase + 8ull * (uint64_t)v0 * (uint64_t)ld;
         float K = kFloor2p23;
 #pragma unroll 4
-        for (int v = v0; v < v1; ++v) {
-            const float4 V = sview[v];
-#pragma unroll
-            for (int p = 0; p < PX; ++p) {
-                const float tcp = tc + 32.f * p;        // exact: integers and half-integers
-                float fj, w;
-                if (FAN) {
-                    const float pe = fmaf(tr, V.x, -tcp * V.y);
-                    const float bb = fmaf(-tcp, V.x, fmaf(-tr, V.y, sid_h));
-                    const float rbb = __fdividef(1.f, bb);
-                    const float t1 = pe * rbb;
-                    fj = fmaf(t1, k_u, gam);
-                    w = rbb * sqrtf(fmaf(t1, t1, 1.f));
-                } else {
-                    fj = fmaf(V.z, tcp, fmaf(V.w, tr, gam));
-                    w = 1.f;
-                }
-                if (CLAMP) fj = fminf(fmaxf(fj, 0.f), hi);
-                const float sk = __fadd_rd(fj, K);
-                const float f = fj - (sk - K);
-                if (PX == 1 || valid[p]) {
-                    // taps j and j + 1 of view v
-                    const float2 ab = __ldg(reinterpret_cast<const float2 *>(rb + 8ull * __float_as_uint(sk)));
-                    acc[p] = fmaf(w, fmaf(f, ab.y - ab.x, ab.x), acc[p]);
-                }
-            }
+        for (int vv = v0; vv < v1; ++vv) {
+            pixbp2d_view<FAN, CLAMP>(sv1[vv], tc, tr, gam, hi, sid_h, k_u, K, rb, acc);
             K += (float)ld;
         }
     }
-#pragma unroll
-    for (int p = 0; p < PX; ++p)
-        if (valid[p]) x[(int64_t)r * nx + c0 + 32 * p] = acc[p] * (FAN ? k_w : w_par);
+    x[(int64_t)r * nx + c] = acc * (FAN ? k_w : w_par);
 }
 
-template <bool FAN, bool CLAMP, int PX>
+template <bool FAN, bool CLAMP, int VP>
 static void launch_pixbp2d_t(const ct_geom *g, const float2 *ypad, float *x, const int *stop,
                              cudaStream_t s)
 {
     const DeviceGeom &d = g->dg;
     const int rows = d.tune_b_rows > 0 ? d.tune_b_rows : 8;
-    dim3 block(32, rows), grid((d.nx + 32 * PX - 1) / (32 * PX), (d.ny + rows - 1) / rows);
-    const size_t smem = sizeof(float4) * (size_t)d.n_views;
+    dim3 block(32, rows), grid((d.nx + 31) / 32, (d.ny + rows - 1) / rows);
+    const size_t smem = sizeof(float4) * (size_t)(d.n_views + (VP == 2 ? d.n_views / 2 : 0));
     const float sid_h = d.sid / d.h, k_u = d.sdd / d.pitch_u, k_w = d.h * d.sdd / d.pitch_u;
     const float w_par = d.h * d.h / d.pitch_u;
-    pixbp2d_kernel<FAN, CLAMP, PX><<<grid, block, smem, s>>>(d.views, d.n_views, ypad, d.sino_ld,
+    pixbp2d_kernel<FAN, CLAMP, VP><<<grid, block, smem, s>>>(d.views, d.n_views, ypad, d.sino_ld,
                                                              floor_chunk(d.sino_ld), d.ndu, d.nx,
                                                              d.ny, sid_h, k_u, k_w, w_par, x, stop);
 }
@@ -346,7 +392,7 @@ cudaError_t launch_pixbp2d(const ct_geom *g, const float2 *ypad, float *x, const
                            cudaStream_t s)
 {
     const DeviceGeom &d = g->dg;
-    const bool fan = d.kind == CT_FANFLAT2D, clamp = !d.b_noclamp, two = d.tune_b_px == 2;
+    const bool fan = d.kind == CT_FANFLAT2D, clamp = !d.b_noclamp, two = d.tune_b_views == 2;
     if (fan) {
         if (clamp) two ? launch_pixbp2d_t<true, true, 2>(g, ypad, x, stop, s)
                        : launch_pixbp2d_t<true, true, 1>(g, ypad, x, stop, s);

@@ -72,6 +72,13 @@ def test_solver_rejects_bad_options(lib):
     assert st == Bn.CT_EINVAL
 
 
+def test_launch_shape_entry_points_reject_null_arguments(lib):
+    from paper_2602_17892_gb300 import _binding as Bn
+    sh = Bn.LaunchShapes(256, 1, 16, 8, 1)
+    assert lib.ct_geom_set_launch_shapes(None, ctypes.byref(sh)) == Bn.CT_EINVAL
+    assert lib.ct_geom_get_launch_shapes(None, ctypes.byref(sh)) == Bn.CT_EINVAL
+
+
 def test_learned_lambda_entry_points_reject_bad_arguments(lib):
     from paper_2602_17892_gb300 import _binding as Bn
     o = Bn.HybridOpts()

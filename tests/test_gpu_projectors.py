@@ -63,3 +63,24 @@ def test_projectors_are_linear_and_unmatched():
     rhs_at = float(x1 @ OP.back_adjoint(g, y1).reshape(-1))
     assert abs(lhs - rhs_at) <= 1e-5 * abs(lhs) + 1e-3
     assert abs(lhs - rhs_bt) > 1e-4 * abs(lhs)      # B is not A^T
+
+
+@pytest.mark.parametrize("name", ["fan_64", "fan_ragged_50x33", "parallel_ragged_37x45"])
+def test_launch_shapes_leave_results_bitwise_unchanged(name):
+    """Every 2D launch shape (rays and views per Joseph block; pixel rows per B block and one or
+    two views per B iteration) computes each ray and pixel with the same operations in the same
+    order: A and B agree bit for bit across shapes."""
+    from paper_2602_17892_gb300 import ct_geom_get_launch_shapes, ct_geom_set_launch_shapes
+    g = GEOMS[name]
+    G = gpu_geom(g)
+    x = f32(synth.standard_normal(g.n, 21))
+    y = f32(synth.standard_normal(g.m, 22))
+    base = ct_geom_get_launch_shapes(G)
+    ya, xb = gpu_A(G, x), gpu_B(G, y)
+    for a_threads, a_views in ((128, 1), (256, 2), (512, 8)):
+        for b_rows, b_views in ((4, 1), (8, 2), (16, 2)):
+            sh = dict(base, a_threads=a_threads, a_views=a_views, b_rows=b_rows, b_views=b_views)
+            ct_geom_set_launch_shapes(G, sh)
+            assert ct_geom_get_launch_shapes(G) == sh
+            assert np.array_equal(gpu_A(G, x), ya)
+            assert np.array_equal(gpu_B(G, y), xb)
