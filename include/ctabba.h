@@ -192,19 +192,22 @@ ct_status ba_gmres_hybrid_restarted(ct_geom *g, const float *b_dev, float *x_dev
 
 /* Launch shapes of the projector kernels of a geometry. */
 typedef struct {
-    int a_threads;   /* 2D Joseph A: rays (threads) per block                             */
-    int a_views;     /* Joseph A: 2D, consecutive views per block (each warp one view);
-                        3D, detector rows per block of 32 columns (each warp one row)       */
+    int a_threads;   /* 2D Joseph A: threads per block                                    */
+    int a_views;     /* Joseph A: 2D, warp rows per block (each warp one view, or two
+                        adjacent views when a_rays = 2); 3D, detector rows per block of 32
+                        columns (each warp one row)                                         */
     int a_slab;      /* 3D Joseph A: z-slab thickness (tap rows) of one pass; each pass
                         reads one slab of the volume's pair layouts, so it stays in L2    */
     int b_rows;      /* 2D pixel-driven B: pixel rows per block                           */
     int b_views;     /* 2D pixel-driven B: views per loop iteration (1, or 2 with paired FP32
                         arithmetic; the same operations, so results do not change)         */
+    int a_rays;      /* 2D Joseph A: rays per thread (1, or 2: the same bin in two adjacent
+                        views, in paired FP32 arithmetic; results do not change)           */
 } ct_launch_shapes;
 
 /* Time the candidate launch shapes of the projectors on this geometry and keep the fastest for
- * later calls on `g`.  2D: Joseph A with (rays, views) per block in (128, 1), (256, 1),
- * (512, 1), (128, 2), (256, 2), (256, 4), (512, 4), (512, 8); pixel-driven B with 4, 8 or 16
+ * later calls on `g`.  2D: Joseph A with (threads, warp rows) per block in (128, 1), (128, 2),
+ * (256, 2), (256, 4), each with one or two rays per thread; pixel-driven B with 4, 8 or 16
  * pixel rows per block and 1 or 2 views per loop iteration.  3D: Joseph (slab thickness, detector
  * rows per block) in (16, 1), (16, 4), (16, 8), (64, 4), (64, 8) and one pass over the whole
  * volume with 1, 4 or 8 rows (the voxel-driven
@@ -216,7 +219,7 @@ ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_shapes *out
 /* Set the projectors' launch shapes of `g` explicitly (for instance a shape an earlier autotune
  * found, or a fixed one for timing).  Values: a_threads in {128, 256, 512} with a_threads /
  * a_views >= 32 and a_views in {1, 2, 4, 8} (2D), a_slab >= 1 (3D; >= nz + 1 is one pass),
- * a_views in 1..8 detector rows (3D), b_rows in {4, 8, 16}, b_views in {1, 2}; anything else
+ * a_views in 1..8 detector rows (3D), b_rows in {4, 8, 16}, b_views and a_rays in {1, 2}; anything else
  * returns CT_EINVAL and leaves `g` unchanged.  Host-only; shapes change the order of work, not a
  * sample's arithmetic. */
 ct_status ct_geom_set_launch_shapes(ct_geom *g, const ct_launch_shapes *shapes);

@@ -411,6 +411,7 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     dg.tune_a_views = cone ? 8 : 1;
     dg.tune_b_rows = cone ? 4 : 8;
     dg.tune_b_views = 1;
+    dg.tune_a_rays = 1;
     dg.b_noclamp = cone ? 0 : (pixels_inside_detector(&g->desc) ? 1 : 0);
     dg.tune_a_slab = 16;
 
@@ -1142,6 +1143,7 @@ static ct_launch_shapes shapes_of(const DeviceGeom &d)
     r.a_slab = d.tune_a_slab;
     r.b_rows = d.tune_b_rows;
     r.b_views = d.tune_b_views;
+    r.a_rays = d.tune_a_rays;
     return r;
 }
 
@@ -1153,7 +1155,7 @@ extern "C" ct_status ct_geom_set_launch_shapes(ct_geom *g, const ct_launch_shape
         for (int u : set) if (v == u) return true;
         return false;
     };
-    bool ok = in(sh->b_rows, {4, 8, 16}) && in(sh->b_views, {1, 2});
+    bool ok = in(sh->b_rows, {4, 8, 16}) && in(sh->b_views, {1, 2}) && in(sh->a_rays, {1, 2});
     if (cone)
         ok = ok && sh->a_slab >= 1 && sh->a_views >= 1 && sh->a_views <= 8;
     else
@@ -1166,6 +1168,7 @@ extern "C" ct_status ct_geom_set_launch_shapes(ct_geom *g, const ct_launch_shape
     dg.tune_a_slab = sh->a_slab;
     dg.tune_b_rows = sh->b_rows;
     dg.tune_b_views = sh->b_views;
+    dg.tune_a_rays = sh->a_rays;
     return CT_OK;
 }
 
@@ -1195,6 +1198,7 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
             dg.tune_a_slab = it->second.a_slab;
             dg.tune_b_rows = it->second.b_rows;
             dg.tune_b_views = it->second.b_views;
+            dg.tune_a_rays = it->second.a_rays;
             if (out) *out = it->second;
             return CT_OK;
         }
@@ -1234,8 +1238,9 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
     // 2D Joseph A: (rays per block, views per block); 3D: z-slab thickness of the Joseph passes;
     // 2D B: (pixel rows per 32-wide block, views per loop iteration); the 3D backprojector has
     // one shape
-    static const int a2[8][2] = {{128, 1}, {256, 1}, {512, 1}, {128, 2},
-                                 {256, 2}, {256, 4}, {512, 4}, {512, 8}};
+    // 2D Joseph: (rays per block, warp rows per block, rays per thread)
+    static const int a2[8][3] = {{128, 1, 1}, {128, 2, 1}, {256, 2, 1}, {256, 4, 1},
+                                 {128, 1, 2}, {128, 2, 2}, {256, 2, 2}, {256, 4, 2}};
     // 3D: (z-slab thickness, detector rows per block); 1 << 20 = one pass over the volume
     static const int a3[8][2] = {{16, 1}, {16, 4}, {16, 8}, {64, 4}, {64, 8},
                                  {1 << 20, 1}, {1 << 20, 4}, {1 << 20, 8}};
@@ -1245,7 +1250,11 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
     if (cone)
         st = time_best(fwd, 8, [&](int c) { dg.tune_a_slab = a3[c][0]; dg.tune_a_views = a3[c][1]; });
     else
-        st = time_best(fwd, 8, [&](int c) { dg.tune_a_threads = a2[c][0]; dg.tune_a_views = a2[c][1]; });
+        st = time_best(fwd, 8, [&](int c) {
+            dg.tune_a_threads = a2[c][0];
+            dg.tune_a_views = a2[c][1];
+            dg.tune_a_rays = a2[c][2];
+        });
     if (st == CT_OK && !cone)
         st = time_best([&]() { return launch_back_proj(g, y, x, nullptr, s); }, 6,
                        [&](int c) { dg.tune_b_rows = b2[c][0]; dg.tune_b_views = b2[c][1]; });

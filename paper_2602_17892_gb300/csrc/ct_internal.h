@@ -62,6 +62,7 @@ struct DeviceGeom {
     int sino_ld;        // padded sinogram row length: ndu + 4 (2 zero bins each side)
     int tune_a_threads; // Joseph A: rays (threads) per block, chosen by ct_geom_autotune
     int tune_a_views;   // 2D Joseph A: views per block (each warp one view)
+    int tune_a_rays;    // 2D Joseph A: rays per thread (1, or 2 adjacent views in paired FP32)
     int tune_b_rows;    // pixel-driven B: block of 32 x tune_b_rows pixels
     int tune_b_views;   // 2D pixel-driven B: views per loop iteration (1, or 2 in paired FP32)
     int b_noclamp;      // 2D: every pixel centre projects inside the detector in every view

@@ -184,8 +184,68 @@ __device__ __forceinline__ float joseph2d_span(int ta, int tb, int t_lo, int t_h
     return acc;
 }
 
-// CHUNKED: the lines are walked in chunks of `chunk` (images whose line offsets exceed 2^22)
-template <bool CHUNKED>
+// Two rays per thread (views v and v + 1 at the same bin): positions, floors and weights of
+// both in paired FP32 arithmetic (one fma.f32x2 / add.rm.f32x2 each), the same operations per
+// ray as joseph2d_span, so the results are bitwise those of one ray per thread.
+__device__ __forceinline__ void joseph2d_span2(int ta, int tb, int lo0, int hi0, int lo1, int hi1,
+                                               float2 pmid2, float2 slope2, float2 tmid2,
+                                               int st0, int st1, uint64_t ab0, uint64_t ab1,
+                                               float &acc0, float &acc1)
+{
+    float2 tf2 = make_float2((float)ta - tmid2.x, (float)ta - tmid2.y);
+    float2 K2 = make_float2(kFloorK0, kFloorK0);
+    const float2 dK2 = make_float2((float)st0, (float)st1);
+    const float2 one2 = make_float2(1.f, 1.f), m1 = make_float2(-1.f, -1.f);
+    const uint64_t lb0 = ab0 + 8ull * (uint64_t)ta * (uint64_t)st0;
+    const uint64_t lb1 = ab1 + 8ull * (uint64_t)ta * (uint64_t)st1;
+#pragma unroll 4
+    for (int t = ta; t <= tb; ++t) {
+        const float2 pos2 = __ffma2_rn(slope2, tf2, pmid2);
+        const float2 sk2 = __fadd2_rd(pos2, K2);
+        const float2 f2 = __ffma2_rn(__ffma2_rn(K2, m1, sk2), m1, pos2);   // pos - (sk - K)
+        if (t >= lo0 && t <= hi0) {
+            const float2 p = __ldg(reinterpret_cast<const float2 *>(lb0 + 8ull * __float_as_uint(sk2.x)));
+            acc0 += fmaf(f2.x, p.y - p.x, p.x);
+        }
+        if (t >= lo1 && t <= hi1) {
+            const float2 p = __ldg(reinterpret_cast<const float2 *>(lb1 + 8ull * __float_as_uint(sk2.y)));
+            acc1 += fmaf(f2.y, p.y - p.x, p.x);
+        }
+        tf2 = __fadd2_rn(tf2, one2);
+        K2 = __fadd2_rn(K2, dK2);
+    }
+}
+
+struct JRay {
+    float pmid, slope, tmid, weight;
+    int lo, hi, stride;
+    uint64_t abase;
+};
+
+__device__ __forceinline__ JRay joseph2d_ray(const Ray2D *__restrict__ rays, bool valid,
+                                             int64_t idx, const float2 *prow, int prow_ld,
+                                             const float2 *pcol, int pcol_ld, int nx, int ny)
+{
+    const Ray2D R = rays[valid ? idx : 0];
+    JRay j;
+    j.lo = valid ? (int)(R.packed & 0x7fff) : 1;
+    j.hi = valid ? (int)((R.packed >> 15) & 0x7fff) : 0;
+    const int axis = (R.packed >> 30) & 1;
+    const float2 *base;          // line 0 of the layout the ray reads
+    int n_drive;
+    if (axis == 0) { base = pcol; j.stride = pcol_ld; n_drive = nx; }   // drive along x
+    else { base = prow; j.stride = prow_ld; n_drive = ny; }             // drive along y
+    j.tmid = 0.5f * (float)(n_drive - 1);
+    j.pmid = R.pmid;
+    j.slope = R.slope;
+    j.weight = R.weight;
+    j.abase = reinterpret_cast<uint64_t>(base) - 8ull * ((uint64_t)__float_as_uint(kFloor2p23) + 1ull);
+    return j;
+}
+
+// CHUNKED: the lines are walked in chunks of `chunk` (images whose line offsets exceed 2^22).
+// RP rays per thread: views RP r .. RP r + RP - 1 of warp row r at one bin.
+template <bool CHUNKED, int RP>
 __global__ void __launch_bounds__(512) joseph2d_kernel(
     const Ray2D *__restrict__ rays, int n_views, int ndu, int vpb,
     const float2 *__restrict__ prow, int prow_ld, const float2 *__restrict__ pcol, int pcol_ld,
@@ -194,43 +254,53 @@ __global__ void __launch_bounds__(512) joseph2d_kernel(
     if (stop && stop[0] != 0) return;
     const int bins_pb = blockDim.x / vpb;
     const int bin = blockIdx.x * bins_pb + (int)threadIdx.x % bins_pb;
-    const int view0 = blockIdx.y * vpb + (int)threadIdx.x / bins_pb;
-    const bool valid = bin < ndu && view0 < n_views;   // all lanes stay for the warp range
-    const Ray2D R = rays[valid ? (int64_t)view0 * ndu + bin : 0];
-    int t_lo = R.packed & 0x7fff;
-    int t_hi = (R.packed >> 15) & 0x7fff;
-    if (!valid) { t_lo = 1; t_hi = 0; }
-    const int axis = (R.packed >> 30) & 1;
-    const float2 *base;          // line 0 of the layout the ray reads
-    int stride, n_drive;
-    if (axis == 0) { base = pcol; stride = pcol_ld; n_drive = nx; }   // drive along x
-    else { base = prow; stride = prow_ld; n_drive = ny; }             // drive along y
-    const float tmid = 0.5f * (float)(n_drive - 1);
+    const int row = blockIdx.y * vpb + (int)threadIdx.x / bins_pb;
+    // all lanes stay for the warp range
+    const int v0 = row * RP, v1 = v0 + 1;
+    const bool valid0 = bin < ndu && v0 < n_views, valid1 = RP == 2 && bin < ndu && v1 < n_views;
+    const JRay r0 = joseph2d_ray(rays, valid0, (int64_t)v0 * ndu + bin, prow, prow_ld, pcol,
+                                 pcol_ld, nx, ny);
+    JRay r1 = r0;
+    if (RP == 2)
+        r1 = joseph2d_ray(rays, valid1, (int64_t)v1 * ndu + bin, prow, prow_ld, pcol, pcol_ld,
+                          nx, ny);
+    else
+        r1.lo = 1, r1.hi = 0;
     // the warp steps through the union of its lanes' driving ranges together, so that at every
     // step its lanes read neighbouring pairs of one line (a lane outside its own range idles)
-    const int wlo = __reduce_min_sync(0xffffffffu, t_hi >= t_lo ? t_lo : 0x7fffffff);
-    const int whi = __reduce_max_sync(0xffffffffu, t_hi >= t_lo ? t_hi : -1);
-    const uint64_t abase = reinterpret_cast<uint64_t>(base) -
-                           8ull * ((uint64_t)__float_as_uint(kFloor2p23) + 1ull);
-    float acc = 0.f;
+    int lmin = r0.hi >= r0.lo ? r0.lo : 0x7fffffff, lmax = r0.hi >= r0.lo ? r0.hi : -1;
+    if (RP == 2 && r1.hi >= r1.lo) { lmin = min(lmin, r1.lo); lmax = max(lmax, r1.hi); }
+    const int wlo = __reduce_min_sync(0xffffffffu, lmin);
+    const int whi = __reduce_max_sync(0xffffffffu, lmax);
+    float acc0 = 0.f, acc1 = 0.f;
+    auto span = [&](int ta, int tb) {
+        if (RP == 2)
+            joseph2d_span2(ta, tb, r0.lo, r0.hi, r1.lo, r1.hi, make_float2(r0.pmid, r1.pmid),
+                           make_float2(r0.slope, r1.slope), make_float2(r0.tmid, r1.tmid),
+                           r0.stride, r1.stride, r0.abase, r1.abase, acc0, acc1);
+        else
+            acc0 = joseph2d_span(ta, tb, r0.lo, r0.hi, r0.pmid, r0.slope, r0.tmid, r0.stride,
+                                 r0.abase, acc0);
+    };
     if (!CHUNKED) {
-        acc = joseph2d_span(wlo, whi, t_lo, t_hi, R.pmid, R.slope, tmid, stride, abase, acc);
+        span(wlo, whi);
     } else {
-        for (int t0 = wlo; t0 <= whi; t0 += chunk)
-            acc = joseph2d_span(t0, min(whi, t0 + chunk - 1), t_lo, t_hi, R.pmid, R.slope, tmid,
-                                stride, abase, acc);
+        for (int t0 = wlo; t0 <= whi; t0 += chunk) span(t0, min(whi, t0 + chunk - 1));
     }
-    if (valid) y[(int64_t)view0 * y_ld + y_off + bin] = acc * R.weight;
+    if (valid0) y[(int64_t)v0 * y_ld + y_off + bin] = acc0 * r0.weight;
+    if (RP == 2 && valid1) y[(int64_t)v1 * y_ld + y_off + bin] = acc1 * r1.weight;
 }
 
-cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, const int *stop,
-                            cudaStream_t s)
+template <int RP>
+static void launch_joseph2d_t(const ct_geom *g, float *y, int y_ld, int y_off, const int *stop,
+                              cudaStream_t s)
 {
     const DeviceGeom &d = g->dg;
     const int threads = d.tune_a_threads > 0 ? d.tune_a_threads : 256;
     const int vpb = (d.tune_a_views > 0 && threads / d.tune_a_views >= 32) ? d.tune_a_views : 1;
     const int bins_pb = threads / vpb;
-    dim3 grid((d.ndu + bins_pb - 1) / bins_pb, (d.n_views + vpb - 1) / vpb);
+    const int rows = (d.n_views + RP - 1) / RP;
+    dim3 grid((d.ndu + bins_pb - 1) / bins_pb, (rows + vpb - 1) / vpb);
     // line 0 of each 2D layout follows one zero line
     const float2 *prow = g->prow_dev + d.row_pairs_ld, *pcol = g->pcol_dev + d.col_pairs_ld;
     // one chunk length for both layouts (the loop bounds stay warp-uniform); one chunk when
@@ -238,13 +308,22 @@ cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, con
     const int ldm = std::max(d.row_pairs_ld, d.col_pairs_ld);
     const int chunk = floor_chunk(ldm);
     if (std::max(d.nx, d.ny) <= chunk)
-        joseph2d_kernel<false><<<grid, threads, 0, s>>>(g->rays_dev, d.n_views, d.ndu, vpb, prow,
-                                                        d.row_pairs_ld, pcol, d.col_pairs_ld,
-                                                        chunk, d.nx, d.ny, y, y_ld, y_off, stop);
+        joseph2d_kernel<false, RP><<<grid, threads, 0, s>>>(g->rays_dev, d.n_views, d.ndu, vpb,
+                                                            prow, d.row_pairs_ld, pcol,
+                                                            d.col_pairs_ld, chunk, d.nx, d.ny, y,
+                                                            y_ld, y_off, stop);
     else
-        joseph2d_kernel<true><<<grid, threads, 0, s>>>(g->rays_dev, d.n_views, d.ndu, vpb, prow,
-                                                       d.row_pairs_ld, pcol, d.col_pairs_ld,
-                                                       chunk, d.nx, d.ny, y, y_ld, y_off, stop);
+        joseph2d_kernel<true, RP><<<grid, threads, 0, s>>>(g->rays_dev, d.n_views, d.ndu, vpb,
+                                                           prow, d.row_pairs_ld, pcol,
+                                                           d.col_pairs_ld, chunk, d.nx, d.ny, y,
+                                                           y_ld, y_off, stop);
+}
+
+cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, const int *stop,
+                            cudaStream_t s)
+{
+    if (g->dg.tune_a_rays == 2) launch_joseph2d_t<2>(g, y, y_ld, y_off, stop, s);
+    else launch_joseph2d_t<1>(g, y, y_ld, y_off, stop, s);
     return cudaGetLastError();
 }
 
