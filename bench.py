@@ -4,13 +4,17 @@
 Workload (one "step"): the 512 x 512 fan-beam problem (720 views over 360 deg, 768 bins,
 SID 1000, SDD 1500, 2 % Gaussian noise, seeded ellipse phantom), solved by hybrid AB-GMRES and
 by hybrid BA-GMRES, 100 iterations each, lambda by the discrepancy principle (tau = 1.01).
+The two solves of a step run as one batch (ct_batch: one CUDA graph whose two branches are
+the solves, so the GPU runs them concurrently).
 Metric: solver iterations per second over the whole job.  Inputs are resident in HBM when
 the timed region starts; L2 is flushed (256 MiB write) between timed steps.
 
-Reported beside the metric: per-phase device time (CUDA events on the launching stream),
-projector GUPS, the roofline of the dominant kernel, an end-to-end number through the C ABI
-with host buffers, the GPU clocks seen during the timed region, the FP64 CPU oracle timed
-on a bounded sample of the same workload (with the GPU's error against it), and "variants":
+Reported beside the metric: per-phase device time and the roofline of the dominant kernel
+(CUDA events on the launching stream, from a second timed region that runs the same solves one
+after the other, so that every kernel's duration is its own), projector GUPS, an end-to-end
+number through the C ABI with host buffers, the GPU clocks seen during the timed region, the
+FP64 CPU oracle timed on a bounded sample of the same workload (with the GPU's error against
+it), and "variants":
 the 16-bit Krylov bases, the learned lambda rule, a sample of the uneven batched-slice
 workload under one CUDA graph, and the 512^3 cone workload (FP32 and BF16 basis).
 
@@ -177,16 +181,23 @@ def bench_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     geom, x_true, case = workload(rank)
+    # one geometry object per problem of the batch (each owns its problem's workspace)
     G = P.Geom.from_geometry(geom)
-    shapes = P.ct_geom_autotune(G)              # setup: projector launch shapes for this geometry
+    G_ba = P.Geom.from_geometry(geom)
+    batch = P.Batch([G, G_ba], ["ab", "ba"], max_iters=ITERS, rule="dp", tau=TAU, autotune=True)
+    shapes = P.ct_geom_get_launch_shapes(G)     # setup: projector launch shapes (autotuned)
     b, b_dev, noise_ab, noise_ba = make_data_gpu(P, torch, G, geom, x_true, case, rank)
     x_ab = torch.zeros(G.n, device="cuda")
     x_ba = torch.zeros(G.n, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda", dtype=torch.float32)
     stream = torch.cuda.current_stream()
 
+    def batch_step():
+        infos = batch.solve([b_dev, b_dev], [x_ab, x_ba], [noise_ab, noise_ba])
+        return sum(i["iters_done"] for i in infos)
+
     for _ in range(args.warmup):
-        run_step(P, G, b_dev, x_ab, x_ba, noise_ab, noise_ba)
+        batch_step()
     torch.cuda.synchronize()
 
     if dist:
@@ -195,20 +206,16 @@ def bench_ours(args, rank, world, local_rank):
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
     iters_done = 0
-    launches0 = Bn.ct_launch_count()
-    Bn.ct_profile_enable(True)
     wall0 = time.perf_counter()
     with ClockSampler(local_rank) as clk:
         for i in range(args.steps):
             flush.fill_(float(i))            # L2 flush, outside the events
             evs[i][0].record(stream)
-            iters_done += run_step(P, G, b_dev, x_ab, x_ba, noise_ab, noise_ba)
+            iters_done += batch_step()
             evs[i][1].record(stream)
         torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
-    phases = Bn.ct_profile_collect()
-    Bn.ct_profile_enable(False)
-    launches = Bn.ct_launch_count() - launches0
+    launches = batch.launches() * args.steps
     step_ms = [a.elapsed_time(b_) for a, b_ in evs]
     total_ms = sum(step_ms)
     if dist:
@@ -223,6 +230,24 @@ def bench_ours(args, rank, world, local_rank):
         iters_all = float(iters_done)
     value = iters_all / (total_ms / 1e3)
 
+    # ---- per-kernel timing: the same two solves one after the other, per-phase CUDA events
+    # on the launching stream (inside the batch's graph the two solves' kernels overlap)
+    for _ in range(1):
+        run_step(P, G, b_dev, x_ab, x_ba, noise_ab, noise_ba)
+    torch.cuda.synchronize()
+    seq_ms = 0.0
+    Bn.ct_profile_enable(True)
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        run_step(P, G, b_dev, x_ab, x_ba, noise_ab, noise_ba)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        seq_ms += ea.elapsed_time(eb)
+    phases = Bn.ct_profile_collect()
+    Bn.ct_profile_enable(False)
+
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the region
     b_host = torch.from_numpy(b.astype(np.float32)).pin_memory()
     xa_host = torch.empty(G.n, dtype=torch.float32).pin_memory()
@@ -234,7 +259,7 @@ def bench_ours(args, rank, world, local_rank):
         ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ea.record(stream)
         b_dev.copy_(b_host, non_blocking=True)
-        e2e_iters += run_step(P, G, b_dev, x_ab, x_ba, noise_ab, noise_ba)
+        e2e_iters += batch_step()
         xa_host.copy_(x_ab, non_blocking=True)
         xb_host.copy_(x_ba, non_blocking=True)
         eb.record(stream)
@@ -314,6 +339,8 @@ def bench_ours(args, rank, world, local_rank):
                                "SID 1000, SDD 1500, 2 % noise; hybrid AB + BA, 100 its each, DP",
                    "image": [512, 512], "views": 720, "bins": 768, "iters_per_solve": ITERS,
                    "rule": "dp", "tau": TAU, "l2": "flushed between steps (256 MiB write)",
+                   "execution": "the AB and BA solves as one ct_batch (one CUDA graph, two "
+                                "concurrent branches)",
                    "launch_shapes": shapes,
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": "iters/s",
@@ -322,6 +349,9 @@ def bench_ours(args, rank, world, local_rank):
         "roofline": roof,
         "kernels": kernels,
         "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
+        "sequential_ms_per_step": seq_ms / args.steps,
+        "per_kernel_timing": "second timed region: the same AB and BA solves one after the "
+                             "other on one stream, CUDA events around every phase",
         "projector_gups": {k: v["gups"] for k, v in kernels.items() if "gups" in v},
         "err_vs_fp64": err,
         "clocks": clk_sum,
@@ -371,6 +401,29 @@ def variant_basis_precision(P, torch, G, b_dev, x_true, noise_ab):
                       "rel_to_f32_basis": float(torch.linalg.vector_norm(x - ref) /
                                                 torch.linalg.vector_norm(ref)),
                       "basis_gb": (ITERS + 1) * L * (4 if basis == "f32" else 2) / 1e9}
+    return out
+
+
+def variant_matched(P, torch, G, b_dev, x_true, noise_ab):
+    """The matched pair on the 512^2 fan workload: A^T alone (G samples/s, the same sample count
+    as A) and hybrid AB-GMRES with B = A^T (LSQR's subspace, 100 its, DP) beside the unmatched
+    solve: iterations/s and relative error to the phantom."""
+    xt = torch.from_numpy(x_true.astype(np.float32).reshape(-1)).cuda()
+    y = torch.rand(G.m, device="cuda")
+    xo = torch.empty(G.n, device="cuda")
+    ms_at, _ = _timed(torch, lambda: P.ct_back_AT(G, y, xo), reps=20)
+    ms_b, _ = _timed(torch, lambda: P.ct_back_B(G, y, xo), reps=20)
+    out = {"AT_ms": ms_at, "AT_gsamples_s": G.a_samples / (ms_at * 1e-3) / 1e9,
+           "B_ms": ms_b}
+    for kind in ("pixel", "adjoint"):
+        P.ct_geom_set_backprojector(G, kind)
+        x = torch.zeros(G.n, device="cuda")
+        ms, _ = _timed(torch, lambda: P.ab_gmres_hybrid(G, b_dev, x, max_iters=ITERS, rule="dp",
+                                                        noise_norm=noise_ab, tau=TAU,
+                                                        history=False), reps=2)
+        out[kind] = {"iters_s": ITERS / (ms * 1e-3), "ms_per_solve": ms,
+                     "rre": float(torch.linalg.vector_norm(x - xt) / torch.linalg.vector_norm(xt))}
+    P.ct_geom_set_backprojector(G, "pixel")
     return out
 
 
@@ -520,6 +573,7 @@ def run_variants(P, torch, G, b_dev, x_true, noise_ab, which):
     jobs = {"basis_precision_fan512_ab": lambda: variant_basis_precision(P, torch, G, b_dev, x_true, noise_ab),
             "learned_lambda_parallel256": lambda: variant_learned(P, torch),
             "batched_slices_sample": lambda: variant_batched(P, torch),
+            "matched_pair_fan512_ab": lambda: variant_matched(P, torch, G, b_dev, x_true, noise_ab),
             "cone512": lambda: variant_cone(P, torch)}
     for name, fn in jobs.items():
         if which != "all" and name not in which.split(","):

@@ -94,8 +94,22 @@ ct_status ct_forward_A(ct_geom *g, const float *x_dev, float *y_dev, ct_stream_t
  * weight h^2/(ray spacing at the pixel) so that B has the scale of A^T:
  *   parallel h^2/pitch;  fan h^2 (SDD^2+u^2)/(L pitch SDD);
  *   cone h^3 (SDD^2+u^2+v^2)^{3/2}/(L^2 pitch_u pitch_v SDD), L = |pixel - source|.
- * y_dev: m floats, x_dev: n floats (overwritten). */
+ * y_dev: m floats, x_dev: n floats (overwritten).  With ct_geom_set_backprojector(g,
+ * CT_BACK_ADJOINT) the geometry's B is A^T instead (here and in the solvers). */
 ct_status ct_back_B(ct_geom *g, const float *y_dev, float *x_dev, ct_stream_t stream);
+
+/* x = A^T y, the exact transpose of ct_forward_A (Sec. 2, the matched case; with B = A^T
+ * AB-GMRES is LSQR and BA-GMRES is LSMR in exact arithmetic): every ray's samples, at the
+ * same FP32 positions as A, add weight (1 - f) y_ray and weight f y_ray to their two taps'
+ * pixels (atomic FP32 additions: the summation order, and so the last bits, vary run to run).
+ * 2D geometries only (CT_EINVAL for cone).  y_dev: m floats, x_dev: n floats (overwritten). */
+ct_status ct_back_AT(ct_geom *g, const float *y_dev, float *x_dev, ct_stream_t stream);
+
+/* The backprojector the solvers (and ct_back_B) use on `g`: CT_BACK_PIXEL (the unmatched
+ * pixel-driven B, the default) or CT_BACK_ADJOINT (A^T, 2D only: the matched pair, for the
+ * LSQR / LSMR comparison of Sec. 2).  Host-only. */
+typedef enum { CT_BACK_PIXEL = 0, CT_BACK_ADJOINT = 1 } ct_backprojector;
+ct_status ct_geom_set_backprojector(ct_geom *g, ct_backprojector kind);
 
 /* ------------------------------------------------------------------ hybrid solvers */
 

@@ -116,6 +116,8 @@ def load(path: str = LIB_PATH):
     lib.ct_launch_count.argtypes = []
     lib.ct_geom_autotune.argtypes = [vp, vp, ctypes.POINTER(LaunchShapes)]
     lib.ct_geom_set_launch_shapes.argtypes = [vp, ctypes.POINTER(LaunchShapes)]
+    lib.ct_back_AT.argtypes = [vp, vp, vp, vp]
+    lib.ct_geom_set_backprojector.argtypes = [vp, ctypes.c_int]
     lib.ct_geom_get_launch_shapes.argtypes = [vp, ctypes.POINTER(LaunchShapes)]
     lib.ct_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(HybridOpts), ctypes.c_int, ctypes.POINTER(vp)]
@@ -342,6 +344,17 @@ def ct_profile_collect() -> dict:
 
 def ct_launch_count() -> int:
     return int(load().ct_launch_count())
+
+
+def ct_back_AT(g: Geom, y, x, stream=None):
+    """x = A^T y (2D; the matched adjoint of ct_forward_A)."""
+    _check(load().ct_back_AT(g.handle, _ptr(y), _ptr(x), _stream(stream)))
+
+
+def ct_geom_set_backprojector(g: Geom, kind: str):
+    """'pixel' (the unmatched B, default) or 'adjoint' (B = A^T, 2D)."""
+    k = {"pixel": 0, "adjoint": 1}[kind]
+    _check(load().ct_geom_set_backprojector(g.handle, k))
 
 
 def ct_geom_set_launch_shapes(g: Geom, shapes: dict):

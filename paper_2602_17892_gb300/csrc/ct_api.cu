@@ -158,6 +158,9 @@ static cudaError_t dalloc(T **p, size_t count)
     return e;
 }
 
+// kernel launches of one backprojection (pair conversion + B, or the adjoint alone)
+static int back_launches(const ct_geom *g) { return g->dg.back_adjoint ? 1 : 2; }
+
 // kernel launches of one forward projection (3D: one per z slab)
 static int fwd_launches(const ct_geom *g)
 {
@@ -412,6 +415,7 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     dg.tune_b_rows = cone ? 4 : 8;
     dg.tune_b_views = 1;
     dg.tune_a_rays = 1;
+    dg.back_adjoint = 0;
     dg.b_noclamp = cone ? 0 : (pixels_inside_detector(&g->desc) ? 1 : 0);
     dg.tune_a_slab = 16;
 
@@ -526,6 +530,27 @@ ct_status ct_forward_A(ct_geom *g, const float *x_dev, float *y_dev, ct_stream_t
     return CT_OK;
 }
 
+ct_status ct_back_AT(ct_geom *g, const float *y_dev, float *x_dev, ct_stream_t stream)
+{
+    if (!g || !y_dev || !x_dev) return einval("ct_back_AT: null argument");
+    if (g->desc.kind == CT_CONE3D) return einval("ct_back_AT: 2D geometries only");
+    cudaStream_t s = (cudaStream_t)stream;
+    CT_PHASE(CT_PH_BACK, 1, s);
+    CT_CUDA(launch_adjoint2d(g, y_dev, g->dg.ndu, 0, x_dev, nullptr, s));
+    return CT_OK;
+}
+
+ct_status ct_geom_set_backprojector(ct_geom *g, ct_backprojector kind)
+{
+    if (!g) return einval("ct_geom_set_backprojector: null geometry");
+    if (kind != CT_BACK_PIXEL && kind != CT_BACK_ADJOINT)
+        return einval("ct_geom_set_backprojector: unknown backprojector");
+    if (kind == CT_BACK_ADJOINT && g->desc.kind == CT_CONE3D)
+        return einval("ct_geom_set_backprojector: the adjoint is built for 2D geometries only");
+    g->dg.back_adjoint = kind == CT_BACK_ADJOINT ? 1 : 0;
+    return CT_OK;
+}
+
 ct_status ct_back_B(ct_geom *g, const float *y_dev, float *x_dev, ct_stream_t stream)
 {
     if (!g || !y_dev || !x_dev) return einval("ct_back_B: null argument");
@@ -534,7 +559,7 @@ ct_status ct_back_B(ct_geom *g, const float *y_dev, float *x_dev, ct_stream_t st
         CT_PHASE(CT_PH_LAYOUT, 1, s);
         CT_CUDA(launch_pad_sino(g, y_dev, g->sino_pad_dev, s));
     }
-    CT_PHASE(CT_PH_BACK, 2, s);
+    CT_PHASE(CT_PH_BACK, back_launches(g), s);
     CT_CUDA(launch_back_proj(g, g->sino_pad_dev, x_dev, nullptr, s));
     return CT_OK;
 }
@@ -725,7 +750,7 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
         const int k = step - 1;
         const float *wk = w->cur ? w->cur : static_cast<float *>(w->W) + (int64_t)k * ld;
         {
-            CT_PHASE(CT_PH_BACK, 2, s);
+            CT_PHASE(CT_PH_BACK, back_launches(g), s);
             CT_CUDA(launch_back_proj(g, wk, w->img, w->stop, s));       // line 5: B w_k
         }
         {
@@ -755,7 +780,7 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
                                      kMaxBlocks, s));
     }
     {
-        CT_PHASE(CT_PH_BACK, 2, s);
+        CT_PHASE(CT_PH_BACK, back_launches(g), s);
         CT_CUDA(launch_back_proj(g, w->q, x_dev, nullptr, s));
     }
     return CT_OK;
@@ -827,7 +852,7 @@ static ct_status enqueue_ba(ct_geom *g, const float *b_dev, const float *x0_dev,
             CT_CUDA(launch_forward_proj(g, w->sino, true, w->stop, s));
         }
         {
-            CT_PHASE(CT_PH_BACK, 2, s);
+            CT_PHASE(CT_PH_BACK, back_launches(g), s);
             CT_CUDA(launch_back_proj(g, w->sino, w->q, w->stop, s));     //          B (A w_k)
         }
         {

@@ -63,6 +63,7 @@ struct DeviceGeom {
     int tune_a_threads; // Joseph A: rays (threads) per block, chosen by ct_geom_autotune
     int tune_a_views;   // 2D Joseph A: views per block (each warp one view)
     int tune_a_rays;    // 2D Joseph A: rays per thread (1, or 2 adjacent views in paired FP32)
+    int back_adjoint;   // the geometry's backprojector: 0 pixel-driven B, 1 A^T (2D)
     int tune_b_rows;    // pixel-driven B: block of 32 x tune_b_rows pixels
     int tune_b_views;   // 2D pixel-driven B: views per loop iteration (1, or 2 in paired FP32)
     int b_noclamp;      // 2D: every pixel centre projects inside the detector in every view
@@ -118,6 +119,9 @@ inline int floor_chunk(int64_t stride)
 // start, the kernel returns at once (a solver that met breakdown skips the remaining steps).
 // Image x (row-major, n floats) -> the two padded pair layouts used by the Joseph kernels.
 cudaError_t launch_image_pairs(const ct_geom *g, const float *x, const int *stop, cudaStream_t s);
+// x = A^T y (2D matched adjoint; y with row stride y_ld and bin offset y_off)
+cudaError_t launch_adjoint2d(const ct_geom *g, const float *y, int y_ld, int y_off, float *x,
+                             const int *stop, cudaStream_t s);
 // y[view][v][u] -> padded sinogram (sino_view_ld floats per view, row length sino_ld, bin u of
 // row v at index sino_row0 + v * sino_ld + u + 2).
 cudaError_t launch_pad_sino(const ct_geom *g, const float *y, float *ypad, cudaStream_t s);

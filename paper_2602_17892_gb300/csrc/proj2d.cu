@@ -138,6 +138,10 @@ cudaError_t launch_forward_proj(const ct_geom *g, float *y, bool padded, const i
 cudaError_t launch_back_proj(const ct_geom *g, const float *ypad, float *x, const int *stop,
                              cudaStream_t s)
 {
+    if (g->dg.back_adjoint) {
+        if (g->dg.kind == CT_CONE3D) return cudaErrorNotSupported;
+        return launch_adjoint2d(g, ypad, g->dg.sino_ld, 2, x, stop, s);
+    }
     cudaError_t e = launch_sino_pairs(g, ypad, stop, s);
     if (e != cudaSuccess) return e;
     if (g->dg.kind == CT_CONE3D) return launch_voxbp3d(g, g->sino_pairs_dev, x, stop, s);
@@ -324,6 +328,53 @@ cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, con
 {
     if (g->dg.tune_a_rays == 2) launch_joseph2d_t<2>(g, y, y_ld, y_off, stop, s);
     else launch_joseph2d_t<1>(g, y, y_ld, y_off, stop, s);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------- matched adjoint
+// x = A^T y, the transpose of the Joseph projector above (the matched case B = A^T of Sec. 2,
+// where AB-/BA-GMRES reduce to LSQR / LSMR): one thread per ray walks the ray's samples with
+// the same FP32 positions as joseph2d_kernel (pos = pmid + slope (t - t_mid), the taps
+// floor(pos) and floor(pos) + 1 with weights 1 - f and f) and adds weight (1 - f) y_ray and
+// weight f y_ray to the two taps' pixels by atomic FP32 additions (the order of the additions
+// varies from run to run).  Taps outside the image have no pixel.  x must be zero on entry.
+__global__ void __launch_bounds__(256) joseph2d_adjoint_kernel(
+    const Ray2D *__restrict__ rays, int n_views, int ndu, const float *__restrict__ y, int y_ld,
+    int y_off, int nx, int ny, float *__restrict__ x, const int *stop)
+{
+    if (stop && stop[0] != 0) return;
+    const int64_t ray = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (ray >= (int64_t)n_views * ndu) return;
+    const int view = (int)(ray / ndu), bin = (int)(ray - (int64_t)view * ndu);
+    const Ray2D R = rays[ray];
+    const float yw = y[(int64_t)view * y_ld + y_off + bin] * R.weight;
+    const int t_lo = R.packed & 0x7fff, t_hi = (R.packed >> 15) & 0x7fff;
+    const int axis = (R.packed >> 30) & 1;
+    const int n_drive = axis == 0 ? nx : ny, n_other = axis == 0 ? ny : nx;
+    // pixel (line t, tap i): axis 0 drives along x (line = column t, taps along rows i),
+    // axis 1 along y (line = row t, taps along columns i)
+    const int step_t = axis == 0 ? 1 : nx, step_i = axis == 0 ? nx : 1;
+    float tf = (float)t_lo - 0.5f * (float)(n_drive - 1);
+    for (int t = t_lo; t <= t_hi; ++t, tf += 1.f) {
+        const float pos = fmaf(R.slope, tf, R.pmid);
+        const float fl = floorf(pos);
+        const float f = pos - fl;
+        const int i0 = (int)fl;
+        float *p = x + (int64_t)t * step_t + (int64_t)i0 * step_i;
+        if (i0 >= 0) atomicAdd(p, yw * (1.f - f));
+        if (i0 + 1 < n_other) atomicAdd(p + step_i, yw * f);
+    }
+}
+
+cudaError_t launch_adjoint2d(const ct_geom *g, const float *y, int y_ld, int y_off, float *x,
+                             const int *stop, cudaStream_t s)
+{
+    const DeviceGeom &d = g->dg;
+    cudaError_t e = cudaMemsetAsync(x, 0, sizeof(float) * (size_t)d.nx * d.ny, s);
+    if (e != cudaSuccess) return e;
+    const int64_t rays = (int64_t)d.n_views * d.ndu;
+    joseph2d_adjoint_kernel<<<(unsigned)((rays + 255) / 256), 256, 0, s>>>(
+        g->rays_dev, d.n_views, d.ndu, y, y_ld, y_off, d.nx, d.ny, x, stop);
     return cudaGetLastError();
 }
 
