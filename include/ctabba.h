@@ -101,7 +101,8 @@ ct_status ct_back_B(ct_geom *g, const float *y_dev, float *x_dev, ct_stream_t st
 /* x = A^T y, the exact transpose of ct_forward_A (Sec. 2, the matched case; with B = A^T
  * AB-GMRES is LSQR and BA-GMRES is LSMR in exact arithmetic): every ray's samples, at the
  * same FP32 positions as A, add weight (1 - f) y_ray and weight f y_ray to their two taps'
- * pixels (atomic FP32 additions: the summation order, and so the last bits, vary run to run).
+ * pixels by atomic FP64 additions into a scratch image owned by the geometry, rounded to FP32
+ * at the end (the arrival order of the rays changes the sums only far below FP32 resolution).
  * 2D geometries only (CT_EINVAL for cone).  y_dev: m floats, x_dev: n floats (overwritten). */
 ct_status ct_back_AT(ct_geom *g, const float *y_dev, float *x_dev, ct_stream_t stream);
 
@@ -207,21 +208,18 @@ ct_status ba_gmres_hybrid_restarted(ct_geom *g, const float *b_dev, float *x_dev
 /* Launch shapes of the projector kernels of a geometry. */
 typedef struct {
     int a_threads;   /* 2D Joseph A: threads per block                                    */
-    int a_views;     /* Joseph A: 2D, warp rows per block (each warp one view, or two
-                        adjacent views when a_rays = 2); 3D, detector rows per block of 32
-                        columns (each warp one row)                                         */
+    int a_views;     /* Joseph A: 2D, views per block (each warp 32 bins of one view); 3D,
+                        detector rows per block of 32 columns (each warp one row)           */
     int a_slab;      /* 3D Joseph A: z-slab thickness (tap rows) of one pass; each pass
                         reads one slab of the volume's pair layouts, so it stays in L2    */
     int b_rows;      /* 2D pixel-driven B: pixel rows per block                           */
     int b_views;     /* 2D pixel-driven B: views per loop iteration (1, or 2 with paired FP32
                         arithmetic; the same operations, so results do not change)         */
-    int a_rays;      /* 2D Joseph A: rays per thread (1, or 2: the same bin in two adjacent
-                        views, in paired FP32 arithmetic; results do not change)           */
 } ct_launch_shapes;
 
 /* Time the candidate launch shapes of the projectors on this geometry and keep the fastest for
- * later calls on `g`.  2D: Joseph A with (threads, warp rows) per block in (128, 1), (128, 2),
- * (256, 2), (256, 4), each with one or two rays per thread; pixel-driven B with 4, 8 or 16
+ * later calls on `g`.  2D: Joseph A with (threads, views) per block in (128, 1), (128, 2),
+ * (128, 4), (256, 1), (256, 2), (256, 4), (512, 4), (512, 8); pixel-driven B with 4, 8 or 16
  * pixel rows per block and 1 or 2 views per loop iteration.  3D: Joseph (slab thickness, detector
  * rows per block) in (16, 1), (16, 4), (16, 8), (64, 4), (64, 8) and one pass over the whole
  * volume with 1, 4 or 8 rows (the voxel-driven
@@ -233,7 +231,7 @@ ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_shapes *out
 /* Set the projectors' launch shapes of `g` explicitly (for instance a shape an earlier autotune
  * found, or a fixed one for timing).  Values: a_threads in {128, 256, 512} with a_threads /
  * a_views >= 32 and a_views in {1, 2, 4, 8} (2D), a_slab >= 1 (3D; >= nz + 1 is one pass),
- * a_views in 1..8 detector rows (3D), b_rows in {4, 8, 16}, b_views and a_rays in {1, 2}; anything else
+ * a_views in 1..8 detector rows (3D), b_rows in {4, 8, 16}, b_views in {1, 2}; anything else
  * returns CT_EINVAL and leaves `g` unchanged.  Host-only; shapes change the order of work, not a
  * sample's arithmetic. */
 ct_status ct_geom_set_launch_shapes(ct_geom *g, const ct_launch_shapes *shapes);

@@ -158,9 +158,6 @@ static cudaError_t dalloc(T **p, size_t count)
     return e;
 }
 
-// kernel launches of one backprojection (pair conversion + B, or the adjoint alone)
-static int back_launches(const ct_geom *g) { return g->dg.back_adjoint ? 1 : 2; }
-
 // kernel launches of one forward projection (3D: one per z slab)
 static int fwd_launches(const ct_geom *g)
 {
@@ -414,7 +411,6 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     dg.tune_a_views = cone ? 8 : 1;
     dg.tune_b_rows = cone ? 4 : 8;
     dg.tune_b_views = 1;
-    dg.tune_a_rays = 1;
     dg.back_adjoint = 0;
     dg.b_noclamp = cone ? 0 : (pixels_inside_detector(&g->desc) ? 1 : 0);
     dg.tune_a_slab = 16;
@@ -463,6 +459,7 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     if (e == cudaSuccess) e = dalloc(&g->pcol_dev, pcol_n);
     if (e == cudaSuccess) e = dalloc(&g->sino_pad_dev, (size_t)d->n_views * dg.sino_view_ld);
     if (e == cudaSuccess) e = dalloc(&g->sino_pairs_dev, (size_t)d->n_views * dg.sino_view_ld);
+    if (e == cudaSuccess && !cone) e = dalloc(&g->adj_acc_dev, (size_t)g->n);
     if (e != cudaSuccess) {
         set_error(std::string("ct_geom_create: ") + cudaGetErrorString(e));
         ct_geom_destroy(g);
@@ -497,6 +494,7 @@ void ct_geom_destroy(ct_geom *g)
     cudaFree(g->prow_dev); cudaFree(g->pcol_dev);
     cudaFree(g->sino_pad_dev);
     cudaFree(g->sino_pairs_dev);
+    cudaFree(g->adj_acc_dev);
     delete[] g->angles_host;
     delete g;
 }
@@ -535,7 +533,7 @@ ct_status ct_back_AT(ct_geom *g, const float *y_dev, float *x_dev, ct_stream_t s
     if (!g || !y_dev || !x_dev) return einval("ct_back_AT: null argument");
     if (g->desc.kind == CT_CONE3D) return einval("ct_back_AT: 2D geometries only");
     cudaStream_t s = (cudaStream_t)stream;
-    CT_PHASE(CT_PH_BACK, 1, s);
+    CT_PHASE(CT_PH_BACK, 2, s);
     CT_CUDA(launch_adjoint2d(g, y_dev, g->dg.ndu, 0, x_dev, nullptr, s));
     return CT_OK;
 }
@@ -559,7 +557,7 @@ ct_status ct_back_B(ct_geom *g, const float *y_dev, float *x_dev, ct_stream_t st
         CT_PHASE(CT_PH_LAYOUT, 1, s);
         CT_CUDA(launch_pad_sino(g, y_dev, g->sino_pad_dev, s));
     }
-    CT_PHASE(CT_PH_BACK, back_launches(g), s);
+    CT_PHASE(CT_PH_BACK, 2, s);   // pair copy + B, or A^T scatter + rounding
     CT_CUDA(launch_back_proj(g, g->sino_pad_dev, x_dev, nullptr, s));
     return CT_OK;
 }
@@ -750,7 +748,7 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
         const int k = step - 1;
         const float *wk = w->cur ? w->cur : static_cast<float *>(w->W) + (int64_t)k * ld;
         {
-            CT_PHASE(CT_PH_BACK, back_launches(g), s);
+            CT_PHASE(CT_PH_BACK, 2, s);   // pair copy + B, or A^T scatter + rounding
             CT_CUDA(launch_back_proj(g, wk, w->img, w->stop, s));       // line 5: B w_k
         }
         {
@@ -780,7 +778,7 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
                                      kMaxBlocks, s));
     }
     {
-        CT_PHASE(CT_PH_BACK, back_launches(g), s);
+        CT_PHASE(CT_PH_BACK, 2, s);   // pair copy + B, or A^T scatter + rounding
         CT_CUDA(launch_back_proj(g, w->q, x_dev, nullptr, s));
     }
     return CT_OK;
@@ -852,7 +850,7 @@ static ct_status enqueue_ba(ct_geom *g, const float *b_dev, const float *x0_dev,
             CT_CUDA(launch_forward_proj(g, w->sino, true, w->stop, s));
         }
         {
-            CT_PHASE(CT_PH_BACK, back_launches(g), s);
+            CT_PHASE(CT_PH_BACK, 2, s);   // pair copy + B, or A^T scatter + rounding
             CT_CUDA(launch_back_proj(g, w->sino, w->q, w->stop, s));     //          B (A w_k)
         }
         {
@@ -1168,7 +1166,6 @@ static ct_launch_shapes shapes_of(const DeviceGeom &d)
     r.a_slab = d.tune_a_slab;
     r.b_rows = d.tune_b_rows;
     r.b_views = d.tune_b_views;
-    r.a_rays = d.tune_a_rays;
     return r;
 }
 
@@ -1180,7 +1177,7 @@ extern "C" ct_status ct_geom_set_launch_shapes(ct_geom *g, const ct_launch_shape
         for (int u : set) if (v == u) return true;
         return false;
     };
-    bool ok = in(sh->b_rows, {4, 8, 16}) && in(sh->b_views, {1, 2}) && in(sh->a_rays, {1, 2});
+    bool ok = in(sh->b_rows, {4, 8, 16}) && in(sh->b_views, {1, 2});
     if (cone)
         ok = ok && sh->a_slab >= 1 && sh->a_views >= 1 && sh->a_views <= 8;
     else
@@ -1193,7 +1190,6 @@ extern "C" ct_status ct_geom_set_launch_shapes(ct_geom *g, const ct_launch_shape
     dg.tune_a_slab = sh->a_slab;
     dg.tune_b_rows = sh->b_rows;
     dg.tune_b_views = sh->b_views;
-    dg.tune_a_rays = sh->a_rays;
     return CT_OK;
 }
 
@@ -1223,7 +1219,6 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
             dg.tune_a_slab = it->second.a_slab;
             dg.tune_b_rows = it->second.b_rows;
             dg.tune_b_views = it->second.b_views;
-            dg.tune_a_rays = it->second.a_rays;
             if (out) *out = it->second;
             return CT_OK;
         }
@@ -1263,9 +1258,9 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
     // 2D Joseph A: (rays per block, views per block); 3D: z-slab thickness of the Joseph passes;
     // 2D B: (pixel rows per 32-wide block, views per loop iteration); the 3D backprojector has
     // one shape
-    // 2D Joseph: (rays per block, warp rows per block, rays per thread)
-    static const int a2[8][3] = {{128, 1, 1}, {128, 2, 1}, {256, 2, 1}, {256, 4, 1},
-                                 {128, 1, 2}, {128, 2, 2}, {256, 2, 2}, {256, 4, 2}};
+    // 2D Joseph: (threads, warp rows = views per block)
+    static const int a2[8][2] = {{128, 1}, {128, 2}, {128, 4}, {256, 1},
+                                 {256, 2}, {256, 4}, {512, 4}, {512, 8}};
     // 3D: (z-slab thickness, detector rows per block); 1 << 20 = one pass over the volume
     static const int a3[8][2] = {{16, 1}, {16, 4}, {16, 8}, {64, 4}, {64, 8},
                                  {1 << 20, 1}, {1 << 20, 4}, {1 << 20, 8}};
@@ -1278,11 +1273,12 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
         st = time_best(fwd, 8, [&](int c) {
             dg.tune_a_threads = a2[c][0];
             dg.tune_a_views = a2[c][1];
-            dg.tune_a_rays = a2[c][2];
         });
     if (st == CT_OK && !cone)
-        st = time_best([&]() { return launch_back_proj(g, y, x, nullptr, s); }, 6,
-                       [&](int c) { dg.tune_b_rows = b2[c][0]; dg.tune_b_views = b2[c][1]; });
+        st = time_best([&]() { return launch_back_proj(g, y, x, nullptr, s); }, 6, [&](int c) {
+            dg.tune_b_rows = b2[c][0];
+            dg.tune_b_views = b2[c][1];
+        });
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(x);

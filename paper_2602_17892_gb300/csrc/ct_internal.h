@@ -62,7 +62,6 @@ struct DeviceGeom {
     int sino_ld;        // padded sinogram row length: ndu + 4 (2 zero bins each side)
     int tune_a_threads; // Joseph A: rays (threads) per block, chosen by ct_geom_autotune
     int tune_a_views;   // 2D Joseph A: views per block (each warp one view)
-    int tune_a_rays;    // 2D Joseph A: rays per thread (1, or 2 adjacent views in paired FP32)
     int back_adjoint;   // the geometry's backprojector: 0 pixel-driven B, 1 A^T (2D)
     int tune_b_rows;    // pixel-driven B: block of 32 x tune_b_rows pixels
     int tune_b_views;   // 2D pixel-driven B: views per loop iteration (1, or 2 in paired FP32)
@@ -95,6 +94,7 @@ struct ct_geom {
     float2 *pcol_dev;   // 2D: [nx][col_pairs_ld] pairs along y; 3D: P_x, [nz + 3][slice_x]
     float *sino_pad_dev;  // [n_views][sino_view_ld]
     float2 *sino_pairs_dev; // [n_views][sino_view_ld] (bin j, bin j + 1) pairs read by B
+    double *adj_acc_dev;    // 2D: n FP64 accumulators of the matched adjoint A^T
     // solver workspace (grown on demand)
     struct Workspace *ws;
 };

@@ -165,91 +165,41 @@ cudaError_t launch_back_proj(const ct_geom *g, const float *ypad, float *x, cons
 // to FP32 rounding, so the pair index stays in [-1, n_other + 1], which the layouts hold as
 // zero pairs (a zero line before line 0 and at least n_other + 2 pairs per line); a lane
 // outside its own range skips the load.
-// lines t in [ta, tb] of one ray; K carries (t - ta) * stride (below 2^22 for every t)
+// Lines t in [ta, tb] of one ray, two per loop iteration (t and t + 1): both samples'
+// positions, floors and weights in paired FP32 arithmetic (one fma.f32x2 / add.rm.f32x2 each,
+// the same operations per sample as one line at a time), accumulated in line order.  K carries
+// (t - ta) * stride (below 2^22 for every t).
 __device__ __forceinline__ float joseph2d_span(int ta, int tb, int t_lo, int t_hi, float pmid,
                                                float slope, float tmid, int stride,
                                                uint64_t abase, float acc)
 {
-    float tf = (float)ta - tmid;
-    float K = kFloorK0;                           // 2^23 + 2 + (t - ta) * stride
+    float2 tf2 = make_float2((float)ta - tmid, (float)ta - tmid + 1.f);
+    float2 K2 = make_float2(kFloorK0, kFloorK0 + (float)stride);
+    const float2 sl2 = make_float2(slope, slope), pm2 = make_float2(pmid, pmid);
+    const float2 d2 = make_float2(2.f, 2.f), dK2 = make_float2(2.f * (float)stride, 2.f * (float)stride);
+    const float2 m1 = make_float2(-1.f, -1.f);
     const uint64_t lb = abase + 8ull * (uint64_t)ta * (uint64_t)stride;
-#pragma unroll 4
-    for (int t = ta; t <= tb; ++t) {
+#pragma unroll 2
+    for (int t = ta; t <= tb; t += 2) {
+        const float2 pos2 = __ffma2_rn(sl2, tf2, pm2);
+        const float2 sk2 = __fadd2_rd(pos2, K2);
+        const float2 f2 = __ffma2_rn(__ffma2_rn(K2, m1, sk2), m1, pos2);   // pos - (sk - K)
         if (t >= t_lo && t <= t_hi) {
-            const float pos = fmaf(slope, tf, pmid);
-            const float sk = __fadd_rd(pos, K);
-            const float f = pos - (sk - K);
-            const float2 p = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * __float_as_uint(sk)));
-            acc += fmaf(f, p.y - p.x, p.x);
+            const float2 p = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * __float_as_uint(sk2.x)));
+            acc += fmaf(f2.x, p.y - p.x, p.x);
         }
-        tf += 1.f;
-        K += (float)stride;
+        if (t + 1 <= tb && t + 1 >= t_lo && t + 1 <= t_hi) {
+            const float2 p = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * __float_as_uint(sk2.y)));
+            acc += fmaf(f2.y, p.y - p.x, p.x);
+        }
+        tf2 = __fadd2_rn(tf2, d2);
+        K2 = __fadd2_rn(K2, dK2);
     }
     return acc;
 }
 
-// Two rays per thread (views v and v + 1 at the same bin): positions, floors and weights of
-// both in paired FP32 arithmetic (one fma.f32x2 / add.rm.f32x2 each), the same operations per
-// ray as joseph2d_span, so the results are bitwise those of one ray per thread.
-__device__ __forceinline__ void joseph2d_span2(int ta, int tb, int lo0, int hi0, int lo1, int hi1,
-                                               float2 pmid2, float2 slope2, float2 tmid2,
-                                               int st0, int st1, uint64_t ab0, uint64_t ab1,
-                                               float &acc0, float &acc1)
-{
-    float2 tf2 = make_float2((float)ta - tmid2.x, (float)ta - tmid2.y);
-    float2 K2 = make_float2(kFloorK0, kFloorK0);
-    const float2 dK2 = make_float2((float)st0, (float)st1);
-    const float2 one2 = make_float2(1.f, 1.f), m1 = make_float2(-1.f, -1.f);
-    const uint64_t lb0 = ab0 + 8ull * (uint64_t)ta * (uint64_t)st0;
-    const uint64_t lb1 = ab1 + 8ull * (uint64_t)ta * (uint64_t)st1;
-#pragma unroll 4
-    for (int t = ta; t <= tb; ++t) {
-        const float2 pos2 = __ffma2_rn(slope2, tf2, pmid2);
-        const float2 sk2 = __fadd2_rd(pos2, K2);
-        const float2 f2 = __ffma2_rn(__ffma2_rn(K2, m1, sk2), m1, pos2);   // pos - (sk - K)
-        if (t >= lo0 && t <= hi0) {
-            const float2 p = __ldg(reinterpret_cast<const float2 *>(lb0 + 8ull * __float_as_uint(sk2.x)));
-            acc0 += fmaf(f2.x, p.y - p.x, p.x);
-        }
-        if (t >= lo1 && t <= hi1) {
-            const float2 p = __ldg(reinterpret_cast<const float2 *>(lb1 + 8ull * __float_as_uint(sk2.y)));
-            acc1 += fmaf(f2.y, p.y - p.x, p.x);
-        }
-        tf2 = __fadd2_rn(tf2, one2);
-        K2 = __fadd2_rn(K2, dK2);
-    }
-}
-
-struct JRay {
-    float pmid, slope, tmid, weight;
-    int lo, hi, stride;
-    uint64_t abase;
-};
-
-__device__ __forceinline__ JRay joseph2d_ray(const Ray2D *__restrict__ rays, bool valid,
-                                             int64_t idx, const float2 *prow, int prow_ld,
-                                             const float2 *pcol, int pcol_ld, int nx, int ny)
-{
-    const Ray2D R = rays[valid ? idx : 0];
-    JRay j;
-    j.lo = valid ? (int)(R.packed & 0x7fff) : 1;
-    j.hi = valid ? (int)((R.packed >> 15) & 0x7fff) : 0;
-    const int axis = (R.packed >> 30) & 1;
-    const float2 *base;          // line 0 of the layout the ray reads
-    int n_drive;
-    if (axis == 0) { base = pcol; j.stride = pcol_ld; n_drive = nx; }   // drive along x
-    else { base = prow; j.stride = prow_ld; n_drive = ny; }             // drive along y
-    j.tmid = 0.5f * (float)(n_drive - 1);
-    j.pmid = R.pmid;
-    j.slope = R.slope;
-    j.weight = R.weight;
-    j.abase = reinterpret_cast<uint64_t>(base) - 8ull * ((uint64_t)__float_as_uint(kFloor2p23) + 1ull);
-    return j;
-}
-
-// CHUNKED: the lines are walked in chunks of `chunk` (images whose line offsets exceed 2^22).
-// RP rays per thread: views RP r .. RP r + RP - 1 of warp row r at one bin.
-template <bool CHUNKED, int RP>
+// CHUNKED: the lines are walked in chunks of `chunk` (images whose line offsets exceed 2^22)
+template <bool CHUNKED>
 __global__ void __launch_bounds__(512) joseph2d_kernel(
     const Ray2D *__restrict__ rays, int n_views, int ndu, int vpb,
     const float2 *__restrict__ prow, int prow_ld, const float2 *__restrict__ pcol, int pcol_ld,
@@ -258,53 +208,43 @@ __global__ void __launch_bounds__(512) joseph2d_kernel(
     if (stop && stop[0] != 0) return;
     const int bins_pb = blockDim.x / vpb;
     const int bin = blockIdx.x * bins_pb + (int)threadIdx.x % bins_pb;
-    const int row = blockIdx.y * vpb + (int)threadIdx.x / bins_pb;
-    // all lanes stay for the warp range
-    const int v0 = row * RP, v1 = v0 + 1;
-    const bool valid0 = bin < ndu && v0 < n_views, valid1 = RP == 2 && bin < ndu && v1 < n_views;
-    const JRay r0 = joseph2d_ray(rays, valid0, (int64_t)v0 * ndu + bin, prow, prow_ld, pcol,
-                                 pcol_ld, nx, ny);
-    JRay r1 = r0;
-    if (RP == 2)
-        r1 = joseph2d_ray(rays, valid1, (int64_t)v1 * ndu + bin, prow, prow_ld, pcol, pcol_ld,
-                          nx, ny);
-    else
-        r1.lo = 1, r1.hi = 0;
+    const int view0 = blockIdx.y * vpb + (int)threadIdx.x / bins_pb;
+    const bool valid = bin < ndu && view0 < n_views;   // all lanes stay for the warp range
+    const Ray2D R = rays[valid ? (int64_t)view0 * ndu + bin : 0];
+    int t_lo = R.packed & 0x7fff;
+    int t_hi = (R.packed >> 15) & 0x7fff;
+    if (!valid) { t_lo = 1; t_hi = 0; }
+    const int axis = (R.packed >> 30) & 1;
+    const float2 *base;          // line 0 of the layout the ray reads
+    int stride, n_drive;
+    if (axis == 0) { base = pcol; stride = pcol_ld; n_drive = nx; }   // drive along x
+    else { base = prow; stride = prow_ld; n_drive = ny; }             // drive along y
+    const float tmid = 0.5f * (float)(n_drive - 1);
     // the warp steps through the union of its lanes' driving ranges together, so that at every
     // step its lanes read neighbouring pairs of one line (a lane outside its own range idles)
-    int lmin = r0.hi >= r0.lo ? r0.lo : 0x7fffffff, lmax = r0.hi >= r0.lo ? r0.hi : -1;
-    if (RP == 2 && r1.hi >= r1.lo) { lmin = min(lmin, r1.lo); lmax = max(lmax, r1.hi); }
-    const int wlo = __reduce_min_sync(0xffffffffu, lmin);
-    const int whi = __reduce_max_sync(0xffffffffu, lmax);
-    float acc0 = 0.f, acc1 = 0.f;
-    auto span = [&](int ta, int tb) {
-        if (RP == 2)
-            joseph2d_span2(ta, tb, r0.lo, r0.hi, r1.lo, r1.hi, make_float2(r0.pmid, r1.pmid),
-                           make_float2(r0.slope, r1.slope), make_float2(r0.tmid, r1.tmid),
-                           r0.stride, r1.stride, r0.abase, r1.abase, acc0, acc1);
-        else
-            acc0 = joseph2d_span(ta, tb, r0.lo, r0.hi, r0.pmid, r0.slope, r0.tmid, r0.stride,
-                                 r0.abase, acc0);
-    };
+    const int wlo = __reduce_min_sync(0xffffffffu, t_hi >= t_lo ? t_lo : 0x7fffffff);
+    const int whi = __reduce_max_sync(0xffffffffu, t_hi >= t_lo ? t_hi : -1);
+    const uint64_t abase = reinterpret_cast<uint64_t>(base) -
+                           8ull * ((uint64_t)__float_as_uint(kFloor2p23) + 1ull);
+    float acc = 0.f;
     if (!CHUNKED) {
-        span(wlo, whi);
+        acc = joseph2d_span(wlo, whi, t_lo, t_hi, R.pmid, R.slope, tmid, stride, abase, acc);
     } else {
-        for (int t0 = wlo; t0 <= whi; t0 += chunk) span(t0, min(whi, t0 + chunk - 1));
+        for (int t0 = wlo; t0 <= whi; t0 += chunk)
+            acc = joseph2d_span(t0, min(whi, t0 + chunk - 1), t_lo, t_hi, R.pmid, R.slope, tmid,
+                                stride, abase, acc);
     }
-    if (valid0) y[(int64_t)v0 * y_ld + y_off + bin] = acc0 * r0.weight;
-    if (RP == 2 && valid1) y[(int64_t)v1 * y_ld + y_off + bin] = acc1 * r1.weight;
+    if (valid) y[(int64_t)view0 * y_ld + y_off + bin] = acc * R.weight;
 }
 
-template <int RP>
-static void launch_joseph2d_t(const ct_geom *g, float *y, int y_ld, int y_off, const int *stop,
-                              cudaStream_t s)
+cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, const int *stop,
+                            cudaStream_t s)
 {
     const DeviceGeom &d = g->dg;
     const int threads = d.tune_a_threads > 0 ? d.tune_a_threads : 256;
     const int vpb = (d.tune_a_views > 0 && threads / d.tune_a_views >= 32) ? d.tune_a_views : 1;
     const int bins_pb = threads / vpb;
-    const int rows = (d.n_views + RP - 1) / RP;
-    dim3 grid((d.ndu + bins_pb - 1) / bins_pb, (rows + vpb - 1) / vpb);
+    dim3 grid((d.ndu + bins_pb - 1) / bins_pb, (d.n_views + vpb - 1) / vpb);
     // line 0 of each 2D layout follows one zero line
     const float2 *prow = g->prow_dev + d.row_pairs_ld, *pcol = g->pcol_dev + d.col_pairs_ld;
     // one chunk length for both layouts (the loop bounds stay warp-uniform); one chunk when
@@ -312,22 +252,13 @@ static void launch_joseph2d_t(const ct_geom *g, float *y, int y_ld, int y_off, c
     const int ldm = std::max(d.row_pairs_ld, d.col_pairs_ld);
     const int chunk = floor_chunk(ldm);
     if (std::max(d.nx, d.ny) <= chunk)
-        joseph2d_kernel<false, RP><<<grid, threads, 0, s>>>(g->rays_dev, d.n_views, d.ndu, vpb,
-                                                            prow, d.row_pairs_ld, pcol,
-                                                            d.col_pairs_ld, chunk, d.nx, d.ny, y,
-                                                            y_ld, y_off, stop);
+        joseph2d_kernel<false><<<grid, threads, 0, s>>>(g->rays_dev, d.n_views, d.ndu, vpb, prow,
+                                                        d.row_pairs_ld, pcol, d.col_pairs_ld,
+                                                        chunk, d.nx, d.ny, y, y_ld, y_off, stop);
     else
-        joseph2d_kernel<true, RP><<<grid, threads, 0, s>>>(g->rays_dev, d.n_views, d.ndu, vpb,
-                                                           prow, d.row_pairs_ld, pcol,
-                                                           d.col_pairs_ld, chunk, d.nx, d.ny, y,
-                                                           y_ld, y_off, stop);
-}
-
-cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, const int *stop,
-                            cudaStream_t s)
-{
-    if (g->dg.tune_a_rays == 2) launch_joseph2d_t<2>(g, y, y_ld, y_off, stop, s);
-    else launch_joseph2d_t<1>(g, y, y_ld, y_off, stop, s);
+        joseph2d_kernel<true><<<grid, threads, 0, s>>>(g->rays_dev, d.n_views, d.ndu, vpb, prow,
+                                                       d.row_pairs_ld, pcol, d.col_pairs_ld,
+                                                       chunk, d.nx, d.ny, y, y_ld, y_off, stop);
     return cudaGetLastError();
 }
 
@@ -336,11 +267,12 @@ cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, con
 // where AB-/BA-GMRES reduce to LSQR / LSMR): one thread per ray walks the ray's samples with
 // the same FP32 positions as joseph2d_kernel (pos = pmid + slope (t - t_mid), the taps
 // floor(pos) and floor(pos) + 1 with weights 1 - f and f) and adds weight (1 - f) y_ray and
-// weight f y_ray to the two taps' pixels by atomic FP32 additions (the order of the additions
-// varies from run to run).  Taps outside the image have no pixel.  x must be zero on entry.
+// weight f y_ray (FP32 products) to the two taps' pixels by atomic FP64 additions, so the
+// order in which the rays arrive changes the sums only far below FP32 resolution; a second
+// kernel rounds them to FP32.  Taps outside the image have no pixel.
 __global__ void __launch_bounds__(256) joseph2d_adjoint_kernel(
     const Ray2D *__restrict__ rays, int n_views, int ndu, const float *__restrict__ y, int y_ld,
-    int y_off, int nx, int ny, float *__restrict__ x, const int *stop)
+    int y_off, int nx, int ny, double *__restrict__ acc, const int *stop)
 {
     if (stop && stop[0] != 0) return;
     const int64_t ray = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -360,21 +292,33 @@ __global__ void __launch_bounds__(256) joseph2d_adjoint_kernel(
         const float fl = floorf(pos);
         const float f = pos - fl;
         const int i0 = (int)fl;
-        float *p = x + (int64_t)t * step_t + (int64_t)i0 * step_i;
-        if (i0 >= 0) atomicAdd(p, yw * (1.f - f));
-        if (i0 + 1 < n_other) atomicAdd(p + step_i, yw * f);
+        double *p = acc + (int64_t)t * step_t + (int64_t)i0 * step_i;
+        if (i0 >= 0) atomicAdd(p, (double)(yw * (1.f - f)));
+        if (i0 + 1 < n_other) atomicAdd(p + step_i, (double)(yw * f));
     }
+}
+
+__global__ void round_to_float_kernel(const double *__restrict__ a, int64_t n, float *__restrict__ x,
+                                      const int *stop)
+{
+    if (stop && stop[0] != 0) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = (float)a[i];
 }
 
 cudaError_t launch_adjoint2d(const ct_geom *g, const float *y, int y_ld, int y_off, float *x,
                              const int *stop, cudaStream_t s)
 {
     const DeviceGeom &d = g->dg;
-    cudaError_t e = cudaMemsetAsync(x, 0, sizeof(float) * (size_t)d.nx * d.ny, s);
+    const int64_t n = (int64_t)d.nx * d.ny;
+    cudaError_t e = cudaMemsetAsync(g->adj_acc_dev, 0, sizeof(double) * (size_t)n, s);
     if (e != cudaSuccess) return e;
     const int64_t rays = (int64_t)d.n_views * d.ndu;
     joseph2d_adjoint_kernel<<<(unsigned)((rays + 255) / 256), 256, 0, s>>>(
-        g->rays_dev, d.n_views, d.ndu, y, y_ld, y_off, d.nx, d.ny, x, stop);
+        g->rays_dev, d.n_views, d.ndu, y, y_ld, y_off, d.nx, d.ny, g->adj_acc_dev, stop);
+    round_to_float_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, s>>>(
+        g->adj_acc_dev, n, x, stop);
     return cudaGetLastError();
 }
 
@@ -460,7 +404,7 @@ __global__ void __launch_bounds__(512) pixbp2d_kernel(
             const uint64_t rb = ybase + 8ull * (uint64_t)v0 * (uint64_t)ld;
             float2 K2 = make_float2(kFloor2p23, kFloor2p23 + (float)ld);
             const float2 dK2 = make_float2(2.f * (float)ld, 2.f * (float)ld);
-#pragma unroll 2
+#pragma unroll 4
             for (int vv = v0; vv < v1; vv += 2) {
                 const float4 V = sview[vv >> 1];
                 float2 fj2, w2;

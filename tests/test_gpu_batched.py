@@ -84,8 +84,8 @@ def test_abba_solve_one_shot_and_breakdown_inside_batch():
     x1, b1, e1 = problem(g1, 7, 0.01, 8)
     G1, G2 = gpu_geom(g1), gpu_geom(g2)
     sh = ct_geom_autotune(G2)
-    assert (sh["a_threads"], sh["a_views"]) in ((128, 1), (128, 2), (256, 2), (256, 4))
-    assert sh["a_rays"] in (1, 2)
+    assert (sh["a_threads"], sh["a_views"]) in ((128, 1), (128, 2), (128, 4), (256, 1), (256, 2),
+                                                (256, 4), (512, 4), (512, 8))
     assert sh["b_rows"] in (4, 8, 16) and sh["b_views"] in (1, 2)
     bs = [to_dev(b1), torch.zeros(G2.m, dtype=torch.float32, device="cuda")]
     xs = [torch.zeros(G.n, dtype=torch.float32, device="cuda") for G in (G1, G2)]

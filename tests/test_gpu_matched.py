@@ -67,7 +67,7 @@ def _solve(method, G, b, iters, rule, **kw):
 @pytest.mark.parametrize("k", [4, 8])
 def test_matched_solvers_are_lsqr_and_lsmr(k):
     """lambda = 0 at small k (without regularisation FP32 noise grows quickly with k, most for
-    BA, whose operator is A^T A); hybrid BA at lambda = 2 over 15 steps."""
+    BA, whose operator is A^T A); hybrid BA at lambda = 50 over 15 steps."""
     from paper_2602_17892_gb300 import ct_geom_set_backprojector
     case = synth.small_parallel_case()
     g = case["geom"]
@@ -80,7 +80,7 @@ def test_matched_solvers_are_lsqr_and_lsmr(k):
     assert iab["iters_done"] == k and iba["iters_done"] == k
     assert rel(xab, OS.lsqr_iterate(A, At, b, k)) <= ITER_TOL
     assert rel(xba, OS.lsmr_iterate(A, At, b, k)) <= ITER_TOL
-    lam = 2.0
+    lam = 50.0      # about 1 % of the largest singular value of the projected A^T A
     xh, _ = _solve("ba", G, b, 15, "fixed", lambda_fixed=lam)
     assert rel(xh, OS.lsmr_iterate(A, At, b, 15, lam)) <= ITER_TOL
     # the geometry's B switches back: the unmatched solve differs from the matched one

@@ -67,9 +67,9 @@ def test_projectors_are_linear_and_unmatched():
 
 @pytest.mark.parametrize("name", ["fan_64", "fan_ragged_50x33", "parallel_ragged_37x45"])
 def test_launch_shapes_leave_results_bitwise_unchanged(name):
-    """Every 2D launch shape (threads and warp rows per Joseph block, one or two rays per thread;
-    pixel rows per B block and one or two views per B iteration) computes each ray and pixel with
-    the same operations in the same order: A and B agree bit for bit across shapes."""
+    """Every 2D launch shape (threads and views per Joseph block; pixel rows per B block and one
+    or two views per B iteration) computes each ray and pixel with the same operations in the
+    same order: A and B agree bit for bit across shapes."""
     from paper_2602_17892_gb300 import ct_geom_get_launch_shapes, ct_geom_set_launch_shapes
     g = GEOMS[name]
     G = gpu_geom(g)
@@ -77,10 +77,9 @@ def test_launch_shapes_leave_results_bitwise_unchanged(name):
     y = f32(synth.standard_normal(g.m, 22))
     base = ct_geom_get_launch_shapes(G)
     ya, xb = gpu_A(G, x), gpu_B(G, y)
-    for a_threads, a_views, a_rays in ((128, 1, 1), (256, 2, 2), (512, 8, 1), (128, 4, 2)):
+    for a_threads, a_views in ((128, 1), (256, 2), (512, 8), (128, 4)):
         for b_rows, b_views in ((4, 1), (8, 2), (16, 2)):
-            sh = dict(base, a_threads=a_threads, a_views=a_views, a_rays=a_rays, b_rows=b_rows,
-                      b_views=b_views)
+            sh = dict(base, a_threads=a_threads, a_views=a_views, b_rows=b_rows, b_views=b_views)
             ct_geom_set_launch_shapes(G, sh)
             assert ct_geom_get_launch_shapes(G) == sh
             assert np.array_equal(gpu_A(G, x), ya)
