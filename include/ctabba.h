@@ -103,12 +103,13 @@ ct_status ct_back_B(ct_geom *g, const float *y_dev, float *x_dev, ct_stream_t st
  * same FP32 positions as A, add weight (1 - f) y_ray and weight f y_ray to their two taps'
  * pixels by atomic FP64 additions into a scratch image owned by the geometry, rounded to FP32
  * at the end (the arrival order of the rays changes the sums only far below FP32 resolution).
- * 2D geometries only (CT_EINVAL for cone).  y_dev: m floats, x_dev: n floats (overwritten). */
+ * Cone geometries: bilinear taps, four per sample; the first call allocates the geometry's n
+ * FP64 accumulators.  y_dev: m floats, x_dev: n floats (overwritten). */
 ct_status ct_back_AT(ct_geom *g, const float *y_dev, float *x_dev, ct_stream_t stream);
 
 /* The backprojector the solvers (and ct_back_B) use on `g`: CT_BACK_PIXEL (the unmatched
- * pixel-driven B, the default) or CT_BACK_ADJOINT (A^T, 2D only: the matched pair, for the
- * LSQR / LSMR comparison of Sec. 2).  Host-only. */
+ * pixel/voxel-driven B, the default) or CT_BACK_ADJOINT (A^T: the matched pair, for the
+ * LSQR / LSMR comparison of Sec. 2; allocates the accumulators ct_back_AT needs).  Host-only. */
 typedef enum { CT_BACK_PIXEL = 0, CT_BACK_ADJOINT = 1 } ct_backprojector;
 ct_status ct_geom_set_backprojector(ct_geom *g, ct_backprojector kind);
 

@@ -528,13 +528,30 @@ ct_status ct_forward_A(ct_geom *g, const float *x_dev, float *y_dev, ct_stream_t
     return CT_OK;
 }
 
+// the FP64 accumulators of A^T (cone geometries allocate them on first use: n doubles)
+static ct_status adjoint_scratch(ct_geom *g)
+{
+    if (g->adj_acc_dev) return CT_OK;
+    if (dalloc(&g->adj_acc_dev, (size_t)g->n) != cudaSuccess) {
+        set_error("ct_back_AT: allocating the adjoint's FP64 accumulators failed");
+        return CT_ENOMEM;
+    }
+    return CT_OK;
+}
+
 ct_status ct_back_AT(ct_geom *g, const float *y_dev, float *x_dev, ct_stream_t stream)
 {
     if (!g || !y_dev || !x_dev) return einval("ct_back_AT: null argument");
-    if (g->desc.kind == CT_CONE3D) return einval("ct_back_AT: 2D geometries only");
+    ct_status st = adjoint_scratch(g);
+    if (st != CT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    const DeviceGeom &d = g->dg;
     CT_PHASE(CT_PH_BACK, 2, s);
-    CT_CUDA(launch_adjoint2d(g, y_dev, g->dg.ndu, 0, x_dev, nullptr, s));
+    if (d.kind == CT_CONE3D)
+        CT_CUDA(launch_adjoint3d(g, y_dev, (int64_t)d.ndv * d.ndu, d.ndu, 0, g->adj_acc_dev,
+                                 x_dev, nullptr, s));
+    else
+        CT_CUDA(launch_adjoint2d(g, y_dev, d.ndu, 0, x_dev, nullptr, s));
     return CT_OK;
 }
 
@@ -543,8 +560,10 @@ ct_status ct_geom_set_backprojector(ct_geom *g, ct_backprojector kind)
     if (!g) return einval("ct_geom_set_backprojector: null geometry");
     if (kind != CT_BACK_PIXEL && kind != CT_BACK_ADJOINT)
         return einval("ct_geom_set_backprojector: unknown backprojector");
-    if (kind == CT_BACK_ADJOINT && g->desc.kind == CT_CONE3D)
-        return einval("ct_geom_set_backprojector: the adjoint is built for 2D geometries only");
+    if (kind == CT_BACK_ADJOINT) {
+        ct_status st = adjoint_scratch(g);
+        if (st != CT_OK) return st;
+    }
     g->dg.back_adjoint = kind == CT_BACK_ADJOINT ? 1 : 0;
     return CT_OK;
 }

@@ -62,7 +62,7 @@ struct DeviceGeom {
     int sino_ld;        // padded sinogram row length: ndu + 4 (2 zero bins each side)
     int tune_a_threads; // Joseph A: rays (threads) per block, chosen by ct_geom_autotune
     int tune_a_views;   // 2D Joseph A: views per block (each warp one view)
-    int back_adjoint;   // the geometry's backprojector: 0 pixel-driven B, 1 A^T (2D)
+    int back_adjoint;   // the geometry's backprojector: 0 pixel/voxel-driven B, 1 A^T
     int tune_b_rows;    // pixel-driven B: block of 32 x tune_b_rows pixels
     int tune_b_views;   // 2D pixel-driven B: views per loop iteration (1, or 2 in paired FP32)
     int b_noclamp;      // 2D: every pixel centre projects inside the detector in every view
@@ -94,7 +94,8 @@ struct ct_geom {
     float2 *pcol_dev;   // 2D: [nx][col_pairs_ld] pairs along y; 3D: P_x, [nz + 3][slice_x]
     float *sino_pad_dev;  // [n_views][sino_view_ld]
     float2 *sino_pairs_dev; // [n_views][sino_view_ld] (bin j, bin j + 1) pairs read by B
-    double *adj_acc_dev;    // 2D: n FP64 accumulators of the matched adjoint A^T
+    double *adj_acc_dev;    // n FP64 accumulators of the matched adjoint A^T (2D: from creation;
+                            // cone: allocated when the adjoint is first selected)
     // solver workspace (grown on demand)
     struct Workspace *ws;
 };
@@ -122,6 +123,13 @@ cudaError_t launch_image_pairs(const ct_geom *g, const float *x, const int *stop
 // x = A^T y (2D matched adjoint; y with row stride y_ld and bin offset y_off)
 cudaError_t launch_adjoint2d(const ct_geom *g, const float *y, int y_ld, int y_off, float *x,
                              const int *stop, cudaStream_t s);
+// x = A^T y (cone matched adjoint; y with view stride y_view_ld, row stride y_ld, bin offset
+// y_off; acc: n FP64 accumulators)
+cudaError_t launch_adjoint3d(const ct_geom *g, const float *y, int64_t y_view_ld, int y_ld,
+                             int y_off, double *acc, float *x, const int *stop, cudaStream_t s);
+// x[i] = (float)a[i]
+cudaError_t launch_round_to_float(const double *a, int64_t n, float *x, const int *stop,
+                                  cudaStream_t s);
 // y[view][v][u] -> padded sinogram (sino_view_ld floats per view, row length sino_ld, bin u of
 // row v at index sino_row0 + v * sino_ld + u + 2).
 cudaError_t launch_pad_sino(const ct_geom *g, const float *y, float *ypad, cudaStream_t s);

@@ -139,8 +139,11 @@ cudaError_t launch_back_proj(const ct_geom *g, const float *ypad, float *x, cons
                              cudaStream_t s)
 {
     if (g->dg.back_adjoint) {
-        if (g->dg.kind == CT_CONE3D) return cudaErrorNotSupported;
-        return launch_adjoint2d(g, ypad, g->dg.sino_ld, 2, x, stop, s);
+        const DeviceGeom &d = g->dg;
+        if (d.kind == CT_CONE3D)
+            return launch_adjoint3d(g, ypad, d.sino_view_ld, d.sino_ld, d.sino_row0 + 2,
+                                    g->adj_acc_dev, x, stop, s);
+        return launch_adjoint2d(g, ypad, d.sino_ld, 2, x, stop, s);
     }
     cudaError_t e = launch_sino_pairs(g, ypad, stop, s);
     if (e != cudaSuccess) return e;
@@ -307,6 +310,14 @@ __global__ void round_to_float_kernel(const double *__restrict__ a, int64_t n, f
         x[i] = (float)a[i];
 }
 
+cudaError_t launch_round_to_float(const double *a, int64_t n, float *x, const int *stop,
+                                  cudaStream_t s)
+{
+    round_to_float_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, s>>>(
+        a, n, x, stop);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_adjoint2d(const ct_geom *g, const float *y, int y_ld, int y_off, float *x,
                              const int *stop, cudaStream_t s)
 {
@@ -317,9 +328,9 @@ cudaError_t launch_adjoint2d(const ct_geom *g, const float *y, int y_ld, int y_o
     const int64_t rays = (int64_t)d.n_views * d.ndu;
     joseph2d_adjoint_kernel<<<(unsigned)((rays + 255) / 256), 256, 0, s>>>(
         g->rays_dev, d.n_views, d.ndu, y, y_ld, y_off, d.nx, d.ny, g->adj_acc_dev, stop);
-    round_to_float_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, s>>>(
-        g->adj_acc_dev, n, x, stop);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_round_to_float(g->adj_acc_dev, n, x, stop, s);
 }
 
 // ---------------------------------------------------------------------------- pixel-driven B

@@ -319,6 +319,105 @@ int joseph3d_launches(const ct_geom *g)
     return (d.nz + 1 + slab - 1) / slab;
 }
 
+// ---------------------------------------------------------------------------- matched adjoint
+// x = A^T y for the cone Joseph projector (the matched case of Sec. 2): one thread per ray
+// walks the ray's samples with the forward kernel's FP32 positions (rays driven along x or y:
+// b = bmid + bslope t', z = zmid + zslope t' over the ray's in-plane range; rays driven along
+// z: x and y from the FP64 fields per plane) and scatters weight * y_ray times the four
+// bilinear weights to the taps inside the volume, by atomic FP64 additions (rounded to FP32 by
+// a second kernel).  Samples the forward kernel skips (z beyond the volume by more than a
+// plane) have all four taps outside and add nothing here either.
+__global__ void __launch_bounds__(256) joseph3d_adjoint_kernel(
+    const RayXY *__restrict__ rxy, int n_views, int ndu, int ndv, double pitch_v, double h,
+    const float *__restrict__ y, int64_t y_view_ld, int y_ld, int y_off, int nx, int ny, int nz,
+    double *__restrict__ acc, const int *stop)
+{
+    if (stop && stop[0] != 0) return;
+    const int64_t ray = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (ray >= (int64_t)n_views * ndv * ndu) return;
+    const int iu = (int)(ray % ndu);
+    const int64_t vr = ray / ndu;
+    const int iv = (int)(vr % ndv), view = (int)(vr / ndv);
+    const RayXY R = rxy[(int64_t)view * ndu + iu];
+    const float yv = y[(int64_t)view * y_view_ld + (int64_t)iv * y_ld + y_off + iu];
+    const int64_t sxy = (int64_t)nx * ny;
+    const double v = (iv - 0.5 * (ndv - 1)) * pitch_v;
+    const bool zdrive = fabs(v) * fabs(R.rda) > 1.0;
+    if (!zdrive) {
+        const int mode = (int)((R.packed >> 30) & 3);
+        const bool ax = mode == 0;
+        const int n_drive = ax ? nx : ny;
+        const float tmid = 0.5f * (float)(n_drive - 1);
+        const double zsl_d = v * R.rda;
+        const float zs = (float)zsl_d, zm = (float)(0.5 * (nz - 1) - R.sa_h * zsl_d);
+        const float s = yv * ((float)h * sqrtf(R.dxy2 + zs * zs));
+        const int lo = R.packed & 0x7fff, hi = (R.packed >> 15) & 0x7fff;
+        float tf = (float)lo - tmid;
+        for (int t = lo; t <= hi; ++t, tf += 1.f) {
+            const float pz = fmaf(zs, tf, zm), pb = fmaf(R.bslope, tf, R.bmid);
+            const float fz = floorf(pz), fb = floorf(pb);
+            const float wz = pz - fz, wb = pb - fb;
+            const int z0 = (int)fz, b0 = (int)fb;
+            if (z0 + 1 < 0 || z0 >= nz) continue;
+            // (z, b) taps: b along y when driven along x (line t = x), along x when along y
+            for (int dz = 0; dz < 2; ++dz) {
+                const int z = z0 + dz;
+                if (z < 0 || z >= nz) continue;
+                const float wzz = dz ? wz : 1.f - wz;
+                for (int db = 0; db < 2; ++db) {
+                    const int b = b0 + db;
+                    const float w = wzz * (db ? wb : 1.f - wb);
+                    if (ax) {
+                        if (b >= 0 && b < ny)
+                            atomicAdd(acc + (int64_t)z * sxy + (int64_t)b * nx + t, (double)(s * w));
+                    } else {
+                        if (b >= 0 && b < nx)
+                            atomicAdd(acc + (int64_t)z * sxy + (int64_t)t * nx + b, (double)(s * w));
+                    }
+                }
+            }
+        }
+    } else {
+        const Ray3D q = setup_ray3d(R, iv, ndv, pitch_v, h, nx, ny, nz);
+        const float s = yv * q.weight;
+        const double zt = 0.5 * (nz - 1);
+        for (int t = q.lo; t <= q.hi; ++t) {
+            const double tfd = t - zt;
+            const float pxf = (float)(q.xmid + q.xs * tfd), pyf = (float)(q.ymid + q.ys * tfd);
+            const float fx = floorf(pxf), fy = floorf(pyf);
+            const float wx = pxf - fx, wy = pyf - fy;
+            const int x0 = (int)fx, y0 = (int)fy;
+            for (int dy = 0; dy < 2; ++dy) {
+                const int yy = y0 + dy;
+                if (yy < 0 || yy >= ny) continue;
+                const float wyy = dy ? wy : 1.f - wy;
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int xx = x0 + dx;
+                    if (xx < 0 || xx >= nx) continue;
+                    atomicAdd(acc + (int64_t)t * sxy + (int64_t)yy * nx + xx,
+                              (double)(s * (wyy * (dx ? wx : 1.f - wx))));
+                }
+            }
+        }
+    }
+}
+
+cudaError_t launch_adjoint3d(const ct_geom *g, const float *y, int64_t y_view_ld, int y_ld,
+                             int y_off, double *acc, float *x, const int *stop, cudaStream_t s)
+{
+    const DeviceGeom &d = g->dg;
+    const int64_t n = (int64_t)d.nx * d.ny * d.nz;
+    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)n, s);
+    if (e != cudaSuccess) return e;
+    const int64_t rays = (int64_t)d.n_views * d.ndv * d.ndu;
+    joseph3d_adjoint_kernel<<<(unsigned)((rays + 255) / 256), 256, 0, s>>>(
+        d.rays_xy, d.n_views, d.ndu, d.ndv, (double)g->desc.pitch_v, g->desc.pixel, y, y_view_ld,
+        y_ld, y_off, d.nx, d.ny, d.nz, acc, stop);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_round_to_float(acc, n, x, stop, s);
+}
+
 // ---------------------------------------------------------------------------- voxel-driven B
 // One thread per (x, y) column and kZChunk consecutive z; blocks of 32 x 4 columns; all views
 // per thread (per-view cos and sin staged in shared memory).  With p the voxel centre in units
