@@ -156,17 +156,25 @@ __global__ void __launch_bounds__(256) joseph3d_kernel(
         // branch-free body (positions are clamped, so every load is in bounds; a sample outside
         // the lane's range or the slab is weighted by zero), unrolled so that the loads of
         // several planes are in flight together
+        // the z and in-plane coordinates of a sample as one pair (z, b): positions, floors and
+        // weights in paired FP32 arithmetic, the same operations per coordinate
+        const float2 sl2 = make_float2(zs, bsl), mid2 = make_float2(zm, bmid);
+        const float2 m1 = make_float2(-1.f, -1.f), one2 = make_float2(1.f, 1.f);
+        float2 tf2 = make_float2(tf, tf);
         for (int t0 = wlo; t0 <= whi; t0 += chunk) {
             const int t1 = min(whi, t0 + chunk - 1);
             const uint64_t cb = lbase + 8ull * (uint64_t)t0 * (uint64_t)ld;
-            float Kb = kFloorK0;
+            float2 K2 = make_float2(kFloorK0, kFloorK0);     // (z, b + (t - t0) ld)
+            const float2 dK2 = make_float2(0.f, (float)ld);
 #pragma unroll 4
             for (int t = t0; t <= t1; ++t) {
-                const float pz = fminf(fmaxf(fmaf(zs, tf, zm), -1.f), zhi);
-                const float pb = fminf(fmaxf(fmaf(bsl, tf, bmid), -1.f), bhi);
-                const float sb = __fadd_rd(pb, Kb), sz = __fadd_rd(pz, kFloorK0);
-                const float fz = sz - kFloorK0;
-                const float wb = pb - (sb - Kb), wz = pz - fz;
+                const float2 q2 = __ffma2_rn(sl2, tf2, mid2);
+                const float2 p2 = make_float2(fminf(fmaxf(q2.x, -1.f), zhi), fminf(fmaxf(q2.y, -1.f), bhi));
+                const float2 s2 = __fadd2_rd(p2, K2);                  // (sz, sb)
+                const float2 fl2 = __ffma2_rn(K2, m1, s2);             // (fz, sb - Kb)
+                const float2 w2 = __ffma2_rn(fl2, m1, p2);             // (wz, wb)
+                const float fz = fl2.x, wz = w2.x, wb = w2.y;
+                const float sb = s2.y, sz = s2.x;
                 const uint64_t a0 = cb + 8ull * __float_as_uint(sb) + zsl8 * __float_as_uint(sz);
                 const float2 p0 = __ldg(reinterpret_cast<const float2 *>(a0));
                 const float2 p1 = __ldg(reinterpret_cast<const float2 *>(a0 + zsl8));
@@ -175,8 +183,8 @@ __global__ void __launch_bounds__(256) joseph3d_kernel(
                 const bool in = t >= lo && t <= hi && (!SLAB || (fz >= fz_lo && fz < fz_hi));
                 acc += in ? fmaf(wz, a1v - a0v, a0v) : 0.f;
                 any |= in;
-                tf += 1.f;
-                Kb += (float)ld;
+                tf2 = __fadd2_rn(tf2, one2);
+                K2 = __fadd2_rn(K2, dK2);
             }
         }
     }
