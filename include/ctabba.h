@@ -215,13 +215,14 @@ typedef struct {
                         reads one slab of the volume's pair layouts, so it stays in L2    */
     int b_rows;      /* 2D pixel-driven B: pixel rows per block                           */
     int b_views;     /* 2D pixel-driven B: views per loop iteration (1, or 2 with paired FP32
-                        arithmetic; the same operations, so results do not change)         */
+                        arithmetic, gathers in batches of 8 view pairs, at most 8 rows per
+                        block; the same operations, so results do not change)              */
 } ct_launch_shapes;
 
 /* Time the candidate launch shapes of the projectors on this geometry and keep the fastest for
  * later calls on `g`.  2D: Joseph A with (threads, views) per block in (128, 1), (128, 2),
  * (128, 4), (256, 1), (256, 2), (256, 4), (512, 4), (512, 8); pixel-driven B with 4, 8 or 16
- * pixel rows per block and 1 or 2 views per loop iteration.  3D: Joseph (slab thickness, detector
+ * pixel rows per block and one view per loop iteration, or 4 or 8 rows and two.  3D: Joseph (slab thickness, detector
  * rows per block) in (16, 1), (16, 4), (16, 8), (64, 4), (64, 8) and one pass over the whole
  * volume with 1, 4 or 8 rows (the voxel-driven
  * B has one shape, 32 x 4 columns of 8 voxels).  The shapes change only the order of work, not
@@ -232,7 +233,8 @@ ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_shapes *out
 /* Set the projectors' launch shapes of `g` explicitly (for instance a shape an earlier autotune
  * found, or a fixed one for timing).  Values: a_threads in {128, 256, 512} with a_threads /
  * a_views >= 32 and a_views in {1, 2, 4, 8} (2D), a_slab >= 1 (3D; >= nz + 1 is one pass),
- * a_views in 1..8 detector rows (3D), b_rows in {4, 8, 16}, b_views in {1, 2}; anything else
+ * a_views in 1..8 detector rows (3D), b_rows in {4, 8, 16}, b_views in {1, 2} (b_rows 16 only
+ * with b_views 1); anything else
  * returns CT_EINVAL and leaves `g` unchanged.  Host-only; shapes change the order of work, not a
  * sample's arithmetic. */
 ct_status ct_geom_set_launch_shapes(ct_geom *g, const ct_launch_shapes *shapes);

@@ -1196,7 +1196,9 @@ extern "C" ct_status ct_geom_set_launch_shapes(ct_geom *g, const ct_launch_shape
         for (int u : set) if (v == u) return true;
         return false;
     };
-    bool ok = in(sh->b_rows, {4, 8, 16}) && in(sh->b_views, {1, 2});
+    // the paired-view B kernel is compiled for blocks of at most 256 threads (8 rows)
+    bool ok = in(sh->b_rows, {4, 8, 16}) && in(sh->b_views, {1, 2}) &&
+              !(sh->b_views == 2 && sh->b_rows > 8);
     if (cone)
         ok = ok && sh->a_slab >= 1 && sh->a_views >= 1 && sh->a_views <= 8;
     else
@@ -1283,7 +1285,7 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
     // 3D: (z-slab thickness, detector rows per block); 1 << 20 = one pass over the volume
     static const int a3[8][2] = {{16, 1}, {16, 4}, {16, 8}, {64, 4}, {64, 8},
                                  {1 << 20, 1}, {1 << 20, 4}, {1 << 20, 8}};
-    static const int b2[6][2] = {{4, 1}, {8, 1}, {16, 1}, {4, 2}, {8, 2}, {16, 2}};
+    static const int b2[5][2] = {{4, 1}, {8, 1}, {16, 1}, {4, 2}, {8, 2}};
     auto fwd = [&]() { return launch_forward_proj(g, y, true, nullptr, s); };
     ct_status st;
     if (cone)
@@ -1294,7 +1296,7 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
             dg.tune_a_views = a2[c][1];
         });
     if (st == CT_OK && !cone)
-        st = time_best([&]() { return launch_back_proj(g, y, x, nullptr, s); }, 6, [&](int c) {
+        st = time_best([&]() { return launch_back_proj(g, y, x, nullptr, s); }, 5, [&](int c) {
             dg.tune_b_rows = b2[c][0];
             dg.tune_b_views = b2[c][1];
         });

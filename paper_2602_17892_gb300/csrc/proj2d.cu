@@ -339,9 +339,13 @@ cudaError_t launch_adjoint2d(const ct_geom *g, const float *y, int y_ld, int y_o
 // Parallel: bin position fj = a (c - cm) + b (r - rm) + (nd-1)/2, weight h^2/pitch.
 // Fan:      pe = p.e_u, bb = SID - p.(cos, sin) (in units of h), u = SDD pe / bb,
 //           weight h SDD / pitch * sqrt(1 + (pe/bb)^2) / bb  (= h^2 (SDD^2+u^2)/(L pitch SDD)).
-// VP = 2 takes two views per loop iteration with paired FP32 arithmetic (one fma.f32x2 forms
-// both views' values; the kernel is issue-bound), in the same operations and order as VP = 1,
-// so the launch shape never changes a result.
+// VP = 2 takes two views at a time with paired FP32 arithmetic (one fma.f32x2 forms both
+// views' values), in the same operations and order as VP = 1, so the launch shape never
+// changes a result.  It works through batches of kBPBatch view pairs: first the positions and
+// weights of the whole batch, then its 2 kBPBatch sinogram gathers, then the sums, so that
+// each warp has that many gathers in flight (the kernel is bound by the gathers' latency, and
+// the compiler does not hoist loads that far across the accumulation chain by itself); the
+// launch bounds trade occupancy (24 warps per SM) for the registers this takes.
 // floor(fj) and the pair address come from one round-down addition (as in the Joseph kernel):
 // K = 2^23 + (v - v0) ld over chunks of views; fj >= 0 in the padded row.
 // CLAMP = false when every pixel centre of the image projects inside the detector in every
@@ -370,8 +374,39 @@ __device__ __forceinline__ void pixbp2d_view(const float4 V, float tc, float tr,
     acc = fmaf(w, fmaf(f, ab.y - ab.x, ab.x), acc);
 }
 
+// positions, weights and tap-pair indices of views (2j, 2j + 1) for the paired loop
+template <bool FAN, bool CLAMP>
+__device__ __forceinline__ void pixbp2d_pair(const float4 V, float2 tr2, float2 tc2, float2 ntc2,
+                                             float2 ntr2, float2 sid2, float2 ku2, float2 gam2,
+                                             float hi, float2 K2, float2 &f2, float2 &w2,
+                                             uint32_t &ia, uint32_t &ib)
+{
+    const float2 one2 = make_float2(1.f, 1.f), m1 = make_float2(-1.f, -1.f);
+    float2 fj2;
+    if (FAN) {
+        const float2 cs2 = make_float2(V.x, V.y), sn2 = make_float2(V.z, V.w);
+        const float2 pe2 = __ffma2_rn(tr2, cs2, __fmul2_rn(ntc2, sn2));
+        const float2 bb2 = __ffma2_rn(ntc2, cs2, __ffma2_rn(ntr2, sn2, sid2));
+        const float2 rb2 = make_float2(__fdividef(1.f, bb2.x), __fdividef(1.f, bb2.y));
+        const float2 t12 = __fmul2_rn(pe2, rb2);
+        fj2 = __ffma2_rn(t12, ku2, gam2);
+        const float2 s2 = __ffma2_rn(t12, t12, one2);
+        w2 = __fmul2_rn(rb2, make_float2(sqrtf(s2.x), sqrtf(s2.y)));
+    } else {
+        fj2 = __ffma2_rn(make_float2(V.x, V.y), tc2, __ffma2_rn(make_float2(V.z, V.w), tr2, gam2));
+        w2 = one2;
+    }
+    if (CLAMP) fj2 = make_float2(fminf(fmaxf(fj2.x, 0.f), hi), fminf(fmaxf(fj2.y, 0.f), hi));
+    const float2 sk2 = __fadd2_rd(fj2, K2);
+    f2 = __ffma2_rn(__ffma2_rn(K2, m1, sk2), m1, fj2);   // fj - (sk - K)
+    ia = __float_as_uint(sk2.x);
+    ib = __float_as_uint(sk2.y);
+}
+
+constexpr int kBPBatch = 8;   // view pairs per batch of the paired loop
+
 template <bool FAN, bool CLAMP, int VP>
-__global__ void __launch_bounds__(512) pixbp2d_kernel(
+__global__ void __launch_bounds__(VP == 2 ? 256 : 512, VP == 2 ? 3 : 1) pixbp2d_kernel(
     const ViewBP *__restrict__ views, int n_views, const float2 *__restrict__ ypair, int ld,
     int vchunk, int nd, int nx, int ny, float sid_h, float k_u, float k_w, float w_par,
     float *__restrict__ x, const int *stop)
@@ -407,39 +442,44 @@ __global__ void __launch_bounds__(512) pixbp2d_kernel(
         const float2 tc2 = make_float2(tc, tc), tr2 = make_float2(tr, tr);
         const float2 ntc2 = make_float2(-tc, -tc), ntr2 = make_float2(-tr, -tr);
         const float2 sid2 = make_float2(sid_h, sid_h), ku2 = make_float2(k_u, k_u);
-        const float2 gam2 = make_float2(gam, gam), one2 = make_float2(1.f, 1.f);
-        const float2 m1 = make_float2(-1.f, -1.f);
+        const float2 gam2 = make_float2(gam, gam);
         const int vch = vchunk & ~1;
         for (int v0 = 0; v0 < 2 * npair; v0 += vch) {
             const int v1 = min(2 * npair, v0 + vch);
             const uint64_t rb = ybase + 8ull * (uint64_t)v0 * (uint64_t)ld;
             float2 K2 = make_float2(kFloor2p23, kFloor2p23 + (float)ld);
             const float2 dK2 = make_float2(2.f * (float)ld, 2.f * (float)ld);
-#pragma unroll 4
-            for (int vv = v0; vv < v1; vv += 2) {
-                const float4 V = sview[vv >> 1];
-                float2 fj2, w2;
-                if (FAN) {
-                    const float2 cs2 = make_float2(V.x, V.y), sn2 = make_float2(V.z, V.w);
-                    const float2 pe2 = __ffma2_rn(tr2, cs2, __fmul2_rn(ntc2, sn2));
-                    const float2 bb2 = __ffma2_rn(ntc2, cs2, __ffma2_rn(ntr2, sn2, sid2));
-                    const float2 rb2 = make_float2(__fdividef(1.f, bb2.x), __fdividef(1.f, bb2.y));
-                    const float2 t12 = __fmul2_rn(pe2, rb2);
-                    fj2 = __ffma2_rn(t12, ku2, gam2);
-                    const float2 s2 = __ffma2_rn(t12, t12, one2);
-                    w2 = __fmul2_rn(rb2, make_float2(sqrtf(s2.x), sqrtf(s2.y)));
-                } else {
-                    fj2 = __ffma2_rn(make_float2(V.x, V.y), tc2,
-                                     __ffma2_rn(make_float2(V.z, V.w), tr2, gam2));
-                    w2 = one2;
+            const int j0 = v0 >> 1, j1 = v1 >> 1;
+            const int jfull = j1 - (j1 - j0) % kBPBatch;
+            for (int jb = j0; jb < jfull; jb += kBPBatch) {
+                float2 f[kBPBatch], w[kBPBatch], a[kBPBatch], b[kBPBatch];
+                uint32_t ia[kBPBatch], ib[kBPBatch];
+#pragma unroll
+                for (int q = 0; q < kBPBatch; ++q) {
+                    pixbp2d_pair<FAN, CLAMP>(sview[jb + q], tr2, tc2, ntc2, ntr2, sid2, ku2, gam2,
+                                             hi, K2, f[q], w[q], ia[q], ib[q]);
+                    K2 = __fadd2_rn(K2, dK2);
                 }
-                if (CLAMP) fj2 = make_float2(fminf(fmaxf(fj2.x, 0.f), hi), fminf(fmaxf(fj2.y, 0.f), hi));
-                const float2 sk2 = __fadd2_rd(fj2, K2);
-                const float2 f2 = __ffma2_rn(__ffma2_rn(K2, m1, sk2), m1, fj2);   // fj - (sk - K)
-                const float2 a = __ldg(reinterpret_cast<const float2 *>(rb + 8ull * __float_as_uint(sk2.x)));
-                const float2 b = __ldg(reinterpret_cast<const float2 *>(rb + 8ull * __float_as_uint(sk2.y)));
-                acc = fmaf(w2.x, fmaf(f2.x, a.y - a.x, a.x), acc);
-                acc = fmaf(w2.y, fmaf(f2.y, b.y - b.x, b.x), acc);
+#pragma unroll
+                for (int q = 0; q < kBPBatch; ++q) {
+                    a[q] = __ldg(reinterpret_cast<const float2 *>(rb + 8ull * ia[q]));
+                    b[q] = __ldg(reinterpret_cast<const float2 *>(rb + 8ull * ib[q]));
+                }
+#pragma unroll
+                for (int q = 0; q < kBPBatch; ++q) {
+                    acc = fmaf(w[q].x, fmaf(f[q].x, a[q].y - a[q].x, a[q].x), acc);
+                    acc = fmaf(w[q].y, fmaf(f[q].y, b[q].y - b[q].x, b[q].x), acc);
+                }
+            }
+            for (int jj = jfull; jj < j1; ++jj) {
+                float2 f, w;
+                uint32_t ia, ib;
+                pixbp2d_pair<FAN, CLAMP>(sview[jj], tr2, tc2, ntc2, ntr2, sid2, ku2, gam2, hi, K2,
+                                         f, w, ia, ib);
+                const float2 a = __ldg(reinterpret_cast<const float2 *>(rb + 8ull * ia));
+                const float2 b = __ldg(reinterpret_cast<const float2 *>(rb + 8ull * ib));
+                acc = fmaf(w.x, fmaf(f.x, a.y - a.x, a.x), acc);
+                acc = fmaf(w.y, fmaf(f.y, b.y - b.x, b.x), acc);
                 K2 = __fadd2_rn(K2, dK2);
             }
         }
@@ -478,6 +518,7 @@ cudaError_t launch_pixbp2d(const ct_geom *g, const float2 *ypad, float *x, const
 {
     const DeviceGeom &d = g->dg;
     const bool fan = d.kind == CT_FANFLAT2D, clamp = !d.b_noclamp, two = d.tune_b_views == 2;
+    if (two && d.tune_b_rows > 8) return cudaErrorInvalidConfiguration;   // 256-thread bound
     if (fan) {
         if (clamp) two ? launch_pixbp2d_t<true, true, 2>(g, ypad, x, stop, s)
                        : launch_pixbp2d_t<true, true, 1>(g, ypad, x, stop, s);

@@ -86,7 +86,7 @@ def test_abba_solve_one_shot_and_breakdown_inside_batch():
     sh = ct_geom_autotune(G2)
     assert (sh["a_threads"], sh["a_views"]) in ((128, 1), (128, 2), (128, 4), (256, 1), (256, 2),
                                                 (256, 4), (512, 4), (512, 8))
-    assert sh["b_rows"] in (4, 8, 16) and sh["b_views"] in (1, 2)
+    assert (sh["b_rows"], sh["b_views"]) in ((4, 1), (8, 1), (16, 1), (4, 2), (8, 2))
     bs = [to_dev(b1), torch.zeros(G2.m, dtype=torch.float32, device="cuda")]
     xs = [torch.zeros(G.n, dtype=torch.float32, device="cuda") for G in (G1, G2)]
     infos = abba_solve([G1, G2], bs, xs, methods=["ab", "ab"], max_iters=8, rule="gcv")

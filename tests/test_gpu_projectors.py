@@ -78,9 +78,46 @@ def test_launch_shapes_leave_results_bitwise_unchanged(name):
     base = ct_geom_get_launch_shapes(G)
     ya, xb = gpu_A(G, x), gpu_B(G, y)
     for a_threads, a_views in ((128, 1), (256, 2), (512, 8), (128, 4)):
-        for b_rows, b_views in ((4, 1), (8, 2), (16, 2)):
+        for b_rows, b_views in ((4, 1), (8, 2), (16, 1), (4, 2)):
             sh = dict(base, a_threads=a_threads, a_views=a_views, b_rows=b_rows, b_views=b_views)
             ct_geom_set_launch_shapes(G, sh)
             assert ct_geom_get_launch_shapes(G) == sh
             assert np.array_equal(gpu_A(G, x), ya)
             assert np.array_equal(gpu_B(G, y), xb)
+
+
+@pytest.mark.parametrize("kind", ["parallel", "fan"])
+def test_backprojector_view_chunks(kind):
+    """More views than one chunk of the round-down floor's offset range (2^22 floats of padded
+    sinogram): 501 views of 19001 bins make chunks of 220 views, so the paired loop meets full
+    chunks of 13 gather batches and 6 single pairs, a last chunk of 3 batches and 6 pairs, and
+    an odd last view; every B launch shape agrees with the oracle and bit for bit with the
+    others."""
+    from paper_2602_17892_gb300 import ct_geom_get_launch_shapes, ct_geom_set_launch_shapes
+    if kind == "parallel":
+        g = synth.parallel2d(16, 501, 19001, pitch=0.002)
+    else:
+        g = synth.fanflat2d(16, 501, 19001, 60.0, 100.0)
+    y = f32(np.abs(synth.standard_normal(g.m, 31)) + 1.0)
+    G = gpu_geom(g)
+    xo = OP.back_pixel(g, y).reshape(-1)
+    base = ct_geom_get_launch_shapes(G)
+    ref = None
+    for b_rows, b_views in ((8, 1), (8, 2), (4, 2), (16, 1)):
+        ct_geom_set_launch_shapes(G, dict(base, b_rows=b_rows, b_views=b_views))
+        xg = gpu_B(G, y)
+        assert rel(xg, xo) <= TOL
+        if ref is None:
+            ref = xg
+        assert np.array_equal(xg, ref)
+
+
+def test_paired_backprojector_rejects_tall_blocks():
+    """The paired-view B kernel is built for blocks of at most 8 pixel rows (256 threads)."""
+    from paper_2602_17892_gb300 import _binding as Bn
+    from paper_2602_17892_gb300 import ct_geom_get_launch_shapes, ct_geom_set_launch_shapes
+    G = gpu_geom(GEOMS["fan_64"])
+    base = ct_geom_get_launch_shapes(G)
+    with pytest.raises(Bn.CtError):
+        ct_geom_set_launch_shapes(G, dict(base, b_rows=16, b_views=2))
+    assert ct_geom_get_launch_shapes(G) == base
