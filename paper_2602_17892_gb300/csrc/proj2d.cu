@@ -168,10 +168,14 @@ cudaError_t launch_back_proj(const ct_geom *g, const float *ypad, float *x, cons
 // to FP32 rounding, so the pair index stays in [-1, n_other + 1], which the layouts hold as
 // zero pairs (a zero line before line 0 and at least n_other + 2 pairs per line); a lane
 // outside its own range skips the load.
-// Lines t in [ta, tb] of one ray, two per loop iteration (t and t + 1): both samples'
-// positions, floors and weights in paired FP32 arithmetic (one fma.f32x2 / add.rm.f32x2 each,
-// the same operations per sample as one line at a time), accumulated in line order.  K carries
-// (t - ta) * stride (below 2^22 for every t).
+// Lines t in [ta, tb] of one ray, two at a time (t and t + 1): both samples' positions, floors
+// and weights in paired FP32 arithmetic (one fma.f32x2 / add.rm.f32x2 each, the same operations
+// per sample as one line at a time), accumulated in line order.  K carries (t - ta) * stride
+// (below 2^22 for every t).  The lines go in batches of NB pairs: first all positions and
+// floors, then all 2 NB gathers, then the sums in line order, so that each thread has 2 NB
+// gathers in flight (the kernel is bound by the gathers' latency; the compiler does not hoist
+// loads that far across the accumulation chain by itself); single pairs finish the range.
+template <int NB>
 __device__ __forceinline__ float joseph2d_span(int ta, int tb, int t_lo, int t_hi, float pmid,
                                                float slope, float tmid, int stride,
                                                uint64_t abase, float acc)
@@ -182,11 +186,43 @@ __device__ __forceinline__ float joseph2d_span(int ta, int tb, int t_lo, int t_h
     const float2 d2 = make_float2(2.f, 2.f), dK2 = make_float2(2.f * (float)stride, 2.f * (float)stride);
     const float2 m1 = make_float2(-1.f, -1.f);
     const uint64_t lb = abase + 8ull * (uint64_t)ta * (uint64_t)stride;
-#pragma unroll 2
-    for (int t = ta; t <= tb; t += 2) {
+    int t = ta;
+    // tb - t: a warp whose lanes all have empty ranges has ta = INT_MAX and tb = -1, for which
+    // t + 2 NB - 1 would overflow; tb - t >= INT_MIN does not
+    for (; tb - t >= 2 * NB - 1; t += 2 * NB) {
+        float2 f[NB], pa[NB], pb[NB];
+        uint32_t ia[NB], ib[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const float2 pos2 = __ffma2_rn(sl2, tf2, pm2);
+            const float2 sk2 = __fadd2_rd(pos2, K2);
+            f[q] = __ffma2_rn(__ffma2_rn(K2, m1, sk2), m1, pos2);   // pos - (sk - K)
+            ia[q] = __float_as_uint(sk2.x);
+            ib[q] = __float_as_uint(sk2.y);
+            tf2 = __fadd2_rn(tf2, d2);
+            K2 = __fadd2_rn(K2, dK2);
+        }
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const int tq = t + 2 * q;
+            pa[q] = make_float2(0.f, 0.f);
+            pb[q] = make_float2(0.f, 0.f);
+            if (tq >= t_lo && tq <= t_hi)
+                pa[q] = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * ia[q]));
+            if (tq + 1 >= t_lo && tq + 1 <= t_hi)
+                pb[q] = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * ib[q]));
+        }
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const int tq = t + 2 * q;
+            if (tq >= t_lo && tq <= t_hi) acc += fmaf(f[q].x, pa[q].y - pa[q].x, pa[q].x);
+            if (tq + 1 >= t_lo && tq + 1 <= t_hi) acc += fmaf(f[q].y, pb[q].y - pb[q].x, pb[q].x);
+        }
+    }
+    for (; t <= tb; t += 2) {
         const float2 pos2 = __ffma2_rn(sl2, tf2, pm2);
         const float2 sk2 = __fadd2_rd(pos2, K2);
-        const float2 f2 = __ffma2_rn(__ffma2_rn(K2, m1, sk2), m1, pos2);   // pos - (sk - K)
+        const float2 f2 = __ffma2_rn(__ffma2_rn(K2, m1, sk2), m1, pos2);
         if (t >= t_lo && t <= t_hi) {
             const float2 p = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * __float_as_uint(sk2.x)));
             acc += fmaf(f2.x, p.y - p.x, p.x);
@@ -202,8 +238,11 @@ __device__ __forceinline__ float joseph2d_span(int ta, int tb, int t_lo, int t_h
 }
 
 // CHUNKED: the lines are walked in chunks of `chunk` (images whose line offsets exceed 2^22)
+constexpr int kJBatch = 4;   // line pairs per batch of the Joseph loop
+
+// at most 64 registers a thread (two blocks of 512 threads per SM) for the batched gathers
 template <bool CHUNKED>
-__global__ void __launch_bounds__(512) joseph2d_kernel(
+__global__ void __launch_bounds__(512, 2) joseph2d_kernel(
     const Ray2D *__restrict__ rays, int n_views, int ndu, int vpb,
     const float2 *__restrict__ prow, int prow_ld, const float2 *__restrict__ pcol, int pcol_ld,
     int chunk, int nx, int ny, float *__restrict__ y, int y_ld, int y_off, const int *stop)
@@ -231,11 +270,12 @@ __global__ void __launch_bounds__(512) joseph2d_kernel(
                            8ull * ((uint64_t)__float_as_uint(kFloor2p23) + 1ull);
     float acc = 0.f;
     if (!CHUNKED) {
-        acc = joseph2d_span(wlo, whi, t_lo, t_hi, R.pmid, R.slope, tmid, stride, abase, acc);
+        acc = joseph2d_span<kJBatch>(wlo, whi, t_lo, t_hi, R.pmid, R.slope, tmid, stride, abase,
+                                     acc);
     } else {
         for (int t0 = wlo; t0 <= whi; t0 += chunk)
-            acc = joseph2d_span(t0, min(whi, t0 + chunk - 1), t_lo, t_hi, R.pmid, R.slope, tmid,
-                                stride, abase, acc);
+            acc = joseph2d_span<kJBatch>(t0, min(whi, t0 + chunk - 1), t_lo, t_hi, R.pmid,
+                                         R.slope, tmid, stride, abase, acc);
     }
     if (valid) y[(int64_t)view0 * y_ld + y_off + bin] = acc * R.weight;
 }
