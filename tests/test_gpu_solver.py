@@ -76,6 +76,39 @@ def test_projected_solve_matches_oracle(k, rule):
     assert rel(y.cpu().numpy(), y_o) <= 1e-8
 
 
+@pytest.mark.parametrize("k", [3, 40, 100])
+@pytest.mark.parametrize("where", ["below", "above", "near_pairs"])
+def test_projected_dp_bracket_ends(k, where):
+    """The discrepancy rule when the target lies outside [rho(sigma_1 1e-8), rho(sigma_1)]
+    (lambda is then that end of the search range) and on a Hessenberg matrix whose singular
+    values come in near pairs."""
+    torch = _torch()
+    from paper_2602_17892_gb300 import ct_projected_solve, build
+    build.build()
+    H = _hessenberg(k, 2000 + k, decay=-3)
+    if where == "near_pairs":
+        # near-degenerate singular value pairs: two copies of each column scale
+        H[:, 1::2] = H[:, 0:k - 1:2] * (1.0 + 1e-9)
+        H = np.triu(H, -1)
+    beta = 2.3
+    s, c, Vt = OS.projected_svd(H, beta)
+    lo = math.sqrt(OS.residual_sq(s[0] * 1e-8, s, c))
+    hi = math.sqrt(OS.residual_sq(s[0], s, c))
+    target = {"below": 0.5 * lo, "above": 2.0 * hi, "near_pairs": 0.5 * (lo + hi)}[where]
+    lam_o = OS.choose_lambda("dp", s, c, None, target)
+    y_o = OS.tikhonov_y(lam_o, s, c, Vt)
+    r_o = math.sqrt(OS.residual_sq(lam_o, s, c))
+    Hd = torch.from_numpy(np.asfortranarray(H).reshape(-1, order="F").copy()).cuda()
+    y = torch.zeros(k, dtype=torch.float64, device="cuda")
+    lam = torch.zeros(1, dtype=torch.float64, device="cuda")
+    res = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ct_projected_solve(Hd, k + 1, k, beta, "dp", 0.0, target, y, lam, res)
+    torch.cuda.synchronize()
+    assert abs(lam.item() - lam_o) <= 1e-9 * lam_o
+    assert abs(res.item() - r_o) <= 1e-9 * r_o + 1e-14
+    assert rel(y.cpu().numpy(), y_o) <= 1e-8
+
+
 # ----------------------------------------------------------------------------- Arnoldi step
 @pytest.mark.parametrize("L,k", [(4096, 0), (555_840, 7), (262_144, 40), (1_000, 3)])
 def test_arnoldi_step_matches_fp64_gram_schmidt(L, k):
