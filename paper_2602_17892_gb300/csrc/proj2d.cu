@@ -173,8 +173,8 @@ cudaError_t launch_back_proj(const ct_geom *g, const float *ypad, float *x, cons
 // per sample as one line at a time), accumulated in line order.  K carries (t - ta) * stride
 // (below 2^22 for every t).  The lines go in batches of NB pairs: first all positions and
 // floors, then all 2 NB gathers, then the sums in line order, so that each thread has 2 NB
-// gathers in flight (the kernel is bound by the gathers' latency; the compiler does not hoist
-// loads that far across the accumulation chain by itself); single pairs finish the range.
+// gathers in flight (with one pair per iteration the kernel waited on its gathers: 14
+// long-scoreboard stalls per issue); single pairs finish the range.
 template <int NB>
 __device__ __forceinline__ float joseph2d_span(int ta, int tb, int t_lo, int t_hi, float pmid,
                                                float slope, float tmid, int stride,
@@ -383,9 +383,9 @@ cudaError_t launch_adjoint2d(const ct_geom *g, const float *y, int y_ld, int y_o
 // views' values), in the same operations and order as VP = 1, so the launch shape never
 // changes a result.  It works through batches of kBPBatch view pairs: first the positions and
 // weights of the whole batch, then its 2 kBPBatch sinogram gathers, then the sums, so that
-// each warp has that many gathers in flight (the kernel is bound by the gathers' latency, and
-// the compiler does not hoist loads that far across the accumulation chain by itself); the
-// launch bounds trade occupancy (24 warps per SM) for the registers this takes.
+// each warp has that many gathers in flight (with one view pair per iteration the kernel
+// waited on its gathers: 25 long-scoreboard stalls per issue); the launch bounds trade
+// occupancy (24 warps per SM) for the registers this takes.
 // floor(fj) and the pair address come from one round-down addition (as in the Joseph kernel):
 // K = 2^23 + (v - v0) ld over chunks of views; fj >= 0 in the padded row.
 // CLAMP = false when every pixel centre of the image projects inside the detector in every
