@@ -92,8 +92,11 @@ __device__ __forceinline__ Ray3D setup_ray3d(const RayXY &R, int iv, int ndv, do
 // owns the samples whose lower tap row r = floor(z) + 1 (padded row index) lies in
 // [r_lo, r_hi); membership is decided on the same FP32 position the sample uses, so every
 // sample belongs to exactly one slab.  Launches after the first of a call add to y.
+constexpr int kJ3Batch = 4;   // planes per batch of the cone Joseph loop
+
+// at most 85 registers a thread (three blocks of 256 threads per SM) for the batched gathers
 template <bool SLAB>
-__global__ void __launch_bounds__(256) joseph3d_kernel(
+__global__ void __launch_bounds__(256, 3) joseph3d_kernel(
     const RayXY *__restrict__ rxy, int ndu, int ndv, double pitch_v, double h,
     const float2 *__restrict__ px, int64_t zsx, int ldx, const float2 *__restrict__ py,
     int64_t zsy, int ldy, int chunk, int nx, int ny, int nz, float *__restrict__ y,
@@ -154,8 +157,8 @@ __global__ void __launch_bounds__(256) joseph3d_kernel(
         const float fz_lo = (float)(r_lo - 1), fz_hi = (float)(r_hi - 1);   // slab: r = fz + 1
         float tf = (float)wlo - tmid;
         // branch-free body (positions are clamped, so every load is in bounds; a sample outside
-        // the lane's range or the slab is weighted by zero), unrolled so that the loads of
-        // several planes are in flight together
+        // the lane's range or the slab is weighted by zero), in batches of planes so that the
+        // loads of several planes are in flight together
         // the z and in-plane coordinates of a sample as one pair (z, b): positions, floors and
         // weights in paired FP32 arithmetic, the same operations per coordinate
         const float2 sl2 = make_float2(zs, bsl), mid2 = make_float2(zm, bmid);
@@ -166,8 +169,46 @@ __global__ void __launch_bounds__(256) joseph3d_kernel(
             const uint64_t cb = lbase + 8ull * (uint64_t)t0 * (uint64_t)ld;
             float2 K2 = make_float2(kFloorK0, kFloorK0);     // (z, b + (t - t0) ld)
             const float2 dK2 = make_float2(0.f, (float)ld);
+            // batches of NB planes: the NB samples' positions, weights and addresses first, then
+            // their 2 NB gathers, then the sums in plane order (the same operations and order as
+            // one plane at a time); single planes finish the range
+            constexpr int NB = kJ3Batch;
+            int t = t0;
+            for (; t1 - t >= NB - 1; t += NB) {
+                uint64_t ad[NB];
+                float wzq[NB], wbq[NB];
+                bool inq[NB];
+                float2 p0q[NB], p1q[NB];
+#pragma unroll
+                for (int q = 0; q < NB; ++q) {
+                    const float2 q2 = __ffma2_rn(sl2, tf2, mid2);
+                    const float2 p2 = make_float2(fminf(fmaxf(q2.x, -1.f), zhi), fminf(fmaxf(q2.y, -1.f), bhi));
+                    const float2 s2 = __fadd2_rd(p2, K2);
+                    const float2 fl2 = __ffma2_rn(K2, m1, s2);
+                    const float2 w2 = __ffma2_rn(fl2, m1, p2);
+                    wzq[q] = w2.x;
+                    wbq[q] = w2.y;
+                    ad[q] = cb + 8ull * __float_as_uint(s2.y) + zsl8 * __float_as_uint(s2.x);
+                    const int tq = t + q;
+                    inq[q] = tq >= lo && tq <= hi && (!SLAB || (fl2.x >= fz_lo && fl2.x < fz_hi));
+                    tf2 = __fadd2_rn(tf2, one2);
+                    K2 = __fadd2_rn(K2, dK2);
+                }
+#pragma unroll
+                for (int q = 0; q < NB; ++q) {
+                    p0q[q] = __ldg(reinterpret_cast<const float2 *>(ad[q]));
+                    p1q[q] = __ldg(reinterpret_cast<const float2 *>(ad[q] + zsl8));
+                }
+#pragma unroll
+                for (int q = 0; q < NB; ++q) {
+                    const float a0v = fmaf(wbq[q], p0q[q].y - p0q[q].x, p0q[q].x);
+                    const float a1v = fmaf(wbq[q], p1q[q].y - p1q[q].x, p1q[q].x);
+                    acc += inq[q] ? fmaf(wzq[q], a1v - a0v, a0v) : 0.f;
+                    any |= inq[q];
+                }
+            }
 #pragma unroll 4
-            for (int t = t0; t <= t1; ++t) {
+            for (; t <= t1; ++t) {
                 const float2 q2 = __ffma2_rn(sl2, tf2, mid2);
                 const float2 p2 = make_float2(fminf(fmaxf(q2.x, -1.f), zhi), fminf(fmaxf(q2.y, -1.f), bhi));
                 const float2 s2 = __fadd2_rd(p2, K2);                  // (sz, sb)
@@ -305,14 +346,12 @@ cudaError_t launch_joseph3d(const ct_geom *g, float *y, int64_t y_view_ld, int y
             joseph3d_kernel<true><<<grid, block, 0, s>>>(
                 d.rays_xy, d.ndu, d.ndv, (double)g->desc.pitch_v, h, g->pcol_dev, d.slice_x,
                 d.col_pairs_ld, g->prow_dev, d.slice_y, d.row_pairs_ld, chunk, d.nx, d.ny, d.nz, y,
-                y_view_ld, y_ld,
-                y_off, iv_lo, iv_hi, r_lo, r_hi, 1, stop);
+                y_view_ld, y_ld, y_off, iv_lo, iv_hi, r_lo, r_hi, 1, stop);
         else   // one pass: every tap row is in [0, nz + 1], no slab test
             joseph3d_kernel<false><<<grid, block, 0, s>>>(
                 d.rays_xy, d.ndu, d.ndv, (double)g->desc.pitch_v, h, g->pcol_dev, d.slice_x,
                 d.col_pairs_ld, g->prow_dev, d.slice_y, d.row_pairs_ld, chunk, d.nx, d.ny, d.nz, y,
-                y_view_ld, y_ld,
-                y_off, iv_lo, iv_hi, r_lo, r_hi, 0, stop);
+                y_view_ld, y_ld, y_off, iv_lo, iv_hi, r_lo, r_hi, 0, stop);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
