@@ -427,11 +427,11 @@ def variant_matched(P, torch, G, b_dev, x_true, noise_ab):
     return out
 
 
-def variant_batched(P, torch, n_slices=32, iters=60):
-    """A sample of the uneven batch (first `n_slices` of the 256-slice recipe: N in
-    {256..1024}, parallel/fan, 180-1440 views, 1 % noise, AB/BA by shape, 60 its, GCV): one
-    graph replay of the whole batch vs the same solves issued one after another, with
-    autotuned and with default launch shapes."""
+def variant_batched(P, torch, n_slices=32, iters=60, default_shapes=True):
+    """The uneven batch (the first `n_slices` of the 256-slice recipe: N in {256..1024},
+    parallel/fan, 180-1440 views, 1 % noise, AB/BA by shape, 60 its, GCV): one graph replay of
+    the whole batch vs the same solves issued one after another, with autotuned (and, if
+    `default_shapes`, with default) launch shapes; device memory in use during the replay."""
     import synth
     cases = synth.batched_slices(256, seed=7)[:n_slices]
     geoms, bs, xs, work = [], [], [], 0
@@ -450,17 +450,18 @@ def variant_batched(P, torch, n_slices=32, iters=60):
     total_iters = iters * len(cases)
     res = {"slices": len(cases), "iters_per_slice": iters,
            "pixels": int(sum(G.n for G in geoms)), "views": [int(c["geom"].n_views) for c in cases]}
-    for tuned in (True, False):
+    for tuned in ((True, False) if default_shapes else (True,)):
         bt = P.Batch(geoms, ["auto"] * len(geoms), max_iters=iters, rule="gcv", autotune=tuned)
         t0 = time.perf_counter()
         bt.solve(bs, xs)                          # first call captures the graph
         torch.cuda.synchronize()
         capture_s = time.perf_counter() - t0
+        free, total = torch.cuda.mem_get_info()
         ms, _ = _timed(torch, lambda: bt.solve(bs, xs))
         key = "graph_tuned" if tuned else "graph_default_shapes"
         res[key] = {"iters_s": total_iters / (ms * 1e-3), "ms": ms,
                     "gups": work / (ms * 1e-3) / 1e9, "first_call_s": capture_s,
-                    "launches_per_replay": bt.launches()}
+                    "launches_per_replay": bt.launches(), "device_gb_in_use": (total - free) / 1e9}
         bt.close()
     methods = ["ab" if G.m < G.n else "ba" for G in geoms]
 
@@ -574,9 +575,13 @@ def run_variants(P, torch, G, b_dev, x_true, noise_ab, which):
             "learned_lambda_parallel256": lambda: variant_learned(P, torch),
             "batched_slices_sample": lambda: variant_batched(P, torch),
             "matched_pair_fan512_ab": lambda: variant_matched(P, torch, G, b_dev, x_true, noise_ab),
-            "cone512": lambda: variant_cone(P, torch)}
+            "cone512": lambda: variant_cone(P, torch),
+            # the whole 256-slice batch (about 45 GB on the device, a minute or two): only when
+            # named, never part of "all"
+            "batched_slices_full": lambda: variant_batched(P, torch, n_slices=256,
+                                                           default_shapes=False)}
     for name, fn in jobs.items():
-        if which != "all" and name not in which.split(","):
+        if (which != "all" or name == "batched_slices_full") and name not in which.split(","):
             continue
         try:
             t0 = time.perf_counter()
@@ -684,7 +689,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--variants", default="all",
                     help="'all', 'none' or a comma list of: basis_precision_fan512_ab, "
-                         "learned_lambda_parallel256, batched_slices_sample, cone512")
+                         "learned_lambda_parallel256, batched_slices_sample, cone512, "
+                         "matched_pair_fan512_ab, batched_slices_full (only when named)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
