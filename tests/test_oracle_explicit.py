@@ -231,3 +231,13 @@ def test_oracle_voxel_backprojector_equals_explicit_matrix(name):
     Bo = oracle_matrix(lambda e: OP.back_pixel(g, e), g.m)
     assert np.max(np.abs(B)) > 0
     assert np.max(np.abs(Bo - B)) <= 1e-13 * np.max(np.abs(B))
+
+
+@pytest.mark.parametrize("name", ["parallel_9x7", "fan_h_1.3", "cone_4_steep"])
+def test_oracle_matched_adjoint_equals_explicit_transpose(name):
+    """The matched backprojector A^T (Sec. 2, LSQR / LSMR comparators) is the transpose of
+    the explicit Joseph matrix."""
+    g = GEOMS.get(name) or GEOMS3[name]
+    A = explicit_A3(g) if g.kind == synth.CONE3D else explicit_A(g)
+    ATo = oracle_matrix(lambda e: OP.back_adjoint(g, e), g.m)
+    assert np.max(np.abs(ATo - A.T)) <= 1e-13 * np.max(np.abs(A))
