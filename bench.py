@@ -114,6 +114,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ----------------------------------------------------------------------------- ranks
+def reduce_over_ranks(dist, device, total_ms, iters_done):
+    """Whole-job numbers of the replicas (one independent problem per rank): the slowest
+    rank's time and all ranks' iterations.  `dist` is None on one process."""
+    if dist is None:
+        return float(total_ms), float(iters_done)
+    import torch
+    t = torch.tensor([float(total_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    it = torch.tensor([float(iters_done)], device=device, dtype=torch.float64)
+    dist.all_reduce(it, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(it.item())
+
+
 # ----------------------------------------------------------------------------- workload
 def workload(seed: int):
     import synth
@@ -218,16 +232,9 @@ def bench_ours(args, rank, world, local_rank):
     launches = batch.launches() * args.steps
     step_ms = [a.elapsed_time(b_) for a, b_ in evs]
     total_ms = sum(step_ms)
+    total_ms, iters_all = reduce_over_ranks(dist, "cuda", total_ms, iters_done)
     if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        it = torch.tensor([iters_done], device="cuda", dtype=torch.float64)
-        dist.all_reduce(it, op=dist.ReduceOp.SUM)
-        iters_all = float(it.item())
         dist.barrier()
-    else:
-        iters_all = float(iters_done)
     value = iters_all / (total_ms / 1e3)
 
     # ---- per-kernel timing: the same two solves one after the other, per-phase CUDA events
@@ -265,11 +272,8 @@ def bench_ours(args, rank, world, local_rank):
         eb.record(stream)
         torch.cuda.synchronize()
         e2e_ms += ea.elapsed_time(eb)
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = e2e_iters * world / (e2e_ms / 1e3)
+    e2e_ms, e2e_iters_all = reduce_over_ranks(dist, "cuda", e2e_ms, e2e_iters)
+    e2e_value = e2e_iters_all / (e2e_ms / 1e3)
 
     if rank != 0:
         if dist:
