@@ -34,7 +34,7 @@ def _rank_main(rank, world, port, out):
 
 def test_two_gloo_ranks_reduce_time_and_iterations():
     port = _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:     # no fork of a multi-threaded process
         out = mgr.dict()
         mp.spawn(_rank_main, args=(2, port, out), nprocs=2, join=True)
         res = dict(out)
