@@ -174,8 +174,9 @@ void ct_hybrid_opts_default(ct_hybrid_opts *o);
 /* Hybrid AB-GMRES, Algorithm 1 (Sec. 3): x0 = B u0 (u0 = 0 when u0_dev is NULL),
  * r0 = b - A x0, Arnoldi on A B with classical Gram-Schmidt applied twice, lambda_k by
  * `o->rule`, y_k from Eq. (hybrid_proj) through the SVD of H_k in FP64, and
- * x_K = x0 + B W_K y_K.  b_dev: m floats; x_dev: n floats (output).  The residual of
- * Alg. 1 line 14 is not recomputed: ||b - A x_k|| equals the projected residual.
+ * x_K = x0 + B W_K y_K.  b_dev: m floats; x_dev: n floats (output).  The residual
+ * r_k = b - A x_k of Algorithm 1 is not recomputed for the norm-based rules: ||b - A x_k||
+ * equals the projected residual.
  * Allocates its workspace on the first call for a geometry (reused while max_iters and
  * basis do not grow).  Synchronises `stream` before returning to fill `info` and the
  * host histories. */
@@ -272,7 +273,7 @@ ct_status abba_solve(int n_prob, ct_geom *const *geoms, const float *const *b_de
 
 /* ------------------------------------------------------------------ building blocks */
 
-/* One Arnoldi orthogonalisation step (Sec. 2.1, Eq. (Hessenberg); Alg. 1 lines 6-11).
+/* One Arnoldi orthogonalisation step (Sec. 2.1, Eq. (Hessenberg)).
  * Allocates its scratch with stream-ordered cudaMallocAsync/cudaFreeAsync on every call.
  * given k+1 orthonormal rows W[0..k] (each `len` floats, row stride `ld` floats) and
  * q = M w_k, compute h[i] = <q, w_i> by classical Gram-Schmidt applied twice (the second

@@ -7,16 +7,20 @@ matrices, or with the matched pair B = A^T.
 
 Step by step it follows the paper:
 
-* Sec. 2.1, Eq. (AB_optimality)/(BA_optimality): the Krylov spaces of AB and BA;
-* Eq. (Hessenberg): Arnoldi with modified Gram-Schmidt (Alg. 1/2, lines 5-10), followed by
-  one full second MGS pass whose coefficients are added to H (reorthogonalisation);
+* Sec. 2.1, Eq. (AB_optimality)/(BA_optimality): the Krylov spaces of AB and BA, started from
+  r0 = b - A x0 (AB, x0 = B u0) or r0 = B (b - A x0) (BA);
+* Eq. (Hessenberg): the Arnoldi relation M W_k = W_{k+1} H_k, built with modified
+  Gram-Schmidt and one full second MGS pass whose coefficients are added to H
+  (reorthogonalisation);
 * Eq. (hybrid_proj): Tikhonov on the projected problem, solved through the SVD of the
   (k+1) x k Hessenberg matrix H_k = U diag(sigma) V^T, c = ||r0|| U^T e1,
   y = sum_i v_i sigma_i c_i / (sigma_i^2 + lambda^2);
 * Sec. 3.1: GCV(lambda) = ||H y - beta e1||^2 / trace(I - H H_lambda)^2 with
   H_lambda = (H^T H + lambda^2 I)^{-1} H^T (lambda^2 throughout, as in Eq. (tikhonov));
 * Sec. 3.2: the discrepancy principle, used here to pick lambda: ||H y - beta e1|| = tau eta;
-* Alg. 1 line 13 / Alg. 2 line 13: x_k = x0 + B W_k y_k (AB) or x0 + W_k y_k (BA).
+  the stopping criteria DP, NCP and RNS;
+* Sec. 3 (the hybrid iterate): x_k = x0 + B W_k y_k (AB) or x0 + W_k y_k (BA);
+* Sec. 3.3: restarting from the previous cycle's iterate.
 
 Readings where the paper is silent (the GPU library implements the same readings):
 * GCV minimiser: 256 log-spaced lambda in [sigma_1 1e-8, sigma_1], first grid minimum, then
@@ -24,7 +28,12 @@ Readings where the paper is silent (the GPU library implements the same readings
   refined value is kept only if it is not worse than the grid point.
 * DP as a lambda rule: solve rho(lambda) = tau * noise_norm by 60 bisection steps in log
   lambda over the same range; clamp to the range ends when there is no root.
-* x0 = 0 (u0 = 0); breakdown when h_{k+1,k} <= 1e-14 ||M w_k||.
+* x0 = 0 (u0 = 0) unless given; breakdown when h_{k+1,k} <= 1e-14 ||M w_k||.
+* NCP (Sec. 3.2, after Hansen's normalized cumulative periodogram): the data-space residual
+  b - A x_k, split into detector rows, each row's periodogram without the zero frequency,
+  normalised and accumulated; the rows' NCPs are averaged and compared with the white-noise
+  line i/q.  The iteration stops at the first checked step whose distance from that line is
+  larger than at the previous checked step, and returns the previous checked step's iterate.
 """
 from __future__ import annotations
 
@@ -192,13 +201,54 @@ def givens_gmres_y(Hk: np.ndarray, beta: float):
     return y, abs(g[k])
 
 
-# ----------------------------------------------------------------------------- Algorithms 1 / 2
+# ----------------------------------------------------------------------------- stopping rules
+
+NCP_KS_95 = 1.358      # asymptotic Kolmogorov-Smirnov critical value at 5 % significance
+
+
+def periodogram(rows: np.ndarray) -> np.ndarray:
+    """|DFT|^2 of every row of a (R, n) array at the frequencies 1..q, q = floor(n/2) (the
+    zero frequency is left out: it carries the row's mean, not its whiteness)."""
+    rows = np.asarray(rows, np.float64)
+    q = rows.shape[1] // 2
+    return np.abs(np.fft.fft(rows, axis=1)[:, 1:q + 1]) ** 2
+
+
+def ncp(rows: np.ndarray) -> np.ndarray:
+    """Normalized cumulative periodogram (Sec. 3.2; Hansen's NCP) of a residual split into
+    rows of one detector row each: per row c_i = (p_1 + ... + p_i) / (p_1 + ... + p_q), then the
+    mean over the rows whose periodogram is not zero.  For white noise c_i is close to i/q.
+    Returns None when no row has any power (an exactly fitted residual)."""
+    p = periodogram(rows)
+    tot = p.sum(axis=1)
+    keep = tot > 0
+    if not keep.any():
+        return None
+    c = np.cumsum(p[keep], axis=1) / tot[keep, None]
+    return c.mean(axis=0)
+
+
+def ncp_distance(rows: np.ndarray) -> float:
+    """||c - c_white||_2 with c_white,i = i/q (0 for a residual without power)."""
+    c = ncp(rows)
+    if c is None:
+        return 0.0
+    q = c.size
+    return float(np.linalg.norm(c - np.arange(1, q + 1) / q))
+
+
+def ncp_is_white(row: np.ndarray) -> bool:
+    """Kolmogorov-Smirnov test of one row's NCP against the white-noise line at 5 %."""
+    c = ncp(np.asarray(row, np.float64).reshape(1, -1))
+    q = c.size
+    return bool(np.max(np.abs(c - np.arange(1, q + 1) / q)) < NCP_KS_95 / math.sqrt(q))
+
 
 def stop_reached(stop_rule, resid, k: int, stop_target=None, stop_tol=None) -> bool:
-    """Stopping criteria of Sec. 3.2 on the residual norms rho_1..rho_k (resid, 0-based):
-    'dp'  stops at the first k with rho_k <= tau ||e|| (stop_target; the paper prints the
-          inequality reversed), 'rns' at the first k >= 2 with
-          |rho_{k-1} - rho_k| / rho_{k-1} < stop_tol."""
+    """Norm-based stopping criteria of Sec. 3.2 on the residual norms rho_1..rho_k (resid,
+    0-based): 'dp'  stops at the first k with rho_k <= tau ||e|| (stop_target; the paper prints
+    the inequality reversed), 'rns' at the first k >= 2 with
+    |rho_{k-1} - rho_k| / rho_{k-1} < stop_tol."""
     if stop_rule is None or stop_rule == "none":
         return False
     if stop_rule == "dp":
@@ -208,27 +258,31 @@ def stop_reached(stop_rule, resid, k: int, stop_target=None, stop_tol=None) -> b
     raise ValueError(stop_rule)
 
 
+# ----------------------------------------------------------------------------- Algorithms 1 / 2
+
 def hybrid_gmres(method: str, A, B, b, iters: int, rule: str = "gcv", lam_fixed=None,
                  dp_target=None, reorth: bool = True, keep_iterates=(), x0=None,
-                 true_residual: bool = False, stop_rule=None, stop_tol=None, stop_target=None):
+                 true_residual: bool = False, stop_rule=None, stop_tol=None, stop_target=None,
+                 ncp_row=None, stop_every: int = 1):
     """Hybrid AB-GMRES (method='ab', Algorithm 1) or hybrid BA-GMRES ('ba', Algorithm 2).
 
     A, B: callables on flat FP64 vectors.  rule in {'none', 'fixed', 'gcv', 'dp', 'lcurve'};
     dp_target is tau * ||e|| for AB and tau * ||B e|| for BA (the noise in the space where
-    Alg. 2 measures its residual).  stop_rule in {None, 'dp', 'rns'} ends the iteration early
-    (Sec. 3.2; stop_target, stop_tol).  Returns a dict with the final iterate, the
-    per-iteration lambda and projected residual, H, W, y and iterates at the steps in
-    keep_iterates.
+    Alg. 2 measures its residual).  x0: initial image (AB: x0 = B u0 for some u0).
+    stop_rule in {None, 'dp', 'rns', 'ncp'} ends the iteration early (Sec. 3.2; stop_target,
+    stop_tol; 'ncp' needs ncp_row, the detector row length that the data residual is split by,
+    and is checked at the steps stop_every, 2 stop_every, ... and the last).  Returns a dict
+    with the final iterate, the per-iteration lambda and projected residual, H, W, y, the NCP
+    distances of the checked steps and the iterates at the steps in keep_iterates.
     """
     b = np.asarray(b, dtype=np.float64).reshape(-1)
+    x0v = np.zeros_like(B(b)) if x0 is None else np.asarray(x0, np.float64).reshape(-1)
+    # Krylov spaces of Sec. 2.1, shifted by the initial guess: AB-GMRES solves A B u = r0 with
+    # r0 = b - A x0 in the data space; BA-GMRES solves B A x = r0 with r0 = B (b - A x0)
     if method == "ab":
-        # Alg. 1, lines 1-3: x0 = B u0 (u0 = 0 unless x0 is given), r0 = b - A x0
-        x0v = np.zeros_like(B(b)) if x0 is None else np.asarray(x0, np.float64).reshape(-1)
         r0 = b - A(x0v)
         M = lambda w: A(B(w))
     elif method == "ba":
-        # Alg. 2, lines 1-3: r0 = B (b - A x0)
-        x0v = np.zeros_like(B(b)) if x0 is None else np.asarray(x0, np.float64).reshape(-1)
         r0 = B(b - A(x0v))
         M = lambda w: B(A(w))
     else:
@@ -236,7 +290,8 @@ def hybrid_gmres(method: str, A, B, b, iters: int, rule: str = "gcv", lam_fixed=
 
     L = r0.size
     beta = float(np.linalg.norm(r0))
-    out = dict(lambdas=[], resid=[], status="ok", iterates={}, beta=beta, true_resid=[])
+    out = dict(lambdas=[], resid=[], status="ok", iterates={}, beta=beta, true_resid=[],
+               ncp=[])
     if beta == 0.0:
         out.update(x=x0v.copy(), H=np.zeros((1, 0)), W=np.zeros((0, L)), y=np.zeros(0), k=0,
                    status="breakdown")
@@ -246,37 +301,54 @@ def hybrid_gmres(method: str, A, B, b, iters: int, rule: str = "gcv", lam_fixed=
     W[0] = r0 / beta
     y = np.zeros(0)
     k_done = 0
+    ncp_prev = None                                      # (k, distance, y) of the last check
     for k in range(1, iters + 1):
-        q = M(W[k - 1])                                  # line 5: q_k = AB w_k (or BA w_k)
+        # Arnoldi relation M W_k = W_{k+1} H_k (Eq. (Hessenberg)): column k of H from
+        # q = M w_k by modified Gram-Schmidt, then one more full pass (reorthogonalisation)
+        q = M(W[k - 1])
         qnorm0 = float(np.linalg.norm(q))
-        for _pass in range(2 if reorth else 1):          # lines 6-9 (+ one more pass)
+        for _pass in range(2 if reorth else 1):
             for i in range(k):
                 d = float(q @ W[i])
                 H[i, k - 1] += d
                 q = q - d * W[i]
-        hk = float(np.linalg.norm(q))                    # line 10
+        hk = float(np.linalg.norm(q))
         H[k, k - 1] = hk
         broke = hk <= BREAKDOWN_TOL * qnorm0
         if not broke:
-            W[k] = q / hk                                # line 11
+            W[k] = q / hk
+        # projected Tikhonov problem (Eq. (hybrid_proj)) with lambda_k from the rule
         Hk = H[: k + 1, :k]
-        s, c, Vt = projected_svd(Hk, beta)               # line 12: find lambda
+        s, c, Vt = projected_svd(Hk, beta)
         lam = choose_lambda(rule, s, c, lam_fixed, dp_target)
-        y = tikhonov_y(lam, s, c, Vt)                    # line 13: projected Tikhonov
+        y = tikhonov_y(lam, s, c, Vt)
         out["lambdas"].append(lam)
         out["resid"].append(math.sqrt(residual_sq(lam, s, c)))
         k_done = k
-        if k in keep_iterates or true_residual:
-            xk = _form_x(method, B, x0v, W[:k], y)       # line 14
+        ncp_check = stop_rule == "ncp" and (k % stop_every == 0 or k == iters)
+        if k in keep_iterates or true_residual or ncp_check:
+            xk = _form_x(method, B, x0v, W[:k], y)       # the hybrid iterate of Sec. 3
             if k in keep_iterates:
                 out["iterates"][k] = xk
-            if true_residual:
+            if true_residual or ncp_check:
                 r = b - A(xk)
+            if true_residual:
                 out["true_resid"].append(float(np.linalg.norm(r if method == "ab" else B(r))))
+            if ncp_check:
+                dist = ncp_distance(r.reshape(-1, ncp_row))
+                out["ncp"].append((k, dist))
+                if ncp_prev is not None and dist > ncp_prev[1]:
+                    k_done, y = ncp_prev[0], ncp_prev[2]
+                    out["lambdas"] = out["lambdas"][:k_done]
+                    out["resid"] = out["resid"][:k_done]
+                    out["status"] = "stopped"
+                    break
+                ncp_prev = (k, dist, y)
         if broke:
             out["status"] = "breakdown"
             break
-        if stop_reached(stop_rule, out["resid"], k, stop_target, stop_tol):
+        if stop_rule != "ncp" and stop_reached(stop_rule, out["resid"], k, stop_target,
+                                               stop_tol):
             out["status"] = "stopped"
             break
     out.update(x=_form_x(method, B, x0v, W[:k_done], y), H=H[: k_done + 1, :k_done],
@@ -285,13 +357,15 @@ def hybrid_gmres(method: str, A, B, b, iters: int, rule: str = "gcv", lam_fixed=
 
 
 def _form_x(method, B, x0v, Wk, y):
+    """x_k = x0 + B W_k y (hybrid AB-GMRES) or x0 + W_k y (hybrid BA-GMRES), Sec. 3."""
     z = Wk.T @ y
     return x0v + (B(z) if method == "ab" else z)
 
 
-def restarted_hybrid_gmres(method, A, B, b, cycle: int, n_cycles: int, **kw):
-    """Sec. 3.3: after p = cycle iterations restart from the current iterate."""
-    x = None
+def restarted_hybrid_gmres(method, A, B, b, cycle: int, n_cycles: int, x0=None, **kw):
+    """Sec. 3.3: after p = cycle iterations the method starts again from the current iterate
+    (the first cycle from x0, zero when not given)."""
+    x = x0
     hist = []
     for _ in range(n_cycles):
         res = hybrid_gmres(method, A, B, b, cycle, x0=x, **kw)

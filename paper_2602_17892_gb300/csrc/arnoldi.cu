@@ -1,6 +1,5 @@
-// Arnoldi orthogonalisation (Sec. 2.1, Eq. (Hessenberg); Algorithm 1/2 lines 6-11) as
-// classical Gram-Schmidt applied twice, plus the basis combination x = x0 + W y of Alg. 1/2
-// line 13.
+// Arnoldi orthogonalisation (Sec. 2.1, Eq. (Hessenberg)) as classical Gram-Schmidt applied
+// twice, plus the basis combination x = x0 + W y of the hybrid iterate (Sec. 3).
 //
 // The paper's loop is modified Gram-Schmidt: h_i = <q, w_i>; q -= h_i w_i, one i at a time.
 // On a GPU each of those k dot products needs a grid-wide reduction before the next axpy.
@@ -859,7 +858,8 @@ cudaError_t arnoldi_step_basis(int basis, void *W, int64_t L, int64_t ld, int k,
     }
 }
 
-// beta = ||r||, w0 = r / beta (Alg. 1/2 line 3) in the basis type; beta stored in aux[2].
+// beta = ||r||, w0 = r / beta (the first basis vector of Algorithms 1/2) in the basis type;
+// beta stored in aux[2].
 cudaError_t normalize_first_basis(int basis, const float *r, int64_t L, void *w0,
                                   const ArnoldiScratch &sc, double *aux, int *stop, float *cur,
                                   cudaStream_t s)

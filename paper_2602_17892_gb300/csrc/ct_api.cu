@@ -662,7 +662,7 @@ static ct_status read_info(Workspace *w, const ct_hybrid_opts *o, ct_hybrid_info
     return CT_OK;
 }
 
-// The hybrid step (Alg. 1/2 lines 12-13) of step k depends only on H's first k columns, and with
+// The hybrid step (Eq. (hybrid_proj)) of step k depends only on H's first k columns, and with
 // a fixed iteration count nothing in the Arnoldi chain depends on it.  All K projected problems
 // are therefore solved after the loop in one launch, one CTA per k (the lambda_k history is
 // the same as if each had been solved inside its iteration); y is formed for the final k.
@@ -746,7 +746,7 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
     CT_CUDA(cudaMemsetAsync(w->stop, 0, 2 * sizeof(int), s));
     CT_CUDA(cudaMemsetAsync(w->counter, 0, 4 * sizeof(unsigned), s));
     CT_CUDA(cudaMemsetAsync(w->path, 0, sizeof(int) * K, s));
-    // Alg. 1 lines 1-3: x0 = B u0, r0 = b - A x0, w1 = r0 / ||r0||
+    // Algorithm 1 set-up: x0 = B u0, r0 = b - A x0, w1 = r0 / ||r0||
     {
         CT_PHASE(CT_PH_OTHER, u0_dev ? 8 : 3, s);
         CT_CUDA(launch_pad_sino(g, b_dev, w->vec, s));
@@ -768,7 +768,7 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
         const float *wk = w->cur ? w->cur : static_cast<float *>(w->W) + (int64_t)k * ld;
         {
             CT_PHASE(CT_PH_BACK, 2, s);   // pair copy + B, or A^T scatter + rounding
-            CT_CUDA(launch_back_proj(g, wk, w->img, w->stop, s));       // line 5: B w_k
+            CT_CUDA(launch_back_proj(g, wk, w->img, w->stop, s));       // q = A B w_k: B w_k
         }
         {
             CT_PHASE(CT_PH_LAYOUT, 1, s);
@@ -779,7 +779,7 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
             CT_CUDA(launch_forward_proj(g, w->q, true, w->stop, s));   //          A (B w_k)
         }
         {
-            // lines 6-11
+            // Arnoldi relation, Eq. (Hessenberg): column k of H_k and w_{k+1}
             CT_PHASE(CT_PH_ARNOLDI, arnoldi_step_launches(o->basis, ld, k, sc, o->reorth != 0, true),
                      s);
             CT_CUDA(arnoldi_step_basis(o->basis, w->W, L, ld, k, w->q, w->H + (int64_t)k * ldh,
@@ -787,8 +787,8 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
         }
         if ((st = stop_checkpoint(w, o, s, dp_target, step, checked)) != CT_OK) return st;
     }
-    if ((st = run_small_solves(w, o, s, dp_target)) != CT_OK) return st;        // lines 12-13
-    // line 13 at k = K: x = x0 + B W y = B (u0 + W y)
+    if ((st = run_small_solves(w, o, s, dp_target)) != CT_OK) return st;   // Eq. (hybrid_proj)
+    // the hybrid iterate at the last (or stopping) step: x = x0 + B W y = B (u0 + W y)
     {
         CT_PHASE(CT_PH_OTHER, u0_dev ? 2 : 1, s);
         if (u0_dev && !u0_padded) CT_CUDA(launch_pad_sino(g, u0_dev, w->sino, s));
@@ -832,7 +832,7 @@ static ct_status enqueue_ba(ct_geom *g, const float *b_dev, const float *x0_dev,
     CT_CUDA(cudaMemsetAsync(w->stop, 0, 2 * sizeof(int), s));
     CT_CUDA(cudaMemsetAsync(w->counter, 0, 4 * sizeof(unsigned), s));
     CT_CUDA(cudaMemsetAsync(w->path, 0, sizeof(int) * K, s));
-    // Alg. 2 lines 1-3: r0 = B (b - A x0), w1 = r0 / ||r0||
+    // Algorithm 2 set-up: r0 = B (b - A x0), w1 = r0 / ||r0||
     {
         CT_PHASE(CT_PH_OTHER, x0_dev ? 7 : 4, s);
         CT_CUDA(launch_pad_sino(g, b_dev, w->sino, s));
@@ -862,7 +862,7 @@ static ct_status enqueue_ba(ct_geom *g, const float *b_dev, const float *x0_dev,
         const float *wk = w->cur ? w->cur : static_cast<float *>(w->W) + (int64_t)k * ld;
         {
             CT_PHASE(CT_PH_LAYOUT, 1, s);
-            CT_CUDA(launch_image_pairs(g, wk, w->stop, s));           // line 5: A w_k
+            CT_CUDA(launch_image_pairs(g, wk, w->stop, s));           // q = B A w_k: A w_k
         }
         {
             CT_PHASE(CT_PH_FORWARD, fwd_launches(g), s);
@@ -880,8 +880,8 @@ static ct_status enqueue_ba(ct_geom *g, const float *b_dev, const float *x0_dev,
         }
         if ((st = stop_checkpoint(w, o, s, dp_target, step, checked)) != CT_OK) return st;
     }
-    if ((st = run_small_solves(w, o, s, dp_target)) != CT_OK) return st;        // lines 12-13
-    // line 13: x = x0 + W y
+    if ((st = run_small_solves(w, o, s, dp_target)) != CT_OK) return st;   // Eq. (hybrid_proj)
+    // the hybrid iterate: x = x0 + W y
     {
         CT_PHASE(CT_PH_OTHER, 1, s);
         if (x0_dev) {

@@ -1,4 +1,5 @@
-// The hybrid step of Algorithms 1 and 2 (lines 12-13) on the device, in FP64:
+// The hybrid step of Algorithms 1 and 2 (the lambda choice and Eq. (hybrid_proj)) on the
+// device, in FP64:
 // choose lambda for the (k+1) x k Hessenberg matrix H_k and solve Eq. (hybrid_proj)
 //     y = argmin || [H_k; lambda I] y - beta [e1; 0] ||.
 //

@@ -141,3 +141,102 @@ def _ray_weights(g):
                  np.array([-g.sdd * c - u * s, -g.sdd * s + u * c]))
             w.append(g.h * np.linalg.norm(D) / np.max(np.abs(D)))
     return np.array(w)
+
+
+# ----------------------------------------------------------------------------- initial guess,
+# restarting and the NCP: the function's own source with one plausible mistake substituted
+import inspect
+import textwrap
+
+from tests import test_oracle_ncp as NCP_PINS
+from tests import test_oracle_solver as SOLVER_PINS
+
+
+def _mutant(fn, old, new):
+    src = textwrap.dedent(inspect.getsource(fn))
+    assert src.count(old) == 1, (fn.__name__, old)
+    ns = {}
+    exec(compile(src.replace(old, new), f"<mutant of {fn.__name__}>", "exec"), fn.__globals__, ns)
+    return ns[fn.__name__]
+
+
+X0_PINS = [lambda: SOLVER_PINS.test_initial_guess_iterate_matches_shifted_krylov_minimiser("ab"),
+           lambda: SOLVER_PINS.test_initial_guess_iterate_matches_shifted_krylov_minimiser("ba"),
+           SOLVER_PINS.test_matched_ab_from_initial_guess_is_lsqr_of_shifted_data,
+           SOLVER_PINS.test_restart_at_full_dimension_follows_the_closed_form]
+
+
+def _some_pin_fails(pins):
+    failed = 0
+    for pin in pins:
+        try:
+            pin()
+        except AssertionError:
+            failed += 1
+    return failed
+
+
+def test_x0_and_restart_pins_pass_on_the_oracle_as_it_is():
+    assert _some_pin_fails(X0_PINS) == 0
+    SOLVER_PINS.test_restarted_cycles_are_shifted_krylov_minimisers("ab")
+
+
+@pytest.mark.parametrize("old,new", [
+    ("return x0v + (B(z)", "return 0 * x0v + (B(z)"),     # x0 dropped from the iterate
+])
+def test_dropped_initial_guess_in_the_iterate_is_caught(monkeypatch, old, new):
+    monkeypatch.setattr(S, "_form_x", _mutant(S._form_x, old, new))
+    assert _some_pin_fails(X0_PINS) >= 3
+
+
+@pytest.mark.parametrize("old,new", [
+    ("r0 = b - A(x0v)\n", "r0 = b + A(x0v)\n"),            # sign of the AB shift
+    ("r0 = b - A(x0v)\n", "r0 = b - 0 * A(x0v)\n"),        # AB residual ignores x0
+    ("r0 = B(b - A(x0v))", "r0 = B(b)"),                   # BA residual ignores x0
+])
+def test_wrong_initial_residual_is_caught(monkeypatch, old, new):
+    monkeypatch.setattr(S, "hybrid_gmres", _mutant(S.hybrid_gmres, old, new))
+    assert _some_pin_fails(X0_PINS) >= 1
+
+
+@pytest.mark.parametrize("old,new", [
+    ("cycle, x0=x,", "cycle, x0=x0,"),                       # every cycle starts from x0
+    ("x = res[\"x\"]", "x = res[\"x\"] - (x if x is not None else 0)"),  # keeps only the update
+])
+def test_wrong_restart_is_caught(monkeypatch, old, new):
+    monkeypatch.setattr(S, "restarted_hybrid_gmres", _mutant(S.restarted_hybrid_gmres, old, new))
+    with pytest.raises(AssertionError):
+        SOLVER_PINS.test_restart_at_full_dimension_follows_the_closed_form()
+    with pytest.raises(AssertionError):
+        SOLVER_PINS.test_restarted_cycles_are_shifted_krylov_minimisers("ba")
+
+
+NCP_CLOSED_FORMS = [lambda: NCP_PINS.test_ncp_of_a_sinusoid_is_a_step(17),
+                    lambda: NCP_PINS.test_ncp_of_a_sinusoid_is_a_step(768),
+                    NCP_PINS.test_ncp_ignores_mean_scale_and_circular_shift,
+                    NCP_PINS.test_ncp_averages_rows_and_skips_rows_without_power]
+
+
+def test_ncp_pins_pass_on_the_oracle_as_it_is():
+    assert _some_pin_fails(NCP_CLOSED_FORMS) == 0
+
+
+@pytest.mark.parametrize("fn,old,new", [
+    ("periodogram", "[:, 1:q + 1]", "[:, 0:q]"),            # zero frequency kept
+    ("periodogram", "[:, 1:q + 1]", "[:, 1:]"),             # mirrored half kept (q = n - 1)
+    ("ncp", "c.mean(axis=0)", "c.sum(axis=0)"),             # rows summed, not averaged
+    ("ncp", "/ tot[keep, None]", "/ tot.sum()"),            # one normalisation for all rows
+])
+def test_ncp_mistakes_are_caught(monkeypatch, fn, old, new):
+    monkeypatch.setattr(S, fn, _mutant(getattr(S, fn), old, new))
+    assert _some_pin_fails(NCP_CLOSED_FORMS) >= 1
+
+
+@pytest.mark.parametrize("old,new", [
+    ("dist > ncp_prev[1]", "dist < ncp_prev[1]"),           # stops while the distance falls
+    ("k_done, y = ncp_prev[0], ncp_prev[2]", "pass"),       # returns the step that grew
+])
+def test_ncp_stop_mistakes_are_caught(monkeypatch, old, new):
+    monkeypatch.setattr(S, "hybrid_gmres", _mutant(S.hybrid_gmres, old, new))
+    with pytest.raises(AssertionError):
+        NCP_PINS.test_ncp_stop_returns_the_last_checked_iterate_before_the_distance_grows("ab", 1)

@@ -283,3 +283,102 @@ def test_rns_stopping_rule():
     rel_change = [abs(tr[j - 1] - tr[j]) / tr[j - 1] for j in range(1, len(tr))]
     first = next(j + 2 for j, v in enumerate(rel_change) if v < 1e-3 * (1 + 1e-6))
     assert k == first
+
+
+# ----------------------------------------------------------------------------- initial guess
+def _shifted_krylov_minimiser(method, A, B, b, x0, k, lam):
+    """x0 + (B) Q z with Q an orthonormal basis of the Krylov space of Sec. 2.1 started at the
+    shifted residual (AB: K_k(AB, b - A x0); BA: K_k(BA, B(b - A x0))) and z the minimiser of
+    ||M Q z - r0||^2 + lam^2 ||z||^2 by dense least squares."""
+    if method == "ab":
+        M, r0 = (lambda w: A(B(w))), b - A(x0)
+    else:
+        M, r0 = (lambda w: B(A(w))), B(b - A(x0))
+    Q = _krylov_basis(M, r0, k)
+    MQ = np.stack([M(Q[:, i]) for i in range(k)], axis=1)
+    z = np.linalg.lstsq(np.vstack([MQ, lam * np.eye(k)]), np.concatenate([r0, np.zeros(k)]),
+                        rcond=None)[0]
+    return x0 + (B(Q @ z) if method == "ab" else Q @ z), float(np.linalg.norm(MQ @ z - r0))
+
+
+@pytest.mark.parametrize("method", ["ab", "ba"])
+def test_initial_guess_iterate_matches_shifted_krylov_minimiser(method):
+    """Algorithms 1/2 from x0 != 0 (AB: x0 = B u0): the iterate is x0 plus the hybrid
+    minimiser over the Krylov space of the initial residual, and the projected residual is
+    that minimiser's residual."""
+    g, x, b, e = _problem("fan", N=12, views=16, seed=2)
+    A, B = P.operators(g)
+    rng = np.random.Generator(np.random.PCG64(17))
+    x0 = B(rng.standard_normal(g.m)) if method == "ab" else 0.5 * x + rng.random(g.n)
+    k, lam = 5, 0.7
+    res = S.hybrid_gmres(method, A, B, b, k, rule="fixed", lam_fixed=lam, x0=x0)
+    xb, rb = _shifted_krylov_minimiser(method, A, B, b, x0, k, lam)
+    np.testing.assert_allclose(res["x"], xb, rtol=1e-7, atol=1e-9 * np.abs(xb).max())
+    np.testing.assert_allclose(res["resid"][-1], rb, rtol=1e-8)
+    # the initial guess really moved the answer (the pin is not the x0 = 0 case again)
+    x_zero = S.hybrid_gmres(method, A, B, b, k, rule="fixed", lam_fixed=lam)["x"]
+    assert np.linalg.norm(res["x"] - x_zero) > 1e-3 * np.linalg.norm(x_zero)
+
+
+def test_matched_ab_from_initial_guess_is_lsqr_of_shifted_data():
+    """B = A^T, lambda = 0: AB-GMRES from x0 = A^T u0 equals x0 + LSQR(b - A x0) (Sec. 3,
+    relation to existing methods, applied to the shifted system A d = b - A x0)."""
+    g, x, b, e = _problem("parallel", N=12, views=16, seed=5)
+    A, At = P.operators(g, matched=True)
+    rng = np.random.Generator(np.random.PCG64(23))
+    x0 = At(rng.standard_normal(g.m))
+    for k in (3, 7):
+        ab = S.hybrid_gmres("ab", A, At, b, k, rule="none", x0=x0)["x"]
+        lq = x0 + S.lsqr_iterate(A, At, b - A(x0), k)
+        assert np.linalg.norm(ab - lq) <= 1e-8 * np.linalg.norm(lq)
+
+
+# ----------------------------------------------------------------------------- restarting
+def _dense_pair(m, n, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    A = rng.standard_normal((m, n))
+    B = A.T + 0.3 * rng.standard_normal((n, m))
+    return A, B, rng.standard_normal(m), rng.standard_normal(n)
+
+
+def test_restart_at_full_dimension_follows_the_closed_form():
+    """Sec. 3.3 with p = n (BA) or p = m (AB): each cycle from x_{c-1} lands on the closed form
+    of Sec. 3 (optimality conditions, lambda^2 reading) for the shifted system, so
+    x_c = x_{c-1} + (M^T M + lam^2 I)^{-1} M^T r(x_{c-1}) (BA: M = BA, r = B(b - A x);
+    AB: x_c = x_{c-1} + B (N^T N + lam^2 I)^{-1} N^T (b - A x_{c-1}), N = AB).
+    The regularisation acts on the update, not on the iterate, so the cycles keep moving."""
+    lam = 0.4
+    A, B, b, x0 = _dense_pair(14, 9, 3)
+    Af, Bf = (lambda v: A @ v), (lambda v: B @ v)
+    M = B @ A
+    x, hist = S.restarted_hybrid_gmres("ba", Af, Bf, b, 9, 3, x0=x0, rule="fixed", lam_fixed=lam)
+    xc = x0.copy()
+    for c in range(3):
+        xc = xc + np.linalg.solve(M.T @ M + lam ** 2 * np.eye(9), M.T @ (B @ (b - A @ xc)))
+        np.testing.assert_allclose(hist[c]["x"], xc, rtol=1e-9, atol=1e-11)
+    A, B, b, _ = _dense_pair(8, 13, 4)
+    Af, Bf = (lambda v: A @ v), (lambda v: B @ v)
+    N = A @ B
+    x, hist = S.restarted_hybrid_gmres("ab", Af, Bf, b, 8, 2, rule="fixed", lam_fixed=lam)
+    xc = np.zeros(13)
+    for c in range(2):
+        xc = xc + B @ np.linalg.solve(N.T @ N + lam ** 2 * np.eye(8), N.T @ (b - A @ xc))
+        np.testing.assert_allclose(hist[c]["x"], xc, rtol=1e-9, atol=1e-11)
+    assert np.linalg.norm(hist[1]["x"] - hist[0]["x"]) > 1e-3 * np.linalg.norm(hist[0]["x"])
+
+
+@pytest.mark.parametrize("method", ["ab", "ba"])
+def test_restarted_cycles_are_shifted_krylov_minimisers(method):
+    """Sec. 3.3 on a CT problem: cycle 1 is the minimiser over K_p from x = 0, cycle 2 the
+    minimiser over K_p of the residual of cycle 1's iterate, added to it; one cycle of the
+    restarted solve is the plain solve."""
+    g, x, b, e = _problem("fan", N=12, views=16, seed=6)
+    A, B = P.operators(g)
+    p, lam = 4, 0.5
+    xr, hist = S.restarted_hybrid_gmres(method, A, B, b, p, 2, rule="fixed", lam_fixed=lam)
+    x1, _ = _shifted_krylov_minimiser(method, A, B, b, np.zeros(g.n), p, lam)
+    x2, _ = _shifted_krylov_minimiser(method, A, B, b, x1, p, lam)
+    np.testing.assert_allclose(hist[0]["x"], x1, rtol=1e-7, atol=1e-9 * np.abs(x1).max())
+    np.testing.assert_allclose(xr, x2, rtol=1e-7, atol=1e-9 * np.abs(x2).max())
+    plain = S.hybrid_gmres(method, A, B, b, p, rule="fixed", lam_fixed=lam)["x"]
+    np.testing.assert_allclose(hist[0]["x"], plain, rtol=1e-12, atol=1e-14)
