@@ -129,13 +129,20 @@ typedef enum {
 
 typedef enum { CT_BASIS_F32 = 0, CT_BASIS_BF16 = 1, CT_BASIS_F16 = 2 } ct_basis_dtype;
 
-/* Stopping rules (Sec. 3.2) on rho_k = ||H_k y_k - beta e1|| (= ||b - A x_k|| for AB,
- * ||B (b - A x_k)|| for BA): the solve returns x_k at the first step k that meets the rule (or
- * x_K).  DP: rho_k <= tau * noise_norm (the paper prints the inequality reversed);
+/* Stopping rules (Sec. 3.2).  DP and RNS use rho_k = ||H_k y_k - beta e1|| (= ||b - A x_k||
+ * for AB, ||B (b - A x_k)|| for BA): the solve returns x_k at the first step k that meets the
+ * rule (or x_K).  DP: rho_k <= tau * noise_norm (the paper prints the inequality reversed);
  * RNS: |rho_{k-1} - rho_k| < stop_tol * rho_{k-1}, k >= 2.  The rule is checked on the device
  * every stop_every steps, so up to stop_every - 1 steps beyond the stopping step are computed
- * (and discarded); once it fires, the remaining launches of the solve return at once. */
-typedef enum { CT_STOP_NONE = 0, CT_STOP_DP = 1, CT_STOP_RNS = 2 } ct_stop_rule;
+ * (and discarded); once it fires, the remaining launches of the solve return at once.
+ * NCP (normalized cumulative periodogram): at the steps stop_every, 2 stop_every, ... and K the
+ * data residual r_k = b - A x_k is formed (one extra B and A per check for AB, one extra A for
+ * BA), each detector row's periodogram |DFT|^2 at the frequencies 1..q = n_det_u / 2 is
+ * accumulated and normalised, the rows' NCPs are averaged and their distance
+ * ||c - (1..q)/q||_2 from the white-noise line is recorded; the solve stops at the first
+ * checked step whose distance is larger than at the previous check and returns the iterate of
+ * that previous check (iters_done = its step).  Needs 2 <= n_det_u <= 8192. */
+typedef enum { CT_STOP_NONE = 0, CT_STOP_DP = 1, CT_STOP_RNS = 2, CT_STOP_NCP = 3 } ct_stop_rule;
 
 typedef struct {
     int max_iters;           /* K >= 1                                                     */
@@ -154,6 +161,8 @@ typedef struct {
     ct_stop_rule stop_rule;  /* CT_STOP_NONE (default): exactly max_iters steps             */
     double stop_tol;         /* CT_STOP_RNS tolerance (> 0)                                 */
     int stop_every;          /* steps between device-side checks of the rule (>= 1)         */
+    double *ncp_hist;        /* host, max_iters entries, may be NULL: the NCP distance of every
+                                checked step (CT_STOP_NCP), NaN at the other steps          */
 } ct_hybrid_opts;
 
 typedef struct {
@@ -392,6 +401,30 @@ ct_status ct_profile_enable(int on);
 ct_status ct_profile_collect(ct_phase_time *out);
 /* Number of kernels this library has launched since it was loaded (all phases). */
 int64_t ct_launch_count(void);
+
+/* Throughput probes for the rooflines of the gather-bound projectors: one wave of resident
+ * blocks on every SM of the current device doing only the elementary work of a projector
+ * sample, so that its duration (timed by the caller with events on `stream`) gives a measured
+ * ceiling.  CT_PROBE_GATHER8: one 8-byte load from an L1-resident table (each warp reads 32
+ * consecutive pairs, the best case of the projectors' near-contiguous tap-pair gathers) plus
+ * one fused multiply-add that consumes it.  CT_PROBE_MUFU: one reciprocal and one square root
+ * (the special-function pair of a fan-beam pixel-driven sample) plus one addition.  Every
+ * thread does `reps` operations (rounded up to a multiple of 8) in 8 independent chains and
+ * writes one float to out_dev (out_floats >= resident blocks x 256; 152 SMs x 8 x 256 always
+ * suffices).  *ops (host) receives the operation count of the launch.  Asynchronous. */
+typedef enum { CT_PROBE_GATHER8 = 0, CT_PROBE_MUFU = 1 } ct_probe_kind;
+ct_status ct_probe(int kind, int64_t reps, float *out_dev, int64_t out_floats, int64_t *ops,
+                   ct_stream_t stream);
+
+/* Test hook of failure detection (off by default; not for production use).  enable != 0 arms
+ * it on the current device: the next Gram-Schmidt tile pass launched there leaves the
+ * asynchronous copies of its block 0's first tile unissued (nothing is in flight for them), so
+ * that block's bounded waits run out after wait_cycles GPU clocks (2^16 .. 2^31); the pass
+ * records CT_ETIMEOUT in the solver's state and returns, the rest of that solve is skipped and
+ * the solver returns CT_ETIMEOUT (its iterate is not valid); later solves run normally.  The
+ * hook disarms itself after that one use; enable = 0 disarms it and restores the default wait
+ * limit (about 2^31 clocks).  Synchronous host call. */
+ct_status ct_test_drop_tile_copy(int enable, int64_t wait_cycles);
 
 /* Status name and the calling thread's last error message. */
 const char *ct_status_string(ct_status s);

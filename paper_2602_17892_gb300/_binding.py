@@ -22,7 +22,7 @@ KINDS = {"parallel2d": 0, "fanflat2d": 1, "cone3d": 2}
 RULES = {"none": 0, "fixed": 1, "gcv": 2, "dp": 3, "learned": 4, "lcurve": 5}
 CT_MLP_NIN, CT_MLP_NPARAMS = 80, 9569
 BASIS = {"f32": 0, "bf16": 1, "f16": 2}
-STOPS = {"none": 0, "dp": 1, "rns": 2}
+STOPS = {"none": 0, "dp": 1, "rns": 2, "ncp": 3}
 
 # the entry points of include/ctabba.h
 EXPORTS = ("ct_geom_create", "ct_geom_destroy", "ct_geom_dims", "ct_geom_work", "ct_forward_A", "ct_back_B",
@@ -31,7 +31,8 @@ EXPORTS = ("ct_geom_create", "ct_geom_destroy", "ct_geom_dims", "ct_geom_work", 
            "ct_profile_collect", "ct_launch_count", "ct_geom_autotune", "ct_batch_create",
            "ct_batch_solve", "ct_batch_launches", "ct_batch_destroy", "abba_solve", "ct_mlp_forward",
            "ct_mlp_grad", "ct_mlp_adam", "ct_mlp_train", "ct_lambda_samples",
-           "ab_gmres_hybrid_restarted", "ba_gmres_hybrid_restarted")
+           "ab_gmres_hybrid_restarted", "ba_gmres_hybrid_restarted", "ct_test_drop_tile_copy",
+           "ct_probe")
 PHASES = ("forward_A", "back_B", "layout", "arnoldi", "small_solve", "other")
 
 
@@ -57,7 +58,7 @@ class HybridOpts(ctypes.Structure):
                 ("resid_hist", ctypes.POINTER(ctypes.c_double)),
                 ("lambda_net_dev", ctypes.c_void_p), ("features_dev", ctypes.c_void_p),
                 ("stop_rule", ctypes.c_int), ("stop_tol", ctypes.c_double),
-                ("stop_every", ctypes.c_int)]
+                ("stop_every", ctypes.c_int), ("ncp_hist", ctypes.POINTER(ctypes.c_double))]
 
 
 class PhaseTime(ctypes.Structure):
@@ -118,6 +119,8 @@ def load(path: str = LIB_PATH):
     lib.ct_back_AT.argtypes = [vp, vp, vp, vp]
     lib.ct_geom_set_backprojector.argtypes = [vp, ctypes.c_int]
     lib.ct_geom_get_launch_shapes.argtypes = [vp, ctypes.POINTER(LaunchShapes)]
+    lib.ct_test_drop_tile_copy.argtypes = [ctypes.c_int, i64]
+    lib.ct_probe.argtypes = [ctypes.c_int, i64, vp, i64, ctypes.POINTER(i64), vp]
     lib.ct_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(HybridOpts), ctypes.c_int, ctypes.POINTER(vp)]
     lib.ct_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
@@ -231,20 +234,23 @@ def _opts(max_iters, rule, lambda_fixed, noise_norm, tau, reorth, basis, history
     o.stop_every = int(stop_every)
     o.lambda_net_dev = _ptr(lambda_net).value if lambda_net is not None else None
     o.features_dev = _ptr(features).value if features is not None else None
-    lam = res = None
+    lam = res = ncp = None
     if history:
         lam = np.full(int(max_iters), np.nan)
         res = np.full(int(max_iters), np.nan)
         o.lambda_hist = lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         o.resid_hist = res.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-    return o, lam, res
+        if o.stop_rule == STOPS["ncp"]:
+            ncp = np.full(int(max_iters), np.nan)
+            o.ncp_hist = ncp.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return o, lam, res, ncp
 
 
 def _solve(fn, g, b, x, x0, max_iters, rule, lambda_fixed, noise_norm, tau, reorth, basis,
            history, stream, lambda_net=None, features=None, stop=None, stop_tol=1e-3,
            stop_every=5):
-    o, lam, res = _opts(max_iters, rule, lambda_fixed, noise_norm, tau, reorth, basis, history,
-                        lambda_net, features, stop, stop_tol, stop_every)
+    o, lam, res, ncp = _opts(max_iters, rule, lambda_fixed, noise_norm, tau, reorth, basis,
+                             history, lambda_net, features, stop, stop_tol, stop_every)
     info = HybridInfo()
     st = fn(g.handle, _ptr(b), _ptr(x0), _ptr(x), ctypes.byref(o), ctypes.byref(info),
             _stream(stream))
@@ -252,6 +258,8 @@ def _solve(fn, g, b, x, x0, max_iters, rule, lambda_fixed, noise_norm, tau, reor
     out = _info_dict(info)
     if history:
         out["lambdas"], out["resid"] = lam, res
+        if ncp is not None:
+            out["ncp"] = ncp
     return out
 
 
@@ -275,8 +283,8 @@ def ba_gmres_hybrid(g, b, x, x0=None, max_iters=30, rule="gcv", lambda_fixed=0.0
 
 def _solve_restarted(fn, g, b, x, cycles, max_iters, rule, lambda_fixed, noise_norm, tau,
                      reorth, basis, history, stream, lambda_net):
-    o, _, _ = _opts(max_iters, rule, lambda_fixed, noise_norm, tau, reorth, basis, False,
-                    lambda_net)
+    o, _, _, _ = _opts(max_iters, rule, lambda_fixed, noise_norm, tau, reorth, basis, False,
+                       lambda_net)
     lam = res = None
     if history:
         lam = np.full(int(cycles) * int(max_iters), np.nan)
@@ -392,7 +400,8 @@ class Batch:
         lib = load()
         self.geoms = list(geoms)
         n = len(self.geoms)
-        o, _, _ = _opts(max_iters, rule, lambda_fixed, 0.0, tau, reorth, basis, False, lambda_net)
+        o, _, _, _ = _opts(max_iters, rule, lambda_fixed, 0.0, tau, reorth, basis, False,
+                           lambda_net)
         self._o = o
         self._net = lambda_net
         gh = (ctypes.c_void_p * n)(*[g.handle.value for g in self.geoms])
@@ -435,7 +444,7 @@ def abba_solve(geoms, b_list, x_list, methods=None, max_iters=30, rule="gcv", la
     """One-shot batched solve (creates, solves and destroys a ct_batch)."""
     lib = load()
     n = len(geoms)
-    o, _, _ = _opts(max_iters, rule, lambda_fixed, 0.0, tau, 1, basis, False, lambda_net)
+    o, _, _, _ = _opts(max_iters, rule, lambda_fixed, 0.0, tau, 1, basis, False, lambda_net)
     gh = (ctypes.c_void_p * n)(*[g.handle.value for g in geoms])
     mth = None
     if methods is not None:
@@ -480,9 +489,26 @@ def ct_mlp_train(params, m, v, X, Y, batch, epochs, lr, t=0, loss_hist=None, bf1
 
 def ct_lambda_samples(g, b, x_true, x, feats, labels, max_iters=30, rule="gcv", stream=None):
     """Features (K x 80) and labels (K) of the learned lambda rule from one AB solve."""
-    o, _, _ = _opts(max_iters, rule, 0.0, 0.0, 1.01, 1, "f32", False)
+    o, _, _, _ = _opts(max_iters, rule, 0.0, 0.0, 1.01, 1, "f32", False)
     info = HybridInfo()
     _check(load().ct_lambda_samples(g.handle, _ptr(b), _ptr(x_true), ctypes.byref(o), _ptr(x),
                                     _ptr(feats), _ptr(labels), ctypes.byref(info),
                                     _stream(stream)))
     return _info_dict(info)
+
+
+def ct_test_drop_tile_copy(enable: bool, wait_cycles: int = 1 << 20):
+    """Test hook of the bounded device waits (see include/ctabba.h): armed, the next
+    Gram-Schmidt tile pass leaves one tile's copies unissued so its wait runs out."""
+    _check(load().ct_test_drop_tile_copy(1 if enable else 0, int(wait_cycles)))
+
+
+PROBES = {"gather8": 0, "mufu": 1}
+
+
+def ct_probe(kind, reps, out, stream=None) -> int:
+    """Launch one throughput probe ('gather8' or 'mufu'); returns its operation count."""
+    ops = ctypes.c_int64(0)
+    _check(load().ct_probe(PROBES[kind] if isinstance(kind, str) else int(kind), int(reps),
+                           _ptr(out), int(out.numel()), ctypes.byref(ops), _stream(stream)))
+    return int(ops.value)

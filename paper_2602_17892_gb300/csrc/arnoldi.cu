@@ -359,6 +359,14 @@ constexpr int kTilePair = 110 * 1024;           // at most this much for two CTA
 constexpr long long kWaitCycles = 1ll << 31;    // bounded mbarrier waits (about a second)
 enum { T_DOTS = 0, T_UPD_DOTS = 1, T_UPD_SCALE = 2 };
 
+// Test hook of the bounded waits (off by default, armed only by ct_test_drop_tile_copy): when
+// g_drop_tile_copy is set, the next tile pass whose block 0 takes it (atomic exchange) issues
+// neither the copies of its first tile nor their expected byte count, so nothing is in flight
+// for that stage and its waits run out after g_wait_cycles; the pass then records CT_ETIMEOUT
+// in the solver's stop word and returns.
+__device__ int g_drop_tile_copy = 0;
+__device__ long long g_wait_cycles = kWaitCycles;
+
 struct TileArgs {
     const void *W; int64_t ld; int nvec;         // rows W[0..nvec-1], storage type T
     const float *q; float *qout;                 // q (ld floats); T2 writes q' to qout (= q)
@@ -405,8 +413,8 @@ __device__ __forceinline__ void tensor_g2s(void *dst, const CUtensorMap *map, in
                  "r"(smem_u32(bar)) : "memory");
 }
 
-// waits for phase `parity` of `bar` to complete; false after about kWaitCycles
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
+// waits for phase `parity` of `bar` to complete; false after about `limit` cycles
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long long limit)
 {
     const uint32_t a = smem_u32(bar);
     const long long t0 = clock64();
@@ -416,8 +424,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
                      "selp.u32 %0, 1, 0, p;\n\t}"
                      : "=r"(done) : "r"(a), "r"(parity) : "memory");
         if (done) return true;
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     }
+}
+
+// arms (enable != 0) or disarms the test hook above; while armed the waits give up after
+// wait_cycles, disarmed they use the default limit
+cudaError_t arnoldi_test_drop_tile_copy(int enable, long long wait_cycles)
+{
+    const int arm = enable ? 1 : 0;
+    const long long lim = enable ? wait_cycles : kWaitCycles;
+    cudaError_t e = cudaMemcpyToSymbol(g_wait_cycles, &lim, sizeof(lim));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_drop_tile_copy, &arm, sizeof(arm));
+    return e;
 }
 
 template <typename T>
@@ -524,16 +543,18 @@ __global__ void __launch_bounds__(kThreads, 2) cgs_tile_kernel(const __grid_cons
         tensor_g2s(dst, &wmap, e0, &bars[st]);
         bulk_g2s(dst + (size_t)nvec * seg, a.q + e0, kTileElems * 4, &bars[st]);
     };
+    const long long wlim = g_wait_cycles;
     if (tid == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        for (int i = 0; i < S && i < nt; ++i) issue(i);
+        const bool drop = blockIdx.x == 0 && nt > 0 && atomicExch(&g_drop_tile_copy, 0) != 0;
+        for (int i = drop ? 1 : 0; i < S && i < nt; ++i) issue(i);
     }
     bool ok = true;
     float nn = 0.f;                      // lane partial of ||q||^2 (T1) or ||q'||^2 (T2), warp 0
     int i = 0;
     for (; i < nt; ++i) {
         const int st = i % S;
-        if (!mbar_wait(&bars[st], (unsigned)((i / S) & 1))) { ok = false; break; }
+        if (!mbar_wait(&bars[st], (unsigned)((i / S) & 1), wlim)) { ok = false; break; }
         const unsigned char *tileb = tsm + (size_t)st * stage_bytes;
         const float4 qv = reinterpret_cast<const float4 *>(tileb + (size_t)nvec * seg)[lane];
         float4 v = qv;                   // the vector the dots are taken with (q or q')
@@ -613,7 +634,8 @@ __global__ void __launch_bounds__(kThreads, 2) cgs_tile_kernel(const __grid_cons
         // a copy never completed: record it, then wait (bounded) for the copies still in flight
         if (lane == 0) atomicCAS(a.stop, 0, a.step > 0 ? a.step : -1);
         if (tid == 0) a.stop[1] = CT_ETIMEOUT;
-        for (int j = i; j < nt && j < i + S; ++j) mbar_wait(&bars[j % S], (unsigned)((j / S) & 1));
+        for (int j = i; j < nt && j < i + S; ++j)
+            mbar_wait(&bars[j % S], (unsigned)((j / S) & 1), wlim);
     }
     if (MODE == T_UPD_SCALE) return;
     if (warp == 0) {

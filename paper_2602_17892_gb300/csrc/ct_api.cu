@@ -134,6 +134,11 @@ struct Workspace {
     double *partial = nullptr;
     unsigned *counter = nullptr;
     int *stop = nullptr;
+    // NCP stopping rule (allocated on first use): DFT twiddles of one detector row, per-view
+    // partial NCP sums, the distance of every checked step
+    float2 *ncp_tw = nullptr;
+    float *ncp_part = nullptr;
+    double *ncp = nullptr;
 };
 
 static void ws_free(Workspace *w)
@@ -143,6 +148,7 @@ static void ws_free(Workspace *w)
     cudaFree(w->sino2);
     cudaFree(w->H); cudaFree(w->Y); cudaFree(w->lam); cudaFree(w->res); cudaFree(w->aux);
     cudaFree(w->partial); cudaFree(w->counter); cudaFree(w->stop); cudaFree(w->path);
+    cudaFree(w->ncp_tw); cudaFree(w->ncp_part); cudaFree(w->ncp);
     delete w;
 }
 
@@ -200,6 +206,34 @@ static ct_status ws_get(ct_geom *g, int method, int K, int basis, Workspace **ou
     }
     ex->ws[method] = w;
     *out = w;
+    return CT_OK;
+}
+
+// The NCP rule's tables (host set-up, before any capture): twiddles cos, sin(2 pi t / n) of
+// one detector row in FP64 rounded to FP32, the per-view partial sums, the distances.
+static ct_status ncp_ready(ct_geom *g, Workspace *w)
+{
+    const int n = g->dg.ndu, q = n / 2;
+    if (n < 2 || n > kNcpMaxBins)
+        return einval("solver: the NCP rule needs 2 <= n_det_u <= " + std::to_string(kNcpMaxBins));
+    if (w->ncp_tw) return CT_OK;
+    std::vector<float2> tw((size_t)n);
+    for (int t = 0; t < n; ++t) {
+        const double a = 2.0 * M_PI * (double)t / (double)n;
+        tw[(size_t)t] = make_float2((float)cos(a), (float)sin(a));
+    }
+    cudaError_t e = dalloc(&w->ncp_tw, (size_t)n);
+    if (e == cudaSuccess) e = dalloc(&w->ncp_part, (size_t)g->dg.n_views * (q + 1));
+    if (e == cudaSuccess) e = dalloc(&w->ncp, (size_t)w->K);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(w->ncp_tw, tw.data(), sizeof(float2) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = ncp_prepare(n);
+    if (e != cudaSuccess) {
+        cudaFree(w->ncp_tw); cudaFree(w->ncp_part); cudaFree(w->ncp);
+        w->ncp_tw = nullptr; w->ncp_part = nullptr; w->ncp = nullptr;
+        set_error(std::string("NCP tables: ") + cudaGetErrorString(e));
+        return CT_ENOMEM;
+    }
     return CT_OK;
 }
 
@@ -610,7 +644,7 @@ static ct_status check_opts(const ct_hybrid_opts *o)
     if (o->rule == CT_LAMBDA_DP && (!(o->noise_norm >= 0) || !(o->tau > 0)))
         return einval("solver: DP needs noise_norm >= 0 and tau > 0");
     if (o->basis < CT_BASIS_F32 || o->basis > CT_BASIS_F16) return einval("solver: bad basis type");
-    if (o->stop_rule < CT_STOP_NONE || o->stop_rule > CT_STOP_RNS) return einval("solver: bad stop rule");
+    if (o->stop_rule < CT_STOP_NONE || o->stop_rule > CT_STOP_NCP) return einval("solver: bad stop rule");
     if (o->stop_rule != CT_STOP_NONE && o->stop_every < 1) return einval("solver: stop_every must be >= 1");
     if (o->stop_rule == CT_STOP_DP && (!(o->noise_norm >= 0) || !(o->tau > 0)))
         return einval("solver: the DP stop needs noise_norm >= 0 and tau > 0");
@@ -643,6 +677,12 @@ static ct_status read_info(Workspace *w, const ct_hybrid_opts *o, ct_hybrid_info
     for (int i = kf; i < K; ++i) lam[i] = res[i] = NAN;
     if (o->lambda_hist) memcpy(o->lambda_hist, lam.data(), sizeof(double) * K);
     if (o->resid_hist) memcpy(o->resid_hist, res.data(), sizeof(double) * K);
+    if (o->ncp_hist) {
+        if (o->stop_rule == CT_STOP_NCP && w->ncp)
+            CT_CUDA(cudaMemcpy(o->ncp_hist, w->ncp, sizeof(double) * K, cudaMemcpyDeviceToHost));
+        else
+            for (int i = 0; i < K; ++i) o->ncp_hist[i] = NAN;
+    }
     ct_status st = (stop[0] == 0) ? CT_OK : (ct_status)stop[1];
     if (info) {
         info->iters_done = kf;
@@ -659,6 +699,11 @@ static ct_status read_info(Workspace *w, const ct_hybrid_opts *o, ct_hybrid_info
             }
     }
     if (st == CT_ENONFINITE) { set_error("solver: non-finite value met"); return st; }
+    if (st == CT_ETIMEOUT) {
+        set_error("solver: a bounded device wait of the Gram-Schmidt pass expired (the returned "
+                  "iterate is not valid)");
+        return st;
+    }
     return CT_OK;
 }
 
@@ -686,18 +731,85 @@ static SmallSolveParams small_params(Workspace *w, const ct_hybrid_opts *o, doub
 // With a stopping rule the hybrid steps run inside the loop, every stop_every steps, for the
 // steps since the last check, followed by the device-side check of the rule; after the loop
 // one launch forms y at the stopping (or last) step.
+// The NCP rule (Sec. 3.2) needs the residual vector itself: at a checked step the iterate
+// x_k = x0 + B W_k y_k (AB) or x0 + W_k y_k (BA) is formed, projected, and the periodograms of
+// the rows of b - A x_k are taken (one extra B and A for AB, one extra A for BA per check).
+struct NcpCtx {
+    ct_geom *g = nullptr;
+    int method = 0;
+    const float *b = nullptr;       // the caller's dense data
+    const float *x0 = nullptr;      // AB: padded u0 (or null); BA: x0 image (or null)
+};
+
 static ct_status stop_checkpoint(Workspace *w, const ct_hybrid_opts *o, cudaStream_t s,
-                                 double dp_target, int step, int &checked)
+                                 double dp_target, int step, int &checked, const NcpCtx &nc)
 {
     if (o->stop_rule == CT_STOP_NONE) return CT_OK;
     if (step % o->stop_every != 0 && step != o->max_iters) return CT_OK;
     SmallSolveParams p = small_params(w, o, dp_target);
     p.kfirst = checked;
     p.k = step - checked;
-    CT_PHASE(CT_PH_SMALL, 2, s);
-    CT_CUDA(launch_small_solve_batched(p, s));
-    CT_CUDA(launch_stop_check(w->res, checked, step, o->stop_rule, o->tau * o->noise_norm,
-                              o->stop_tol, w->stop, s));
+    if (o->stop_rule != CT_STOP_NCP) {
+        CT_PHASE(CT_PH_SMALL, 2, s);
+        CT_CUDA(launch_small_solve_batched(p, s));
+        CT_CUDA(launch_stop_check(w->res, checked, step, o->stop_rule, o->tau * o->noise_norm,
+                                  o->stop_tol, w->stop, s));
+        checked = step;
+        return CT_OK;
+    }
+    p.y_at = step;
+    {
+        CT_PHASE(CT_PH_SMALL, 1, s);
+        CT_CUDA(launch_small_solve_batched(p, s));
+    }
+    ct_geom *g = nc.g;
+    const int64_t L = w->L, ld = w->ld;
+    const float *ax;                         // A x_k in the padded sinogram layout
+    if (nc.method == 0) {
+        {
+            CT_PHASE(CT_PH_OTHER, 1, s);     // u = u0 + W_k y_k
+            CT_CUDA(launch_combine_basis(o->basis, w->W, L, ld, w->Y, w->K, w->K, nullptr, step,
+                                         nc.x0, w->q, kMaxBlocks, s));
+        }
+        {
+            CT_PHASE(CT_PH_BACK, 2, s);      // x_k = B u
+            CT_CUDA(launch_back_proj(g, w->q, w->img, w->stop, s));
+        }
+        {
+            CT_PHASE(CT_PH_LAYOUT, 1, s);
+            CT_CUDA(launch_image_pairs(g, w->img, w->stop, s));
+        }
+        {
+            CT_PHASE(CT_PH_FORWARD, fwd_launches(g), s);
+            CT_CUDA(launch_forward_proj(g, w->q, true, w->stop, s));
+        }
+        ax = w->q;
+    } else {
+        {
+            CT_PHASE(CT_PH_OTHER, 1, s);     // x_k = x0 + W_k y_k
+            if (nc.x0) {
+                CT_CUDA(cudaMemsetAsync(w->img, 0, sizeof(float) * L, s));
+                CT_CUDA(cudaMemcpyAsync(w->img, nc.x0, sizeof(float) * g->n,
+                                        cudaMemcpyDeviceToDevice, s));
+            }
+            CT_CUDA(launch_combine_basis(o->basis, w->W, L, ld, w->Y, w->K, w->K, nullptr, step,
+                                         nc.x0 ? w->img : nullptr, w->q, kMaxBlocks, s));
+        }
+        {
+            CT_PHASE(CT_PH_LAYOUT, 1, s);
+            CT_CUDA(launch_image_pairs(g, w->q, w->stop, s));
+        }
+        {
+            CT_PHASE(CT_PH_FORWARD, fwd_launches(g), s);
+            CT_CUDA(launch_forward_proj(g, w->sino, true, w->stop, s));
+        }
+        ax = w->sino;
+    }
+    {
+        CT_PHASE(CT_PH_OTHER, 2, s);
+        CT_CUDA(launch_ncp_check(g, nc.b, ax, w->ncp_tw, w->ncp_part, w->ncp, step, checked,
+                                 w->stop, s));
+    }
     checked = step;
     return CT_OK;
 }
@@ -743,9 +855,14 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
     const int64_t L = w->L, ld = w->ld;
     ArnoldiScratch sc{w->partial, w->counter, kMaxBlocks, w->K};
     const double dp_target = o->tau * o->noise_norm;
+    if (o->stop_rule == CT_STOP_NCP && (st = ncp_ready(g, w)) != CT_OK) return st;
     CT_CUDA(cudaMemsetAsync(w->stop, 0, 2 * sizeof(int), s));
     CT_CUDA(cudaMemsetAsync(w->counter, 0, 4 * sizeof(unsigned), s));
     CT_CUDA(cudaMemsetAsync(w->path, 0, sizeof(int) * K, s));
+    if (w->ncp) CT_CUDA(cudaMemsetAsync(w->ncp, 0xff, sizeof(double) * w->K, s));   // NaN
+    NcpCtx nc;
+    nc.g = g; nc.method = 0; nc.b = b_dev;
+    nc.x0 = u0_dev ? (u0_padded ? u0_dev : w->sino) : nullptr;   // padded u0 (kept in sino)
     // Algorithm 1 set-up: x0 = B u0, r0 = b - A x0, w1 = r0 / ||r0||
     {
         CT_PHASE(CT_PH_OTHER, u0_dev ? 8 : 3, s);
@@ -785,7 +902,7 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
             CT_CUDA(arnoldi_step_basis(o->basis, w->W, L, ld, k, w->q, w->H + (int64_t)k * ldh,
                                        sc, w->aux, w->stop, step, o->reorth != 0, w->cur, true, s));
         }
-        if ((st = stop_checkpoint(w, o, s, dp_target, step, checked)) != CT_OK) return st;
+        if ((st = stop_checkpoint(w, o, s, dp_target, step, checked, nc)) != CT_OK) return st;
     }
     if ((st = run_small_solves(w, o, s, dp_target)) != CT_OK) return st;   // Eq. (hybrid_proj)
     // the hybrid iterate at the last (or stopping) step: x = x0 + B W y = B (u0 + W y)
@@ -829,9 +946,13 @@ static ct_status enqueue_ba(ct_geom *g, const float *b_dev, const float *x0_dev,
     const int64_t msino = (int64_t)g->dg.n_views * g->dg.sino_view_ld;
     ArnoldiScratch sc{w->partial, w->counter, kMaxBlocks, w->K};
     const double dp_target = o->tau * o->noise_norm;
+    if (o->stop_rule == CT_STOP_NCP && (st = ncp_ready(g, w)) != CT_OK) return st;
     CT_CUDA(cudaMemsetAsync(w->stop, 0, 2 * sizeof(int), s));
     CT_CUDA(cudaMemsetAsync(w->counter, 0, 4 * sizeof(unsigned), s));
     CT_CUDA(cudaMemsetAsync(w->path, 0, sizeof(int) * K, s));
+    if (w->ncp) CT_CUDA(cudaMemsetAsync(w->ncp, 0xff, sizeof(double) * w->K, s));   // NaN
+    NcpCtx nc;
+    nc.g = g; nc.method = 1; nc.b = b_dev; nc.x0 = x0_dev;
     // Algorithm 2 set-up: r0 = B (b - A x0), w1 = r0 / ||r0||
     {
         CT_PHASE(CT_PH_OTHER, x0_dev ? 7 : 4, s);
@@ -878,7 +999,7 @@ static ct_status enqueue_ba(ct_geom *g, const float *b_dev, const float *x0_dev,
             CT_CUDA(arnoldi_step_basis(o->basis, w->W, L, ld, k, w->q, w->H + (int64_t)k * ldh,
                                        sc, w->aux, w->stop, step, o->reorth != 0, w->cur, true, s));
         }
-        if ((st = stop_checkpoint(w, o, s, dp_target, step, checked)) != CT_OK) return st;
+        if ((st = stop_checkpoint(w, o, s, dp_target, step, checked, nc)) != CT_OK) return st;
     }
     if ((st = run_small_solves(w, o, s, dp_target)) != CT_OK) return st;   // Eq. (hybrid_proj)
     // the hybrid iterate: x = x0 + W y
@@ -925,6 +1046,7 @@ static ct_status restarted(ct_geom *g, const float *b_dev, float *x_dev, int cyc
     oc.lambda_hist = o->lambda_hist ? lam.data() : nullptr;
     oc.resid_hist = o->resid_hist ? res.data() : nullptr;
     oc.features_dev = nullptr;
+    oc.ncp_hist = nullptr;
     float *u = nullptr;
     ct_hybrid_info total{};
     for (int c = 0; c < cycles; ++c) {
@@ -1173,6 +1295,33 @@ extern "C" ct_status ct_profile_collect(ct_phase_time *out)
 
 extern "C" int64_t ct_launch_count(void) { return g_launches.load(); }
 
+extern "C" ct_status ct_probe(int kind, int64_t reps, float *out_dev, int64_t out_floats,
+                              int64_t *ops, ct_stream_t stream)
+{
+    if (kind != CT_PROBE_GATHER8 && kind != CT_PROBE_MUFU) return einval("ct_probe: bad kind");
+    if (!out_dev || !ops || reps < 1) return einval("ct_probe: need out_dev, ops and reps >= 1");
+    int dev = 0, sms = 0;
+    CT_CUDA(cudaGetDevice(&dev));
+    CT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = probe_blocks_per_sm(kind) * sms;
+    const int64_t threads = (int64_t)blocks * probe_threads();
+    if (out_floats < threads)
+        return einval("ct_probe: out_dev needs " + std::to_string(threads) + " floats");
+    const int64_t r = (reps + probe_chains() - 1) / probe_chains() * probe_chains();
+    CT_CUDA(launch_probe(kind, r, out_dev, blocks, (cudaStream_t)stream));
+    g_launches += 1;
+    *ops = threads * r;
+    return CT_OK;
+}
+
+extern "C" ct_status ct_test_drop_tile_copy(int enable, int64_t wait_cycles)
+{
+    if (enable && (wait_cycles < (1 << 16) || wait_cycles > (1ll << 31)))
+        return einval("ct_test_drop_tile_copy: wait_cycles must be in [2^16, 2^31]");
+    CT_CUDA(arnoldi_test_drop_tile_copy(enable, (long long)wait_cycles));
+    return CT_OK;
+}
+
 // ============================================================================ autotuning
 static std::mutex g_tune_mu;
 static std::map<std::tuple<int, int, int, int, int, int, int, int>, ct_launch_shapes> g_tune_cache;
@@ -1353,7 +1502,7 @@ extern "C" ct_status ct_batch_create(int n_prob, ct_geom *const *geoms, const in
     *out = nullptr;
     ct_status st = check_opts(o);
     if (st != CT_OK) return st;
-    if (o->lambda_hist || o->resid_hist || o->features_dev)
+    if (o->lambda_hist || o->resid_hist || o->features_dev || o->ncp_hist)
         return einval("ct_batch_create: history and feature pointers must be NULL");
     for (int i = 0; i < n_prob; ++i) {
         if (!geoms[i]) return einval("ct_batch_create: null geometry");
@@ -1380,7 +1529,8 @@ extern "C" ct_status ct_batch_create(int n_prob, ct_geom *const *geoms, const in
             ct_batch_destroy(bt);
             return st;
         }
-        if ((st = ws_get(geoms[i], mth, o->max_iters, o->basis, &bt->ws[i])) != CT_OK) {
+        if ((st = ws_get(geoms[i], mth, o->max_iters, o->basis, &bt->ws[i])) != CT_OK ||
+            (o->stop_rule == CT_STOP_NCP && (st = ncp_ready(geoms[i], bt->ws[i])) != CT_OK)) {
             ct_batch_destroy(bt);
             return st;
         }

@@ -165,6 +165,8 @@ struct ArnoldiScratch {
 
 // caches the Gram-Schmidt kernels' one-wave grid for the current device (before a capture)
 cudaError_t arnoldi_prepare();
+// test hook of the bounded TMA waits (see ct_test_drop_tile_copy)
+cudaError_t arnoldi_test_drop_tile_copy(int enable, long long wait_cycles);
 
 // ----------------------------------------------------------------------------- small solve
 constexpr int kMaxSmallK = 160;   // largest projected problem held in shared memory
@@ -186,6 +188,7 @@ struct SmallSolveParams {
     int kfirst = 0;   // batched launch over k = kfirst + 1 .. kfirst + k (outputs indexed k - 1)
     int only_y = 0;   // batched launch: only the block of the final step (stop[0] when set,
                       // else kmax) runs, and it forms y
+    int y_at = 0;     // also form y at this step (the NCP check's iterate)
 };
 cudaError_t launch_small_solve(const SmallSolveParams &p, cudaStream_t s);
 // sets the kernel's shared-memory limit on the current device (call before a stream capture)
@@ -197,6 +200,24 @@ cudaError_t launch_small_solve_batched(const SmallSolveParams &p, cudaStream_t s
 cudaError_t launch_stop_check(const double *res, int k0, int k1, int rule, double target,
                               double tol, int *stop, cudaStream_t s);
 size_t small_solve_smem_bytes(int k);
+
+// ----------------------------------------------------------------------------- probes
+int probe_threads();
+int probe_chains();
+int probe_blocks_per_sm(int kind);
+// kind 0: 8-byte L1 gathers; kind 1: reciprocal + square root pairs; `blocks` x probe_threads()
+// threads, each `reps` operations (a multiple of probe_chains()), one float each into out
+cudaError_t launch_probe(int kind, int64_t reps, float *out, int blocks, cudaStream_t s);
+
+// ----------------------------------------------------------------------------- NCP stop rule
+constexpr int kNcpMaxBins = 8192;   // detector row length the NCP kernels hold in shared memory
+size_t ncp_smem_bytes(int n);
+cudaError_t ncp_prepare(int n);     // shared-memory limit of the row kernel (before a capture)
+// distances[step - 1] = NCP distance of the rows of b - ax (b dense [view][v][u], ax padded);
+// stops the solve at `prev` (stop[0] = prev) when the distance grew since that check
+cudaError_t launch_ncp_check(const ct_geom *g, const float *b, const float *ax_pad,
+                             const float2 *tw, float *part, double *dist, int step, int prev,
+                             int *stop, cudaStream_t s);
 
 // ----------------------------------------------------------------------------- learned lambda
 // network kernels (mlp.cu): P = FP32 parameter vector, X = n x 80 row-major features

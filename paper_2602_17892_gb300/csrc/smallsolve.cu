@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(kSSThreads, 1) small_solve_kernel(SmallSolvePa
         const int target = (P.stop && P.stop[0] > 0) ? P.stop[0] : P.kmax;
         if (k != target) return;
     }
-    const bool need_y = P.always_y || k == P.kmax || stop_now || P.only_y;
+    const bool need_y = P.always_y || k == P.kmax || stop_now || P.only_y || k == P.y_at;
     extern __shared__ double sd[];
     const int lda = k + 1;
     double *A = sd;                       // (k+1) x k, column-major

@@ -98,3 +98,18 @@ def test_learned_lambda_entry_points_reject_bad_arguments(lib):
                              ctypes.byref(o), None, None)
     assert st == Bn.CT_EINVAL and b"lambda_net_dev" in lib.ct_last_error()
     assert Bn.CT_MLP_NPARAMS == 64 * 80 + 64 + 64 * 64 + 64 + 64 + 1 + 2 * 80
+
+
+def test_ncp_rule_and_test_hook_are_checked_on_the_host(lib):
+    from paper_2602_17892_gb300 import _binding as Bn
+    o = Bn.HybridOpts()
+    lib.ct_hybrid_opts_default(ctypes.byref(o))
+    assert not o.ncp_hist
+    o.stop_rule = 4                                     # no such rule
+    assert lib.ab_gmres_hybrid(ctypes.c_void_p(1), ctypes.c_void_p(16), None,
+                               ctypes.c_void_p(16), ctypes.byref(o), None, None) == Bn.CT_EINVAL
+    o.stop_rule = Bn.STOPS["ncp"]
+    o.stop_every = 0
+    assert lib.ba_gmres_hybrid(ctypes.c_void_p(1), ctypes.c_void_p(16), None,
+                               ctypes.c_void_p(16), ctypes.byref(o), None, None) == Bn.CT_EINVAL
+    assert lib.ct_test_drop_tile_copy(1, 10) == Bn.CT_EINVAL   # limit below 2^16

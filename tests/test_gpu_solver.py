@@ -317,3 +317,62 @@ def test_stopping_rules_match_oracle(method, stop, rule):
         assert info["iters_done"] == ref["k"], (every, info, ref["k"], ref["status"])
         assert info["status"] == "CT_OK"
         assert rel(xg, ref["x"]) <= ITER_TOL
+
+
+# Distances of the NCP: the FP32 residual b - A x_k moves them by a few 1e-4 relative.
+NCP_TOL = 5e-3
+
+
+@pytest.mark.parametrize("method,rule,every", [
+    ("ab", "none", 1), ("ab", "gcv", 1), ("ba", "gcv", 1), ("ab", "none", 3),
+    ("ba", "none", 3), ("ab", "lcurve", 3), ("ba", "lcurve", 3), ("ba", "gcv", 3)])
+def test_ncp_stopping_rule_matches_oracle(method, rule, every):
+    """Sec. 3.2, the NCP criterion: the device forms b - A x_k at every checked step, the
+    rows' normalized cumulative periodograms and their distance from the white-noise line,
+    and stops at the same step as the oracle, returning the previous check's iterate."""
+    g = synth.fanflat2d(45, 60, 70, 150.0, 240.0, ny=38)
+    x_true, b, e = problem(g, 5, 0.02, 77)
+    A, B = OP.operators(g)
+    ref = OS.hybrid_gmres(method, A, B, b, 40, rule=rule, stop_rule="ncp", ncp_row=g.n_det_u,
+                          stop_every=every)
+    assert ref["status"] == "stopped"
+    d_ref = dict(ref["ncp"])
+    ks = sorted(d_ref)
+    for a, c in zip(ks, ks[1:]):          # decisions clear of the FP32 distance error
+        assert abs(d_ref[c] - d_ref[a]) > 4 * NCP_TOL * d_ref[a], (a, c, d_ref)
+    G = gpu_geom(g)
+    xg, info = _gpu_solve(method, G, b, 40, rule, stop="ncp", stop_every=every)
+    assert info["status"] == "CT_OK" and info["iters_done"] == ref["k"], (info, ref["k"])
+    for k, d in d_ref.items():
+        assert abs(info["ncp"][k - 1] - d) <= NCP_TOL * d, (k, info["ncp"][k - 1], d)
+    unchecked = [k for k in range(1, 41) if k not in d_ref]
+    assert np.all(np.isnan(info["ncp"][np.array(unchecked) - 1]))
+    assert rel(xg, ref["x"]) <= ITER_TOL
+
+
+@pytest.mark.parametrize("method", ["ab", "ba"])
+def test_ncp_stop_from_an_initial_guess(method):
+    """The NCP residual b - A x_k includes the initial guess (AB: x0 = B u0)."""
+    torch = _torch()
+    from paper_2602_17892_gb300 import ab_gmres_hybrid, ba_gmres_hybrid
+    g = synth.fanflat2d(45, 60, 70, 150.0, 240.0, ny=38)
+    x_true, b, e = problem(g, 5, 0.02, 77)
+    A, B = OP.operators(g)
+    G = gpu_geom(g)
+    x = torch.zeros(g.n, dtype=torch.float32, device="cuda")
+    if method == "ab":
+        u0 = f32(0.02 * synth.standard_normal(g.m, 8))
+        info = ab_gmres_hybrid(G, to_dev(b), x, u0=to_dev(u0), max_iters=30, rule="gcv",
+                               stop="ncp", stop_every=2)
+        x0 = B(u0)
+    else:
+        x0 = f32(0.3 * x_true.reshape(-1))
+        info = ba_gmres_hybrid(G, to_dev(b), x, x0=to_dev(x0), max_iters=30, rule="gcv",
+                               stop="ncp", stop_every=2)
+    torch.cuda.synchronize()
+    ref = OS.hybrid_gmres(method, A, B, b, 30, rule="gcv", x0=x0, stop_rule="ncp",
+                          ncp_row=g.n_det_u, stop_every=2)
+    assert info["iters_done"] == ref["k"]
+    for k, d in ref["ncp"]:
+        assert abs(info["ncp"][k - 1] - d) <= NCP_TOL * d
+    assert rel(x.cpu().numpy(), ref["x"]) <= ITER_TOL

@@ -49,6 +49,37 @@ def test_noalloc_step_matches_allocating_step_twice():
         assert abs(np.linalg.norm(w_new) - 1.0) <= TOL_H
 
 
+def _fp64_mgs_twice(W, q, k):
+    """FP64 modified Gram-Schmidt, two passes, on the same FP32 inputs (Eq. (Hessenberg))."""
+    W64 = W[: k + 1].astype(np.float64)
+    qq = q.astype(np.float64)
+    h = np.zeros(k + 2)
+    for _ in range(2):
+        for i in range(k + 1):
+            d = qq @ W64[i]
+            h[i] += d
+            qq -= d * W64[i]
+    h[k + 1] = np.linalg.norm(qq)
+    return h, qq / h[k + 1]
+
+
+def test_noalloc_step_at_its_limit_then_smaller_matches_fp64_gram_schmidt():
+    """k = 126 fills the static scratch (128 partial-sum columns of each block, the last h
+    slot); a smaller step afterwards must not see the previous call's contents."""
+    from paper_2602_17892_gb300 import _binding as Bn
+    for call, (L, k, seed) in enumerate([(4096, 126, 5), (8192, 17, 6), (4096, 126, 7),
+                                         (1024, 0, 8)]):
+        W, q = _inputs(L, k, seed)
+        h_ref, w_ref = _run(Bn.ct_arnoldi_step, W, q, L, k)
+        h_new, w_new = _run(Bn.ct_arnoldi_step_noalloc, W, q, L, k)
+        h64, w64 = _fp64_mgs_twice(W, q, k)
+        assert np.all(np.isfinite(h_new)), f"call {call}"
+        assert np.linalg.norm(h_new - h64) <= TOL_H * np.linalg.norm(h64), f"call {call}"
+        assert np.linalg.norm(w_new - w64) <= TOL_W * np.linalg.norm(w64), f"call {call}"
+        assert np.linalg.norm(h_new - h_ref) <= TOL_H * np.linalg.norm(h_ref), f"call {call}"
+        assert np.linalg.norm(w_new - w_ref) <= TOL_W * np.linalg.norm(w_ref), f"call {call}"
+
+
 def test_noalloc_step_rejects_sizes_beyond_its_scratch():
     import torch
     from paper_2602_17892_gb300 import _binding as Bn
