@@ -57,3 +57,35 @@ def problem(geom, phantom_seed, eta, noise_seed):
     bt = OP.forward(geom, x).reshape(-1)
     b, e = synth.add_noise(bt, eta, noise_seed)
     return x.reshape(-1), f32(b), e
+
+
+EPS32 = 2.0 ** -24
+
+
+def max_filter(a, shape, axes):
+    """Largest |a| over each entry and its +-1 neighbours along `axes` (zero outside)."""
+    m = np.abs(np.asarray(a, np.float64).reshape(shape))
+    out = m.copy()
+    for ax in axes:
+        for sh in (-1, 1):
+            r = np.roll(m, sh, axis=ax)
+            idx = [slice(None)] * m.ndim
+            idx[ax] = 0 if sh == 1 else -1
+            r[tuple(idx)] = 0.0
+            out = np.maximum(out, r)
+    return out
+
+
+def assert_elementwise(got, ref, scale, units, what=""):
+    """max_i |got_i - ref_i| <= 8 units eps32 scale_i (+ 1 % of the largest such bound): the
+    FP32 rounding of a projector entry grows with the number of interpolation positions it
+    walks (units) times the magnitudes it interpolates (scale, the operator applied to the
+    local maximum of |input|).  Catches a wrong row, bin or pixel that relative L2 hides."""
+    got = np.asarray(got, np.float64).reshape(-1)
+    ref = np.asarray(ref, np.float64).reshape(-1)
+    scale = np.asarray(scale, np.float64).reshape(-1)
+    lim = 8.0 * units * EPS32 * scale
+    lim = lim + 1e-2 * lim.max() + 1e-30
+    err = np.abs(got - ref)
+    i = int(np.argmax(err / lim))
+    assert err[i] <= lim[i], (what, i, err[i], lim[i], got[i], ref[i])

@@ -6,7 +6,7 @@ import pytest
 
 import synth
 from oracle import proj as OP
-from tests._common import f32, gpu_A, gpu_B, gpu_geom, rel
+from tests._common import assert_elementwise, f32, gpu_A, gpu_B, gpu_geom, max_filter, rel
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -31,6 +31,7 @@ def test_forward_matches_oracle(name):
     yg = gpu_A(G, x)
     yo = OP.forward(g, x).reshape(-1)
     assert rel(yg, yo) <= TOL
+    _check_A_entries(g, x, yg, yo)
 
 
 @pytest.mark.parametrize("name", sorted(GEOMS))
@@ -41,6 +42,20 @@ def test_backprojector_matches_oracle(name):
     xg = gpu_B(G, y)
     xo = OP.back_pixel(g, y).reshape(-1)
     assert rel(xg, xo) <= TOL
+    _check_B_entries(g, y, xg, xo)
+
+
+def _check_A_entries(g, x, yg, yo):
+    """Every ray, not just the norm: |A_gpu x - A x| within the FP32 bound of that ray."""
+    scale = OP.forward(g, max_filter(x, g.image_shape, range(len(g.image_shape))))
+    assert_elementwise(yg, yo, scale, max(g.nx, g.ny, g.nz), "A")
+
+
+def _check_B_entries(g, y, xg, xo):
+    """Every pixel: |B_gpu y - B y| within the FP32 bound of that pixel."""
+    axes = (1, 2) if g.kind == synth.CONE3D else (1,)
+    scale = OP.back_pixel(g, max_filter(y, g.sino_shape, axes))
+    assert_elementwise(xg, xo, scale, max(g.n_det_u, g.n_det_v, g.n_views), "B")
 
 
 def test_fan512_full_size_projectors():
@@ -48,9 +63,13 @@ def test_fan512_full_size_projectors():
     g = synth.fan512_case()["geom"]
     x = f32(synth.ellipse_phantom(512, seed=0))
     G = gpu_geom(g)
-    assert rel(gpu_A(G, x), OP.forward(g, x)) <= TOL
-    y = f32(OP.forward(g, x))
-    assert rel(gpu_B(G, y), OP.back_pixel(g, y)) <= TOL
+    yg, yo = gpu_A(G, x), OP.forward(g, x).reshape(-1)
+    assert rel(yg, yo) <= TOL
+    _check_A_entries(g, x, yg, yo)
+    y = f32(yo)
+    xg, xo = gpu_B(G, y), OP.back_pixel(g, y).reshape(-1)
+    assert rel(xg, xo) <= TOL
+    _check_B_entries(g, y, xg, xo)
 
 
 def test_projectors_are_linear_and_unmatched():

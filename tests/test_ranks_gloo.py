@@ -56,3 +56,58 @@ def test_reference_arm_other_ranks_do_no_work(capsys):
     import bench
     assert bench.bench_reference(None, 1, 2) is None
     assert capsys.readouterr().out == ""
+
+
+def _slices_rank_main(rank, world, port, out):
+    """Each gloo rank computes its own share of the 256-slice batch (no communication) and the
+    ranks then gather the shares to check them against each other."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import bench
+        import synth
+        cases = synth.batched_slices(256, seed=7)
+        works = [bench.slice_work(c["geom"], 60) for c in cases]
+        mine = bench.partition_slices(works, world)[rank]
+        shares = [None] * world
+        dist.all_gather_object(shares, (mine, sum(works[i] for i in mine)))
+        out[rank] = (shares, works)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_slice_batch_partition_over_gloo_ranks(world):
+    """--workload slices: every slice is solved by exactly one rank, every rank computes the
+    same partition, and the heaviest rank carries at most total / world + the largest slice."""
+    port = _free_port()
+    with mp.get_context("spawn").Manager() as mgr:
+        out = mgr.dict()
+        mp.spawn(_slices_rank_main, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    shares0, works = res[0]
+    for r in range(world):
+        assert res[r][0] == shares0                # the same answer on every rank
+    idx = sorted(i for part, _ in shares0 for i in part)
+    assert idx == list(range(256))                 # each slice exactly once
+    loads = [w for _, w in shares0]
+    assert max(loads) <= sum(works) / world + max(works)
+    assert max(loads) / (sum(works) / world) < 1.02    # and close to even on this batch
+
+
+def test_partition_edge_cases():
+    import bench
+    assert bench.partition_slices([5, 3], 1) == [[0, 1]]
+    assert bench.partition_slices([1, 1, 1], 4) == [[0], [1], [2], []]
+    assert bench.partition_slices([], 2) == [[], []]
+    assert bench.partition_slices([10, 1, 1, 8], 2) == [[0], [1, 2, 3]]
+
+
+def test_rank_launch_is_checked_against_gpus():
+    import bench
+    assert bench.check_ranks(1, {}) is None
+    assert bench.check_ranks(4, {"WORLD_SIZE": "4"}) is None
+    assert "torch.distributed.run" in bench.check_ranks(8, {})
+    assert "does not match" in bench.check_ranks(2, {"WORLD_SIZE": "4"})
+    assert bench.check_ranks(0, {}) is not None
