@@ -160,31 +160,76 @@ def _oracle(method, geom, b, iters, rule, **kw):
     return OS.hybrid_gmres(method, A, B, b, iters, rule=rule, **kw)
 
 
+def _noisy(op, eps, seed):
+    """The operator with relative noise eps on every output (FP64): a model of projector
+    outputs that carry errors at the projectors' parity tolerance."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+
+    def f(v):
+        y = op(v)
+        return y + eps * np.linalg.norm(y) * rng.standard_normal(y.size) / math.sqrt(y.size)
+    return f
+
+
 def test_small_parallel_ab_gcv_matches_oracle():
-    """64x64 ellipses, 90 parallel views x 95 bins, 1 % noise, hybrid AB-GMRES, 30 its, GCV."""
+    """64x64 ellipses, 90 parallel views x 95 bins, 1 % noise, hybrid AB-GMRES, 30 its, GCV,
+    checked at every one of the 30 steps.
+
+    Per step k the test holds:
+    (1) the GPU's projected residual rho_k to the true residual ||b - A x_k|| of the GPU's own
+        iterate x_k (FP64 oracle A; the solve is rerun with K = k), within the FP32 Arnoldi
+        relation's error (eps32 sqrt(k+1) + eps_op) sigma_1 ||y|| + eps32 beta, eps_op = 1e-5 the
+        projectors' tolerance;
+    (2) rho_k to the oracle's rho_k(lambda_k) on the oracle's H_k, and the GCV value of the
+        GPU's lambda_k on the oracle's H_k to the oracle's minimum, within 3x what the oracle
+        itself shows at step k when its operator outputs carry relative noise eps_op (three
+        seeded runs).  The exact FP64 Krylov space of this problem is fragile between k = 16 and
+        26: any perturbation of the operator above ~1e-9 (FP32 rounding, or the noise model)
+        moves rho_k(lambda) there by up to 1.5e-2 and all perturbed runs agree with one another,
+        so the bound comes from the oracle's sensitivity, not from a fixed number;
+    and, at k = 30, the iterate against the oracle iterate at the GPU's lambda within 1e-4, and
+    with the oracle's final lambda injected, the iterate within 1e-4 of the oracle's."""
     case = synth.small_parallel_case()
     g = case["geom"]
     x_true, b, e = problem(g, case["phantom_seed"], case["eta"], case["noise_seed"])
     G = gpu_geom(g)
-    xg, info = _gpu_solve("ab", G, b, 30, "gcv")
-    ref = _oracle("ab", g, b, 30, "gcv")
-    assert info["status"] == "CT_OK" and info["iters_done"] == 30
-    # GCV is flat near its minimum, so the FP32-perturbed projected problem may move the
-    # argument by a few per cent (and the iterate with it by ~1e-4 after 30 steps): the GPU
-    # iterate is compared with the oracle's iterate at the lambda the GPU's GCV chose, and that
-    # choice by the GCV value it attains on the oracle's projected problem against the oracle's
-    # minimum (unique).  Projected residuals at a given lambda are not compared per step: with
-    # sigma_min(H_k) ~ 1e-4 sigma_1 they move by ~1e-3 between an FP32 and an FP64 Krylov
-    # basis, while the regularised iterate does not.
-    ref_g = _oracle("ab", g, b, 30, "fixed", lam_fixed=info["lambdas"][-1])
+    K = 30
+    xg, info = _gpu_solve("ab", G, b, K, "gcv")
+    ref = _oracle("ab", g, b, K, "gcv")
+    assert info["status"] == "CT_OK" and info["iters_done"] == K
+    A, B = OP.operators(g)
+    eps32, eps_op = 2.0 ** -24, 1e-5
+    svd = [OS.projected_svd(ref["H"][: k + 1, :k], ref["beta"]) for k in range(1, K + 1)]
+    lam_g, rho_g = info["lambdas"], info["resid"]
+    rho_ref = np.array([math.sqrt(OS.residual_sq(lam_g[k - 1], *svd[k - 1][:2]))
+                        for k in range(1, K + 1)])
+    gcv_min = np.array([OS.gcv_value(ref["lambdas"][k - 1], *svd[k - 1][:2]) for k in range(1, K + 1)])
+    # the oracle's own sensitivity to operator errors of the projectors' size, per step
+    dev_rho, dev_gcv = np.zeros(K), np.zeros(K)
+    for seed in (901, 902, 903):
+        pr = OS.hybrid_gmres("ab", _noisy(A, eps_op, seed), B, b, K, rule="gcv")
+        for k in range(1, K + 1):
+            s, c, _ = OS.projected_svd(pr["H"][: k + 1, :k], pr["beta"])
+            d = abs(math.sqrt(OS.residual_sq(lam_g[k - 1], s, c)) - rho_ref[k - 1]) / rho_ref[k - 1]
+            dev_rho[k - 1] = max(dev_rho[k - 1], d)
+            gp = OS.gcv_value(pr["lambdas"][k - 1], *svd[k - 1][:2]) / gcv_min[k - 1] - 1.0
+            dev_gcv[k - 1] = max(dev_gcv[k - 1], gp)
+    for k in range(1, K + 1):
+        s, c, Vt = svd[k - 1]
+        y = OS.tikhonov_y(lam_g[k - 1], s, c, Vt)
+        xk = xg if k == K else _gpu_solve("ab", G, b, k, "gcv")[0]
+        true_res = np.linalg.norm(b - A(xk))
+        bound = ((eps32 * math.sqrt(k + 1) + eps_op) * s[0] * np.linalg.norm(y)
+                 + eps32 * ref["beta"])
+        assert abs(rho_g[k - 1] - true_res) <= bound, (k, rho_g[k - 1], true_res, bound)
+        assert abs(rho_g[k - 1] - rho_ref[k - 1]) <= (3 * dev_rho[k - 1] + 1e-6) * rho_ref[k - 1], \
+            (k, rho_g[k - 1], rho_ref[k - 1], dev_rho[k - 1])
+        g_gpu = OS.gcv_value(lam_g[k - 1], s, c)
+        assert g_gpu <= gcv_min[k - 1] * (1 + 3 * dev_gcv[k - 1] + 1e-9), (k, g_gpu, gcv_min[k - 1])
+    ref_g = _oracle("ab", g, b, K, "fixed", lam_fixed=lam_g[-1])
     assert rel(xg, ref_g["x"]) <= ITER_TOL
-    for k in range(1, 31):
-        s, c, _ = OS.projected_svd(ref["H"][: k + 1, :k], ref["beta"])
-        g_gpu = OS.gcv_value(info["lambdas"][k - 1], s, c)
-        g_ref = OS.gcv_value(ref["lambdas"][k - 1], s, c)
-        assert g_gpu <= g_ref * (1 + 1e-2), k
     # the oracle's final lambda injected: isolates the Krylov path from the lambda choice
-    xf, _ = _gpu_solve("ab", G, b, 30, "fixed", lambda_fixed=ref["lambdas"][-1])
+    xf, _ = _gpu_solve("ab", G, b, K, "fixed", lambda_fixed=ref["lambdas"][-1])
     assert rel(xf, ref["x"]) <= ITER_TOL
     assert OS.rre(xg, x_true) < 0.5
 
