@@ -227,15 +227,20 @@ typedef struct {
     int b_views;     /* 2D pixel-driven B: views per loop iteration (1, or 2 with paired FP32
                         arithmetic, gathers in batches of 8 view pairs, at most 8 rows per
                         block; the same operations, so results do not change)              */
+    int a_rays;      /* 3D Joseph A: detector rows per thread, 1 or 2 (two rays of one detector
+                        column share their in-plane tap positions; the same operations per
+                        sample, so results do not change); ignored in 2D                    */
 } ct_launch_shapes;
 
 /* Time the candidate launch shapes of the projectors on this geometry and keep the fastest for
  * later calls on `g`.  2D: Joseph A with (threads, views) per block in (128, 1), (128, 2),
  * (128, 4), (256, 1), (256, 2), (256, 4), (512, 4), (512, 8); pixel-driven B with 4, 8 or 16
- * pixel rows per block and one view per loop iteration, or 4 or 8 rows and two.  3D: Joseph (slab thickness, detector
- * rows per block) in (16, 1), (16, 4), (16, 8), (64, 4), (64, 8) and one pass over the whole
- * volume with 1, 4 or 8 rows (the voxel-driven
- * B has one shape, 32 x 4 columns of 8 voxels).  The shapes change only the order of work, not
+ * pixel rows per block and one view per loop iteration, or 4 or 8 rows and two.  3D: Joseph
+ * (slab thickness, warp rows per block, detector rows per thread) in (16, 1, 1), (16, 4, 1),
+ * (16, 8, 1), (64, 4, 1), (64, 8, 1), one pass over the whole volume with 1, 4 or 8 warp rows
+ * and one detector row per thread, and (16, 4, 2), (64, 4, 2), one pass with 2 or 4 warp rows
+ * and two detector rows per thread (the voxel-driven B has one shape, 32 x 4 columns of 8
+ * voxels).  The shapes change only the order of work, not
  * the arithmetic of a sample.  Geometries of the same kind and sizes reuse an earlier result.
  * Runs a few dozen projector launches on `stream`, synchronises it, and allocates two temporary
  * device buffers.  The chosen shapes are written to *out (may be NULL). */
@@ -243,8 +248,8 @@ ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_shapes *out
 /* Set the projectors' launch shapes of `g` explicitly (for instance a shape an earlier autotune
  * found, or a fixed one for timing).  Values: a_threads in {128, 256, 512} with a_threads /
  * a_views >= 32 and a_views in {1, 2, 4, 8} (2D), a_slab >= 1 (3D; >= nz + 1 is one pass),
- * a_views in 1..8 detector rows (3D), b_rows in {4, 8, 16}, b_views in {1, 2} (b_rows 16 only
- * with b_views 1); anything else
+ * a_views in 1..8 warp rows (3D), a_rays in {1, 2} (3D), b_rows in {4, 8, 16}, b_views in
+ * {1, 2} (b_rows 16 only with b_views 1); anything else
  * returns CT_EINVAL and leaves `g` unchanged.  Host-only; shapes change the order of work, not a
  * sample's arithmetic. */
 ct_status ct_geom_set_launch_shapes(ct_geom *g, const ct_launch_shapes *shapes);

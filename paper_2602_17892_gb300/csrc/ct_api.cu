@@ -448,6 +448,7 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     dg.back_adjoint = 0;
     dg.b_noclamp = cone ? 0 : (pixels_inside_detector(&g->desc) ? 1 : 0);
     dg.tune_a_slab = 16;
+    dg.tune_a_rays = 1;
 
     std::vector<Ray2D> rays;
     std::vector<RayXY> rays_xy;
@@ -1334,6 +1335,7 @@ static ct_launch_shapes shapes_of(const DeviceGeom &d)
     r.a_slab = d.tune_a_slab;
     r.b_rows = d.tune_b_rows;
     r.b_views = d.tune_b_views;
+    r.a_rays = d.tune_a_rays;
     return r;
 }
 
@@ -1349,7 +1351,7 @@ extern "C" ct_status ct_geom_set_launch_shapes(ct_geom *g, const ct_launch_shape
     bool ok = in(sh->b_rows, {4, 8, 16}) && in(sh->b_views, {1, 2}) &&
               !(sh->b_views == 2 && sh->b_rows > 8);
     if (cone)
-        ok = ok && sh->a_slab >= 1 && sh->a_views >= 1 && sh->a_views <= 8;
+        ok = ok && sh->a_slab >= 1 && sh->a_views >= 1 && sh->a_views <= 8 && in(sh->a_rays, {1, 2});
     else
         ok = ok && in(sh->a_threads, {128, 256, 512}) && in(sh->a_views, {1, 2, 4, 8}) &&
              sh->a_threads / sh->a_views >= 32;
@@ -1360,6 +1362,7 @@ extern "C" ct_status ct_geom_set_launch_shapes(ct_geom *g, const ct_launch_shape
     dg.tune_a_slab = sh->a_slab;
     dg.tune_b_rows = sh->b_rows;
     dg.tune_b_views = sh->b_views;
+    dg.tune_a_rays = cone ? sh->a_rays : 1;
     return CT_OK;
 }
 
@@ -1389,6 +1392,7 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
             dg.tune_a_slab = it->second.a_slab;
             dg.tune_b_rows = it->second.b_rows;
             dg.tune_b_views = it->second.b_views;
+            dg.tune_a_rays = it->second.a_rays;
             if (out) *out = it->second;
             return CT_OK;
         }
@@ -1431,14 +1435,20 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
     // 2D Joseph: (threads, warp rows = views per block)
     static const int a2[8][2] = {{128, 1}, {128, 2}, {128, 4}, {256, 1},
                                  {256, 2}, {256, 4}, {512, 4}, {512, 8}};
-    // 3D: (z-slab thickness, detector rows per block); 1 << 20 = one pass over the volume
-    static const int a3[8][2] = {{16, 1}, {16, 4}, {16, 8}, {64, 4}, {64, 8},
-                                 {1 << 20, 1}, {1 << 20, 4}, {1 << 20, 8}};
+    // 3D: (z-slab thickness, warp rows per block, detector rows per thread); 1 << 20 = one
+    // pass over the volume
+    static const int a3[12][3] = {{16, 1, 1}, {16, 4, 1}, {16, 8, 1}, {64, 4, 1}, {64, 8, 1},
+                                  {1 << 20, 1, 1}, {1 << 20, 4, 1}, {1 << 20, 8, 1},
+                                  {16, 4, 2}, {64, 4, 2}, {1 << 20, 2, 2}, {1 << 20, 4, 2}};
     static const int b2[5][2] = {{4, 1}, {8, 1}, {16, 1}, {4, 2}, {8, 2}};
     auto fwd = [&]() { return launch_forward_proj(g, y, true, nullptr, s); };
     ct_status st;
     if (cone)
-        st = time_best(fwd, 8, [&](int c) { dg.tune_a_slab = a3[c][0]; dg.tune_a_views = a3[c][1]; });
+        st = time_best(fwd, 12, [&](int c) {
+            dg.tune_a_slab = a3[c][0];
+            dg.tune_a_views = a3[c][1];
+            dg.tune_a_rays = a3[c][2];
+        });
     else
         st = time_best(fwd, 8, [&](int c) {
             dg.tune_a_threads = a2[c][0];

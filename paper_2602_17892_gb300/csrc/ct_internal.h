@@ -67,6 +67,8 @@ struct DeviceGeom {
     int tune_b_views;   // 2D pixel-driven B: views per loop iteration (1, or 2 in paired FP32)
     int b_noclamp;      // 2D: every pixel centre projects inside the detector in every view
     int tune_a_slab;    // 3D Joseph A: z slab thickness (tap rows) per launch
+    int tune_a_rays;    // 3D Joseph A: detector rows per thread (1, or 2 sharing the in-plane
+                        // coordinate)
     int64_t sino_view_ld; // floats per view in the padded sinogram (2D: sino_ld; 3D: (ndv + 2)
                           // rows of sino_ld, detector row 0 at row 1)
     int sino_row0;      // offset of detector row 0 inside a padded view (0 in 2D, sino_ld in 3D)

@@ -259,6 +259,208 @@ __global__ void __launch_bounds__(256, 3) joseph3d_kernel(
     else if (any) *out += acc * weight;
 }
 
+// The same projector with two rays per thread: detector rows iv and iv + 1 of one column iu.
+// Their x-y projections coincide (the fan ray of the column), so at every driving plane they
+// share the in-plane tap position, its floor, weight and address part; only z differs.  The
+// per-ray arithmetic is the single-ray kernel's, operation for operation (the in-plane
+// coordinate in scalar FP32, the two rays' z coordinates as one f32x2 pair, the sums in plane
+// order), so the results are bitwise those of joseph3d_kernel.  Planes go in batches of
+// kJ3PairBatch (4 gathers per plane in flight).
+constexpr int kJ3PairBatch = 2;
+
+__device__ __forceinline__ void ray_z_range(float zs, float tmid, float zm, int r_lo, int r_hi,
+                                            int &lo, int &hi)
+{
+    if (fabsf(zs) > 1e-20f) {
+        const float r = __frcp_rn(zs);
+        const float ta = tmid + ((float)(r_lo - 2) - zm) * r;
+        const float tb = tmid + ((float)r_hi - zm) * r;
+        lo = max(lo, (int)floorf(fminf(ta, tb)) - 2);
+        hi = min(hi, (int)ceilf(fmaxf(ta, tb)) + 2);
+    }
+}
+
+template <bool SLAB>
+__global__ void __launch_bounds__(256, 3) joseph3d_pair_kernel(
+    const RayXY *__restrict__ rxy, int ndu, int ndv, double pitch_v, double h,
+    const float2 *__restrict__ px, int64_t zsx, int ldx, const float2 *__restrict__ py,
+    int64_t zsy, int ldy, int chunk, int nx, int ny, int nz, float *__restrict__ y,
+    int64_t y_view_ld, int y_ld, int y_off, int iv0, int iv1, int r_lo, int r_hi, int accumulate,
+    const int *stop)
+{
+    if (stop && stop[0] != 0) return;
+    // a block is 32 detector columns x 2 blockDim.y detector rows of one view; warp w takes rows
+    // 2w and 2w + 1 of the block (rays a and b of each lane)
+    const int iu = blockIdx.x * 32 + threadIdx.x;
+    const int view = blockIdx.y;
+    const int iva_raw = iv0 + 2 * (blockIdx.z * blockDim.y + threadIdx.y);
+    const bool col_ok = iu < ndu;
+    const bool va_ok = col_ok && iva_raw <= iv1, vb_ok = col_ok && iva_raw + 1 <= iv1;
+    const int iva = va_ok ? iva_raw : iv0, ivb = vb_ok ? iva_raw + 1 : iv0;
+    const RayXY R = rxy[(int64_t)view * ndu + (col_ok ? iu : 0)];
+    const double va = (iva - 0.5 * (ndv - 1)) * pitch_v, vb = (ivb - 0.5 * (ndv - 1)) * pitch_v;
+    const bool zda = fabs(va) * fabs(R.rda) > 1.0, zdb = fabs(vb) * fabs(R.rda) > 1.0;
+    const int mode = (int)((R.packed >> 30) & 3);          // in-plane driving axis
+    const bool ax = mode == 0;
+    const int n_drive = ax ? nx : ny;
+    const float tmid = 0.5f * (float)(n_drive - 1);
+    const double zsa_d = va * R.rda, zsb_d = vb * R.rda;
+    const float zsa = (float)zsa_d, zma = (float)(0.5 * (nz - 1) - R.sa_h * zsa_d);
+    const float zsb = (float)zsb_d, zmb = (float)(0.5 * (nz - 1) - R.sa_h * zsb_d);
+    float acca = 0.f, accb = 0.f;
+    bool anya = false, anyb = false;
+    const int lo0 = R.packed & 0x7fff, hi0 = (R.packed >> 15) & 0x7fff;
+    int loa = lo0, hia = hi0, lob = lo0, hib = hi0;
+    if (!va_ok || zda) { loa = 1; hia = 0; } else ray_z_range(zsa, tmid, zma, r_lo, r_hi, loa, hia);
+    if (!vb_ok || zdb) { lob = 1; hib = 0; } else ray_z_range(zsb, tmid, zmb, r_lo, r_hi, lob, hib);
+    const int tlo = min(hia >= loa ? loa : 0x7fffffff, hib >= lob ? lob : 0x7fffffff);
+    const int thi = max(hia >= loa ? hia : -1, hib >= lob ? hib : -1);
+    const int wlo = __reduce_min_sync(0xffffffffu, tlo);
+    const int whi = __reduce_max_sync(0xffffffffu, thi);
+    if (wlo <= whi) {
+        const float2 *L = ax ? px : py;
+        const int64_t zsl = ax ? zsx : zsy;
+        const int ld = ax ? ldx : ldy;
+        const float bhi = (float)(ax ? ny : nx), zhi = (float)nz;
+        const float bmid = R.bmid, bsl = R.bslope;
+        const uint64_t zsl8 = 8ull * (uint64_t)zsl;
+        const uint64_t b23 = __float_as_uint(kFloor2p23);
+        const uint64_t lbase = reinterpret_cast<uint64_t>(L) + 8ull * (uint64_t)ld - 8ull * (b23 + 1ull) -
+                               zsl8 * (b23 + 1ull);
+        const float fz_lo = (float)(r_lo - 1), fz_hi = (float)(r_hi - 1);
+        const float2 zs2 = make_float2(zsa, zsb), zm2 = make_float2(zma, zmb);
+        const float2 m1 = make_float2(-1.f, -1.f);
+        const float2 Kz2 = make_float2(kFloorK0, kFloorK0);
+        float tf = (float)wlo - tmid;
+        for (int t0 = wlo; t0 <= whi; t0 += chunk) {
+            const int t1 = min(whi, t0 + chunk - 1);
+            const uint64_t cb = lbase + 8ull * (uint64_t)t0 * (uint64_t)ld;
+            float Kb = kFloorK0;                             // b + (t - t0) ld
+            const float dKb = (float)ld;
+            constexpr int NB = kJ3PairBatch;
+            int t = t0;
+            for (; t1 - t >= NB - 1; t += NB) {
+                uint64_t ada[NB], adb[NB];
+                float wbq[NB];
+                float2 wzq[NB];
+                bool ina[NB], inb[NB];
+                float2 p0a[NB], p1a[NB], p0b[NB], p1b[NB];
+#pragma unroll
+                for (int q = 0; q < NB; ++q) {
+                    // in-plane coordinate (shared): the same operations as the b half of the
+                    // single-ray kernel's (z, b) pair
+                    const float qb = fmaf(bsl, tf, bmid);
+                    const float pb = fminf(fmaxf(qb, -1.f), bhi);
+                    const float sb = __fadd_rd(pb, Kb);
+                    const float flb = fmaf(Kb, -1.f, sb);
+                    wbq[q] = fmaf(flb, -1.f, pb);
+                    // the two rays' z coordinates as one pair
+                    const float2 qz = __ffma2_rn(zs2, make_float2(tf, tf), zm2);
+                    const float2 pz = make_float2(fminf(fmaxf(qz.x, -1.f), zhi), fminf(fmaxf(qz.y, -1.f), zhi));
+                    const float2 sz = __fadd2_rd(pz, Kz2);
+                    const float2 flz = __ffma2_rn(Kz2, m1, sz);
+                    wzq[q] = __ffma2_rn(flz, m1, pz);
+                    const uint64_t base = cb + 8ull * __float_as_uint(sb);
+                    ada[q] = base + zsl8 * __float_as_uint(sz.x);
+                    adb[q] = base + zsl8 * __float_as_uint(sz.y);
+                    const int tq = t + q;
+                    ina[q] = tq >= loa && tq <= hia && (!SLAB || (flz.x >= fz_lo && flz.x < fz_hi));
+                    inb[q] = tq >= lob && tq <= hib && (!SLAB || (flz.y >= fz_lo && flz.y < fz_hi));
+                    tf += 1.f;
+                    Kb += dKb;
+                }
+#pragma unroll
+                for (int q = 0; q < NB; ++q) {
+                    p0a[q] = __ldg(reinterpret_cast<const float2 *>(ada[q]));
+                    p1a[q] = __ldg(reinterpret_cast<const float2 *>(ada[q] + zsl8));
+                    p0b[q] = __ldg(reinterpret_cast<const float2 *>(adb[q]));
+                    p1b[q] = __ldg(reinterpret_cast<const float2 *>(adb[q] + zsl8));
+                }
+#pragma unroll
+                for (int q = 0; q < NB; ++q) {
+                    const float a0 = fmaf(wbq[q], p0a[q].y - p0a[q].x, p0a[q].x);
+                    const float a1 = fmaf(wbq[q], p1a[q].y - p1a[q].x, p1a[q].x);
+                    acca += ina[q] ? fmaf(wzq[q].x, a1 - a0, a0) : 0.f;
+                    anya |= ina[q];
+                    const float b0 = fmaf(wbq[q], p0b[q].y - p0b[q].x, p0b[q].x);
+                    const float b1 = fmaf(wbq[q], p1b[q].y - p1b[q].x, p1b[q].x);
+                    accb += inb[q] ? fmaf(wzq[q].y, b1 - b0, b0) : 0.f;
+                    anyb |= inb[q];
+                }
+            }
+            for (; t <= t1; ++t) {
+                const float qb = fmaf(bsl, tf, bmid);
+                const float pb = fminf(fmaxf(qb, -1.f), bhi);
+                const float sb = __fadd_rd(pb, Kb);
+                const float flb = fmaf(Kb, -1.f, sb);
+                const float wb = fmaf(flb, -1.f, pb);
+                const float2 qz = __ffma2_rn(zs2, make_float2(tf, tf), zm2);
+                const float2 pz = make_float2(fminf(fmaxf(qz.x, -1.f), zhi), fminf(fmaxf(qz.y, -1.f), zhi));
+                const float2 sz = __fadd2_rd(pz, Kz2);
+                const float2 flz = __ffma2_rn(Kz2, m1, sz);
+                const float2 wz = __ffma2_rn(flz, m1, pz);
+                const uint64_t base = cb + 8ull * __float_as_uint(sb);
+                const uint64_t a_ = base + zsl8 * __float_as_uint(sz.x);
+                const uint64_t b_ = base + zsl8 * __float_as_uint(sz.y);
+                const float2 q0a = __ldg(reinterpret_cast<const float2 *>(a_));
+                const float2 q1a = __ldg(reinterpret_cast<const float2 *>(a_ + zsl8));
+                const float2 q0b = __ldg(reinterpret_cast<const float2 *>(b_));
+                const float2 q1b = __ldg(reinterpret_cast<const float2 *>(b_ + zsl8));
+                const bool ia = t >= loa && t <= hia && (!SLAB || (flz.x >= fz_lo && flz.x < fz_hi));
+                const bool ib = t >= lob && t <= hib && (!SLAB || (flz.y >= fz_lo && flz.y < fz_hi));
+                const float a0 = fmaf(wb, q0a.y - q0a.x, q0a.x);
+                const float a1 = fmaf(wb, q1a.y - q1a.x, q1a.x);
+                acca += ia ? fmaf(wz.x, a1 - a0, a0) : 0.f;
+                anya |= ia;
+                const float b0 = fmaf(wb, q0b.y - q0b.x, q0b.x);
+                const float b1 = fmaf(wb, q1b.y - q1b.x, q1b.x);
+                accb += ib ? fmaf(wz.y, b1 - b0, b0) : 0.f;
+                anyb |= ib;
+                tf += 1.f;
+                Kb += dKb;
+            }
+        }
+    }
+    float wa = (float)h * sqrtf(R.dxy2 + zsa * zsa), wbw = (float)h * sqrtf(R.dxy2 + zsb * zsb);
+    // rays driven along z (FP64 per sample; rare): as in the single-ray kernel
+    for (int r = 0; r < 2; ++r) {
+        const bool ok = r == 0 ? (va_ok && zda) : (vb_ok && zdb);
+        if (!ok) continue;
+        const int iv = r == 0 ? iva : ivb;
+        const Ray3D q = setup_ray3d(R, iv, ndv, pitch_v, h, nx, ny, nz);
+        const double zt = 0.5 * (nz - 1);
+        const float xhi = (float)nx, yhi = (float)ny;
+        const int zlo = max(q.lo, r_lo - 1), zhi2 = min(q.hi, r_hi - 2);
+        float acc = 0.f;
+        bool any = false;
+        for (int t = zlo; t <= zhi2; ++t) {
+            const double tfd = t - zt;
+            const float pxf = fminf(fmaxf((float)(q.xmid + q.xs * tfd), -1.f), xhi);
+            const float pyf = fminf(fmaxf((float)(q.ymid + q.ys * tfd), -1.f), yhi);
+            const float fx = floorf(pxf), fy = floorf(pyf);
+            const float wx = pxf - fx, wy = pyf - fy;
+            const float2 *row = py + (int64_t)(t + 1) * zsy + (int64_t)((int)fy + 1) * ldy + (int)fx + 1;
+            const float2 p0 = __ldg(row), p1 = __ldg(row + ldy);
+            const float a0 = fmaf(wx, p0.y - p0.x, p0.x);
+            const float a1 = fmaf(wx, p1.y - p1.x, p1.x);
+            acc += fmaf(wy, a1 - a0, a0);
+            any = true;
+        }
+        if (r == 0) { acca = acc; anya = any; wa = q.weight; }
+        else { accb = acc; anyb = any; wbw = q.weight; }
+    }
+    if (va_ok) {
+        float *out = y + (int64_t)view * y_view_ld + (int64_t)iva * y_ld + y_off + iu;
+        if (!accumulate) *out = acca * wa;
+        else if (anya) *out += acca * wa;
+    }
+    if (vb_ok) {
+        float *out = y + (int64_t)view * y_view_ld + (int64_t)ivb * y_ld + y_off + iu;
+        if (!accumulate) *out = accb * wbw;
+        else if (anyb) *out += accb * wbw;
+    }
+}
+
 // Total number of Joseph samples of the geometry (sum of the clipped plane ranges), for the
 // projector's work count.
 __global__ void joseph3d_count_kernel(const RayXY *__restrict__ rxy, int ndu, int ndv,
@@ -341,6 +543,23 @@ cudaError_t launch_joseph3d(const ct_geom *g, float *y, int64_t y_view_ld, int y
             if (iv_hi < iv_lo) continue;
         }
         const int vb = (d.tune_a_views >= 1 && d.tune_a_views <= 8) ? d.tune_a_views : 8;
+        if (d.tune_a_rays == 2) {
+            // two detector rows per thread: blocks of 32 columns x 2 vb rows
+            dim3 block(32, vb), grid((d.ndu + 31) / 32, d.n_views, (iv_hi - iv_lo + 2 * vb) / (2 * vb));
+            if (n_slabs > 1)
+                joseph3d_pair_kernel<true><<<grid, block, 0, s>>>(
+                    d.rays_xy, d.ndu, d.ndv, (double)g->desc.pitch_v, h, g->pcol_dev, d.slice_x,
+                    d.col_pairs_ld, g->prow_dev, d.slice_y, d.row_pairs_ld, chunk, d.nx, d.ny, d.nz,
+                    y, y_view_ld, y_ld, y_off, iv_lo, iv_hi, r_lo, r_hi, 1, stop);
+            else
+                joseph3d_pair_kernel<false><<<grid, block, 0, s>>>(
+                    d.rays_xy, d.ndu, d.ndv, (double)g->desc.pitch_v, h, g->pcol_dev, d.slice_x,
+                    d.col_pairs_ld, g->prow_dev, d.slice_y, d.row_pairs_ld, chunk, d.nx, d.ny, d.nz,
+                    y, y_view_ld, y_ld, y_off, iv_lo, iv_hi, r_lo, r_hi, 0, stop);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            continue;
+        }
         dim3 block(32, vb), grid((d.ndu + 31) / 32, d.n_views, (iv_hi - iv_lo + vb) / vb);
         if (n_slabs > 1)
             joseph3d_kernel<true><<<grid, block, 0, s>>>(

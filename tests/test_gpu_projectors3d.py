@@ -130,8 +130,9 @@ def test_autotuned_slab_thickness_keeps_the_result():
     G = gpu_geom(g)
     y_default = gpu_A(G, x)
     sh = ct_geom_autotune(G)
-    assert (sh["a_slab"], sh["a_views"]) in ((16, 1), (16, 4), (16, 8), (64, 4), (64, 8),
-                                             (1 << 20, 1), (1 << 20, 4), (1 << 20, 8))
+    assert (sh["a_slab"], sh["a_views"], sh["a_rays"]) in (
+        (16, 1, 1), (16, 4, 1), (16, 8, 1), (64, 4, 1), (64, 8, 1), (1 << 20, 1, 1),
+        (1 << 20, 4, 1), (1 << 20, 8, 1), (16, 4, 2), (64, 4, 2), (1 << 20, 2, 2), (1 << 20, 4, 2))
     y_tuned = gpu_A(G, x)
     assert rel(y_tuned, y_default) <= 1e-6
     assert rel(y_tuned, OP.forward(g, x).reshape(-1)) <= TOL
@@ -168,3 +169,29 @@ def test_cone64_k100_iterates_match_oracle():
     print(f"cone 64^3 K=100: FP32 basis {err32:.2e}, BF16 basis {err16:.2e} vs FP64")
     assert err32 <= 1e-4, err32
     assert err16 <= 2e-2, err16
+
+
+@pytest.mark.parametrize("name", sorted(GEOMS))
+def test_two_rays_per_thread_is_bitwise_the_single_ray_kernel(name):
+    """The cone Joseph kernel with two detector rows per thread (shared in-plane coordinate)
+    performs each ray's operations in the same order as the one-ray kernel: A agrees bit for
+    bit across rays per thread, warp rows per block and z-slab thickness, including rays
+    driven along z, ragged volumes and odd detector row counts."""
+    from paper_2602_17892_gb300 import ct_geom_get_launch_shapes, ct_geom_set_launch_shapes
+    g = GEOMS[name]
+    x = _volume(g, 6)
+    G = gpu_geom(g)
+    base = ct_geom_get_launch_shapes(G)
+    yo = OP.forward(g, x).reshape(-1)
+    one_pass = None
+    for slab in (1 << 20, 16, 3):
+        ref = None                        # slabs add per-slab partial sums: one order per slab
+        for views, rays in ((1, 1), (4, 1), (8, 1), (1, 2), (2, 2), (4, 2), (8, 2)):
+            ct_geom_set_launch_shapes(G, dict(base, a_slab=slab, a_views=views, a_rays=rays))
+            y = gpu_A(G, x)
+            if ref is None:
+                ref = y
+                assert rel(y, yo) <= TOL
+                one_pass = y if one_pass is None else one_pass
+                assert rel(y, one_pass) <= 1e-6
+            assert np.array_equal(y, ref), (slab, views, rays)

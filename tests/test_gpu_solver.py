@@ -309,18 +309,27 @@ def test_fan512_dp_full_size_matches_oracle(method):
             assert errs[basis] <= tol, errs
 
 
-@pytest.mark.parametrize("basis", ["f16", "bf16"])
 @pytest.mark.parametrize("method", ["ab", "ba"])
-def test_low_precision_basis_small(method, basis):
+def test_low_precision_basis_small(method):
+    """16-bit bases on the ragged fan problem (20 its, DP) against the FP64 oracle.  The
+    error of a 16-bit basis scales with its unit roundoff (FP16 2^-11, BF16 2^-9): the BF16
+    error may be at most 16x the FP16 error of the same solve (4x the ratio of the two
+    roundoffs), which a wrong conversion or a wrong row in the BF16 path would exceed; BA with
+    BF16, which loses the reconstruction on the 512^2 problem, is held to that bound and to
+    0.1 here."""
     g = synth.fanflat2d(45, 60, 70, 150.0, 240.0, ny=38)
     x_true, b, e = problem(g, 5, 0.02, 77)
     noise = np.linalg.norm(e) if method == "ab" else np.linalg.norm(OP.back_pixel(g, e))
     G = gpu_geom(g)
-    xg, info = _gpu_solve(method, G, b, 20, "dp", noise_norm=noise, tau=1.01, basis=basis)
     ref = _oracle(method, g, b, 20, "dp", dp_target=1.01 * noise)
-    err = rel(xg, ref["x"])
-    tol = BASIS_TOL[method][basis]
-    assert np.isfinite(err) and (tol is None or err <= tol), err
+    err = {}
+    for basis in ("f16", "bf16"):
+        xg, info = _gpu_solve(method, G, b, 20, "dp", noise_norm=noise, tau=1.01, basis=basis)
+        err[basis] = rel(xg, ref["x"])
+        tol = BASIS_TOL[method][basis]
+        assert np.isfinite(err[basis]) and (tol is None or err[basis] <= tol), err
+    assert err["bf16"] <= 16 * err["f16"], err
+    assert err["bf16"] <= 0.1, err
 
 
 @pytest.mark.parametrize("method", ["ab", "ba"])
