@@ -6,12 +6,11 @@
 //   P_x[z+1][x+1][y+1] = (x[z][y][x], x[z][y+1][x]) for z in [-1, nz+1], x in [-1, M+1], y in [-1, ny]
 //   P_y[z+1][y+1][x+1] = (x[z][y][x], x[z][y][x+1]) for z in [-1, nz+1], y in [-1, M+1], x in [-1, nx]
 // with M = max(nx, ny) (zero outside the volume; rows of ld >= n + 2 pairs, one z slice after
-// the other).  A
-// Joseph sample is two 8-byte loads (the two z rows of its 2 x 2 taps) with no bounds test:
-// rays driven along x read P_x, along y P_y, and the rare rays driven along z read P_y (two y
-// rows of one slice).  Tap positions are clamped to [-1, n]: a sample outside the volume then
-// reads only zero padding and adds exactly zero, so a ray's plane range only has to contain
-// its samples inside the volume (it is computed in FP32 with a margin).
+// the other).  A Joseph sample is two 8-byte loads (the two z rows of its 2 x 2 taps) with no
+// bounds test: rays driven along x read P_x, along y P_y, and the rare rays driven along z read
+// P_y (two y rows of one slice).  (Quads holding both z rows in one 16-byte load were measured
+// slower: they store every voxel twice, and two rays of neighbouring detector rows then no
+// longer share the z row between them in L1 - L1 hit rate 46 % -> 10 %, DRAM reads x4.6.)
 // z is the slowest index so that consecutive samples of a ray (one step along x or y) are one
 // row apart in memory: a ray stays within a few pages while it crosses the volume, and a z slab
 // of rows is one contiguous block.
@@ -261,13 +260,52 @@ __global__ void __launch_bounds__(256, 3) joseph3d_kernel(
 
 // The same projector with two rays per thread: detector rows iv and iv + 1 of one column iu.
 // Their x-y projections coincide (the fan ray of the column), so at every driving plane they
-// share the in-plane tap position, its floor, weight and address part; only z differs.  The
-// per-ray arithmetic is the single-ray kernel's, operation for operation (the in-plane
-// coordinate in scalar FP32, the two rays' z coordinates as one f32x2 pair, the sums in plane
-// order), so the results are bitwise those of joseph3d_kernel.  Planes go in batches of
-// kJ3PairBatch (4 gathers per plane in flight).
+// share the in-plane tap position, its floor, weight and address part; only z differs (the two
+// z coordinates run as one f32x2 pair).  Each ray's plane range is made exact for the
+// loop's own FP32 arithmetic: the planes whose z = fma(zslope, t - tmid, zmid) lies in
+// [-1, nz] (monotone in t, so an interval, found from an FP32 estimate and checked at its ends).
+// Inside that range a sample's taps are slices floor(z) + 1 .. floor(z) + 2 in [0, nz + 2] and
+// its in-plane pair index is in [-1, n + 1] (the host range keeps b in [-1, n] up to FP32
+// rounding; index -1 is the previous row's zero tail), so no position needs a clamp; lanes
+// outside their own range skip the loads.  The samples this leaves out are those whose taps
+// all lie in the zero margins, which the one-ray kernel adds as exact zeros: the sums, taken in
+// the same order with the same operations, are bitwise those of joseph3d_kernel.  Planes go in
+// batches of kJ3PairBatch (four gathers per plane).
 constexpr int kJ3PairBatch = 2;
 
+// planes of [lo, hi] whose FP32 z lies in [-1, zhi] (lo > hi when there is none)
+__device__ __forceinline__ void exact_z_range(float zs, float zm, float tmid, float zhi, int &lo,
+                                              int &hi)
+{
+    auto zin = [&](int t) {
+        const float z = fmaf(zs, (float)t - tmid, zm);
+        return z >= -1.f && z <= zhi;
+    };
+    if (lo > hi) return;
+    if (zs == 0.f) {
+        if (!zin(lo)) hi = lo - 1;
+        return;
+    }
+    // the crossings of z = -1 and z = zhi in FP32 (within a plane of the exact ones), widened by
+    // two planes and clipped to [lo, hi]; then the ends are stepped inwards to the first planes
+    // inside (at most eight steps; with none found the range is empty)
+    const float r = __frcp_rn(zs);
+    const float ta = tmid + (-1.f - zm) * r, tb = tmid + (zhi - zm) * r;
+    const float flo = fmaxf((float)lo, fminf((float)hi, floorf(fminf(ta, tb)) - 2.f));
+    const float fhi = fmaxf((float)lo, fminf((float)hi, ceilf(fmaxf(ta, tb)) + 2.f));
+    int a = (int)flo, b = (int)fhi;
+    for (int i = 0; i < 8 && a <= b && !zin(a); ++i) ++a;
+    for (int i = 0; i < 8 && b >= a && !zin(b); --b, ++i) {}
+    if (a > b || !zin(a) || !zin(b)) {
+        hi = lo - 1;
+        return;
+    }
+    lo = a;
+    hi = b;
+}
+
+// planes whose z can fall in a slab's tap rows [r_lo - 2, r_hi] (FP32, two planes of margin;
+// a superset: membership is decided per sample)
 __device__ __forceinline__ void ray_z_range(float zs, float tmid, float zm, int r_lo, int r_hi,
                                             int &lo, int &hi)
 {
@@ -307,12 +345,21 @@ __global__ void __launch_bounds__(256, 3) joseph3d_pair_kernel(
     const double zsa_d = va * R.rda, zsb_d = vb * R.rda;
     const float zsa = (float)zsa_d, zma = (float)(0.5 * (nz - 1) - R.sa_h * zsa_d);
     const float zsb = (float)zsb_d, zmb = (float)(0.5 * (nz - 1) - R.sa_h * zsb_d);
+    const float zhi = (float)nz;
     float acca = 0.f, accb = 0.f;
     bool anya = false, anyb = false;
     const int lo0 = R.packed & 0x7fff, hi0 = (R.packed >> 15) & 0x7fff;
     int loa = lo0, hia = hi0, lob = lo0, hib = hi0;
-    if (!va_ok || zda) { loa = 1; hia = 0; } else ray_z_range(zsa, tmid, zma, r_lo, r_hi, loa, hia);
-    if (!vb_ok || zdb) { lob = 1; hib = 0; } else ray_z_range(zsb, tmid, zmb, r_lo, r_hi, lob, hib);
+    if (!va_ok || zda) { loa = 1; hia = 0; }
+    else {
+        exact_z_range(zsa, zma, tmid, zhi, loa, hia);
+        if (SLAB) ray_z_range(zsa, tmid, zma, r_lo, r_hi, loa, hia);
+    }
+    if (!vb_ok || zdb) { lob = 1; hib = 0; }
+    else {
+        exact_z_range(zsb, zmb, tmid, zhi, lob, hib);
+        if (SLAB) ray_z_range(zsb, tmid, zmb, r_lo, r_hi, lob, hib);
+    }
     const int tlo = min(hia >= loa ? loa : 0x7fffffff, hib >= lob ? lob : 0x7fffffff);
     const int thi = max(hia >= loa ? hia : -1, hib >= lob ? hib : -1);
     const int wlo = __reduce_min_sync(0xffffffffu, tlo);
@@ -321,16 +368,20 @@ __global__ void __launch_bounds__(256, 3) joseph3d_pair_kernel(
         const float2 *L = ax ? px : py;
         const int64_t zsl = ax ? zsx : zsy;
         const int ld = ax ? ldx : ldy;
-        const float bhi = (float)(ax ? ny : nx), zhi = (float)nz;
         const float bmid = R.bmid, bsl = R.bslope;
-        const uint64_t zsl8 = 8ull * (uint64_t)zsl;
+        const uint32_t zsl8 = 8u * (uint32_t)zsl;           // < 2^32: checked by the launcher
+        const uint64_t zsl8w = zsl8;
         const uint64_t b23 = __float_as_uint(kFloor2p23);
         const uint64_t lbase = reinterpret_cast<uint64_t>(L) + 8ull * (uint64_t)ld - 8ull * (b23 + 1ull) -
-                               zsl8 * (b23 + 1ull);
+                               zsl8w * (b23 + 1ull);
         const float fz_lo = (float)(r_lo - 1), fz_hi = (float)(r_hi - 1);
         const float2 zs2 = make_float2(zsa, zsb), zm2 = make_float2(zma, zmb);
         const float2 m1 = make_float2(-1.f, -1.f);
         const float2 Kz2 = make_float2(kFloorK0, kFloorK0);
+        // a ray's planes [lo, hi] as an unsigned window: t in range iff (t - lo) <= (hi - lo)
+        const uint32_t wa = hia >= loa ? (uint32_t)(hia - loa) : 0u;
+        const uint32_t wb_ = hib >= lob ? (uint32_t)(hib - lob) : 0u;
+        const int la = hia >= loa ? loa : 0x3fffffff, lb = hib >= lob ? lob : 0x3fffffff;
         float tf = (float)wlo - tmid;
         for (int t0 = wlo; t0 <= whi; t0 += chunk) {
             const int t1 = min(whi, t0 + chunk - 1);
@@ -347,81 +398,88 @@ __global__ void __launch_bounds__(256, 3) joseph3d_pair_kernel(
                 float2 p0a[NB], p1a[NB], p0b[NB], p1b[NB];
 #pragma unroll
                 for (int q = 0; q < NB; ++q) {
-                    // in-plane coordinate (shared): the same operations as the b half of the
-                    // single-ray kernel's (z, b) pair
-                    const float qb = fmaf(bsl, tf, bmid);
-                    const float pb = fminf(fmaxf(qb, -1.f), bhi);
+                    // in-plane coordinate (shared): the b half of the one-ray kernel's (z, b)
+                    // pair, without its clamp
+                    const float pb = fmaf(bsl, tf, bmid);
                     const float sb = __fadd_rd(pb, Kb);
                     const float flb = fmaf(Kb, -1.f, sb);
                     wbq[q] = fmaf(flb, -1.f, pb);
-                    // the two rays' z coordinates as one pair
-                    const float2 qz = __ffma2_rn(zs2, make_float2(tf, tf), zm2);
-                    const float2 pz = make_float2(fminf(fmaxf(qz.x, -1.f), zhi), fminf(fmaxf(qz.y, -1.f), zhi));
+                    const float2 pz = __ffma2_rn(zs2, make_float2(tf, tf), zm2);
                     const float2 sz = __fadd2_rd(pz, Kz2);
                     const float2 flz = __ffma2_rn(Kz2, m1, sz);
                     wzq[q] = __ffma2_rn(flz, m1, pz);
-                    const uint64_t base = cb + 8ull * __float_as_uint(sb);
-                    ada[q] = base + zsl8 * __float_as_uint(sz.x);
-                    adb[q] = base + zsl8 * __float_as_uint(sz.y);
+                    const uint64_t base = cb + 8ull * (uint64_t)__float_as_uint(sb);
+                    ada[q] = base + (uint64_t)zsl8 * __float_as_uint(sz.x);
+                    adb[q] = base + (uint64_t)zsl8 * __float_as_uint(sz.y);
                     const int tq = t + q;
-                    ina[q] = tq >= loa && tq <= hia && (!SLAB || (flz.x >= fz_lo && flz.x < fz_hi));
-                    inb[q] = tq >= lob && tq <= hib && (!SLAB || (flz.y >= fz_lo && flz.y < fz_hi));
+                    ina[q] = (uint32_t)(tq - la) <= wa && (!SLAB || (flz.x >= fz_lo && flz.x < fz_hi));
+                    inb[q] = (uint32_t)(tq - lb) <= wb_ && (!SLAB || (flz.y >= fz_lo && flz.y < fz_hi));
                     tf += 1.f;
                     Kb += dKb;
                 }
 #pragma unroll
                 for (int q = 0; q < NB; ++q) {
-                    p0a[q] = __ldg(reinterpret_cast<const float2 *>(ada[q]));
-                    p1a[q] = __ldg(reinterpret_cast<const float2 *>(ada[q] + zsl8));
-                    p0b[q] = __ldg(reinterpret_cast<const float2 *>(adb[q]));
-                    p1b[q] = __ldg(reinterpret_cast<const float2 *>(adb[q] + zsl8));
+                    if (ina[q]) {
+                        p0a[q] = __ldg(reinterpret_cast<const float2 *>(ada[q]));
+                        p1a[q] = __ldg(reinterpret_cast<const float2 *>(ada[q] + zsl8w));
+                    }
+                    if (inb[q]) {
+                        p0b[q] = __ldg(reinterpret_cast<const float2 *>(adb[q]));
+                        p1b[q] = __ldg(reinterpret_cast<const float2 *>(adb[q] + zsl8w));
+                    }
                 }
 #pragma unroll
                 for (int q = 0; q < NB; ++q) {
-                    const float a0 = fmaf(wbq[q], p0a[q].y - p0a[q].x, p0a[q].x);
-                    const float a1 = fmaf(wbq[q], p1a[q].y - p1a[q].x, p1a[q].x);
-                    acca += ina[q] ? fmaf(wzq[q].x, a1 - a0, a0) : 0.f;
-                    anya |= ina[q];
-                    const float b0 = fmaf(wbq[q], p0b[q].y - p0b[q].x, p0b[q].x);
-                    const float b1 = fmaf(wbq[q], p1b[q].y - p1b[q].x, p1b[q].x);
-                    accb += inb[q] ? fmaf(wzq[q].y, b1 - b0, b0) : 0.f;
-                    anyb |= inb[q];
+                    if (ina[q]) {
+                        const float a0 = fmaf(wbq[q], p0a[q].y - p0a[q].x, p0a[q].x);
+                        const float a1 = fmaf(wbq[q], p1a[q].y - p1a[q].x, p1a[q].x);
+                        acca += fmaf(wzq[q].x, a1 - a0, a0);
+                        if (SLAB) anya = true;
+                    }
+                    if (inb[q]) {
+                        const float b0 = fmaf(wbq[q], p0b[q].y - p0b[q].x, p0b[q].x);
+                        const float b1 = fmaf(wbq[q], p1b[q].y - p1b[q].x, p1b[q].x);
+                        accb += fmaf(wzq[q].y, b1 - b0, b0);
+                        if (SLAB) anyb = true;
+                    }
                 }
             }
             for (; t <= t1; ++t) {
-                const float qb = fmaf(bsl, tf, bmid);
-                const float pb = fminf(fmaxf(qb, -1.f), bhi);
+                const float pb = fmaf(bsl, tf, bmid);
                 const float sb = __fadd_rd(pb, Kb);
                 const float flb = fmaf(Kb, -1.f, sb);
                 const float wb = fmaf(flb, -1.f, pb);
-                const float2 qz = __ffma2_rn(zs2, make_float2(tf, tf), zm2);
-                const float2 pz = make_float2(fminf(fmaxf(qz.x, -1.f), zhi), fminf(fmaxf(qz.y, -1.f), zhi));
+                const float2 pz = __ffma2_rn(zs2, make_float2(tf, tf), zm2);
                 const float2 sz = __fadd2_rd(pz, Kz2);
                 const float2 flz = __ffma2_rn(Kz2, m1, sz);
                 const float2 wz = __ffma2_rn(flz, m1, pz);
-                const uint64_t base = cb + 8ull * __float_as_uint(sb);
-                const uint64_t a_ = base + zsl8 * __float_as_uint(sz.x);
-                const uint64_t b_ = base + zsl8 * __float_as_uint(sz.y);
-                const float2 q0a = __ldg(reinterpret_cast<const float2 *>(a_));
-                const float2 q1a = __ldg(reinterpret_cast<const float2 *>(a_ + zsl8));
-                const float2 q0b = __ldg(reinterpret_cast<const float2 *>(b_));
-                const float2 q1b = __ldg(reinterpret_cast<const float2 *>(b_ + zsl8));
-                const bool ia = t >= loa && t <= hia && (!SLAB || (flz.x >= fz_lo && flz.x < fz_hi));
-                const bool ib = t >= lob && t <= hib && (!SLAB || (flz.y >= fz_lo && flz.y < fz_hi));
-                const float a0 = fmaf(wb, q0a.y - q0a.x, q0a.x);
-                const float a1 = fmaf(wb, q1a.y - q1a.x, q1a.x);
-                acca += ia ? fmaf(wz.x, a1 - a0, a0) : 0.f;
-                anya |= ia;
-                const float b0 = fmaf(wb, q0b.y - q0b.x, q0b.x);
-                const float b1 = fmaf(wb, q1b.y - q1b.x, q1b.x);
-                accb += ib ? fmaf(wz.y, b1 - b0, b0) : 0.f;
-                anyb |= ib;
+                const uint64_t base = cb + 8ull * (uint64_t)__float_as_uint(sb);
+                const bool ia = (uint32_t)(t - la) <= wa && (!SLAB || (flz.x >= fz_lo && flz.x < fz_hi));
+                const bool ib = (uint32_t)(t - lb) <= wb_ && (!SLAB || (flz.y >= fz_lo && flz.y < fz_hi));
+                if (ia) {
+                    const uint64_t a_ = base + (uint64_t)zsl8 * __float_as_uint(sz.x);
+                    const float2 q0a = __ldg(reinterpret_cast<const float2 *>(a_));
+                    const float2 q1a = __ldg(reinterpret_cast<const float2 *>(a_ + zsl8w));
+                    const float a0 = fmaf(wb, q0a.y - q0a.x, q0a.x);
+                    const float a1 = fmaf(wb, q1a.y - q1a.x, q1a.x);
+                    acca += fmaf(wz.x, a1 - a0, a0);
+                    if (SLAB) anya = true;
+                }
+                if (ib) {
+                    const uint64_t b_ = base + (uint64_t)zsl8 * __float_as_uint(sz.y);
+                    const float2 q0b = __ldg(reinterpret_cast<const float2 *>(b_));
+                    const float2 q1b = __ldg(reinterpret_cast<const float2 *>(b_ + zsl8w));
+                    const float b0 = fmaf(wb, q0b.y - q0b.x, q0b.x);
+                    const float b1 = fmaf(wb, q1b.y - q1b.x, q1b.x);
+                    accb += fmaf(wz.y, b1 - b0, b0);
+                    if (SLAB) anyb = true;
+                }
                 tf += 1.f;
                 Kb += dKb;
             }
         }
     }
-    float wa = (float)h * sqrtf(R.dxy2 + zsa * zsa), wbw = (float)h * sqrtf(R.dxy2 + zsb * zsb);
+    float wa_ = (float)h * sqrtf(R.dxy2 + zsa * zsa), wbw = (float)h * sqrtf(R.dxy2 + zsb * zsb);
     // rays driven along z (FP64 per sample; rare): as in the single-ray kernel
     for (int r = 0; r < 2; ++r) {
         const bool ok = r == 0 ? (va_ok && zda) : (vb_ok && zdb);
@@ -446,13 +504,13 @@ __global__ void __launch_bounds__(256, 3) joseph3d_pair_kernel(
             acc += fmaf(wy, a1 - a0, a0);
             any = true;
         }
-        if (r == 0) { acca = acc; anya = any; wa = q.weight; }
+        if (r == 0) { acca = acc; anya = any; wa_ = q.weight; }
         else { accb = acc; anyb = any; wbw = q.weight; }
     }
     if (va_ok) {
         float *out = y + (int64_t)view * y_view_ld + (int64_t)iva * y_ld + y_off + iu;
-        if (!accumulate) *out = acca * wa;
-        else if (anya) *out += acca * wa;
+        if (!accumulate) *out = acca * wa_;
+        else if (anya) *out += acca * wa_;
     }
     if (vb_ok) {
         float *out = y + (int64_t)view * y_view_ld + (int64_t)ivb * y_ld + y_off + iu;
@@ -543,7 +601,8 @@ cudaError_t launch_joseph3d(const ct_geom *g, float *y, int64_t y_view_ld, int y
             if (iv_hi < iv_lo) continue;
         }
         const int vb = (d.tune_a_views >= 1 && d.tune_a_views <= 8) ? d.tune_a_views : 8;
-        if (d.tune_a_rays == 2) {
+        // the two-ray kernel forms slice offsets as 32-bit products: 8 pairs-per-slice < 2^32
+        if (d.tune_a_rays == 2 && 8ull * (uint64_t)std::max(d.slice_x, d.slice_y) < (1ull << 32)) {
             // two detector rows per thread: blocks of 32 columns x 2 vb rows
             dim3 block(32, vb), grid((d.ndu + 31) / 32, d.n_views, (iv_hi - iv_lo + 2 * vb) / (2 * vb));
             if (n_slabs > 1)

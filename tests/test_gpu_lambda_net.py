@@ -271,11 +271,14 @@ def test_learned_rule_evaluates_the_network_and_falls_back_to_gcv():
 def test_trained_network_beats_gcv_on_held_out_problems():
     """The committed network, trained by the library's own kernels on solves that the library
     generated, against GCV on problems outside its training seeds: smaller mean reconstruction
-    error, never a GCV fallback."""
+    error, never a GCV fallback, and per problem no worse than GCV's error + 2 % (relative) on
+    at least three quarters of the held-out problems."""
     from paper_2602_17892_gb300.lambda_net import compare_rules, load_params
     P, meta = load_params()
     seeds = np.arange(20_000_000, 20_000_000 + 12)
     r = compare_rules(P, seeds)
-    learned, gcv = np.mean(r["learned"]), np.mean(r["gcv"])
+    learned, gcv = np.asarray(r["learned"]), np.asarray(r["gcv"])
     assert r["fallback_steps"] == 0
-    assert learned < gcv, (learned, gcv, r)
+    assert learned.mean() < gcv.mean(), (learned, gcv, r)
+    ok = int(np.sum(learned <= 1.02 * gcv))
+    assert ok >= int(np.ceil(0.75 * len(seeds))), (ok, learned / gcv)
