@@ -257,7 +257,9 @@ static void ray_setup(const ct_geom_desc *d, int view, int bin, double p0[2], do
     }
 }
 
-static Ray2D make_ray(const ct_geom_desc *d, int view, int bin)
+// The ray's table entry (FP64 geometry, stored as described at Ray2D) and its number of samples
+// (the driving lines whose tap index lies in [-1, n_other), for the projector's work count).
+static Ray2D make_ray(const ct_geom_desc *d, int view, int bin, int64_t *samples)
 {
     double p0[2], dir[2];
     ray_setup(d, view, bin, p0, dir);
@@ -278,7 +280,6 @@ static Ray2D make_ray(const ct_geom_desc *d, int view, int bin)
     double slope = a_other / a_drive;
     double tmid = (n_drive - 1) / 2.0;
     int lo = 0, hi = n_drive - 1;
-    // keep the samples whose tap index lies in [-1, n_other)
     if (fabs(slope) < 1e-300) {
         if (!(pmid >= -1.0 && pmid < n_other)) { lo = 1; hi = 0; }
     } else {
@@ -289,11 +290,11 @@ static Ray2D make_ray(const ct_geom_desc *d, int view, int bin)
         if (chi < hi) hi = (chi < lo - 1) ? lo - 1 : (int)chi;
         if (hi < lo) { lo = 1; hi = 0; }
     }
+    *samples = hi >= lo ? hi - lo + 1 : 0;
     Ray2D r;
     r.pmid = (float)pmid;
-    r.slope = (float)slope;
-    r.weight = (float)(h / fabs(a_drive));
-    r.packed = (uint32_t)lo | ((uint32_t)hi << 15) | ((uint32_t)axis << 30);
+    const double q = std::max(-1.0, std::min(1.0, slope)) * 536870912.0;   // 2^29
+    r.enc = (int32_t)(llround(q) * 2 + axis);
     return r;
 }
 
@@ -462,10 +463,9 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
         rays.resize((size_t)g->m);
         for (int v = 0; v < d->n_views; ++v)
             for (int j = 0; j < d->n_det_u; ++j) {
-                Ray2D r = make_ray(&g->desc, v, j);
-                rays[(size_t)v * d->n_det_u + j] = r;
-                int lo = r.packed & 0x7fff, hi = (r.packed >> 15) & 0x7fff;
-                if (hi >= lo) g->a_samples += hi - lo + 1;
+                int64_t ns = 0;
+                rays[(size_t)v * d->n_det_u + j] = make_ray(&g->desc, v, j, &ns);
+                g->a_samples += ns;
             }
     }
     std::vector<ViewBP> views(d->n_views);
@@ -476,8 +476,11 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
         views[v].a = (float)(d->pixel * c / d->pitch_u);
         views[v].b = (float)(d->pixel * s / d->pitch_u);
     }
-    const size_t prow_n = cone ? (size_t)(nz + 3) * dg.slice_y : (size_t)(d->ny + 2) * dg.row_pairs_ld;
-    const size_t pcol_n = cone ? (size_t)(nz + 3) * dg.slice_x : (size_t)(d->nx + 2) * dg.col_pairs_ld;
+    // 2D: lines -1 .. max(nx, ny) in both layouts (the Joseph kernel's warps may walk, for a ray
+    // driven along the shorter side, lines beyond that side: zero lines)
+    const size_t nlines = (size_t)std::max(d->nx, d->ny) + 2;
+    const size_t prow_n = cone ? (size_t)(nz + 3) * dg.slice_y : nlines * dg.row_pairs_ld;
+    const size_t pcol_n = cone ? (size_t)(nz + 3) * dg.slice_x : nlines * dg.col_pairs_ld;
     cudaError_t e = cudaSuccess;
     if (cone) {
         e = dalloc(&g->rays_xy_dev, rays_xy.size());

@@ -20,14 +20,16 @@ ct_status cuda_fail(cudaError_t e, const char *what);
     } while (0)
 
 // ----------------------------------------------------------------------------- geometry
-// One Joseph ray in index units: along the driving axis the sample at integer index t lies
-// at fractional index pos = pmid + slope * (t - (n_drive-1)/2) of the other axis.  t runs
-// over [t_lo, t_hi]; axis = 0 drives along x (columns), 1 along y (rows).
-struct __align__(16) Ray2D {
+// One Joseph ray in index units, 8 bytes: along the driving axis the sample at integer index t
+// lies at fractional index pos = pmid + slope * (t - (n_drive-1)/2) of the other axis.  The
+// slope (|slope| <= 1: the driving axis is the ray's longer component) is stored in fixed point,
+// round(slope 2^29), shifted left by one with the driving axis (0 = x, 1 = y) in bit 0.  The
+// kernels form the FP32 slope, the sample weight h sqrt(1 + slope^2) and the range of t whose
+// FP32 positions lie in [-1, n_other] themselves (decode_ray2d), so the table is half the size
+// a table of those values would be.
+struct __align__(8) Ray2D {
     float pmid;
-    float slope;
-    float weight;   // h / |d_drive|
-    uint32_t packed; // t_lo (bits 0-14) | t_hi (bits 15-29) | axis (bit 30)
+    int32_t enc;
 };
 
 // Per-view constants of the pixel-driven backprojector.

@@ -164,10 +164,10 @@ cudaError_t launch_back_proj(const ct_geom *g, const float *ypad, float *x, cons
 // (t - t0) * stride, an integer kept exactly in FP32, so the pair address is one multiply-add
 // of that bit pattern; chunks of lines keep (t - t0) * stride below 2^22.
 //
-// No clamp: within a ray's clipped range [t_lo, t_hi] its position lies in [-1, n_other] up
-// to FP32 rounding, so the pair index stays in [-1, n_other + 1], which the layouts hold as
-// zero pairs (a zero line before line 0 and at least n_other + 2 pairs per line); a lane
-// outside its own range skips the load.
+// No clamp: a sample is taken only where its FP32 position lies in [-1, n_other], so the pair
+// index floor(pos) + 1 stays in [0, n_other + 1], which the layouts hold (at least n_other + 2
+// pairs per line, zero beyond the image); lines run over [-1, max(nx, ny)] in both layouts, so
+// every line of a warp's range exists whatever axis a lane drives along.
 // Lines t in [ta, tb] of one ray, two at a time (t and t + 1): both samples' positions, floors
 // and weights in paired FP32 arithmetic (one fma.f32x2 / add.rm.f32x2 each, the same operations
 // per sample as one line at a time), accumulated in line order.  K carries (t - ta) * stride
@@ -176,7 +176,7 @@ cudaError_t launch_back_proj(const ct_geom *g, const float *ypad, float *x, cons
 // gathers in flight (with one pair per iteration the kernel waited on its gathers: 14
 // long-scoreboard stalls per issue); single pairs finish the range.
 template <int NB>
-__device__ __forceinline__ float joseph2d_span(int ta, int tb, int t_lo, int t_hi, float pmid,
+__device__ __forceinline__ float joseph2d_span(int ta, int tb, float ohi, float pmid,
                                                float slope, float tmid, int stride,
                                                uint64_t abase, float acc)
 {
@@ -192,6 +192,7 @@ __device__ __forceinline__ float joseph2d_span(int ta, int tb, int t_lo, int t_h
     for (; tb - t >= 2 * NB - 1; t += 2 * NB) {
         float2 f[NB], pa[NB], pb[NB];
         uint32_t ia[NB], ib[NB];
+        bool ina[NB], inb[NB];
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
             const float2 pos2 = __ffma2_rn(sl2, tf2, pm2);
@@ -199,35 +200,33 @@ __device__ __forceinline__ float joseph2d_span(int ta, int tb, int t_lo, int t_h
             f[q] = __ffma2_rn(__ffma2_rn(K2, m1, sk2), m1, pos2);   // pos - (sk - K)
             ia[q] = __float_as_uint(sk2.x);
             ib[q] = __float_as_uint(sk2.y);
+            ina[q] = pos2.x >= -1.f && pos2.x <= ohi;
+            inb[q] = pos2.y >= -1.f && pos2.y <= ohi;
             tf2 = __fadd2_rn(tf2, d2);
             K2 = __fadd2_rn(K2, dK2);
         }
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
-            const int tq = t + 2 * q;
             pa[q] = make_float2(0.f, 0.f);
             pb[q] = make_float2(0.f, 0.f);
-            if (tq >= t_lo && tq <= t_hi)
-                pa[q] = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * ia[q]));
-            if (tq + 1 >= t_lo && tq + 1 <= t_hi)
-                pb[q] = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * ib[q]));
+            if (ina[q]) pa[q] = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * ia[q]));
+            if (inb[q]) pb[q] = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * ib[q]));
         }
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
-            const int tq = t + 2 * q;
-            if (tq >= t_lo && tq <= t_hi) acc += fmaf(f[q].x, pa[q].y - pa[q].x, pa[q].x);
-            if (tq + 1 >= t_lo && tq + 1 <= t_hi) acc += fmaf(f[q].y, pb[q].y - pb[q].x, pb[q].x);
+            if (ina[q]) acc += fmaf(f[q].x, pa[q].y - pa[q].x, pa[q].x);
+            if (inb[q]) acc += fmaf(f[q].y, pb[q].y - pb[q].x, pb[q].x);
         }
     }
     for (; t <= tb; t += 2) {
         const float2 pos2 = __ffma2_rn(sl2, tf2, pm2);
         const float2 sk2 = __fadd2_rd(pos2, K2);
         const float2 f2 = __ffma2_rn(__ffma2_rn(K2, m1, sk2), m1, pos2);
-        if (t >= t_lo && t <= t_hi) {
+        if (pos2.x >= -1.f && pos2.x <= ohi) {
             const float2 p = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * __float_as_uint(sk2.x)));
             acc += fmaf(f2.x, p.y - p.x, p.x);
         }
-        if (t + 1 <= tb && t + 1 >= t_lo && t + 1 <= t_hi) {
+        if (t + 1 <= tb && pos2.y >= -1.f && pos2.y <= ohi) {
             const float2 p = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * __float_as_uint(sk2.y)));
             acc += fmaf(f2.y, p.y - p.x, p.x);
         }
@@ -235,6 +234,45 @@ __device__ __forceinline__ float joseph2d_span(int ta, int tb, int t_lo, int t_h
         K2 = __fadd2_rn(K2, dK2);
     }
     return acc;
+}
+
+// A ray of the table in FP32: slope, weight, driving axis, n_other and a range of lines [lo, hi]
+// that contains every line t whose FP32 position fma(slope, t - tmid, pmid) - the sample loop's
+// own arithmetic - lies in [-1, n_other] (an FP32 estimate of the crossings widened by two
+// lines and clipped to the image; empty when the ray misses it).  The loop takes a sample only
+// where its position is in [-1, n_other]: the tap pair floor(pos) + 1 is then in
+// [0, n_other + 1], inside the line's zero-padded pairs, so no position needs a clamp; a line
+// beyond the ray's own image extent (a warp's rays may drive along different axes of a
+// non-square image) is one of the zero lines both layouts carry up to max(nx, ny).
+struct RayJ {
+    float pmid, slope, weight, ohi;
+    int axis, lo, hi;
+};
+
+__device__ __forceinline__ RayJ decode_ray2d(const Ray2D R, int nx, int ny, float h)
+{
+    RayJ r;
+    r.pmid = R.pmid;
+    r.axis = R.enc & 1;
+    r.slope = (float)(R.enc >> 1) * 1.862645149230957e-9f;          // 2^-29
+    r.weight = h * sqrtf(fmaf(r.slope, r.slope, 1.f));
+    const int n_drive = r.axis ? ny : nx, n_other = r.axis ? nx : ny;
+    const float tmid = 0.5f * (float)(n_drive - 1);
+    r.ohi = (float)n_other;
+    const float tmax = (float)(n_drive - 1);
+    if (r.slope != 0.f) {
+        const float rs = __frcp_rn(r.slope);
+        const float ta = tmid + (-1.f - r.pmid) * rs, tb = tmid + (r.ohi - r.pmid) * rs;
+        const float lo = fmaxf(0.f, floorf(fminf(ta, tb)) - 2.f);
+        const float hi = fminf(tmax, ceilf(fmaxf(ta, tb)) + 2.f);
+        r.lo = lo <= hi ? (int)lo : 1;
+        r.hi = lo <= hi ? (int)hi : 0;
+    } else {
+        const bool in = r.pmid >= -1.f && r.pmid <= r.ohi;
+        r.lo = in ? 0 : 1;
+        r.hi = in ? n_drive - 1 : 0;
+    }
+    return r;
 }
 
 // CHUNKED: the lines are walked in chunks of `chunk` (images whose line offsets exceed 2^22)
@@ -245,18 +283,18 @@ template <bool CHUNKED>
 __global__ void __launch_bounds__(512, 2) joseph2d_kernel(
     const Ray2D *__restrict__ rays, int n_views, int ndu, int vpb,
     const float2 *__restrict__ prow, int prow_ld, const float2 *__restrict__ pcol, int pcol_ld,
-    int chunk, int nx, int ny, float *__restrict__ y, int y_ld, int y_off, const int *stop)
+    int chunk, int nx, int ny, float h, float *__restrict__ y, int y_ld, int y_off,
+    const int *stop)
 {
     if (stop && stop[0] != 0) return;
     const int bins_pb = blockDim.x / vpb;
     const int bin = blockIdx.x * bins_pb + (int)threadIdx.x % bins_pb;
     const int view0 = blockIdx.y * vpb + (int)threadIdx.x / bins_pb;
     const bool valid = bin < ndu && view0 < n_views;   // all lanes stay for the warp range
-    const Ray2D R = rays[valid ? (int64_t)view0 * ndu + bin : 0];
-    int t_lo = R.packed & 0x7fff;
-    int t_hi = (R.packed >> 15) & 0x7fff;
+    const RayJ R = decode_ray2d(rays[valid ? (int64_t)view0 * ndu + bin : 0], nx, ny, h);
+    int t_lo = R.lo, t_hi = R.hi;
     if (!valid) { t_lo = 1; t_hi = 0; }
-    const int axis = (R.packed >> 30) & 1;
+    const int axis = R.axis;
     const float2 *base;          // line 0 of the layout the ray reads
     int stride, n_drive;
     if (axis == 0) { base = pcol; stride = pcol_ld; n_drive = nx; }   // drive along x
@@ -270,12 +308,11 @@ __global__ void __launch_bounds__(512, 2) joseph2d_kernel(
                            8ull * ((uint64_t)__float_as_uint(kFloor2p23) + 1ull);
     float acc = 0.f;
     if (!CHUNKED) {
-        acc = joseph2d_span<kJBatch>(wlo, whi, t_lo, t_hi, R.pmid, R.slope, tmid, stride, abase,
-                                     acc);
+        acc = joseph2d_span<kJBatch>(wlo, whi, R.ohi, R.pmid, R.slope, tmid, stride, abase, acc);
     } else {
         for (int t0 = wlo; t0 <= whi; t0 += chunk)
-            acc = joseph2d_span<kJBatch>(t0, min(whi, t0 + chunk - 1), t_lo, t_hi, R.pmid,
-                                         R.slope, tmid, stride, abase, acc);
+            acc = joseph2d_span<kJBatch>(t0, min(whi, t0 + chunk - 1), R.ohi, R.pmid, R.slope,
+                                         tmid, stride, abase, acc);
     }
     if (valid) y[(int64_t)view0 * y_ld + y_off + bin] = acc * R.weight;
 }
@@ -297,11 +334,11 @@ cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, con
     if (std::max(d.nx, d.ny) <= chunk)
         joseph2d_kernel<false><<<grid, threads, 0, s>>>(g->rays_dev, d.n_views, d.ndu, vpb, prow,
                                                         d.row_pairs_ld, pcol, d.col_pairs_ld,
-                                                        chunk, d.nx, d.ny, y, y_ld, y_off, stop);
+                                                        chunk, d.nx, d.ny, d.h, y, y_ld, y_off, stop);
     else
         joseph2d_kernel<true><<<grid, threads, 0, s>>>(g->rays_dev, d.n_views, d.ndu, vpb, prow,
                                                        d.row_pairs_ld, pcol, d.col_pairs_ld,
-                                                       chunk, d.nx, d.ny, y, y_ld, y_off, stop);
+                                                       chunk, d.nx, d.ny, d.h, y, y_ld, y_off, stop);
     return cudaGetLastError();
 }
 
@@ -315,16 +352,16 @@ cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, con
 // kernel rounds them to FP32.  Taps outside the image have no pixel.
 __global__ void __launch_bounds__(256) joseph2d_adjoint_kernel(
     const Ray2D *__restrict__ rays, int n_views, int ndu, const float *__restrict__ y, int y_ld,
-    int y_off, int nx, int ny, double *__restrict__ acc, const int *stop)
+    int y_off, int nx, int ny, float h, double *__restrict__ acc, const int *stop)
 {
     if (stop && stop[0] != 0) return;
     const int64_t ray = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (ray >= (int64_t)n_views * ndu) return;
     const int view = (int)(ray / ndu), bin = (int)(ray - (int64_t)view * ndu);
-    const Ray2D R = rays[ray];
+    const RayJ R = decode_ray2d(rays[ray], nx, ny, h);
     const float yw = y[(int64_t)view * y_ld + y_off + bin] * R.weight;
-    const int t_lo = R.packed & 0x7fff, t_hi = (R.packed >> 15) & 0x7fff;
-    const int axis = (R.packed >> 30) & 1;
+    const int t_lo = R.lo, t_hi = R.hi;
+    const int axis = R.axis;
     const int n_drive = axis == 0 ? nx : ny, n_other = axis == 0 ? ny : nx;
     // pixel (line t, tap i): axis 0 drives along x (line = column t, taps along rows i),
     // axis 1 along y (line = row t, taps along columns i)
@@ -332,12 +369,14 @@ __global__ void __launch_bounds__(256) joseph2d_adjoint_kernel(
     float tf = (float)t_lo - 0.5f * (float)(n_drive - 1);
     for (int t = t_lo; t <= t_hi; ++t, tf += 1.f) {
         const float pos = fmaf(R.slope, tf, R.pmid);
+        if (!(pos >= -1.f && pos <= R.ohi)) continue;   // the samples the forward kernel takes
         const float fl = floorf(pos);
         const float f = pos - fl;
         const int i0 = (int)fl;
-        double *p = acc + (int64_t)t * step_t + (int64_t)i0 * step_i;
-        if (i0 >= 0) atomicAdd(p, (double)(yw * (1.f - f)));
-        if (i0 + 1 < n_other) atomicAdd(p + step_i, (double)(yw * f));
+        double *p = acc + (int64_t)t * step_t;
+        if (i0 >= 0 && i0 < n_other) atomicAdd(p + (int64_t)i0 * step_i, (double)(yw * (1.f - f)));
+        if (i0 + 1 >= 0 && i0 + 1 < n_other)
+            atomicAdd(p + (int64_t)(i0 + 1) * step_i, (double)(yw * f));
     }
 }
 
@@ -367,7 +406,7 @@ cudaError_t launch_adjoint2d(const ct_geom *g, const float *y, int y_ld, int y_o
     if (e != cudaSuccess) return e;
     const int64_t rays = (int64_t)d.n_views * d.ndu;
     joseph2d_adjoint_kernel<<<(unsigned)((rays + 255) / 256), 256, 0, s>>>(
-        g->rays_dev, d.n_views, d.ndu, y, y_ld, y_off, d.nx, d.ny, g->adj_acc_dev, stop);
+        g->rays_dev, d.n_views, d.ndu, y, y_ld, y_off, d.nx, d.ny, d.h, g->adj_acc_dev, stop);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_round_to_float(g->adj_acc_dev, n, x, stop, s);
