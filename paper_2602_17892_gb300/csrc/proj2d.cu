@@ -176,10 +176,15 @@ cudaError_t launch_back_proj(const ct_geom *g, const float *ypad, float *x, cons
 // gathers in flight (with one pair per iteration the kernel waited on its gathers: 14
 // long-scoreboard stalls per issue); single pairs finish the range.
 template <int NB>
-__device__ __forceinline__ float joseph2d_span(int ta, int tb, float ohi, float pmid,
-                                               float slope, float tmid, int stride,
-                                               uint64_t abase, float acc)
+__device__ __forceinline__ float2 joseph2d_span(int ta, int tb, float ohi, float pmid,
+                                                float slope, float tmid, int stride,
+                                                uint64_t abase, float2 acc_even_odd)
 {
+    // the pairs (t, t + 1) start at ta: their first line is odd when ta is, so the sums of the
+    // even and of the odd lines are swapped for the span (the split is by absolute line
+    // parity, whatever range a warp walks)
+    const bool odd = ta & 1;
+    float2 acc = odd ? make_float2(acc_even_odd.y, acc_even_odd.x) : acc_even_odd;
     float2 tf2 = make_float2((float)ta - tmid, (float)ta - tmid + 1.f);
     float2 K2 = make_float2(kFloorK0, kFloorK0 + (float)stride);
     const float2 sl2 = make_float2(slope, slope), pm2 = make_float2(pmid, pmid);
@@ -212,28 +217,28 @@ __device__ __forceinline__ float joseph2d_span(int ta, int tb, float ohi, float 
             if (ina[q]) pa[q] = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * ia[q]));
             if (inb[q]) pb[q] = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * ib[q]));
         }
+        // a sample not taken has zero taps, so its term is an exact zero
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
-            if (ina[q]) acc += fmaf(f[q].x, pa[q].y - pa[q].x, pa[q].x);
-            if (inb[q]) acc += fmaf(f[q].y, pb[q].y - pb[q].x, pb[q].x);
+            const float va = fmaf(f[q].x, pa[q].y - pa[q].x, pa[q].x);
+            const float vb = fmaf(f[q].y, pb[q].y - pb[q].x, pb[q].x);
+            acc = __fadd2_rn(acc, make_float2(va, vb));
         }
     }
     for (; t <= tb; t += 2) {
         const float2 pos2 = __ffma2_rn(sl2, tf2, pm2);
         const float2 sk2 = __fadd2_rd(pos2, K2);
         const float2 f2 = __ffma2_rn(__ffma2_rn(K2, m1, sk2), m1, pos2);
-        if (pos2.x >= -1.f && pos2.x <= ohi) {
-            const float2 p = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * __float_as_uint(sk2.x)));
-            acc += fmaf(f2.x, p.y - p.x, p.x);
-        }
-        if (t + 1 <= tb && pos2.y >= -1.f && pos2.y <= ohi) {
-            const float2 p = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * __float_as_uint(sk2.y)));
-            acc += fmaf(f2.y, p.y - p.x, p.x);
-        }
+        float2 pa = make_float2(0.f, 0.f), pb = make_float2(0.f, 0.f);
+        if (pos2.x >= -1.f && pos2.x <= ohi)
+            pa = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * __float_as_uint(sk2.x)));
+        if (t + 1 <= tb && pos2.y >= -1.f && pos2.y <= ohi)
+            pb = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * __float_as_uint(sk2.y)));
+        acc = __fadd2_rn(acc, make_float2(fmaf(f2.x, pa.y - pa.x, pa.x), fmaf(f2.y, pb.y - pb.x, pb.x)));
         tf2 = __fadd2_rn(tf2, d2);
         K2 = __fadd2_rn(K2, dK2);
     }
-    return acc;
+    return odd ? make_float2(acc.y, acc.x) : acc;
 }
 
 // A ray of the table in FP32: slope, weight, driving axis, n_other and a range of lines [lo, hi]
@@ -306,7 +311,8 @@ __global__ void __launch_bounds__(512, 2) joseph2d_kernel(
     const int whi = __reduce_max_sync(0xffffffffu, t_hi >= t_lo ? t_hi : -1);
     const uint64_t abase = reinterpret_cast<uint64_t>(base) -
                            8ull * ((uint64_t)__float_as_uint(kFloor2p23) + 1ull);
-    float acc = 0.f;
+    // two sums, of the even and of the odd lines (in line order each), added at the end
+    float2 acc = make_float2(0.f, 0.f);
     if (!CHUNKED) {
         acc = joseph2d_span<kJBatch>(wlo, whi, R.ohi, R.pmid, R.slope, tmid, stride, abase, acc);
     } else {
@@ -314,7 +320,7 @@ __global__ void __launch_bounds__(512, 2) joseph2d_kernel(
             acc = joseph2d_span<kJBatch>(t0, min(whi, t0 + chunk - 1), R.ohi, R.pmid, R.slope,
                                          tmid, stride, abase, acc);
     }
-    if (valid) y[(int64_t)view0 * y_ld + y_off + bin] = acc * R.weight;
+    if (valid) y[(int64_t)view0 * y_ld + y_off + bin] = (acc.x + acc.y) * R.weight;
 }
 
 cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, const int *stop,
@@ -514,7 +520,10 @@ __global__ void __launch_bounds__(VP == 2 ? 256 : 512, VP == 2 ? 3 : 1) pixbp2d_
     const float gam = 0.5f * (float)(nd - 1) + 2.f;   // +2: padded row offset
     const float hi = (float)(nd + 2);
     const uint64_t ybase = reinterpret_cast<uint64_t>(ypair) - 8ull * __float_as_uint(kFloor2p23);
-    float acc = 0.f;
+    // two sums, of the even and of the odd views (in view order each), added at the end: the
+    // paired loop accumulates both with one fma.f32x2 per view pair, the single-view loop the same
+    // way, so every launch shape gives the same result
+    float2 acc2 = make_float2(0.f, 0.f);
     int v = 0;
     if (VP == 2) {
         // view pairs (2j, 2j + 1): both views' positions, weights and floors in paired FP32
@@ -546,8 +555,9 @@ __global__ void __launch_bounds__(VP == 2 ? 256 : 512, VP == 2 ? 3 : 1) pixbp2d_
                 }
 #pragma unroll
                 for (int q = 0; q < kBPBatch; ++q) {
-                    acc = fmaf(w[q].x, fmaf(f[q].x, a[q].y - a[q].x, a[q].x), acc);
-                    acc = fmaf(w[q].y, fmaf(f[q].y, b[q].y - b[q].x, b[q].x), acc);
+                    const float va = fmaf(f[q].x, a[q].y - a[q].x, a[q].x);
+                    const float vb = fmaf(f[q].y, b[q].y - b[q].x, b[q].x);
+                    acc2 = __ffma2_rn(w[q], make_float2(va, vb), acc2);
                 }
             }
             for (int jj = jfull; jj < j1; ++jj) {
@@ -557,8 +567,9 @@ __global__ void __launch_bounds__(VP == 2 ? 256 : 512, VP == 2 ? 3 : 1) pixbp2d_
                                          f, w, ia, ib);
                 const float2 a = __ldg(reinterpret_cast<const float2 *>(rb + 8ull * ia));
                 const float2 b = __ldg(reinterpret_cast<const float2 *>(rb + 8ull * ib));
-                acc = fmaf(w.x, fmaf(f.x, a.y - a.x, a.x), acc);
-                acc = fmaf(w.y, fmaf(f.y, b.y - b.x, b.x), acc);
+                const float va = fmaf(f.x, a.y - a.x, a.x);
+                const float vb = fmaf(f.y, b.y - b.x, b.x);
+                acc2 = __ffma2_rn(w, make_float2(va, vb), acc2);
                 K2 = __fadd2_rn(K2, dK2);
             }
         }
@@ -570,11 +581,12 @@ __global__ void __launch_bounds__(VP == 2 ? 256 : 512, VP == 2 ? 3 : 1) pixbp2d_
         float K = kFloor2p23;
 #pragma unroll 4
         for (int vv = v0; vv < v1; ++vv) {
-            pixbp2d_view<FAN, CLAMP>(sv1[vv], tc, tr, gam, hi, sid_h, k_u, K, rb, acc);
+            if (vv & 1) pixbp2d_view<FAN, CLAMP>(sv1[vv], tc, tr, gam, hi, sid_h, k_u, K, rb, acc2.y);
+            else pixbp2d_view<FAN, CLAMP>(sv1[vv], tc, tr, gam, hi, sid_h, k_u, K, rb, acc2.x);
             K += (float)ld;
         }
     }
-    x[(int64_t)r * nx + c] = acc * (FAN ? k_w : w_par);
+    x[(int64_t)r * nx + c] = (acc2.x + acc2.y) * (FAN ? k_w : w_par);
 }
 
 template <bool FAN, bool CLAMP, int VP>
