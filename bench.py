@@ -281,7 +281,17 @@ def bench_ours(args, rank, world, local_rank):
     # one geometry object per problem of the batch (each owns its problem's workspace)
     G = P.Geom.from_geometry(geom)
     G_ba = P.Geom.from_geometry(geom)
-    batch = P.Batch([G, G_ba], ["ab", "ba"], max_iters=ITERS, rule="dp", tau=TAU, autotune=True)
+    if args.launch_shapes:
+        # fixed shapes (a profiler run repeats the shapes a plain run chose: the autotuner's
+        # timings under a profiler would pick differently)
+        vals = [int(v) for v in args.launch_shapes.split(",")]
+        if len(vals) != len(SHAPE_KEYS):
+            raise SystemExit("--launch-shapes takes six integers: " + ",".join(SHAPE_KEYS))
+        fixed = dict(zip(SHAPE_KEYS, vals))
+        for g in (G, G_ba):
+            P.ct_geom_set_launch_shapes(g, fixed)
+    batch = P.Batch([G, G_ba], ["ab", "ba"], max_iters=ITERS, rule="dp", tau=TAU,
+                    autotune=not args.launch_shapes)
     shapes = P.ct_geom_get_launch_shapes(G)     # setup: projector launch shapes (autotuned)
     b, b_dev, noise_ab, noise_ba = make_data_gpu(P, torch, G, geom, x_true, case, rank)
     x_ab = torch.zeros(G.n, device="cuda")
@@ -443,6 +453,7 @@ def bench_ours(args, rank, world, local_rank):
                    "execution": "the AB and BA solves as one ct_batch (one CUDA graph, two "
                                 "concurrent branches)",
                    "launch_shapes": shapes,
+                   "launch_shapes_from": "--launch-shapes" if args.launch_shapes else "autotuned",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": "iters/s",
                 "h2d_bytes_per_step": int(G.m * 4), "d2h_bytes_per_step": int(2 * G.n * 4)},
@@ -977,6 +988,9 @@ def check_ranks(gpus, env):
     return None
 
 
+SHAPE_KEYS = ("a_threads", "a_views", "a_slab", "b_rows", "b_views", "a_rays")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -988,6 +1002,9 @@ def main():
     ap.add_argument("--projectors", choices=["fan512", "cone256", "cone512"], default=None,
                     help="time A and B alone on this workload instead of the solver benchmark")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--launch-shapes", default=None,
+                    help="fixed projector launch shapes for the solver benchmark instead of "
+                         "autotuning: " + ",".join(SHAPE_KEYS) + " as six integers")
     ap.add_argument("--variants", default="all",
                     help="'all', 'none' or a comma list of: basis_precision_fan512_ab, "
                          "learned_lambda_parallel256, batched_slices_256, cone512, "
