@@ -284,10 +284,7 @@ def bench_ours(args, rank, world, local_rank):
     if args.launch_shapes:
         # fixed shapes (a profiler run repeats the shapes a plain run chose: the autotuner's
         # timings under a profiler would pick differently)
-        vals = [int(v) for v in args.launch_shapes.split(",")]
-        if len(vals) != len(SHAPE_KEYS):
-            raise SystemExit("--launch-shapes takes six integers: " + ",".join(SHAPE_KEYS))
-        fixed = dict(zip(SHAPE_KEYS, vals))
+        fixed = dict(zip(SHAPE_KEYS, parse_shapes(args.launch_shapes)))
         for g in (G, G_ba):
             P.ct_geom_set_launch_shapes(g, fixed)
     batch = P.Batch([G, G_ba], ["ab", "ba"], max_iters=ITERS, rule="dp", tau=TAU,
@@ -904,7 +901,11 @@ def bench_projectors(args):
         g = synth.cone512_case(N)["geom"]
         x = synth.ellipsoid_phantom(N, seed=0)
     G = P.Geom.from_geometry(g)
-    shapes = P.ct_geom_autotune(G) if not args.no_autotune else None
+    if args.launch_shapes:
+        shapes = dict(zip(SHAPE_KEYS, parse_shapes(args.launch_shapes)))
+        P.ct_geom_set_launch_shapes(G, shapes)
+    else:
+        shapes = P.ct_geom_autotune(G) if not args.no_autotune else None
     xd = torch.from_numpy(x.astype(np.float32).reshape(-1)).cuda()
     yd = torch.empty(G.m, device="cuda")
     xb = torch.empty(G.n, device="cuda")
@@ -991,6 +992,13 @@ def check_ranks(gpus, env):
 SHAPE_KEYS = ("a_threads", "a_views", "a_slab", "b_rows", "b_views", "a_rays")
 
 
+def parse_shapes(text):
+    vals = [int(v) for v in text.split(",")]
+    if len(vals) != len(SHAPE_KEYS):
+        raise SystemExit("--launch-shapes takes six integers: " + ",".join(SHAPE_KEYS))
+    return vals
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1003,8 +1011,8 @@ def main():
                     help="time A and B alone on this workload instead of the solver benchmark")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--launch-shapes", default=None,
-                    help="fixed projector launch shapes for the solver benchmark instead of "
-                         "autotuning: " + ",".join(SHAPE_KEYS) + " as six integers")
+                    help="fixed projector launch shapes (solver and projector benchmarks) "
+                         "instead of autotuning: " + ",".join(SHAPE_KEYS) + " as six integers")
     ap.add_argument("--variants", default="all",
                     help="'all', 'none' or a comma list of: basis_precision_fan512_ab, "
                          "learned_lambda_parallel256, batched_slices_256, cone512, "

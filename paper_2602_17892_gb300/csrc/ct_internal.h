@@ -97,7 +97,7 @@ struct ct_geom {
     float2 *prow_dev;   // 2D: [ny][row_pairs_ld] pairs along x; 3D: P_y, [nz + 3][slice_y]
     float2 *pcol_dev;   // 2D: [nx][col_pairs_ld] pairs along y; 3D: P_x, [nz + 3][slice_x]
     float *sino_pad_dev;  // [n_views][sino_view_ld]
-    float2 *sino_pairs_dev; // [n_views][sino_view_ld] (bin j, bin j + 1) pairs read by B
+    float2 *sino_pairs_dev; // [n_views][sino_view_ld] (bin j, bin j + 1 - bin j) pairs read by B
     double *adj_acc_dev;    // n FP64 accumulators of the matched adjoint A^T (2D: from creation;
                             // cone: allocated when the adjoint is first selected)
     // solver workspace (grown on demand)

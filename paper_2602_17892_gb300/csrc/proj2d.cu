@@ -1,13 +1,15 @@
 // 2D projector kernels: ray-driven Joseph forward projector A and pixel-driven linear-
 // interpolation backprojector B (the unmatched pair of Sec. 2 of arXiv 2602.17892).
 //
-// Data layout in HBM (all FP32):
-//   P_row[r][j]  = (x[r][j-1], x[r][j])   j in [0, nx], zero outside the image
-//   P_col[c][i]  = (x[i-1][c], x[i][c])   i in [0, ny]
-// so every Joseph sample is ONE 8-byte load of the two neighbours it interpolates, with no
-// bounds test: rays driven along x read P_col (neighbouring rays of a warp read adjacent
-// pairs), rays driven along y read P_row.  The padded sinogram has 2 zero bins on each side
-// of every detector row, so the backprojector's two taps also need no bounds test.
+// Data layout in HBM (all FP32), "slope pairs" (a value and the difference to its neighbour):
+//   P_row[r][j]  = (x[r][j-1], x[r][j] - x[r][j-1])   j in [0, nx], zero outside the image
+//   P_col[c][i]  = (x[i-1][c], x[i][c] - x[i-1][c])   i in [0, ny]
+// so every Joseph sample is ONE 8-byte load of what it interpolates, with no bounds test, and
+// the linear interpolation a + w (b - a) is one fma (the FP32 difference is formed once, by the
+// layout kernel, instead of at every sample; the result is bitwise the same): rays driven along
+// x read P_col (neighbouring rays of a warp read adjacent pairs), rays driven along y read
+// P_row.  The padded sinogram has 2 zero bins on each side of every detector row, so the
+// backprojector's two taps also need no bounds test; it is read as slope pairs too.
 #include <algorithm>
 
 #include "ct_internal.h"
@@ -40,7 +42,8 @@ __global__ void __launch_bounds__(256) image_pairs_kernel(
         int tr = t / 32, tj = t % 32;
         int r = r0 + tr, j = c0 + tj;
         if (r < ny && j <= nx)
-            pr[(int64_t)r * rs + j] = make_float2(tile[tr + 1][tj], tile[tr + 1][tj + 1]);
+            pr[(int64_t)r * rs + j] =
+                make_float2(tile[tr + 1][tj], tile[tr + 1][tj + 1] - tile[tr + 1][tj]);
     }
     // P_col: column c in [c0, c0+32) (< nx), pair index i in [r0, r0+32) (<= ny)
     float2 *pc = pcol + (int64_t)off * cs + (int64_t)(z + off) * czs;
@@ -48,7 +51,8 @@ __global__ void __launch_bounds__(256) image_pairs_kernel(
         int tc = t / 32, ti = t % 32;
         int c = c0 + tc, i = r0 + ti;
         if (c < nx && i <= ny)
-            pc[(int64_t)c * cs + i] = make_float2(tile[ti][tc + 1], tile[ti + 1][tc + 1]);
+            pc[(int64_t)c * cs + i] =
+                make_float2(tile[ti][tc + 1], tile[ti + 1][tc + 1] - tile[ti][tc + 1]);
     }
 }
 
@@ -94,9 +98,9 @@ cudaError_t launch_pad_sino(const ct_geom *g, const float *y, float *ypad, cudaS
 }
 
 // ---------------------------------------------------------------------------- sinogram pairs
-// pairs[e] = (ypad[e], ypad[e + 1]) over the whole padded sinogram (the element after a row's
-// last one is the next row's first zero margin, or zero at the end): a backprojector tap pair
-// is then one aligned 8-byte load.
+// pairs[e] = (ypad[e], ypad[e + 1] - ypad[e]) over the whole padded sinogram (the element after
+// a row's last one is the next row's first zero margin, or zero at the end): a backprojector
+// tap pair is then one aligned 8-byte load and its interpolation one fma.
 __global__ void sino_pairs_kernel(const float *__restrict__ ypad, int64_t total,
                                   float2 *__restrict__ pairs, const int *stop)
 {
@@ -108,8 +112,8 @@ __global__ void sino_pairs_kernel(const float *__restrict__ ypad, int64_t total,
          e += (int64_t)gridDim.x * blockDim.x) {
         const float4 a = __ldg(y4 + e);
         const float nx = (e + 1 < n4) ? __ldg(ypad + 4 * (e + 1)) : 0.f;
-        p4[2 * e] = make_float4(a.x, a.y, a.y, a.z);
-        p4[2 * e + 1] = make_float4(a.z, a.w, a.w, nx);
+        p4[2 * e] = make_float4(a.x, a.y - a.x, a.y, a.z - a.y);
+        p4[2 * e + 1] = make_float4(a.z, a.w - a.z, a.w, nx - a.w);
     }
 }
 
@@ -220,8 +224,8 @@ __device__ __forceinline__ float2 joseph2d_span(int ta, int tb, float ohi, float
         // a sample not taken has zero taps, so its term is an exact zero
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
-            const float va = fmaf(f[q].x, pa[q].y - pa[q].x, pa[q].x);
-            const float vb = fmaf(f[q].y, pb[q].y - pb[q].x, pb[q].x);
+            const float va = fmaf(f[q].x, pa[q].y, pa[q].x);
+            const float vb = fmaf(f[q].y, pb[q].y, pb[q].x);
             acc = __fadd2_rn(acc, make_float2(va, vb));
         }
     }
@@ -234,7 +238,7 @@ __device__ __forceinline__ float2 joseph2d_span(int ta, int tb, float ohi, float
             pa = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * __float_as_uint(sk2.x)));
         if (t + 1 <= tb && pos2.y >= -1.f && pos2.y <= ohi)
             pb = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * __float_as_uint(sk2.y)));
-        acc = __fadd2_rn(acc, make_float2(fmaf(f2.x, pa.y - pa.x, pa.x), fmaf(f2.y, pb.y - pb.x, pb.x)));
+        acc = __fadd2_rn(acc, make_float2(fmaf(f2.x, pa.y, pa.x), fmaf(f2.y, pb.y, pb.x)));
         tf2 = __fadd2_rn(tf2, d2);
         K2 = __fadd2_rn(K2, dK2);
     }
@@ -456,7 +460,7 @@ __device__ __forceinline__ void pixbp2d_view(const float4 V, float tc, float tr,
     const float sk = __fadd_rd(fj, K);
     const float f = fj - (sk - K);
     const float2 ab = __ldg(reinterpret_cast<const float2 *>(rb + 8ull * __float_as_uint(sk)));
-    acc = fmaf(w, fmaf(f, ab.y - ab.x, ab.x), acc);
+    acc = fmaf(w, fmaf(f, ab.y, ab.x), acc);
 }
 
 // positions, weights and tap-pair indices of views (2j, 2j + 1) for the paired loop
@@ -555,8 +559,8 @@ __global__ void __launch_bounds__(VP == 2 ? 256 : 512, VP == 2 ? 3 : 1) pixbp2d_
                 }
 #pragma unroll
                 for (int q = 0; q < kBPBatch; ++q) {
-                    const float va = fmaf(f[q].x, a[q].y - a[q].x, a[q].x);
-                    const float vb = fmaf(f[q].y, b[q].y - b[q].x, b[q].x);
+                    const float va = fmaf(f[q].x, a[q].y, a[q].x);
+                    const float vb = fmaf(f[q].y, b[q].y, b[q].x);
                     acc2 = __ffma2_rn(w[q], make_float2(va, vb), acc2);
                 }
             }
@@ -567,8 +571,8 @@ __global__ void __launch_bounds__(VP == 2 ? 256 : 512, VP == 2 ? 3 : 1) pixbp2d_
                                          f, w, ia, ib);
                 const float2 a = __ldg(reinterpret_cast<const float2 *>(rb + 8ull * ia));
                 const float2 b = __ldg(reinterpret_cast<const float2 *>(rb + 8ull * ib));
-                const float va = fmaf(f.x, a.y - a.x, a.x);
-                const float vb = fmaf(f.y, b.y - b.x, b.x);
+                const float va = fmaf(f.x, a.y, a.x);
+                const float vb = fmaf(f.y, b.y, b.x);
                 acc2 = __ffma2_rn(w, make_float2(va, vb), acc2);
                 K2 = __fadd2_rn(K2, dK2);
             }

@@ -2,9 +2,9 @@
 // planes of the driving axis) and voxel-driven backprojector B (bilinear interpolation on the
 // flat detector), the 3D form of the unmatched pair of Sec. 2.
 //
-// Data layout in HBM (all FP32; the volume is x[z][y][x]):
-//   P_x[z+1][x+1][y+1] = (x[z][y][x], x[z][y+1][x]) for z in [-1, nz+1], x in [-1, M+1], y in [-1, ny]
-//   P_y[z+1][y+1][x+1] = (x[z][y][x], x[z][y][x+1]) for z in [-1, nz+1], y in [-1, M+1], x in [-1, nx]
+// Data layout in HBM (all FP32; the volume is x[z][y][x]), slope pairs as in 2D:
+//   P_x[z+1][x+1][y+1] = (x[z][y][x], x[z][y+1][x] - x[z][y][x]) for z in [-1, nz+1], x in [-1, M+1], y in [-1, ny]
+//   P_y[z+1][y+1][x+1] = (x[z][y][x], x[z][y][x+1] - x[z][y][x]) for z in [-1, nz+1], y in [-1, M+1], x in [-1, nx]
 // with M = max(nx, ny) (zero outside the volume; rows of ld >= n + 2 pairs, one z slice after
 // the other).  A Joseph sample is two 8-byte loads (the two z rows of its 2 x 2 taps) with no
 // bounds test: rays driven along x read P_x, along y P_y, and the rare rays driven along z read
@@ -200,8 +200,8 @@ __global__ void __launch_bounds__(256, 3) joseph3d_kernel(
                 }
 #pragma unroll
                 for (int q = 0; q < NB; ++q) {
-                    const float a0v = fmaf(wbq[q], p0q[q].y - p0q[q].x, p0q[q].x);
-                    const float a1v = fmaf(wbq[q], p1q[q].y - p1q[q].x, p1q[q].x);
+                    const float a0v = fmaf(wbq[q], p0q[q].y, p0q[q].x);
+                    const float a1v = fmaf(wbq[q], p1q[q].y, p1q[q].x);
                     acc += inq[q] ? fmaf(wzq[q], a1v - a0v, a0v) : 0.f;
                     any |= inq[q];
                 }
@@ -218,8 +218,8 @@ __global__ void __launch_bounds__(256, 3) joseph3d_kernel(
                 const uint64_t a0 = cb + 8ull * __float_as_uint(sb) + zsl8 * __float_as_uint(sz);
                 const float2 p0 = __ldg(reinterpret_cast<const float2 *>(a0));
                 const float2 p1 = __ldg(reinterpret_cast<const float2 *>(a0 + zsl8));
-                const float a0v = fmaf(wb, p0.y - p0.x, p0.x);
-                const float a1v = fmaf(wb, p1.y - p1.x, p1.x);
+                const float a0v = fmaf(wb, p0.y, p0.x);
+                const float a1v = fmaf(wb, p1.y, p1.x);
                 const bool in = t >= lo && t <= hi && (!SLAB || (fz >= fz_lo && fz < fz_hi));
                 acc += in ? fmaf(wz, a1v - a0v, a0v) : 0.f;
                 any |= in;
@@ -246,8 +246,8 @@ __global__ void __launch_bounds__(256, 3) joseph3d_kernel(
             const float wx = pxf - fx, wy = pyf - fy;
             const float2 *row = py + (int64_t)(t + 1) * zsy + (int64_t)((int)fy + 1) * ldy + (int)fx + 1;
             const float2 p0 = __ldg(row), p1 = __ldg(row + ldy);
-            const float a0 = fmaf(wx, p0.y - p0.x, p0.x);
-            const float a1 = fmaf(wx, p1.y - p1.x, p1.x);
+            const float a0 = fmaf(wx, p0.y, p0.x);
+            const float a1 = fmaf(wx, p1.y, p1.x);
             acc += fmaf(wy, a1 - a0, a0);
             any = true;
         }
@@ -431,14 +431,14 @@ __global__ void __launch_bounds__(256, 3) joseph3d_pair_kernel(
 #pragma unroll
                 for (int q = 0; q < NB; ++q) {
                     if (ina[q]) {
-                        const float a0 = fmaf(wbq[q], p0a[q].y - p0a[q].x, p0a[q].x);
-                        const float a1 = fmaf(wbq[q], p1a[q].y - p1a[q].x, p1a[q].x);
+                        const float a0 = fmaf(wbq[q], p0a[q].y, p0a[q].x);
+                        const float a1 = fmaf(wbq[q], p1a[q].y, p1a[q].x);
                         acca += fmaf(wzq[q].x, a1 - a0, a0);
                         if (SLAB) anya = true;
                     }
                     if (inb[q]) {
-                        const float b0 = fmaf(wbq[q], p0b[q].y - p0b[q].x, p0b[q].x);
-                        const float b1 = fmaf(wbq[q], p1b[q].y - p1b[q].x, p1b[q].x);
+                        const float b0 = fmaf(wbq[q], p0b[q].y, p0b[q].x);
+                        const float b1 = fmaf(wbq[q], p1b[q].y, p1b[q].x);
                         accb += fmaf(wzq[q].y, b1 - b0, b0);
                         if (SLAB) anyb = true;
                     }
@@ -460,8 +460,8 @@ __global__ void __launch_bounds__(256, 3) joseph3d_pair_kernel(
                     const uint64_t a_ = base + (uint64_t)zsl8 * __float_as_uint(sz.x);
                     const float2 q0a = __ldg(reinterpret_cast<const float2 *>(a_));
                     const float2 q1a = __ldg(reinterpret_cast<const float2 *>(a_ + zsl8w));
-                    const float a0 = fmaf(wb, q0a.y - q0a.x, q0a.x);
-                    const float a1 = fmaf(wb, q1a.y - q1a.x, q1a.x);
+                    const float a0 = fmaf(wb, q0a.y, q0a.x);
+                    const float a1 = fmaf(wb, q1a.y, q1a.x);
                     acca += fmaf(wz.x, a1 - a0, a0);
                     if (SLAB) anya = true;
                 }
@@ -469,8 +469,8 @@ __global__ void __launch_bounds__(256, 3) joseph3d_pair_kernel(
                     const uint64_t b_ = base + (uint64_t)zsl8 * __float_as_uint(sz.y);
                     const float2 q0b = __ldg(reinterpret_cast<const float2 *>(b_));
                     const float2 q1b = __ldg(reinterpret_cast<const float2 *>(b_ + zsl8w));
-                    const float b0 = fmaf(wb, q0b.y - q0b.x, q0b.x);
-                    const float b1 = fmaf(wb, q1b.y - q1b.x, q1b.x);
+                    const float b0 = fmaf(wb, q0b.y, q0b.x);
+                    const float b1 = fmaf(wb, q1b.y, q1b.x);
                     accb += fmaf(wz.y, b1 - b0, b0);
                     if (SLAB) anyb = true;
                 }
@@ -499,8 +499,8 @@ __global__ void __launch_bounds__(256, 3) joseph3d_pair_kernel(
             const float wx = pxf - fx, wy = pyf - fy;
             const float2 *row = py + (int64_t)(t + 1) * zsy + (int64_t)((int)fy + 1) * ldy + (int)fx + 1;
             const float2 p0 = __ldg(row), p1 = __ldg(row + ldy);
-            const float a0 = fmaf(wx, p0.y - p0.x, p0.x);
-            const float a1 = fmaf(wx, p1.y - p1.x, p1.x);
+            const float a0 = fmaf(wx, p0.y, p0.x);
+            const float a1 = fmaf(wx, p1.y, p1.x);
             acc += fmaf(wy, a1 - a0, a0);
             any = true;
         }
@@ -796,9 +796,9 @@ __global__ void __launch_bounds__(128) voxbp3d_kernel(
             const float fvl = floorf(fv);
             const float wv = fv - fvl;
             const float2 *p = col + (int64_t)(int)fvl * ld;
-            const float2 t0 = __ldg(p), t1 = __ldg(p + ld);     // (bin u, bin u + 1) of two rows
-            const float r0 = fmaf(wu, t0.y - t0.x, t0.x);
-            const float r1 = fmaf(wu, t1.y - t1.x, t1.x);
+            const float2 t0 = __ldg(p), t1 = __ldg(p + ld);     // bin u and its slope, two rows
+            const float r0 = fmaf(wu, t0.y, t0.x);
+            const float r1 = fmaf(wu, t1.y, t1.x);
             const float q = fmaf(b, b, s2);
             acc[j] = fmaf(rho2 * (q * rsqrtf(q)), fmaf(wv, r1 - r0, r0), acc[j]);
         }
