@@ -36,8 +36,9 @@
 //
 // Parameter readings shared with the FP64 CPU oracle: GCV is evaluated on 256 log-spaced
 // lambda in [sigma_1 1e-8, sigma_1], the first grid minimum is refined by 40 golden-section
-// steps in log lambda on the neighbouring bracket (kept only if not worse); DP solves
-// rho(lambda) = tau ||e|| by 60 bisection steps in log lambda over the same range.
+// steps in log lambda on the neighbouring bracket (kept only if not worse); DP takes the root
+// of rho(lambda) = tau ||e|| in that range (the oracle by 60 bisection steps in log lambda,
+// this kernel by safeguarded Newton steps in log lambda: the same root up to rounding).
 #include <algorithm>
 
 #include "ct_internal.h"
@@ -92,11 +93,19 @@ __device__ __forceinline__ void givens(double a, double b, double &c, double &s,
     s = b / r;
 }
 
-// 1/x in FP64 from the FP32 reciprocal and two Newton steps (relative error ~1e-16)
+// The rescaling tests and the Sturm signs read only the high 32 bits of an FP64 value (sign,
+// exponent, top of the mantissa): 32-bit integer operations on the value's upper register.
+// With 64-bit patterns the same tests cost a Sturm step about 300 cycles instead of 185 on
+// GB300, where each FP64 instruction takes about 67 cycles of its sub-partition's pipe.
+// |v|'s high word ordered as an integer
+__device__ __forceinline__ int abs_hi(double v) { return __double2hiint(v) & 0x7fffffff; }
+
+// 1/x in FP64 from the FP32 reciprocal and two Newton steps (relative error ~1e-16); the range
+// test (|x| in (2^-100, 2^100), else a division) on the high word, in integer operations
 __device__ __forceinline__ double rcp64(double x)
 {
-    const double ax = fabs(x);
-    if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
+    const int ax = abs_hi(x);
+    if (!(ax > 0x39b00000 && ax < 0x46300000)) return 1.0 / x;
     double r = (double)__frcp_rn((float)x);
     r = r * fma(-x, r, 2.0);
     r = r * fma(-x, r, 2.0);
@@ -104,14 +113,15 @@ __device__ __forceinline__ double rcp64(double x)
 }
 
 // Householder vector (LAPACK dlarfg convention): H = I - tau [1; v][1; v]^T maps [alpha; x]
-// to [beta; 0] with v = x * scale.
+// to [beta; 0] with v = x * scale.  The two reciprocals come from rcp64 (a division costs
+// about twice its FP64 instructions, and a reflector's set-up is serial work of the block).
 __device__ void make_reflector(double alpha, double xnorm2, double &beta, double &tau, double &scale)
 {
     if (xnorm2 == 0.0) { beta = alpha; tau = 0.0; scale = 0.0; return; }
     double nrm = sqrt(alpha * alpha + xnorm2);
     beta = (alpha >= 0.0) ? -nrm : nrm;
-    tau = (beta - alpha) / beta;
-    scale = 1.0 / (alpha - beta);
+    tau = (beta - alpha) * rcp64(beta);
+    scale = rcp64(alpha - beta);
 }
 
 // Implicit-shift QR on the upper bidiagonal (d, e), left rotations applied to g.  One thread.
@@ -191,10 +201,13 @@ __device__ int bidiag_svd_serial(double *d, double *e, double *g, int n)
     return iter >= max_iter ? -1 : 0;
 }
 
-// |v| ordered as an integer: the bit pattern without the sign
-__device__ __forceinline__ long long abs_bits(double v)
+constexpr int kHi2p400 = 0x58f00000;    // high word of 2^400
+constexpr int kHi2m400 = 0x26f00000;    // high word of 2^-400
+// outside [2^-400, 2^400] (by the high word; a zero high word is an exact zero here: the
+// recurrences never get near the subnormal range)
+__device__ __forceinline__ bool needs_rescale(int mag)
 {
-    return __double_as_longlong(v) & 0x7fffffffffffffffll;
+    return mag > kHi2p400 || (mag < kHi2m400 && mag != 0);
 }
 
 // det(theta I - T_{first..n-1}) and its derivative by the three-term recurrence, value * 2^ex.
@@ -205,17 +218,15 @@ __device__ void charpoly(const double *t2, int first, int n, double th, double &
 {
     double pm2 = 1.0, pm1 = th, qm2 = 0.0, qm1 = 1.0;   // size-1 block: det = theta, d/dth = 1
     int e = 0;
-    const long long big = __double_as_longlong(0x1p+400), small = __double_as_longlong(0x1p-400);
     for (int j = first + 1; j < n; ++j) {
         const double a = t2[j - 1];
         const double pj = th * pm1 - a * pm2;
         const double qj = pm1 + th * qm1 - a * qm2;
         pm2 = pm1; pm1 = pj; qm2 = qm1; qm1 = qj;
         if (((j - first) & 3) == 0) {
-            const long long mag = max(max(abs_bits(pm1), abs_bits(pm2)),
-                                      max(abs_bits(qm1), abs_bits(qm2)));
-            if (mag > big || (mag < small && mag != 0)) {
-                const int sh = (mag > big) ? -400 : 400;
+            const int mag = max(max(abs_hi(pm1), abs_hi(pm2)), max(abs_hi(qm1), abs_hi(qm2)));
+            if (needs_rescale(mag)) {
+                const int sh = (mag > kHi2p400) ? -400 : 400;
                 pm1 = ldexp(pm1, sh); pm2 = ldexp(pm2, sh);
                 qm1 = ldexp(qm1, sh); qm2 = ldexp(qm2, sh);
                 e -= sh;
@@ -231,24 +242,28 @@ __device__ void charpoly(const double *t2, int first, int n, double th, double &
 // T - x I = L D L^T are p_j / p_{j-1}).  Division-free; a zero minor takes the sign opposite to
 // its predecessor (as a zero pivot replaced by a tiny negative one would).  Rescaled by powers
 // of two every fourth step as in charpoly (x <= 2).
+// negative, or zero after a positive predecessor (sprev = false)
+__device__ __forceinline__ bool sturm_neg(double v, bool sprev)
+{
+    const int hi = __double2hiint(v);
+    return ((hi << 1) == 0) ? !sprev : (hi < 0);
+}
+
 __device__ int count64(const double *t2, int n, double x)
 {
     double pm2 = 1.0, pm1 = -x;
-    const long long b1 = __double_as_longlong(pm1);
-    bool sprev = b1 < 0 || (b1 << 1) == 0;
+    bool sprev = sturm_neg(pm1, false);
     int cnt = sprev;
-    const long long big = __double_as_longlong(0x1p+400), small = __double_as_longlong(0x1p-400);
     for (int j = 2; j <= n; ++j) {
         const double pj = -x * pm1 - t2[j - 2] * pm2;
-        const long long bj = __double_as_longlong(pj);
-        const bool sj = ((bj << 1) == 0) ? !sprev : (bj < 0);
+        const bool sj = sturm_neg(pj, sprev);
         cnt += sj != sprev;
         sprev = sj;
         pm2 = pm1; pm1 = pj;
         if ((j & 3) == 0) {
-            const long long mag = max(abs_bits(pm1), abs_bits(pm2));
-            if (mag > big || (mag < small && mag != 0)) {
-                const int sh = (mag > big) ? -400 : 400;
+            const int mag = max(abs_hi(pm1), abs_hi(pm2));
+            if (needs_rescale(mag)) {
+                const int sh = (mag > kHi2p400) ? -400 : 400;
                 pm1 = ldexp(pm1, sh); pm2 = ldexp(pm2, sh);
             }
         }
@@ -256,7 +271,8 @@ __device__ int count64(const double *t2, int n, double x)
     return cnt;
 }
 
-// det(z I - T) for complex z (rows first..n-1), power-of-two rescaled: value * 2^ex.
+// det(z I - T) for complex z (rows first..n-1), power-of-two rescaled every fourth step (|z|
+// stays below 3, so four steps grow the magnitudes by at most 4^4): value * 2^ex.
 __device__ void charpoly_c(const double *t2, int first, int n, double zr, double zi,
                            double &pr, double &pi, int &ex)
 {
@@ -267,14 +283,32 @@ __device__ void charpoly_c(const double *t2, int first, int n, double zr, double
         double cr = zr * br - zi * bi - a * ar;
         double ci = zr * bi + zi * br - a * ai;
         ar = br; ai = bi; br = cr; bi = ci;
-        double mag = fabs(cr) + fabs(ci);
-        if (mag > 0x1p+400 || (mag < 0x1p-400 && mag != 0.0)) {
-            int sh = (mag > 0x1p+400) ? -400 : 400;
+        if (((j - first) & 3) != 0) continue;
+        const int mag = max(max(abs_hi(ar), abs_hi(ai)), max(abs_hi(br), abs_hi(bi)));
+        if (needs_rescale(mag)) {
+            const int sh = (mag > kHi2p400) ? -400 : 400;
             ar = ldexp(ar, sh); ai = ldexp(ai, sh); br = ldexp(br, sh); bi = ldexp(bi, sh);
             e -= sh;
         }
     }
     pr = br; pi = bi; ex = e;
+}
+
+// x[m * sx] -= w * v[m * sv] for m in [0, n): four loads of each operand first, then the four
+// FP64 multiply-adds, then the four stores, so that a store waits for an FP64 result once per
+// four elements (with one element at a time every store waited for its multiply-add, about 67
+// cycles on GB300's FP64 pipe)
+__device__ __forceinline__ void axpy_sub(double *x, int sx, const double *v, int sv, int n, double w)
+{
+    int m = 0;
+    for (; m + 3 < n; m += 4) {
+        const double x0 = x[m * sx], x1 = x[(m + 1) * sx], x2 = x[(m + 2) * sx], x3 = x[(m + 3) * sx];
+        const double v0 = v[m * sv], v1 = v[(m + 1) * sv], v2 = v[(m + 2) * sv], v3 = v[(m + 3) * sv];
+        const double y0 = fma(-w, v0, x0), y1 = fma(-w, v1, x1);
+        const double y2 = fma(-w, v2, x2), y3 = fma(-w, v3, x3);
+        x[m * sx] = y0; x[(m + 1) * sx] = y1; x[(m + 2) * sx] = y2; x[(m + 3) * sx] = y3;
+    }
+    for (; m < n; ++m) x[m * sx] = fma(-w, v[m * sv], x[m * sx]);
 }
 
 size_t small_solve_smem_bytes(int k)
@@ -415,7 +449,8 @@ __global__ void __launch_bounds__(kSSThreads, 1) small_solve_kernel(SmallSolvePa
                     if (l < k) w0 += A[l * lda + j] * A[l * lda + i];
                     const double w = (w0 + w1) * tau;
                     A[j * lda + i] -= w;
-                    for (int m = j + 1; m < k; ++m) A[m * lda + i] -= w * A[m * lda + j];
+                    axpy_sub(A + (size_t)(j + 1) * lda + i, lda, A + (size_t)(j + 1) * lda + j, lda,
+                             k - j - 1, w);
                 }
             }
             if (tid == 0) { A[j * lda + j] = bt; d[j] = bt; tauR[j] = tau; }
@@ -448,7 +483,7 @@ __global__ void __launch_bounds__(kSSThreads, 1) small_solve_kernel(SmallSolvePa
                     if (i <= k) w0 += A[j * lda + i] * col[i];
                     const double w = (w0 + w1) * tau;
                     col[j + 1] -= w;
-                    for (int m = j + 2; m <= k; ++m) col[m] -= w * A[j * lda + m];
+                    axpy_sub(col + j + 2, 1, A + (size_t)j * lda + j + 2, 1, k - j - 1, w);
                 }
             }
             if (tid == 0) { A[j * lda + j + 1] = bt; e[j] = bt; }
@@ -944,6 +979,13 @@ __global__ void __launch_bounds__(kSSThreads, 1) small_solve_kernel(SmallSolvePa
         if (rr / (tt * tt) > gbest) lr = gridlam(ibest);
         lam = lr;
     } else {  // CT_LAMBDA_DP
+        // the root of rho(lambda) = target in u = log(lambda) on [log(sigma_1 1e-8), log sigma_1]
+        // (rho increases with lambda, so the root is unique): safeguarded Newton on
+        // rho^2 - target^2, bisecting whenever a step leaves the bracket.  The bracket halves at
+        // least at every bisection, so the 60 steps that plain bisection takes bound the
+        // iteration, and the root agrees with the bisection's to rounding.  Each step is one
+        // block pass in FP64 (about 70 dependent FP64 instructions on GB300, 2-4 us), so
+        // Newton's 5-10 passes replace the bisection's 60.
         const double target = P.dp_target;
         double lo = log(s1 * 1e-8), hi = log(s1);
         double rlo, tlo, rhi, thi;
@@ -953,12 +995,48 @@ __global__ void __launch_bounds__(kSSThreads, 1) small_solve_kernel(SmallSolvePa
         } else if (sqrt(rhi) <= target) {
             lam = exp(hi);
         } else {
+            // rho^2 at lambda and its derivative in log(lambda),
+            // d rho^2 / d log(lambda) = 4 sum_i (f_i c_i)^2 sigma_i^2 / (sigma_i^2 + lambda^2),
+            // f_i = lambda^2 / (sigma_i^2 + lambda^2); the whole block, one term per thread
+            auto eval_dp = [&](double l, double &r2, double &dr2) {
+                const double l2 = l * l;
+                double r = 0.0, dr = 0.0;
+                for (int i = tid; i < k; i += kSSThreads) {
+                    const double inv = rcp64(sig2[i] + l2);
+                    const double fc = l2 * inv * cv[i];
+                    r += fc * fc;
+                    dr += fc * fc * (sig2[i] * inv);
+                }
+                r = warp_sum_d(r);
+                dr = warp_sum_d(dr);
+                __syncthreads();
+                if (lane == 0) { misc[16 + 2 * warp] = r; misc[17 + 2 * warp] = dr; }
+                __syncthreads();
+                double sr = 0.0, sd = 0.0;
+                for (int w = 0; w < nwarps; ++w) { sr += misc[16 + 2 * w]; sd += misc[17 + 2 * w]; }
+                r2 = sr + cv[k] * cv[k];
+                dr2 = 4.0 * sd;
+            };
+            const double t2g = target * target;
+            double u = 0.5 * (lo + hi), fprev = 1e300;
             for (int it = 0; it < 60; ++it) {
-                double mid = 0.5 * (lo + hi), r, t, rd, td;
-                eval2(exp(mid), exp(mid), r, t, rd, td);
-                if (sqrt(r) < target) lo = mid; else hi = mid;
+                double r2, dr2;
+                eval_dp(exp(u), r2, dr2);
+                const double f = r2 - t2g;
+                // u is the root to the rounding of rho^2 (the oracle's bisection ends inside the
+                // same interval of u, |du| <= 1e-14 target^2 / (d rho^2 / du))
+                if (fabs(f) <= 1e-14 * t2g) break;
+                if (f < 0.0) lo = u; else hi = u;
+                // Newton, or bisection where the step leaves the bracket or |f| did not halve
+                double nu = (dr2 > 0.0) ? u - f / dr2 : 0.5 * (lo + hi);
+                if (!(nu > lo && nu < hi) || fabs(f) > 0.5 * fprev) nu = 0.5 * (lo + hi);
+                fprev = fabs(f);
+                const double step = fabs(nu - u);
+                u = nu;
+                if (step <= 1e-14 * fmax(1.0, fabs(u)) || hi - lo <= 1e-14 * fmax(1.0, fabs(u)))
+                    break;
             }
-            lam = exp(0.5 * (lo + hi));
+            lam = exp(u);
         }
     }
 
@@ -1011,7 +1089,7 @@ __global__ void __launch_bounds__(kSSThreads, 1) small_solve_kernel(SmallSolvePa
             }
             for (int i = k - 1; i >= 0; --i) {
                 double num = z[i] - ((i < k - 1) ? esv[i] * z[i + 1] : 0.0);
-                z[i] = (dsv[i] != 0.0) ? num / dsv[i] : 0.0;
+                z[i] = (dsv[i] != 0.0) ? num * rcp64(dsv[i]) : 0.0;
             }
         }
         __syncthreads();
