@@ -1,15 +1,21 @@
 // 2D projector kernels: ray-driven Joseph forward projector A and pixel-driven linear-
 // interpolation backprojector B (the unmatched pair of Sec. 2 of arXiv 2602.17892).
 //
-// Data layout in HBM (all FP32), "slope pairs" (a value and the difference to its neighbour):
-//   P_row[r][j]  = (x[r][j-1], x[r][j] - x[r][j-1])   j in [0, nx], zero outside the image
-//   P_col[c][i]  = (x[i-1][c], x[i][c] - x[i-1][c])   i in [0, ny]
-// so every Joseph sample is ONE 8-byte load of what it interpolates, with no bounds test, and
-// the linear interpolation a + w (b - a) is one fma (the FP32 difference is formed once, by the
-// layout kernel, instead of at every sample; the result is bitwise the same): rays driven along
-// x read P_col (neighbouring rays of a warp read adjacent pairs), rays driven along y read
-// P_row.  The padded sinogram has 2 zero bins on each side of every detector row, so the
-// backprojector's two taps also need no bounds test; it is read as slope pairs too.
+// Data layout in HBM (all FP32), "centred slope pairs": for the segment between samples
+// s_{i-1} and s_i of a line, the difference d = s_i - s_{i-1} and the value of the segment's
+// line at the line's centre index c, a = s_{i-1} - (i - 1 - c) d, so that at a position p
+// (index units) of the segment the linear interpolant is ONE fma, a + (p - c) d, with no
+// fraction p - floor(p) to form:
+//   P_row[r][j] = (x[r][j-1] - (j-1-cx) d, d), d = x[r][j] - x[r][j-1], j in [0, nx], cx = nx / 2
+//   P_col[c][i] = (x[i-1][c] - (i-1-cy) d, d), d = x[i][c] - x[i-1][c], i in [0, ny], cy = ny / 2
+// zero outside the image.  Every Joseph sample is one 8-byte load with no bounds test and one
+// fma: rays driven along x read P_col (neighbouring rays of a warp read adjacent pairs), rays
+// driven along y read P_row.  The rounding: a and p - c carry errors of the order of ulp(c d)
+// and ulp(p), the same order as the fraction p - floor(p) that the plain form interpolates
+// with (its error is ulp(p)).  The padded sinogram has 2 zero bins on each side of every
+// detector row, so the backprojector's two taps also need no bounds test; the 2D
+// backprojector reads it as centred slope pairs about the row's centre bin, the cone one as
+// plain slope pairs (y_j, y_{j+1} - y_j) (the 3D layouts are plain slope pairs as well).
 #include <algorithm>
 
 #include "ct_internal.h"
@@ -22,9 +28,12 @@ namespace ct {
 // prow[(z + off) * rzs + (r + off) * rs + j] and pair (c, i) of P_col to
 // pcol[(z + off) * czs + (c + off) * cs + i] (off = 1: a zero row of padding on each side,
 // and in 3D a zero slice on each side; 2D has one slice and rzs = czs = 0).
+// centred != 0: the centred form about cx = nx / 2 (P_row) and cy = ny / 2 (P_col) (2D);
+// otherwise plain slope pairs (x_{i-1}, x_i - x_{i-1}) (3D).
 __global__ void __launch_bounds__(256) image_pairs_kernel(
     const float *__restrict__ x, int nx, int ny, float2 *__restrict__ prow, int64_t rs,
-    int64_t rzs, float2 *__restrict__ pcol, int64_t cs, int64_t czs, int off, const int *stop)
+    int64_t rzs, float2 *__restrict__ pcol, int64_t cs, int64_t czs, int off, int centred,
+    const int *stop)
 {
     if (stop && stop[0] != 0) return;
     __shared__ float tile[33][34];
@@ -41,18 +50,22 @@ __global__ void __launch_bounds__(256) image_pairs_kernel(
     for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
         int tr = t / 32, tj = t % 32;
         int r = r0 + tr, j = c0 + tj;
-        if (r < ny && j <= nx)
-            pr[(int64_t)r * rs + j] =
-                make_float2(tile[tr + 1][tj], tile[tr + 1][tj + 1] - tile[tr + 1][tj]);
+        if (r < ny && j <= nx) {
+            const float a = tile[tr + 1][tj], d = tile[tr + 1][tj + 1] - a;
+            const float k = centred ? (float)(j - 1 - (nx >> 1)) : 0.f;
+            pr[(int64_t)r * rs + j] = make_float2(fmaf(-k, d, a), d);
+        }
     }
     // P_col: column c in [c0, c0+32) (< nx), pair index i in [r0, r0+32) (<= ny)
     float2 *pc = pcol + (int64_t)off * cs + (int64_t)(z + off) * czs;
     for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
         int tc = t / 32, ti = t % 32;
         int c = c0 + tc, i = r0 + ti;
-        if (c < nx && i <= ny)
-            pc[(int64_t)c * cs + i] =
-                make_float2(tile[ti][tc + 1], tile[ti + 1][tc + 1] - tile[ti][tc + 1]);
+        if (c < nx && i <= ny) {
+            const float a = tile[ti][tc + 1], d = tile[ti + 1][tc + 1] - a;
+            const float k = centred ? (float)(i - 1 - (ny >> 1)) : 0.f;
+            pc[(int64_t)c * cs + i] = make_float2(fmaf(-k, d, a), d);
+        }
     }
 }
 
@@ -63,10 +76,10 @@ cudaError_t launch_image_pairs(const ct_geom *g, const float *x, const int *stop
     if (d.kind == CT_CONE3D)
         image_pairs_kernel<<<grid, 256, 0, s>>>(x, d.nx, d.ny, g->prow_dev, d.row_pairs_ld,
                                                 d.slice_y, g->pcol_dev, d.col_pairs_ld,
-                                                d.slice_x, 1, stop);
+                                                d.slice_x, 1, 0, stop);
     else
         image_pairs_kernel<<<grid, 256, 0, s>>>(x, d.nx, d.ny, g->prow_dev, d.row_pairs_ld, 0,
-                                                g->pcol_dev, d.col_pairs_ld, 0, 1, stop);
+                                                g->pcol_dev, d.col_pairs_ld, 0, 1, 1, stop);
     return cudaGetLastError();
 }
 
@@ -98,22 +111,29 @@ cudaError_t launch_pad_sino(const ct_geom *g, const float *y, float *ypad, cudaS
 }
 
 // ---------------------------------------------------------------------------- sinogram pairs
-// pairs[e] = (ypad[e], ypad[e + 1] - ypad[e]) over the whole padded sinogram (the element after
-// a row's last one is the next row's first zero margin, or zero at the end): a backprojector
-// tap pair is then one aligned 8-byte load and its interpolation one fma.
+// Over the whole padded sinogram (the element after a row's last one is the next row's first
+// zero margin, or zero at the end), with d_e = ypad[e + 1] - ypad[e] and j = e mod ld the bin of
+// e in its row: centred (2D, rows of ld bins one after the other) pairs[e] =
+// (ypad[e] - (j - cb) d_e, d_e), cb the row's centre bin; plain (cone) pairs[e] = (ypad[e], d_e).
+// A backprojector tap pair is then one aligned 8-byte load and its interpolation one fma.
 __global__ void sino_pairs_kernel(const float *__restrict__ ypad, int64_t total,
-                                  float2 *__restrict__ pairs, const int *stop)
+                                  float2 *__restrict__ pairs, int ld, int cb, int centred,
+                                  const int *stop)
 {
     if (stop && stop[0] != 0) return;
-    const int64_t n4 = total / 4;               // total is a multiple of 4 (rows are)
+    const int64_t n4 = total / 4;               // total and ld are multiples of 4
     const float4 *y4 = reinterpret_cast<const float4 *>(ypad);
     float4 *p4 = reinterpret_cast<float4 *>(pairs);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n4;
          e += (int64_t)gridDim.x * blockDim.x) {
         const float4 a = __ldg(y4 + e);
         const float nx = (e + 1 < n4) ? __ldg(ypad + 4 * (e + 1)) : 0.f;
-        p4[2 * e] = make_float4(a.x, a.y - a.x, a.y, a.z - a.y);
-        p4[2 * e + 1] = make_float4(a.z, a.w - a.z, a.w, nx - a.w);
+        const float4 d = make_float4(a.y - a.x, a.z - a.y, a.w - a.z, nx - a.w);
+        const float k0 = centred ? (float)((int)((4 * e) % ld) - cb) : 0.f;
+        const float k1 = centred ? k0 + 1.f : 0.f, k2 = centred ? k0 + 2.f : 0.f;
+        const float k3 = centred ? k0 + 3.f : 0.f;
+        p4[2 * e] = make_float4(fmaf(-k0, d.x, a.x), d.x, fmaf(-k1, d.y, a.y), d.y);
+        p4[2 * e + 1] = make_float4(fmaf(-k2, d.z, a.z), d.z, fmaf(-k3, d.w, a.w), d.w);
     }
 }
 
@@ -123,7 +143,11 @@ static cudaError_t launch_sino_pairs(const ct_geom *g, const float *ypad, const 
     const DeviceGeom &d = g->dg;
     const int64_t total = (int64_t)d.n_views * d.sino_view_ld;
     const int blocks = (int)std::min<int64_t>((total / 4 + 255) / 256, 152 * 8);
-    sino_pairs_kernel<<<blocks, 256, 0, s>>>(ypad, total, g->sino_pairs_dev, stop);
+    // 2D: one padded row per view (view stride = ld), centred about the backprojector's centre
+    // bin (n_det_u + 3) / 2; cone: plain slope pairs
+    const bool centred = d.kind != CT_CONE3D;
+    sino_pairs_kernel<<<blocks, 256, 0, s>>>(ypad, total, g->sino_pairs_dev, d.sino_ld,
+                                             (d.ndu + 3) >> 1, centred ? 1 : 0, stop);
     return cudaGetLastError();
 }
 
@@ -161,27 +185,29 @@ cudaError_t launch_back_proj(const ct_geom *g, const float *ypad, float *x, cons
 // A block covers blockDim.x / vpb consecutive bins of vpb consecutive views (each warp one
 // view): the views of a block cross nearly the same pixels, so their warps share L1 lines.
 //
+// The loop works with the centred position pc = pos - co (co = n_other / 2, the layouts'
+// centre), pc = fma(slope, t - t_mid, pmid - co), and interpolates with one fma, a + pc d.
 // floor(pos) and the pair address come from ONE round-down FP32 addition: for K an integer
 // with 2^23 <= K + pos < 2^24 (unit spacing there), s = K + pos rounded towards -infinity is
-// exactly K + floor(pos), s - K and pos - (s - K) are exact, and the bit pattern of s is the
-// integer 0x4B000000 + (s - 2^23).  K also carries the offset of line t from a chunk base
-// (t - t0) * stride, an integer kept exactly in FP32, so the pair address is one multiply-add
-// of that bit pattern; chunks of lines keep (t - t0) * stride below 2^22.
+// exactly K + floor(pos), and the bit pattern of s is the integer 0x4B000000 + (s - 2^23);
+// here s = (K + co) + pc with K + co an integer.  K also carries the offset of line t from a
+// chunk base (t - t0) * stride, an integer kept exactly in FP32, so the pair address is one
+// multiply-add of that bit pattern; chunks of lines keep (t - t0) * stride below 2^22.
 //
 // No clamp: a sample is taken only where its FP32 position lies in [-1, n_other], so the pair
 // index floor(pos) + 1 stays in [0, n_other + 1], which the layouts hold (at least n_other + 2
 // pairs per line, zero beyond the image); lines run over [-1, max(nx, ny)] in both layouts, so
 // every line of a warp's range exists whatever axis a lane drives along.
-// Lines t in [ta, tb] of one ray, two at a time (t and t + 1): both samples' positions, floors
-// and weights in paired FP32 arithmetic (one fma.f32x2 / add.rm.f32x2 each, the same operations
+// Lines t in [ta, tb] of one ray, two at a time (t and t + 1): both samples' positions and
+// floors in paired FP32 arithmetic (one fma.f32x2 / add.rm.f32x2 each, the same operations
 // per sample as one line at a time), accumulated in line order.  K carries (t - ta) * stride
 // (below 2^22 for every t).  The lines go in batches of NB pairs: first all positions and
 // floors, then all 2 NB gathers, then the sums in line order, so that each thread has 2 NB
 // gathers in flight (with one pair per iteration the kernel waited on its gathers: 14
 // long-scoreboard stalls per issue); single pairs finish the range.
 template <int NB>
-__device__ __forceinline__ float2 joseph2d_span(int ta, int tb, float ohi, float pmid,
-                                                float slope, float tmid, int stride,
+__device__ __forceinline__ float2 joseph2d_span(int ta, int tb, float plo, float phi, float pmc,
+                                                float co, float slope, float tmid, int stride,
                                                 uint64_t abase, float2 acc_even_odd)
 {
     // the pairs (t, t + 1) start at ta: their first line is odd when ta is, so the sums of the
@@ -190,27 +216,25 @@ __device__ __forceinline__ float2 joseph2d_span(int ta, int tb, float ohi, float
     const bool odd = ta & 1;
     float2 acc = odd ? make_float2(acc_even_odd.y, acc_even_odd.x) : acc_even_odd;
     float2 tf2 = make_float2((float)ta - tmid, (float)ta - tmid + 1.f);
-    float2 K2 = make_float2(kFloorK0, kFloorK0 + (float)stride);
-    const float2 sl2 = make_float2(slope, slope), pm2 = make_float2(pmid, pmid);
+    float2 K2 = make_float2(kFloorK0 + co, kFloorK0 + co + (float)stride);
+    const float2 sl2 = make_float2(slope, slope), pm2 = make_float2(pmc, pmc);
     const float2 d2 = make_float2(2.f, 2.f), dK2 = make_float2(2.f * (float)stride, 2.f * (float)stride);
-    const float2 m1 = make_float2(-1.f, -1.f);
     const uint64_t lb = abase + 8ull * (uint64_t)ta * (uint64_t)stride;
     int t = ta;
     // tb - t: a warp whose lanes all have empty ranges has ta = INT_MAX and tb = -1, for which
     // t + 2 NB - 1 would overflow; tb - t >= INT_MIN does not
     for (; tb - t >= 2 * NB - 1; t += 2 * NB) {
-        float2 f[NB], pa[NB], pb[NB];
+        float2 pc[NB], pa[NB], pb[NB];
         uint32_t ia[NB], ib[NB];
         bool ina[NB], inb[NB];
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
-            const float2 pos2 = __ffma2_rn(sl2, tf2, pm2);
-            const float2 sk2 = __fadd2_rd(pos2, K2);
-            f[q] = __ffma2_rn(__ffma2_rn(K2, m1, sk2), m1, pos2);   // pos - (sk - K)
+            pc[q] = __ffma2_rn(sl2, tf2, pm2);                       // pos - co
+            const float2 sk2 = __fadd2_rd(pc[q], K2);
             ia[q] = __float_as_uint(sk2.x);
             ib[q] = __float_as_uint(sk2.y);
-            ina[q] = pos2.x >= -1.f && pos2.x <= ohi;
-            inb[q] = pos2.y >= -1.f && pos2.y <= ohi;
+            ina[q] = pc[q].x >= plo && pc[q].x <= phi;
+            inb[q] = pc[q].y >= plo && pc[q].y <= phi;
             tf2 = __fadd2_rn(tf2, d2);
             K2 = __fadd2_rn(K2, dK2);
         }
@@ -224,21 +248,20 @@ __device__ __forceinline__ float2 joseph2d_span(int ta, int tb, float ohi, float
         // a sample not taken has zero taps, so its term is an exact zero
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
-            const float va = fmaf(f[q].x, pa[q].y, pa[q].x);
-            const float vb = fmaf(f[q].y, pb[q].y, pb[q].x);
+            const float va = fmaf(pc[q].x, pa[q].y, pa[q].x);
+            const float vb = fmaf(pc[q].y, pb[q].y, pb[q].x);
             acc = __fadd2_rn(acc, make_float2(va, vb));
         }
     }
     for (; t <= tb; t += 2) {
-        const float2 pos2 = __ffma2_rn(sl2, tf2, pm2);
-        const float2 sk2 = __fadd2_rd(pos2, K2);
-        const float2 f2 = __ffma2_rn(__ffma2_rn(K2, m1, sk2), m1, pos2);
+        const float2 pc2 = __ffma2_rn(sl2, tf2, pm2);
+        const float2 sk2 = __fadd2_rd(pc2, K2);
         float2 pa = make_float2(0.f, 0.f), pb = make_float2(0.f, 0.f);
-        if (pos2.x >= -1.f && pos2.x <= ohi)
+        if (pc2.x >= plo && pc2.x <= phi)
             pa = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * __float_as_uint(sk2.x)));
-        if (t + 1 <= tb && pos2.y >= -1.f && pos2.y <= ohi)
+        if (t + 1 <= tb && pc2.y >= plo && pc2.y <= phi)
             pb = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * __float_as_uint(sk2.y)));
-        acc = __fadd2_rn(acc, make_float2(fmaf(f2.x, pa.y, pa.x), fmaf(f2.y, pb.y, pb.x)));
+        acc = __fadd2_rn(acc, make_float2(fmaf(pc2.x, pa.y, pa.x), fmaf(pc2.y, pb.y, pb.x)));
         tf2 = __fadd2_rn(tf2, d2);
         K2 = __fadd2_rn(K2, dK2);
     }
@@ -253,8 +276,11 @@ __device__ __forceinline__ float2 joseph2d_span(int ta, int tb, float ohi, float
 // [0, n_other + 1], inside the line's zero-padded pairs, so no position needs a clamp; a line
 // beyond the ray's own image extent (a warp's rays may drive along different axes of a
 // non-square image) is one of the zero lines both layouts carry up to max(nx, ny).
+// co = n_other / 2 (the centre of the layout the ray reads), pmc = pmid - co, and the
+// centred sample window [plo, phi] = [-1 - co, n_other - co].
 struct RayJ {
     float pmid, slope, weight, ohi;
+    float co, pmc, plo, phi;
     int axis, lo, hi;
 };
 
@@ -268,6 +294,10 @@ __device__ __forceinline__ RayJ decode_ray2d(const Ray2D R, int nx, int ny, floa
     const int n_drive = r.axis ? ny : nx, n_other = r.axis ? nx : ny;
     const float tmid = 0.5f * (float)(n_drive - 1);
     r.ohi = (float)n_other;
+    r.co = (float)(n_other >> 1);
+    r.pmc = r.pmid - r.co;
+    r.plo = -1.f - r.co;
+    r.phi = r.ohi - r.co;
     const float tmax = (float)(n_drive - 1);
     if (r.slope != 0.f) {
         const float rs = __frcp_rn(r.slope);
@@ -318,11 +348,12 @@ __global__ void __launch_bounds__(512, 2) joseph2d_kernel(
     // two sums, of the even and of the odd lines (in line order each), added at the end
     float2 acc = make_float2(0.f, 0.f);
     if (!CHUNKED) {
-        acc = joseph2d_span<kJBatch>(wlo, whi, R.ohi, R.pmid, R.slope, tmid, stride, abase, acc);
+        acc = joseph2d_span<kJBatch>(wlo, whi, R.plo, R.phi, R.pmc, R.co, R.slope, tmid, stride,
+                                     abase, acc);
     } else {
         for (int t0 = wlo; t0 <= whi; t0 += chunk)
-            acc = joseph2d_span<kJBatch>(t0, min(whi, t0 + chunk - 1), R.ohi, R.pmid, R.slope,
-                                         tmid, stride, abase, acc);
+            acc = joseph2d_span<kJBatch>(t0, min(whi, t0 + chunk - 1), R.plo, R.phi, R.pmc, R.co,
+                                         R.slope, tmid, stride, abase, acc);
     }
     if (valid) y[(int64_t)view0 * y_ld + y_off + bin] = (acc.x + acc.y) * R.weight;
 }
@@ -355,8 +386,9 @@ cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, con
 // ---------------------------------------------------------------------------- matched adjoint
 // x = A^T y, the transpose of the Joseph projector above (the matched case B = A^T of Sec. 2,
 // where AB-/BA-GMRES reduce to LSQR / LSMR): one thread per ray walks the ray's samples with
-// the same FP32 positions as joseph2d_kernel (pos = pmid + slope (t - t_mid), the taps
-// floor(pos) and floor(pos) + 1 with weights 1 - f and f) and adds weight (1 - f) y_ray and
+// the same FP32 positions as joseph2d_kernel (the centred pc = (pmid - co) + slope (t - t_mid),
+// the taps co + floor(pc) and co + floor(pc) + 1 with weights 1 - f and f, f = pc - floor(pc))
+// and adds weight (1 - f) y_ray and
 // weight f y_ray (FP32 products) to the two taps' pixels by atomic FP64 additions, so the
 // order in which the rays arrive changes the sums only far below FP32 resolution; a second
 // kernel rounds them to FP32.  Taps outside the image have no pixel.
@@ -378,11 +410,11 @@ __global__ void __launch_bounds__(256) joseph2d_adjoint_kernel(
     const int step_t = axis == 0 ? 1 : nx, step_i = axis == 0 ? nx : 1;
     float tf = (float)t_lo - 0.5f * (float)(n_drive - 1);
     for (int t = t_lo; t <= t_hi; ++t, tf += 1.f) {
-        const float pos = fmaf(R.slope, tf, R.pmid);
-        if (!(pos >= -1.f && pos <= R.ohi)) continue;   // the samples the forward kernel takes
-        const float fl = floorf(pos);
-        const float f = pos - fl;
-        const int i0 = (int)fl;
+        const float pc = fmaf(R.slope, tf, R.pmc);      // the forward kernel's centred position
+        if (!(pc >= R.plo && pc <= R.phi)) continue;    // the samples the forward kernel takes
+        const float fl = floorf(pc);
+        const float f = pc - fl;
+        const int i0 = (int)fl + (int)R.co;
         double *p = acc + (int64_t)t * step_t;
         if (i0 >= 0 && i0 < n_other) atomicAdd(p + (int64_t)i0 * step_i, (double)(yw * (1.f - f)));
         if (i0 + 1 >= 0 && i0 + 1 < n_other)
@@ -436,13 +468,15 @@ cudaError_t launch_adjoint2d(const ct_geom *g, const float *y, int y_ld, int y_o
 // waited on its gathers: 25 long-scoreboard stalls per issue); the launch bounds trade
 // occupancy (24 warps per SM) for the registers this takes.
 // floor(fj) and the pair address come from one round-down addition (as in the Joseph kernel):
-// K = 2^23 + (v - v0) ld over chunks of views; fj >= 0 in the padded row.
+// K = 2^23 + cb + (v - v0) ld over chunks of views, where the loop works with the centred bin
+// position fj - cb (cb = (n_det_u + 3) / 2, the centre of the slope pairs) and interpolates
+// with one fma, a + (fj - cb) d; fj >= 0 in the padded row.
 // CLAMP = false when every pixel centre of the image projects inside the detector in every
 // view (checked on the host at geometry creation): the bin positions then need no clamp.
 template <bool FAN, bool CLAMP>
 __device__ __forceinline__ void pixbp2d_view(const float4 V, float tc, float tr, float gam,
-                                             float hi, float sid_h, float k_u, float K,
-                                             uint64_t rb, float &acc)
+                                             float clo, float chi, float sid_h, float k_u,
+                                             float K, uint64_t rb, float &acc)
 {
     float fj, w;
     if (FAN) {
@@ -456,22 +490,20 @@ __device__ __forceinline__ void pixbp2d_view(const float4 V, float tc, float tr,
         fj = fmaf(V.z, tc, fmaf(V.w, tr, gam));
         w = 1.f;
     }
-    if (CLAMP) fj = fminf(fmaxf(fj, 0.f), hi);
+    if (CLAMP) fj = fminf(fmaxf(fj, clo), chi);
     const float sk = __fadd_rd(fj, K);
-    const float f = fj - (sk - K);
     const float2 ab = __ldg(reinterpret_cast<const float2 *>(rb + 8ull * __float_as_uint(sk)));
-    acc = fmaf(w, fmaf(f, ab.y, ab.x), acc);
+    acc = fmaf(w, fmaf(fj, ab.y, ab.x), acc);
 }
 
-// positions, weights and tap-pair indices of views (2j, 2j + 1) for the paired loop
+// centred positions, weights and tap-pair indices of views (2j, 2j + 1) for the paired loop
 template <bool FAN, bool CLAMP>
 __device__ __forceinline__ void pixbp2d_pair(const float4 V, float2 tr2, float2 tc2, float2 ntc2,
                                              float2 ntr2, float2 sid2, float2 ku2, float2 gam2,
-                                             float hi, float2 K2, float2 &f2, float2 &w2,
-                                             uint32_t &ia, uint32_t &ib)
+                                             float clo, float chi, float2 K2, float2 &fj2,
+                                             float2 &w2, uint32_t &ia, uint32_t &ib)
 {
-    const float2 one2 = make_float2(1.f, 1.f), m1 = make_float2(-1.f, -1.f);
-    float2 fj2;
+    const float2 one2 = make_float2(1.f, 1.f);
     if (FAN) {
         const float2 cs2 = make_float2(V.x, V.y), sn2 = make_float2(V.z, V.w);
         const float2 pe2 = __ffma2_rn(tr2, cs2, __fmul2_rn(ntc2, sn2));
@@ -485,9 +517,8 @@ __device__ __forceinline__ void pixbp2d_pair(const float4 V, float2 tr2, float2 
         fj2 = __ffma2_rn(make_float2(V.x, V.y), tc2, __ffma2_rn(make_float2(V.z, V.w), tr2, gam2));
         w2 = one2;
     }
-    if (CLAMP) fj2 = make_float2(fminf(fmaxf(fj2.x, 0.f), hi), fminf(fmaxf(fj2.y, 0.f), hi));
+    if (CLAMP) fj2 = make_float2(fminf(fmaxf(fj2.x, clo), chi), fminf(fmaxf(fj2.y, clo), chi));
     const float2 sk2 = __fadd2_rd(fj2, K2);
-    f2 = __ffma2_rn(__ffma2_rn(K2, m1, sk2), m1, fj2);   // fj - (sk - K)
     ia = __float_as_uint(sk2.x);
     ib = __float_as_uint(sk2.y);
 }
@@ -521,8 +552,10 @@ __global__ void __launch_bounds__(VP == 2 ? 256 : 512, VP == 2 ? 3 : 1) pixbp2d_
     if (c >= nx || r >= ny) return;
     const float tc = (float)c - 0.5f * (float)(nx - 1);
     const float tr = (float)r - 0.5f * (float)(ny - 1);
-    const float gam = 0.5f * (float)(nd - 1) + 2.f;   // +2: padded row offset
-    const float hi = (float)(nd + 2);
+    // bin position fj (in the padded row: +2) centred on the slope pairs' centre bin cb
+    const float cb = (float)((nd + 3) >> 1);
+    const float gam = 0.5f * (float)(nd - 1) + 2.f - cb;
+    const float clo = -cb, chi = (float)(nd + 2) - cb;
     const uint64_t ybase = reinterpret_cast<uint64_t>(ypair) - 8ull * __float_as_uint(kFloor2p23);
     // two sums, of the even and of the odd views (in view order each), added at the end: the
     // paired loop accumulates both with one fma.f32x2 per view pair, the single-view loop the same
@@ -539,17 +572,17 @@ __global__ void __launch_bounds__(VP == 2 ? 256 : 512, VP == 2 ? 3 : 1) pixbp2d_
         for (int v0 = 0; v0 < 2 * npair; v0 += vch) {
             const int v1 = min(2 * npair, v0 + vch);
             const uint64_t rb = ybase + 8ull * (uint64_t)v0 * (uint64_t)ld;
-            float2 K2 = make_float2(kFloor2p23, kFloor2p23 + (float)ld);
+            float2 K2 = make_float2(kFloor2p23 + cb, kFloor2p23 + cb + (float)ld);
             const float2 dK2 = make_float2(2.f * (float)ld, 2.f * (float)ld);
             const int j0 = v0 >> 1, j1 = v1 >> 1;
             const int jfull = j1 - (j1 - j0) % kBPBatch;
             for (int jb = j0; jb < jfull; jb += kBPBatch) {
-                float2 f[kBPBatch], w[kBPBatch], a[kBPBatch], b[kBPBatch];
+                float2 fc[kBPBatch], w[kBPBatch], a[kBPBatch], b[kBPBatch];
                 uint32_t ia[kBPBatch], ib[kBPBatch];
 #pragma unroll
                 for (int q = 0; q < kBPBatch; ++q) {
                     pixbp2d_pair<FAN, CLAMP>(sview[jb + q], tr2, tc2, ntc2, ntr2, sid2, ku2, gam2,
-                                             hi, K2, f[q], w[q], ia[q], ib[q]);
+                                             clo, chi, K2, fc[q], w[q], ia[q], ib[q]);
                     K2 = __fadd2_rn(K2, dK2);
                 }
 #pragma unroll
@@ -559,20 +592,20 @@ __global__ void __launch_bounds__(VP == 2 ? 256 : 512, VP == 2 ? 3 : 1) pixbp2d_
                 }
 #pragma unroll
                 for (int q = 0; q < kBPBatch; ++q) {
-                    const float va = fmaf(f[q].x, a[q].y, a[q].x);
-                    const float vb = fmaf(f[q].y, b[q].y, b[q].x);
+                    const float va = fmaf(fc[q].x, a[q].y, a[q].x);
+                    const float vb = fmaf(fc[q].y, b[q].y, b[q].x);
                     acc2 = __ffma2_rn(w[q], make_float2(va, vb), acc2);
                 }
             }
             for (int jj = jfull; jj < j1; ++jj) {
-                float2 f, w;
+                float2 fc, w;
                 uint32_t ia, ib;
-                pixbp2d_pair<FAN, CLAMP>(sview[jj], tr2, tc2, ntc2, ntr2, sid2, ku2, gam2, hi, K2,
-                                         f, w, ia, ib);
+                pixbp2d_pair<FAN, CLAMP>(sview[jj], tr2, tc2, ntc2, ntr2, sid2, ku2, gam2, clo, chi, K2,
+                                         fc, w, ia, ib);
                 const float2 a = __ldg(reinterpret_cast<const float2 *>(rb + 8ull * ia));
                 const float2 b = __ldg(reinterpret_cast<const float2 *>(rb + 8ull * ib));
-                const float va = fmaf(f.x, a.y, a.x);
-                const float vb = fmaf(f.y, b.y, b.x);
+                const float va = fmaf(fc.x, a.y, a.x);
+                const float vb = fmaf(fc.y, b.y, b.x);
                 acc2 = __ffma2_rn(w, make_float2(va, vb), acc2);
                 K2 = __fadd2_rn(K2, dK2);
             }
@@ -582,11 +615,11 @@ __global__ void __launch_bounds__(VP == 2 ? 256 : 512, VP == 2 ? 3 : 1) pixbp2d_
     for (int v0 = v; v0 < n_views; v0 += vchunk) {
         const int v1 = min(n_views, v0 + vchunk);
         const uint64_t rb = ybase + 8ull * (uint64_t)v0 * (uint64_t)ld;
-        float K = kFloor2p23;
+        float K = kFloor2p23 + cb;
 #pragma unroll 4
         for (int vv = v0; vv < v1; ++vv) {
-            if (vv & 1) pixbp2d_view<FAN, CLAMP>(sv1[vv], tc, tr, gam, hi, sid_h, k_u, K, rb, acc2.y);
-            else pixbp2d_view<FAN, CLAMP>(sv1[vv], tc, tr, gam, hi, sid_h, k_u, K, rb, acc2.x);
+            if (vv & 1) pixbp2d_view<FAN, CLAMP>(sv1[vv], tc, tr, gam, clo, chi, sid_h, k_u, K, rb, acc2.y);
+            else pixbp2d_view<FAN, CLAMP>(sv1[vv], tc, tr, gam, clo, chi, sid_h, k_u, K, rb, acc2.x);
             K += (float)ld;
         }
     }
