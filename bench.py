@@ -56,12 +56,15 @@ PHASE_KERNELS = {"pixel_B": ("pixbp2d_kernel", "paper_2602_17892_gb300/csrc/proj
 TRAFFIC_TABLE = os.path.join(ROOT, "profiles", "dram_traffic_fan512.md")
 
 
-def kernel_traffic(name):
-    """dram__bytes_read.sum + dram__bytes_write.sum per launch of the kernel behind `name`, from
-    the committed ncu summary, or None when the kernel's source file has changed since the
-    capture (its SHA-256 prefix no longer matches the one recorded beside the number)."""
+def kernel_traffic(name, shapes=None):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch of the kernel behind `name` (for
+    the pixel-driven B: the four-fold kernel when the launch shapes select it), from the
+    committed ncu summary, or None when the kernel's source file has changed since the capture
+    (its SHA-256 prefix no longer matches the one recorded beside the number)."""
     import hashlib
     kern, src = PHASE_KERNELS.get(name, (None, None))
+    if name == "pixel_B" and shapes and shapes.get("b_views") == 4:
+        kern = "pixbp2d_rot4_kernel"
     if kern is None or not os.path.exists(TRAFFIC_TABLE):
         return None
     sha = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
@@ -389,7 +392,10 @@ def bench_ours(args, rank, world, local_rank):
     if b_n:
         upd = G.b_samples * b_n
         gups = upd / (b_ms * 1e-3) / 1e9
-        pk = min(probe["gather8"], probe["mufu"])    # fan: one tap-pair load and one rcp+sqrt
+        # fan: one tap-pair load per pixel-view pair and one rcp+sqrt (the four-fold kernel:
+        # one rcp+sqrt per four pairs)
+        rot4 = shapes.get("b_views") == 4
+        pk = min(probe["gather8"], (4.0 if rot4 else 1.0) * probe["mufu"])
         kernels["pixel_B"] = {"ms": b_ms, "launches": b_n, "gups": gups, "peak_gups": pk,
                               "frac": gups / pk,
                               "hbm_gbs": proj_bytes * b_n / (b_ms * 1e-3) / 1e9}
@@ -419,10 +425,10 @@ def bench_ours(args, rank, world, local_rank):
         # ceiling is the measured rate of the elementary work of one sample (probes above)
         kd = kernels[dom]
         src = ("ct_probe gather8 (one 8-byte L1 tap-pair load + one FMA per sample)"
-               if dom == "joseph_A" or probe["gather8"] <= probe["mufu"] else
+               if kd["peak_gups"] == probe["gather8"] else
                "ct_probe mufu (one reciprocal + one square root per pixel-view pair)")
         roof = {"kernel": dom, "bound": "alu", "achieved": kd["gups"], "peak": kd["peak_gups"],
-                "unit": "Gupdates/s", "frac": kd["frac"], "traffic": kernel_traffic(dom),
+                "unit": "Gupdates/s", "frac": kd["frac"], "traffic": kernel_traffic(dom, shapes),
                 "peak_source": f"measured in this run: {src}",
                 "hbm": {"achieved_gbs": kd["hbm_gbs"], "peak_gbs": peaks["hbm_gbs"],
                         "frac": kd["hbm_frac"],

@@ -323,6 +323,28 @@ static bool pixels_inside_detector(const ct_geom_desc *d)
     return true;
 }
 
+// Views in quadruples a quarter turn apart on a square image of even side (fan-flat): view
+// k + m n/4 at angle theta_k + m pi/2 for m = 1, 2, 3 (cos and sin within 1e-9), at most 16384
+// views.  Then a quarter turn of the image maps pixels onto pixels and each view onto another
+// view of the scan, which the four-fold backprojector uses.
+static bool rot4_symmetric(const ct_geom_desc *d)
+{
+    if (d->kind != CT_FANFLAT2D || d->nx != d->ny || (d->nx & 1) || d->n_views % 4 != 0 ||
+        d->n_views > 16384)
+        return false;
+    const int q = d->n_views / 4;
+    for (int k = 0; k < q; ++k) {
+        const double c0 = cos(d->angles[k]), s0 = sin(d->angles[k]);
+        const double ec[3] = {-s0, -c0, s0}, es[3] = {c0, -s0, -c0};   // rotated by m pi/2
+        for (int m = 1; m < 4; ++m) {
+            const double a = d->angles[k + m * q];
+            if (!(fabs(cos(a) - ec[m - 1]) <= 1e-9 && fabs(sin(a) - es[m - 1]) <= 1e-9))
+                return false;
+        }
+    }
+    return true;
+}
+
 // In-plane (fan) part of the rays of column iu of a cone view: every ray of the column has the
 // x-y projection of the fan ray through detector column iu, D = P - S unnormalised.
 static RayXY make_ray_xy(const ct_geom_desc *d, int view, int iu)
@@ -448,6 +470,7 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     dg.tune_b_views = 1;
     dg.back_adjoint = 0;
     dg.b_noclamp = cone ? 0 : (pixels_inside_detector(&g->desc) ? 1 : 0);
+    dg.b_rot4 = rot4_symmetric(&g->desc) ? 1 : 0;
     dg.tune_a_slab = 16;
     dg.tune_a_rays = 1;
 
@@ -1328,7 +1351,7 @@ extern "C" ct_status ct_test_drop_tile_copy(int enable, int64_t wait_cycles)
 
 // ============================================================================ autotuning
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int, int, int, int, int, int>, ct_launch_shapes> g_tune_cache;
+static std::map<std::tuple<int, int, int, int, int, int, int, int, int>, ct_launch_shapes> g_tune_cache;
 
 static ct_launch_shapes shapes_of(const DeviceGeom &d)
 {
@@ -1350,9 +1373,11 @@ extern "C" ct_status ct_geom_set_launch_shapes(ct_geom *g, const ct_launch_shape
         for (int u : set) if (v == u) return true;
         return false;
     };
-    // the paired-view B kernel is compiled for blocks of at most 256 threads (8 rows)
-    bool ok = in(sh->b_rows, {4, 8, 16}) && in(sh->b_views, {1, 2}) &&
-              !(sh->b_views == 2 && sh->b_rows > 8);
+    // the paired-view B kernel is compiled for blocks of at most 256 threads (8 rows); the
+    // four-fold kernel (b_views 4) needs a b_rot4 geometry and b_rows 4 or 8
+    bool ok = in(sh->b_rows, {4, 8, 16}) && in(sh->b_views, {1, 2, 4}) &&
+              !(sh->b_views == 2 && sh->b_rows > 8) &&
+              !(sh->b_views == 4 && !(g->dg.b_rot4 && sh->b_rows <= 8));
     if (cone)
         ok = ok && sh->a_slab >= 1 && sh->a_views >= 1 && sh->a_views <= 8 && in(sh->a_rays, {1, 2});
     else
@@ -1385,7 +1410,8 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
     int dev = 0;
     CT_CUDA(cudaGetDevice(&dev));
     const auto key = std::make_tuple(dev, (int)g->desc.kind, g->desc.nx, g->desc.ny, g->desc.nz,
-                                     g->desc.n_views, g->desc.n_det_u, g->desc.n_det_v);
+                                     g->desc.n_views, g->desc.n_det_u, g->desc.n_det_v,
+                                     dg.b_rot4);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -1443,7 +1469,8 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
     static const int a3[12][3] = {{16, 1, 1}, {16, 4, 1}, {16, 8, 1}, {64, 4, 1}, {64, 8, 1},
                                   {1 << 20, 1, 1}, {1 << 20, 4, 1}, {1 << 20, 8, 1},
                                   {16, 4, 2}, {64, 4, 2}, {1 << 20, 2, 2}, {1 << 20, 4, 2}};
-    static const int b2[5][2] = {{4, 1}, {8, 1}, {16, 1}, {4, 2}, {8, 2}};
+    // B: (pixel rows per block, views per iteration); b_views 4 = the four-fold kernel
+    static const int b2[7][2] = {{4, 1}, {8, 1}, {16, 1}, {4, 2}, {8, 2}, {4, 4}, {8, 4}};
     auto fwd = [&]() { return launch_forward_proj(g, y, true, nullptr, s); };
     ct_status st;
     if (cone)
@@ -1458,7 +1485,8 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
             dg.tune_a_views = a2[c][1];
         });
     if (st == CT_OK && !cone)
-        st = time_best([&]() { return launch_back_proj(g, y, x, nullptr, s); }, 5, [&](int c) {
+        st = time_best([&]() { return launch_back_proj(g, y, x, nullptr, s); }, dg.b_rot4 ? 7 : 5,
+                       [&](int c) {
             dg.tune_b_rows = b2[c][0];
             dg.tune_b_views = b2[c][1];
         });

@@ -66,8 +66,12 @@ struct DeviceGeom {
     int tune_a_views;   // 2D Joseph A: views per block (each warp one view)
     int back_adjoint;   // the geometry's backprojector: 0 pixel/voxel-driven B, 1 A^T
     int tune_b_rows;    // pixel-driven B: block of 32 x tune_b_rows pixels
-    int tune_b_views;   // 2D pixel-driven B: views per loop iteration (1, or 2 in paired FP32)
+    int tune_b_views;   // 2D pixel-driven B: views per loop iteration (1, or 2 in paired FP32);
+                        // 4: the four-fold rotation kernel (b_rot4 geometries only)
     int b_noclamp;      // 2D: every pixel centre projects inside the detector in every view
+    int b_rot4;         // fan, square image of even side, views in quadruples 90 degrees apart
+                        // (view k + m n/4 at angle theta_k + m pi/2): B may use the rotation
+                        // kernel
     int tune_a_slab;    // 3D Joseph A: z slab thickness (tap rows) per launch
     int tune_a_rays;    // 3D Joseph A: detector rows per thread (1, or 2 sharing the in-plane
                         // coordinate)

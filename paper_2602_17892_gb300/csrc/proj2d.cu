@@ -626,6 +626,127 @@ __global__ void __launch_bounds__(VP == 2 ? 256 : 512, VP == 2 ? 3 : 1) pixbp2d_
     x[(int64_t)r * nx + c] = (acc2.x + acc2.y) * (FAN ? k_w : w_par);
 }
 
+// ---------------------------------------------------------------------------- four-fold B
+// Fan geometries whose views come in quadruples 90 degrees apart (view k + m n/4 at angle
+// theta_k + m pi/2, m = 1..3, checked on the host) on a square image of even side N: the pixel
+// grid is invariant under a quarter turn, and in centred coordinates view theta + pi/2 sees
+// pixel (tc, tr) exactly where view theta sees pixel (tr, -tc): the same bin position fj and
+// the same weight.  A thread takes the orbit of four pixels
+//   p0 = (tc, tr), p1 = (tr, -tc), p2 = (-tc, -tr), p3 = (-tr, tc)
+// (grid (c, r), (r, N-1-c), (N-1-c, N-1-r), (N-1-r, c), with (c, r) in the first quadrant)
+// and, for each base view k < n/4, forms the four geometries g_j = (fj, w)(theta_k, p_j) once
+// (pe_2 = -pe_0 and pe_3 = -pe_1 exactly); pixel p_i takes view k + m n/4 at g_{(i+m) mod 4}:
+// 16 pixel-view pairs from 4 geometry evaluations.  The 16 gathers of a base view are issued
+// together, then the sums (pixel by pixel, m in order).  The base views are split between the
+// block's two z-halves, whose sums are added in shared memory.  The arithmetic of one
+// pixel-view pair is the one of pixbp2d_view; only the views' constants (those of view k, for
+// the rotated pixel) and the order of the sums differ from the general kernel.
+template <bool CLAMP>
+__global__ void __launch_bounds__(256, 3) pixbp2d_rot4_kernel(
+    const ViewBP *__restrict__ views, int q4, const float2 *__restrict__ ypair, int ld,
+    int vchunk, int nd, int N, float sid_h, float k_u, float k_w, float *__restrict__ x,
+    const int *stop)
+{
+    if (stop && stop[0] != 0) return;
+    extern __shared__ float2 srot[];                 // (cos, sin) of the base views, then sums
+    float *red = reinterpret_cast<float *>(srot + q4);
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    const int tid = ((int)threadIdx.z * blockDim.y + threadIdx.y) * 32 + threadIdx.x;
+    for (int k = tid; k < q4; k += nthr) srot[k] = make_float2(views[k].cs, views[k].sn);
+    __syncthreads();
+    const int half = N >> 1;
+    const int c = blockIdx.x * 32 + threadIdx.x;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    const bool valid = c < half && r < half;
+    const float hN = 0.5f * (float)(N - 1);
+    const float tc = (float)c - hN, tr = (float)r - hN;
+    // centred bin positions, as in pixbp2d_kernel
+    const float cb = (float)((nd + 3) >> 1);
+    const float gam = 0.5f * (float)(nd - 1) + 2.f - cb;
+    const float clo = -cb, chi = (float)(nd + 2) - cb;
+    const int kz0 = threadIdx.z ? (q4 + 1) / 2 : 0, kz1 = threadIdx.z ? q4 : (q4 + 1) / 2;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const uint64_t ybase = reinterpret_cast<uint64_t>(ypair) - 8ull * __float_as_uint(kFloor2p23);
+    const uint64_t moff = 8ull * (uint64_t)q4 * (uint64_t)ld;     // bytes from row k to k + n/4
+    if (valid) {
+        for (int k0 = kz0; k0 < kz1; k0 += vchunk) {
+            const int k1 = min(kz1, k0 + vchunk);
+            uint64_t rb[4];
+            rb[0] = ybase + 8ull * (uint64_t)k0 * (uint64_t)ld;
+#pragma unroll
+            for (int m = 1; m < 4; ++m) rb[m] = rb[m - 1] + moff;
+            float K = kFloor2p23 + cb;                   // + (k - k0) ld
+            for (int k = k0; k < k1; ++k) {
+                const float2 V = srot[k];
+                const float cs = V.x, sn = V.y;
+                float pe[4], bb[4], fj[4], w[4];
+                uint32_t ia[4];
+                pe[0] = fmaf(tr, cs, -tc * sn);
+                pe[1] = fmaf(-tc, cs, -tr * sn);
+                pe[2] = -pe[0];
+                pe[3] = -pe[1];
+                bb[0] = fmaf(-tc, cs, fmaf(-tr, sn, sid_h));
+                bb[1] = fmaf(-tr, cs, fmaf(tc, sn, sid_h));
+                bb[2] = fmaf(tc, cs, fmaf(tr, sn, sid_h));
+                bb[3] = fmaf(tr, cs, fmaf(-tc, sn, sid_h));
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float rbb = __fdividef(1.f, bb[j]);
+                    const float t1 = pe[j] * rbb;
+                    float f = fmaf(t1, k_u, gam);
+                    if (CLAMP) f = fminf(fmaxf(f, clo), chi);
+                    fj[j] = f;
+                    w[j] = rbb * sqrtf(fmaf(t1, t1, 1.f));
+                    ia[j] = __float_as_uint(__fadd_rd(f, K));
+                }
+                float2 tap[16];
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        tap[4 * m + i] = __ldg(reinterpret_cast<const float2 *>(rb[m] + 8ull * ia[(i + m) & 3]));
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const int g = (i + m) & 3;
+                        acc[i] = fmaf(w[g], fmaf(fj[g], tap[4 * m + i].y, tap[4 * m + i].x), acc[i]);
+                    }
+                K += (float)ld;
+            }
+        }
+    }
+    // the second half's sums join the first's
+    const int slot = 4 * ((int)threadIdx.y * 32 + (int)threadIdx.x);
+    if (threadIdx.z == 1) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) red[slot + i] = acc[i];
+    }
+    __syncthreads();
+    if (threadIdx.z != 0 || !valid) return;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i] += red[slot + i];
+    const int M = N - 1;
+    x[(int64_t)r * N + c] = acc[0] * k_w;
+    x[(int64_t)(M - c) * N + r] = acc[1] * k_w;
+    x[(int64_t)(M - r) * N + (M - c)] = acc[2] * k_w;
+    x[(int64_t)c * N + (M - r)] = acc[3] * k_w;
+}
+
+template <bool CLAMP>
+static void launch_pixbp2d_rot4_t(const ct_geom *g, const float2 *ypad, float *x, const int *stop,
+                                  cudaStream_t s)
+{
+    const DeviceGeom &d = g->dg;
+    const int half = d.nx >> 1, ry = d.tune_b_rows / 2;     // b_rows 4 or 8: 2 or 4 orbit rows
+    dim3 block(32, ry, 2), grid((half + 31) / 32, (half + ry - 1) / ry);
+    const int q4 = d.n_views / 4;
+    const size_t smem = sizeof(float2) * (size_t)q4 + sizeof(float) * 4 * 32 * (size_t)ry;
+    pixbp2d_rot4_kernel<CLAMP><<<grid, block, smem, s>>>(
+        d.views, q4, ypad, d.sino_ld, floor_chunk(d.sino_ld), d.ndu, d.nx, d.sid / d.h,
+        d.sdd / d.pitch_u, d.h * d.sdd / d.pitch_u, x, stop);
+}
+
 template <bool FAN, bool CLAMP, int VP>
 static void launch_pixbp2d_t(const ct_geom *g, const float2 *ypad, float *x, const int *stop,
                              cudaStream_t s)
@@ -647,6 +768,13 @@ cudaError_t launch_pixbp2d(const ct_geom *g, const float2 *ypad, float *x, const
     const DeviceGeom &d = g->dg;
     const bool fan = d.kind == CT_FANFLAT2D, clamp = !d.b_noclamp, two = d.tune_b_views == 2;
     if (two && d.tune_b_rows > 8) return cudaErrorInvalidConfiguration;   // 256-thread bound
+    if (d.tune_b_views == 4) {
+        if (!fan || !d.b_rot4 || (d.tune_b_rows != 4 && d.tune_b_rows != 8))
+            return cudaErrorInvalidConfiguration;
+        clamp ? launch_pixbp2d_rot4_t<true>(g, ypad, x, stop, s)
+              : launch_pixbp2d_rot4_t<false>(g, ypad, x, stop, s);
+        return cudaGetLastError();
+    }
     if (fan) {
         if (clamp) two ? launch_pixbp2d_t<true, true, 2>(g, ypad, x, stop, s)
                        : launch_pixbp2d_t<true, true, 1>(g, ypad, x, stop, s);

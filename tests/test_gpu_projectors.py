@@ -140,3 +140,48 @@ def test_paired_backprojector_rejects_tall_blocks():
     with pytest.raises(Bn.CtError):
         ct_geom_set_launch_shapes(G, dict(base, b_rows=16, b_views=2))
     assert ct_geom_get_launch_shapes(G) == base
+
+
+@pytest.mark.parametrize("name", ["fan_64", "fan512"])
+def test_four_fold_backprojector(name):
+    """The four-fold B (b_views 4) on fan scans whose views come in quadruples a quarter turn
+    apart: each pixel within its element-wise FP32 bound of the oracle, within FP32 rounding of
+    the general kernel, and bitwise the same for both block heights."""
+    from paper_2602_17892_gb300 import ct_geom_get_launch_shapes, ct_geom_set_launch_shapes
+    g = GEOMS["fan_64"] if name == "fan_64" else synth.fan512_case()["geom"]
+    y = f32(np.abs(synth.standard_normal(g.m, 41)) + 1.0)
+    G = gpu_geom(g)
+    base = dict(ct_geom_get_launch_shapes(G), b_rows=8, b_views=1)
+    ct_geom_set_launch_shapes(G, base)
+    x_general = gpu_B(G, y)
+    xo = OP.back_pixel(g, y).reshape(-1)
+    outs = []
+    for rows in (4, 8):
+        ct_geom_set_launch_shapes(G, dict(base, b_rows=rows, b_views=4))
+        xg = gpu_B(G, y)
+        assert rel(xg, xo) <= TOL
+        _check_B_entries(g, y, xg, xo)
+        assert rel(xg, x_general) <= 1e-6
+        outs.append(xg)
+    assert np.array_equal(outs[0], outs[1])
+
+
+NOT_FOUR_FOLD = {
+    "ragged_image": GEOMS["fan_ragged_50x33"],
+    "half_turn_scan": synth.fanflat2d(64, 72, 96, 200.0, 320.0, angle_range=math.pi),
+    "odd_side": synth.fanflat2d(63, 72, 96, 200.0, 320.0),
+    "parallel_beam": GEOMS["parallel_64_90x95"],
+}
+
+
+@pytest.mark.parametrize("name", sorted(NOT_FOUR_FOLD))
+def test_four_fold_backprojector_needs_the_symmetry(name):
+    """Geometries without the quarter-turn symmetry (a ragged image, views over half a turn, an
+    odd image side, parallel beam) refuse the four-fold shape and keep their shapes."""
+    from paper_2602_17892_gb300 import _binding as Bn
+    from paper_2602_17892_gb300 import ct_geom_get_launch_shapes, ct_geom_set_launch_shapes
+    G = gpu_geom(NOT_FOUR_FOLD[name])
+    base = ct_geom_get_launch_shapes(G)
+    with pytest.raises(Bn.CtError):
+        ct_geom_set_launch_shapes(G, dict(base, b_rows=8, b_views=4))
+    assert ct_geom_get_launch_shapes(G) == base
