@@ -235,7 +235,8 @@ typedef struct {
                         pixel-view pair has the same operations, with view k's cos and sin
                         for the rotated pixel, and the views are summed in another order, so
                         results agree with b_views 1 and 2 to FP32 rounding, not bit for bit
-                        (b_rows 4 or 8: 2 or 4 rows of orbits per block)                  */
+                        (b_rows 4, 8, 16: blocks of 32 x 2, 32 x 4, 32 x 2 orbits with the
+                        base views split into 2, 2, 4 parts)                              */
     int a_rays;      /* 3D Joseph A: detector rows per thread, 1 or 2 (two rays of one detector
                         column share their in-plane tap positions; the same operations per
                         sample, so results do not change); ignored in 2D                    */
@@ -245,7 +246,7 @@ typedef struct {
  * later calls on `g`.  2D: Joseph A with (threads, views) per block in (128, 1), (128, 2),
  * (128, 4), (256, 1), (256, 2), (256, 4), (512, 4), (512, 8); pixel-driven B with 4, 8 or 16
  * pixel rows per block and one view per loop iteration, or 4 or 8 rows and two, and for
- * geometries with the four-fold symmetry also the four-fold kernel with 4 or 8 rows.  3D: Joseph
+ * geometries with the four-fold symmetry also the four-fold kernel (b_rows 4, 8, 16).  3D: Joseph
  * (slab thickness, warp rows per block, detector rows per thread) in (16, 1, 1), (16, 4, 1),
  * (16, 8, 1), (64, 4, 1), (64, 8, 1), one pass over the whole volume with 1, 4 or 8 warp rows
  * and one detector row per thread, and (16, 4, 2), (64, 4, 2), one pass with 2 or 4 warp rows
@@ -261,7 +262,7 @@ ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_shapes *out
  * a_views >= 32 and a_views in {1, 2, 4, 8} (2D), a_slab >= 1 (3D; >= nz + 1 is one pass),
  * a_views in 1..8 warp rows (3D), a_rays in {1, 2} (3D), b_rows in {4, 8, 16}, b_views in
  * {1, 2, 4} (b_rows 16 only with b_views 1; b_views 4 only on a geometry with the four-fold
- * symmetry described at ct_launch_shapes, with b_rows 4 or 8); anything else
+ * symmetry described at ct_launch_shapes); anything else
  * returns CT_EINVAL and leaves `g` unchanged.  Host-only; shapes change the order of work, not a
  * sample's arithmetic. */
 ct_status ct_geom_set_launch_shapes(ct_geom *g, const ct_launch_shapes *shapes);

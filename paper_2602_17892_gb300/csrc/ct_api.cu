@@ -1374,10 +1374,9 @@ extern "C" ct_status ct_geom_set_launch_shapes(ct_geom *g, const ct_launch_shape
         return false;
     };
     // the paired-view B kernel is compiled for blocks of at most 256 threads (8 rows); the
-    // four-fold kernel (b_views 4) needs a b_rot4 geometry and b_rows 4 or 8
+    // four-fold kernel (b_views 4) needs a b_rot4 geometry
     bool ok = in(sh->b_rows, {4, 8, 16}) && in(sh->b_views, {1, 2, 4}) &&
-              !(sh->b_views == 2 && sh->b_rows > 8) &&
-              !(sh->b_views == 4 && !(g->dg.b_rot4 && sh->b_rows <= 8));
+              !(sh->b_views == 2 && sh->b_rows > 8) && !(sh->b_views == 4 && !g->dg.b_rot4);
     if (cone)
         ok = ok && sh->a_slab >= 1 && sh->a_views >= 1 && sh->a_views <= 8 && in(sh->a_rays, {1, 2});
     else
@@ -1470,7 +1469,7 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
                                   {1 << 20, 1, 1}, {1 << 20, 4, 1}, {1 << 20, 8, 1},
                                   {16, 4, 2}, {64, 4, 2}, {1 << 20, 2, 2}, {1 << 20, 4, 2}};
     // B: (pixel rows per block, views per iteration); b_views 4 = the four-fold kernel
-    static const int b2[7][2] = {{4, 1}, {8, 1}, {16, 1}, {4, 2}, {8, 2}, {4, 4}, {8, 4}};
+    static const int b2[8][2] = {{4, 1}, {8, 1}, {16, 1}, {4, 2}, {8, 2}, {4, 4}, {8, 4}, {16, 4}};
     auto fwd = [&]() { return launch_forward_proj(g, y, true, nullptr, s); };
     ct_status st;
     if (cone)
@@ -1485,7 +1484,7 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
             dg.tune_a_views = a2[c][1];
         });
     if (st == CT_OK && !cone)
-        st = time_best([&]() { return launch_back_proj(g, y, x, nullptr, s); }, dg.b_rot4 ? 7 : 5,
+        st = time_best([&]() { return launch_back_proj(g, y, x, nullptr, s); }, dg.b_rot4 ? 8 : 5,
                        [&](int c) {
             dg.tune_b_rows = b2[c][0];
             dg.tune_b_views = b2[c][1];

@@ -637,8 +637,9 @@ __global__ void __launch_bounds__(VP == 2 ? 256 : 512, VP == 2 ? 3 : 1) pixbp2d_
 // and, for each base view k < n/4, forms the four geometries g_j = (fj, w)(theta_k, p_j) once
 // (pe_2 = -pe_0 and pe_3 = -pe_1 exactly); pixel p_i takes view k + m n/4 at g_{(i+m) mod 4}:
 // 16 pixel-view pairs from 4 geometry evaluations.  The 16 gathers of a base view are issued
-// together, then the sums (pixel by pixel, m in order).  The base views are split between the
-// block's two z-halves, whose sums are added in shared memory.  The arithmetic of one
+// together, then the sums (pixel by pixel, m in order).  The base views are split into
+// blockDim.z consecutive parts (2 or 4), one per z layer of the block, whose sums are added in
+// shared memory in part order (more parts: more threads in flight and a shorter last wave).  The arithmetic of one
 // pixel-view pair is the one of pixbp2d_view; only the views' constants (those of view k, for
 // the rotated pixel) and the order of the sums differ from the general kernel.
 template <bool CLAMP>
@@ -664,7 +665,8 @@ __global__ void __launch_bounds__(256, 3) pixbp2d_rot4_kernel(
     const float cb = (float)((nd + 3) >> 1);
     const float gam = 0.5f * (float)(nd - 1) + 2.f - cb;
     const float clo = -cb, chi = (float)(nd + 2) - cb;
-    const int kz0 = threadIdx.z ? (q4 + 1) / 2 : 0, kz1 = threadIdx.z ? q4 : (q4 + 1) / 2;
+    const int nz = blockDim.z;
+    const int kz0 = (int)(((int64_t)q4 * threadIdx.z) / nz), kz1 = (int)(((int64_t)q4 * (threadIdx.z + 1)) / nz);
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     const uint64_t ybase = reinterpret_cast<uint64_t>(ypair) - 8ull * __float_as_uint(kFloor2p23);
     const uint64_t moff = 8ull * (uint64_t)q4 * (uint64_t)ld;     // bytes from row k to k + n/4
@@ -716,16 +718,18 @@ __global__ void __launch_bounds__(256, 3) pixbp2d_rot4_kernel(
             }
         }
     }
-    // the second half's sums join the first's
+    // the other parts' sums join part 0's, in part order
+    const int slots = 4 * 32 * blockDim.y;
     const int slot = 4 * ((int)threadIdx.y * 32 + (int)threadIdx.x);
-    if (threadIdx.z == 1) {
+    if (threadIdx.z > 0) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) red[slot + i] = acc[i];
+        for (int i = 0; i < 4; ++i) red[(threadIdx.z - 1) * slots + slot + i] = acc[i];
     }
     __syncthreads();
     if (threadIdx.z != 0 || !valid) return;
+    for (int z = 1; z < nz; ++z)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) acc[i] += red[slot + i];
+        for (int i = 0; i < 4; ++i) acc[i] += red[(z - 1) * slots + slot + i];
     const int M = N - 1;
     x[(int64_t)r * N + c] = acc[0] * k_w;
     x[(int64_t)(M - c) * N + r] = acc[1] * k_w;
@@ -738,10 +742,11 @@ static void launch_pixbp2d_rot4_t(const ct_geom *g, const float2 *ypad, float *x
                                   cudaStream_t s)
 {
     const DeviceGeom &d = g->dg;
-    const int half = d.nx >> 1, ry = d.tune_b_rows / 2;     // b_rows 4 or 8: 2 or 4 orbit rows
-    dim3 block(32, ry, 2), grid((half + 31) / 32, (half + ry - 1) / ry);
+    // b_rows 4, 8, 16: (orbit rows, view parts) per block (2, 2), (4, 2), (2, 4)
+    const int half = d.nx >> 1, ry = d.tune_b_rows == 8 ? 4 : 2, parts = d.tune_b_rows == 16 ? 4 : 2;
+    dim3 block(32, ry, parts), grid((half + 31) / 32, (half + ry - 1) / ry);
     const int q4 = d.n_views / 4;
-    const size_t smem = sizeof(float2) * (size_t)q4 + sizeof(float) * 4 * 32 * (size_t)ry;
+    const size_t smem = sizeof(float2) * (size_t)q4 + sizeof(float) * 4 * 32 * (size_t)ry * (parts - 1);
     pixbp2d_rot4_kernel<CLAMP><<<grid, block, smem, s>>>(
         d.views, q4, ypad, d.sino_ld, floor_chunk(d.sino_ld), d.ndu, d.nx, d.sid / d.h,
         d.sdd / d.pitch_u, d.h * d.sdd / d.pitch_u, x, stop);
@@ -769,8 +774,7 @@ cudaError_t launch_pixbp2d(const ct_geom *g, const float2 *ypad, float *x, const
     const bool fan = d.kind == CT_FANFLAT2D, clamp = !d.b_noclamp, two = d.tune_b_views == 2;
     if (two && d.tune_b_rows > 8) return cudaErrorInvalidConfiguration;   // 256-thread bound
     if (d.tune_b_views == 4) {
-        if (!fan || !d.b_rot4 || (d.tune_b_rows != 4 && d.tune_b_rows != 8))
-            return cudaErrorInvalidConfiguration;
+        if (!fan || !d.b_rot4) return cudaErrorInvalidConfiguration;
         clamp ? launch_pixbp2d_rot4_t<true>(g, ypad, x, stop, s)
               : launch_pixbp2d_rot4_t<false>(g, ypad, x, stop, s);
         return cudaGetLastError();

@@ -146,7 +146,7 @@ def test_paired_backprojector_rejects_tall_blocks():
 def test_four_fold_backprojector(name):
     """The four-fold B (b_views 4) on fan scans whose views come in quadruples a quarter turn
     apart: each pixel within its element-wise FP32 bound of the oracle, within FP32 rounding of
-    the general kernel, and bitwise the same for both block heights."""
+    the general kernel, and bitwise the same for both block heights with two view parts."""
     from paper_2602_17892_gb300 import ct_geom_get_launch_shapes, ct_geom_set_launch_shapes
     g = GEOMS["fan_64"] if name == "fan_64" else synth.fan512_case()["geom"]
     y = f32(np.abs(synth.standard_normal(g.m, 41)) + 1.0)
@@ -156,14 +156,15 @@ def test_four_fold_backprojector(name):
     x_general = gpu_B(G, y)
     xo = OP.back_pixel(g, y).reshape(-1)
     outs = []
-    for rows in (4, 8):
+    for rows in (4, 8, 16):
         ct_geom_set_launch_shapes(G, dict(base, b_rows=rows, b_views=4))
         xg = gpu_B(G, y)
         assert rel(xg, xo) <= TOL
         _check_B_entries(g, y, xg, xo)
         assert rel(xg, x_general) <= 1e-6
         outs.append(xg)
-    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[1])          # the same two view parts
+    assert rel(outs[2], outs[0]) <= 1e-6             # four parts: another order of the sums
 
 
 NOT_FOUR_FOLD = {
