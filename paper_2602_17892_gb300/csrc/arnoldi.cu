@@ -518,6 +518,8 @@ __global__ void __launch_bounds__(kThreads, 2) cgs_tile_kernel(const __grid_cons
             else a.aux[1] = 1.0 / nrm;
         }
         if (bad || brk) return;
+        // the solve's last step needs h_{k+1,k} but not w_{k+1}: launched as one block without it
+        if (a.wnext == nullptr) return;
         inv_nu = (float)(1.0 / nrm);
     } else if (MODE == T_UPD_DOTS) {
         for (int i = tid; i < nvec; i += kThreads) scoef[i] = (float)a.coef[i];
@@ -777,7 +779,7 @@ static bool tile_eligible(int64_t ld, int k, const ArnoldiScratch &sc)
 template <typename T>
 static bool arnoldi_step_tiled(void *W, int64_t ld, int k, float *q, double *hcol,
                                const ArnoldiScratch &sc, double *aux, int *stop, int step,
-                               float *cur, cudaStream_t s, cudaError_t &err)
+                               float *cur, cudaStream_t s, cudaError_t &err, bool next)
 {
     const int nvec = k + 1;
     int stages, per_sm;
@@ -801,9 +803,9 @@ static bool arnoldi_step_tiled(void *W, int64_t ld, int k, float *q, double *hco
     cgs_tile_kernel<T_UPD_DOTS, T><<<blocks, kThreads, smem, s>>>(wmap, a);
     cgs_tile_reduce_kernel<T_UPD_DOTS><<<rblocks, kThreads, 0, s>>>(a, blocks);
     a.coef = h2; a.coef_out = nullptr;
-    a.wnext = static_cast<char *>(W) + (size_t)(k + 1) * ld * sizeof(T);
-    a.cur = cur;
-    cgs_tile_kernel<T_UPD_SCALE, T><<<blocks, kThreads, smem, s>>>(wmap, a);
+    a.wnext = next ? static_cast<char *>(W) + (size_t)(k + 1) * ld * sizeof(T) : nullptr;
+    a.cur = next ? cur : nullptr;
+    cgs_tile_kernel<T_UPD_SCALE, T><<<next ? blocks : 1, kThreads, smem, s>>>(wmap, a);
     err = cudaGetLastError();
     return true;
 }
@@ -814,10 +816,12 @@ static bool arnoldi_step_tiled(void *W, int64_t ld, int k, float *q, double *hco
 template <typename T>
 static cudaError_t arnoldi_step_t(void *W, int64_t L, int64_t ld, int k, float *q, double *hcol,
                                   const ArnoldiScratch &sc, double *aux, int *stop, int step,
-                                  bool reorth, float *cur, bool q_padded, cudaStream_t s)
+                                  bool reorth, float *cur, bool q_padded, cudaStream_t s,
+                                  bool next = true)
 {
     cudaError_t err = cudaSuccess;
-    if (reorth && q_padded && arnoldi_step_tiled<T>(W, ld, k, q, hcol, sc, aux, stop, step, cur, s, err))
+    if (reorth && q_padded &&
+        arnoldi_step_tiled<T>(W, ld, k, q, hcol, sc, aux, stop, step, cur, s, err, next))
         return err;
     const int64_t L4 = L / 4;
     const int nvec = k + 1;
@@ -865,18 +869,19 @@ cudaError_t arnoldi_step_dev(float *W, int64_t L, int64_t ld, int k, float *q, d
 
 cudaError_t arnoldi_step_basis(int basis, void *W, int64_t L, int64_t ld, int k, float *q,
                                double *hcol, const ArnoldiScratch &sc, double *aux, int *stop,
-                               int step, bool reorth, float *cur, bool q_padded, cudaStream_t s)
+                               int step, bool reorth, float *cur, bool q_padded, cudaStream_t s,
+                               bool next)
 {
     switch (basis) {
     case CT_BASIS_BF16:
         return arnoldi_step_t<__nv_bfloat16>(W, L, ld, k, q, hcol, sc, aux, stop, step, reorth,
-                                             cur, q_padded, s);
+                                             cur, q_padded, s, next);
     case CT_BASIS_F16:
         return arnoldi_step_t<__half>(W, L, ld, k, q, hcol, sc, aux, stop, step, reorth, cur,
-                                      q_padded, s);
+                                      q_padded, s, next);
     default:
         return arnoldi_step_t<float>(W, L, ld, k, q, hcol, sc, aux, stop, step, reorth, cur,
-                                     q_padded, s);
+                                     q_padded, s, next);
     }
 }
 

@@ -47,10 +47,12 @@ cudaError_t launch_combine(const float *W, int64_t L, int64_t ld, const double *
                            int max_blocks, cudaStream_t s);
 cudaError_t launch_rsub(const float *b, float *r, int64_t L, int max_blocks, cudaStream_t s);
 // q_padded: q holds ld floats with a zero tail beyond L (the solver's own vectors), which
-// allows the tiled path when ld is a multiple of 128
+// allows the tiled path when ld is a multiple of 128; next = false (a solve's last step): the
+// tiled path records h_{k+1,k} without writing w_{k+1}, which no later step reads
 cudaError_t arnoldi_step_basis(int basis, void *W, int64_t L, int64_t ld, int k, float *q,
                                double *hcol, const ArnoldiScratch &sc, double *aux, int *stop,
-                               int step, bool reorth, float *cur, bool q_padded, cudaStream_t s);
+                               int step, bool reorth, float *cur, bool q_padded, cudaStream_t s,
+                               bool next);
 int arnoldi_step_launches(int basis, int64_t ld, int k, const ArnoldiScratch &sc, bool reorth,
                           bool q_padded);
 cudaError_t normalize_first_basis(int basis, const float *r, int64_t L, void *w0,
@@ -935,7 +937,8 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
             CT_PHASE(CT_PH_ARNOLDI, arnoldi_step_launches(o->basis, ld, k, sc, o->reorth != 0, true),
                      s);
             CT_CUDA(arnoldi_step_basis(o->basis, w->W, L, ld, k, w->q, w->H + (int64_t)k * ldh,
-                                       sc, w->aux, w->stop, step, o->reorth != 0, w->cur, true, s));
+                                       sc, w->aux, w->stop, step, o->reorth != 0, w->cur, true, s,
+                                       step < K));
         }
         if ((st = stop_checkpoint(w, o, s, dp_target, step, checked, nc)) != CT_OK) return st;
     }
@@ -1032,7 +1035,8 @@ static ct_status enqueue_ba(ct_geom *g, const float *b_dev, const float *x0_dev,
             CT_PHASE(CT_PH_ARNOLDI, arnoldi_step_launches(o->basis, ld, k, sc, o->reorth != 0, true),
                      s);
             CT_CUDA(arnoldi_step_basis(o->basis, w->W, L, ld, k, w->q, w->H + (int64_t)k * ldh,
-                                       sc, w->aux, w->stop, step, o->reorth != 0, w->cur, true, s));
+                                       sc, w->aux, w->stop, step, o->reorth != 0, w->cur, true, s,
+                                       step < K));
         }
         if ((st = stop_checkpoint(w, o, s, dp_target, step, checked, nc)) != CT_OK) return st;
     }
