@@ -878,32 +878,59 @@ static ct_status run_small_solves(Workspace *w, const ct_hybrid_opts *o, cudaStr
     return CT_OK;
 }
 
-// Algorithm 1, enqueued on s without any host synchronisation (graph-capturable once the
-// workspace exists); the caller reads the results with read_info after synchronising.
-static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev, float *x_dev,
-                            const ct_hybrid_opts *o, cudaStream_t s, Workspace **wout,
-                            bool u0_padded = false)
+// One hybrid solve (Algorithm 1 or 2) enqueued in pieces: set-up, then per step the operator
+// phase (the projectors and their layouts, w_k -> q) and the Arnoldi phase (Eq. (Hessenberg) and
+// the stopping checkpoint), then the small solves and the iterate.  enqueue_ab / enqueue_ba run
+// the pieces in order on one stream; a batch of two solves interleaves them across its streams.
+struct SolveRun {
+    ct_geom *g = nullptr;
+    const float *b = nullptr;
+    const float *init = nullptr;    // AB: u0 (padded when u0_padded), BA: x0; may be null
+    float *x = nullptr;
+    const ct_hybrid_opts *o = nullptr;
+    cudaStream_t s = nullptr;
+    int method = 0;
+    bool u0_padded = false;
+    Workspace *w = nullptr;
+    int K = 0, ldh = 0, checked = 0;
+    int64_t L = 0, ld = 0;
+    ArnoldiScratch sc{nullptr, nullptr, 0, 0};
+    double dp_target = 0.0;
+    NcpCtx nc;
+};
+
+// Algorithm 1 (AB) / 2 (BA) set-up, enqueued on r.s without any host synchronisation
+// (graph-capturable once the workspace exists); the caller reads the results with read_info
+// after synchronising.
+static ct_status run_begin(SolveRun &r)
 {
     ct_status st;
-    Workspace *w;
-    if ((st = ws_get(g, 0, o->max_iters, o->basis, &w)) != CT_OK) return st;
-    *wout = w;
-    const int K = o->max_iters;
-    const int64_t L = w->L, ld = w->ld;
-    ArnoldiScratch sc{w->partial, w->counter, gs_blocks(), w->K};
-    const double dp_target = o->tau * o->noise_norm;
+    const ct_hybrid_opts *o = r.o;
+    ct_geom *g = r.g;
+    cudaStream_t s = r.s;
+    if ((st = ws_get(g, r.method, o->max_iters, o->basis, &r.w)) != CT_OK) return st;
+    Workspace *w = r.w;
+    r.K = o->max_iters;
+    r.L = w->L;
+    r.ld = w->ld;
+    r.ldh = w->K + 1;
+    r.sc = ArnoldiScratch{w->partial, w->counter, gs_blocks(), w->K};
+    r.dp_target = o->tau * o->noise_norm;
+    const int64_t L = r.L;
+    const ArnoldiScratch &sc = r.sc;
     if (o->stop_rule == CT_STOP_NCP && (st = ncp_ready(g, w)) != CT_OK) return st;
     CT_CUDA(cudaMemsetAsync(w->stop, 0, 2 * sizeof(int), s));
     CT_CUDA(cudaMemsetAsync(w->counter, 0, 4 * sizeof(unsigned), s));
-    CT_CUDA(cudaMemsetAsync(w->path, 0, sizeof(int) * K, s));
+    CT_CUDA(cudaMemsetAsync(w->path, 0, sizeof(int) * r.K, s));
     if (w->ncp) CT_CUDA(cudaMemsetAsync(w->ncp, 0xff, sizeof(double) * w->K, s));   // NaN
-    NcpCtx nc;
-    nc.g = g; nc.method = 0; nc.b = b_dev;
-    nc.x0 = u0_dev ? (u0_padded ? u0_dev : w->sino) : nullptr;   // padded u0 (kept in sino)
-    // Algorithm 1 set-up: x0 = B u0, r0 = b - A x0, w1 = r0 / ||r0||
-    {
+    r.nc.g = g; r.nc.method = r.method; r.nc.b = r.b;
+    if (r.method == 0) {
+        const float *u0_dev = r.init;
+        const bool u0_padded = r.u0_padded;
+        r.nc.x0 = u0_dev ? (u0_padded ? u0_dev : w->sino) : nullptr;   // padded u0 (kept in sino)
+        // Algorithm 1 set-up: x0 = B u0, r0 = b - A x0, w1 = r0 / ||r0||
         CT_PHASE(CT_PH_OTHER, u0_dev ? 8 : 3, s);
-        CT_CUDA(launch_pad_sino(g, b_dev, w->vec, s));
+        CT_CUDA(launch_pad_sino(g, r.b, w->vec, s));
         if (u0_dev) {
             if (!u0_padded) CT_CUDA(launch_pad_sino(g, u0_dev, w->sino, s));
             CT_CUDA(launch_back_proj(g, u0_padded ? u0_dev : w->sino, w->img, nullptr, s));
@@ -914,87 +941,13 @@ static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev,
         } else {
             CT_CUDA(normalize_first_basis(o->basis, w->vec, L, w->W, sc, w->aux, w->stop, w->cur, s));
         }
-    }
-    const int ldh = w->K + 1;
-    int checked = 0;                 // steps whose hybrid step ran (stopping rules)
-    for (int step = 1; step <= K; ++step) {
-        const int k = step - 1;
-        const float *wk = w->cur ? w->cur : static_cast<float *>(w->W) + (int64_t)k * ld;
-        {
-            CT_PHASE(CT_PH_BACK, 2, s);   // pair copy + B, or A^T scatter + rounding
-            CT_CUDA(launch_back_proj(g, wk, w->img, w->stop, s));       // q = A B w_k: B w_k
-        }
-        {
-            CT_PHASE(CT_PH_LAYOUT, 1, s);
-            CT_CUDA(launch_image_pairs(g, w->img, w->stop, s));
-        }
-        {
-            CT_PHASE(CT_PH_FORWARD, fwd_launches(g), s);
-            CT_CUDA(launch_forward_proj(g, w->q, true, w->stop, s));   //          A (B w_k)
-        }
-        {
-            // Arnoldi relation, Eq. (Hessenberg): column k of H_k and w_{k+1}
-            CT_PHASE(CT_PH_ARNOLDI, arnoldi_step_launches(o->basis, ld, k, sc, o->reorth != 0, true),
-                     s);
-            CT_CUDA(arnoldi_step_basis(o->basis, w->W, L, ld, k, w->q, w->H + (int64_t)k * ldh,
-                                       sc, w->aux, w->stop, step, o->reorth != 0, w->cur, true, s,
-                                       step < K));
-        }
-        if ((st = stop_checkpoint(w, o, s, dp_target, step, checked, nc)) != CT_OK) return st;
-    }
-    if ((st = run_small_solves(w, o, s, dp_target)) != CT_OK) return st;   // Eq. (hybrid_proj)
-    // the hybrid iterate at the last (or stopping) step: x = x0 + B W y = B (u0 + W y)
-    {
-        CT_PHASE(CT_PH_OTHER, u0_dev ? 2 : 1, s);
-        if (u0_dev && !u0_padded) CT_CUDA(launch_pad_sino(g, u0_dev, w->sino, s));
-        CT_CUDA(launch_combine_basis(o->basis, w->W, L, ld, w->Y, K, w->K, w->stop, 0,
-                                     u0_dev ? (u0_padded ? u0_dev : w->sino) : nullptr, w->q,
-                                     kMaxBlocks, s));
-    }
-    {
-        CT_PHASE(CT_PH_BACK, 2, s);   // pair copy + B, or A^T scatter + rounding
-        CT_CUDA(launch_back_proj(g, w->q, x_dev, nullptr, s));
-    }
-    return CT_OK;
-}
-
-extern "C" ct_status ab_gmres_hybrid(ct_geom *g, const float *b_dev, const float *u0_dev,
-                                     float *x_dev, const ct_hybrid_opts *o, ct_hybrid_info *info,
-                                     ct_stream_t stream)
-{
-    if (!g || !b_dev || !x_dev) return einval("ab_gmres_hybrid: null argument");
-    ct_status st = check_opts(o);
-    if (st != CT_OK) return st;
-    cudaStream_t s = (cudaStream_t)stream;
-    Workspace *w = nullptr;
-    if ((st = enqueue_ab(g, b_dev, u0_dev, x_dev, o, s, &w)) != CT_OK) return st;
-    return finish(w, o, info, s);
-}
-
-// Algorithm 2, enqueued on s without host synchronisation (see enqueue_ab).
-static ct_status enqueue_ba(ct_geom *g, const float *b_dev, const float *x0_dev, float *x_dev,
-                            const ct_hybrid_opts *o, cudaStream_t s, Workspace **wout)
-{
-    ct_status st;
-    Workspace *w;
-    if ((st = ws_get(g, 1, o->max_iters, o->basis, &w)) != CT_OK) return st;
-    *wout = w;
-    const int K = o->max_iters;
-    const int64_t L = w->L, ld = w->ld;
-    const int64_t msino = (int64_t)g->dg.n_views * g->dg.sino_view_ld;
-    ArnoldiScratch sc{w->partial, w->counter, gs_blocks(), w->K};
-    const double dp_target = o->tau * o->noise_norm;
-    if (o->stop_rule == CT_STOP_NCP && (st = ncp_ready(g, w)) != CT_OK) return st;
-    CT_CUDA(cudaMemsetAsync(w->stop, 0, 2 * sizeof(int), s));
-    CT_CUDA(cudaMemsetAsync(w->counter, 0, 4 * sizeof(unsigned), s));
-    CT_CUDA(cudaMemsetAsync(w->path, 0, sizeof(int) * K, s));
-    if (w->ncp) CT_CUDA(cudaMemsetAsync(w->ncp, 0xff, sizeof(double) * w->K, s));   // NaN
-    NcpCtx nc;
-    nc.g = g; nc.method = 1; nc.b = b_dev; nc.x0 = x0_dev;
-    // Algorithm 2 set-up: r0 = B (b - A x0), w1 = r0 / ||r0||
-    {
+    } else {
+        const float *x0_dev = r.init;
+        const int64_t msino = (int64_t)g->dg.n_views * g->dg.sino_view_ld;
+        r.nc.x0 = x0_dev;
+        // Algorithm 2 set-up: r0 = B (b - A x0), w1 = r0 / ||r0||
         CT_PHASE(CT_PH_OTHER, x0_dev ? 7 : 4, s);
-        CT_CUDA(launch_pad_sino(g, b_dev, w->sino, s));
+        CT_CUDA(launch_pad_sino(g, r.b, w->sino, s));
         if (x0_dev) {
             if (!w->sino2) {            // b - A x0 needs a second sinogram (q is image-sized)
                 cudaError_t e = dalloc(&w->sino2, (size_t)msino);
@@ -1014,11 +967,31 @@ static ct_status enqueue_ba(ct_geom *g, const float *b_dev, const float *x0_dev,
         }
         CT_CUDA(normalize_first_basis(o->basis, w->vec, L, w->W, sc, w->aux, w->stop, w->cur, s));
     }
-    const int ldh = w->K + 1;
-    int checked = 0;                 // steps whose hybrid step ran (stopping rules)
-    for (int step = 1; step <= K; ++step) {
-        const int k = step - 1;
-        const float *wk = w->cur ? w->cur : static_cast<float *>(w->W) + (int64_t)k * ld;
+    return CT_OK;
+}
+
+// the operator phase of step `step`: q = A B w_k (AB) or q = B A w_k (BA)
+static ct_status run_operator(SolveRun &r, int step)
+{
+    Workspace *w = r.w;
+    ct_geom *g = r.g;
+    cudaStream_t s = r.s;
+    const int k = step - 1;
+    const float *wk = w->cur ? w->cur : static_cast<float *>(w->W) + (int64_t)k * r.ld;
+    if (r.method == 0) {
+        {
+            CT_PHASE(CT_PH_BACK, 2, s);   // pair copy + B, or A^T scatter + rounding
+            CT_CUDA(launch_back_proj(g, wk, w->img, w->stop, s));       // q = A B w_k: B w_k
+        }
+        {
+            CT_PHASE(CT_PH_LAYOUT, 1, s);
+            CT_CUDA(launch_image_pairs(g, w->img, w->stop, s));
+        }
+        {
+            CT_PHASE(CT_PH_FORWARD, fwd_launches(g), s);
+            CT_CUDA(launch_forward_proj(g, w->q, true, w->stop, s));   //          A (B w_k)
+        }
+    } else {
         {
             CT_PHASE(CT_PH_LAYOUT, 1, s);
             CT_CUDA(launch_image_pairs(g, wk, w->stop, s));           // q = B A w_k: A w_k
@@ -1031,28 +1004,111 @@ static ct_status enqueue_ba(ct_geom *g, const float *b_dev, const float *x0_dev,
             CT_PHASE(CT_PH_BACK, 2, s);   // pair copy + B, or A^T scatter + rounding
             CT_CUDA(launch_back_proj(g, w->sino, w->q, w->stop, s));     //          B (A w_k)
         }
-        {
-            CT_PHASE(CT_PH_ARNOLDI, arnoldi_step_launches(o->basis, ld, k, sc, o->reorth != 0, true),
-                     s);
-            CT_CUDA(arnoldi_step_basis(o->basis, w->W, L, ld, k, w->q, w->H + (int64_t)k * ldh,
-                                       sc, w->aux, w->stop, step, o->reorth != 0, w->cur, true, s,
-                                       step < K));
-        }
-        if ((st = stop_checkpoint(w, o, s, dp_target, step, checked, nc)) != CT_OK) return st;
     }
-    if ((st = run_small_solves(w, o, s, dp_target)) != CT_OK) return st;   // Eq. (hybrid_proj)
-    // the hybrid iterate: x = x0 + W y
+    return CT_OK;
+}
+
+// the Arnoldi phase of step `step`: column k of H_k and w_{k+1} (Eq. (Hessenberg)), then the
+// stopping checkpoint
+static ct_status run_arnoldi(SolveRun &r, int step)
+{
+    Workspace *w = r.w;
+    const ct_hybrid_opts *o = r.o;
+    cudaStream_t s = r.s;
+    const int k = step - 1;
     {
+        CT_PHASE(CT_PH_ARNOLDI, arnoldi_step_launches(o->basis, r.ld, k, r.sc, o->reorth != 0, true),
+                 s);
+        CT_CUDA(arnoldi_step_basis(o->basis, w->W, r.L, r.ld, k, w->q, w->H + (int64_t)k * r.ldh,
+                                   r.sc, w->aux, w->stop, step, o->reorth != 0, w->cur, true, s,
+                                   step < r.K));
+    }
+    return stop_checkpoint(w, o, s, r.dp_target, step, r.checked, r.nc);
+}
+
+// the hybrid step (Eq. (hybrid_proj)) and the iterate at the last (or stopping) step:
+// AB x = x0 + B W y = B (u0 + W y), BA x = x0 + W y
+static ct_status run_end(SolveRun &r)
+{
+    ct_status st;
+    Workspace *w = r.w;
+    ct_geom *g = r.g;
+    const ct_hybrid_opts *o = r.o;
+    cudaStream_t s = r.s;
+    const int64_t L = r.L, ld = r.ld;
+    if ((st = run_small_solves(w, o, s, r.dp_target)) != CT_OK) return st;
+    if (r.method == 0) {
+        const float *u0_dev = r.init;
+        const bool u0_padded = r.u0_padded;
+        {
+            CT_PHASE(CT_PH_OTHER, u0_dev ? 2 : 1, s);
+            if (u0_dev && !u0_padded) CT_CUDA(launch_pad_sino(g, u0_dev, w->sino, s));
+            CT_CUDA(launch_combine_basis(o->basis, w->W, L, ld, w->Y, r.K, w->K, w->stop, 0,
+                                         u0_dev ? (u0_padded ? u0_dev : w->sino) : nullptr, w->q,
+                                         kMaxBlocks, s));
+        }
+        {
+            CT_PHASE(CT_PH_BACK, 2, s);   // pair copy + B, or A^T scatter + rounding
+            CT_CUDA(launch_back_proj(g, w->q, r.x, nullptr, s));
+        }
+    } else {
+        const float *x0_dev = r.init;
         CT_PHASE(CT_PH_OTHER, 1, s);
         if (x0_dev) {
             CT_CUDA(cudaMemsetAsync(w->img, 0, sizeof(float) * L, s));
             CT_CUDA(cudaMemcpyAsync(w->img, x0_dev, sizeof(float) * g->n, cudaMemcpyDeviceToDevice, s));
         }
-        CT_CUDA(launch_combine_basis(o->basis, w->W, L, ld, w->Y, K, w->K, w->stop, 0,
+        CT_CUDA(launch_combine_basis(o->basis, w->W, L, ld, w->Y, r.K, w->K, w->stop, 0,
                                      x0_dev ? w->img : nullptr, w->q, kMaxBlocks, s));
-        CT_CUDA(cudaMemcpyAsync(x_dev, w->q, sizeof(float) * g->n, cudaMemcpyDeviceToDevice, s));
+        CT_CUDA(cudaMemcpyAsync(r.x, w->q, sizeof(float) * g->n, cudaMemcpyDeviceToDevice, s));
     }
     return CT_OK;
+}
+
+static ct_status run_all(SolveRun &r, Workspace **wout)
+{
+    ct_status st = run_begin(r);
+    *wout = r.w;
+    if (st != CT_OK) return st;
+    for (int step = 1; step <= r.K; ++step) {
+        if ((st = run_operator(r, step)) != CT_OK) return st;
+        if ((st = run_arnoldi(r, step)) != CT_OK) return st;
+    }
+    return run_end(r);
+}
+
+// Algorithm 1, enqueued on s without any host synchronisation (graph-capturable once the
+// workspace exists); the caller reads the results with read_info after synchronising.
+static ct_status enqueue_ab(ct_geom *g, const float *b_dev, const float *u0_dev, float *x_dev,
+                            const ct_hybrid_opts *o, cudaStream_t s, Workspace **wout,
+                            bool u0_padded = false)
+{
+    SolveRun r;
+    r.g = g; r.b = b_dev; r.init = u0_dev; r.x = x_dev; r.o = o; r.s = s; r.method = 0;
+    r.u0_padded = u0_padded;
+    return run_all(r, wout);
+}
+
+extern "C" ct_status ab_gmres_hybrid(ct_geom *g, const float *b_dev, const float *u0_dev,
+                                     float *x_dev, const ct_hybrid_opts *o, ct_hybrid_info *info,
+                                     ct_stream_t stream)
+{
+    if (!g || !b_dev || !x_dev) return einval("ab_gmres_hybrid: null argument");
+    ct_status st = check_opts(o);
+    if (st != CT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace *w = nullptr;
+    if ((st = enqueue_ab(g, b_dev, u0_dev, x_dev, o, s, &w)) != CT_OK) return st;
+    return finish(w, o, info, s);
+}
+
+// Algorithm 2, enqueued on s without host synchronisation (see enqueue_ab).
+static ct_status enqueue_ba(ct_geom *g, const float *b_dev, const float *x0_dev, float *x_dev,
+                            const ct_hybrid_opts *o, cudaStream_t s, Workspace **wout)
+{
+    SolveRun r;
+    r.g = g; r.b = b_dev; r.init = x0_dev; r.x = x_dev; r.o = o; r.s = s; r.method = 1;
+    return run_all(r, wout);
 }
 
 extern "C" ct_status ba_gmres_hybrid(ct_geom *g, const float *b_dev, const float *x0_dev,
@@ -1523,6 +1579,7 @@ struct ct_batch {
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> join;
     cudaEvent_t fork = nullptr;
+    cudaEvent_t opdone[2] = {nullptr, nullptr};   // two-solve batches: the operator phases
     cudaStream_t cap = nullptr;         // capture stream (the legacy default stream cannot capture)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -1541,6 +1598,7 @@ extern "C" void ct_batch_destroy(ct_batch *bt)
     for (auto s : bt->streams) if (s) cudaStreamDestroy(s);
     for (auto e : bt->join) if (e) cudaEventDestroy(e);
     if (bt->fork) cudaEventDestroy(bt->fork);
+    for (auto e : bt->opdone) if (e) cudaEventDestroy(e);
     if (bt->cap) cudaStreamDestroy(bt->cap);
     delete bt;
 }
@@ -1590,6 +1648,8 @@ extern "C" ct_status ct_batch_create(int n_prob, ct_geom *const *geoms, const in
     bt->streams.assign(n_prob, nullptr);
     bt->join.assign(n_prob, nullptr);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bt->fork, cudaEventDisableTiming);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&bt->opdone[i], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking);
     for (int i = 0; i < n_prob && e == cudaSuccess; ++i) {
         e = cudaStreamCreateWithFlags(&bt->streams[i], cudaStreamNonBlocking);
@@ -1620,7 +1680,37 @@ static ct_status batch_capture(ct_batch *bt)
         g_gs_block_cap = std::min(sms, kMaxBlocks);
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) e = cudaEventRecord(bt->fork, s);
-    for (int i = 0; i < bt->n && e == cudaSuccess && st == CT_OK; ++i) {
+    if (bt->n == 2) {
+        // two solves: their steps alternate operator phases (each waits for the other solve's
+        // last one), so one solve's projectors run beside the other's HBM-bound Gram-Schmidt
+        // passes instead of beside its projectors
+        ct_hybrid_opts oi[2];
+        SolveRun r[2];
+        for (int i = 0; i < 2; ++i) {
+            oi[i] = bt->o;
+            oi[i].noise_norm = bt->noise[i];
+            r[i].g = bt->g[i]; r[i].b = bt->b_ptrs[i]; r[i].x = bt->x_ptrs[i]; r[i].o = &oi[i];
+            r[i].s = bt->streams[i]; r[i].method = bt->method[i];
+        }
+        for (int i = 0; i < 2 && e == cudaSuccess && st == CT_OK; ++i) {
+            e = cudaStreamWaitEvent(r[i].s, bt->fork, 0);
+            if (e == cudaSuccess) st = run_begin(r[i]);
+            bt->ws[i] = r[i].w;
+        }
+        for (int step = 1; step <= bt->o.max_iters && e == cudaSuccess && st == CT_OK; ++step)
+            for (int i = 0; i < 2 && e == cudaSuccess && st == CT_OK; ++i) {
+                if (step > 1 || i == 1) e = cudaStreamWaitEvent(r[i].s, bt->opdone[1 - i], 0);
+                if (e == cudaSuccess) st = run_operator(r[i], step);
+                if (st == CT_OK && e == cudaSuccess) e = cudaEventRecord(bt->opdone[i], r[i].s);
+                if (st == CT_OK && e == cudaSuccess) st = run_arnoldi(r[i], step);
+            }
+        for (int i = 0; i < 2 && e == cudaSuccess && st == CT_OK; ++i) {
+            st = run_end(r[i]);
+            if (st == CT_OK) e = cudaEventRecord(bt->join[i], r[i].s);
+            if (st == CT_OK && e == cudaSuccess) e = cudaStreamWaitEvent(s, bt->join[i], 0);
+        }
+    }
+    for (int i = 0; bt->n != 2 && i < bt->n && e == cudaSuccess && st == CT_OK; ++i) {
         cudaStream_t si = bt->streams[i];
         e = cudaStreamWaitEvent(si, bt->fork, 0);
         if (e != cudaSuccess) break;
