@@ -413,6 +413,20 @@ __device__ __forceinline__ void tensor_g2s(void *dst, const CUtensorMap *map, in
                  "r"(smem_u32(bar)) : "memory");
 }
 
+// The same load with an L2 evict-first policy: the basis stream (hundreds of MB per step)
+// then gives way in L2 to the projectors' operands (the pair layouts and the ray table, about
+// 11 MB at the 512^2 fan workload) that the other solve of a batch reads at the same time
+// (measured: 39.8 -> 39.5 ms a step of the AB + BA batch; the passes themselves not slower).
+__device__ __forceinline__ void tensor_g2s_ef(void *dst, const CUtensorMap *map, int x, uint64_t *bar)
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+                 " [%0], [%1, {%2, %3}], [%4], %5;"
+                 ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(0),
+                 "r"(smem_u32(bar)), "l"(pol) : "memory");
+}
+
 // waits for phase `parity` of `bar` to complete; false after about `limit` cycles
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long long limit)
 {
@@ -542,7 +556,7 @@ __global__ void __launch_bounds__(kThreads, 2) cgs_tile_kernel(const __grid_cons
         unsigned char *dst = tsm + (size_t)st * stage_bytes;
         const int e0 = tile_of(i) * kTileElems;
         mbar_expect_tx(&bars[st], (unsigned)stage_bytes);
-        tensor_g2s(dst, &wmap, e0, &bars[st]);
+        tensor_g2s_ef(dst, &wmap, e0, &bars[st]);
         bulk_g2s(dst + (size_t)nvec * seg, a.q + e0, kTileElems * 4, &bars[st]);
     };
     const long long wlim = g_wait_cycles;
