@@ -391,6 +391,34 @@ static RayXY make_ray_xy(const ct_geom_desc *d, int view, int iu)
     r.packed = (uint32_t)lo | ((uint32_t)hi << 15) | ((uint32_t)axis << 30);
     r.rda = 1.0 / Da;
     r.sa_h = Sa / h;
+    // z part for the kernels' FP32 set-up (pairs hi + lo of the FP64 factors) and the rows the
+    // kernels drive along x or y: |v| |rda| <= 1 in the same FP64 expression as before, an
+    // interval of rows around the detector's centre row (|v| grows away from it)
+    const double P = d->pitch_v * r.rda, Q = r.sa_h * P;
+    r.zp_hi = (float)P;
+    r.zp_lo = (float)(P - (double)r.zp_hi);
+    r.zq_hi = (float)Q;
+    r.zq_lo = (float)(Q - (double)r.zq_hi);
+    const int ndv = d->n_det_v;
+    auto xy_driven = [&](int iv) {
+        const double v = (iv - 0.5 * (ndv - 1)) * d->pitch_v;
+        return !(fabs(v) * fabs(r.rda) > 1.0);
+    };
+    const int cen = (ndv - 1) / 2;
+    int lo_iv = cen, hi_iv = cen;
+    if (!xy_driven(cen)) {
+        lo_iv = 1; hi_iv = 0;                      // no row (a pitch this coarse cannot happen)
+    } else {
+        int a = 0, b = cen;                        // smallest row of the interval
+        while (a < b) { const int m = (a + b) / 2; if (xy_driven(m)) b = m; else a = m + 1; }
+        lo_iv = a;
+        a = cen; b = ndv - 1;                      // largest row of the interval
+        while (a < b) { const int m = (a + b + 1) / 2; if (xy_driven(m)) a = m; else b = m - 1; }
+        hi_iv = a;
+    }
+    r.iv_lo = lo_iv;
+    r.iv_hi = hi_iv;
+    r.pad0 = r.pad1 = 0;
     r.sx_h = Sx / h;
     r.sy_h = Sy / h;
     r.dx = Dx;

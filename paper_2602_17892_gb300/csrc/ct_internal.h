@@ -47,6 +47,12 @@ struct __align__(16) RayXY {
                           // (index units) and its change per plane
     float dxy2;           // (Dx^2 + Dy^2) / Da^2
     uint32_t packed;      // t_lo (bits 0-14) | t_hi (bits 15-29) | axis (bits 30-31: 0 x, 1 y)
+    // the z part in FP32 for the row offset c = iv - (ndv - 1) / 2 (exact in FP32):
+    // z slope pitch_v / Da and z at the central plane (nz - 1) / 2 - c pitch_v Sa / (h Da), each
+    // factor as an FP32 pair hi + lo of its FP64 value; rows iv in [iv_lo, iv_hi] are driven
+    // along x or y (the FP64 test |v| |1 / Da| <= 1, evaluated on the host), the others along z
+    float zp_hi, zp_lo, zq_hi, zq_lo;
+    int32_t iv_lo, iv_hi, pad0, pad1;
     double rda;           // 1 / Da
     double sa_h;          // source coordinate on the driving axis / h
     double sx_h, sy_h;    // source / h      (rays driven along z)

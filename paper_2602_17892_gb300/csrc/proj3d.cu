@@ -87,6 +87,21 @@ __device__ __forceinline__ Ray3D setup_ray3d(const RayXY &R, int iv, int ndv, do
     return q;
 }
 
+// z slope and z at the central driving plane of row iv of a column (x- or y-driven rows), in
+// FP32 from the table's pairs: with c = iv - (ndv - 1) / 2 (exact), zs = c (pitch_v / Da) and
+// zm = (nz - 1) / 2 - c (pitch_v Sa / (h Da)), each product carried to about one FP32 rounding
+// (the low halves and the product's exact error folded in).  No FP64 instruction: on GB300 the
+// FP64 set-up of a thread's rays took a quarter of the FP64 pipe's cycles of the kernel.
+__device__ __forceinline__ void ray_z_f32(const RayXY &R, int iv, int ndv, int nz, float &zs,
+                                          float &zm)
+{
+    const float c = (float)iv - 0.5f * (float)(ndv - 1);
+    zs = fmaf(c, R.zp_hi, c * R.zp_lo);
+    const float p = c * R.zq_hi;
+    const float e = fmaf(c, R.zq_hi, -p);
+    zm = (0.5f * (float)(nz - 1) - p) - fmaf(c, R.zq_lo, e);
+}
+
 // The volume is processed in z slabs so that the pair rows a launch reads stay in L2: slab s
 // owns the samples whose lower tap row r = floor(z) + 1 (padded row index) lies in
 // [r_lo, r_hi); membership is decided on the same FP32 position the sample uses, so every
@@ -111,15 +126,14 @@ __global__ void __launch_bounds__(256, 3) joseph3d_kernel(
     const bool valid = iu < ndu && iv_raw <= iv1;   // all lanes stay for the warp-wide range
     const int iv = valid ? iv_raw : iv0;
     const RayXY R = rxy[(int64_t)view * ndu + (valid ? iu : 0)];
-    const double v = (iv - 0.5 * (ndv - 1)) * pitch_v;
-    const bool zdrive = fabs(v) * fabs(R.rda) > 1.0;      // |v| > |Da|: driven along z
+    const bool zdrive = iv < R.iv_lo || iv > R.iv_hi;    // |v| > |Da|: driven along z
     const int mode = zdrive ? 2 : (int)((R.packed >> 30) & 3);
     const bool ax = mode == 0;
     const int n_drive = ax ? nx : ny;
     const float tmid = 0.5f * (float)(n_drive - 1);
-    // z of the samples: z(t) = zmid + zslope (t - tmid), zslope = v / Da (FP64, two operations)
-    const double zsl_d = v * R.rda;
-    const float zs = (float)zsl_d, zm = (float)(0.5 * (nz - 1) - R.sa_h * zsl_d);
+    // z of the samples: z(t) = zmid + zslope (t - tmid), zslope = v / Da
+    float zs, zm;
+    ray_z_f32(R, iv, ndv, nz, zs, zm);
     float acc = 0.f;
     bool any = false;
     int lo = R.packed & 0x7fff, hi = (R.packed >> 15) & 0x7fff;
@@ -336,15 +350,14 @@ __global__ void __launch_bounds__(256, 3) joseph3d_pair_kernel(
     const bool va_ok = col_ok && iva_raw <= iv1, vb_ok = col_ok && iva_raw + 1 <= iv1;
     const int iva = va_ok ? iva_raw : iv0, ivb = vb_ok ? iva_raw + 1 : iv0;
     const RayXY R = rxy[(int64_t)view * ndu + (col_ok ? iu : 0)];
-    const double va = (iva - 0.5 * (ndv - 1)) * pitch_v, vb = (ivb - 0.5 * (ndv - 1)) * pitch_v;
-    const bool zda = fabs(va) * fabs(R.rda) > 1.0, zdb = fabs(vb) * fabs(R.rda) > 1.0;
+    const bool zda = iva < R.iv_lo || iva > R.iv_hi, zdb = ivb < R.iv_lo || ivb > R.iv_hi;
     const int mode = (int)((R.packed >> 30) & 3);          // in-plane driving axis
     const bool ax = mode == 0;
     const int n_drive = ax ? nx : ny;
     const float tmid = 0.5f * (float)(n_drive - 1);
-    const double zsa_d = va * R.rda, zsb_d = vb * R.rda;
-    const float zsa = (float)zsa_d, zma = (float)(0.5 * (nz - 1) - R.sa_h * zsa_d);
-    const float zsb = (float)zsb_d, zmb = (float)(0.5 * (nz - 1) - R.sa_h * zsb_d);
+    float zsa, zma, zsb, zmb;
+    ray_z_f32(R, iva, ndv, nz, zsa, zma);
+    ray_z_f32(R, ivb, ndv, nz, zsb, zmb);
     const float zhi = (float)nz;
     float acca = 0.f, accb = 0.f;
     bool anya = false, anyb = false;
@@ -666,15 +679,14 @@ __global__ void __launch_bounds__(256) joseph3d_adjoint_kernel(
     const RayXY R = rxy[(int64_t)view * ndu + iu];
     const float yv = y[(int64_t)view * y_view_ld + (int64_t)iv * y_ld + y_off + iu];
     const int64_t sxy = (int64_t)nx * ny;
-    const double v = (iv - 0.5 * (ndv - 1)) * pitch_v;
-    const bool zdrive = fabs(v) * fabs(R.rda) > 1.0;
+    const bool zdrive = iv < R.iv_lo || iv > R.iv_hi;
     if (!zdrive) {
         const int mode = (int)((R.packed >> 30) & 3);
         const bool ax = mode == 0;
         const int n_drive = ax ? nx : ny;
         const float tmid = 0.5f * (float)(n_drive - 1);
-        const double zsl_d = v * R.rda;
-        const float zs = (float)zsl_d, zm = (float)(0.5 * (nz - 1) - R.sa_h * zsl_d);
+        float zs, zm;                       // the forward kernels' z set-up
+        ray_z_f32(R, iv, ndv, nz, zs, zm);
         const float s = yv * ((float)h * sqrtf(R.dxy2 + zs * zs));
         const int lo = R.packed & 0x7fff, hi = (R.packed >> 15) & 0x7fff;
         float tf = (float)lo - tmid;
