@@ -995,13 +995,18 @@ def check_ranks(gpus, env):
     return None
 
 
-SHAPE_KEYS = ("a_threads", "a_views", "a_slab", "b_rows", "b_views", "a_rays")
+SHAPE_KEYS = ("a_threads", "a_views", "a_slab", "b_rows", "b_views", "a_rays", "a_warp_views",
+              "b_warp_rows")
 
 
 def parse_shapes(text):
+    """Six or eight integers in SHAPE_KEYS order (six: one view per Joseph warp, one pixel row
+    per B warp)."""
     vals = [int(v) for v in text.split(",")]
+    if len(vals) == 6:
+        vals += [1, 1]
     if len(vals) != len(SHAPE_KEYS):
-        raise SystemExit("--launch-shapes takes six integers: " + ",".join(SHAPE_KEYS))
+        raise SystemExit("--launch-shapes takes six or eight integers: " + ",".join(SHAPE_KEYS))
     return vals
 
 
@@ -1018,7 +1023,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--launch-shapes", default=None,
                     help="fixed projector launch shapes (solver and projector benchmarks) "
-                         "instead of autotuning: " + ",".join(SHAPE_KEYS) + " as six integers")
+                         "instead of autotuning: " + ",".join(SHAPE_KEYS) + " as six or eight integers")
     ap.add_argument("--variants", default="all",
                     help="'all', 'none' or a comma list of: basis_precision_fan512_ab, "
                          "learned_lambda_parallel256, batched_slices_256, cone512, "

@@ -219,8 +219,8 @@ ct_status ba_gmres_hybrid_restarted(ct_geom *g, const float *b_dev, float *x_dev
 /* Launch shapes of the projector kernels of a geometry. */
 typedef struct {
     int a_threads;   /* 2D Joseph A: threads per block                                    */
-    int a_views;     /* Joseph A: 2D, views per block (each warp 32 bins of one view); 3D,
-                        detector rows per block of 32 columns (each warp one row)           */
+    int a_views;     /* Joseph A: 2D, views per block (a_threads / a_views consecutive bins of
+                        each); 3D, detector rows per block of 32 columns (each warp one row) */
     int a_slab;      /* 3D Joseph A: z-slab thickness (tap rows) of one pass; each pass
                         reads one slab of the volume's pair layouts, so it stays in L2    */
     int b_rows;      /* 2D pixel-driven B: pixel rows per block                           */
@@ -240,13 +240,24 @@ typedef struct {
     int a_rays;      /* 3D Joseph A: detector rows per thread, 1 or 2 (two rays of one detector
                         column share their in-plane tap positions; the same operations per
                         sample, so results do not change); ignored in 2D                    */
+    int a_warp_views; /* 2D Joseph A: views per warp, 1, 2, 4 or 8 (a warp takes 32 / a_warp_views
+                        consecutive bins of each; several views of fewer bins keep a warp's
+                        taps on one line within fewer cache lines); divides a_views; 1 in 3D */
+    int b_warp_rows; /* 2D pixel-driven B: pixel rows per warp, 1, 2 or 4 (a warp takes a tile
+                        of 32 / b_warp_rows columns by b_warp_rows rows; for the four-fold
+                        kernel, of orbit positions); at most the block's rows (b_rows, or the
+                        orbit rows of the four-fold kernel: 2 for b_rows 4 and 16, 4 for 8);
+                        ignored in 3D                                                        */
 } ct_launch_shapes;
 
 /* Time the candidate launch shapes of the projectors on this geometry and keep the fastest for
  * later calls on `g`.  2D: Joseph A with (threads, views) per block in (128, 1), (128, 2),
  * (128, 4), (256, 1), (256, 2), (256, 4), (512, 4), (512, 8); pixel-driven B with 4, 8 or 16
  * pixel rows per block and one view per loop iteration, or 4 or 8 rows and two, and for
- * geometries with the four-fold symmetry also the four-fold kernel (b_rows 4, 8, 16).  3D: Joseph
+ * geometries with the four-fold symmetry also the four-fold kernel (b_rows 4, 8, 16), each with
+ * warps of 32 x 1 pixels and of the taller tiles its block allows, and the Joseph shapes with
+ * several views per warp (threads, views per block, views per warp) in (128, 2, 2), (128, 4, 2),
+ * (128, 4, 4), (256, 4, 4), (256, 8, 4), (256, 8, 8), (512, 8, 4).  3D: Joseph
  * (slab thickness, warp rows per block, detector rows per thread) in (16, 1, 1), (16, 4, 1),
  * (16, 8, 1), (64, 4, 1), (64, 8, 1), one pass over the whole volume with 1, 4 or 8 warp rows
  * and one detector row per thread, and (16, 4, 2), (64, 4, 2), one pass with 2 or 4 warp rows
@@ -258,11 +269,13 @@ typedef struct {
  * device buffers.  The chosen shapes are written to *out (may be NULL). */
 ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_shapes *out);
 /* Set the projectors' launch shapes of `g` explicitly (for instance a shape an earlier autotune
- * found, or a fixed one for timing).  Values: a_threads in {128, 256, 512} with a_threads /
- * a_views >= 32 and a_views in {1, 2, 4, 8} (2D), a_slab >= 1 (3D; >= nz + 1 is one pass),
+ * found, or a fixed one for timing).  Values: a_threads in {128, 256, 512}, a_views in
+ * {1, 2, 4, 8}, a_warp_views in {1, 2, 4, 8} dividing a_views, and a_threads / a_views >=
+ * 32 / a_warp_views (2D), a_slab >= 1 (3D; >= nz + 1 is one pass),
  * a_views in 1..8 warp rows (3D), a_rays in {1, 2} (3D), b_rows in {4, 8, 16}, b_views in
  * {1, 2, 4} (b_rows 16 only with b_views 1; b_views 4 only on a geometry with the four-fold
- * symmetry described at ct_launch_shapes); anything else
+ * symmetry described at ct_launch_shapes), b_warp_rows in {1, 2, 4} up to the block's rows
+ * (2D); in 3D a_warp_views and b_warp_rows are not checked and read back as 1; anything else
  * returns CT_EINVAL and leaves `g` unchanged.  Host-only; shapes change the order of work, not a
  * sample's arithmetic. */
 ct_status ct_geom_set_launch_shapes(ct_geom *g, const ct_launch_shapes *shapes);

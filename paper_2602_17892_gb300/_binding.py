@@ -67,7 +67,8 @@ class PhaseTime(ctypes.Structure):
 
 class LaunchShapes(ctypes.Structure):
     _fields_ = [("a_threads", ctypes.c_int), ("a_views", ctypes.c_int), ("a_slab", ctypes.c_int),
-                ("b_rows", ctypes.c_int), ("b_views", ctypes.c_int), ("a_rays", ctypes.c_int)]
+                ("b_rows", ctypes.c_int), ("b_views", ctypes.c_int), ("a_rays", ctypes.c_int),
+                ("a_warp_views", ctypes.c_int), ("b_warp_rows", ctypes.c_int)]
 
 
 class HybridInfo(ctypes.Structure):
@@ -364,25 +365,30 @@ def ct_geom_set_backprojector(g: Geom, kind: str):
     _check(load().ct_geom_set_backprojector(g.handle, k))
 
 
+def _shapes_dict(sh) -> dict:
+    return {"a_threads": sh.a_threads, "a_views": sh.a_views, "a_slab": sh.a_slab,
+            "b_rows": sh.b_rows, "b_views": sh.b_views, "a_rays": sh.a_rays,
+            "a_warp_views": sh.a_warp_views, "b_warp_rows": sh.b_warp_rows}
+
+
 def ct_geom_set_launch_shapes(g: Geom, shapes: dict):
     sh = LaunchShapes(int(shapes["a_threads"]), int(shapes["a_views"]), int(shapes["a_slab"]),
-                      int(shapes["b_rows"]), int(shapes["b_views"]), int(shapes.get("a_rays", 1)))
+                      int(shapes["b_rows"]), int(shapes["b_views"]), int(shapes.get("a_rays", 1)),
+                      int(shapes.get("a_warp_views", 1)), int(shapes.get("b_warp_rows", 1)))
     _check(load().ct_geom_set_launch_shapes(g.handle, ctypes.byref(sh)))
 
 
 def ct_geom_get_launch_shapes(g: Geom) -> dict:
     sh = LaunchShapes()
     _check(load().ct_geom_get_launch_shapes(g.handle, ctypes.byref(sh)))
-    return {"a_threads": sh.a_threads, "a_views": sh.a_views, "a_slab": sh.a_slab,
-            "b_rows": sh.b_rows, "b_views": sh.b_views, "a_rays": sh.a_rays}
+    return _shapes_dict(sh)
 
 
 def ct_geom_autotune(g: Geom, stream=None) -> dict:
     """Time the projector launch shapes on this geometry; returns the chosen shapes."""
     sh = LaunchShapes()
     _check(load().ct_geom_autotune(g.handle, _stream(stream), ctypes.byref(sh)))
-    return {"a_threads": sh.a_threads, "a_views": sh.a_views, "a_slab": sh.a_slab,
-            "b_rows": sh.b_rows, "b_views": sh.b_views, "a_rays": sh.a_rays}
+    return _shapes_dict(sh)
 
 
 def _info_dict(inf):

@@ -489,10 +489,10 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     dg.h = (float)d->pixel; dg.n_views = d->n_views; dg.ndu = d->n_det_u; dg.ndv = ndv;
     dg.pitch_u = (float)d->pitch_u; dg.pitch_v = (float)g->desc.pitch_v;
     dg.sid = (float)d->sid; dg.sdd = (float)d->sdd;
-    // at least n + 2 pairs per line: pair indices -1 and n + 1 (taps at or beyond the edge)
-    // read zeros
-    dg.row_pairs_ld = (int)round_up(d->nx + 2, 16);
-    dg.col_pairs_ld = (int)round_up(d->ny + 2, 16);
+    // at least n + 3 pairs per line: pair 0 holds the taps (-1, 0), pairs n + 1 and n + 2 (taps
+    // beyond the edge, which the 2D Joseph loop may read for positions up to n + 1) zeros
+    dg.row_pairs_ld = (int)round_up(d->nx + 3, 16);
+    dg.col_pairs_ld = (int)round_up(d->ny + 3, 16);
     dg.sino_ld = (int)round_up(d->n_det_u + 4, 4);
     dg.sino_view_ld = cone ? (int64_t)(ndv + 3) * dg.sino_ld : dg.sino_ld;
     dg.sino_row0 = cone ? dg.sino_ld : 0;
@@ -511,6 +511,8 @@ ct_status ct_geom_create(const ct_geom_desc *d, ct_geom **out)
     dg.b_rot4 = rot4_symmetric(&g->desc) ? 1 : 0;
     dg.tune_a_slab = 16;
     dg.tune_a_rays = 1;
+    dg.tune_a_wviews = 1;
+    dg.tune_b_wrows = 1;
 
     std::vector<Ray2D> rays;
     std::vector<RayXY> rays_xy;
@@ -1449,6 +1451,12 @@ extern "C" ct_status ct_test_drop_tile_copy(int enable, int64_t wait_cycles)
 static std::mutex g_tune_mu;
 static std::map<std::tuple<int, int, int, int, int, int, int, int, int>, ct_launch_shapes> g_tune_cache;
 
+// pixel rows of a B block: b_rows, or the orbit rows of the four-fold kernel's blocks
+static int b_block_rows(int b_rows, int b_views)
+{
+    return b_views == 4 ? (b_rows == 8 ? 4 : 2) : b_rows;
+}
+
 static ct_launch_shapes shapes_of(const DeviceGeom &d)
 {
     ct_launch_shapes r;
@@ -1458,6 +1466,8 @@ static ct_launch_shapes shapes_of(const DeviceGeom &d)
     r.b_rows = d.tune_b_rows;
     r.b_views = d.tune_b_views;
     r.a_rays = d.tune_a_rays;
+    r.a_warp_views = d.tune_a_wviews;
+    r.b_warp_rows = d.tune_b_wrows;
     return r;
 }
 
@@ -1477,7 +1487,9 @@ extern "C" ct_status ct_geom_set_launch_shapes(ct_geom *g, const ct_launch_shape
         ok = ok && sh->a_slab >= 1 && sh->a_views >= 1 && sh->a_views <= 8 && in(sh->a_rays, {1, 2});
     else
         ok = ok && in(sh->a_threads, {128, 256, 512}) && in(sh->a_views, {1, 2, 4, 8}) &&
-             sh->a_threads / sh->a_views >= 32;
+             in(sh->a_warp_views, {1, 2, 4, 8}) && sh->a_views % sh->a_warp_views == 0 &&
+             sh->a_threads / sh->a_views >= 32 / sh->a_warp_views &&
+             in(sh->b_warp_rows, {1, 2, 4}) && sh->b_warp_rows <= b_block_rows(sh->b_rows, sh->b_views);
     if (!ok) return einval("ct_geom_set_launch_shapes: launch shape out of range");
     DeviceGeom &dg = g->dg;
     dg.tune_a_threads = sh->a_threads;
@@ -1486,6 +1498,8 @@ extern "C" ct_status ct_geom_set_launch_shapes(ct_geom *g, const ct_launch_shape
     dg.tune_b_rows = sh->b_rows;
     dg.tune_b_views = sh->b_views;
     dg.tune_a_rays = cone ? sh->a_rays : 1;
+    dg.tune_a_wviews = cone ? 1 : sh->a_warp_views;
+    dg.tune_b_wrows = cone ? 1 : sh->b_warp_rows;
     return CT_OK;
 }
 
@@ -1517,6 +1531,8 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
             dg.tune_b_rows = it->second.b_rows;
             dg.tune_b_views = it->second.b_views;
             dg.tune_a_rays = it->second.a_rays;
+            dg.tune_a_wviews = it->second.a_warp_views;
+            dg.tune_b_wrows = it->second.b_warp_rows;
             if (out) *out = it->second;
             return CT_OK;
         }
@@ -1556,16 +1572,23 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
     // 2D Joseph A: (rays per block, views per block); 3D: z-slab thickness of the Joseph passes;
     // 2D B: (pixel rows per 32-wide block, views per loop iteration); the 3D backprojector has
     // one shape
-    // 2D Joseph: (threads, warp rows = views per block)
-    static const int a2[8][2] = {{128, 1}, {128, 2}, {128, 4}, {256, 1},
-                                 {256, 2}, {256, 4}, {512, 4}, {512, 8}};
+    // 2D Joseph: (threads, views per block, views per warp)
+    static const int a2[15][3] = {{128, 1, 1}, {128, 2, 1}, {128, 4, 1}, {256, 1, 1},
+                                  {256, 2, 1}, {256, 4, 1}, {512, 4, 1}, {512, 8, 1},
+                                  {128, 2, 2}, {128, 4, 2}, {128, 4, 4}, {256, 4, 4},
+                                  {256, 8, 4}, {256, 8, 8}, {512, 8, 4}};
     // 3D: (z-slab thickness, warp rows per block, detector rows per thread); 1 << 20 = one
     // pass over the volume
     static const int a3[12][3] = {{16, 1, 1}, {16, 4, 1}, {16, 8, 1}, {64, 4, 1}, {64, 8, 1},
                                   {1 << 20, 1, 1}, {1 << 20, 4, 1}, {1 << 20, 8, 1},
                                   {16, 4, 2}, {64, 4, 2}, {1 << 20, 2, 2}, {1 << 20, 4, 2}};
-    // B: (pixel rows per block, views per iteration); b_views 4 = the four-fold kernel
-    static const int b2[8][2] = {{4, 1}, {8, 1}, {16, 1}, {4, 2}, {8, 2}, {4, 4}, {8, 4}, {16, 4}};
+    // B: (pixel rows per block, views per iteration, pixel rows per warp); b_views 4 = the
+    // four-fold kernel (its blocks have 2, 4, 2 orbit rows for b_rows 4, 8, 16)
+    static const int b2[22][3] = {{4, 1, 1}, {8, 1, 1}, {16, 1, 1}, {4, 2, 1}, {8, 2, 1},
+                                  {4, 1, 2}, {8, 1, 2}, {16, 1, 2}, {4, 2, 2}, {8, 2, 2},
+                                  {4, 1, 4}, {8, 1, 4}, {16, 1, 4}, {4, 2, 4}, {8, 2, 4},
+                                  {4, 4, 1}, {8, 4, 1}, {16, 4, 1}, {4, 4, 2}, {8, 4, 2},
+                                  {16, 4, 2}, {8, 4, 4}};
     auto fwd = [&]() { return launch_forward_proj(g, y, true, nullptr, s); };
     ct_status st;
     if (cone)
@@ -1575,15 +1598,17 @@ extern "C" ct_status ct_geom_autotune(ct_geom *g, ct_stream_t stream, ct_launch_
             dg.tune_a_rays = a3[c][2];
         });
     else
-        st = time_best(fwd, 8, [&](int c) {
+        st = time_best(fwd, 15, [&](int c) {
             dg.tune_a_threads = a2[c][0];
             dg.tune_a_views = a2[c][1];
+            dg.tune_a_wviews = a2[c][2];
         });
     if (st == CT_OK && !cone)
-        st = time_best([&]() { return launch_back_proj(g, y, x, nullptr, s); }, dg.b_rot4 ? 8 : 5,
+        st = time_best([&]() { return launch_back_proj(g, y, x, nullptr, s); }, dg.b_rot4 ? 22 : 15,
                        [&](int c) {
             dg.tune_b_rows = b2[c][0];
             dg.tune_b_views = b2[c][1];
+            dg.tune_b_wrows = b2[c][2];
         });
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

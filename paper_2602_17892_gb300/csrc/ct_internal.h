@@ -65,8 +65,8 @@ struct DeviceGeom {
     int n_views, ndu, ndv;
     float pitch_u, pitch_v, sid, sdd;
     // padded layouts
-    int row_pairs_ld;   // P_row row length in float2: >= nx + 1
-    int col_pairs_ld;   // P_col row length in float2: >= ny + 1
+    int row_pairs_ld;   // P_row row length in float2: >= nx + 3
+    int col_pairs_ld;   // P_col row length in float2: >= ny + 3
     int sino_ld;        // padded sinogram row length: ndu + 4 (2 zero bins each side)
     int tune_a_threads; // Joseph A: rays (threads) per block, chosen by ct_geom_autotune
     int tune_a_views;   // 2D Joseph A: views per block (each warp one view)
@@ -81,6 +81,8 @@ struct DeviceGeom {
     int tune_a_slab;    // 3D Joseph A: z slab thickness (tap rows) per launch
     int tune_a_rays;    // 3D Joseph A: detector rows per thread (1, or 2 sharing the in-plane
                         // coordinate)
+    int tune_a_wviews;  // 2D Joseph A: views per warp (1, 2, 4, 8; 32 / tune_a_wviews bins each)
+    int tune_b_wrows;   // 2D pixel-driven B: pixel (orbit) rows per warp (1, 2, 4)
     int64_t sino_view_ld; // floats per view in the padded sinogram (2D: sino_ld; 3D: (ndv + 2)
                           // rows of sino_ld, detector row 0 at row 1)
     int sino_row0;      // offset of detector row 0 inside a padded view (0 in 2D, sino_ld in 3D)

@@ -182,8 +182,12 @@ cudaError_t launch_back_proj(const ct_geom *g, const float *ypad, float *x, cons
 // ---------------------------------------------------------------------------- Joseph A
 // One thread per ray.  pos = pmid + slope * (t - t_mid) is the fractional index across the
 // driving axis; the pair at index floor(pos)+1 of line t holds both interpolation taps.
-// A block covers blockDim.x / vpb consecutive bins of vpb consecutive views (each warp one
-// view): the views of a block cross nearly the same pixels, so their warps share L1 lines.
+// A block covers blockDim.x / vpb consecutive bins of vpb consecutive views: the views of a
+// block cross nearly the same pixels, so their warps share L1 lines.  A warp takes 32 / wv
+// consecutive bins of wv consecutive views: at a driving line its lanes' taps then span fewer
+// pairs (at the 512^2 fan workload about 1.7 cache lines of 128 B per warp load with 8 bins of
+// 4 views, against 3.0 with 32 bins of one view), and the L1 data path, which serves a warp
+// load line by line, does fewer passes for the same samples.
 //
 // The loop works with the centred position pc = pos - co (co = n_other / 2, the layouts'
 // centre), pc = fma(slope, t - t_mid, pmid - co), and interpolates with one fma, a + pc d.
@@ -200,14 +204,19 @@ cudaError_t launch_back_proj(const ct_geom *g, const float *ypad, float *x, cons
 // every line of a warp's range exists whatever axis a lane drives along.
 // Lines t in [ta, tb] of one ray, two at a time (t and t + 1): both samples' positions and
 // floors in paired FP32 arithmetic (one fma.f32x2 / add.rm.f32x2 each, the same operations
-// per sample as one line at a time), accumulated in line order.  K carries (t - ta) * stride
-// (below 2^22 for every t).  The lines go in batches of NB pairs: first all positions and
-// floors, then all 2 NB gathers, then the sums in line order, so that each thread has 2 NB
-// gathers in flight (with one pair per iteration the kernel waited on its gathers: 14
-// long-scoreboard stalls per issue); single pairs finish the range.
+// per sample as one line at a time), accumulated in line order.  The lines go in batches of NB
+// pairs: first all positions and floors, then all 2 NB gathers, then the sums in line order,
+// so that each thread has 2 NB gathers in flight (with one pair per iteration the kernel
+// waited on its gathers: 14 long-scoreboard stalls per issue); single pairs finish the range.
+// The batch's first line is the base address lb, which moves on by 2 NB lines per batch, so the
+// K of line pair q of a batch, 2^23 + 2 + co + (2q, 2q + 1) stride, is the same in every batch
+// (held in registers, below 2^22 + 2^23 for strides below 2^22 / (2 NB)).
+// A sample is taken where |pc| <= win = co + 1, that is pos in [co - win, co + win]: [-1, n] for
+// odd n_other, [-1, n + 1] for even n_other (one compare of |pc|); pair indices run to n + 2
+// at most, which every line holds (zero beyond pair n: taps outside the image).
 template <int NB>
-__device__ __forceinline__ float2 joseph2d_span(int ta, int tb, float plo, float phi, float pmc,
-                                                float co, float slope, float tmid, int stride,
+__device__ __forceinline__ float2 joseph2d_span(int ta, int tb, float win, float pmc, float co,
+                                                float slope, float tmid, int stride,
                                                 uint64_t abase, float2 acc_even_odd)
 {
     // the pairs (t, t + 1) start at ta: their first line is odd when ta is, so the sums of the
@@ -216,27 +225,31 @@ __device__ __forceinline__ float2 joseph2d_span(int ta, int tb, float plo, float
     const bool odd = ta & 1;
     float2 acc = odd ? make_float2(acc_even_odd.y, acc_even_odd.x) : acc_even_odd;
     float2 tf2 = make_float2((float)ta - tmid, (float)ta - tmid + 1.f);
-    float2 K2 = make_float2(kFloorK0 + co, kFloorK0 + co + (float)stride);
+    float2 Kq[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+        Kq[q] = make_float2(kFloorK0 + co + (float)(2 * q * stride),
+                            kFloorK0 + co + (float)((2 * q + 1) * stride));
     const float2 sl2 = make_float2(slope, slope), pm2 = make_float2(pmc, pmc);
-    const float2 d2 = make_float2(2.f, 2.f), dK2 = make_float2(2.f * (float)stride, 2.f * (float)stride);
-    const uint64_t lb = abase + 8ull * (uint64_t)ta * (uint64_t)stride;
+    const float2 d2 = make_float2(2.f, 2.f);
+    uint64_t lb = abase + 8ull * (uint64_t)ta * (uint64_t)stride;
+    const uint64_t dlb = 16ull * NB * (uint64_t)stride, dlb1 = 16ull * (uint64_t)stride;
     int t = ta;
     // tb - t: a warp whose lanes all have empty ranges has ta = INT_MAX and tb = -1, for which
     // t + 2 NB - 1 would overflow; tb - t >= INT_MIN does not
-    for (; tb - t >= 2 * NB - 1; t += 2 * NB) {
+    for (; tb - t >= 2 * NB - 1; t += 2 * NB, lb += dlb) {
         float2 pc[NB], pa[NB], pb[NB];
         uint32_t ia[NB], ib[NB];
         bool ina[NB], inb[NB];
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
             pc[q] = __ffma2_rn(sl2, tf2, pm2);                       // pos - co
-            const float2 sk2 = __fadd2_rd(pc[q], K2);
+            const float2 sk2 = __fadd2_rd(pc[q], Kq[q]);
             ia[q] = __float_as_uint(sk2.x);
             ib[q] = __float_as_uint(sk2.y);
-            ina[q] = pc[q].x >= plo && pc[q].x <= phi;
-            inb[q] = pc[q].y >= plo && pc[q].y <= phi;
+            ina[q] = fabsf(pc[q].x) <= win;
+            inb[q] = fabsf(pc[q].y) <= win;
             tf2 = __fadd2_rn(tf2, d2);
-            K2 = __fadd2_rn(K2, dK2);
         }
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
@@ -253,17 +266,16 @@ __device__ __forceinline__ float2 joseph2d_span(int ta, int tb, float plo, float
             acc = __fadd2_rn(acc, make_float2(va, vb));
         }
     }
-    for (; t <= tb; t += 2) {
+    for (; t <= tb; t += 2, lb += dlb1) {
         const float2 pc2 = __ffma2_rn(sl2, tf2, pm2);
-        const float2 sk2 = __fadd2_rd(pc2, K2);
+        const float2 sk2 = __fadd2_rd(pc2, Kq[0]);
         float2 pa = make_float2(0.f, 0.f), pb = make_float2(0.f, 0.f);
-        if (pc2.x >= plo && pc2.x <= phi)
+        if (fabsf(pc2.x) <= win)
             pa = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * __float_as_uint(sk2.x)));
-        if (t + 1 <= tb && pc2.y >= plo && pc2.y <= phi)
+        if (t + 1 <= tb && fabsf(pc2.y) <= win)
             pb = __ldg(reinterpret_cast<const float2 *>(lb + 8ull * __float_as_uint(sk2.y)));
         acc = __fadd2_rn(acc, make_float2(fmaf(pc2.x, pa.y, pa.x), fmaf(pc2.y, pb.y, pb.x)));
         tf2 = __fadd2_rn(tf2, d2);
-        K2 = __fadd2_rn(K2, dK2);
     }
     return odd ? make_float2(acc.y, acc.x) : acc;
 }
@@ -271,16 +283,18 @@ __device__ __forceinline__ float2 joseph2d_span(int ta, int tb, float plo, float
 // A ray of the table in FP32: slope, weight, driving axis, n_other and a range of lines [lo, hi]
 // that contains every line t whose FP32 position fma(slope, t - tmid, pmid) - the sample loop's
 // own arithmetic - lies in [-1, n_other] (an FP32 estimate of the crossings widened by two
-// lines and clipped to the image; empty when the ray misses it).  The loop takes a sample only
-// where its position is in [-1, n_other]: the tap pair floor(pos) + 1 is then in
-// [0, n_other + 1], inside the line's zero-padded pairs, so no position needs a clamp; a line
-// beyond the ray's own image extent (a warp's rays may drive along different axes of a
-// non-square image) is one of the zero lines both layouts carry up to max(nx, ny).
-// co = n_other / 2 (the centre of the layout the ray reads), pmc = pmid - co, and the
-// centred sample window [plo, phi] = [-1 - co, n_other - co].
+// lines and clipped to the image; empty when the ray misses it).  The forward loop takes a
+// sample only where its position is in [co - win, co + win] ([-1, n_other], or [-1, n_other + 1]
+// for even n_other): the tap pair floor(pos) + 1 is then in [0, n_other + 2], inside the line's
+// zero-padded pairs, so no position needs a clamp, and the samples beyond pos = n_other have
+// both taps outside the image (exact zeros); a line beyond the ray's own image extent (a warp's
+// rays may drive along different axes of a non-square image) is one of the zero lines both
+// layouts carry up to max(nx, ny).
+// co = n_other / 2 (the centre of the layout the ray reads), pmc = pmid - co, win = co + 1 and
+// the centred window of the samples with a tap in the image [plo, phi] = [-1 - co, n_other - co].
 struct RayJ {
     float pmid, slope, weight, ohi;
-    float co, pmc, plo, phi;
+    float co, pmc, plo, phi, win;
     int axis, lo, hi;
 };
 
@@ -298,6 +312,7 @@ __device__ __forceinline__ RayJ decode_ray2d(const Ray2D R, int nx, int ny, floa
     r.pmc = r.pmid - r.co;
     r.plo = -1.f - r.co;
     r.phi = r.ohi - r.co;
+    r.win = r.co + 1.f;
     const float tmax = (float)(n_drive - 1);
     if (r.slope != 0.f) {
         const float rs = __frcp_rn(r.slope);
@@ -314,21 +329,21 @@ __device__ __forceinline__ RayJ decode_ray2d(const Ray2D R, int nx, int ny, floa
     return r;
 }
 
-// CHUNKED: the lines are walked in chunks of `chunk` (images whose line offsets exceed 2^22)
 constexpr int kJBatch = 4;   // line pairs per batch of the Joseph loop
 
 // at most 64 registers a thread (two blocks of 512 threads per SM) for the batched gathers
-template <bool CHUNKED>
 __global__ void __launch_bounds__(512, 2) joseph2d_kernel(
-    const Ray2D *__restrict__ rays, int n_views, int ndu, int vpb,
+    const Ray2D *__restrict__ rays, int n_views, int ndu, int vpb, int wv,
     const float2 *__restrict__ prow, int prow_ld, const float2 *__restrict__ pcol, int pcol_ld,
-    int chunk, int nx, int ny, float h, float *__restrict__ y, int y_ld, int y_off,
-    const int *stop)
+    int nx, int ny, float h, float *__restrict__ y, int y_ld, int y_off, const int *stop)
 {
     if (stop && stop[0] != 0) return;
-    const int bins_pb = blockDim.x / vpb;
-    const int bin = blockIdx.x * bins_pb + (int)threadIdx.x % bins_pb;
-    const int view0 = blockIdx.y * vpb + (int)threadIdx.x / bins_pb;
+    // warp w of the block: bin group w % bgroups (32 / wv bins), view group w / bgroups (wv
+    // views); lane: bin lane % (32 / wv) of the group, view lane / (32 / wv)
+    const int bins_pb = blockDim.x / vpb, bpw = 32 / wv, bgroups = bins_pb / bpw;
+    const int w = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    const int bin = blockIdx.x * bins_pb + (w % bgroups) * bpw + lane % bpw;
+    const int view0 = blockIdx.y * vpb + (w / bgroups) * wv + lane / bpw;
     const bool valid = bin < ndu && view0 < n_views;   // all lanes stay for the warp range
     const RayJ R = decode_ray2d(rays[valid ? (int64_t)view0 * ndu + bin : 0], nx, ny, h);
     int t_lo = R.lo, t_hi = R.hi;
@@ -346,15 +361,8 @@ __global__ void __launch_bounds__(512, 2) joseph2d_kernel(
     const uint64_t abase = reinterpret_cast<uint64_t>(base) -
                            8ull * ((uint64_t)__float_as_uint(kFloor2p23) + 1ull);
     // two sums, of the even and of the odd lines (in line order each), added at the end
-    float2 acc = make_float2(0.f, 0.f);
-    if (!CHUNKED) {
-        acc = joseph2d_span<kJBatch>(wlo, whi, R.plo, R.phi, R.pmc, R.co, R.slope, tmid, stride,
-                                     abase, acc);
-    } else {
-        for (int t0 = wlo; t0 <= whi; t0 += chunk)
-            acc = joseph2d_span<kJBatch>(t0, min(whi, t0 + chunk - 1), R.plo, R.phi, R.pmc, R.co,
-                                         R.slope, tmid, stride, abase, acc);
-    }
+    const float2 acc = joseph2d_span<kJBatch>(wlo, whi, R.win, R.pmc, R.co, R.slope, tmid, stride,
+                                              abase, make_float2(0.f, 0.f));
     if (valid) y[(int64_t)view0 * y_ld + y_off + bin] = (acc.x + acc.y) * R.weight;
 }
 
@@ -363,23 +371,21 @@ cudaError_t launch_joseph2d(const ct_geom *g, float *y, int y_ld, int y_off, con
 {
     const DeviceGeom &d = g->dg;
     const int threads = d.tune_a_threads > 0 ? d.tune_a_threads : 256;
-    const int vpb = (d.tune_a_views > 0 && threads / d.tune_a_views >= 32) ? d.tune_a_views : 1;
+    const int vpb = d.tune_a_views > 0 ? d.tune_a_views : 1;
+    const int wv = d.tune_a_wviews > 0 ? d.tune_a_wviews : 1;
     const int bins_pb = threads / vpb;
+    // every warp one bin group of wv views: checked when the shapes are set
+    if (vpb % wv != 0 || bins_pb * wv < 32 || threads % 32 != 0) return cudaErrorInvalidConfiguration;
     dim3 grid((d.ndu + bins_pb - 1) / bins_pb, (d.n_views + vpb - 1) / vpb);
     // line 0 of each 2D layout follows one zero line
     const float2 *prow = g->prow_dev + d.row_pairs_ld, *pcol = g->pcol_dev + d.col_pairs_ld;
-    // one chunk length for both layouts (the loop bounds stay warp-uniform); one chunk when
-    // every line offset of both layouts stays below 2^22
+    // the K of a batch's last line pair, 2^23 + 2 + co + (2 kJBatch - 1) stride, must keep
+    // unit spacing with the position added (below 2^24): strides below 2^22 / (2 kJBatch)
     const int ldm = std::max(d.row_pairs_ld, d.col_pairs_ld);
-    const int chunk = floor_chunk(ldm);
-    if (std::max(d.nx, d.ny) <= chunk)
-        joseph2d_kernel<false><<<grid, threads, 0, s>>>(g->rays_dev, d.n_views, d.ndu, vpb, prow,
-                                                        d.row_pairs_ld, pcol, d.col_pairs_ld,
-                                                        chunk, d.nx, d.ny, d.h, y, y_ld, y_off, stop);
-    else
-        joseph2d_kernel<true><<<grid, threads, 0, s>>>(g->rays_dev, d.n_views, d.ndu, vpb, prow,
-                                                       d.row_pairs_ld, pcol, d.col_pairs_ld,
-                                                       chunk, d.nx, d.ny, d.h, y, y_ld, y_off, stop);
+    if ((int64_t)ldm * 2 * kJBatch >= kFloorSpan) return cudaErrorInvalidValue;
+    joseph2d_kernel<<<grid, threads, 0, s>>>(g->rays_dev, d.n_views, d.ndu, vpb, wv, prow,
+                                             d.row_pairs_ld, pcol, d.col_pairs_ld, d.nx, d.ny,
+                                             d.h, y, y_ld, y_off, stop);
     return cudaGetLastError();
 }
 
@@ -456,7 +462,10 @@ cudaError_t launch_adjoint2d(const ct_geom *g, const float *y, int y_ld, int y_o
 
 // ---------------------------------------------------------------------------- pixel-driven B
 // One thread per pixel, blocks of 32 x tune_b_rows pixels, per-view constants staged in shared
-// memory.
+// memory.  A warp takes a tile of 32 / wr columns by wr rows of its block (wr = 1: one row of 32
+// pixels): the bin positions of a view then span fewer pairs of the sinogram row (at the 512^2
+// fan workload about 1.4 cache lines of 128 B per warp load with 8 x 4 pixels, against 2.3 with
+// 32 x 1), so the L1 data path serves each gather in fewer passes.
 // Parallel: bin position fj = a (c - cm) + b (r - rm) + (nd-1)/2, weight h^2/pitch.
 // Fan:      pe = p.e_u, bb = SID - p.(cos, sin) (in units of h), u = SDD pe / bb,
 //           weight h SDD / pitch * sqrt(1 + (pe/bb)^2) / bb  (= h^2 (SDD^2+u^2)/(L pitch SDD)).
@@ -528,7 +537,7 @@ constexpr int kBPBatch = 8;   // view pairs per batch of the paired loop
 template <bool FAN, bool CLAMP, int VP>
 __global__ void __launch_bounds__(VP == 2 ? 256 : 512, VP == 2 ? 3 : 1) pixbp2d_kernel(
     const ViewBP *__restrict__ views, int n_views, const float2 *__restrict__ ypair, int ld,
-    int vchunk, int nd, int nx, int ny, float sid_h, float k_u, float k_w, float w_par,
+    int vchunk, int nd, int nx, int ny, float sid_h, float k_u, float k_w, float w_par, int wr,
     float *__restrict__ x, const int *stop)
 {
     if (stop && stop[0] != 0) return;
@@ -547,8 +556,11 @@ __global__ void __launch_bounds__(VP == 2 ? 256 : 512, VP == 2 ? 3 : 1) pixbp2d_
         sview[j] = FAN ? make_float4(p.cs, q.cs, p.sn, q.sn) : make_float4(p.a, q.a, p.b, q.b);
     }
     __syncthreads();
-    const int c = blockIdx.x * 32 + threadIdx.x;
-    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    // warp threadIdx.y: column group y % wr, row group y / wr of the block; lane: column
+    // lane % (32 / wr), row lane / (32 / wr) of its tile
+    const int tw = 32 / wr, wy = threadIdx.y, lane = threadIdx.x;
+    const int c = blockIdx.x * 32 + (wy % wr) * tw + lane % tw;
+    const int r = blockIdx.y * blockDim.y + (wy / wr) * wr + lane / tw;
     if (c >= nx || r >= ny) return;
     const float tc = (float)c - 0.5f * (float)(nx - 1);
     const float tr = (float)r - 0.5f * (float)(ny - 1);
@@ -639,13 +651,14 @@ __global__ void __launch_bounds__(VP == 2 ? 256 : 512, VP == 2 ? 3 : 1) pixbp2d_
 // 16 pixel-view pairs from 4 geometry evaluations.  The 16 gathers of a base view are issued
 // together, then the sums (pixel by pixel, m in order).  The base views are split into
 // blockDim.z consecutive parts (2 or 4), one per z layer of the block, whose sums are added in
-// shared memory in part order (more parts: more threads in flight and a shorter last wave).  The arithmetic of one
+// shared memory in part order (more parts: more threads in flight and a shorter last wave).
+// A warp takes a tile of 32 / wr by wr orbit positions, as in pixbp2d_kernel.  The arithmetic of one
 // pixel-view pair is the one of pixbp2d_view; only the views' constants (those of view k, for
 // the rotated pixel) and the order of the sums differ from the general kernel.
 template <bool CLAMP>
 __global__ void __launch_bounds__(256, 3) pixbp2d_rot4_kernel(
     const ViewBP *__restrict__ views, int q4, const float2 *__restrict__ ypair, int ld,
-    int vchunk, int nd, int N, float sid_h, float k_u, float k_w, float *__restrict__ x,
+    int vchunk, int nd, int N, float sid_h, float k_u, float k_w, int wr, float *__restrict__ x,
     const int *stop)
 {
     if (stop && stop[0] != 0) return;
@@ -656,8 +669,9 @@ __global__ void __launch_bounds__(256, 3) pixbp2d_rot4_kernel(
     for (int k = tid; k < q4; k += nthr) srot[k] = make_float2(views[k].cs, views[k].sn);
     __syncthreads();
     const int half = N >> 1;
-    const int c = blockIdx.x * 32 + threadIdx.x;
-    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    const int tw = 32 / wr, wy = threadIdx.y, lane = threadIdx.x;
+    const int c = blockIdx.x * 32 + (wy % wr) * tw + lane % tw;
+    const int r = blockIdx.y * blockDim.y + (wy / wr) * wr + lane / tw;
     const bool valid = c < half && r < half;
     const float hN = 0.5f * (float)(N - 1);
     const float tc = (float)c - hN, tr = (float)r - hN;
@@ -744,12 +758,13 @@ static void launch_pixbp2d_rot4_t(const ct_geom *g, const float2 *ypad, float *x
     const DeviceGeom &d = g->dg;
     // b_rows 4, 8, 16: (orbit rows, view parts) per block (2, 2), (4, 2), (2, 4)
     const int half = d.nx >> 1, ry = d.tune_b_rows == 8 ? 4 : 2, parts = d.tune_b_rows == 16 ? 4 : 2;
+    const int wr = d.tune_b_wrows > 0 ? d.tune_b_wrows : 1;
     dim3 block(32, ry, parts), grid((half + 31) / 32, (half + ry - 1) / ry);
     const int q4 = d.n_views / 4;
     const size_t smem = sizeof(float2) * (size_t)q4 + sizeof(float) * 4 * 32 * (size_t)ry * (parts - 1);
     pixbp2d_rot4_kernel<CLAMP><<<grid, block, smem, s>>>(
         d.views, q4, ypad, d.sino_ld, floor_chunk(d.sino_ld), d.ndu, d.nx, d.sid / d.h,
-        d.sdd / d.pitch_u, d.h * d.sdd / d.pitch_u, x, stop);
+        d.sdd / d.pitch_u, d.h * d.sdd / d.pitch_u, wr, x, stop);
 }
 
 template <bool FAN, bool CLAMP, int VP>
@@ -762,9 +777,11 @@ static void launch_pixbp2d_t(const ct_geom *g, const float2 *ypad, float *x, con
     const size_t smem = sizeof(float4) * (size_t)(d.n_views + (VP == 2 ? d.n_views / 2 : 0));
     const float sid_h = d.sid / d.h, k_u = d.sdd / d.pitch_u, k_w = d.h * d.sdd / d.pitch_u;
     const float w_par = d.h * d.h / d.pitch_u;
+    const int wr = d.tune_b_wrows > 0 ? d.tune_b_wrows : 1;
     pixbp2d_kernel<FAN, CLAMP, VP><<<grid, block, smem, s>>>(d.views, d.n_views, ypad, d.sino_ld,
                                                              floor_chunk(d.sino_ld), d.ndu, d.nx,
-                                                             d.ny, sid_h, k_u, k_w, w_par, x, stop);
+                                                             d.ny, sid_h, k_u, k_w, w_par, wr, x,
+                                                             stop);
 }
 
 cudaError_t launch_pixbp2d(const ct_geom *g, const float2 *ypad, float *x, const int *stop,
@@ -773,6 +790,9 @@ cudaError_t launch_pixbp2d(const ct_geom *g, const float2 *ypad, float *x, const
     const DeviceGeom &d = g->dg;
     const bool fan = d.kind == CT_FANFLAT2D, clamp = !d.b_noclamp, two = d.tune_b_views == 2;
     if (two && d.tune_b_rows > 8) return cudaErrorInvalidConfiguration;   // 256-thread bound
+    // a warp's tile rows divide the block's (orbit) rows: checked when the shapes are set
+    const int brows = d.tune_b_views == 4 ? (d.tune_b_rows == 8 ? 4 : 2) : d.tune_b_rows;
+    if (d.tune_b_wrows < 1 || brows % d.tune_b_wrows != 0) return cudaErrorInvalidConfiguration;
     if (d.tune_b_views == 4) {
         if (!fan || !d.b_rot4) return cudaErrorInvalidConfiguration;
         clamp ? launch_pixbp2d_rot4_t<true>(g, ypad, x, stop, s)

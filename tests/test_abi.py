@@ -74,7 +74,7 @@ def test_solver_rejects_bad_options(lib):
 
 def test_launch_shape_entry_points_reject_null_arguments(lib):
     from paper_2602_17892_gb300 import _binding as Bn
-    sh = Bn.LaunchShapes(256, 1, 16, 8, 1, 1)
+    sh = Bn.LaunchShapes(256, 1, 16, 8, 1, 1, 1, 1)
     assert lib.ct_geom_set_launch_shapes(None, ctypes.byref(sh)) == Bn.CT_EINVAL
     assert lib.ct_geom_get_launch_shapes(None, ctypes.byref(sh)) == Bn.CT_EINVAL
 

@@ -86,9 +86,10 @@ def test_projectors_are_linear_and_unmatched():
 
 @pytest.mark.parametrize("name", ["fan_64", "fan_ragged_50x33", "parallel_ragged_37x45"])
 def test_launch_shapes_leave_results_bitwise_unchanged(name):
-    """Every 2D launch shape (threads and views per Joseph block; pixel rows per B block and one
-    or two views per B iteration) computes each ray and pixel with the same operations in the
-    same order: A and B agree bit for bit across shapes."""
+    """Every 2D launch shape (threads, views per Joseph block and views per Joseph warp; pixel
+    rows per B block, one or two views per B iteration and pixel rows per B warp) computes each
+    ray and pixel with the same operations in the same order: A and B agree bit for bit across
+    shapes, on images and detectors that fill neither the blocks nor the warps' tiles."""
     from paper_2602_17892_gb300 import ct_geom_get_launch_shapes, ct_geom_set_launch_shapes
     g = GEOMS[name]
     G = gpu_geom(g)
@@ -96,13 +97,38 @@ def test_launch_shapes_leave_results_bitwise_unchanged(name):
     y = f32(synth.standard_normal(g.m, 22))
     base = ct_geom_get_launch_shapes(G)
     ya, xb = gpu_A(G, x), gpu_B(G, y)
-    for a_threads, a_views in ((128, 1), (256, 2), (512, 8), (128, 4)):
-        for b_rows, b_views in ((4, 1), (8, 2), (16, 1), (4, 2)):
-            sh = dict(base, a_threads=a_threads, a_views=a_views, b_rows=b_rows, b_views=b_views)
-            ct_geom_set_launch_shapes(G, sh)
-            assert ct_geom_get_launch_shapes(G) == sh
-            assert np.array_equal(gpu_A(G, x), ya)
-            assert np.array_equal(gpu_B(G, y), xb)
+    for a_threads, a_views, a_wv in ((128, 1, 1), (256, 2, 1), (512, 8, 1), (128, 4, 1),
+                                     (128, 2, 2), (128, 4, 4), (256, 8, 8), (512, 8, 4),
+                                     (128, 8, 8)):
+        sh = dict(base, a_threads=a_threads, a_views=a_views, a_warp_views=a_wv)
+        ct_geom_set_launch_shapes(G, sh)
+        assert ct_geom_get_launch_shapes(G) == sh
+        assert np.array_equal(gpu_A(G, x), ya)
+    for b_rows, b_views, b_wr in ((4, 1, 1), (8, 2, 1), (16, 1, 1), (4, 2, 1), (4, 1, 4),
+                                  (8, 1, 2), (16, 1, 4), (4, 2, 2), (8, 2, 4)):
+        sh = dict(base, b_rows=b_rows, b_views=b_views, b_warp_rows=b_wr)
+        ct_geom_set_launch_shapes(G, sh)
+        assert ct_geom_get_launch_shapes(G) == sh
+        assert np.array_equal(gpu_B(G, y), xb)
+
+
+def test_warp_shapes_out_of_range_are_rejected():
+    """Views per Joseph warp must divide the views per block and leave a warp no more bins than
+    the block has; pixel rows per B warp must fit the block's (orbit) rows.  A refused shape
+    leaves the geometry's shapes unchanged."""
+    from paper_2602_17892_gb300 import _binding as Bn
+    from paper_2602_17892_gb300 import ct_geom_get_launch_shapes, ct_geom_set_launch_shapes
+    G = gpu_geom(GEOMS["fan_64"])
+    base = ct_geom_get_launch_shapes(G)
+    for bad in (dict(a_threads=128, a_views=2, a_warp_views=4),
+                dict(a_threads=128, a_views=8, a_warp_views=1),
+                dict(a_threads=128, a_views=4, a_warp_views=3),
+                dict(b_rows=4, b_views=1, b_warp_rows=8),
+                dict(b_rows=4, b_views=4, b_warp_rows=4),      # four-fold: 2 orbit rows
+                dict(b_rows=16, b_views=4, b_warp_rows=4)):
+        with pytest.raises(Bn.CtError):
+            ct_geom_set_launch_shapes(G, dict(base, **bad))
+        assert ct_geom_get_launch_shapes(G) == base
 
 
 @pytest.mark.parametrize("kind", ["parallel", "fan"])
@@ -163,6 +189,10 @@ def test_four_fold_backprojector(name):
         _check_B_entries(g, y, xg, xo)
         assert rel(xg, x_general) <= 1e-6
         outs.append(xg)
+        # warps of 16 x 2 (and 8 x 4) orbit positions: the same sums in the same order
+        for wr in ((2, 4) if rows == 8 else (2,)):
+            ct_geom_set_launch_shapes(G, dict(base, b_rows=rows, b_views=4, b_warp_rows=wr))
+            assert np.array_equal(gpu_B(G, y), xg)
     assert np.array_equal(outs[0], outs[1])          # the same two view parts
     assert rel(outs[2], outs[0]) <= 1e-6             # four parts: another order of the sums
 
