@@ -329,10 +329,11 @@ __device__ __forceinline__ RayJ decode_ray2d(const Ray2D R, int nx, int ny, floa
     return r;
 }
 
-constexpr int kJBatch = 4;   // line pairs per batch of the Joseph loop
+constexpr int kJBatch = 8;   // line pairs per batch of the Joseph loop
 
-// at most 64 registers a thread (two blocks of 512 threads per SM) for the batched gathers
-__global__ void __launch_bounds__(512, 2) joseph2d_kernel(
+// 16 gathers in flight a thread (8 line pairs per batch) take 96 registers: 5 blocks of 128
+// threads (20 warps) per SM, against 27 warps with 8 gathers at 64 registers (4 % slower)
+__global__ void __launch_bounds__(512, 1) joseph2d_kernel(
     const Ray2D *__restrict__ rays, int n_views, int ndu, int vpb, int wv,
     const float2 *__restrict__ prow, int prow_ld, const float2 *__restrict__ pcol, int pcol_ld,
     int nx, int ny, float h, float *__restrict__ y, int y_ld, int y_off, const int *stop)
@@ -648,15 +649,17 @@ __global__ void __launch_bounds__(VP == 2 ? 256 : 512, VP == 2 ? 3 : 1) pixbp2d_
 // (grid (c, r), (r, N-1-c), (N-1-c, N-1-r), (N-1-r, c), with (c, r) in the first quadrant)
 // and, for each base view k < n/4, forms the four geometries g_j = (fj, w)(theta_k, p_j) once
 // (pe_2 = -pe_0 and pe_3 = -pe_1 exactly); pixel p_i takes view k + m n/4 at g_{(i+m) mod 4}:
-// 16 pixel-view pairs from 4 geometry evaluations.  The 16 gathers of a base view are issued
-// together, then the sums (pixel by pixel, m in order).  The base views are split into
+// 16 pixel-view pairs from 4 geometry evaluations.  Base views go two at a time: both views'
+// geometries, then their 32 gathers together, then the sums (view by view, pixel by pixel, m in
+// order); launch bounds for 16 warps per SM at up to 128 registers (24 warps with one view at
+// a time: 3 % slower).  The base views are split into
 // blockDim.z consecutive parts (2 or 4), one per z layer of the block, whose sums are added in
 // shared memory in part order (more parts: more threads in flight and a shorter last wave).
 // A warp takes a tile of 32 / wr by wr orbit positions, as in pixbp2d_kernel.  The arithmetic of one
 // pixel-view pair is the one of pixbp2d_view; only the views' constants (those of view k, for
 // the rotated pixel) and the order of the sums differ from the general kernel.
 template <bool CLAMP>
-__global__ void __launch_bounds__(256, 3) pixbp2d_rot4_kernel(
+__global__ void __launch_bounds__(256, 2) pixbp2d_rot4_kernel(
     const ViewBP *__restrict__ views, int q4, const float2 *__restrict__ ypair, int ld,
     int vchunk, int nd, int N, float sid_h, float k_u, float k_w, int wr, float *__restrict__ x,
     const int *stop)
@@ -692,7 +695,57 @@ __global__ void __launch_bounds__(256, 3) pixbp2d_rot4_kernel(
 #pragma unroll
             for (int m = 1; m < 4; ++m) rb[m] = rb[m - 1] + moff;
             float K = kFloor2p23 + cb;                   // + (k - k0) ld
-            for (int k = k0; k < k1; ++k) {
+            // two base views per iteration: both views' geometry, then their 32 gathers, then
+            // the sums in view order (the same operations and order as one view at a time)
+            int k = k0;
+            for (; k + 1 < k1; k += 2) {
+                float fj[2][4], w[2][4];
+                uint32_t ia[2][4];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const float2 V = srot[k + u];
+                    const float cs = V.x, sn = V.y;
+                    float pe[4], bb[4];
+                    pe[0] = fmaf(tr, cs, -tc * sn);
+                    pe[1] = fmaf(-tc, cs, -tr * sn);
+                    pe[2] = -pe[0];
+                    pe[3] = -pe[1];
+                    bb[0] = fmaf(-tc, cs, fmaf(-tr, sn, sid_h));
+                    bb[1] = fmaf(-tr, cs, fmaf(tc, sn, sid_h));
+                    bb[2] = fmaf(tc, cs, fmaf(tr, sn, sid_h));
+                    bb[3] = fmaf(tr, cs, fmaf(-tc, sn, sid_h));
+                    const float Ku = K + (float)(u * ld);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float rbb = __fdividef(1.f, bb[j]);
+                        const float t1 = pe[j] * rbb;
+                        float f = fmaf(t1, k_u, gam);
+                        if (CLAMP) f = fminf(fmaxf(f, clo), chi);
+                        fj[u][j] = f;
+                        w[u][j] = rbb * sqrtf(fmaf(t1, t1, 1.f));
+                        ia[u][j] = __float_as_uint(__fadd_rd(f, Ku));
+                    }
+                }
+                float2 tap[2][16];
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            tap[u][4 * m + i] = __ldg(reinterpret_cast<const float2 *>(rb[m] + 8ull * ia[u][(i + m) & 3]));
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            const int g = (i + m) & 3;
+                            acc[i] = fmaf(w[u][g], fmaf(fj[u][g], tap[u][4 * m + i].y, tap[u][4 * m + i].x), acc[i]);
+                        }
+                K += 2.f * (float)ld;
+            }
+            for (; k < k1; ++k) {
                 const float2 V = srot[k];
                 const float cs = V.x, sn = V.y;
                 float pe[4], bb[4], fj[4], w[4];

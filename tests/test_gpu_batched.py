@@ -84,9 +84,16 @@ def test_abba_solve_one_shot_and_breakdown_inside_batch():
     x1, b1, e1 = problem(g1, 7, 0.01, 8)
     G1, G2 = gpu_geom(g1), gpu_geom(g2)
     sh = ct_geom_autotune(G2)
-    assert (sh["a_threads"], sh["a_views"]) in ((128, 1), (128, 2), (128, 4), (256, 1), (256, 2),
-                                                (256, 4), (512, 4), (512, 8))
-    assert (sh["b_rows"], sh["b_views"]) in ((4, 1), (8, 1), (16, 1), (4, 2), (8, 2))
+    # the autotuner's candidates (threads, views per block, views per warp) for the Joseph A and
+    # (pixel rows per block, views per iteration, pixel rows per warp) for B; this scan has no
+    # four-fold symmetry (30 views), so B's four-fold shapes are not among them
+    assert (sh["a_threads"], sh["a_views"], sh["a_warp_views"]) in (
+        (128, 1, 1), (128, 2, 1), (128, 4, 1), (256, 1, 1), (256, 2, 1), (256, 4, 1), (512, 4, 1),
+        (512, 8, 1), (128, 2, 2), (128, 4, 2), (128, 4, 4), (256, 4, 4), (256, 8, 4), (256, 8, 8),
+        (512, 8, 4))
+    assert (sh["b_rows"], sh["b_views"], sh["b_warp_rows"]) in tuple(
+        (rows, views, wr) for wr in (1, 2, 4) for rows, views in ((4, 1), (8, 1), (16, 1), (4, 2),
+                                                                  (8, 2)))
     bs = [to_dev(b1), torch.zeros(G2.m, dtype=torch.float32, device="cuda")]
     xs = [torch.zeros(G.n, dtype=torch.float32, device="cuda") for G in (G1, G2)]
     infos = abba_solve([G1, G2], bs, xs, methods=["ab", "ab"], max_iters=8, rule="gcv")
