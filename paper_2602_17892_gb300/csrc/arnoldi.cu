@@ -354,6 +354,11 @@ cudaError_t arnoldi_prepare()
 // order, so results are reproducible run to run.
 constexpr int kTileUnits = 32;                  // 4-element units per tile row (one per lane)
 constexpr int kTileElems = 4 * kTileUnits;      // 128 elements
+// threads of a tile CTA: the passes stream HBM through TMA copies and their arithmetic is light
+// (a few instructions a tile row a warp), so four warps keep up, and a CTA holds half the
+// registers that eight would: in a batch the other solve's projector kernels share the SM
+constexpr int kTileThreads = 128;
+constexpr int kTileWarps = kTileThreads / 32;
 constexpr int kTileSmemMax = 220 * 1024;        // dynamic shared memory of one CTA at most
 constexpr int kTilePair = 110 * 1024;           // at most this much for two CTAs per SM
 constexpr long long kWaitCycles = 1ll << 31;    // bounded mbarrier waits (about a second)
@@ -485,7 +490,7 @@ __host__ __device__ constexpr int tile_stage_bytes(int nvec)
 }
 
 template <int MODE, typename T>
-__global__ void __launch_bounds__(kThreads, 2) cgs_tile_kernel(const __grid_constant__ CUtensorMap wmap,
+__global__ void __launch_bounds__(kTileThreads, 2) cgs_tile_kernel(const __grid_constant__ CUtensorMap wmap,
                                                                TileArgs a)
 {
     if (a.stop[0] != 0) return;
@@ -501,18 +506,18 @@ __global__ void __launch_bounds__(kThreads, 2) cgs_tile_kernel(const __grid_cons
     float *acc = reinterpret_cast<float *>(p);
     p += 16 * ((nvec + 1 + 3) / 4);
     float4 *red = reinterpret_cast<float4 *>(p);
-    float4 *qs = red + kWarps * kTileUnits;
+    float4 *qs = red + kTileWarps * kTileUnits;
     float *scoef = reinterpret_cast<float *>(qs + kTileUnits);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ncol = nvec + 1;
-    for (int i = tid; i < ncol; i += kThreads) acc[i] = 0.f;
+    for (int i = tid; i < ncol; i += kTileThreads) acc[i] = 0.f;
     float inv_nu = 0.f;
     if (MODE == T_UPD_SCALE) {
         // h_{k+1,k} = nu = sqrt(||q'||^2 - ||h2||^2), every block the same value (fixed order);
         // block 0 records it and the breakdown test of the paper's Arnoldi loop
-        __shared__ double hsum[kWarps];
+        __shared__ double hsum[kTileWarps];
         double h2 = 0.0;
-        for (int i = tid; i < nvec; i += kThreads) {
+        for (int i = tid; i < nvec; i += kTileThreads) {
             const double c = a.coef[i];
             h2 = fma(c, c, h2);
             scoef[i] = (float)c;
@@ -522,7 +527,7 @@ __global__ void __launch_bounds__(kThreads, 2) cgs_tile_kernel(const __grid_cons
         if (lane == 0) hsum[warp] = h2;
         __syncthreads();
         double t = 0.0;
-        for (int w = 0; w < kWarps; ++w) t += hsum[w];
+        for (int w = 0; w < kTileWarps; ++w) t += hsum[w];
         const double nrm = sqrt(fmax(a.aux[4] - t, 0.0));
         const bool bad = !isfinite(nrm), brk = !(nrm > kBreakdownTol * a.aux[0]);
         if (blockIdx.x == 0 && tid == 0) {
@@ -536,7 +541,7 @@ __global__ void __launch_bounds__(kThreads, 2) cgs_tile_kernel(const __grid_cons
         if (a.wnext == nullptr) return;
         inv_nu = (float)(1.0 / nrm);
     } else if (MODE == T_UPD_DOTS) {
-        for (int i = tid; i < nvec; i += kThreads) scoef[i] = (float)a.coef[i];
+        for (int i = tid; i < nvec; i += kTileThreads) scoef[i] = (float)a.coef[i];
     }
     if (tid == 0) {
         for (int st = 0; st < S; ++st) mbar_init(&bars[st], 1);
@@ -577,7 +582,7 @@ __global__ void __launch_bounds__(kThreads, 2) cgs_tile_kernel(const __grid_cons
         if (MODE != T_DOTS) {
             // per-lane sum over this warp's rows of coef_r * W[r], then the 8 warps' sums
             float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int r = warp; r < nvec; r += kWarps) {
+            for (int r = warp; r < nvec; r += kTileWarps) {
                 const float c = scoef[r];
                 const float4 w = unit_from_smem<T>(tileb + (size_t)r * seg, lane);
                 u.x = fmaf(c, w.x, u.x); u.y = fmaf(c, w.y, u.y);
@@ -588,7 +593,7 @@ __global__ void __launch_bounds__(kThreads, 2) cgs_tile_kernel(const __grid_cons
             if (warp == 0) {
                 float4 t = red[lane];
 #pragma unroll
-                for (int w = 1; w < kWarps; ++w) {
+                for (int w = 1; w < kTileWarps; ++w) {
                     const float4 o = red[w * kTileUnits + lane];
                     t.x += o.x; t.y += o.y; t.z += o.z; t.w += o.w;
                 }
@@ -613,7 +618,7 @@ __global__ void __launch_bounds__(kThreads, 2) cgs_tile_kernel(const __grid_cons
         }
         if (MODE != T_UPD_SCALE) {
             // dots of this warp's rows with v: 8 rows at a time, transposed shuffle reduction
-            for (int r0 = warp * 8; r0 < nvec; r0 += kWarps * 8) {
+            for (int r0 = warp * 8; r0 < nvec; r0 += kTileWarps * 8) {
                 float pd[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
@@ -661,7 +666,7 @@ __global__ void __launch_bounds__(kThreads, 2) cgs_tile_kernel(const __grid_cons
     __syncthreads();
     // block sums; cgs_tile_reduce_kernel adds them across blocks
     double *prow = a.partial + (int64_t)blockIdx.x * ncol;
-    for (int c = tid; c < ncol; c += kThreads) prow[c] = (double)acc[c];
+    for (int c = tid; c < ncol; c += kTileThreads) prow[c] = (double)acc[c];
 }
 
 // Cross-block sums of a T1 / T2 pass, one warp per column (all columns in parallel, each in a
@@ -694,7 +699,7 @@ static void tile_plan(int nvec, int &stages, int &per_sm, size_t &smem)
 {
     const int sb = tile_stage_bytes<T>(nvec);
     // mbarriers (<= 6 stages), block sums, warp partials and q', coefficients, spare
-    const int extra = 48 + 16 * ((nvec + 4) / 4) + 16 * (kWarps + 1) * kTileUnits + 4 * nvec + 64;
+    const int extra = 48 + 16 * ((nvec + 4) / 4) + 16 * (kTileWarps + 1) * kTileUnits + 4 * nvec + 64;
     if (2 * sb + extra <= kTilePair) {
         stages = std::min(6, (kTilePair - extra) / sb);
         per_sm = 2;
@@ -811,15 +816,15 @@ static bool arnoldi_step_tiled(void *W, int64_t ld, int k, float *q, double *hco
     TileArgs a{W, ld, nvec, q, q, ntiles, stages, nullptr, sc.partial, sc.counter, hcol, aux,
                h1, stop, step, nullptr, nullptr};
     const int rblocks = (nvec + 1 + kWarps - 1) / kWarps;
-    cgs_tile_kernel<T_DOTS, T><<<blocks, kThreads, smem, s>>>(wmap, a);
+    cgs_tile_kernel<T_DOTS, T><<<blocks, kTileThreads, smem, s>>>(wmap, a);
     cgs_tile_reduce_kernel<T_DOTS><<<rblocks, kThreads, 0, s>>>(a, blocks);
     a.coef = h1; a.coef_out = h2;
-    cgs_tile_kernel<T_UPD_DOTS, T><<<blocks, kThreads, smem, s>>>(wmap, a);
+    cgs_tile_kernel<T_UPD_DOTS, T><<<blocks, kTileThreads, smem, s>>>(wmap, a);
     cgs_tile_reduce_kernel<T_UPD_DOTS><<<rblocks, kThreads, 0, s>>>(a, blocks);
     a.coef = h2; a.coef_out = nullptr;
     a.wnext = next ? static_cast<char *>(W) + (size_t)(k + 1) * ld * sizeof(T) : nullptr;
     a.cur = next ? cur : nullptr;
-    cgs_tile_kernel<T_UPD_SCALE, T><<<next ? blocks : 1, kThreads, smem, s>>>(wmap, a);
+    cgs_tile_kernel<T_UPD_SCALE, T><<<next ? blocks : 1, kTileThreads, smem, s>>>(wmap, a);
     err = cudaGetLastError();
     return true;
 }

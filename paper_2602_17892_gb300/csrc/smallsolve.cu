@@ -544,22 +544,60 @@ __global__ void __launch_bounds__(kSSThreads, 1) small_solve_kernel(SmallSolvePa
         hi32[i] = hi;
     }
     __syncthreads();
-    // FP64: brackets that overlap a neighbour's are isolated by FP64 Sturm-count bisection, then
-    // safeguarded Newton on det(theta I - T); c_i^2 by the first-component formula
+    // FP64: brackets that overlap a neighbour's are isolated by FP64 Sturm-count multisection,
+    // one warp per value: its 32 lanes count at 32 points of the bracket at once (an FP64 warp
+    // instruction costs the same with 1 or 32 lanes active), which narrows the bracket 33-fold
+    // per round where bisection halves it.  Then safeguarded Newton on det(theta I - T), one
+    // thread per value; c_i^2 by the first-component formula.
+    double *sblo = dsv, *sbhi = esv;                 // brackets (dsv, esv are free until y)
+    int *niso = reinterpret_cast<int *>(gsv);        // the values to isolate, then their count
     for (int i = tid; i < k; i += kSSThreads) {
-        double blo = (double)lo32[i] * (1.0 - 2e-4), bhi = (double)hi32[i] * (1.0 + 2e-4);
+        const double blo = (double)lo32[i] * (1.0 - 2e-4), bhi = (double)hi32[i] * (1.0 + 2e-4);
         const bool iso = (i == 0 || (double)lo32[i - 1] * (1.0 - 2e-4) > bhi) &&
                          (i == k - 1 || (double)hi32[i + 1] * (1.0 + 2e-4) < blo);
-        if (!iso) {
-            const int tgt = k - i;
-            int clo = count64(t2, n, blo) - (k + 1), chi = count64(t2, n, bhi) - (k + 1);
-            if (!(clo <= tgt - 1 && chi >= tgt)) { blo = 0.0; bhi = 2.0; clo = 0; chi = k; }
-            for (int it = 0; it < 200 && chi - clo > 1 && bhi - blo > 1e-15 * bhi; ++it) {
-                double mid = 0.5 * (blo + bhi);
-                int cm = count64(t2, n, mid) - (k + 1);
-                if (cm >= tgt) { bhi = mid; chi = cm; } else { blo = mid; clo = cm; }
+        sblo[i] = blo;
+        sbhi[i] = iso ? bhi : -bhi;                  // sign: still to isolate
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int m = 0;
+        for (int i = 0; i < k; ++i)
+            if (sbhi[i] < 0.0) { sbhi[i] = -sbhi[i]; niso[1 + m++] = i; }
+        niso[0] = m;
+    }
+    __syncthreads();
+    for (int v = warp; v < niso[0]; v += nwarps) {
+        const int i = niso[1 + v], tgt = k - i;
+        double blo = sblo[i], bhi = sbhi[i];
+        int clo = 0, chi = k;
+        // round 0 counts at both ends (lanes 0 and 31) and 30 points between; later rounds at
+        // 32 interior points.  Counts grow with x; the first lane with count >= tgt bounds the
+        // value from above, the lane before it from below.
+        for (int round = 0; round < 40; ++round) {
+            const double w = bhi - blo;
+            const double x = (round == 0) ? blo + w * ((double)lane * (1.0 / 31.0))
+                                          : blo + w * ((double)(lane + 1) * (1.0 / 33.0));
+            const int c = count64(t2, n, x) - (k + 1);
+            if (round == 0) {
+                const int c0 = __shfl_sync(0xffffffffu, c, 0), c31 = __shfl_sync(0xffffffffu, c, 31);
+                if (!(c0 <= tgt - 1 && c31 >= tgt)) {     // not a bracket: the whole range
+                    blo = 0.0; bhi = 2.0; clo = 0; chi = k;
+                    continue;
+                }
             }
+            const unsigned up = __ballot_sync(0xffffffffu, c >= tgt);
+            const int f = up ? __ffs(up) - 1 : 32;
+            const double xf = __shfl_sync(0xffffffffu, x, f & 31), xb = __shfl_sync(0xffffffffu, x, (f + 31) & 31);
+            const int cf = __shfl_sync(0xffffffffu, c, f & 31), cb = __shfl_sync(0xffffffffu, c, (f + 31) & 31);
+            if (f < 32) { bhi = xf; chi = cf; }
+            if (f > 0) { blo = xb; clo = cb; }
+            if (!(chi - clo > 1 && bhi - blo > 1e-15 * bhi)) break;
         }
+        if (lane == 0) { sblo[i] = blo; sbhi[i] = bhi; }
+    }
+    __syncthreads();
+    for (int i = tid; i < k; i += kSSThreads) {
+        double blo = sblo[i], bhi = sbhi[i];
         double th = 0.5 * (blo + bhi), th_eval = th;
         double p = 0.0, dp = 0.0;
         int ex = 0;
