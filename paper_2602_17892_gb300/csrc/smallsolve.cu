@@ -124,6 +124,120 @@ __device__ void make_reflector(double alpha, double xnorm2, double &beta, double
     scale = rcp64(alpha - beta);
 }
 
+// Double-FP32 ("double-float") arithmetic for the fast path's bidiagonalisation: a value is an
+// unevaluated sum hi + lo of two FP32 numbers with |lo| <= ulp(hi) / 2 (about 48 significant
+// bits).  The error-free transformations are the published ones: Knuth's TwoSum for a sum,
+// the fused multiply-add form of Dekker's TwoProduct for a product, and Dekker's FastTwoSum to
+// renormalise; the operations carry explicit rounding (no contraction into other operations).
+// On GB300 an FP64 instruction holds its sub-partition's FP64 unit for about 67 cycles, while
+// these FP32 operations pipeline at full rate, so a double-float multiply-add of about fifteen
+// FP32 operations is several times faster than one FP64 multiply-add in a serial chain.
+__device__ __forceinline__ float2 df_fast_two_sum(float s, float e)
+{
+    const float h = __fadd_rn(s, e);
+    return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+__device__ __forceinline__ float2 df_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+    return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+// c + a b
+__device__ __forceinline__ float2 df_fma(float2 c, float2 a, float2 b)
+{
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    const float2 st = df_two_sum(c.x, p);
+    return df_fast_two_sum(st.x, __fadd_rn(st.y, __fadd_rn(c.y, e)));
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b)
+{
+    const float2 st = df_two_sum(a.x, b.x);
+    return df_fast_two_sum(st.x, __fadd_rn(st.y, __fadd_rn(a.y, b.y)));
+}
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b)
+{
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 df_from(double v)
+{
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+}
+__device__ __forceinline__ double df_to(float2 a) { return (double)a.x + (double)a.y; }
+// x[m * sx] += w * v[m * sv] for m in [0, n), four elements at a time: their loads first, then
+// the four independent double-float multiply-adds, then the stores (a shared-memory load cannot
+// pass a store to a possibly equal address, so one element at a time would serialise them)
+__device__ __forceinline__ void df_axpy(float2 *x, int sx, const float2 *v, int sv, int n, float2 w)
+{
+    int m = 0;
+    for (; m + 3 < n; m += 4) {
+        const float2 x0 = x[m * sx], x1 = x[(m + 1) * sx], x2 = x[(m + 2) * sx], x3 = x[(m + 3) * sx];
+        const float2 v0 = v[m * sv], v1 = v[(m + 1) * sv], v2 = v[(m + 2) * sv], v3 = v[(m + 3) * sv];
+        const float2 y0 = df_fma(x0, w, v0), y1 = df_fma(x1, w, v1);
+        const float2 y2 = df_fma(x2, w, v2), y3 = df_fma(x3, w, v3);
+        x[m * sx] = y0; x[(m + 1) * sx] = y1; x[(m + 2) * sx] = y2; x[(m + 3) * sx] = y3;
+    }
+    for (; m < n; ++m) x[m * sx] = df_fma(x[m * sx], w, v[m * sv]);
+}
+// sum over m in [0, n) of a[m * sa] b[m * sb], in four interleaved double-float sums
+__device__ __forceinline__ float2 df_dot(const float2 *a, int sa, const float2 *b, int sb, int n)
+{
+    float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;
+    int m = 0;
+    for (; m + 3 < n; m += 4) {
+        s0 = df_fma(s0, a[m * sa], b[m * sb]);
+        s1 = df_fma(s1, a[(m + 1) * sa], b[(m + 1) * sb]);
+        s2 = df_fma(s2, a[(m + 2) * sa], b[(m + 2) * sb]);
+        s3 = df_fma(s3, a[(m + 3) * sa], b[(m + 3) * sb]);
+    }
+    for (; m < n; ++m) s0 = df_fma(s0, a[m * sa], b[m * sb]);
+    return df_add(df_add(s0, s1), df_add(s2, s3));
+}
+// sqrt(q), q > 0: the correctly rounded FP32 root refined by one Newton step (Karp's form,
+// s + (q - s^2) / (2 s), with s^2 split exactly): about 48 bits
+__device__ __forceinline__ float2 df_sqrt(float2 q)
+{
+    const float sr = __fsqrt_rn(q.x);
+    const float p = __fmul_rn(sr, sr), e = __fmaf_rn(sr, sr, -p);
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(q.x, p), e), q.y);
+    return df_fast_two_sum(sr, __fmul_rn(r, __fdividef(0.5f, sr)));
+}
+// 1 / b, b != 0: the correctly rounded FP32 reciprocal refined by one Newton step,
+// x + x (1 - b x) with b x split exactly
+__device__ __forceinline__ float2 df_rcp(float2 b)
+{
+    const float x = __frcp_rn(b.x);
+    const float p = __fmul_rn(b.x, x), e = __fmaf_rn(b.x, x, -p);
+    const float r = __fsub_rn(__fsub_rn(__fsub_rn(1.f, p), e), __fmul_rn(b.y, x));
+    return df_fast_two_sum(x, __fmul_rn(x, r));
+}
+// make_reflector in double-float: [alpha; x] -> [beta; 0] by I - tau [1; v][1; v]^T,
+// v = x * scale, from alpha and ||x||^2
+__device__ __forceinline__ void make_reflector_df(float2 alpha, float2 xn2, float2 &beta,
+                                                  float2 &tau, float2 &scale)
+{
+    if (xn2.x == 0.f) { beta = alpha; tau = make_float2(0.f, 0.f); scale = tau; return; }
+    const float2 nrm = df_sqrt(df_fma(xn2, alpha, alpha));
+    beta = (alpha.x >= 0.f) ? df_neg(nrm) : nrm;
+    tau = df_mul(df_add(beta, df_neg(alpha)), df_rcp(beta));
+    scale = df_rcp(df_add(alpha, df_neg(beta)));
+}
+__device__ __forceinline__ float2 warp_sum_df(float2 v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = df_add(v, make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)));
+    return v;
+}
+
 // Implicit-shift QR on the upper bidiagonal (d, e), left rotations applied to g.  One thread.
 __device__ int bidiag_svd_serial(double *d, double *e, double *g, int n)
 {
@@ -313,7 +427,7 @@ __device__ __forceinline__ void axpy_sub(double *x, int sx, const double *v, int
 
 size_t small_solve_smem_bytes(int k)
 {
-    size_t nd = (size_t)(k + 1) * k + 16 * (size_t)(k + 1) + kGcvGrid + 64;
+    size_t nd = (size_t)((k + 1) | 1) * k + 16 * (size_t)(k + 1) + kGcvGrid + 64;
     return nd * sizeof(double);
 }
 
@@ -342,8 +456,11 @@ __global__ void __launch_bounds__(kSSThreads, 1) small_solve_kernel(SmallSolvePa
     }
     const bool need_y = P.always_y || k == P.kmax || stop_now || P.only_y || k == P.y_at;
     extern __shared__ double sd[];
-    const int lda = k + 1;
-    double *A = sd;                       // (k+1) x k, column-major
+    // (k+1) x k, column-major, leading dimension odd: a warp's threads walking columns at once
+    // (one column each) then touch 8-byte words lda apart, which an even lda would put in one
+    // shared-memory bank
+    const int lda = (k + 1) | 1;
+    double *A = sd;
     double *g = A + (size_t)lda * k;      // k+1
     double *d = g + (k + 1);              // k
     double *e = d + (k + 1);              // k
@@ -368,7 +485,7 @@ __global__ void __launch_bounds__(kSSThreads, 1) small_solve_kernel(SmallSolvePa
     auto load_H = [&]() {
         for (int t = tid; t < lda * k; t += kSSThreads) {
             int c = t / lda, r = t - c * lda;
-            A[t] = P.H[(size_t)c * P.ldh + r];
+            A[t] = (r <= k) ? P.H[(size_t)c * P.ldh + r] : 0.0;   // the padding row is zero
         }
         for (int t = tid; t <= k; t += kSSThreads) g[t] = (t == 0) ? beta : 0.0;
         __syncthreads();
@@ -421,75 +538,97 @@ __global__ void __launch_bounds__(kSSThreads, 1) small_solve_kernel(SmallSolvePa
     // ================================================================ fast path
     // lower bidiagonalisation of H_k ((k+1) x k) with e1 fixed: right reflector on row j
     // (columns j..k-1) -> alpha_j = d[j]; left reflector on column j (rows j+1..k) ->
-    // beta_{j+1} = e[j].  Rows/columns are applied one per thread (no shuffles).
+    // beta_{j+1} = e[j].  Rows/columns are applied one per thread (no shuffles).  The matrix is
+    // held in double-float in place of its FP64 copy (an element's hi and lo in its 8 bytes) and
+    // the updates run in double-float; each reflector is formed in FP64 from its double-float
+    // vector (make_reflector), and d, e, tau are kept in FP64.  At the end the matrix, which now
+    // holds the scaled right reflectors the y step applies, is turned back into FP64.  Double-
+    // float has FP32's exponent range, so the matrix is first scaled by a power of two that
+    // brings its largest entry into [1, 2) (the reflectors do not change; d and e are scaled
+    // back); the exponents are compared as integers on the high words.
+    float2 *Af = reinterpret_cast<float2 *>(A);
+    int *emax = reinterpret_cast<int *>(misc + 12);
+    if (tid == 0) *emax = 0;
+    __syncthreads();
+    {
+        int em = 0;
+        for (int t = tid; t < lda * k; t += kSSThreads) em = max(em, (__double2hiint(A[t]) >> 20) & 0x7ff);
+        em = __reduce_max_sync(0xffffffffu, em);
+        if (lane == 0) atomicMax(emax, em);
+    }
+    __syncthreads();
+    // 2^(1023 - emax) and its inverse as FP64 bit patterns (a zero or subnormal matrix: 1)
+    const int eb = (*emax >= 1 && *emax <= 2045) ? *emax : 1023;
+    const double dscale = __hiloint2double((2046 - eb) << 20, 0);
+    const double dunscale = __hiloint2double(eb << 20, 0);
+    for (int t = tid; t < lda * k; t += kSSThreads) Af[t] = df_from(A[t] * dscale);
+    __syncthreads();
+    // reflector constants (beta, tau, scale) in double-float, and d, e, tau kept in double-float
+    // in their FP64 slots until the end
+    float2 *mf = reinterpret_cast<float2 *>(misc + 16);
+    float2 *dF = reinterpret_cast<float2 *>(d), *eF = reinterpret_cast<float2 *>(e);
+    float2 *tF = reinterpret_cast<float2 *>(tauR);
     for (int j = 0; j < k; ++j) {
         if (warp == 0) {
-            double s2 = 0.0;
-            for (int l = j + 1 + lane; l < k; l += 32) s2 += A[l * lda + j] * A[l * lda + j];
-            s2 = warp_sum_d(s2);
-            if (lane == 0) {
-                double bt, tau, sc;
-                make_reflector(A[j * lda + j], s2, bt, tau, sc);
-                misc[0] = bt; misc[1] = tau; misc[2] = sc;
-            }
+            float2 s2 = make_float2(0.f, 0.f);
+            for (int l = j + 1 + lane; l < k; l += 32) s2 = df_fma(s2, Af[l * lda + j], Af[l * lda + j]);
+            s2 = warp_sum_df(s2);
+            if (lane == 0) make_reflector_df(Af[j * lda + j], s2, mf[0], mf[1], mf[2]);
         }
         __syncthreads();
         {
-            const double bt = misc[0], tau = misc[1], sc = misc[2];
-            for (int l = j + 1 + tid; l < k; l += kSSThreads) A[l * lda + j] *= sc;
+            const float2 bt = mf[0], tauf = mf[1], scf = mf[2];
+            for (int l = j + 1 + tid; l < k; l += kSSThreads) Af[l * lda + j] = df_mul(Af[l * lda + j], scf);
             __syncthreads();
-            if (tau != 0.0) {
+            if (tauf.x != 0.f) {
                 for (int i = j + 1 + tid; i <= k; i += kSSThreads) {   // row i
-                    double w0 = A[j * lda + i], w1 = 0.0;
-                    int l = j + 1;
-                    for (; l + 1 < k; l += 2) {
-                        w0 += A[l * lda + j] * A[l * lda + i];
-                        w1 += A[(l + 1) * lda + j] * A[(l + 1) * lda + i];
-                    }
-                    if (l < k) w0 += A[l * lda + j] * A[l * lda + i];
-                    const double w = (w0 + w1) * tau;
-                    A[j * lda + i] -= w;
-                    axpy_sub(A + (size_t)(j + 1) * lda + i, lda, A + (size_t)(j + 1) * lda + j, lda,
-                             k - j - 1, w);
+                    const float2 *vj = Af + (size_t)(j + 1) * lda + j;  // v_l, l > j (stride lda)
+                    float2 *ri = Af + (size_t)(j + 1) * lda + i;         // A[i][l], l > j
+                    const float2 w = df_add(Af[j * lda + i], df_dot(vj, lda, ri, lda, k - j - 1));
+                    const float2 nw = df_neg(df_mul(w, tauf));
+                    Af[j * lda + i] = df_add(Af[j * lda + i], nw);
+                    df_axpy(ri, lda, vj, lda, k - j - 1, nw);
                 }
             }
-            if (tid == 0) { A[j * lda + j] = bt; d[j] = bt; tauR[j] = tau; }
+            if (tid == 0) { Af[j * lda + j] = bt; dF[j] = bt; tF[j] = tauf; }
         }
         __syncthreads();
         if (warp == 0) {
-            double s2 = 0.0;
-            for (int i = j + 2 + lane; i <= k; i += 32) s2 += A[j * lda + i] * A[j * lda + i];
-            s2 = warp_sum_d(s2);
-            if (lane == 0) {
-                double bt, tau, sc;
-                make_reflector(A[j * lda + j + 1], s2, bt, tau, sc);
-                misc[0] = bt; misc[1] = tau; misc[2] = sc;
-            }
+            float2 s2 = make_float2(0.f, 0.f);
+            for (int i = j + 2 + lane; i <= k; i += 32) s2 = df_fma(s2, Af[j * lda + i], Af[j * lda + i]);
+            s2 = warp_sum_df(s2);
+            if (lane == 0) make_reflector_df(Af[j * lda + j + 1], s2, mf[0], mf[1], mf[2]);
         }
         __syncthreads();
         {
-            const double bt = misc[0], tau = misc[1], sc = misc[2];
-            for (int i = j + 2 + tid; i <= k; i += kSSThreads) A[j * lda + i] *= sc;
+            const float2 bt = mf[0], tauf = mf[1], scf = mf[2];
+            for (int i = j + 2 + tid; i <= k; i += kSSThreads) Af[j * lda + i] = df_mul(Af[j * lda + i], scf);
             __syncthreads();
-            if (tau != 0.0) {
+            if (tauf.x != 0.f) {
                 for (int l = j + 1 + tid; l < k; l += kSSThreads) {     // column l
-                    double *col = A + (size_t)l * lda;
-                    double w0 = col[j + 1], w1 = 0.0;
-                    int i = j + 2;
-                    for (; i + 1 <= k; i += 2) {
-                        w0 += A[j * lda + i] * col[i];
-                        w1 += A[j * lda + i + 1] * col[i + 1];
-                    }
-                    if (i <= k) w0 += A[j * lda + i] * col[i];
-                    const double w = (w0 + w1) * tau;
-                    col[j + 1] -= w;
-                    axpy_sub(col + j + 2, 1, A + (size_t)j * lda + j + 2, 1, k - j - 1, w);
+                    float2 *col = Af + (size_t)l * lda;
+                    const float2 *vj = Af + (size_t)j * lda + j + 2;     // v_i, i > j + 1
+                    const float2 w = df_add(col[j + 1], df_dot(vj, 1, col + j + 2, 1, k - j - 1));
+                    const float2 nw = df_neg(df_mul(w, tauf));
+                    col[j + 1] = df_add(col[j + 1], nw);
+                    df_axpy(col + j + 2, 1, vj, 1, k - j - 1, nw);
                 }
             }
-            if (tid == 0) { A[j * lda + j + 1] = bt; e[j] = bt; }
+            if (tid == 0) { Af[j * lda + j + 1] = bt; eF[j] = bt; }
         }
         __syncthreads();
     }
+    // d, e (scaled back) and tau to FP64 in place
+    for (int i = tid; i < k; i += kSSThreads) {
+        const double di = df_to(dF[i]) * dunscale, ei = df_to(eF[i]) * dunscale, ti = df_to(tF[i]);
+        d[i] = di; e[i] = ei; tauR[i] = ti;
+    }
+    // back to FP64 in place: each thread reads its elements before writing them
+    for (int t = tid; t < lda * k; t += kSSThreads) {
+        const double v = df_to(Af[t]);
+        A[t] = v;
+    }
+    __syncthreads();
     // Golub-Kahan tridiagonal T (n = 2k+1, zero diagonal) of the (k+1) x k lower bidiagonal:
     // off-diagonals alpha_0, beta_1, alpha_1, ..., alpha_{k-1}, beta_k; eigenvalues +-sigma_i, 0
     const int n = 2 * k + 1;
