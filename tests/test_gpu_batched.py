@@ -40,7 +40,7 @@ def _single(G, method, b, K, rule, **kw):
 @pytest.mark.parametrize("rule", ["gcv", "dp"])
 def test_batch_matches_single_solves_and_oracle(rule):
     import torch
-    from paper_2602_17892_gb300 import Batch
+    from paper_2602_17892_gb300 import Batch, ct_geom_get_launch_shapes, ct_geom_set_launch_shapes
     cases = _cases()
     data, geoms, methods, noises = [], [], [], []
     for i, (g, m) in enumerate(cases):
@@ -60,7 +60,12 @@ def test_batch_matches_single_solves_and_oracle(rule):
     for i, (g, mm, b, noise) in enumerate(data):
         assert infos[i]["iters_done"] == K, infos[i]
         xb = xs[i].cpu().numpy().astype(np.float64)
-        xs1 = _single(gpu_geom(g), mm, b, K, rule, noise_norm=noise, tau=1.01)
+        # the single solve with the launch shapes the batch's autotuner chose for this problem:
+        # shapes only reorder FP32 sums, and a GCV minimiser moves with such rounding by up to
+        # ~sqrt(eps), so the comparison is made at equal shapes
+        G1 = gpu_geom(g)
+        ct_geom_set_launch_shapes(G1, ct_geom_get_launch_shapes(geoms[i]))
+        xs1 = _single(G1, mm, b, K, rule, noise_norm=noise, tau=1.01)
         assert rel(xb, xs1) <= 1e-6, i
         if i in (0, 1):
             A, B = OP.operators(g)
