@@ -1,5 +1,5 @@
 // The hybrid step of Algorithms 1 and 2 (the lambda choice and Eq. (hybrid_proj)) on the
-// device, in FP64:
+// device, in FP64 (the fast path's bidiagonalisation in double-float, about 48 bits):
 // choose lambda for the (k+1) x k Hessenberg matrix H_k and solve Eq. (hybrid_proj)
 //     y = argmin || [H_k; lambda I] y - beta [e1; 0] ||.
 //
@@ -14,12 +14,12 @@
 //  1. Householder reduction of H_k to (k+1) x k LOWER bidiagonal Bd = P^T H_k Q with P e1 = e1
 //     (the left reflectors act on rows >= 2), so c_i = beta u_i(1) with u_i the left singular
 //     vectors of Bd: only first components are needed.  Reflectors are applied one row or one
-//     column per thread.
+//     column per thread, in double-float arithmetic (pairs of FP32 numbers) on the FP32 pipe.
 //  2. sigma_i: eigenvalues of the Golub-Kahan tridiagonal T of Bd (order 2k+1, zero diagonal,
 //     off-diagonals alpha_1, beta_2, alpha_2, ..., beta_{k+1}; eigenvalues +-sigma_i and 0):
 //     FP32 bisection (one thread per sigma_i, Sturm counts) gives a bracket, FP64 safeguarded
 //     Newton on det(theta I - T) refines it; brackets that touch a neighbour's are first
-//     isolated by FP64 Sturm-count bisection.
+//     isolated by FP64 Sturm-count multisection, one warp per value (32 counts a round).
 //  3. c_i^2 = 2 beta^2 z_i(1)^2 with z_i(1)^2 = det(sigma_i I - T_{2:n}) / p'(sigma_i), the
 //     first-component formula of a symmetric tridiagonal's eigenvectors.  For clusters
 //     (relative gap < 1e-6) the formula is ill-conditioned; their total weight is a contour
