@@ -113,3 +113,21 @@ def test_ncp_rule_and_test_hook_are_checked_on_the_host(lib):
     assert lib.ba_gmres_hybrid(ctypes.c_void_p(1), ctypes.c_void_p(16), None,
                                ctypes.c_void_p(16), ctypes.byref(o), None, None) == Bn.CT_EINVAL
     assert lib.ct_test_drop_tile_copy(1, 10) == Bn.CT_EINVAL   # limit below 2^16
+
+
+def test_launch_shape_fields_match_the_header_and_the_bench():
+    """ct_launch_shapes in include/ctabba.h, the binding's ctypes structure and the benchmark's
+    --launch-shapes keys list the same int fields in the same order; --launch-shapes takes six
+    integers (one view per Joseph warp, one pixel row per B warp) or all eight."""
+    import bench
+    from paper_2602_17892_gb300 import _binding as Bn
+    text = open(os.path.join(ROOT, "include", "ctabba.h")).read()
+    body = text.split("} ct_launch_shapes;")[0].rsplit("typedef struct {", 1)[1]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\bint\s+(\w+)\s*;", body)
+    assert fields == [f[0] for f in Bn.LaunchShapes._fields_]
+    assert list(bench.SHAPE_KEYS) == fields
+    assert bench.parse_shapes("128,4,16,4,4,1") == [128, 4, 16, 4, 4, 1, 1, 1]
+    assert bench.parse_shapes("128,4,16,4,4,1,4,2") == [128, 4, 16, 4, 4, 1, 4, 2]
+    with pytest.raises(SystemExit):
+        bench.parse_shapes("128,4,16,4,4,1,4")
