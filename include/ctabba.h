@@ -182,7 +182,8 @@ void ct_hybrid_opts_default(ct_hybrid_opts *o);
 
 /* Hybrid AB-GMRES, Algorithm 1 (Sec. 3): x0 = B u0 (u0 = 0 when u0_dev is NULL),
  * r0 = b - A x0, Arnoldi on A B with classical Gram-Schmidt applied twice, lambda_k by
- * `o->rule`, y_k from Eq. (hybrid_proj) through the SVD of H_k in FP64, and
+ * `o->rule`, y_k from Eq. (hybrid_proj) through the SVD of H_k in FP64 (its Householder
+ * bidiagonalisation in double-float, pairs of FP32 numbers with about 48 bits), and
  * x_K = x0 + B W_K y_K.  b_dev: m floats; x_dev: n floats (output).  The residual
  * r_k = b - A x_k of Algorithm 1 is not recomputed for the norm-based rules: ||b - A x_k||
  * equals the projected residual.
@@ -346,7 +347,9 @@ ct_status ct_arnoldi_step_noalloc(float *W_dev, int64_t len, int64_t ld, int k, 
  * (k+1) x k Hessenberg matrix H (FP64, column-major, leading dimension ldh >= k+1) and
  * beta = ||r0||, choose lambda by `rule` and return y (k doubles), lambda and the projected
  * residual ||H y - beta e1||.  All pointers are device pointers.  1 <= k <= 160;
- * any rule but CT_LAMBDA_LEARNED. */
+ * any rule but CT_LAMBDA_LEARNED.  The singular values and first components come from a
+ * bidiagonal form computed in double-float (about 48 bits) and FP64 Sturm counts and Newton
+ * steps; if their Parseval check fails, the solve falls back to a sequential FP64 SVD. */
 ct_status ct_projected_solve(const double *H_dev, int ldh, int k, double beta,
                              ct_lambda_rule rule, double lambda_fixed, double dp_target,
                              double *y_dev, double *lambda_dev, double *resid_dev,
@@ -419,7 +422,7 @@ enum {
     CT_PH_BACK = 1,      /* pixel-driven B kernel                             */
     CT_PH_LAYOUT = 2,    /* image pair layouts / padded sinogram copies        */
     CT_PH_ARNOLDI = 3,   /* the four Gram-Schmidt kernels of one Arnoldi step  */
-    CT_PH_SMALL = 4,     /* the FP64 hybrid small solve                       */
+    CT_PH_SMALL = 4,     /* the hybrid small solve (FP64; double-float bidiagonalisation) */
     CT_PH_OTHER = 5,     /* first normalisation, x = x0 + W y, residual updates */
     CT_PH_COUNT = 6
 };
