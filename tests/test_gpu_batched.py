@@ -1,9 +1,11 @@
 """Batched solves (ct_batch / abba_solve): many uneven problems in one captured CUDA graph.
 
 Each problem in a batch runs the same kernels on the same data as its single-problem solve, so
-the iterates must agree with ab_gmres_hybrid / ba_gmres_hybrid (to rounding: the launch shapes
-chosen by the autotuner do not change any per-ray or per-pixel arithmetic) and, through them,
-with the FP64 oracle.
+at the same launch shapes the iterates must agree with ab_gmres_hybrid / ba_gmres_hybrid (to
+rounding: the batch caps the Gram-Schmidt passes at one block per SM, which only reorders their
+FP32 block sums on large problems) and, through them, with the FP64 oracle.  Launch shapes
+leave a ray's and a pixel's arithmetic unchanged except for the four-fold backprojector, whose
+view parts reorder each pixel's sum.
 """
 import numpy as np
 import pytest
